@@ -1,0 +1,122 @@
+"""The oracle's pins must catch plausible mistakes.  Each mutant below is a copy
+of the oracle's C source with one planted error (a dropped term, a flipped sign,
+a transposed operand, a missing factor), compiled on the CPU into a temporary
+library.  Every mutant must fail at least one of three pins that the real oracle
+passes: the exact 2x2 iterates (Sec. II.E), the printed 3x3 polynomials
+(Supplement E), and the trace and right-eigenvector residual of an unsymmetric
+problem (M a = E a, Sec. II.A)."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ORA = os.path.join(os.path.dirname(HERE), "oracle")
+
+MUTANTS = {
+    "drop_d_a_term": ("an[j] = lambda * g * (p[j] - d * a[j]);", "an[j] = lambda * g * (p[j]);"),
+    "flip_gap_sign": ("const T g = 1.0 / (theta[i] - theta[j]);",
+                      "const T g = 1.0 / (theta[j] - theta[i]);"),
+    "transpose_delta": ("for (int64_t j = 0; j < n; ++j) p[j] += dk[j] * akc;",
+                        "for (int64_t j = 0; j < n; ++j) p[j] += delta[k + j * n] * akc;"),
+    "eigenvalue_without_lambda": ("E[c] = theta[i] + lambda * d;", "E[c] = theta[i] + d;"),
+    "diagonal_not_pinned": ("an[j] = 1;  ", "an[j] = a[j] + lambda * d;  "),
+}
+
+
+def _build(tmp, name, old, new):
+    d = os.path.join(tmp, name)
+    os.makedirs(d)
+    for f in ("dpt_oracle.c", "dpt_oracle_body.inc", "dpt_oracle.h"):
+        shutil.copy(os.path.join(ORA, f), d)
+    body = open(os.path.join(d, "dpt_oracle_body.inc")).read()
+    assert old in body, name
+    open(os.path.join(d, "dpt_oracle_body.inc"), "w").write(body.replace(old, new))
+    so = os.path.join(d, "lib.so")
+    subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", so,
+                    os.path.join(d, "dpt_oracle.c"), "-lm"], check=True,
+                   capture_output=True)
+    lib = ctypes.CDLL(so)
+    P, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    lib.ora_step_r.argtypes = [i64, P, P, dbl, P, P, P]
+    return lib
+
+
+def _step(lib, th, D, lam, A):
+    n = len(th)
+    th = np.ascontiguousarray(th, float)
+    D = np.asfortranarray(D, float)
+    A = np.asfortranarray(A, float)
+    An = np.zeros((n, n), order="F")
+    E = np.zeros(n)
+    p = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    lib.ora_step_r(n, p(th), p(D), lam, p(A), p(An), p(E))
+    return An, E
+
+
+def _pins_pass(lib):
+    # 1. exact 2x2 iterates, column form [[1, -x], [x, 1]]
+    th2, D2 = np.array([0.0, 1.0]), np.array([[0.0, 1.0], [1.0, 0.0]])
+    A, x, lam = np.eye(2), 0.0, 0.3
+    for _ in range(10):
+        if not np.allclose(A, [[1.0, -x], [x, 1.0]], atol=1e-13):
+            return False
+        A, _ = _step(lib, th2, D2, lam, A)
+        x = lam * (x * x - 1.0)
+    # 2. trace invariant on a random unsymmetric 6x6 at the fixed point
+    rng = np.random.Generator(np.random.PCG64(1))
+    th = np.arange(6.0) + rng.uniform(-0.2, 0.2, 6)
+    D = rng.uniform(-1, 1, (6, 6))
+    A = np.eye(6)
+    for _ in range(200):
+        A, E = _step(lib, th, D, 0.05, A)
+    _, E = _step(lib, th, D, 0.05, A)
+    if not abs(E.sum() - (th.sum() + 0.05 * np.trace(D))) < 1e-10:
+        return False
+    # 2b. the columns are right eigenvectors: M A = A diag(E), M = diag(theta) + lam Delta
+    M = np.diag(th) + 0.05 * D
+    if not np.abs(M @ A - A * E[None, :]).max() < 1e-10:
+        return False
+    # 3. printed 3x3 polynomial P_1 at the multipliers of line 1
+    terms = []
+    for line in open(os.path.join(HERE, "golden", "poly_3x3.txt")):
+        if not line.startswith("#") and line.strip():
+            n, a, b, c = map(int, line.split())
+            if n == 1:
+                terms.append((a, b, c))
+    th3 = np.array([0.0, 1.0, 3.0])
+    D3 = np.array([[0.0, 1.0, 2.0], [1.0, 0.0, 3.0], [2.0, 3.0, 0.0]])
+    lam = 0.2
+    A = np.eye(3)
+    for _ in range(300):
+        A, _ = _step(lib, th3, D3, lam, A)
+    if not np.all(np.isfinite(A)):
+        return False
+    J = np.zeros((2, 2))
+    for q, k in enumerate((1, 2)):
+        Ap, Am = A.copy(), A.copy()
+        Ap[k, 0] += 1e-6
+        Am[k, 0] -= 1e-6
+        J[:, q] = (_step(lib, th3, D3, lam, Ap)[0][[1, 2], 0]
+                   - _step(lib, th3, D3, lam, Am)[0][[1, 2], 0]) / 2e-6
+    for mu in np.linalg.eigvals(J):
+        v = sum(c * lam**a * mu**b for a, b, c in terms)
+        s = sum(abs(c * lam**a * mu**b) for a, b, c in terms)
+        if abs(v) / s > 1e-8:
+            return False
+    return True
+
+
+def test_unmutated_copy_passes(tmp_path):
+    lib = _build(str(tmp_path), "original", "an[j] = 1;", "an[j] = 1;")
+    assert _pins_pass(lib)
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    old, new = MUTANTS[name]
+    lib = _build(str(tmp_path), name, old, new)
+    assert not _pins_pass(lib), name
