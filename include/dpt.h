@@ -1,0 +1,141 @@
+/* libdpt: dynamical perturbation theory (DPT) eigensolver for one GB300 GPU.
+ *
+ * Method: M. Kenmoe, M. Smerlak, A. Zadorin, "Dynamical perturbation theory for
+ * eigenvalue problems", arXiv:2002.12872.  For M = D + lambda * Delta with
+ * D = diag(theta) and simple unperturbed eigenvalues theta (Sec. II.B), the
+ * eigenvectors are the fixed points of the map of Eq. (dyn).  In the column
+ * convention used throughout this library (column i of A is eigenvector i; the
+ * paper stores it as row i and multiplies by Delta'):
+ *
+ *     A  <-  I + lambda * G o (Delta A - A diag(Delta A)),
+ *     G_ji = 1 / (theta_i - theta_j) for j != i,   G_ii = 0,
+ *     E  =  theta + lambda * diag(Delta A)          (read-out of Sec. II.B),
+ *
+ * iterated from A = I.  Every column keeps A_ii = 1 (the affine chart z^n = 1 of
+ * Sec. II.A).  The dominant-eigenvector form iterates one column, n* = argmax
+ * theta, with a matrix-vector product in place of the matrix product (the
+ * single-vector map of Eq. (single_line_dyn), Sec. II.H).
+ *
+ * Conventions for every entry point:
+ *   - Dense matrices are column-major with a leading dimension ld >= n.
+ *   - A pointer argument may point to device memory or to host memory (pinned or
+ *     pageable); the library checks each pointer with cudaPointerGetAttributes
+ *     and stages host buffers through device memory itself.  Host outputs are
+ *     complete when the call returns.
+ *   - The caller owns every input and output buffer.  Inputs are never modified.
+ *     Scratch memory comes from a per-device pool inside the library that grows
+ *     on demand and is kept between calls (dpt_release_workspace frees it).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  All device
+ *     work is ordered on it; the solve calls block until their results are ready.
+ *   - Errors are reported only through the returned dpt_status; nothing aborts
+ *     and nothing is thrown across this boundary.  On an error the outputs are
+ *     unspecified, except that *info (when non-NULL) is filled.
+ *   - Calls on different streams may run concurrently; each call uses its own
+ *     scratch block from the pool.
+ */
+#ifndef DPT_H
+#define DPT_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DPT_API __attribute__((visibility("default")))
+#else
+#define DPT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DPT_OK = 0,
+  DPT_PENDING = 1,            /* server request not finished yet */
+  DPT_ERR_ARG = -1,           /* invalid argument or non-finite input */
+  DPT_ERR_DEGENERATE = -2,    /* theta_i == theta_j for some i != j (Sec. II.B) */
+  DPT_ERR_MAXITER = -3,       /* max_iter reached before the tolerance */
+  DPT_ERR_DIVERGED = -4,      /* non-finite iterate, or residual growth: the orbit
+                                 cycles or escapes outside the convergence domain
+                                 (Sec. II.E) */
+  DPT_ERR_NOMEM = -5,         /* device or host allocation failed */
+  DPT_ERR_CUDA = -6,          /* a CUDA runtime call failed */
+  DPT_ERR_TIMEOUT = -7,       /* a bounded device-side wait expired */
+  DPT_ERR_UNSUPPORTED = -8    /* option combination not implemented */
+} dpt_status;
+
+typedef enum {
+  DPT_R64 = 0,    /* real: theta, Delta, A, E are double */
+  DPT_C128 = 1    /* complex: Delta, A, E are interleaved complex double (re, im);
+                     theta and lambda stay real */
+} dpt_dtype;
+
+typedef enum {
+  DPT_PREC_FP64 = 0,        /* every product in FP64 on the CUDA cores: the map of
+                               Eq. (dyn) applied literally */
+  DPT_PREC_MIXED_BF16 = 1   /* tensor-core products: each iteration multiplies Delta,
+                               split into up to three BF16 slices, by the BF16
+                               increment of A, with FP32 accumulation; A, the
+                               residual and the eigenvalues are carried in extended
+                               precision, so the iteration refines to the FP64
+                               fixed point */
+} dpt_prec;
+
+typedef struct {
+  double tol;              /* stop when max_i rho_i <= tol, where
+                              rho_i = ||M a_i - E_i a_i||_2 / (s ||a_i||_2),
+                              s = max|theta| + |lambda| max_j sum_k |Delta_jk|.
+                              Default 1e-12. */
+  int32_t max_iter;        /* maximum map applications (default 200) */
+  int32_t prec;            /* dpt_prec (default DPT_PREC_MIXED_BF16) */
+  int32_t epstein_nesbet;  /* nonzero: move lambda*diag(Delta) into theta first
+                              (the partition of Sec. II.H); same eigenpairs */
+  int32_t graph_iters;     /* iterations per captured CUDA graph replay between
+                              host convergence checks (default 4; 0 = no graph) */
+  int32_t max_slices;      /* BF16 slices of Delta in the mixed path, 1..3 (default 3) */
+  int32_t reserved;
+  double slice_tol;        /* mixed path: after an iteration whose largest increment
+                              |delta A| is below slice_tol, the next product uses one
+                              slice (default 1e-8) */
+} dpt_options;
+
+typedef struct {
+  int32_t iters;           /* map applications before the returned iterate */
+  int32_t slice_gemms;     /* mixed path: sum over iterations of the slices used */
+  double residual;         /* max_i rho_i of the returned iterate, as tracked by
+                              the iteration */
+  int32_t status;          /* dpt_status of the solve */
+  int32_t nstar;           /* dominant form: the eigenvector index used */
+  double seconds;          /* wall time of the call */
+} dpt_info;
+
+/* Fill *opt with the defaults listed above. */
+DPT_API void dpt_options_default(dpt_options* opt);
+
+/* Human-readable name of a status code (static string). */
+DPT_API const char* dpt_status_string(dpt_status s);
+
+/* Full spectrum: all n eigenpairs of M = diag(theta) + lambda * Delta.
+ *   n          matrix size, n >= 1
+ *   dtype      DPT_R64 or DPT_C128 (the latter with DPT_PREC_FP64 or MIXED_BF16)
+ *   theta      n doubles, pairwise distinct and finite
+ *   delta      n x n, column-major, leading dimension ld_delta >= n, finite
+ *   lambda     real perturbation strength
+ *   opt        options (NULL = defaults)
+ *   A_out      n x n output, column-major, ld_a >= n: column i is the eigenvector
+ *              continued from e_i, normalised so that A_out[i + i*ld_a] == 1
+ *   E_out      n outputs: E_i = theta_i + lambda (Delta a_i)_i
+ *   info       optional diagnostics
+ * Returns DPT_OK when the tolerance was met.  DPT_ERR_MAXITER / DPT_ERR_DIVERGED
+ * still write the last iterate and its eigenvalues.  Blocks until done. */
+DPT_API dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta,
+                          const void* delta, int64_t ld_delta, double lambda,
+                          const dpt_options* opt, void* A_out, int64_t ld_a,
+                          void* E_out, dpt_info* info, void* stream);
+
+/* Free the scratch pool of the current device (no solve may be running). */
+DPT_API void dpt_release_workspace(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

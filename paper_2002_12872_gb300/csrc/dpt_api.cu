@@ -1,0 +1,586 @@
+// libdpt C-ABI entry points and host runtime: argument validation, host/device
+// pointer staging, the per-device scratch pool, TMA descriptor encoding and the
+// iteration loop (CUDA-graph replays of several iterations between host checks).
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/dpt.h"
+#include "dpt_internal.h"
+
+namespace dpt {
+cudaError_t launch_check_finite(int n, const double* D, int64_t ldd, int cplx, IterState* st,
+                                cudaStream_t s);
+}
+
+using namespace dpt;
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Fail {
+  dpt_status st;
+};
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) throw Fail{DPT_ERR_CUDA};          \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// A block of device scratch memory plus the resources a solve needs with it.
+struct Block {
+  int dev = -1;
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  bool busy = false;
+  IterState* host_state = nullptr;   // pinned
+  cudaStream_t stream = nullptr;     // internal non-blocking stream
+  cudaEvent_t ev = nullptr;
+};
+
+std::mutex g_mu;
+std::vector<Block*> g_pool;
+
+Block* acquire(size_t bytes) {
+  int dev;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_mu);
+  Block* pick = nullptr;
+  for (Block* b : g_pool)
+    if (!b->busy && b->dev == dev && b->bytes >= bytes) { pick = b; break; }
+  if (!pick)
+    for (Block* b : g_pool)
+      if (!b->busy && b->dev == dev) { pick = b; break; }
+  if (!pick) {
+    pick = new Block();
+    pick->dev = dev;
+    if (cudaHostAlloc((void**)&pick->host_state, sizeof(IterState), cudaHostAllocDefault) !=
+            cudaSuccess ||
+        cudaStreamCreateWithFlags(&pick->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&pick->ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      delete pick;
+      throw Fail{DPT_ERR_NOMEM};
+    }
+    g_pool.push_back(pick);
+  }
+  if (pick->bytes < bytes) {
+    if (pick->ptr) cudaFree(pick->ptr);
+    pick->ptr = nullptr;
+    pick->bytes = 0;
+    if (cudaMalloc(&pick->ptr, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      throw Fail{DPT_ERR_NOMEM};
+    }
+    pick->bytes = bytes;
+  }
+  pick->busy = true;
+  return pick;
+}
+
+void release(Block* b) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  b->busy = false;
+}
+
+// Bump allocator over a scratch block (256-byte alignment).
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (size_t)round_up((int64_t)off, 256);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+template <class F>
+size_t measure(F&& f) {
+  Carve c{nullptr};
+  f(c);
+  return (size_t)round_up((int64_t)c.off, 256) + 256;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// 2-D BF16 tensor map: inner extent `inner` (contiguous), outer extent `outer`,
+// row pitch `pitch_elems`, box 64 x box_rows, 128-byte swizzle.
+CUtensorMap make_tmap_bf16(const void* base, uint64_t inner, uint64_t outer,
+                           uint64_t pitch_elems, uint32_t box_rows) {
+  CUtensorMap m;
+  auto fn = encode_fn();
+  if (!fn) throw Fail{DPT_ERR_CUDA};
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {pitch_elems * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Fail{DPT_ERR_CUDA};
+  return m;
+}
+
+dpt_status from_state(int s) {
+  switch (s) {
+    case ST_CONVERGED: return DPT_OK;
+    case ST_MAXITER: return DPT_ERR_MAXITER;
+    case ST_DIVERGED: return DPT_ERR_DIVERGED;
+    case ST_TIMEOUT: return DPT_ERR_TIMEOUT;
+    case ST_BADINPUT: return DPT_ERR_ARG;
+    default: return DPT_ERR_CUDA;
+  }
+}
+
+// Validates theta on the host: finite, pairwise distinct (after the optional
+// Epstein-Nesbet shift).  Returns the shifted copy.
+dpt_status host_theta(int64_t n, const double* theta, bool theta_dev, std::vector<double>& th) {
+  th.resize((size_t)n);
+  if (theta_dev) {
+    if (cudaMemcpy(th.data(), theta, sizeof(double) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return DPT_ERR_CUDA;
+  } else {
+    std::memcpy(th.data(), theta, sizeof(double) * n);
+  }
+  for (double v : th)
+    if (!std::isfinite(v)) return DPT_ERR_ARG;
+  return DPT_OK;
+}
+
+dpt_status check_distinct(const std::vector<double>& th) {
+  std::vector<double> s(th);
+  std::sort(s.begin(), s.end());
+  for (size_t q = 1; q < s.size(); ++q)
+    if (s[q] == s[q - 1]) return DPT_ERR_DEGENERATE;
+  return DPT_OK;
+}
+
+// Runs `iter` (which enqueues `per` iterations) as graph replays until the state
+// leaves ST_RUNNING.  graph_iters == 0: plain launches, one host check per chunk
+// of 4 iterations.
+template <class F>
+void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, F&& iter) {
+  cudaStream_t s = b->stream;
+  const int per = graph_iters > 0 ? graph_iters : 4;
+  cudaGraphExec_t exec = nullptr;
+  if (graph_iters > 0) {
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int q = 0; q < per; ++q) iter();
+    CK(cudaStreamEndCapture(s, &g));
+    cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) throw Fail{DPT_ERR_CUDA};
+  }
+  const int max_chunks = max_iter / per + 2;
+  try {
+    for (int c = 0; c < max_chunks; ++c) {
+      if (exec) {
+        CK(cudaGraphLaunch(exec, s));
+      } else {
+        for (int q = 0; q < per; ++q) iter();
+      }
+      CK(cudaMemcpyAsync(b->host_state, dst, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (b->host_state->status != ST_RUNNING) break;
+    }
+  } catch (...) {
+    if (exec) cudaGraphExecDestroy(exec);
+    throw;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+}
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double sec() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Full solve, mixed precision (real)
+// ---------------------------------------------------------------------------
+dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
+                                 const double* delta_in, bool delta_dev, int64_t ld_delta,
+                                 double lambda, const dpt_options& o, double* A_out,
+                                 bool a_dev, int64_t ld_a, double* E_out, bool e_dev,
+                                 dpt_info* info, cudaStream_t user) {
+  const int n = (int)n64;
+  const int ld = (int)round_up(n64, 64);
+  const int S = o.max_slices;
+  const int ntm = (n + 127) / 128, ntn = (n + 127) / 128;
+  auto layout = [&](Carve& c) {
+    c.take<IterState>(1);
+    c.take<double>(ld);                        // theta (shifted)
+    c.take<float>(ld); c.take<float>(ld);      // theta hi/lo
+    c.take<double>(ld); c.take<double>(ld);    // d, E
+    c.take<float>(ld); c.take<float>(ld);      // e_col, dprev_col
+    c.take<float>((size_t)3 * ntm * ld);       // column partials
+    c.take<float>((size_t)ntn * ld);           // row partials
+    c.take<float>((size_t)ld * n);             // Dt (row-major FP32)
+    c.take<__nv_bfloat16>((size_t)S * ld * n); // Dcat
+    for (int q = 0; q < 2; ++q) { c.take<float>((size_t)ld * n); c.take<float>((size_t)ld * n); }
+    for (int q = 0; q < 2; ++q) c.take<__nv_bfloat16>((size_t)ld * n);
+    c.take<float>((size_t)ld * n);             // L
+    if (!delta_dev) c.take<double>((size_t)ld * n);
+    if (!a_dev) c.take<double>((size_t)ld * n);
+  };
+  Block* b = acquire(measure(layout));
+  dpt_status ret = DPT_OK;
+  try {
+    Carve c{(char*)b->ptr};
+    IterState* st = c.take<IterState>(1);
+    double* thd = c.take<double>(ld);
+    float* thh = c.take<float>(ld);
+    float* thl = c.take<float>(ld);
+    double* d = c.take<double>(ld);
+    double* E = c.take<double>(ld);
+    float* e_col = c.take<float>(ld);
+    float* dprev = c.take<float>(ld);
+    float* part = c.take<float>((size_t)3 * ntm * ld);
+    float* rowpart = c.take<float>((size_t)ntn * ld);
+    float* Dt = c.take<float>((size_t)ld * n);
+    __nv_bfloat16* Dcat = c.take<__nv_bfloat16>((size_t)S * ld * n);
+    float *Ahi[2], *Alo[2];
+    for (int q = 0; q < 2; ++q) { Ahi[q] = c.take<float>((size_t)ld * n); Alo[q] = c.take<float>((size_t)ld * n); }
+    __nv_bfloat16* dtb[2];
+    for (int q = 0; q < 2; ++q) dtb[q] = c.take<__nv_bfloat16>((size_t)ld * n);
+    float* L = c.take<float>((size_t)ld * n);
+    const double* delta = delta_in;
+    int64_t ldd = ld_delta;
+    cudaStream_t s = b->stream;
+    CK(cudaEventRecord(b->ev, user));
+    CK(cudaStreamWaitEvent(s, b->ev, 0));
+    if (!delta_dev) {
+      double* Dd = c.take<double>((size_t)ld * n);
+      CK(cudaMemcpy2DAsync(Dd, sizeof(double) * ld, delta_in, sizeof(double) * ld_delta,
+                           sizeof(double) * n, n, cudaMemcpyHostToDevice, s));
+      delta = Dd;
+      ldd = ld;
+    }
+    double* Astage = a_dev ? A_out : c.take<double>((size_t)ld * n);
+    const int64_t lda_dev = a_dev ? ld_a : ld;
+
+    IterState h{};
+    h.status = ST_RUNNING;
+    h.max_iter = o.max_iter;
+    h.max_slices = S;
+    h.slices = S;
+    h.lam = lambda;
+    h.tol = o.tol;
+    h.slice_tol = o.slice_tol;
+    h.best = INFINITY;
+    double tm = 0;
+    for (double v : th) tm = std::max(tm, std::fabs(v));
+    h.theta_max = tm;
+    *b->host_state = h;
+    CK(cudaMemcpyAsync(st, b->host_state, sizeof(IterState), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(thd, th.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(dtb[0], 0, sizeof(__nv_bfloat16) * (size_t)ld * n * 2, s));
+    CK(launch_theta_ff(n, thd, thh, thl, s));
+    CK(launch_prep_delta(delta, ldd, n, ld, S, o.epstein_nesbet, Dt, Dcat, st, s));
+    CK(launch_iter0(delta, ldd, thd, lambda, n, ld, o.epstein_nesbet, Dt, Ahi[1], Alo[1],
+                    dtb[0], L, d, part, rowpart, st, s));
+    CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
+
+    const CUtensorMap tA = make_tmap_bf16(Dcat, (uint64_t)S * ld, n, (uint64_t)S * ld, 128);
+    const CUtensorMap tB0 = make_tmap_bf16(dtb[0], n, n, ld, 128);
+    const CUtensorMap tB1 = make_tmap_bf16(dtb[1], n, n, ld, 128);
+    CK(mixed_set_attributes());
+    GemmEpiParams p{};
+    p.n = n; p.ld = ld; p.ntm = ntm; p.lam = (float)lambda;
+    for (int q = 0; q < 2; ++q) { p.A_hi[q] = Ahi[q]; p.A_lo[q] = Alo[q]; p.dt[q] = dtb[q]; }
+    p.L = L; p.Dt = Dt; p.th_hi = thh; p.th_lo = thl; p.e_col = e_col; p.dprev_col = dprev;
+    p.part = part; p.st = st;
+    run_loop(b, st, o.graph_iters, o.max_iter, [&] {
+      CK(launch_gemm_epi(tA, tB0, tB1, p, s));
+      CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
+    });
+    CK(launch_finalize(n, ld, Ahi[0], Alo[0], Ahi[1], Alo[1], Astage, lda_dev, st, s));
+    if (!a_dev)
+      CK(cudaMemcpy2DAsync(A_out, sizeof(double) * ld_a, Astage, sizeof(double) * ld,
+                           sizeof(double) * n, n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(E_out, E, sizeof(double) * n,
+                       e_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(b->host_state, st, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const IterState& fs = *b->host_state;
+    ret = from_state(fs.status);
+    if (info) {
+      info->iters = fs.k;
+      info->slice_gemms = fs.slice_gemms;
+      info->residual = fs.rho;
+      info->status = ret;
+    }
+    CK(cudaEventRecord(b->ev, s));
+    CK(cudaStreamWaitEvent(user, b->ev, 0));
+  } catch (Fail f) {
+    cudaStreamSynchronize(b->stream);
+    ret = f.st;
+  }
+  release(b);
+  return ret;
+}
+
+// ---------------------------------------------------------------------------
+// Full solve, plain FP64 (real or complex)
+// ---------------------------------------------------------------------------
+dpt_status solve_full_fp64(int64_t n64, bool cplx, const std::vector<double>& th,
+                           const double* delta_in, bool delta_dev, int64_t ld_delta,
+                           double lambda, const dpt_options& o, double* A_out, bool a_dev,
+                           int64_t ld_a, double* E_out, bool e_dev, dpt_info* info,
+                           cudaStream_t user) {
+  const int n = (int)n64;
+  const int ld = (int)round_up(n64, 64);
+  const int w = cplx ? 2 : 1;   // doubles per element
+  const bool copy_delta = !delta_dev || o.epstein_nesbet;
+  auto layout = [&](Carve& c) {
+    c.take<IterState>(1);
+    c.take<double>(ld);                          // theta
+    c.take<double>((size_t)w * ld);              // E
+    for (int q = 0; q < 2; ++q) c.take<double>((size_t)w * ld * n);   // A ping-pong
+    c.take<double>((size_t)w * ld * n);          // P
+    if (copy_delta) c.take<double>((size_t)w * ld * n);
+  };
+  Block* b = acquire(measure(layout));
+  dpt_status ret = DPT_OK;
+  try {
+    Carve c{(char*)b->ptr};
+    IterState* st = c.take<IterState>(1);
+    double* thd = c.take<double>(ld);
+    double* E = c.take<double>((size_t)w * ld);
+    double* A[2];
+    for (int q = 0; q < 2; ++q) A[q] = c.take<double>((size_t)w * ld * n);
+    double* P = c.take<double>((size_t)w * ld * n);
+    cudaStream_t s = b->stream;
+    CK(cudaEventRecord(b->ev, user));
+    CK(cudaStreamWaitEvent(s, b->ev, 0));
+    const double* Dl = delta_in;
+    int64_t ldd = ld_delta;
+    if (copy_delta) {
+      double* Dd = c.take<double>((size_t)w * ld * n);
+      CK(cudaMemcpy2DAsync(Dd, sizeof(double) * w * ld, delta_in, sizeof(double) * w * ld_delta,
+                           sizeof(double) * w * n, n,
+                           delta_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      if (o.epstein_nesbet) {
+        const double zero[2] = {0.0, 0.0};
+        for (int64_t q = 0; q < n; ++q)   // zero diag(Delta): theta was shifted on the host
+          CK(cudaMemcpyAsync(Dd + (size_t)w * (q * ld + q), zero, sizeof(double) * w,
+                             cudaMemcpyHostToDevice, s));
+      }
+      Dl = Dd;
+      ldd = ld;
+    }
+    IterState h{};
+    h.status = ST_RUNNING;
+    h.max_iter = o.max_iter;
+    h.lam = lambda;
+    h.tol = o.tol;
+    h.best = INFINITY;
+    double tm = 0;
+    for (double v : th) tm = std::max(tm, std::fabs(v));
+    h.theta_max = tm;
+    *b->host_state = h;
+    CK(cudaMemcpyAsync(st, b->host_state, sizeof(IterState), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(thd, th.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CK(launch_check_finite(n, Dl, ldd, cplx, st, s));
+    CK(launch_fp64_init(n, ld, cplx, A[0], s));
+    // iteration 0 outside the graph (it also forms the residual scale)
+    auto one = [&](int first, int cur) {
+      if (cplx) CK(launch_gemm_c128(n, Dl, ldd, A[cur], ld, P, st, s));
+      else CK(launch_gemm_f64(n, Dl, ldd, A[cur], ld, P, st, s));
+      CK(launch_epi_f64(n, ld, cplx, thd, lambda, P, A[cur], A[cur ^ 1], Dl, ldd, E, st, first, s));
+    };
+    one(1, 0);
+    CK(cudaMemcpyAsync(b->host_state, st, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (b->host_state->status == ST_RUNNING) {
+      // Two-iteration unit so that buffer parity is fixed inside the graph.
+      dpt_options oo = o;
+      const int per = std::max(2, (o.graph_iters + 1) / 2 * 2);
+      oo.graph_iters = o.graph_iters > 0 ? per : 0;
+      int parity = 1;   // A_1 lives in buffer 1
+      run_loop(b, st, oo.graph_iters, o.max_iter, [&] {
+        one(0, parity);
+        parity ^= 1;
+      });
+    }
+    const int cur = b->host_state->k & 1;
+    if (a_dev) {
+      CK(cudaMemcpy2DAsync(A_out, sizeof(double) * w * ld_a, A[cur], sizeof(double) * w * ld,
+                           sizeof(double) * w * n, n, cudaMemcpyDeviceToDevice, s));
+    } else {
+      CK(cudaMemcpy2DAsync(A_out, sizeof(double) * w * ld_a, A[cur], sizeof(double) * w * ld,
+                           sizeof(double) * w * n, n, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaMemcpyAsync(E_out, E, sizeof(double) * w * n,
+                       e_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(b->host_state, st, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const IterState& fs = *b->host_state;
+    ret = from_state(fs.status);
+    if (info) {
+      info->iters = fs.k;
+      info->slice_gemms = 0;
+      info->residual = fs.rho;
+      info->status = ret;
+    }
+    CK(cudaEventRecord(b->ev, s));
+    CK(cudaStreamWaitEvent(user, b->ev, 0));
+  } catch (Fail f) {
+    cudaStreamSynchronize(b->stream);
+    ret = f.st;
+  }
+  release(b);
+  return ret;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void dpt_options_default(dpt_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-12;
+  o->max_iter = 200;
+  o->prec = DPT_PREC_MIXED_BF16;
+  o->epstein_nesbet = 0;
+  o->graph_iters = 4;
+  o->max_slices = 3;
+  o->slice_tol = 1e-8;
+}
+
+const char* dpt_status_string(dpt_status s) {
+  switch (s) {
+    case DPT_OK: return "DPT_OK";
+    case DPT_PENDING: return "DPT_PENDING";
+    case DPT_ERR_ARG: return "DPT_ERR_ARG";
+    case DPT_ERR_DEGENERATE: return "DPT_ERR_DEGENERATE";
+    case DPT_ERR_MAXITER: return "DPT_ERR_MAXITER";
+    case DPT_ERR_DIVERGED: return "DPT_ERR_DIVERGED";
+    case DPT_ERR_NOMEM: return "DPT_ERR_NOMEM";
+    case DPT_ERR_CUDA: return "DPT_ERR_CUDA";
+    case DPT_ERR_TIMEOUT: return "DPT_ERR_TIMEOUT";
+    case DPT_ERR_UNSUPPORTED: return "DPT_ERR_UNSUPPORTED";
+  }
+  return "DPT_UNKNOWN";
+}
+
+dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const void* delta,
+                          int64_t ld_delta, double lambda, const dpt_options* opt,
+                          void* A_out, int64_t ld_a, void* E_out, dpt_info* info,
+                          void* stream) {
+  Timer timer;
+  if (info) { std::memset(info, 0, sizeof(*info)); info->status = DPT_ERR_ARG; info->nstar = -1; }
+  dpt_options o;
+  dpt_options_default(&o);
+  if (opt) o = *opt;
+  auto done = [&](dpt_status st) {
+    if (info) { info->status = st; info->seconds = timer.sec(); }
+    return st;
+  };
+  if (n < 1 || n > (1 << 20) || !theta || !delta || !A_out || !E_out || ld_delta < n ||
+      ld_a < n || !std::isfinite(lambda) || !(o.tol > 0) || o.max_iter < 0 ||
+      (dtype != DPT_R64 && dtype != DPT_C128))
+    return done(DPT_ERR_ARG);
+  if (o.prec != DPT_PREC_FP64 && o.prec != DPT_PREC_MIXED_BF16) return done(DPT_ERR_ARG);
+  if (o.max_slices < 1 || o.max_slices > 3) return done(DPT_ERR_ARG);
+  if (o.prec == DPT_PREC_MIXED_BF16 && dtype == DPT_C128) return done(DPT_ERR_UNSUPPORTED);
+  try {
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool th_dev = is_device_ptr(theta), d_dev = is_device_ptr(delta),
+               a_dev = is_device_ptr(A_out), e_dev = is_device_ptr(E_out);
+    std::vector<double> th;
+    dpt_status st = host_theta(n, theta, th_dev, th);
+    if (st != DPT_OK) return done(st);
+    if (o.epstein_nesbet) {
+      // theta <- theta + lambda diag(Delta)  (Sec. II.H partition)
+      const int w = dtype == DPT_C128 ? 2 : 1;
+      std::vector<double> dg((size_t)w * n);
+      for (int64_t q = 0; q < n; ++q) {
+        const double* src = (const double*)delta + (size_t)w * (q * ld_delta + q);
+        if (d_dev) CK(cudaMemcpy(&dg[(size_t)w * q], src, sizeof(double) * w, cudaMemcpyDeviceToHost));
+        else std::memcpy(&dg[(size_t)w * q], src, sizeof(double) * w);
+      }
+      for (int64_t q = 0; q < n; ++q) {
+        if (w == 2 && dg[2 * q + 1] != 0.0) return done(DPT_ERR_UNSUPPORTED);  // theta stays real
+        th[q] += lambda * dg[(size_t)w * q];
+      }
+    }
+    st = check_distinct(th);
+    if (st != DPT_OK) return done(st);
+    if (o.prec == DPT_PREC_MIXED_BF16)
+      st = solve_full_mixed_real(n, th, (const double*)delta, d_dev, ld_delta, lambda, o,
+                                 (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info, s);
+    else
+      st = solve_full_fp64(n, dtype == DPT_C128, th, (const double*)delta, d_dev, ld_delta,
+                           lambda, o, (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info,
+                           s);
+    return done(st);
+  } catch (Fail f) {
+    return done(f.st);
+  } catch (...) {
+    return done(DPT_ERR_CUDA);
+  }
+}
+
+void dpt_release_workspace(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = -1;
+  cudaGetDevice(&dev);
+  std::vector<Block*> keep;
+  for (Block* b : g_pool) {
+    if (b->dev == dev && !b->busy) {
+      if (b->ptr) cudaFree(b->ptr);
+      if (b->host_state) cudaFreeHost(b->host_state);
+      if (b->stream) cudaStreamDestroy(b->stream);
+      if (b->ev) cudaEventDestroy(b->ev);
+      delete b;
+    } else {
+      keep.push_back(b);
+    }
+  }
+  g_pool.swap(keep);
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Internal declarations shared by the libdpt host runtime and its kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dpt {
+
+enum : int {
+  ST_RUNNING = 0,
+  ST_CONVERGED = 1,
+  ST_BADINPUT = -1,
+  ST_MAXITER = -3,
+  ST_DIVERGED = -4,
+  ST_TIMEOUT = -7,
+};
+
+// Per-solve iteration state, resident in device memory.  The control kernels
+// advance it; every iteration kernel reads `status` first and returns at once
+// once the solve has finished, so a captured graph of several iterations can be
+// replayed past convergence without changing the result.
+struct IterState {
+  int k;               // index of the current iterate A_k
+  int status;          // ST_*
+  int slices;          // BF16 slices of Delta used by the next product
+  int cur;             // ping-pong index of the buffers holding A_k
+  int grown;           // consecutive iterations with residual > 10 x best
+  int max_iter;
+  int max_slices;
+  int slice_gemms;     // running sum of slices used
+  unsigned blocks_done;
+  unsigned rho_bits;   // atomicMax scratch: max_i sqrt(|R_i|^2 / |a_i|^2)
+  unsigned dmax_bits;  // atomicMax scratch: max |delta A| of the last update
+  unsigned row_bits;   // atomicMax scratch: max_j sum_k |Delta_jk|
+  unsigned bad_input;  // nonzero when a non-finite input value was seen
+  unsigned timeout;    // nonzero when a bounded wait expired
+  double s;            // residual scale max|theta| + |lambda| max_j sum_k |Delta_jk|
+  double theta_max;    // max_j |theta_j|
+  double lam;
+  double tol;
+  double slice_tol;
+  double rho;          // normalised max residual of A_k
+  double best;
+  double rho_last;
+};
+
+// Arguments of the tensor-core iteration kernel (mixed path, real).
+struct GemmEpiParams {
+  int n;               // matrix size
+  int ld;              // padded leading dimension of every n x n work array (multiple of 64)
+  int ntm;             // number of 128-row tiles
+  float lam;
+  float* A_hi[2];      // float-float iterate, column-major, ping-pong by iteration parity
+  float* A_lo[2];
+  __nv_bfloat16* dt[2];   // BF16 increments, column-major (GEMM B operand), ping-pong
+  float* L;            // carried remainder, column-major
+  const float* Dt;     // Delta in FP32, row-major (Dt[i*ld + j] = Delta_ij)
+  const float* th_hi;  // theta as float-float
+  const float* th_lo;
+  const float* e_col;      // e_k = diag(Delta dt_{k-1})
+  const float* dprev_col;  // d_{k-1}
+  float* part;         // column partials [3][ntm][ld]
+  IterState* st;
+};
+
+int mixed_smem_bytes();
+cudaError_t mixed_set_attributes();   // once per device, before any capture
+cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int nslices,
+                              int en, float* Dt, __nv_bfloat16* Dcat, IterState* st,
+                              cudaStream_t s);
+cudaError_t launch_theta_ff(int n, const double* th, float* hi, float* lo, cudaStream_t s);
+cudaError_t launch_iter0(const double* delta, int64_t ld_in, const double* theta, double lam,
+                         int n, int ld, int en, const float* Dt, float* Ahi1, float* Alo1,
+                         __nv_bfloat16* dt0, float* L, double* d, float* part, float* rowpart,
+                         IterState* st, cudaStream_t s);
+cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
+                        const double* theta, double* d, double* E, float* e_col,
+                        float* dprev_col, IterState* st, cudaStream_t s);
+cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
+                            const CUtensorMap& tmB1, const GemmEpiParams& p, cudaStream_t s);
+cudaError_t launch_finalize(int n, int ld, const float* Ahi0, const float* Alo0,
+                            const float* Ahi1, const float* Alo1, double* Aout, int64_t ld_a,
+                            const IterState* st, cudaStream_t s);
+
+// Plain FP64 path (real and complex)
+cudaError_t launch_fp64_init(int n, int ld, int cplx, void* A0, cudaStream_t s);
+cudaError_t launch_gemm_f64(int n, const double* Dl, int64_t ldd, const double* A, int ld,
+                            double* P, const IterState* st, cudaStream_t s);
+cudaError_t launch_gemm_c128(int n, const double* Dl, int64_t ldd, const double* A, int ld,
+                             double* P, const IterState* st, cudaStream_t s);
+cudaError_t launch_epi_f64(int n, int ld, int cplx, const double* theta, double lam,
+                           const double* P, const double* Acur, double* Anext,
+                           const double* Dl, int64_t ldd, double* E, IterState* st,
+                           int first, cudaStream_t s);
+
+}  // namespace dpt

@@ -1,0 +1,190 @@
+"""Python binding of libdpt (C ABI declared in include/dpt.h).
+
+Argument marshalling only: every step of a solve runs in the CUDA library.
+Inputs may be torch tensors (CUDA or CPU) or NumPy arrays; matrices follow the
+mathematical indexing Delta[j, k] and are handed to the library in column-major
+order (a tensor whose strides are already (1, ld) is passed without a copy).
+Outputs are returned as column-major views: A[:, i] is eigenvector i.
+
+There is no CPU fallback: if libdpt.so is missing or the GPU is absent the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdpt.so")
+
+OK, PENDING = 0, 1
+STATUS = {0: "OK", 1: "PENDING", -1: "ERR_ARG", -2: "ERR_DEGENERATE", -3: "ERR_MAXITER",
+          -4: "ERR_DIVERGED", -5: "ERR_NOMEM", -6: "ERR_CUDA", -7: "ERR_TIMEOUT",
+          -8: "ERR_UNSUPPORTED"}
+R64, C128 = 0, 1
+PREC = {"fp64": 0, "mixed": 1, "bf16": 1}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("epstein_nesbet", ctypes.c_int32),
+                ("graph_iters", ctypes.c_int32), ("max_slices", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("slice_tol", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("slice_gemms", ctypes.c_int32),
+                ("residual", ctypes.c_double), ("status", ctypes.c_int32),
+                ("nstar", ctypes.c_int32), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "slice_gemms": self.slice_gemms,
+                "residual": self.residual, "status": STATUS.get(self.status, str(self.status)),
+                "code": self.status, "nstar": self.nstar, "seconds": self.seconds}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdpt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -m paper_2002_12872_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        L.dpt_options_default.argtypes = [ctypes.POINTER(Options)]
+        L.dpt_options_default.restype = None
+        L.dpt_status_string.argtypes = [ctypes.c_int]
+        L.dpt_status_string.restype = ctypes.c_char_p
+        L.dpt_solve_full.argtypes = [i64, ctypes.c_int, P, P, i64, dbl,
+                                     ctypes.POINTER(Options), P, i64, P,
+                                     ctypes.POINTER(Info), P]
+        L.dpt_solve_full.restype = ctypes.c_int
+        L.dpt_release_workspace.argtypes = []
+        L.dpt_release_workspace.restype = None
+        _lib = L
+    return _lib
+
+
+def options(**kw) -> Options:
+    o = Options()
+    lib().dpt_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = PREC[v]
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def status_string(code: int) -> str:
+    return lib().dpt_status_string(int(code)).decode()
+
+
+# ---------------------------------------------------------------------------
+# tensor helpers
+# ---------------------------------------------------------------------------
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _vec_ptr(x, dtype):
+    """(pointer, keepalive) of a contiguous 1-D buffer."""
+    if _is_torch(x):
+        import torch
+        t = x.to(dtype=getattr(torch, dtype)).contiguous()
+        return t.data_ptr(), t
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, a
+
+
+def _colmajor(x, cplx):
+    """(pointer, ld, keepalive) of a matrix in column-major memory."""
+    if _is_torch(x):
+        import torch
+        t = x.to(dtype=torch.complex128 if cplx else torch.float64)
+        n0, n1 = t.shape
+        if t.stride(0) == 1 and t.stride(1) >= n0:
+            return t.data_ptr(), t.stride(1), t
+        c = t.t().contiguous()           # memory = columns of t
+        return c.data_ptr(), n0, c
+    a = np.asfortranarray(x, dtype=np.complex128 if cplx else np.float64)
+    return a.ctypes.data, a.shape[0], a
+
+
+def _empty_colmajor(n, like, cplx):
+    if _is_torch(like):
+        import torch
+        dt = torch.complex128 if cplx else torch.float64
+        return torch.empty((n, n), dtype=dt, device=like.device).t()
+    return np.empty((n, n), dtype=np.complex128 if cplx else np.float64, order="F")
+
+
+def _empty_vec(n, like, cplx):
+    if _is_torch(like):
+        import torch
+        dt = torch.complex128 if cplx else torch.float64
+        return torch.empty((n,), dtype=dt, device=like.device)
+    return np.empty(n, dtype=np.complex128 if cplx else np.float64)
+
+
+def _ptr(x):
+    return x.data_ptr() if _is_torch(x) else x.ctypes.data
+
+
+def _stream_of(x, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if _is_torch(x) and x.is_cuda:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _iscomplex(x) -> bool:
+    if _is_torch(x):
+        return x.is_complex()
+    return np.iscomplexobj(x)
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
+               epstein_nesbet=False, graph_iters=None, max_slices=None, slice_tol=None,
+               A_out=None, E_out=None, stream=None, check=True):
+    """All eigenpairs of M = diag(theta) + lam * Delta by the DPT map (dpt_solve_full).
+
+    Returns (A, E, info): A[:, i] is eigenvector i with A[i, i] = 1 and
+    E[i] = theta[i] + lam * (Delta A)[i, i].  With check=True a status other than
+    OK raises RuntimeError (the outputs are still returned via the exception's
+    ``result`` attribute)."""
+    cplx = _iscomplex(delta)
+    n = int(theta.shape[0])
+    th_ptr, th_keep = _vec_ptr(theta, "float64")
+    d_ptr, ldd, d_keep = _colmajor(delta, cplx)
+    A = _empty_colmajor(n, delta, cplx) if A_out is None else A_out
+    E = _empty_vec(n, delta, cplx) if E_out is None else E_out
+    lda = A.stride(1) if _is_torch(A) else A.strides[1] // A.itemsize
+    o = options(tol=tol, max_iter=max_iter, prec=prec, epstein_nesbet=int(bool(epstein_nesbet)),
+                graph_iters=graph_iters, max_slices=max_slices, slice_tol=slice_tol)
+    info = Info()
+    st = lib().dpt_solve_full(n, C128 if cplx else R64, th_ptr, d_ptr, ldd, float(lam),
+                              ctypes.byref(o), _ptr(A), lda, _ptr(E), ctypes.byref(info),
+                              _stream_of(delta, stream))
+    res = (A, E, info.as_dict())
+    if check and st != OK:
+        err = RuntimeError(f"dpt_solve_full: {status_string(st)}")
+        err.result = res
+        raise err
+    return res
+
+
+def release_workspace():
+    lib().dpt_release_workspace()

@@ -1,0 +1,67 @@
+"""Host-side checks of the C ABI: the library builds and loads, exports every
+symbol that include/*.h declares, and rejects invalid arguments before any GPU
+work (no compute call is made here)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2002_12872_gb300 import build, dpt
+    build.build()
+    return dpt.lib()
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        for m in re.finditer(r"DPT_API\s+[\w\s\*]*?\b(dpt_\w+)\s*\(", open(h).read()):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "dpt_solve_full" in names
+    for nm in names:
+        assert hasattr(lib, nm), nm
+
+
+def test_defaults_and_status_strings(lib):
+    from paper_2002_12872_gb300 import dpt
+    o = dpt.options()
+    assert o.tol == 1e-12 and o.max_iter == 200 and o.prec == 1 and o.max_slices == 3
+    assert dpt.status_string(-2) == "DPT_ERR_DEGENERATE"
+    assert dpt.status_string(0) == "DPT_OK"
+
+
+def test_invalid_arguments_rejected_without_gpu(lib):
+    from paper_2002_12872_gb300 import dpt
+    info = dpt.Info()
+    th = np.zeros(4)
+    d = np.zeros((4, 4), order="F")
+    A = np.zeros((4, 4), order="F")
+    E = np.zeros(4)
+    p = lambda a: a.ctypes.data
+    o = dpt.options()
+    # n < 1
+    assert lib.dpt_solve_full(0, 0, p(th), p(d), 4, 0.1, ctypes.byref(o), p(A), 4, p(E),
+                              ctypes.byref(info), None) == -1
+    # ld_delta < n
+    assert lib.dpt_solve_full(4, 0, p(th), p(d), 3, 0.1, ctypes.byref(o), p(A), 4, p(E),
+                              ctypes.byref(info), None) == -1
+    # null pointers
+    assert lib.dpt_solve_full(4, 0, None, p(d), 4, 0.1, ctypes.byref(o), p(A), 4, p(E),
+                              ctypes.byref(info), None) == -1
+    # bad option values
+    o2 = dpt.options(max_slices=4)
+    assert lib.dpt_solve_full(4, 0, p(th), p(d), 4, 0.1, ctypes.byref(o2), p(A), 4, p(E),
+                              ctypes.byref(info), None) == -1
+    assert info.status == -1
