@@ -92,7 +92,8 @@ typedef struct {
   int32_t graph_iters;     /* iterations per captured CUDA graph replay between
                               host convergence checks (default 4; 0 = no graph) */
   int32_t max_slices;      /* BF16 slices of Delta in the mixed path, 1..3 (default 3) */
-  int32_t reserved;
+  int32_t profile;         /* nonzero: time every product kernel with CUDA events on
+                              the stream it runs on (reported in dpt_info) */
   double slice_tol;        /* mixed path: after an iteration whose largest increment
                               |delta A| is below slice_tol, the next product uses one
                               slice (default 1e-8) */
@@ -106,6 +107,10 @@ typedef struct {
   int32_t status;          /* dpt_status of the solve */
   int32_t nstar;           /* dominant form: the eigenvector index used */
   double seconds;          /* wall time of the call */
+  int32_t launches;        /* kernels this call launched (graph nodes included) */
+  int32_t product_launches;  /* product kernels that did work (one per iteration) */
+  double product_ms;       /* with opt->profile: summed device time of those
+                              product kernels, else 0 */
 } dpt_info;
 
 /* Fill *opt with the defaults listed above. */

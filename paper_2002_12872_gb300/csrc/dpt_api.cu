@@ -190,18 +190,60 @@ dpt_status check_distinct(const std::vector<double>& th) {
   return DPT_OK;
 }
 
-// Runs `iter` (which enqueues `per` iterations) as graph replays until the state
-// leaves ST_RUNNING.  graph_iters == 0: plain launches, one host check per chunk
-// of 4 iterations.
+// Optional per-launch timing of the product kernels: an event pair around the
+// product launch of every iteration slot (recorded into the captured graph).
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  double ms = 0.0;
+  int live = 0;       // product launches that did work
+  int launches = 0;   // every kernel launch (graph nodes included)
+  void make(int slots) {
+    if (!on) return;
+    ev.resize(2 * slots);
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+  }
+  // External records become event-record nodes when the stream is being captured
+  // (a plain record there would only express a capture dependency).
+  static void record(cudaEvent_t e, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs == cudaStreamCaptureStatusActive)
+      CK(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    else
+      CK(cudaEventRecord(e, s));
+  }
+  void before(int q, cudaStream_t s) { if (on) record(ev[2 * q], s); }
+  void after(int q, cudaStream_t s) { if (on) record(ev[2 * q + 1], s); }
+  void collect(int nlive) {
+    live += nlive;
+    if (!on) return;
+    for (int q = 0; q < nlive; ++q) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, ev[2 * q], ev[2 * q + 1]));
+      ms += t;
+    }
+  }
+  ~Prof() {
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+};
+
+// Runs `iter(q)` (which enqueues iteration slot q: one product launch and its
+// epilogue / control launches, `kernels_per_iter` in all) `per` times per chunk,
+// as CUDA-graph replays when graph_iters > 0, until the device state leaves
+// ST_RUNNING.  One small device-to-host read of the state per chunk.
 template <class F>
-void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, F&& iter) {
+void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kernels_per_iter,
+              Prof& prof, F&& iter) {
   cudaStream_t s = b->stream;
   const int per = graph_iters > 0 ? graph_iters : 4;
+  prof.make(per);
   cudaGraphExec_t exec = nullptr;
   if (graph_iters > 0) {
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    for (int q = 0; q < per; ++q) iter();
+    for (int q = 0; q < per; ++q) iter(q);
     CK(cudaStreamEndCapture(s, &g));
     cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
@@ -210,14 +252,18 @@ void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, F&& iter)
   const int max_chunks = max_iter / per + 2;
   try {
     for (int c = 0; c < max_chunks; ++c) {
+      const int k0 = b->host_state->k;
       if (exec) {
         CK(cudaGraphLaunch(exec, s));
       } else {
-        for (int q = 0; q < per; ++q) iter();
+        for (int q = 0; q < per; ++q) iter(q);
       }
+      prof.launches += per * kernels_per_iter;
       CK(cudaMemcpyAsync(b->host_state, dst, sizeof(IterState), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
-      if (b->host_state->status != ST_RUNNING) break;
+      const bool running = b->host_state->status == ST_RUNNING;
+      prof.collect(running ? per : std::max(0, b->host_state->k - k0 + 1));
+      if (!running) break;
     }
   } catch (...) {
     if (exec) cudaGraphExecDestroy(exec);
@@ -242,7 +288,9 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
                                  bool a_dev, int64_t ld_a, double* E_out, bool e_dev,
                                  dpt_info* info, cudaStream_t user) {
   const int n = (int)n64;
-  const int ld = (int)round_up(n64, 64);
+  // a multiple of the 128-row tile: the epilogue's vector accesses cover whole
+  // tiles, so every row of every tile must lie inside its own column
+  const int ld = (int)round_up(n64, 128);
   const int S = o.max_slices;
   const int ntm = (n + 127) / 128, ntn = (n + 127) / 128;
   auto layout = [&](Carve& c) {
@@ -251,10 +299,9 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     c.take<float>(ld); c.take<float>(ld);      // theta hi/lo
     c.take<double>(ld); c.take<double>(ld);    // d, E
     c.take<float>(ld); c.take<float>(ld);      // e_col, dprev_col
-    c.take<float>((size_t)3 * ntm * ld);       // column partials
+    c.take<float>((size_t)4 * ntm * ld);       // column partials
     c.take<float>((size_t)ntn * ld);           // row partials
-    c.take<float>((size_t)ld * n);             // Dt (row-major FP32)
-    c.take<__nv_bfloat16>((size_t)S * ld * n); // Dcat
+    c.take<__nv_bfloat16>((size_t)3 * ld * n); // Dcat (three BF16 slices)
     for (int q = 0; q < 2; ++q) { c.take<float>((size_t)ld * n); c.take<float>((size_t)ld * n); }
     for (int q = 0; q < 2; ++q) c.take<__nv_bfloat16>((size_t)ld * n);
     c.take<float>((size_t)ld * n);             // L
@@ -273,10 +320,9 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     double* E = c.take<double>(ld);
     float* e_col = c.take<float>(ld);
     float* dprev = c.take<float>(ld);
-    float* part = c.take<float>((size_t)3 * ntm * ld);
+    float* part = c.take<float>((size_t)4 * ntm * ld);
     float* rowpart = c.take<float>((size_t)ntn * ld);
-    float* Dt = c.take<float>((size_t)ld * n);
-    __nv_bfloat16* Dcat = c.take<__nv_bfloat16>((size_t)S * ld * n);
+    __nv_bfloat16* Dcat = c.take<__nv_bfloat16>((size_t)3 * ld * n);
     float *Ahi[2], *Alo[2];
     for (int q = 0; q < 2; ++q) { Ahi[q] = c.take<float>((size_t)ld * n); Alo[q] = c.take<float>((size_t)ld * n); }
     __nv_bfloat16* dtb[2];
@@ -314,24 +360,34 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     CK(cudaMemcpyAsync(thd, th.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(dtb[0], 0, sizeof(__nv_bfloat16) * (size_t)ld * n * 2, s));
     CK(launch_theta_ff(n, thd, thh, thl, s));
-    CK(launch_prep_delta(delta, ldd, n, ld, S, o.epstein_nesbet, Dt, Dcat, st, s));
-    CK(launch_iter0(delta, ldd, thd, lambda, n, ld, o.epstein_nesbet, Dt, Ahi[1], Alo[1],
+    CK(launch_prep_delta(delta, ldd, n, ld, o.epstein_nesbet, Dcat, st, s));
+    CK(launch_iter0(delta, ldd, thh, thl, lambda, n, ld, o.epstein_nesbet, Dcat, Ahi[1], Alo[1],
                     dtb[0], L, d, part, rowpart, st, s));
     CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
 
-    const CUtensorMap tA = make_tmap_bf16(Dcat, (uint64_t)S * ld, n, (uint64_t)S * ld, 128);
-    const CUtensorMap tB0 = make_tmap_bf16(dtb[0], n, n, ld, 128);
-    const CUtensorMap tB1 = make_tmap_bf16(dtb[1], n, n, ld, 128);
+    const CUtensorMap tA = make_tmap_bf16(Dcat, (uint64_t)3 * ld, n, (uint64_t)3 * ld, 128);
+    const CUtensorMap tB0 = make_tmap_bf16(dtb[0], n, n, ld, mixed_tile_n());
+    const CUtensorMap tB1 = make_tmap_bf16(dtb[1], n, n, ld, mixed_tile_n());
     CK(mixed_set_attributes());
     GemmEpiParams p{};
     p.n = n; p.ld = ld; p.ntm = ntm; p.lam = (float)lambda;
     for (int q = 0; q < 2; ++q) { p.A_hi[q] = Ahi[q]; p.A_lo[q] = Alo[q]; p.dt[q] = dtb[q]; }
-    p.L = L; p.Dt = Dt; p.th_hi = thh; p.th_lo = thl; p.e_col = e_col; p.dprev_col = dprev;
+    p.L = L; p.Dcat = Dcat; p.cat_ld = (int64_t)3 * ld; p.th_hi = thh; p.th_lo = thl; p.e_col = e_col; p.dprev_col = dprev;
     p.part = part; p.st = st;
-    run_loop(b, st, o.graph_iters, o.max_iter, [&] {
-      CK(launch_gemm_epi(tA, tB0, tB1, p, s));
-      CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
-    });
+    // the state read after iteration 0 seeds the per-chunk iteration count
+    CK(cudaMemcpyAsync(b->host_state, st, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    Prof prof;
+    prof.on = o.profile != 0;
+    prof.launches = 4;   // theta split, Delta preparation, iteration 0, control
+    if (b->host_state->status == ST_RUNNING)
+      run_loop(b, st, o.graph_iters, o.max_iter, 2, prof, [&](int q) {
+        prof.before(q, s);
+        CK(launch_gemm_epi(tA, tB0, tB1, p, s));
+        prof.after(q, s);
+        CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
+      });
+    prof.launches += 1;  // finalize
     CK(launch_finalize(n, ld, Ahi[0], Alo[0], Ahi[1], Alo[1], Astage, lda_dev, st, s));
     if (!a_dev)
       CK(cudaMemcpy2DAsync(A_out, sizeof(double) * ld_a, Astage, sizeof(double) * ld,
@@ -347,6 +403,9 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
       info->slice_gemms = fs.slice_gemms;
       info->residual = fs.rho;
       info->status = ret;
+      info->launches = prof.launches;
+      info->product_launches = prof.live;
+      info->product_ms = prof.ms;
     }
     CK(cudaEventRecord(b->ev, s));
     CK(cudaStreamWaitEvent(user, b->ev, 0));
@@ -422,22 +481,31 @@ dpt_status solve_full_fp64(int64_t n64, bool cplx, const std::vector<double>& th
     CK(launch_check_finite(n, Dl, ldd, cplx, st, s));
     CK(launch_fp64_init(n, ld, cplx, A[0], s));
     // iteration 0 outside the graph (it also forms the residual scale)
-    auto one = [&](int first, int cur) {
+    Prof prof;
+    prof.on = o.profile != 0;
+    auto one = [&](int first, int cur, int q) {
+      prof.before(q, s);
       if (cplx) CK(launch_gemm_c128(n, Dl, ldd, A[cur], ld, P, st, s));
       else CK(launch_gemm_f64(n, Dl, ldd, A[cur], ld, P, st, s));
+      prof.after(q, s);
       CK(launch_epi_f64(n, ld, cplx, thd, lambda, P, A[cur], A[cur ^ 1], Dl, ldd, E, st, first, s));
     };
-    one(1, 0);
+    prof.make(1);
+    one(1, 0, 0);   // iteration 0 outside the graph (it also forms the residual scale)
     CK(cudaMemcpyAsync(b->host_state, st, sizeof(IterState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    prof.collect(1);
+    prof.launches = 4;   // finiteness check, A_0 = I, product, epilogue
+    for (auto& e : prof.ev) cudaEventDestroy(e);
+    prof.ev.clear();
     if (b->host_state->status == ST_RUNNING) {
       // Two-iteration unit so that buffer parity is fixed inside the graph.
       dpt_options oo = o;
       const int per = std::max(2, (o.graph_iters + 1) / 2 * 2);
       oo.graph_iters = o.graph_iters > 0 ? per : 0;
       int parity = 1;   // A_1 lives in buffer 1
-      run_loop(b, st, oo.graph_iters, o.max_iter, [&] {
-        one(0, parity);
+      run_loop(b, st, oo.graph_iters, o.max_iter, 2, prof, [&](int q) {
+        one(0, parity, q);
         parity ^= 1;
       });
     }
@@ -460,6 +528,9 @@ dpt_status solve_full_fp64(int64_t n64, bool cplx, const std::vector<double>& th
       info->slice_gemms = 0;
       info->residual = fs.rho;
       info->status = ret;
+      info->launches = prof.launches;
+      info->product_launches = prof.live;
+      info->product_ms = prof.ms;
     }
     CK(cudaEventRecord(b->ev, s));
     CK(cudaStreamWaitEvent(user, b->ev, 0));
@@ -488,6 +559,7 @@ void dpt_options_default(dpt_options* o) {
   o->graph_iters = 4;
   o->max_slices = 3;
   o->slice_tol = 1e-8;
+  o->profile = 0;
 }
 
 const char* dpt_status_string(dpt_status s) {

@@ -40,6 +40,59 @@ __device__ __forceinline__ void ff_add_f(float ah, float al, float b, float& rh,
   fast_two_sum(s, e, rh, rl);
 }
 
+// Two-product: a*b = p + e exactly (FMA).
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = a * b;
+  e = fmaf(a, b, -p);
+}
+
+// Splits a double into hi + lo floats with integer operations only (on this GPU
+// every FP64 operation, conversions included, runs on a pipe about 60x slower
+// than FP32).  hi is v truncated to 24 significant bits; lo holds the next bits,
+// rounded to 24 by the integer-to-float conversion (48 bits in all).  |v| below
+// 2^-126 is flushed to zero, beyond the float range it becomes +-inf, NaN stays
+// NaN; lo is dropped for |v| < 2^-74.
+__device__ __forceinline__ void split_double(double v, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned hb = (unsigned)(b >> 32);
+  const unsigned sign = hb & 0x80000000u;
+  const int e = (int)((hb >> 20) & 0x7FFu);
+  const unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+  lo = 0.f;
+  if (e == 0x7FF) {
+    hi = __uint_as_float(sign | 0x7F800000u | (mant ? 0x400000u : 0u));
+    return;
+  }
+  const int fe = e - 1023 + 127;
+  if (fe <= 0) { hi = __uint_as_float(sign); return; }
+  if (fe >= 255) { hi = __uint_as_float(sign | 0x7F800000u); return; }
+  hi = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)(mant >> 29));
+  const unsigned rem = (unsigned)(mant & 0x1FFFFFFFull);
+  const int le = e - 1075 + 127;   // biased exponent of 2^(e - 1075)
+  if (rem == 0u || le <= 0) return;
+  lo = __uint_as_float(sign | __float_as_uint(__uint2float_rn(rem) * __uint_as_float((unsigned)le << 23)));
+}
+
+// True unless v is +-inf or NaN (integer test).
+__device__ __forceinline__ bool finite_bits(double v) {
+  return ((unsigned)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FFu) != 0x7FFu;
+}
+
+// Exact float -> double by bit construction (zero and normal floats; subnormal
+// floats, which this library never produces, fall back to the conversion).
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long m = (unsigned long long)(u & 0x7FFFFFu) << 29;
+  if (e == 0u) {
+    if ((u & 0x7FFFFFu) == 0u) return __longlong_as_double((long long)sign);
+    return (double)f;
+  }
+  const unsigned long long de = (e == 0xFFu) ? 0x7FFull : (unsigned long long)(e - 127 + 1023);
+  return __longlong_as_double((long long)(sign | (de << 52) | m));
+}
+
 __device__ __forceinline__ float bf16_round(float x) {
   return __bfloat162float(__float2bfloat16_rn(x));
 }
@@ -74,6 +127,9 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;

@@ -30,19 +30,26 @@
 namespace dpt {
 
 constexpr int BM = 128;          // rows j per tile (TMEM lanes)
-constexpr int BN = 128;          // columns i per tile (TMEM columns)
+constexpr int BN = 256;          // columns i per tile (TMEM columns per accumulator)
 constexpr int BK = 64;           // K per stage: one 128-byte swizzle atom of BF16
 constexpr int UK = 16;           // K per tcgen05.mma (kind::f16)
-constexpr int STAGES = 3;
+constexpr int STAGES = 4;        // operand ring depth (bytes in flight cover the L2 latency)
+constexpr int NACC = 2;          // TMEM accumulators (double buffer)
+constexpr int IT0 = 128;         // columns (and rows) per block of iteration 0
+constexpr int NSLICE = 3;        // BF16 slices of Delta kept (the product uses the first S)
 constexpr int A_TILE = BM * BK * 2;
 constexpr int B_TILE = BN * BK * 2;
-constexpr int NTHREADS = 192;    // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int EPI_WARPS = 8;
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;   // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int SMEM_TILES = STAGES * (A_TILE + B_TILE);
+constexpr int XCH = 32;                         // accumulator columns staged per chunk
+constexpr int SMEM_X = BM * XCH * 4;            // accumulator staging (FP32, column-major)
 
 struct __align__(16) GemmSmemMisc {
   uint64_t full[STAGES];
   uint64_t empty[STAGES];
-  uint64_t accum;
+  uint64_t acc_full[NACC];
+  uint64_t acc_empty[NACC];
   uint32_t tmem_base;
   int k;
   int slices;
@@ -51,9 +58,46 @@ struct __align__(16) GemmSmemMisc {
   float dprev[BN];    // d_{k-1}
   float thh[BN];      // theta_i as float-float
   float thl[BN];
-  float red[4][3][BN];  // per-warp column sums: |R|^2, |a|^2, Delta_ij dt_ji
 };
-constexpr int SMEM_BYTES = SMEM_TILES + 1024 + (int)sizeof(GemmSmemMisc);
+constexpr int SMEM_BYTES = SMEM_TILES + SMEM_X + 1024 + (int)sizeof(GemmSmemMisc);
+
+struct Col4 {
+  float4 ah, al, L;
+  uint2 dtp;      // four BF16
+  uint2 D[3];     // Delta_ij as three BF16 slices, four rows each
+};
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float f4(const float4& v, int e) {
+  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void f4set(float4& v, int e, float x) {
+  if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
+}
+__device__ __forceinline__ float bf_at(uint2 u, int e) {
+  const uint32_t w = (e < 2) ? u.x : u.y;
+  const uint32_t h = (e & 1) ? (w >> 16) : (w & 0xFFFFu);
+  return __uint_as_float(h << 16);
+}
+__device__ __forceinline__ uint32_t bf_bits(float x) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+// Warp reduction of the column sums: |R|^2 and |a|^2 in float, the diagonal
+// increment (eh, el) in float-float.
+__device__ __forceinline__ void warp_sum_ff(float& r2, float& a2, float& eh, float& el) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    const float oh = __shfl_xor_sync(0xffffffffu, eh, o);
+    const float ol = __shfl_xor_sync(0xffffffffu, el, o);
+    float sh, se;
+    two_sum(eh, oh, sh, se);
+    se += el + ol;
+    fast_two_sum(sh, se, eh, el);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Preparation: transpose Delta (column-major FP64) into row-major FP32 and into
@@ -61,8 +105,7 @@ constexpr int SMEM_BYTES = SMEM_TILES + 1024 + (int)sizeof(GemmSmemMisc);
 // diagonal when the Epstein-Nesbet partition is used.
 // ---------------------------------------------------------------------------
 __global__ void k_prep_delta(const double* __restrict__ delta, int64_t ld_in, int n, int ld,
-                             int nslices, int en, float* __restrict__ Dt,
-                             __nv_bfloat16* __restrict__ Dcat, IterState* st) {
+                             int en, __nv_bfloat16* __restrict__ Dcat, IterState* st) {
   __shared__ double tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;  // bx: column k, by: row j of Delta
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -70,102 +113,130 @@ __global__ void k_prep_delta(const double* __restrict__ delta, int64_t ld_in, in
     double v = 0.0;
     if (j < n && k < n) {
       v = delta[(int64_t)k * ld_in + j];
-      if (!isfinite(v)) atomicExch(&st->bad_input, 1u);
+      if (!finite_bits(v)) atomicExch(&st->bad_input, 1u);
       if (en && j == k) v = 0.0;
     }
     tile[r][threadIdx.x] = v;   // tile[k - bx][j - by]
   }
   __syncthreads();
-  const int64_t cat_ld = (int64_t)nslices * ld;
+  const int64_t cat_ld = (int64_t)NSLICE * ld;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int j = by + r, k = bx + threadIdx.x;   // write row j, column k (row-major)
     if (j < n && k < ld) {
-      const double v = (k < n) ? tile[threadIdx.x][r] : 0.0;
-      Dt[(int64_t)j * ld + k] = (float)v;
-      double rem = v;
-      for (int s = 0; s < nslices; ++s) {
-        const __nv_bfloat16 b = __float2bfloat16_rn((float)rem);
+      float rh = 0.f, rl = 0.f;
+      if (k < n) split_double(tile[threadIdx.x][r], rh, rl);
+      // BF16 slices: D1 = bf16(v), D2 = bf16(v - D1), D3 = bf16(v - D1 - D2)
+      // (remainders carried exactly in float-float); D1 + D2 + D3 = v to 2^-24
+      for (int s = 0; s < NSLICE; ++s) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(rh);
         Dcat[(int64_t)j * cat_ld + (int64_t)s * ld + k] = b;
-        rem -= (double)__bfloat162float(b);
+        two_sum(rh - __bfloat162float(b), rl, rh, rl);
       }
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// Iteration 0 (A_0 = I), computed exactly from the FP64 input:
+// Iteration 0 (A_0 = I), computed from the FP64 input in float-float:
 //   R_0 = lambda Delta (off the diagonal), d_0 = diag(Delta),
 //   dt_0 = bf16(G o R_0), L_1 = R_0 - Gap o dt_0, A_1 = I + dt_0,
-// plus the column partials of |R_0|^2, |a|^2 = 1, e_1 = diag(Delta dt_0) and the
-// row partials of sum_k |Delta_jk| for the residual scale.
-// One thread per row j of a 128 x 128 tile; blockIdx.x = column tile.
+// plus the column partials of |R_0|^2, |a|^2 = 1, e_1 = diag(Delta dt_0) (float-
+// float) and the row partials of sum_k |Delta_jk| for the residual scale.
+// One block per 128 x 128 tile, 4 warps; each warp walks 32 columns and lane l
+// owns rows 4l..4l+3 (vector loads along the contiguous row index).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta, int64_t ld_in,
-                                               const double* __restrict__ theta, double lam,
-                                               int n, int ld, int ntm, int en,
-                                               const float* __restrict__ Dt,
+                                               const float* __restrict__ th_hi,
+                                               const float* __restrict__ th_lo, float lam_hi,
+                                               float lam_lo, int n, int ld, int ntm, int en,
+                                               const __nv_bfloat16* __restrict__ Dcat,
                                                float* __restrict__ Ahi1, float* __restrict__ Alo1,
                                                __nv_bfloat16* __restrict__ dt0,
                                                float* __restrict__ L, double* __restrict__ d,
                                                float* __restrict__ part,
                                                float* __restrict__ rowpart, IterState* st) {
-  __shared__ float red[4][3][BN];
-  float mx = 0.f;
+  __shared__ float rows[4][IT0];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-  const int j = m0 + threadIdx.x;
-  const bool rowok = j < n;
-  const double thj = rowok ? theta[j] : 0.0;
-  float rowabs = 0.f;
-  for (int ch = 0; ch < BN / 16; ++ch) {
-    float r2[16], a2[16], ep[16];
+  const int n0 = blockIdx.x * IT0, m0 = blockIdx.y * IT0, tm = blockIdx.y;
+  const int r0 = 4 * lane, j0 = m0 + r0;
+  const int64_t cat_ld = (int64_t)NSLICE * ld;
+  const float4 thj_h = *reinterpret_cast<const float4*>(th_hi + j0);
+  const float4 thj_l = *reinterpret_cast<const float4*>(th_lo + j0);
+  float rowabs[4] = {0.f, 0.f, 0.f, 0.f};
+  float mx = 0.f;
+  for (int c = 0; c < 32; ++c) {
+    const int i = n0 + 32 * w + c;
+    if (i >= n) break;   // uniform across the warp
+    const float thi_h = th_hi[i], thi_l = th_lo[i];
+    const __nv_bfloat16* Drow = Dcat + (int64_t)i * cat_ld + j0;
+    uint2 D[3];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      r2[c] = 0.f; a2[c] = 0.f; ep[c] = 0.f;
-      const int i = n0 + ch * 16 + c;
-      if (rowok && i < n) {
-        const int64_t idx = (int64_t)i * ld + j;
+    for (int sl = 0; sl < 3; ++sl) D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+    float4 oh, oL;
+    uint32_t ob[4];
+    float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = j0 + e;
+      float nh = 0.f, Ln = 0.f, dtn = 0.f;
+      if (j < n) {
         const double v = delta[(int64_t)i * ld_in + j];
-        rowabs += fabsf((float)v);
+        float vh, vl;
+        split_double(v, vh, vl);
+        rowabs[e] += fabsf(vh);
         if (j == i) {
-          Ahi1[idx] = 1.f; Alo1[idx] = 0.f;
-          dt0[idx] = __float2bfloat16_rn(0.f);
-          L[idx] = 0.f;
-          a2[c] = 1.f;
+          nh = 1.f;
+          a2 += 1.f;
           d[i] = en ? 0.0 : v;
         } else {
-          const double R0 = lam * v;
-          const double gap = theta[i] - thj;
-          const float dtn = bf16_round((float)(R0 / gap));
-          L[idx] = (float)(R0 - gap * (double)dtn);
-          Ahi1[idx] = dtn; Alo1[idx] = 0.f;
-          dt0[idx] = __float2bfloat16_rn(dtn);
-          r2[c] = (float)(R0 * R0);
-          ep[c] = Dt[idx] * dtn;   // Delta_ij dt_ji (row-major Delta shares the index)
+          // R_0 = lambda * Delta_ji as float-float
+          float pr, pe;
+          two_prod(lam_hi, vh, pr, pe);
+          pe = fmaf(lam_hi, vl, fmaf(lam_lo, vh, pe));
+          float R0h, R0l;
+          fast_two_sum(pr, pe, R0h, R0l);
+          float gh, gl;
+          ff_sub(thi_h, thi_l, f4(thj_h, e), f4(thj_l, e), gh, gl);
+          dtn = bf16_round(R0h * __frcp_rn(gh));
+          // L_1 = R_0 - Gap * dt_0; R0h - q is exact (q is R0h to BF16 accuracy)
+          float q, qe;
+          two_prod(gh, dtn, q, qe);
+          qe = fmaf(gl, dtn, qe);
+          Ln = (R0h - q) + (R0l - qe);
+          nh = dtn;
+          r2 = fmaf(R0h, R0h, r2);
+          const float p1 = bf_at(D[0], e) * dtn;
+          const float p23 = fmaf(bf_at(D[1], e), dtn, bf_at(D[2], e) * dtn);
+          float sh, se;
+          two_sum(eh, p1, sh, se);
+          se += el + p23;
+          fast_two_sum(sh, se, eh, el);
           mx = fmaxf(mx, fabsf(dtn));
         }
       }
+      f4set(oh, e, nh);
+      f4set(oL, e, Ln);
+      ob[e] = bf_bits(dtn);
     }
-    warp_transpose_sum16(r2, lane);
-    warp_transpose_sum16(a2, lane);
-    warp_transpose_sum16(ep, lane);
-    if ((lane & 1) == 0) {
-      const int col = ch * 16 + transpose_sum16_col(lane);
-      red[w][0][col] = r2[0]; red[w][1][col] = a2[0]; red[w][2][col] = ep[0];
+    const int64_t idx = (int64_t)i * ld + j0;
+    st4(Ahi1 + idx, oh);
+    st4(Alo1 + idx, make_float4(0.f, 0.f, 0.f, 0.f));
+    st4(L + idx, oL);
+    *reinterpret_cast<uint2*>(dt0 + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+    warp_sum_ff(r2, a2, eh, el);
+    if (lane == 0) {
+      part[((int64_t)0 * ntm + tm) * ld + i] = r2;
+      part[((int64_t)1 * ntm + tm) * ld + i] = a2;
+      part[((int64_t)2 * ntm + tm) * ld + i] = eh;
+      part[((int64_t)3 * ntm + tm) * ld + i] = el;
     }
   }
-  __syncthreads();
-  const int i = n0 + threadIdx.x;
-  if (i < n) {
-    const int tm = blockIdx.y;
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float s = ((red[0][q][threadIdx.x] + red[1][q][threadIdx.x]) +
-                       red[2][q][threadIdx.x]) + red[3][q][threadIdx.x];
-      part[((int64_t)q * ntm + tm) * ld + i] = s;
-    }
-  }
-  if (rowok) rowpart[(int64_t)blockIdx.x * ld + j] = rowabs;
+  for (int e = 0; e < 4; ++e) rows[w][r0 + e] = rowabs[e];
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (m0 + r < n)
+    rowpart[(int64_t)blockIdx.x * ld + m0 + r] = ((rows[0][r] + rows[1][r]) + rows[2][r]) + rows[3][r];
   // the slice count of the first product depends on the size of dt_0
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0 && mx > 0.f) atomicMax(&st->dmax_bits, __float_as_uint(mx));
@@ -177,32 +248,50 @@ __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta,
 // advance d, and decide: converged / diverged / max_iter / continue (and with
 // how many Delta slices).  The last block to finish takes the decision.
 // ---------------------------------------------------------------------------
-__global__ void k_ctrl(int n, int ld, int ntm, int ntn, const float* __restrict__ part,
-                       const float* __restrict__ rowpart, const double* __restrict__ theta,
-                       double* __restrict__ d, double* __restrict__ E,
-                       float* __restrict__ e_col, float* __restrict__ dprev_col,
-                       IterState* st) {
+__global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
+                                              const float* __restrict__ part,
+                                              const float* __restrict__ rowpart,
+                                              const double* __restrict__ theta,
+                                              double* __restrict__ d, double* __restrict__ E,
+                                              float* __restrict__ e_col,
+                                              float* __restrict__ dprev_col, IterState* st) {
   if (st->status != ST_RUNNING) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // 64 columns per block, 4 threads per column each summing every 4th tile partial
+  __shared__ float sh[3][4][64];
+  __shared__ double she[4][64];
+  const int c = threadIdx.x & 63, g = threadIdx.x >> 6;
+  const int i = blockIdx.x * 64 + c;
   const bool first = (st->k == 0);
-  float rho_raw = 0.f;
-  if (i < n) {
-    float r2 = 0.f, a2 = 0.f, ep = 0.f;
-    for (int t = 0; t < ntm; ++t) {
-      r2 += part[((int64_t)0 * ntm + t) * ld + i];
-      a2 += part[((int64_t)1 * ntm + t) * ld + i];
-      ep += part[((int64_t)2 * ntm + t) * ld + i];
+  {
+    float r2 = 0.f, a2 = 0.f, rs = 0.f;
+    double ep = 0.0;
+    if (i < n) {
+      for (int t = g; t < ntm; t += 4) {
+        r2 += part[((int64_t)0 * ntm + t) * ld + i];
+        a2 += part[((int64_t)1 * ntm + t) * ld + i];
+        ep += (double)part[((int64_t)2 * ntm + t) * ld + i] +
+              (double)part[((int64_t)3 * ntm + t) * ld + i];
+      }
+      if (first)
+        for (int t = g; t < ntn; t += 4) rs += rowpart[(int64_t)t * ld + i];
     }
+    sh[0][g][c] = r2; sh[1][g][c] = a2; sh[2][g][c] = rs; she[g][c] = ep;
+  }
+  __syncthreads();
+  float rho_raw = 0.f;
+  if (g == 0 && i < n) {
+    const float r2 = ((sh[0][0][c] + sh[0][1][c]) + sh[0][2][c]) + sh[0][3][c];
+    const float a2 = ((sh[1][0][c] + sh[1][1][c]) + sh[1][2][c]) + sh[1][3][c];
+    const double ep = ((she[0][c] + she[1][c]) + she[2][c]) + she[3][c];
     rho_raw = sqrtf(r2 / a2);
     if (!(rho_raw == rho_raw) || isinf(rho_raw)) rho_raw = __int_as_float(0x7f800000);
     const double dk = d[i];
     E[i] = theta[i] + st->lam * dk;
     dprev_col[i] = (float)dk;
-    e_col[i] = ep;
-    d[i] = dk + (double)ep;
+    e_col[i] = (float)ep;
+    d[i] = dk + ep;
     if (first) {
-      float rs = 0.f;
-      for (int t = 0; t < ntn; ++t) rs += rowpart[(int64_t)t * ld + i];
+      const float rs = ((sh[2][0][c] + sh[2][1][c]) + sh[2][2][c]) + sh[2][3][c];
       atomicMax(&st->row_bits, __float_as_uint(rs));
     }
   }
@@ -238,20 +327,45 @@ __global__ void k_ctrl(int n, int ld, int ntm, int ntn, const float* __restrict_
 
 // ---------------------------------------------------------------------------
 // The tensor-core iteration: X = [D1 D2 D3](:, :S) * dt_{k-1} on tcgen05 with TMA
-// loads, fused with the update epilogue.
+// loads, fused with the update epilogue.  Persistent and warp-specialised: one
+// CTA per SM walks the 128 x 128 output tiles round-robin.
+//   warp 0       TMA producer: A (Delta slices) and B (dt) tiles into a STAGES ring
+//   warp 1       MMA issuer: one elected thread, accumulators alternate between two
+//                TMEM buffers so the next tile's products overlap this tile's epilogue
+//   warps 2-9    epilogue, per tile in two phases:
+//                (1) TMEM -> shared memory (column-major FP32 tile), then the TMEM
+//                    buffer is handed back to the MMA warp;
+//                (2) column walk: each warp takes 16 columns, lane l owns rows
+//                    4l..4l+3, so every global access is a 16-byte vector along the
+//                    contiguous row index and each column's sums are one warp
+//                    reduction.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void epilogue_tile(const GemmEpiParams& p, GemmSmemMisc* ms,
-                                              int warp, int lane, int m0, int n0,
-                                              uint32_t tmem, bool ok) {
-  const int q = warp & 3;            // TMEM lane quadrant of this warp
-  const int r = q * 32 + lane;
-  const int j = m0 + r;
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// Barrier over the 256 epilogue threads that also returns the AND of `v` over them,
+// so every epilogue warp takes the same branch afterwards (and the same number of
+// barriers in all).
+__device__ __forceinline__ bool epi_bar_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.and.pred po, 1, 256, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+// Phase 2 for one chunk: update the 4 columns [c0 + 4 ew, c0 + 4 ew + 4) of the
+// tile; Xs holds the chunk's XCH accumulator columns.
+__device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSmemMisc* ms,
+                                                 const float* Xs, int ew, int lane, int tm,
+                                                 int m0, int n0, int c0, float& mx) {
   const int n = p.n, ld = p.ld;
-  const bool rowok = ok && (j < n);
-  const int cur = ms->cur;
+  const bool c1 = (ms->cur != 0);
   // explicit selects: indexing the parameter arrays with a runtime value would
   // copy the parameter block to local memory
-  const bool c1 = (cur != 0);
   const float* __restrict__ Ahc = c1 ? p.A_hi[1] : p.A_hi[0];
   const float* __restrict__ Alc = c1 ? p.A_lo[1] : p.A_lo[0];
   float* __restrict__ Ahn = c1 ? p.A_hi[0] : p.A_hi[1];
@@ -259,59 +373,94 @@ __device__ __forceinline__ void epilogue_tile(const GemmEpiParams& p, GemmSmemMi
   const __nv_bfloat16* __restrict__ dtp = c1 ? p.dt[0] : p.dt[1];   // dt_{k-1}
   __nv_bfloat16* __restrict__ dtn_out = c1 ? p.dt[1] : p.dt[0];     // dt_k
   float* __restrict__ L = p.L;
-  const float* __restrict__ Dt = p.Dt;
   const float lam = p.lam;
-  const float thj_h = rowok ? p.th_hi[j] : 0.f;
-  const float thj_l = rowok ? p.th_lo[j] : 0.f;
-  float mx = 0.f;
-  for (int ch = 0; ch < BN / 16; ++ch) {
-    float x[16];
-    if (ok) tmem_ld_x16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 16), x);
-    float r2[16], a2[16], ep[16];
+  const int r0 = 4 * lane;                // rows r0..r0+3 of the tile
+  const int j0 = m0 + r0;
+  // rows beyond n lie in the padded part of every work array (ld is a multiple of
+  // the tile height): they are read, masked and written back as zeros
+  const float4 thj_h = ld4(p.th_hi + j0);
+  const float4 thj_l = ld4(p.th_lo + j0);
+  constexpr int U = 4;                    // columns in flight per lane
+  {
+    const int cb = c0 + 4 * ew;           // first tile column of this warp
+    Col4 in[U];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) {
-      r2[c] = 0.f; a2[c] = 0.f; ep[c] = 0.f;
-      const int cl = ch * 16 + c;
-      const int i = n0 + cl;
-      if (rowok && i < n) {
-        const int64_t idx = (int64_t)i * ld + j;
-        const float ah = Ahc[idx], al = Alc[idx];
-        if (j == i) {
-          Ahn[idx] = 1.f; Aln[idx] = 0.f;
-          dtn_out[idx] = __float2bfloat16_rn(0.f);
-          L[idx] = 0.f;
-          a2[c] = 1.f;
-        } else {
-          const float dprev = __bfloat162float(dtp[idx]);
-          const float R = L[idx] + lam * (x[c] - ah * ms->e[cl] - dprev * ms->dprev[cl]);
-          float gh, gl;
-          ff_sub(ms->thh[cl], ms->thl[cl], thj_h, thj_l, gh, gl);
-          const float dnew = bf16_round(R * __frcp_rn(gh));
-          L[idx] = fmaf(-gh, dnew, R) - gl * dnew;
-          float nh, nl;
-          ff_add_f(ah, al, dnew, nh, nl);
-          Ahn[idx] = nh; Aln[idx] = nl;
-          dtn_out[idx] = __float2bfloat16_rn(dnew);
-          r2[c] = R * R;
-          a2[c] = ah * ah;
-          ep[c] = Dt[idx] * dnew;
-          mx = fmaxf(mx, fabsf(dnew));
-        }
+    for (int u = 0; u < U; ++u) {
+      const int i = n0 + cb + u;
+      if (i < n) {
+        const int64_t idx = (int64_t)i * ld + j0;
+        in[u].ah = ld4(Ahc + idx);
+        in[u].al = ld4(Alc + idx);
+        in[u].L = ld4(L + idx);
+        in[u].dtp = *reinterpret_cast<const uint2*>(dtp + idx);
+        // Delta_ij for j = j0..j0+3: row i of the row-major slices
+        const __nv_bfloat16* Drow = p.Dcat + (int64_t)i * p.cat_ld + j0;
+#pragma unroll
+        for (int sl = 0; sl < 3; ++sl)
+          in[u].D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
       }
     }
-    warp_transpose_sum16(r2, lane);
-    warp_transpose_sum16(a2, lane);
-    warp_transpose_sum16(ep, lane);
-    if ((lane & 1) == 0) {
-      const int col = ch * 16 + transpose_sum16_col(lane);
-      ms->red[q][0][col] = r2[0]; ms->red[q][1][col] = a2[0]; ms->red[q][2][col] = ep[0];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int cl = cb + u;
+      const int i = n0 + cl;
+      if (i >= n) continue;   // uniform across the warp
+      const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * BM + r0);
+      const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
+      const float thh = ms->thh[cl], thl = ms->thl[cl];
+      float4 oh, ol, oL;
+      uint32_t ob[4];
+      float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = j0 + e;
+        const float ah = f4(in[u].ah, e), al = f4(in[u].al, e);
+        float nh = 0.f, nl = 0.f, Ln = 0.f, dnew = 0.f;
+        if (j == i) {
+          nh = 1.f;
+          a2 += 1.f;
+        } else if (j < n) {
+          const float R = f4(in[u].L, e) +
+                          lam * (f4(x4, e) - ah * e_i - bf_at(in[u].dtp, e) * dp_i);
+          float gh, gl;
+          ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
+          dnew = bf16_round(R * __frcp_rn(gh));
+          Ln = fmaf(-gh, dnew, R) - gl * dnew;
+          ff_add_f(ah, al, dnew, nh, nl);
+          r2 = fmaf(R, R, r2);
+          a2 = fmaf(ah, ah, a2);
+          // e_{k+1} partial Delta_ij dt_ji: the slice products are exact (8-bit
+          // significands), summed in float-float
+          const float p1 = bf_at(in[u].D[0], e) * dnew;
+          const float p23 = fmaf(bf_at(in[u].D[1], e), dnew, bf_at(in[u].D[2], e) * dnew);
+          float sh, se;
+          two_sum(eh, p1, sh, se);
+          se += el + p23;
+          fast_two_sum(sh, se, eh, el);
+          mx = fmaxf(mx, fabsf(dnew));
+        }
+        f4set(oh, e, nh);
+        f4set(ol, e, nl);
+        f4set(oL, e, Ln);
+        ob[e] = bf_bits(dnew);
+      }
+      const int64_t idx = (int64_t)i * ld + j0;
+      st4(Ahn + idx, oh);
+      st4(Aln + idx, ol);
+      st4(L + idx, oL);
+      *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+      warp_sum_ff(r2, a2, eh, el);
+      if (lane == 0) {
+        p.part[((int64_t)0 * p.ntm + tm) * ld + i] = r2;
+        p.part[((int64_t)1 * p.ntm + tm) * ld + i] = a2;
+        p.part[((int64_t)2 * p.ntm + tm) * ld + i] = eh;
+        p.part[((int64_t)3 * p.ntm + tm) * ld + i] = el;
+      }
     }
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (lane == 0 && mx > 0.f) atomicMax(&p.st->dmax_bits, __float_as_uint(mx));
 }
 
-__global__ void __launch_bounds__(NTHREADS, 2)
+__global__ void __launch_bounds__(NTHREADS, 1)
 k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
            const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -320,30 +469,23 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_TILE;
-  GemmSmemMisc* ms = (GemmSmemMisc*)(smem + SMEM_TILES);
+  float* Xs = reinterpret_cast<float*>(smem + SMEM_TILES);
+  GemmSmemMisc* ms = (GemmSmemMisc*)(smem + SMEM_TILES + SMEM_X);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int ntn = (p.n + BN - 1) / BN;
+  const int ntiles = ntn * p.ntm;
 
   if (threadIdx.x == 0) {
     ms->k = st->k;
     ms->slices = st->slices;
     ms->cur = st->cur;
     for (int s = 0; s < STAGES; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], 1); }
-    mbar_init(&ms->accum, 1);
+    for (int b = 0; b < NACC; ++b) { mbar_init(&ms->acc_full[b], 1); mbar_init(&ms->acc_empty[b], 1); }
     fence_mbar_init();
   }
   if (warp == 0) {
-    tmem_alloc(&ms->tmem_base, BN);
+    tmem_alloc(&ms->tmem_base, NACC * BN);
     tmem_relinquish();
-  }
-  if (warp >= 2) {   // per-column parameters of the tile
-    const int t = threadIdx.x - 64;
-    const int i = n0 + t;
-    const bool v = i < p.n;
-    ms->e[t] = v ? p.e_col[i] : 0.f;
-    ms->dprev[t] = v ? p.dprev_col[i] : 0.f;
-    ms->thh[t] = v ? p.th_hi[i] : 0.f;
-    ms->thl[t] = v ? p.th_lo[i] : 0.f;
   }
   tc_fence_before();
   __syncthreads();
@@ -359,68 +501,115 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     // ---- TMA producer ----
     prefetch_tmap(&tmA);
     prefetch_tmap(tmB);
-    const int kb_last = min(kb_per_slice - 1, (n0 + BN - 1) / BK);
-    int it = 0;
-    for (; it < nk; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (it / STAGES) & 1;
-      if (!mbar_wait(&ms->empty[s], ph ^ 1, tflag)) break;
-      mbar_arrive_expect_tx(&ms->full[s], A_TILE + B_TILE);
-      // Accumulation order.  The tensor core accumulates in FP32 and drops the
-      // bits below the running sum at every step, so the error of a chain grows
-      // with the size of the partial sums it carries.  Column i of Delta dt is
-      // dominated by k near i (G_ki ~ 1/(theta_i - theta_k)), so the small slices
-      // go first and each slice's K-blocks are rotated to end on the blocks of this
-      // tile's own columns: the large terms enter last, after few steps remain.
-      const int sl = S - 1 - it / kb_per_slice;
-      const int kb = (kb_last + 1 + it % kb_per_slice) % kb_per_slice;
-      tma_load_2d(sA + s * A_TILE, &tmA, &ms->full[s], sl * p.ld + kb * BK, m0);
-      tma_load_2d(sB + s * B_TILE, tmB, &ms->full[s], kb * BK, n0);
+    uint32_t it = 0;   // running stage counter over all tiles
+    bool alive = true;
+    for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+      const int tm = t / ntn, tn = t % ntn;
+      const int m0 = tm * BM, n0 = tn * BN;
+      const int kb_last = min(kb_per_slice - 1, (n0 + BN - 1) / BK);
+      for (int q = 0; q < nk; ++q, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (it / STAGES) & 1;
+        if (!mbar_wait(&ms->empty[s], ph ^ 1, tflag)) { alive = false; break; }
+        mbar_arrive_expect_tx(&ms->full[s], A_TILE + B_TILE);
+        // Accumulation order.  The tensor core accumulates in FP32 and drops the
+        // bits below the running sum at every step, so the error of a chain grows
+        // with the size of the partial sums it carries.  Column i of Delta dt is
+        // dominated by k near i (G_ki ~ 1/(theta_i - theta_k)), so the small slices
+        // go first and each slice's K-blocks are rotated to end on the blocks of
+        // this tile's own columns: the large terms enter last, with few steps left.
+        const int sl = S - 1 - q / kb_per_slice;
+        const int kb = (kb_last + 1 + q % kb_per_slice) % kb_per_slice;
+        tma_load_2d(sA + s * A_TILE, &tmA, &ms->full[s], sl * p.ld + kb * BK, m0);
+        tma_load_2d(sB + s * B_TILE, tmB, &ms->full[s], kb * BK, n0);
+      }
     }
     // drain: every issued copy must have landed before the CTA can exit
-    for (int t = (it > STAGES ? it - STAGES : 0); t < it; ++t)
+    for (uint32_t t = (it > STAGES ? it - STAGES : 0); t < it; ++t)
       mbar_wait(&ms->full[t % STAGES], (t / STAGES) & 1, tflag);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
     constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % STAGES;
-      const uint32_t ph = (it / STAGES) & 1;
-      if (!mbar_wait(&ms->full[s], ph, tflag)) break;
+    uint32_t it = 0;
+    int lt = 0;   // local tile counter
+    bool alive = true;
+    for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x, ++lt) {
+      const int b = lt & 1;
+      const uint32_t use = (uint32_t)(lt >> 1);
+      if (!mbar_wait(&ms->acc_empty[b], (use & 1) ^ 1, tflag)) break;
       tc_fence_after();
-      const uint64_t da = smem_desc_sw128(sA + s * A_TILE);
-      const uint64_t db = smem_desc_sw128(sB + s * B_TILE);
+      const uint32_t dacc = tmem + (uint32_t)(b * BN);
+      for (int q = 0; q < nk; ++q, ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (it / STAGES) & 1;
+        if (!mbar_wait(&ms->full[s], ph, tflag)) { alive = false; break; }
+        tc_fence_after();
+        const uint64_t da = smem_desc_sw128(sA + s * A_TILE);
+        const uint64_t db = smem_desc_sw128(sB + s * B_TILE);
 #pragma unroll
-      for (int kk = 0; kk < BK / UK; ++kk) {
-        // advance the start address by kk * 32 bytes inside the swizzle atom
-        umma_bf16(tmem, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
-                  (it > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < BK / UK; ++kk) {
+          // advance the start address by kk * 32 bytes inside the swizzle atom
+          umma_bf16(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                    (q > 0 || kk > 0) ? 1u : 0u);
+        }
+        umma_commit(&ms->empty[s]);
       }
-      umma_commit(&ms->empty[s]);
+      umma_commit(&ms->acc_full[b]);
     }
-    umma_commit(&ms->accum);
   } else if (warp >= 2) {
     // ---- epilogue ----
-    const bool ok = mbar_wait(&ms->accum, 0, tflag);
-    tc_fence_after();
-    epilogue_tile(p, ms, warp, lane, m0, n0, tmem, ok);
-    tc_fence_before();
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    const int t = threadIdx.x - 64;
-    const int i = n0 + t;
-    if (ok && i < p.n) {
-#pragma unroll
-      for (int qq = 0; qq < 3; ++qq) {
-        const float s = ((ms->red[0][qq][t] + ms->red[1][qq][t]) + ms->red[2][qq][t]) +
-                        ms->red[3][qq][t];
-        p.part[((int64_t)qq * p.ntm + blockIdx.y) * p.ld + i] = s;
+    const int ew = warp - 2;        // 0..7
+    const int qd = warp & 3;        // TMEM lane quadrant of this warp
+    const int half = ew >> 2;       // which 16 of a chunk's 32 columns this warp copies
+    const int et = threadIdx.x - 64;
+    float mx = 0.f;
+    int lt = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const int tm = t / ntn, tn = t % ntn;
+      const int m0 = tm * BM, n0 = tn * BN;
+      const int b = lt & 1;
+      const uint32_t use = (uint32_t)(lt >> 1);
+      epi_bar();   // the previous tile's column walk has finished with Xs and params
+      if (et < BN) {
+        const int i = n0 + et;
+        const bool v = i < p.n;
+        ms->e[et] = v ? p.e_col[i] : 0.f;
+        ms->dprev[et] = v ? p.dprev_col[i] : 0.f;
+        ms->thh[et] = v ? p.th_hi[i] : 0.f;
+        ms->thl[et] = v ? p.th_lo[i] : 0.f;
       }
+      // warp-uniform: the TMEM loads below are .sync.aligned
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&ms->acc_full[b], use & 1, tflag));
+      tc_fence_after();
+      const uint32_t src = tmem + (uint32_t)(b * BN) + ((uint32_t)(qd * 32) << 16);
+      bool all_ok = true;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += XCH) {
+        if (c0 > 0) epi_bar();   // the previous chunk's column walk is done with Xs
+        // phase 1: this warp's quadrant, 16 of the chunk's 32 columns
+        if (ok) {
+          float x[16];
+          const int cc = half * 16;
+          tmem_ld_x16(src + (uint32_t)(c0 + cc), x);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) Xs[(cc + c) * BM + qd * 32 + lane] = x[c];
+        }
+        if (c0 + XCH == BN) tc_fence_before();
+        all_ok = epi_bar_and(ok);   // Xs holds the chunk
+        // after the last chunk is staged the TMEM buffer can be refilled
+        if (c0 + XCH == BN && et == 0) mbar_arrive(&ms->acc_empty[b]);
+        if (!all_ok) break;
+        epilogue_columns(p, ms, Xs, ew, lane, tm, m0, n0, c0, mx);
+      }
+      if (!all_ok) break;
     }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0 && mx > 0.f) atomicMax(&p.st->dmax_bits, __float_as_uint(mx));
   }
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    tmem_dealloc(tmem, BN);
+    tmem_dealloc(tmem, NACC * BN);
   }
 }
 
@@ -442,7 +631,7 @@ __global__ void k_finalize(int n, int ld, const float* __restrict__ Ahi0,
     const float* hi = (st->cur == 0) ? Ahi0 : Ahi1;
     const float* lo = (st->cur == 0) ? Alo0 : Alo1;
     const int64_t idx = (int64_t)i * ld + j;
-    v = (double)hi[idx] + (double)lo[idx];
+    v = f2d_bits(hi[idx]) + f2d_bits(lo[idx]);
   }
   Aout[(int64_t)i * ld_a + j] = v;
 }
@@ -460,12 +649,12 @@ __global__ void k_theta_ff(int n, const double* __restrict__ th, float* __restri
 // Host launchers
 // ---------------------------------------------------------------------------
 int mixed_smem_bytes() { return SMEM_BYTES; }
+int mixed_tile_n() { return BN; }
 
-cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int nslices,
-                              int en, float* Dt, __nv_bfloat16* Dcat, IterState* st,
-                              cudaStream_t s) {
+cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en,
+                              __nv_bfloat16* Dcat, IterState* st, cudaStream_t s) {
   dim3 grid((ld + 31) / 32, (n + 31) / 32), block(32, 8);
-  k_prep_delta<<<grid, block, 0, s>>>(delta, ld_in, n, ld, nslices, en, Dt, Dcat, st);
+  k_prep_delta<<<grid, block, 0, s>>>(delta, ld_in, n, ld, en, Dcat, st);
   return cudaGetLastError();
 }
 
@@ -474,22 +663,25 @@ cudaError_t launch_theta_ff(int n, const double* th, float* hi, float* lo, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_iter0(const double* delta, int64_t ld_in, const double* theta, double lam,
-                         int n, int ld, int en, const float* Dt, float* Ahi1, float* Alo1,
+cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
+                         const float* th_lo, double lam, int n, int ld, int en,
+                         const __nv_bfloat16* Dcat, float* Ahi1, float* Alo1,
                          __nv_bfloat16* dt0, float* L, double* d, float* part, float* rowpart,
                          IterState* st, cudaStream_t s) {
-  const int ntm = (n + BM - 1) / BM, ntn = (n + BN - 1) / BN;
-  k_iter0<<<dim3(ntn, ntm), 128, 0, s>>>(delta, ld_in, theta, lam, n, ld, ntm, en, Dt, Ahi1,
-                                         Alo1, dt0, L, d, part, rowpart, st);
+  const int ntm = (n + IT0 - 1) / IT0, ntn = (n + IT0 - 1) / IT0;
+  const float lh = (float)lam;
+  const float ll = (float)(lam - (double)lh);
+  k_iter0<<<dim3(ntn, ntm), 128, 0, s>>>(delta, ld_in, th_hi, th_lo, lh, ll, n, ld, ntm, en,
+                                         Dcat, Ahi1, Alo1, dt0, L, d, part, rowpart, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,
                         float* dprev_col, IterState* st, cudaStream_t s) {
-  const int ntm = (n + BM - 1) / BM, ntn = (n + BN - 1) / BN;
-  k_ctrl<<<(n + 255) / 256, 256, 0, s>>>(n, ld, ntm, ntn, part, rowpart, theta, d, E, e_col,
-                                         dprev_col, st);
+  const int ntm = (n + BM - 1) / BM, ntn = (n + IT0 - 1) / IT0;   // row partials: 128-wide blocks
+  k_ctrl<<<(n + 63) / 64, 256, 0, s>>>(n, ld, ntm, ntn, part, rowpart, theta, d, E, e_col,
+                                       dprev_col, st);
   return cudaGetLastError();
 }
 
@@ -500,7 +692,15 @@ cudaError_t mixed_set_attributes() {
 
 cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
                             const CUtensorMap& tmB1, const GemmEpiParams& p, cudaStream_t s) {
-  dim3 grid((p.n + BN - 1) / BN, (p.n + BM - 1) / BM);
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const int ntiles = ((p.n + BN - 1) / BN) * p.ntm;
+  const int grid = ntiles < nsm ? ntiles : nsm;
   k_gemm_epi<<<grid, NTHREADS, SMEM_BYTES, s>>>(tmA, tmB0, tmB1, p);
   return cudaGetLastError();
 }

@@ -49,30 +49,32 @@ struct IterState {
 // Arguments of the tensor-core iteration kernel (mixed path, real).
 struct GemmEpiParams {
   int n;               // matrix size
-  int ld;              // padded leading dimension of every n x n work array (multiple of 64)
+  int ld;              // padded leading dimension of every n x n work array (multiple of 128)
   int ntm;             // number of 128-row tiles
   float lam;
   float* A_hi[2];      // float-float iterate, column-major, ping-pong by iteration parity
   float* A_lo[2];
   __nv_bfloat16* dt[2];   // BF16 increments, column-major (GEMM B operand), ping-pong
   float* L;            // carried remainder, column-major
-  const float* Dt;     // Delta in FP32, row-major (Dt[i*ld + j] = Delta_ij)
+  const __nv_bfloat16* Dcat;   // Delta as 3 BF16 slices, row-major, slices side by side
+  int64_t cat_ld;      // row pitch of Dcat (3 * ld)
   const float* th_hi;  // theta as float-float
   const float* th_lo;
   const float* e_col;      // e_k = diag(Delta dt_{k-1})
   const float* dprev_col;  // d_{k-1}
-  float* part;         // column partials [3][ntm][ld]
+  float* part;         // column partials [4][ntm][ld]: |R|^2, |a|^2, diag hi, diag lo
   IterState* st;
 };
 
 int mixed_smem_bytes();
+int mixed_tile_n();      // columns per output tile of the product kernel
 cudaError_t mixed_set_attributes();   // once per device, before any capture
-cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int nslices,
-                              int en, float* Dt, __nv_bfloat16* Dcat, IterState* st,
-                              cudaStream_t s);
+cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en,
+                              __nv_bfloat16* Dcat, IterState* st, cudaStream_t s);
 cudaError_t launch_theta_ff(int n, const double* th, float* hi, float* lo, cudaStream_t s);
-cudaError_t launch_iter0(const double* delta, int64_t ld_in, const double* theta, double lam,
-                         int n, int ld, int en, const float* Dt, float* Ahi1, float* Alo1,
+cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
+                         const float* th_lo, double lam, int n, int ld, int en,
+                         const __nv_bfloat16* Dcat, float* Ahi1, float* Alo1,
                          __nv_bfloat16* dt0, float* L, double* d, float* part, float* rowpart,
                          IterState* st, cudaStream_t s);
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,

@@ -31,18 +31,22 @@ class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("epstein_nesbet", ctypes.c_int32),
                 ("graph_iters", ctypes.c_int32), ("max_slices", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("slice_tol", ctypes.c_double)]
+                ("profile", ctypes.c_int32), ("slice_tol", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("slice_gemms", ctypes.c_int32),
                 ("residual", ctypes.c_double), ("status", ctypes.c_int32),
-                ("nstar", ctypes.c_int32), ("seconds", ctypes.c_double)]
+                ("nstar", ctypes.c_int32), ("seconds", ctypes.c_double),
+                ("launches", ctypes.c_int32), ("product_launches", ctypes.c_int32),
+                ("product_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {"iters": self.iters, "slice_gemms": self.slice_gemms,
                 "residual": self.residual, "status": STATUS.get(self.status, str(self.status)),
-                "code": self.status, "nstar": self.nstar, "seconds": self.seconds}
+                "code": self.status, "nstar": self.nstar, "seconds": self.seconds,
+                "launches": self.launches, "product_launches": self.product_launches,
+                "product_ms": self.product_ms}
 
 
 _lib = None
@@ -134,6 +138,18 @@ def _empty_vec(n, like, cplx):
     return np.empty(n, dtype=np.complex128 if cplx else np.float64)
 
 
+def colmajor_tensor(a, device="cuda", pin=False):
+    """Torch tensor with the values of the 2-D array `a` stored column-major
+    (strides (1, n0)), the layout the library reads without a copy."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(np.asarray(a).T))   # rows = columns of a
+    if pin:
+        t = t.pin_memory()
+    elif device is not None and str(device) != "cpu":
+        t = t.to(device)
+    return t.t()
+
+
 def _ptr(x):
     return x.data_ptr() if _is_torch(x) else x.ctypes.data
 
@@ -158,7 +174,7 @@ def _iscomplex(x) -> bool:
 # ---------------------------------------------------------------------------
 def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
                epstein_nesbet=False, graph_iters=None, max_slices=None, slice_tol=None,
-               A_out=None, E_out=None, stream=None, check=True):
+               profile=False, A_out=None, E_out=None, stream=None, check=True):
     """All eigenpairs of M = diag(theta) + lam * Delta by the DPT map (dpt_solve_full).
 
     Returns (A, E, info): A[:, i] is eigenvector i with A[i, i] = 1 and
@@ -173,7 +189,8 @@ def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
     E = _empty_vec(n, delta, cplx) if E_out is None else E_out
     lda = A.stride(1) if _is_torch(A) else A.strides[1] // A.itemsize
     o = options(tol=tol, max_iter=max_iter, prec=prec, epstein_nesbet=int(bool(epstein_nesbet)),
-                graph_iters=graph_iters, max_slices=max_slices, slice_tol=slice_tol)
+                graph_iters=graph_iters, max_slices=max_slices, slice_tol=slice_tol,
+                profile=int(bool(profile)))
     info = Info()
     st = lib().dpt_solve_full(n, C128 if cplx else R64, th_ptr, d_ptr, ldd, float(lam),
                               ctypes.byref(o), _ptr(A), lda, _ptr(E), ctypes.byref(info),

@@ -23,8 +23,9 @@ def dpt():
 
 
 def _dev(cfg):
+    from paper_2002_12872_gb300 import dpt
     th = torch.tensor(cfg["theta"], device="cuda")
-    D = torch.tensor(np.asfortranarray(cfg["delta"]), device="cuda")
+    D = dpt.colmajor_tensor(cfg["delta"], "cuda")
     return th, D
 
 
@@ -166,3 +167,40 @@ def test_full_size_unsymmetric_sampled_columns(ora, dpt):
     s = np.abs(cfg["theta"]).max() + cfg["lam"] * np.abs(cfg["delta"]).sum(1).max()
     rho = np.linalg.norm(R, axis=0) / (s * np.linalg.norm(An, axis=0))
     assert rho.max() <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_profiled_solve_reports_product_time(dpt, prec):
+    cfg = inputs.full_unsymmetric(n=300)
+    th, D = _dev(cfg)
+    A1, E1, i1 = dpt.solve_full(th, D, cfg["lam"], prec=prec, profile=True)
+    A2, E2, i2 = dpt.solve_full(th, D, cfg["lam"], prec=prec, profile=False)
+    assert i1["product_launches"] == i1["iters"] + (1 if prec == "fp64" else 0) or \
+        i1["product_launches"] >= i1["iters"]
+    assert i1["product_ms"] > 0 and i2["product_ms"] == 0
+    assert i1["launches"] > i1["product_launches"]
+    assert np.abs(to_np(A1) - to_np(A2)).max() == 0.0
+
+
+@pytest.mark.parametrize("n", [3, 5, 17, 63, 127, 128, 129, 255, 257, 383, 640])
+def test_mixed_size_sweep(ora, dpt, n):
+    """Tile edges and ragged tails of the 128 x 128 tiles and 64-wide K blocks."""
+    cfg = inputs.full_unsymmetric(n=n)
+    Ao, Eo, io = ora.solve_full(cfg["theta"], cfg["delta"], cfg["lam"], tol=1e-13)
+    assert io["status"] == "OK"
+    th, D = _dev(cfg)
+    A, E, info = dpt.solve_full(th, D, cfg["lam"], prec="mixed")
+    ee, ve = _parity(A, E, Ao, Eo)
+    assert ee <= EIG_RTOL and ve <= VEC_TOL, (n, ee, ve, info)
+
+
+def test_repeated_solves_identical(dpt):
+    """The same problem twice through the pooled workspace gives identical bits
+    (deterministic reductions, no state leaking between calls)."""
+    cfg = inputs.full_unsymmetric(n=700)
+    th, D = _dev(cfg)
+    A1, E1, _ = dpt.solve_full(th, D, cfg["lam"])
+    other = inputs.full_symmetric(n=333)
+    dpt.solve_full(*_dev(other), other["lam"])
+    A2, E2, _ = dpt.solve_full(th, D, cfg["lam"])
+    assert torch.equal(A1, A2) and torch.equal(E1, E2)
