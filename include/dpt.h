@@ -137,6 +137,27 @@ DPT_API dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* thet
                           const dpt_options* opt, void* A_out, int64_t ld_a,
                           void* E_out, dpt_info* info, void* stream);
 
+/* Dominant eigenvector: the eigenpair continued from e_{n*}, by the single-vector
+ * map of Eq. (single_line_dyn) (Sec. II.H; for a perturbative matrix this is the
+ * eigenvector of the largest eigenvalue when n* = argmax theta).
+ *   n          size, 1 <= n < 2^31 - 1
+ *   theta      n doubles, finite; theta_m != theta_{n*} for every m != n*
+ *   row_ptr    n + 1 int32, row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz
+ *   col_idx    nnz int32 in [0, n)          (CSR of Delta, rows m)
+ *   vals       nnz float (FP32 values; used exactly, promoted to the working precision)
+ *   nstar      eigenvector index, or -1 for the first index of max theta
+ *   lambda     real perturbation strength
+ *   opt        options (prec: DPT_PREC_MIXED_BF16 = float-float working precision
+ *              on the FP32 pipes, DPT_PREC_FP64 = plain FP64 arithmetic)
+ *   z_out      n doubles: the eigenvector with z_out[n*] = 1
+ *   E_out      one double: E = theta_{n*} + lambda (Delta z)_{n*}
+ * Errors as for dpt_solve_full; a malformed CSR structure gives DPT_ERR_ARG
+ * before any kernel follows it.  Blocks until done. */
+DPT_API dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int32_t* row_ptr,
+                                      const int32_t* col_idx, const float* vals, int64_t nstar,
+                                      double lambda, const dpt_options* opt, double* z_out,
+                                      double* E_out, dpt_info* info, void* stream);
+
 /* Free the scratch pool of the current device (no solve may be running). */
 DPT_API void dpt_release_workspace(void);
 

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dpt.h"
@@ -49,6 +50,8 @@ bool is_device_ptr(const void* p) {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+constexpr size_t kPinnedBytes = 4096;   // pinned host scratch for state read-backs
+
 // A block of device scratch memory plus the resources a solve needs with it.
 struct Block {
   int dev = -1;
@@ -76,7 +79,7 @@ Block* acquire(size_t bytes) {
   if (!pick) {
     pick = new Block();
     pick->dev = dev;
-    if (cudaHostAlloc((void**)&pick->host_state, sizeof(IterState), cudaHostAllocDefault) !=
+    if (cudaHostAlloc((void**)&pick->host_state, kPinnedBytes, cudaHostAllocDefault) !=
             cudaSuccess ||
         cudaStreamCreateWithFlags(&pick->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&pick->ev, cudaEventDisableTiming) != cudaSuccess) {
@@ -235,7 +238,7 @@ struct Prof {
 // ST_RUNNING.  One small device-to-host read of the state per chunk.
 template <class F>
 void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kernels_per_iter,
-              Prof& prof, F&& iter) {
+              Prof& prof, F&& iter, size_t state_bytes = sizeof(IterState)) {
   cudaStream_t s = b->stream;
   const int per = graph_iters > 0 ? graph_iters : 4;
   prof.make(per);
@@ -259,7 +262,7 @@ void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kerne
         for (int q = 0; q < per; ++q) iter(q);
       }
       prof.launches += per * kernels_per_iter;
-      CK(cudaMemcpyAsync(b->host_state, dst, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(b->host_state, dst, state_bytes, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       const bool running = b->host_state->status == ST_RUNNING;
       prof.collect(running ? per : std::max(0, b->host_state->k - k0 + 1));
@@ -542,6 +545,133 @@ dpt_status solve_full_fp64(int64_t n64, bool cplx, const std::vector<double>& th
   return ret;
 }
 
+// ---------------------------------------------------------------------------
+// Dominant eigenvector, CSR perturbation
+// ---------------------------------------------------------------------------
+dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_ptr,
+                          const int32_t* col_idx, const float* vals, int64_t nstar,
+                          double lambda, const dpt_options& o, double* z_out, double* E_out,
+                          dpt_info* info, cudaStream_t user) {
+  const int n = (int)n64;
+  const bool th_dev = is_device_ptr(theta), rp_dev = is_device_ptr(row_ptr),
+             ci_dev = is_device_ptr(col_idx), va_dev = is_device_ptr(vals),
+             z_dev = is_device_ptr(z_out), e_dev = is_device_ptr(E_out);
+  int32_t nnz32 = 0;
+  if (rp_dev) CK(cudaMemcpy(&nnz32, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  else nnz32 = row_ptr[n];
+  if (nnz32 < 0) return DPT_ERR_ARG;
+  const int64_t nnz = nnz32;
+  const bool ff = o.prec != DPT_PREC_FP64;
+  const int G = dom_blocks(n);
+  auto layout = [&](Carve& c) {
+    c.take<DomState>(1);
+    c.take<float>(n); c.take<float>(n);                 // theta float-float
+    for (int q = 0; q < 4; ++q) c.take<float>(n);       // z float-float ping-pong
+    if (!ff) { c.take<double>(n); c.take<double>(n); }  // z FP64 ping-pong
+    c.take<double>((size_t)2 * G);                      // block partials
+    if (!th_dev) c.take<double>(n);
+    if (!rp_dev) c.take<int32_t>(n + 1);
+    if (!ci_dev) c.take<int32_t>(nnz > 0 ? nnz : 1);
+    if (!va_dev) c.take<float>(nnz > 0 ? nnz : 1);
+    if (!z_dev) c.take<double>(n);
+  };
+  Block* b = acquire(measure(layout));
+  dpt_status ret = DPT_OK;
+  try {
+    Carve c{(char*)b->ptr};
+    DomState* st = c.take<DomState>(1);
+    float* thh = c.take<float>(n);
+    float* thl = c.take<float>(n);
+    float* zh[2]; float* zl[2];
+    for (int q = 0; q < 2; ++q) { zh[q] = c.take<float>(n); zl[q] = c.take<float>(n); }
+    double* z64[2] = {nullptr, nullptr};
+    if (!ff) { z64[0] = c.take<double>(n); z64[1] = c.take<double>(n); }
+    double* part = c.take<double>((size_t)2 * G);
+    cudaStream_t s = b->stream;
+    CK(cudaEventRecord(b->ev, user));
+    CK(cudaStreamWaitEvent(s, b->ev, 0));
+    auto stage = [&](auto* src, bool dev, size_t count) {
+      using T = std::remove_const_t<std::remove_pointer_t<decltype(src)>>;
+      if (dev) return const_cast<T*>(src);
+      T* d = c.take<T>(count > 0 ? count : 1);
+      if (count) CK(cudaMemcpyAsync(d, src, sizeof(T) * count, cudaMemcpyHostToDevice, s));
+      return d;
+    };
+    const double* thd = stage(theta, th_dev, n);
+    const int32_t* rpd = stage(row_ptr, rp_dev, (size_t)n + 1);
+    const int32_t* cid = stage(col_idx, ci_dev, (size_t)nnz);
+    const float* vad = stage(vals, va_dev, (size_t)nnz);
+    double* zstage = z_dev ? z_out : c.take<double>(n);
+
+    DomState h{};
+    h.status = ST_RUNNING;
+    h.max_iter = o.max_iter;
+    h.nstar_req = (int)nstar;
+    h.nstar_min = 0x7fffffff;
+    h.lam = lambda;
+    h.lam_hi = (float)lambda;
+    h.lam_lo = (float)(lambda - (double)h.lam_hi);
+    h.tol = o.tol;
+    h.best = INFINITY;
+    DomState* hs = reinterpret_cast<DomState*>(b->host_state);   // pinned scratch (large enough)
+    static_assert(sizeof(DomState) <= kPinnedBytes, "pinned scratch size");
+    *hs = h;
+    CK(cudaMemcpyAsync(st, hs, sizeof(DomState), cudaMemcpyHostToDevice, s));
+    // the CSR structure is validated before anything follows it
+    CK(launch_dom_check(n, nnz, rpd, st, s));
+    CK(cudaMemcpyAsync(hs, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs->bad_input) throw Fail{DPT_ERR_ARG};
+    CK(launch_dom_setup(n, thd, rpd, cid, vad, thh, thl, st, s));
+    CK(cudaMemcpyAsync(hs, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs->bad_input) throw Fail{DPT_ERR_ARG};
+    if (hs->ties != 1u) throw Fail{DPT_ERR_DEGENERATE};
+    const int nst = hs->nstar;
+    CK(launch_dom_init(n, zh[0], zl[0], z64[0], ff, st, s));
+    const double avg = n > 0 ? (double)nnz / n : 0.0;
+    const int V = avg < 24 ? 4 : (avg < 48 ? 8 : (avg < 96 ? 16 : 32));
+    Prof prof;
+    prof.on = o.profile != 0;
+    prof.launches = 9;
+    CK(cudaMemcpyAsync(b->host_state, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    // run_loop reads k from host_state; DomState and IterState share the layout of k/status
+    run_loop(b, reinterpret_cast<IterState*>(st), o.graph_iters, o.max_iter, 2, prof,
+             [&](int q) {
+               prof.before(q, s);
+               CK(launch_dom_iter(n, V, ff, rpd, cid, vad, thh, thl, thd, zh[0], zl[0], zh[1],
+                                  zl[1], z64[0], z64[1], part, st, s));
+               prof.after(q, s);
+             },
+             sizeof(DomState));
+    CK(launch_dom_out(n, zh[0], zl[0], zh[1], zl[1], z64[0], z64[1], ff, zstage, st, s));
+    prof.launches += 1;
+    if (!z_dev) CK(cudaMemcpyAsync(z_out, zstage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hs, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ret = from_state(hs->status);
+    if (e_dev) CK(cudaMemcpy(E_out, &hs->E, sizeof(double), cudaMemcpyHostToDevice));
+    else *E_out = hs->E;
+    if (info) {
+      info->iters = hs->k;
+      info->residual = hs->rho;
+      info->status = ret;
+      info->nstar = nst;
+      info->launches = prof.launches;
+      info->product_launches = prof.live;
+      info->product_ms = prof.ms;
+    }
+    CK(cudaEventRecord(b->ev, s));
+    CK(cudaStreamWaitEvent(user, b->ev, 0));
+  } catch (Fail f) {
+    cudaStreamSynchronize(b->stream);
+    ret = f.st;
+  }
+  release(b);
+  return ret;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -629,6 +759,33 @@ dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const
                            lambda, o, (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info,
                            s);
     return done(st);
+  } catch (Fail f) {
+    return done(f.st);
+  } catch (...) {
+    return done(DPT_ERR_CUDA);
+  }
+}
+
+dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int32_t* row_ptr,
+                              const int32_t* col_idx, const float* vals, int64_t nstar,
+                              double lambda, const dpt_options* opt, double* z_out,
+                              double* E_out, dpt_info* info, void* stream) {
+  Timer timer;
+  if (info) { std::memset(info, 0, sizeof(*info)); info->status = DPT_ERR_ARG; info->nstar = -1; }
+  dpt_options o;
+  dpt_options_default(&o);
+  if (opt) o = *opt;
+  auto done = [&](dpt_status st) {
+    if (info) { info->status = st; info->seconds = timer.sec(); }
+    return st;
+  };
+  if (n < 1 || n > 0x7ffffffe || !theta || !row_ptr || !col_idx || !vals || !z_out || !E_out ||
+      nstar >= n || !std::isfinite(lambda) || !(o.tol > 0) || o.max_iter < 0 ||
+      (o.prec != DPT_PREC_FP64 && o.prec != DPT_PREC_MIXED_BF16))
+    return done(DPT_ERR_ARG);
+  try {
+    return done(solve_dominant(n, theta, row_ptr, col_idx, vals, nstar < 0 ? -1 : nstar, lambda,
+                               o, z_out, E_out, info, (cudaStream_t)stream));
   } catch (Fail f) {
     return done(f.st);
   } catch (...) {

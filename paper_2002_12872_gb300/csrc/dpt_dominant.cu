@@ -1,0 +1,442 @@
+// Dominant eigenvector by the single-vector map of Eq. (single_line_dyn)
+// (arXiv:2002.12872, Sec. II.H) with a CSR perturbation:
+//     y   = Delta z,     y* = y_{n*},     E = theta_{n*} + lambda y*,
+//     R_m = lambda (y_m - y* z_m) - (theta_{n*} - theta_m) z_m      (m != n*)
+//     z_m <- z_m + R_m / (theta_{n*} - theta_m)  =  lambda (y_m - y* z_m) / (theta_{n*} - theta_m)
+// R is the explicit eigen-residual (M z - E z)_m of the current iterate, so its
+// norm is the convergence test.  Two arithmetic variants:
+//   FF    z, y, R carried as float-float (about 48 bits) on the FP32 pipes: every
+//         nonzero costs a few FP32 operations, no FP64 instruction;
+//   FP64  plain double arithmetic (the comparator; FP64-pipe bound on this GPU).
+// The matrix stream (FP32 values + int32 column indices) is read once per
+// iteration with coalesced loads; z (16 B per row in FF form) is gathered
+// through L2.
+#include <cuda_runtime.h>
+
+#include "dpt_device.cuh"
+#include "dpt_internal.h"
+
+namespace dpt {
+
+// float-float product of a float and an (h, l) pair, accumulated into (ah, al)
+__device__ __forceinline__ void ff_fma_acc(float v, float zh, float zl, float& ah, float& al) {
+  float p, pe;
+  two_prod(v, zh, p, pe);
+  pe = fmaf(v, zl, pe);
+  float s, se;
+  two_sum(ah, p, s, se);
+  se += al + pe;
+  fast_two_sum(s, se, ah, al);
+}
+__device__ __forceinline__ void ff_add(float ah, float al, float bh, float bl, float& rh,
+                                       float& rl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e += al + bl;
+  fast_two_sum(s, e, rh, rl);
+}
+// (ah, al) * (bh, bl)
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float& rh,
+                                       float& rl) {
+  float p, pe;
+  two_prod(ah, bh, p, pe);
+  pe = fmaf(ah, bl, fmaf(al, bh, pe));
+  fast_two_sum(p, pe, rh, rl);
+}
+
+// ---------------------------------------------------------------------------
+// Set-up: theta -> float-float, residual scale row sums, CSR validity, argmax.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__global__ void k_dom_setup(int n, const double* __restrict__ theta,
+                            const int32_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ col_idx, const float* __restrict__ vals,
+                            float* __restrict__ th_hi, float* __restrict__ th_lo,
+                            DomState* st) {
+  float rmax = 0.f, amax = 0.f;
+  unsigned long long tmax = 0ull;
+  bool bad = false;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    const double t = theta[m];
+    if (!finite_bits(t)) bad = true;
+    float h, l;
+    split_double(t, h, l);
+    th_hi[m] = h;
+    th_lo[m] = l;
+    amax = fmaxf(amax, fabsf(h));
+    tmax = max(tmax, ordered_bits(t));
+    const int a = row_ptr[m], b = row_ptr[m + 1];
+    if (b < a) { bad = true; continue; }
+    float rs = 0.f;
+    for (int q = a; q < b; ++q) {
+      const int c = col_idx[q];
+      const float v = vals[q];
+      if (c < 0 || c >= n || !(fabsf(v) <= 3.4e38f)) bad = true;
+      rs += fabsf(v);
+    }
+    rmax = fmaxf(rmax, rs);
+  }
+  if (bad) atomicExch(&st->bad_input, 1u);
+  for (int o = 16; o > 0; o >>= 1) {
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&st->row_bits, __float_as_uint(rmax));
+    atomicMax(&st->absmax_bits, __float_as_uint(amax));
+    atomicMax(&st->theta_bits, tmax);
+  }
+}
+
+// row_ptr must be monotone from 0 to nnz before any kernel follows it into
+// col_idx / vals.  Reads row_ptr only.
+__global__ void k_dom_check_rowptr(int n, int64_t nnz, const int32_t* __restrict__ row_ptr,
+                                   DomState* st) {
+  bool bad = false;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    const int a = row_ptr[m], b = row_ptr[m + 1];
+    if (a < 0 || b < a || (int64_t)b > nnz) bad = true;
+    if (m == 0 && a != 0) bad = true;
+    if (m == n - 1 && (int64_t)b != nnz) bad = true;
+  }
+  if (bad) atomicExch(&st->bad_input, 1u);
+}
+
+// n* = first index holding the largest theta.
+__global__ void k_dom_argmax(int n, const double* __restrict__ theta, DomState* st) {
+  const unsigned long long tmax = st->theta_bits;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x)
+    if (ordered_bits(theta[m]) == tmax) atomicMin(&st->nstar_min, m);
+}
+
+__global__ void k_dom_pick(DomState* st) {
+  st->nstar = (st->nstar_req >= 0) ? st->nstar_req : st->nstar_min;
+}
+
+// Number of m with theta_m == theta_{n*} (1 unless the map would divide by zero).
+__global__ void k_dom_ties(int n, const double* __restrict__ theta, DomState* st) {
+  const double ts = theta[st->nstar];
+  unsigned cnt = 0;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x)
+    cnt += (theta[m] == ts) ? 1u : 0u;
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->ties, cnt);
+}
+
+// z_0 = e_{n*} and the residual scale s = max|theta| + |lambda| max_m sum_k |Delta_mk|.
+__global__ void k_dom_init(int n, float* __restrict__ zh, float* __restrict__ zl, DomState* st) {
+  const int nstar = st->nstar;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    zh[m] = (m == nstar) ? 1.f : 0.f;
+    zl[m] = 0.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    st->s = (double)__uint_as_float(st->absmax_bits) +
+            fabs(st->lam) * (double)__uint_as_float(st->row_bits);
+}
+
+// ---------------------------------------------------------------------------
+// Pre-pass: y* = (Delta z)_{n*}, one warp.
+// ---------------------------------------------------------------------------
+template <bool FF>
+__global__ void k_dom_ystar(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+                            const float* __restrict__ vals, const float* __restrict__ zh0,
+                            const float* __restrict__ zl0, const float* __restrict__ zh1,
+                            const float* __restrict__ zl1, const double* __restrict__ z64_0,
+                            const double* __restrict__ z64_1, DomState* st) {
+  if (st->status != ST_RUNNING) return;
+  const int lane = threadIdx.x;
+  const int nstar = st->nstar;
+  const int a = row_ptr[nstar], b = row_ptr[nstar + 1];
+  if (FF) {
+    const float* zh = st->cur ? zh1 : zh0;
+    const float* zl = st->cur ? zl1 : zl0;
+    float ah = 0.f, al = 0.f;
+    for (int q = a + lane; q < b; q += 32) {
+      const int c = col_idx[q];
+      ff_fma_acc(vals[q], zh[c], zl[c], ah, al);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, ah, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, al, o);
+      ff_add(ah, al, oh, ol, ah, al);
+    }
+    if (lane == 0) { st->ys_hi = ah; st->ys_lo = al; }
+  } else {
+    const double* z = st->cur ? z64_1 : z64_0;
+    double acc = 0.0;
+    for (int q = a + lane; q < b; q += 32) acc = fma((double)vals[q], z[col_idx[q]], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) st->ys64 = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Main pass: one group of V lanes per row (V = 4, 8, 16 or 32 by mean row
+// length).  Each group sums its row of Delta z, the group leader applies the
+// update and accumulates |R|^2 and |z|^2; per-block partials; the last block
+// reduces them and takes the convergence decision.
+// ---------------------------------------------------------------------------
+template <bool FF, int V>
+__global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ col_idx,
+                                                  const float* __restrict__ vals,
+                                                  const float* __restrict__ th_hi,
+                                                  const float* __restrict__ th_lo,
+                                                  const double* __restrict__ theta,
+                                                  float* __restrict__ zh0, float* __restrict__ zl0,
+                                                  float* __restrict__ zh1, float* __restrict__ zl1,
+                                                  double* __restrict__ z64_0,
+                                                  double* __restrict__ z64_1,
+                                                  double* __restrict__ part, DomState* st) {
+  if (st->status != ST_RUNNING) return;
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (V - 1);
+  const int groups_per_block = blockDim.x / V;
+  const int g0 = blockIdx.x * groups_per_block + threadIdx.x / V;
+  const int gstride = gridDim.x * groups_per_block;
+  const int nstar = st->nstar;
+  const bool c1 = st->cur != 0;
+  const float lam_h = st->lam_hi, lam_l = st->lam_lo;
+  double r2 = 0.0, z2 = 0.0;
+  if (FF) {
+    const float* zh = c1 ? zh1 : zh0;
+    const float* zl = c1 ? zl1 : zl0;
+    float* nzh = c1 ? zh0 : zh1;
+    float* nzl = c1 ? zl0 : zl1;
+    const float ysh = st->ys_hi, ysl = st->ys_lo;
+    const float tsh = th_hi[nstar], tsl = th_lo[nstar];
+    // rows are visited in rounds; every lane runs the same number of rounds
+    const int rounds = (n + gstride - 1) / gstride;
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int m = g0 + rd * gstride;
+      float ah = 0.f, al = 0.f;
+      if (m < n) {
+        const int a = row_ptr[m], b = row_ptr[m + 1];
+        for (int q = a + gl; q < b; q += V) {
+          const int c = col_idx[q];
+          ff_fma_acc(vals[q], zh[c], zl[c], ah, al);
+        }
+      }
+#pragma unroll
+      for (int o = V / 2; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, ah, o);
+        const float ol = __shfl_xor_sync(0xffffffffu, al, o);
+        ff_add(ah, al, oh, ol, ah, al);
+      }
+      if (gl == 0 && m < n) {
+        const float zmh = zh[m], zml = zl[m];
+        if (m == nstar) {
+          nzh[m] = 1.f; nzl[m] = 0.f;
+          z2 += 1.0;
+        } else {
+          // R = lambda (y - y* z) - gap z, all in float-float
+          float t1h, t1l, t2h, t2l, gh, gl2, uh, ul, vh, vl, Rh, Rl;
+          ff_mul(ysh, ysl, zmh, zml, t1h, t1l);
+          ff_add(ah, al, -t1h, -t1l, t2h, t2l);
+          ff_mul(lam_h, lam_l, t2h, t2l, uh, ul);
+          ff_sub(tsh, tsl, th_hi[m], th_lo[m], gh, gl2);
+          ff_mul(gh, gl2, zmh, zml, vh, vl);
+          ff_add(uh, ul, -vh, -vl, Rh, Rl);
+          const float dlt = Rh * __frcp_rn(gh);
+          float nh, nl;
+          ff_add(zmh, zml, dlt, 0.f, nh, nl);
+          nzh[m] = nh;
+          nzl[m] = nl;
+          r2 += (double)Rh * (double)Rh;
+          z2 += (double)zmh * (double)zmh;
+        }
+      }
+    }
+  } else {
+    const double* z = c1 ? z64_1 : z64_0;
+    double* nz = c1 ? z64_0 : z64_1;
+    const double ys = st->ys64;
+    const double ts = theta[nstar];
+    const double lam = st->lam;
+    const int rounds = (n + gstride - 1) / gstride;
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int m = g0 + rd * gstride;
+      double acc = 0.0;
+      if (m < n) {
+        const int a = row_ptr[m], b = row_ptr[m + 1];
+        for (int q = a + gl; q < b; q += V) acc = fma((double)vals[q], z[col_idx[q]], acc);
+      }
+#pragma unroll
+      for (int o = V / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (gl == 0 && m < n) {
+        const double zm = z[m];
+        if (m == nstar) {
+          nz[m] = 1.0;
+          z2 += 1.0;
+        } else {
+          const double gap = ts - theta[m];
+          const double t = acc - ys * zm;
+          const double R = lam * t - gap * zm;
+          nz[m] = lam * t / gap;
+          r2 += R * R;
+          z2 += zm * zm;
+        }
+      }
+    }
+  }
+  // block reduction, then the last block decides
+  for (int o = 16; o > 0; o >>= 1) {
+    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    z2 += __shfl_xor_sync(0xffffffffu, z2, o);
+  }
+  __shared__ double sr[2][8];
+  __shared__ bool last;
+  const int w = threadIdx.x >> 5;
+  if (lane == 0) { sr[0][w] = r2; sr[1][w] = z2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double R2 = 0.0, Z2 = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { R2 += sr[0][q]; Z2 += sr[1][q]; }
+    part[2 * blockIdx.x] = R2;
+    part[2 * blockIdx.x + 1] = Z2;
+    __threadfence();
+    last = (atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // deterministic final reduction by the last block
+  double R2 = 0.0, Z2 = 0.0;
+  for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+    R2 += ((volatile double*)part)[2 * q];
+    Z2 += ((volatile double*)part)[2 * q + 1];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    R2 += __shfl_xor_sync(0xffffffffu, R2, o);
+    Z2 += __shfl_xor_sync(0xffffffffu, Z2, o);
+  }
+  __syncthreads();
+  if (lane == 0) { sr[0][w] = R2; sr[1][w] = Z2; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  R2 = 0.0; Z2 = 0.0;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { R2 += sr[0][q]; Z2 += sr[1][q]; }
+  volatile DomState* vs = st;
+  vs->blocks_done = 0;
+  // eigenvalue of the iterate that was just assessed
+  if (FF) vs->E = theta[nstar] + vs->lam * ((double)vs->ys_hi + (double)vs->ys_lo);
+  else vs->E = theta[nstar] + vs->lam * vs->ys64;
+  const double rho = sqrt(R2) / (vs->s * sqrt(Z2));
+  vs->rho = rho;
+  if (vs->bad_input) { vs->status = ST_BADINPUT; return; }
+  if (!(rho == rho) || isinf(rho)) { vs->status = ST_DIVERGED; return; }
+  if (rho <= vs->tol) { vs->status = ST_CONVERGED; return; }
+  if (rho < vs->best) { vs->best = rho; vs->grown = 0; }
+  else if (rho > 10.0 * vs->best) {
+    if (++vs->grown >= 20) { vs->status = ST_DIVERGED; return; }
+  } else vs->grown = 0;
+  if (vs->k >= vs->max_iter) { vs->status = ST_MAXITER; return; }
+  vs->k = vs->k + 1;
+  vs->cur = vs->k & 1;
+}
+
+// Output: z (float-float or FP64) of the assessed iterate -> FP64.
+__global__ void k_dom_out(int n, const float* __restrict__ zh0, const float* __restrict__ zl0,
+                          const float* __restrict__ zh1, const float* __restrict__ zl1,
+                          const double* __restrict__ z64_0, const double* __restrict__ z64_1,
+                          int ff, double* __restrict__ out, const DomState* st) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  const bool c1 = st->cur != 0;
+  if (ff) out[m] = c1 ? f2d_bits(zh1[m]) + f2d_bits(zl1[m]) : f2d_bits(zh0[m]) + f2d_bits(zl0[m]);
+  else out[m] = c1 ? z64_1[m] : z64_0[m];
+}
+
+__global__ void k_dom_init64(int n, double* z, const DomState* st) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < n) z[m] = (m == st->nstar) ? 1.0 : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static int dom_grid(int n) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 132;
+  }
+  const int want = (n + 255) / 256;
+  return want < 8 * nsm ? (want > 0 ? want : 1) : 8 * nsm;
+}
+
+int dom_blocks(int n) { return dom_grid(n); }
+
+cudaError_t launch_dom_check(int n, int64_t nnz, const int32_t* row_ptr, DomState* st,
+                             cudaStream_t s) {
+  k_dom_check_rowptr<<<dom_grid(n), 256, 0, s>>>(n, nnz, row_ptr, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dom_setup(int n, const double* theta, const int32_t* row_ptr,
+                             const int32_t* col_idx, const float* vals, float* th_hi,
+                             float* th_lo, DomState* st, cudaStream_t s) {
+  const int g = dom_grid(n);
+  k_dom_setup<<<g, 256, 0, s>>>(n, theta, row_ptr, col_idx, vals, th_hi, th_lo, st);
+  k_dom_argmax<<<g, 256, 0, s>>>(n, theta, st);
+  k_dom_pick<<<1, 1, 0, s>>>(st);
+  k_dom_ties<<<g, 256, 0, s>>>(n, theta, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dom_init(int n, float* zh, float* zl, double* z64, int ff, DomState* st,
+                            cudaStream_t s) {
+  const int g = dom_grid(n);
+  k_dom_init<<<g, 256, 0, s>>>(n, zh, zl, st);
+  if (!ff) k_dom_init64<<<(n + 255) / 256, 256, 0, s>>>(n, z64, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dom_iter(int n, int vlanes, int ff, const int32_t* row_ptr,
+                            const int32_t* col_idx, const float* vals, const float* th_hi,
+                            const float* th_lo, const double* theta, float* zh0, float* zl0,
+                            float* zh1, float* zl1, double* z64_0, double* z64_1, double* part,
+                            DomState* st, cudaStream_t s) {
+  if (ff)
+    k_dom_ystar<true><<<1, 32, 0, s>>>(row_ptr, col_idx, vals, zh0, zl0, zh1, zl1, z64_0, z64_1, st);
+  else
+    k_dom_ystar<false><<<1, 32, 0, s>>>(row_ptr, col_idx, vals, zh0, zl0, zh1, zl1, z64_0, z64_1, st);
+  const int g = dom_grid(n);
+#define DOM_LAUNCH(FFV, VV)                                                                    \
+  k_dom_iter<FFV, VV><<<g, 256, 0, s>>>(n, row_ptr, col_idx, vals, th_hi, th_lo, theta, zh0, \
+                                        zl0, zh1, zl1, z64_0, z64_1, part, st)
+  if (ff) {
+    switch (vlanes) {
+      case 4: DOM_LAUNCH(true, 4); break;
+      case 8: DOM_LAUNCH(true, 8); break;
+      case 16: DOM_LAUNCH(true, 16); break;
+      default: DOM_LAUNCH(true, 32); break;
+    }
+  } else {
+    switch (vlanes) {
+      case 4: DOM_LAUNCH(false, 4); break;
+      case 8: DOM_LAUNCH(false, 8); break;
+      case 16: DOM_LAUNCH(false, 16); break;
+      default: DOM_LAUNCH(false, 32); break;
+    }
+  }
+#undef DOM_LAUNCH
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dom_out(int n, const float* zh0, const float* zl0, const float* zh1,
+                           const float* zl1, const double* z64_0, const double* z64_1, int ff,
+                           double* out, const DomState* st, cudaStream_t s) {
+  k_dom_out<<<(n + 255) / 256, 256, 0, s>>>(n, zh0, zl0, zh1, zl1, z64_0, z64_1, ff, out, st);
+  return cudaGetLastError();
+}
+
+}  // namespace dpt

@@ -46,6 +46,34 @@ struct IterState {
   double rho_last;
 };
 
+// State of a dominant-eigenvector solve (single-vector map), device resident.
+struct DomState {
+  int k;                 // index of the current iterate z_k
+  int status;            // ST_*
+  int cur;               // ping-pong index of z_k
+  int grown;
+  int max_iter;
+  int nstar;             // eigenvector index in use
+  int nstar_req;         // requested index, -1 = argmax theta
+  int nstar_min;         // first index of the largest theta (atomicMin scratch)
+  unsigned ties;         // number of m with theta_m == theta_{n*}
+  unsigned blocks_done;
+  unsigned row_bits;     // max_m sum_k |Delta_mk| (float bits)
+  unsigned absmax_bits;  // max |theta| (float bits)
+  unsigned bad_input;
+  unsigned pad;
+  unsigned long long theta_bits;   // largest theta, order-preserving bits
+  double lam;
+  float lam_hi, lam_lo;
+  float ys_hi, ys_lo;    // y* = (Delta z)_{n*}, float-float
+  double ys64;           // y* in FP64 (FP64 variant)
+  double s;              // residual scale
+  double tol;
+  double rho;
+  double best;
+  double E;              // eigenvalue of the assessed iterate
+};
+
 // Arguments of the tensor-core iteration kernel (mixed path, real).
 struct GemmEpiParams {
   int n;               // matrix size
@@ -96,5 +124,23 @@ cudaError_t launch_epi_f64(int n, int ld, int cplx, const double* theta, double 
                            const double* P, const double* Acur, double* Anext,
                            const double* Dl, int64_t ldd, double* E, IterState* st,
                            int first, cudaStream_t s);
+
+// Dominant form (CSR)
+int dom_blocks(int n);
+cudaError_t launch_dom_check(int n, int64_t nnz, const int32_t* row_ptr, DomState* st,
+                             cudaStream_t s);
+cudaError_t launch_dom_setup(int n, const double* theta, const int32_t* row_ptr,
+                             const int32_t* col_idx, const float* vals, float* th_hi,
+                             float* th_lo, DomState* st, cudaStream_t s);
+cudaError_t launch_dom_init(int n, float* zh, float* zl, double* z64, int ff, DomState* st,
+                            cudaStream_t s);
+cudaError_t launch_dom_iter(int n, int vlanes, int ff, const int32_t* row_ptr,
+                            const int32_t* col_idx, const float* vals, const float* th_hi,
+                            const float* th_lo, const double* theta, float* zh0, float* zl0,
+                            float* zh1, float* zl1, double* z64_0, double* z64_1, double* part,
+                            DomState* st, cudaStream_t s);
+cudaError_t launch_dom_out(int n, const float* zh0, const float* zl0, const float* zh1,
+                           const float* zl1, const double* z64_0, const double* z64_1, int ff,
+                           double* out, const DomState* st, cudaStream_t s);
 
 }  // namespace dpt

@@ -70,6 +70,9 @@ def lib() -> ctypes.CDLL:
                                      ctypes.POINTER(Options), P, i64, P,
                                      ctypes.POINTER(Info), P]
         L.dpt_solve_full.restype = ctypes.c_int
+        L.dpt_solve_dominant.argtypes = [i64, P, P, P, P, i64, dbl, ctypes.POINTER(Options),
+                                         P, P, ctypes.POINTER(Info), P]
+        L.dpt_solve_dominant.restype = ctypes.c_int
         L.dpt_release_workspace.argtypes = []
         L.dpt_release_workspace.restype = None
         _lib = L
@@ -198,6 +201,34 @@ def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
     res = (A, E, info.as_dict())
     if check and st != OK:
         err = RuntimeError(f"dpt_solve_full: {status_string(st)}")
+        err.result = res
+        raise err
+    return res
+
+
+def solve_dominant(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, prec="mixed", tol=1e-12,
+                   max_iter=200, graph_iters=None, profile=False, z_out=None, stream=None,
+                   check=True):
+    """Dominant eigenpair by the single-vector map (dpt_solve_dominant) for a CSR
+    perturbation (int32 row_ptr / col_idx, FP32 values).  Returns (z, E, info)
+    with z[n*] = 1."""
+    n = int(theta.shape[0])
+    th_ptr, k1 = _vec_ptr(theta, "float64")
+    rp_ptr, k2 = _vec_ptr(row_ptr, "int32")
+    ci_ptr, k3 = _vec_ptr(col_idx, "int32")
+    va_ptr, k4 = _vec_ptr(vals, "float32")
+    if z_out is None:
+        z_out = _empty_vec(n, theta, False)
+    E = np.zeros(1)
+    o = options(tol=tol, max_iter=max_iter, prec=prec, graph_iters=graph_iters,
+                profile=int(bool(profile)))
+    info = Info()
+    st = lib().dpt_solve_dominant(n, th_ptr, rp_ptr, ci_ptr, va_ptr, int(nstar), float(lam),
+                                  ctypes.byref(o), _ptr(z_out), E.ctypes.data,
+                                  ctypes.byref(info), _stream_of(theta, stream))
+    res = (z_out, float(E[0]), info.as_dict())
+    if check and st != OK:
+        err = RuntimeError(f"dpt_solve_dominant: {status_string(st)}")
         err.result = res
         raise err
     return res
