@@ -60,7 +60,8 @@ typedef enum {
   DPT_ERR_NOMEM = -5,         /* device or host allocation failed */
   DPT_ERR_CUDA = -6,          /* a CUDA runtime call failed */
   DPT_ERR_TIMEOUT = -7,       /* a bounded device-side wait expired */
-  DPT_ERR_UNSUPPORTED = -8    /* option combination not implemented */
+  DPT_ERR_UNSUPPORTED = -8,   /* option combination not implemented */
+  DPT_ERR_TOO_LARGE = -9      /* problem larger than a fixed-size entry point accepts */
 } dpt_status;
 
 typedef enum {
@@ -157,6 +158,38 @@ DPT_API dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int3
                                       const int32_t* col_idx, const float* vals, int64_t nstar,
                                       double lambda, const dpt_options* opt, double* z_out,
                                       double* E_out, dpt_info* info, void* stream);
+
+/* dpt_solve_dominant for callers that cannot allocate device memory.  (This entry
+ * point has no counterpart in the paper; it is a deployment variant of
+ * dpt_solve_dominant.)
+ *
+ * Some callers may not call cudaMalloc at all: code running inside a host callback
+ * or while another component is capturing a CUDA graph, processes whose device
+ * memory is entirely owned by a framework's caching allocator, and latency-critical
+ * loops that must not take the driver's allocation path.  The other entry points
+ * take their scratch from a pool that grows with cudaMalloc; this one allocates
+ * nothing.  Its scratch is a fixed 6.4 MB block of device memory built into the
+ * library, which every GPU that loads the library holds until the process exits.
+ *
+ *   Limits: n <= 262144 rows (larger problems return DPT_ERR_TOO_LARGE at once);
+ *   float-float working precision only (the default of dpt_solve_dominant).
+ *   theta, row_ptr, col_idx, vals and z_out must be device pointers (there is no
+ *   scratch to stage host buffers through); E_out may be host or device.
+ *   Arguments otherwise as for dpt_solve_dominant; tol and max_iter replace the
+ *   options struct.
+ *   The first call on each device looks up the block's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before
+ *   any stream capture begins.
+ *   All calls share the one block, which keeps the previous call's contents (each
+ *   call rewrites everything it reads).  Calls whose GPU work overlaps — on
+ *   different streams or from different threads — race on the block and give
+ *   wrong results: issue them in order, e.g. on one stream.
+ *   Work runs on `stream`; the call blocks until its results are ready. */
+DPT_API dpt_status dpt_solve_dominant_noalloc(int64_t n, const double* theta,
+                                              const int32_t* row_ptr, const int32_t* col_idx,
+                                              const float* vals, int64_t nstar, double lambda,
+                                              double tol, int32_t max_iter, double* z_out,
+                                              double* E_out, dpt_info* info, void* stream);
 
 /* Free the scratch pool of the current device (no solve may be running). */
 DPT_API void dpt_release_workspace(void);

@@ -704,6 +704,7 @@ const char* dpt_status_string(dpt_status s) {
     case DPT_ERR_CUDA: return "DPT_ERR_CUDA";
     case DPT_ERR_TIMEOUT: return "DPT_ERR_TIMEOUT";
     case DPT_ERR_UNSUPPORTED: return "DPT_ERR_UNSUPPORTED";
+    case DPT_ERR_TOO_LARGE: return "DPT_ERR_TOO_LARGE";
   }
   return "DPT_UNKNOWN";
 }

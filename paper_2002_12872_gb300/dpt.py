@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libdpt.so")
 OK, PENDING = 0, 1
 STATUS = {0: "OK", 1: "PENDING", -1: "ERR_ARG", -2: "ERR_DEGENERATE", -3: "ERR_MAXITER",
           -4: "ERR_DIVERGED", -5: "ERR_NOMEM", -6: "ERR_CUDA", -7: "ERR_TIMEOUT",
-          -8: "ERR_UNSUPPORTED"}
+          -8: "ERR_UNSUPPORTED", -9: "ERR_TOO_LARGE"}
 R64, C128 = 0, 1
 PREC = {"fp64": 0, "mixed": 1, "bf16": 1}
 
@@ -73,6 +73,9 @@ def lib() -> ctypes.CDLL:
         L.dpt_solve_dominant.argtypes = [i64, P, P, P, P, i64, dbl, ctypes.POINTER(Options),
                                          P, P, ctypes.POINTER(Info), P]
         L.dpt_solve_dominant.restype = ctypes.c_int
+        L.dpt_solve_dominant_noalloc.argtypes = [i64, P, P, P, P, i64, dbl, dbl,
+                                                 ctypes.c_int32, P, P, ctypes.POINTER(Info), P]
+        L.dpt_solve_dominant_noalloc.restype = ctypes.c_int
         L.dpt_release_workspace.argtypes = []
         L.dpt_release_workspace.restype = None
         _lib = L
@@ -229,6 +232,27 @@ def solve_dominant(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, prec="mixed"
     res = (z_out, float(E[0]), info.as_dict())
     if check and st != OK:
         err = RuntimeError(f"dpt_solve_dominant: {status_string(st)}")
+        err.result = res
+        raise err
+    return res
+
+
+def solve_dominant_noalloc(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, tol=1e-12,
+                           max_iter=200, z_out=None, stream=None, check=True):
+    """dpt_solve_dominant_noalloc: the dominant solve for callers that cannot allocate
+    device memory (fixed built-in scratch, n <= 262144, device inputs only)."""
+    n = int(theta.shape[0])
+    if z_out is None:
+        z_out = _empty_vec(n, theta, False)
+    E = np.zeros(1)
+    info = Info()
+    st = lib().dpt_solve_dominant_noalloc(n, _ptr(theta), _ptr(row_ptr), _ptr(col_idx),
+                                          _ptr(vals), int(nstar), float(lam), float(tol),
+                                          int(max_iter), _ptr(z_out), E.ctypes.data,
+                                          ctypes.byref(info), _stream_of(theta, stream))
+    res = (z_out, float(E[0]), info.as_dict())
+    if check and st != OK:
+        err = RuntimeError(f"dpt_solve_dominant_noalloc: {status_string(st)}")
         err.result = res
         raise err
     return res
