@@ -138,6 +138,26 @@ DPT_API dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* thet
                           const dpt_options* opt, void* A_out, int64_t ld_a,
                           void* E_out, dpt_info* info, void* stream);
 
+/* Many independent full-spectrum problems in one grouped solve (mixed path): every
+ * stage of an iteration is one launch over all problems' tiles, and each problem
+ * stops at its own convergence (Sec. II.B: each problem is its own fixed-point
+ * iteration).  Arrays of length count:
+ *   n[p]         size of problem p, 1 <= n[p] <= 65536
+ *   theta[p]     device pointer, n[p] distinct finite doubles
+ *   delta[p]     device pointer, column-major n[p] x n[p], leading dimension ld_delta[p]
+ *   lambda[p]    real perturbation strength
+ *   A_out[p], E_out[p]   device outputs as for dpt_solve_full (leading dimension ld_a[p])
+ *   infos[p]     optional per-problem diagnostics (status of each problem)
+ * All pointers must be device pointers (DPT_ERR_UNSUPPORTED otherwise); only
+ * opt->prec == DPT_PREC_MIXED_BF16 without the Epstein-Nesbet shift is supported.
+ * Returns DPT_OK when every problem converged, else the first failing problem's
+ * status (infos[p] tells which).  Blocks until done. */
+DPT_API dpt_status dpt_solve_batched(int64_t count, const int64_t* n, const double* const* theta,
+                                     const double* const* delta, const int64_t* ld_delta,
+                                     const double* lambda, const dpt_options* opt,
+                                     double* const* A_out, const int64_t* ld_a,
+                                     double* const* E_out, dpt_info* infos, void* stream);
+
 /* Dominant eigenvector: the eigenpair continued from e_{n*}, by the single-vector
  * map of Eq. (single_line_dyn) (Sec. II.H; for a perturbative matrix this is the
  * eigenvector of the largest eigenvalue when n* = argmax theta).

@@ -166,6 +166,7 @@ dpt_status from_state(int s) {
     case ST_DIVERGED: return DPT_ERR_DIVERGED;
     case ST_TIMEOUT: return DPT_ERR_TIMEOUT;
     case ST_BADINPUT: return DPT_ERR_ARG;
+    case ST_DEGENERATE: return DPT_ERR_DEGENERATE;
     default: return DPT_ERR_CUDA;
   }
 }
@@ -672,6 +673,203 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
   return ret;
 }
 
+// ---------------------------------------------------------------------------
+// Grouped solve of many independent real problems (mixed path)
+// ---------------------------------------------------------------------------
+// Tile width for a problem of size n: ceil(n / 256) column tiles, each the
+// smallest multiple of 32 covering its share.
+int group_tile_n(int n) {
+  const int ntn = (n + 255) / 256;
+  const int w = (n + ntn - 1) / ntn;
+  return (w + 31) / 32 * 32;
+}
+
+struct GroupPlan {
+  std::vector<GProb> probs;
+  std::vector<int2> tiles;      // product kernel: (problem, tile)
+  std::vector<int4> prep;       // (problem, col block, row block) 32 x 32
+  std::vector<int4> blk128;     // (problem, col tile, row tile) 128 x 128
+  size_t bytes = 0;
+};
+
+// Lays out every problem's work arrays in one arena at `base` (nullptr: size only).
+void plan_group(GroupPlan& g, int count, const int64_t* n, const double* const* theta,
+                const double* const* delta, const int64_t* ld_delta, const double* lambda,
+                double* const* A_out, const int64_t* ld_a, double* const* E_out,
+                const dpt_options& o, char* base, IterState* states_dev) {
+  Carve c{base};
+  g.probs.assign(count, GProb{});
+  g.tiles.clear(); g.prep.clear(); g.blk128.clear();
+  for (int p = 0; p < count; ++p) {
+    GProb& P = g.probs[p];
+    const int np = (int)n[p];
+    const int ld = (int)round_up(np, 128);
+    P.n = np; P.ld = ld; P.ntm = (np + 127) / 128; P.bn = group_tile_n(np);
+    P.ntn = (np + P.bn - 1) / P.bn;
+    P.lam = (float)lambda[p];
+    P.lam_lo = (float)(lambda[p] - (double)P.lam);
+    P.lam64 = lambda[p];
+    P.theta = theta[p];
+    P.delta_in = delta[p];
+    P.ld_in = ld_delta[p];
+    P.A_out = A_out[p];
+    P.ld_a = ld_a[p];
+    P.E_out = E_out[p];
+    P.st = states_dev + p;
+    P.th_hi = c.take<float>(ld); P.th_lo = c.take<float>(ld);
+    P.d = c.take<double>(ld); P.E = c.take<double>(ld);
+    P.e_col = c.take<float>(ld); P.dprev_col = c.take<float>(ld);
+    P.part = c.take<float>((size_t)4 * P.ntm * ld);
+    P.rowpart = c.take<float>((size_t)P.ntm * ld);
+    P.Dcat = c.take<__nv_bfloat16>((size_t)3 * ld * np);
+    P.cat_ld = (int64_t)3 * ld;
+    for (int q = 0; q < 2; ++q) { P.A_hi[q] = c.take<float>((size_t)ld * np); P.A_lo[q] = c.take<float>((size_t)ld * np); }
+    for (int q = 0; q < 2; ++q) P.dt[q] = c.take<__nv_bfloat16>((size_t)ld * np);
+    P.L = c.take<float>((size_t)ld * np);
+    for (int t = 0; t < P.ntm * P.ntn; ++t) g.tiles.push_back(make_int2(p, t));
+    for (int by = 0; by < (np + 31) / 32; ++by)
+      for (int bx = 0; bx < ld / 32; ++bx) g.prep.push_back(make_int4(p, bx, by, 0));
+    for (int tm = 0; tm < P.ntm; ++tm)
+      for (int tn = 0; tn < P.ntm; ++tn) g.blk128.push_back(make_int4(p, tn, tm, 0));
+  }
+  (void)o;
+  g.bytes = (size_t)round_up((int64_t)c.off, 256) + 256;
+}
+
+dpt_status solve_batched(int count, const int64_t* n, const double* const* theta,
+                         const double* const* delta, const int64_t* ld_delta,
+                         const double* lambda, const dpt_options& o, double* const* A_out,
+                         const int64_t* ld_a, double* const* E_out, dpt_info* infos,
+                         cudaStream_t user) {
+  // sizes of the tables and of the arena
+  GroupPlan g;
+  plan_group(g, count, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, o, nullptr, nullptr);
+  const size_t arena = g.bytes;
+  auto layout = [&](Carve& c) {
+    c.take<IterState>(count);
+    c.take<GProb>(count);
+    c.take<int2>(g.tiles.size());
+    c.take<int4>(g.prep.size());
+    c.take<int4>(g.blk128.size());
+    c.take<int>(4);
+    c.take<char>(arena);
+  };
+  Block* b = acquire(measure(layout));
+  dpt_status ret = DPT_OK;
+  try {
+    Carve c{(char*)b->ptr};
+    IterState* st = c.take<IterState>(count);
+    GProb* probs = c.take<GProb>(count);
+    int2* tiles = c.take<int2>(g.tiles.size());
+    int4* prep = c.take<int4>(g.prep.size());
+    int4* blk = c.take<int4>(g.blk128.size());
+    int* flags = c.take<int>(4);      // [0] running count, [1] timeout
+    char* ar = c.take<char>(arena);
+    plan_group(g, count, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, o, ar, st);
+    // TMA descriptors per problem
+    for (int p = 0; p < count; ++p) {
+      GProb& P = g.probs[p];
+      P.tmA = make_tmap_bf16(P.Dcat, (uint64_t)3 * P.ld, P.n, (uint64_t)3 * P.ld, 128);
+      for (int q = 0; q < 2; ++q) P.tmB[q] = make_tmap_bf16(P.dt[q], P.n, P.n, P.ld, P.bn);
+    }
+    std::vector<IterState> hs(count);
+    for (int p = 0; p < count; ++p) {
+      IterState& h = hs[p];
+      h = IterState{};
+      h.status = ST_RUNNING;
+      h.max_iter = o.max_iter;
+      h.max_slices = o.max_slices;
+      h.slices = o.max_slices;
+      h.lam = lambda[p];
+      h.tol = o.tol;
+      h.slice_tol = o.slice_tol;
+      h.best = INFINITY;
+      h.theta_max = 0.0;   // set by the theta check on the device
+    }
+    cudaStream_t s = b->stream;
+    CK(cudaEventRecord(b->ev, user));
+    CK(cudaStreamWaitEvent(s, b->ev, 0));
+    const int hflags[4] = {count, 0, 0, 0};
+    CK(cudaMemcpyAsync(st, hs.data(), sizeof(IterState) * count, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(probs, g.probs.data(), sizeof(GProb) * count, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(tiles, g.tiles.data(), sizeof(int2) * g.tiles.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(prep, g.prep.data(), sizeof(int4) * g.prep.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(blk, g.blk128.data(), sizeof(int4) * g.blk128.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(flags, hflags, sizeof(hflags), cudaMemcpyHostToDevice, s));
+    CK(g_set_attributes());
+    CK(launch_g_check_theta(probs, count, flags, s));
+    CK(launch_g_prep(probs, prep, (int)g.prep.size(), s));
+    CK(launch_g_iter0(probs, blk, (int)g.blk128.size(), s));
+    CK(launch_g_ctrl(probs, count, flags, s));
+    Prof prof;
+    prof.on = o.profile != 0;
+    prof.launches = 4;
+    // host loop: graph replays of G iterations, stop when no problem runs
+    const int per = o.graph_iters > 0 ? o.graph_iters : 4;
+    prof.make(per);
+    cudaGraphExec_t exec = nullptr;
+    auto iter = [&](int q) {
+      prof.before(q, s);
+      CK(launch_g_gemm_epi(probs, tiles, (int)g.tiles.size(), (unsigned*)(flags + 1), s));
+      prof.after(q, s);
+      CK(launch_g_ctrl(probs, count, flags, s));
+    };
+    if (o.graph_iters > 0) {
+      cudaGraph_t gr;
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      for (int q = 0; q < per; ++q) iter(q);
+      CK(cudaStreamEndCapture(s, &gr));
+      cudaError_t e = cudaGraphInstantiate(&exec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (e != cudaSuccess) throw Fail{DPT_ERR_CUDA};
+    }
+    int* hrun = reinterpret_cast<int*>(b->host_state);
+    try {
+      for (int chunk = 0; chunk < o.max_iter / per + 2; ++chunk) {
+        if (exec) CK(cudaGraphLaunch(exec, s));
+        else for (int q = 0; q < per; ++q) iter(q);
+        prof.launches += 2 * per;
+        CK(cudaMemcpyAsync(hrun, flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        // product time of the launches that did work is not separable per problem
+        // here: all per launches are counted while any problem runs
+        prof.collect(per);
+        if (hrun[0] <= 0 || hrun[1]) break;
+      }
+    } catch (...) {
+      if (exec) cudaGraphExecDestroy(exec);
+      throw;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    CK(launch_g_finalize(probs, blk, (int)g.blk128.size(), s));
+    prof.launches += 1;
+    CK(cudaMemcpyAsync(hs.data(), st, sizeof(IterState) * count, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int p = 0; p < count; ++p) {
+      dpt_status sp = from_state(hs[p].status);
+      if (hs[p].status == ST_RUNNING) sp = hrun[1] ? DPT_ERR_TIMEOUT : DPT_ERR_MAXITER;
+      if (sp != DPT_OK && ret == DPT_OK) ret = sp;
+      if (infos) {
+        infos[p].iters = hs[p].k;
+        infos[p].slice_gemms = hs[p].slice_gemms;
+        infos[p].residual = hs[p].rho;
+        infos[p].status = sp;
+        infos[p].nstar = -1;
+        infos[p].launches = prof.launches;
+        infos[p].product_launches = prof.live;
+        infos[p].product_ms = prof.ms;
+      }
+    }
+    CK(cudaEventRecord(b->ev, s));
+    CK(cudaStreamWaitEvent(user, b->ev, 0));
+  } catch (Fail f) {
+    cudaStreamSynchronize(b->stream);
+    ret = f.st;
+  }
+  release(b);
+  return ret;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -791,6 +989,37 @@ dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int32_t* row
     return done(f.st);
   } catch (...) {
     return done(DPT_ERR_CUDA);
+  }
+}
+
+dpt_status dpt_solve_batched(int64_t count, const int64_t* n, const double* const* theta,
+                             const double* const* delta, const int64_t* ld_delta,
+                             const double* lambda, const dpt_options* opt,
+                             double* const* A_out, const int64_t* ld_a,
+                             double* const* E_out, dpt_info* infos, void* stream) {
+  dpt_options o;
+  dpt_options_default(&o);
+  if (opt) o = *opt;
+  if (count < 1 || count > (1 << 24) || !n || !theta || !delta || !ld_delta || !lambda ||
+      !A_out || !ld_a || !E_out || !(o.tol > 0) || o.max_iter < 0 || o.max_slices < 1 ||
+      o.max_slices > 3)
+    return DPT_ERR_ARG;
+  if (o.prec != DPT_PREC_MIXED_BF16 || o.epstein_nesbet) return DPT_ERR_UNSUPPORTED;
+  for (int64_t p = 0; p < count; ++p) {
+    if (n[p] < 1 || n[p] > 65536 || ld_delta[p] < n[p] || ld_a[p] < n[p] || !theta[p] ||
+        !delta[p] || !A_out[p] || !E_out[p] || !std::isfinite(lambda[p]))
+      return DPT_ERR_ARG;
+  }
+  try {
+    if (!is_device_ptr(theta[0]) || !is_device_ptr(delta[0]) || !is_device_ptr(A_out[0]) ||
+        !is_device_ptr(E_out[0]))
+      return DPT_ERR_UNSUPPORTED;
+    return solve_batched((int)count, n, theta, delta, ld_delta, lambda, o, A_out, ld_a, E_out,
+                         infos, (cudaStream_t)stream);
+  } catch (Fail f) {
+    return f.st;
+  } catch (...) {
+    return DPT_ERR_CUDA;
   }
 }
 

@@ -61,44 +61,6 @@ struct __align__(16) GemmSmemMisc {
 };
 constexpr int SMEM_BYTES = SMEM_TILES + SMEM_X + 1024 + (int)sizeof(GemmSmemMisc);
 
-struct Col4 {
-  float4 ah, al, L;
-  uint2 dtp;      // four BF16
-  uint2 D[3];     // Delta_ij as three BF16 slices, four rows each
-};
-
-__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
-__device__ __forceinline__ float f4(const float4& v, int e) {
-  return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
-}
-__device__ __forceinline__ void f4set(float4& v, int e, float x) {
-  if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
-}
-__device__ __forceinline__ float bf_at(uint2 u, int e) {
-  const uint32_t w = (e < 2) ? u.x : u.y;
-  const uint32_t h = (e & 1) ? (w >> 16) : (w & 0xFFFFu);
-  return __uint_as_float(h << 16);
-}
-__device__ __forceinline__ uint32_t bf_bits(float x) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
-}
-// Warp reduction of the column sums: |R|^2 and |a|^2 in float, the diagonal
-// increment (eh, el) in float-float.
-__device__ __forceinline__ void warp_sum_ff(float& r2, float& a2, float& eh, float& el) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-    const float oh = __shfl_xor_sync(0xffffffffu, eh, o);
-    const float ol = __shfl_xor_sync(0xffffffffu, el, o);
-    float sh, se;
-    two_sum(eh, oh, sh, se);
-    se += el + ol;
-    fast_two_sum(sh, se, eh, el);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Preparation: transpose Delta (column-major FP64) into row-major FP32 and into
 // the BF16 slices D1 + D2 + D3 (row-major, concatenated along K), zeroing the

@@ -1,0 +1,645 @@
+// Grouped full-spectrum DPT: many independent problems of uneven size advanced
+// together, one launch per stage of an iteration for the whole group.
+//
+// Each problem p has an entry in a device-resident table (GProb): its size, its
+// work arrays inside one arena, its own iteration state and its own TMA
+// descriptors.  Kernels walk flat work lists of (problem, tile) items built once on
+// the host, so one launch covers every problem; items of problems that have
+// already converged return at once, so every problem retires at its own
+// convergence (arXiv:2002.12872: each problem is its own fixed-point iteration,
+// Sec. II.B; the arithmetic per problem is that of the single-problem mixed path,
+// see dpt_full_mixed.cu).
+//
+// Tile shape per problem (chosen on the host from n, the "autotuned" width):
+// M = 128 rows, N = the smallest multiple of 32 that covers n in ceil(n / 256)
+// column tiles, so small problems do not pay for 256-wide tiles.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "dpt_device.cuh"
+#include "dpt_internal.h"
+
+namespace dpt {
+
+constexpr int G_BM = 128;
+constexpr int G_BNMAX = 256;
+constexpr int G_BK = 64;
+constexpr int G_UK = 16;
+constexpr int G_STAGES = 4;
+constexpr int G_A_TILE = G_BM * G_BK * 2;
+constexpr int G_B_TILE = G_BNMAX * G_BK * 2;
+constexpr int G_EPI_WARPS = 8;
+constexpr int G_NTHREADS = 64 + 32 * G_EPI_WARPS;
+constexpr int G_XCH = 32;
+constexpr int G_SMEM_TILES = G_STAGES * (G_A_TILE + G_B_TILE);
+constexpr int G_SMEM_X = G_BM * G_XCH * 4;
+constexpr int G_NSLICE = 3;
+
+struct __align__(16) GSmem {
+  uint64_t full[G_STAGES];
+  uint64_t empty[G_STAGES];
+  uint64_t acc_full[2];
+  uint64_t acc_empty[2];
+  uint32_t tmem_base;
+  float e[G_BNMAX];
+  float dprev[G_BNMAX];
+  float thh[G_BNMAX];
+  float thl[G_BNMAX];
+};
+constexpr int G_SMEM_BYTES = G_SMEM_TILES + G_SMEM_X + 1024 + (int)sizeof(GSmem);
+
+__device__ __forceinline__ bool g_running(const GProb* P) {
+  return *((volatile const int*)&P->st->status) == ST_RUNNING;
+}
+
+// ---------------------------------------------------------------------------
+// theta checks: finite and pairwise distinct (one block per problem).
+// ---------------------------------------------------------------------------
+// A problem found invalid stops here (its status leaves ST_RUNNING exactly once,
+// so the group's running count drops exactly once).
+__device__ __forceinline__ void g_fail(const GProb* P, int code, int* running) {
+  if (atomicCAS(&P->st->status, ST_RUNNING, code) == ST_RUNNING) atomicSub(running, 1);
+}
+
+__global__ void k_g_check_theta(const GProb* __restrict__ probs, int count, int* running) {
+  const int p = blockIdx.x;
+  if (p >= count) return;
+  const GProb* P = probs + p;
+  const int n = P->n;
+  const double* th = P->theta;
+  double amax = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double ti = th[i];
+    if (!finite_bits(ti)) g_fail(P, ST_BADINPUT, running);
+    else amax = fmax(amax, fabs(ti));
+    for (int j = i + 1; j < n; ++j)
+      if (th[j] == ti) { g_fail(P, ST_DEGENERATE, running); break; }
+  }
+  // max |theta| for the residual scale
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  __shared__ double sm[4];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = amax;
+  __syncthreads();
+  if (threadIdx.x == 0) P->st->theta_max = fmax(fmax(sm[0], sm[1]), fmax(sm[2], sm[3]));
+}
+
+// ---------------------------------------------------------------------------
+// Delta -> three BF16 slices (row-major) and theta -> float-float.
+// Work item: (problem, 32-column block, 32-row block).
+// ---------------------------------------------------------------------------
+__global__ void k_g_prep(const GProb* __restrict__ probs, const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const GProb* P = probs + it.x;
+  if (!g_running(P)) return;
+  __shared__ double tile[32][33];
+  const int n = P->n, ld = P->ld;
+  const int bx = it.y * 32, by = it.z * 32;
+  const double* delta = P->delta_in;
+  const int64_t ld_in = P->ld_in;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = by + threadIdx.x, k = bx + r;
+    double v = 0.0;
+    if (j < n && k < n) {
+      v = delta[(int64_t)k * ld_in + j];
+      if (!finite_bits(v)) atomicExch(&P->st->bad_input, 1u);
+    }
+    tile[r][threadIdx.x] = v;
+  }
+  if (bx == 0 && threadIdx.y == 0) {   // theta split, rows by..by+31
+    const int j = by + threadIdx.x;
+    if (j < ld) {
+      float h = 0.f, l = 0.f;
+      if (j < n) split_double(P->theta[j], h, l);
+      P->th_hi[j] = h;
+      P->th_lo[j] = l;
+    }
+  }
+  __syncthreads();
+  const int64_t cat_ld = P->cat_ld;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int j = by + r, k = bx + threadIdx.x;
+    if (j < n && k < ld) {
+      float rh = 0.f, rl = 0.f;
+      if (k < n) split_double(tile[threadIdx.x][r], rh, rl);
+      for (int s = 0; s < G_NSLICE; ++s) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(rh);
+        P->Dcat[(int64_t)j * cat_ld + (int64_t)s * ld + k] = b;
+        two_sum(rh - __bfloat162float(b), rl, rh, rl);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Iteration 0 (A_0 = I) in float-float; work item (problem, 128-col tile, 128-row tile).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_g_iter0(const GProb* __restrict__ probs,
+                                                 const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const GProb* P = probs + it.x;
+  if (!g_running(P)) return;
+  __shared__ float rows[4][128];
+  const int n = P->n, ld = P->ld, ntm = P->ntm;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n0 = it.y * 128, m0 = it.z * 128, tm = it.z;
+  const int r0 = 4 * lane, j0 = m0 + r0;
+  const int64_t cat_ld = P->cat_ld;
+  const float lam_hi = P->lam, lam_lo = P->lam_lo;
+  const float4 thj_h = *reinterpret_cast<const float4*>(P->th_hi + j0);
+  const float4 thj_l = *reinterpret_cast<const float4*>(P->th_lo + j0);
+  const double* delta = P->delta_in;
+  const int64_t ld_in = P->ld_in;
+  float rowabs[4] = {0.f, 0.f, 0.f, 0.f};
+  float mx = 0.f;
+  for (int c = 0; c < 32; ++c) {
+    const int i = n0 + 32 * w + c;
+    if (i >= n) break;
+    const float thi_h = P->th_hi[i], thi_l = P->th_lo[i];
+    const __nv_bfloat16* Drow = P->Dcat + (int64_t)i * cat_ld + j0;
+    uint2 D[3];
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+    float4 oh, oL;
+    uint32_t ob[4];
+    float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = j0 + e;
+      float nh = 0.f, Ln = 0.f, dtn = 0.f;
+      if (j < n) {
+        const double v = delta[(int64_t)i * ld_in + j];
+        float vh, vl;
+        split_double(v, vh, vl);
+        rowabs[e] += fabsf(vh);
+        if (j == i) {
+          nh = 1.f;
+          a2 += 1.f;
+          P->d[i] = v;
+        } else {
+          float pr, pe;
+          two_prod(lam_hi, vh, pr, pe);
+          pe = fmaf(lam_hi, vl, fmaf(lam_lo, vh, pe));
+          float R0h, R0l;
+          fast_two_sum(pr, pe, R0h, R0l);
+          float gh, gl;
+          ff_sub(thi_h, thi_l, f4(thj_h, e), f4(thj_l, e), gh, gl);
+          dtn = bf16_round(R0h * __frcp_rn(gh));
+          float q, qe;
+          two_prod(gh, dtn, q, qe);
+          qe = fmaf(gl, dtn, qe);
+          Ln = (R0h - q) + (R0l - qe);
+          nh = dtn;
+          r2 = fmaf(R0h, R0h, r2);
+          const float p1 = bf_at(D[0], e) * dtn;
+          const float p23 = fmaf(bf_at(D[1], e), dtn, bf_at(D[2], e) * dtn);
+          float sh, se;
+          two_sum(eh, p1, sh, se);
+          se += el + p23;
+          fast_two_sum(sh, se, eh, el);
+          mx = fmaxf(mx, fabsf(dtn));
+        }
+      }
+      f4set(oh, e, nh);
+      f4set(oL, e, Ln);
+      ob[e] = bf_bits(dtn);
+    }
+    const int64_t idx = (int64_t)i * ld + j0;
+    st4(P->A_hi[1] + idx, oh);
+    st4(P->A_lo[1] + idx, make_float4(0.f, 0.f, 0.f, 0.f));
+    st4(P->L + idx, oL);
+    *reinterpret_cast<uint2*>(P->dt[0] + idx) =
+        make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+    warp_sum_ff(r2, a2, eh, el);
+    if (lane == 0) {
+      P->part[((int64_t)0 * ntm + tm) * ld + i] = r2;
+      P->part[((int64_t)1 * ntm + tm) * ld + i] = a2;
+      P->part[((int64_t)2 * ntm + tm) * ld + i] = eh;
+      P->part[((int64_t)3 * ntm + tm) * ld + i] = el;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) rows[w][r0 + e] = rowabs[e];
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (m0 + r < n)
+    P->rowpart[(int64_t)it.y * ld + m0 + r] = ((rows[0][r] + rows[1][r]) + rows[2][r]) + rows[3][r];
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0 && mx > 0.f) atomicMax(&P->st->dmax_bits, __float_as_uint(mx));
+}
+
+// ---------------------------------------------------------------------------
+// Control: one block per problem.  Reduces the problem's tile partials, reads out
+// E of the assessed iterate, advances d and takes the problem's decision.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_g_ctrl(const GProb* __restrict__ probs, int count,
+                                                int* running) {
+  const int p = blockIdx.x;
+  if (p >= count) return;
+  const GProb* P = probs + p;
+  IterState* st = P->st;
+  if (st->status != ST_RUNNING) return;
+  const int n = P->n, ld = P->ld, ntm = P->ntm;
+  const int ntn128 = (n + 127) / 128;
+  const bool first = (st->k == 0);
+  float rmax = 0.f, rowmax = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float r2 = 0.f, a2 = 0.f;
+    double ep = 0.0;
+    for (int t = 0; t < ntm; ++t) {
+      r2 += P->part[((int64_t)0 * ntm + t) * ld + i];
+      a2 += P->part[((int64_t)1 * ntm + t) * ld + i];
+      ep += (double)P->part[((int64_t)2 * ntm + t) * ld + i] +
+            (double)P->part[((int64_t)3 * ntm + t) * ld + i];
+    }
+    float rr = sqrtf(r2 / a2);
+    if (!(rr == rr) || isinf(rr)) rr = __int_as_float(0x7f800000);
+    rmax = fmaxf(rmax, rr);
+    const double dk = P->d[i];
+    P->E[i] = P->theta[i] + P->lam64 * dk;
+    P->dprev_col[i] = (float)dk;
+    P->e_col[i] = (float)ep;
+    P->d[i] = dk + ep;
+    if (first) {
+      float rs = 0.f;
+      for (int t = 0; t < ntn128; ++t) rs += P->rowpart[(int64_t)t * ld + i];
+      rowmax = fmaxf(rowmax, rs);
+    }
+  }
+  __shared__ float sm[2][8];
+  for (int o = 16; o > 0; o >>= 1) {
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    rowmax = fmaxf(rowmax, __shfl_xor_sync(0xffffffffu, rowmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) { sm[0][threadIdx.x >> 5] = rmax; sm[1][threadIdx.x >> 5] = rowmax; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+    rmax = fmaxf(rmax, sm[0][q]);
+    rowmax = fmaxf(rowmax, sm[1][q]);
+  }
+  rmax = fmaxf(rmax, sm[0][0]);
+  rowmax = fmaxf(rowmax, sm[1][0]);
+  volatile IterState* vs = st;
+  if (first) vs->s = vs->theta_max + fabs(vs->lam) * (double)rowmax;
+  const float dmax = __uint_as_float(vs->dmax_bits);
+  vs->dmax_bits = 0;
+  if (!decide(vs, (double)rmax / vs->s)) {
+    atomicSub(running, 1);
+    return;
+  }
+  const int S = ((double)dmax < vs->slice_tol) ? 1 : vs->max_slices;
+  vs->slices = S;
+  vs->slice_gemms = vs->slice_gemms + S;
+}
+
+// ---------------------------------------------------------------------------
+// The grouped product kernel (persistent, warp-specialised; one CTA per SM).
+// Same structure and arithmetic as k_gemm_epi, with per-tile problem data.
+// ---------------------------------------------------------------------------
+struct GTileInfo {
+  const GProb* P;
+  int tm, tn, m0, n0, bn, S, cur, kbs;
+  bool live;
+};
+
+__device__ __forceinline__ GTileInfo g_tile(const GProb* probs, const int2* tiles, int t) {
+  GTileInfo ti;
+  const int2 e = tiles[t];
+  ti.P = probs + e.x;
+  const IterState* st = ti.P->st;
+  ti.live = *((volatile const int*)&st->status) == ST_RUNNING;
+  ti.tm = e.y / ti.P->ntn;
+  ti.tn = e.y % ti.P->ntn;
+  ti.bn = ti.P->bn;
+  ti.m0 = ti.tm * G_BM;
+  ti.n0 = ti.tn * ti.bn;
+  ti.S = st->slices;
+  ti.cur = st->cur;
+  ti.kbs = ti.P->ld / G_BK;
+  return ti;
+}
+
+// Column walk of one 32-column chunk (phase 2), warp ew takes 4 columns.
+__device__ __forceinline__ void g_epilogue_columns(const GTileInfo& ti, GSmem* ms, const float* Xs,
+                                                   int ew, int lane, int c0, float& mx) {
+  const GProb* P = ti.P;
+  const int n = P->n, ld = P->ld;
+  const bool c1 = (ti.cur != 0);
+  const float* __restrict__ Ahc = c1 ? P->A_hi[1] : P->A_hi[0];
+  const float* __restrict__ Alc = c1 ? P->A_lo[1] : P->A_lo[0];
+  float* __restrict__ Ahn = c1 ? P->A_hi[0] : P->A_hi[1];
+  float* __restrict__ Aln = c1 ? P->A_lo[0] : P->A_lo[1];
+  const __nv_bfloat16* __restrict__ dtp = c1 ? P->dt[0] : P->dt[1];
+  __nv_bfloat16* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
+  float* __restrict__ L = P->L;
+  const float lam = P->lam;
+  const int r0 = 4 * lane;
+  const int j0 = ti.m0 + r0;
+  const float4 thj_h = ld4(P->th_hi + j0);
+  const float4 thj_l = ld4(P->th_lo + j0);
+  const int cb = c0 + 4 * ew;
+  if (cb >= ti.bn) return;
+  Col4 in[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = ti.n0 + cb + u;
+    if (i < n) {
+      const int64_t idx = (int64_t)i * ld + j0;
+      in[u].ah = ld4(Ahc + idx);
+      in[u].al = ld4(Alc + idx);
+      in[u].L = ld4(L + idx);
+      in[u].dtp = *reinterpret_cast<const uint2*>(dtp + idx);
+      const __nv_bfloat16* Drow = P->Dcat + (int64_t)i * P->cat_ld + j0;
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl)
+        in[u].D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int cl = cb + u;
+    const int i = ti.n0 + cl;
+    if (i >= n) continue;
+    const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * G_BM + r0);
+    const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
+    const float thh = ms->thh[cl], thl = ms->thl[cl];
+    float4 oh, ol, oL;
+    uint32_t ob[4];
+    float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = j0 + e;
+      const float ah = f4(in[u].ah, e), al = f4(in[u].al, e);
+      float nh = 0.f, nl = 0.f, Ln = 0.f, dnew = 0.f;
+      if (j == i) {
+        nh = 1.f;
+        a2 += 1.f;
+      } else if (j < n) {
+        const float R = f4(in[u].L, e) +
+                        lam * (f4(x4, e) - ah * e_i - bf_at(in[u].dtp, e) * dp_i);
+        float gh, gl;
+        ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
+        dnew = bf16_round(R * __frcp_rn(gh));
+        Ln = fmaf(-gh, dnew, R) - gl * dnew;
+        ff_add_f(ah, al, dnew, nh, nl);
+        r2 = fmaf(R, R, r2);
+        a2 = fmaf(ah, ah, a2);
+        const float p1 = bf_at(in[u].D[0], e) * dnew;
+        const float p23 = fmaf(bf_at(in[u].D[1], e), dnew, bf_at(in[u].D[2], e) * dnew);
+        float sh, se;
+        two_sum(eh, p1, sh, se);
+        se += el + p23;
+        fast_two_sum(sh, se, eh, el);
+        mx = fmaxf(mx, fabsf(dnew));
+      }
+      f4set(oh, e, nh);
+      f4set(ol, e, nl);
+      f4set(oL, e, Ln);
+      ob[e] = bf_bits(dnew);
+    }
+    const int64_t idx = (int64_t)i * ld + j0;
+    st4(Ahn + idx, oh);
+    st4(Aln + idx, ol);
+    st4(L + idx, oL);
+    *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+    warp_sum_ff(r2, a2, eh, el);
+    if (lane == 0) {
+      const int ntm = P->ntm;
+      P->part[((int64_t)0 * ntm + ti.tm) * ld + i] = r2;
+      P->part[((int64_t)1 * ntm + ti.tm) * ld + i] = a2;
+      P->part[((int64_t)2 * ntm + ti.tm) * ld + i] = eh;
+      P->part[((int64_t)3 * ntm + ti.tm) * ld + i] = el;
+    }
+  }
+}
+
+__device__ __forceinline__ void g_epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ bool g_epi_bar_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.and.pred po, 1, 256, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+__global__ void __launch_bounds__(G_NTHREADS, 1)
+k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, int ntiles,
+             unsigned* timeout) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + G_STAGES * G_A_TILE;
+  float* Xs = reinterpret_cast<float*>(smem + G_SMEM_TILES);
+  GSmem* ms = (GSmem*)(smem + G_SMEM_TILES + G_SMEM_X);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < G_STAGES; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&ms->acc_full[b], 1); mbar_init(&ms->acc_empty[b], 1); }
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&ms->tmem_base, 2 * G_BNMAX);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ms->tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    uint32_t it = 0;
+    bool alive = true;
+    for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+      const GTileInfo ti = g_tile(probs, tiles, t);
+      if (!ti.live) continue;
+      const CUtensorMap* tA = &ti.P->tmA;
+      const CUtensorMap* tB = (ti.cur == 1) ? &ti.P->tmB[0] : &ti.P->tmB[1];
+      const uint32_t bytes = G_A_TILE + (uint32_t)ti.bn * G_BK * 2;
+      const int nk = ti.S * ti.kbs;
+      const int kb_last = min(ti.kbs - 1, (ti.n0 + ti.bn - 1) / G_BK);
+      for (int q = 0; q < nk; ++q, ++it) {
+        const int s = it % G_STAGES;
+        const uint32_t ph = (it / G_STAGES) & 1;
+        if (!mbar_wait(&ms->empty[s], ph ^ 1, timeout)) { alive = false; break; }
+        mbar_arrive_expect_tx(&ms->full[s], bytes);
+        // small slices first, the tile's diagonal K-blocks last (see k_gemm_epi)
+        const int sl = ti.S - 1 - q / ti.kbs;
+        const int kb = (kb_last + 1 + q % ti.kbs) % ti.kbs;
+        tma_load_2d(sA + s * G_A_TILE, tA, &ms->full[s], sl * ti.P->ld + kb * G_BK, ti.m0);
+        tma_load_2d(sB + s * G_B_TILE, tB, &ms->full[s], kb * G_BK, ti.n0);
+      }
+    }
+    for (uint32_t t = (it > G_STAGES ? it - G_STAGES : 0); t < it; ++t)
+      mbar_wait(&ms->full[t % G_STAGES], (t / G_STAGES) & 1, timeout);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    uint32_t it = 0;
+    int lt = 0;
+    bool alive = true;
+    for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+      const GTileInfo ti = g_tile(probs, tiles, t);
+      if (!ti.live) continue;
+      const int b = lt & 1;
+      const uint32_t use = (uint32_t)(lt >> 1);
+      ++lt;
+      if (!mbar_wait(&ms->acc_empty[b], (use & 1) ^ 1, timeout)) break;
+      tc_fence_after();
+      const uint32_t dacc = tmem + (uint32_t)(b * G_BNMAX);
+      const uint32_t idesc = idesc_bf16_f32(G_BM, ti.bn);
+      const int nk = ti.S * ti.kbs;
+      for (int q = 0; q < nk; ++q, ++it) {
+        const int s = it % G_STAGES;
+        const uint32_t ph = (it / G_STAGES) & 1;
+        if (!mbar_wait(&ms->full[s], ph, timeout)) { alive = false; break; }
+        tc_fence_after();
+        const uint64_t da = smem_desc_sw128(sA + s * G_A_TILE);
+        const uint64_t db = smem_desc_sw128(sB + s * G_B_TILE);
+#pragma unroll
+        for (int kk = 0; kk < G_BK / G_UK; ++kk)
+          umma_bf16(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                    (q > 0 || kk > 0) ? 1u : 0u);
+        umma_commit(&ms->empty[s]);
+      }
+      umma_commit(&ms->acc_full[b]);
+    }
+  } else if (warp >= 2) {
+    // ---- epilogue ----
+    const int ew = warp - 2;
+    const int qd = warp & 3;
+    const int half = ew >> 2;
+    const int et = threadIdx.x - 64;
+    float mx = 0.f;
+    const GProb* mxP = nullptr;
+    int lt = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const GTileInfo ti = g_tile(probs, tiles, t);
+      if (!ti.live) continue;
+      const int b = lt & 1;
+      const uint32_t use = (uint32_t)(lt >> 1);
+      ++lt;
+      // the running maximum of |dt| belongs to one problem: flush it on a change
+      if (mxP != ti.P) {
+        if (mxP) {
+          float m = mx;
+          for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+          if (lane == 0 && m > 0.f) atomicMax(&mxP->st->dmax_bits, __float_as_uint(m));
+        }
+        mxP = ti.P;
+        mx = 0.f;
+      }
+      g_epi_bar();
+      {
+        const int i = ti.n0 + et;
+        const bool v = (et < ti.bn) && (i < ti.P->n);
+        ms->e[et] = v ? ti.P->e_col[i] : 0.f;
+        ms->dprev[et] = v ? ti.P->dprev_col[i] : 0.f;
+        ms->thh[et] = v ? ti.P->th_hi[i] : 0.f;
+        ms->thl[et] = v ? ti.P->th_lo[i] : 0.f;
+      }
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&ms->acc_full[b], use & 1, timeout));
+      tc_fence_after();
+      const uint32_t src = tmem + (uint32_t)(b * G_BNMAX) + ((uint32_t)(qd * 32) << 16);
+      bool all_ok = true;
+      for (int c0 = 0; c0 < ti.bn; c0 += G_XCH) {
+        if (c0 > 0) g_epi_bar();
+        if (ok) {
+          float x[16];
+          const int cc = half * 16;
+          tmem_ld_x16(src + (uint32_t)(c0 + cc), x);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) Xs[(cc + c) * G_BM + qd * 32 + lane] = x[c];
+        }
+        if (c0 + G_XCH >= ti.bn) tc_fence_before();
+        all_ok = g_epi_bar_and(ok);
+        if (c0 + G_XCH >= ti.bn && et == 0) mbar_arrive(&ms->acc_empty[b]);
+        if (!all_ok) break;
+        g_epilogue_columns(ti, ms, Xs, ew, lane, c0, mx);
+      }
+      if (!all_ok) break;
+    }
+    if (mxP) {
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0 && mx > 0.f) atomicMax(&mxP->st->dmax_bits, __float_as_uint(mx));
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 2 * G_BNMAX);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Output: A (float-float -> FP64) and E; work item (problem, 128-col tile, 128-row tile).
+// ---------------------------------------------------------------------------
+__global__ void k_g_finalize(const GProb* __restrict__ probs, const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const GProb* P = probs + it.x;
+  const IterState* st = P->st;
+  const int n = P->n, ld = P->ld;
+  const int k = st->k;
+  const bool c1 = st->cur != 0;
+  const float* hi = c1 ? P->A_hi[1] : P->A_hi[0];
+  const float* lo = c1 ? P->A_lo[1] : P->A_lo[0];
+  const int j = it.z * 128 + threadIdx.x;
+  if (j >= n) return;
+  for (int c = 0; c < 128; ++c) {
+    const int i = it.y * 128 + c;
+    if (i >= n) break;
+    double v;
+    if (k == 0) v = (i == j) ? 1.0 : 0.0;
+    else v = f2d_bits(hi[(int64_t)i * ld + j]) + f2d_bits(lo[(int64_t)i * ld + j]);
+    P->A_out[(int64_t)i * P->ld_a + j] = v;
+  }
+  if (it.y == 0) P->E_out[j] = P->E[j];
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+cudaError_t g_set_attributes() {
+  return cudaFuncSetAttribute(k_g_gemm_epi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              G_SMEM_BYTES);
+}
+cudaError_t launch_g_check_theta(const GProb* probs, int count, int* running, cudaStream_t s) {
+  k_g_check_theta<<<count, 128, 0, s>>>(probs, count, running);
+  return cudaGetLastError();
+}
+cudaError_t launch_g_prep(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {
+  if (nitems) k_g_prep<<<nitems, dim3(32, 8), 0, s>>>(probs, items);
+  return cudaGetLastError();
+}
+cudaError_t launch_g_iter0(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {
+  if (nitems) k_g_iter0<<<nitems, 128, 0, s>>>(probs, items);
+  return cudaGetLastError();
+}
+cudaError_t launch_g_ctrl(const GProb* probs, int count, int* running, cudaStream_t s) {
+  k_g_ctrl<<<count, 256, 0, s>>>(probs, count, running);
+  return cudaGetLastError();
+}
+cudaError_t launch_g_gemm_epi(const GProb* probs, const int2* tiles, int ntiles, unsigned* timeout,
+                              cudaStream_t s) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = ntiles < nsm ? ntiles : nsm;
+  if (grid > 0) k_g_gemm_epi<<<grid, G_NTHREADS, G_SMEM_BYTES, s>>>(probs, tiles, ntiles, timeout);
+  return cudaGetLastError();
+}
+cudaError_t launch_g_finalize(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {
+  if (nitems) k_g_finalize<<<nitems, 128, 0, s>>>(probs, items);
+  return cudaGetLastError();
+}
+
+}  // namespace dpt

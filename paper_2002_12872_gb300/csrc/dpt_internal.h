@@ -12,6 +12,7 @@ enum : int {
   ST_RUNNING = 0,
   ST_CONVERGED = 1,
   ST_BADINPUT = -1,
+  ST_DEGENERATE = -2,
   ST_MAXITER = -3,
   ST_DIVERGED = -4,
   ST_TIMEOUT = -7,
@@ -73,6 +74,46 @@ struct DomState {
   double best;
   double E;              // eigenvalue of the assessed iterate
 };
+
+// One problem of a grouped (batched / served) solve: a device-resident table entry
+// with the problem's size, tile shape, work arrays, state and TMA descriptors.
+struct alignas(128) GProb {
+  CUtensorMap tmA;          // Delta slices (row-major BF16, 3 slices side by side)
+  CUtensorMap tmB[2];       // increment buffers dt[0], dt[1]
+  int n, ld, ntm, ntn, bn, pad0;
+  float lam, lam_lo;
+  double lam64;
+  float* A_hi[2];
+  float* A_lo[2];
+  __nv_bfloat16* dt[2];
+  float* L;
+  __nv_bfloat16* Dcat;
+  int64_t cat_ld;
+  float* th_hi;
+  float* th_lo;
+  const double* theta;      // input theta (device)
+  double* d;
+  double* E;
+  float* e_col;
+  float* dprev_col;
+  float* part;
+  float* rowpart;
+  IterState* st;
+  const double* delta_in;   // input Delta (device, column-major)
+  int64_t ld_in;
+  double* A_out;            // outputs (device)
+  int64_t ld_a;
+  double* E_out;
+};
+
+cudaError_t g_set_attributes();
+cudaError_t launch_g_check_theta(const GProb* probs, int count, int* running, cudaStream_t s);
+cudaError_t launch_g_prep(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
+cudaError_t launch_g_iter0(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
+cudaError_t launch_g_ctrl(const GProb* probs, int count, int* running, cudaStream_t s);
+cudaError_t launch_g_gemm_epi(const GProb* probs, const int2* tiles, int ntiles,
+                              unsigned* timeout, cudaStream_t s);
+cudaError_t launch_g_finalize(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
 
 // Arguments of the tensor-core iteration kernel (mixed path, real).
 struct GemmEpiParams {
