@@ -47,6 +47,10 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the dominant-CSR and batched workloads")
+    ap.add_argument("--only", default="all", choices=["all", "dominant", "batched"],
+                    help="time one secondary workload alone and print its JSON object")
     return ap.parse_args()
 
 
@@ -216,6 +220,87 @@ def cpu_baseline_sized(cfg, target_s=15.0):
 
 
 # ---------------------------------------------------------------------------
+# Secondary workloads (reported beside the headline)
+# ---------------------------------------------------------------------------
+DOM_BYTES_PER_ITER = None   # set from the workload: 8 B per nonzero + 36 B per row
+
+
+def bench_dominant(dpt, inputs, dev, pk, steps=20, warmup=3):
+    """Dominant eigenvector, n = 2e6 CSR with 16 nonzeros per row, lambda = 0.01.
+    Algorithmic bytes per SpMV pass: FP32 value + int32 index per nonzero, and per
+    row the row pointer (4 B), theta (8 B float-float), z read and written (8 + 8 B)
+    and one gather of z (8 B)."""
+    import torch
+    cfg = inputs.dominant_csr()
+    n = cfg["n"]
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    th, rp, ci, va = t(cfg["theta"]), t(cfg["row_ptr"]), t(cfg["col_idx"]), t(cfg["vals"])
+    z = torch.empty(n, dtype=torch.float64, device=dev)
+    nnz = int(cfg["row_ptr"][-1])
+    bytes_iter = 8.0 * nnz + 36.0 * n
+    out = {"workload": "dominant eigenvector, CSR n=2e6, 16 nnz/row, lambda=0.01, tol=1e-12"}
+    for prec in ("mixed", "fp64"):
+        for _ in range(warmup):
+            dpt.solve_dominant(th, rp, ci, va, cfg["lam"], prec=prec, z_out=z, profile=True)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pm, pl, its = 0.0, 0, []
+        e0.record(stream)
+        for _ in range(steps):
+            _, E, info = dpt.solve_dominant(th, rp, ci, va, cfg["lam"], prec=prec, z_out=z,
+                                            profile=True)
+            pm += info["product_ms"]
+            pl += info["product_launches"]
+            its.append(info["iters"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        per_pass = pm / max(1, pl)
+        gbs = bytes_iter / (per_pass * 1e-3) / 1e9
+        out[prec] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iters": float(np.mean(its)),
+                     "spmv_ms_per_pass": per_pass, "achieved_GBs": gbs,
+                     "hbm_frac": gbs / pk["hbm_gbs"], "E": E}
+    out["roofline"] = {"bound": "hbm", "kernel": "k_dom_iter (+ y* pre-pass)",
+                       "achieved": out["mixed"]["achieved_GBs"], "peak": pk["hbm_gbs"],
+                       "unit": "GB/s", "frac": out["mixed"]["hbm_frac"],
+                       "algorithmic_bytes_per_pass": bytes_iter}
+    return out
+
+
+def bench_batched(dpt, inputs, dev, steps=3, warmup=2):
+    """20,000 independent symmetric problems, n log-uniform in [32, 512], one
+    grouped solve per step (inputs resident in HBM)."""
+    import torch
+    probs = inputs.batched_symmetric(count=20000)
+    th = [torch.tensor(p["theta"], device=dev) for p in probs]
+    D = [dpt.colmajor_tensor(p["delta"], dev) for p in probs]
+    lams = [p["lam"] for p in probs]
+    As = [torch.empty((p["n"], p["n"]), dtype=torch.float64, device=dev).t() for p in probs]
+    Es = [torch.empty(p["n"], dtype=torch.float64, device=dev) for p in probs]
+    for _ in range(warmup):
+        dpt.solve_batched(th, D, lams, A_outs=As, E_outs=Es)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        _, _, infos = dpt.solve_batched(th, D, lams, A_outs=As, E_outs=Es, profile=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    its = [i["iters"] for i in infos]
+    n3 = float(np.sum([2.0 * p["n"] ** 3 for p in probs]))
+    return {"workload": "20,000 dense symmetric problems, n log-uniform [32, 512], "
+                        "lambda U[0.01, 0.1], tol=1e-12",
+            "solves_per_s": 20000 * 1e3 / ms, "ms_per_batch": ms,
+            "iters_mean": float(np.mean(its)), "iters_max": int(np.max(its)),
+            "product_ms_per_launch": infos[0]["product_ms"] / max(1, infos[0]["product_launches"]),
+            "algorithmic_tflop_per_iteration": n3 / 1e12,
+            "all_converged": all(i["status"] == "OK" for i in infos)}
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args, world, rank, local):
@@ -324,6 +409,11 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sized(cfg)
 
+    extra = {}
+    if not args.no_extra:
+        extra["dominant_csr"] = bench_dominant(dpt, inputs, dev, pk)
+        extra["batched"] = bench_batched(dpt, inputs, dev)
+
     if rank != 0:
         return
     line = {
@@ -356,12 +446,24 @@ def run_ours(args, world, rank, local):
         "clocks": clk.summary(),
         "wall_s": wall,
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
 
 
 def main():
     args = parse_args()
     world, rank, local = dist_init(args)
+    if args.only != "all":
+        import torch
+        from paper_2002_12872_gb300 import build, dpt, inputs
+        build.build()
+        dev = torch.device("cuda", local)
+        pk, _ = peaks()
+        fn = bench_dominant if args.only == "dominant" else bench_batched
+        out = fn(dpt, inputs, dev, pk) if args.only == "dominant" else fn(dpt, inputs, dev)
+        if rank == 0:
+            print(json.dumps({args.only: out}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

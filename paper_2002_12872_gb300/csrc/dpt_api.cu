@@ -567,7 +567,7 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
   auto layout = [&](Carve& c) {
     c.take<DomState>(1);
     c.take<float>(n); c.take<float>(n);                 // theta float-float
-    for (int q = 0; q < 4; ++q) c.take<float>(n);       // z float-float ping-pong
+    for (int q = 0; q < 2; ++q) c.take<float2>(n);      // z float-float ping-pong
     if (!ff) { c.take<double>(n); c.take<double>(n); }  // z FP64 ping-pong
     c.take<double>((size_t)2 * G);                      // block partials
     if (!th_dev) c.take<double>(n);
@@ -583,8 +583,8 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
     DomState* st = c.take<DomState>(1);
     float* thh = c.take<float>(n);
     float* thl = c.take<float>(n);
-    float* zh[2]; float* zl[2];
-    for (int q = 0; q < 2; ++q) { zh[q] = c.take<float>(n); zl[q] = c.take<float>(n); }
+    float2* zf[2];
+    for (int q = 0; q < 2; ++q) zf[q] = c.take<float2>(n);
     double* z64[2] = {nullptr, nullptr};
     if (!ff) { z64[0] = c.take<double>(n); z64[1] = c.take<double>(n); }
     double* part = c.take<double>((size_t)2 * G);
@@ -629,7 +629,7 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
     if (hs->bad_input) throw Fail{DPT_ERR_ARG};
     if (hs->ties != 1u) throw Fail{DPT_ERR_DEGENERATE};
     const int nst = hs->nstar;
-    CK(launch_dom_init(n, zh[0], zl[0], z64[0], ff, st, s));
+    CK(launch_dom_init(n, zf[0], z64[0], ff, st, s));
     const double avg = n > 0 ? (double)nnz / n : 0.0;
     const int V = avg < 24 ? 4 : (avg < 48 ? 8 : (avg < 96 ? 16 : 32));
     Prof prof;
@@ -641,12 +641,12 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
     run_loop(b, reinterpret_cast<IterState*>(st), o.graph_iters, o.max_iter, 2, prof,
              [&](int q) {
                prof.before(q, s);
-               CK(launch_dom_iter(n, V, ff, rpd, cid, vad, thh, thl, thd, zh[0], zl[0], zh[1],
-                                  zl[1], z64[0], z64[1], part, st, s));
+               CK(launch_dom_iter(n, V, ff, rpd, cid, vad, thh, thl, thd, zf[0], zf[1], z64[0],
+                                  z64[1], part, st, s));
                prof.after(q, s);
              },
              sizeof(DomState));
-    CK(launch_dom_out(n, zh[0], zl[0], zh[1], zl[1], z64[0], z64[1], ff, zstage, st, s));
+    CK(launch_dom_out(n, zf[0], zf[1], z64[0], z64[1], ff, zstage, st, s));
     prof.launches += 1;
     if (!z_dev) CK(cudaMemcpyAsync(z_out, zstage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(hs, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));

@@ -129,12 +129,10 @@ __global__ void k_dom_ties(int n, const double* __restrict__ theta, DomState* st
 }
 
 // z_0 = e_{n*} and the residual scale s = max|theta| + |lambda| max_m sum_k |Delta_mk|.
-__global__ void k_dom_init(int n, float* __restrict__ zh, float* __restrict__ zl, DomState* st) {
+__global__ void k_dom_init(int n, float2* __restrict__ z, DomState* st) {
   const int nstar = st->nstar;
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
-    zh[m] = (m == nstar) ? 1.f : 0.f;
-    zl[m] = 0.f;
-  }
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x)
+    z[m] = make_float2((m == nstar) ? 1.f : 0.f, 0.f);
   if (blockIdx.x == 0 && threadIdx.x == 0)
     st->s = (double)__uint_as_float(st->absmax_bits) +
             fabs(st->lam) * (double)__uint_as_float(st->row_bits);
@@ -145,21 +143,19 @@ __global__ void k_dom_init(int n, float* __restrict__ zh, float* __restrict__ zl
 // ---------------------------------------------------------------------------
 template <bool FF>
 __global__ void k_dom_ystar(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
-                            const float* __restrict__ vals, const float* __restrict__ zh0,
-                            const float* __restrict__ zl0, const float* __restrict__ zh1,
-                            const float* __restrict__ zl1, const double* __restrict__ z64_0,
+                            const float* __restrict__ vals, const float2* __restrict__ z0,
+                            const float2* __restrict__ z1, const double* __restrict__ z64_0,
                             const double* __restrict__ z64_1, DomState* st) {
   if (st->status != ST_RUNNING) return;
   const int lane = threadIdx.x;
   const int nstar = st->nstar;
   const int a = row_ptr[nstar], b = row_ptr[nstar + 1];
   if (FF) {
-    const float* zh = st->cur ? zh1 : zh0;
-    const float* zl = st->cur ? zl1 : zl0;
+    const float2* z = st->cur ? z1 : z0;
     float ah = 0.f, al = 0.f;
     for (int q = a + lane; q < b; q += 32) {
-      const int c = col_idx[q];
-      ff_fma_acc(vals[q], zh[c], zl[c], ah, al);
+      const float2 zc = z[col_idx[q]];
+      ff_fma_acc(vals[q], zc.x, zc.y, ah, al);
     }
     for (int o = 16; o > 0; o >>= 1) {
       const float oh = __shfl_xor_sync(0xffffffffu, ah, o);
@@ -189,8 +185,8 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
                                                   const float* __restrict__ th_hi,
                                                   const float* __restrict__ th_lo,
                                                   const double* __restrict__ theta,
-                                                  float* __restrict__ zh0, float* __restrict__ zl0,
-                                                  float* __restrict__ zh1, float* __restrict__ zl1,
+                                                  float2* __restrict__ z0,
+                                                  float2* __restrict__ z1,
                                                   double* __restrict__ z64_0,
                                                   double* __restrict__ z64_1,
                                                   double* __restrict__ part, DomState* st) {
@@ -203,12 +199,14 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
   const int nstar = st->nstar;
   const bool c1 = st->cur != 0;
   const float lam_h = st->lam_hi, lam_l = st->lam_lo;
+  // per-thread norms of the float-float variant in float (FP64 instructions are
+  // slow on this GPU even with few active lanes); the block reduction is in double
+  float r2f = 0.f, z2f = 0.f;
   double r2 = 0.0, z2 = 0.0;
   if (FF) {
-    const float* zh = c1 ? zh1 : zh0;
-    const float* zl = c1 ? zl1 : zl0;
-    float* nzh = c1 ? zh0 : zh1;
-    float* nzl = c1 ? zl0 : zl1;
+    // z as interleaved (hi, lo): one 8-byte gather per nonzero
+    const float2* z = c1 ? z1 : z0;
+    float2* nz = c1 ? z0 : z1;
     const float ysh = st->ys_hi, ysl = st->ys_lo;
     const float tsh = th_hi[nstar], tsl = th_lo[nstar];
     // rows are visited in rounds; every lane runs the same number of rounds
@@ -218,9 +216,25 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
       float ah = 0.f, al = 0.f;
       if (m < n) {
         const int a = row_ptr[m], b = row_ptr[m + 1];
-        for (int q = a + gl; q < b; q += V) {
-          const int c = col_idx[q];
-          ff_fma_acc(vals[q], zh[c], zl[c], ah, al);
+        // Memory-level parallelism: each pass issues the lane's next four index and
+        // value loads, then the four gathers, before any arithmetic.
+        int q = a + gl;
+        for (;; q += 4 * V) {
+          int c[4];
+          float v[4];
+          float2 zz[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int qq = q + u * V;
+            const bool ok = qq < b;
+            c[u] = ok ? col_idx[qq] : 0;
+            v[u] = ok ? vals[qq] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) zz[u] = z[c[u]];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) ff_fma_acc(v[u], zz[u].x, zz[u].y, ah, al);
+          if (q + 4 * V >= b) break;
         }
       }
 #pragma unroll
@@ -230,10 +244,11 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
         ff_add(ah, al, oh, ol, ah, al);
       }
       if (gl == 0 && m < n) {
-        const float zmh = zh[m], zml = zl[m];
+        const float2 zm2 = z[m];
+        const float zmh = zm2.x, zml = zm2.y;
         if (m == nstar) {
-          nzh[m] = 1.f; nzl[m] = 0.f;
-          z2 += 1.0;
+          nz[m] = make_float2(1.f, 0.f);
+          z2f += 1.f;
         } else {
           // R = lambda (y - y* z) - gap z, all in float-float
           float t1h, t1l, t2h, t2l, gh, gl2, uh, ul, vh, vl, Rh, Rl;
@@ -246,10 +261,9 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
           const float dlt = Rh * __frcp_rn(gh);
           float nh, nl;
           ff_add(zmh, zml, dlt, 0.f, nh, nl);
-          nzh[m] = nh;
-          nzl[m] = nl;
-          r2 += (double)Rh * (double)Rh;
-          z2 += (double)zmh * (double)zmh;
+          nz[m] = make_float2(nh, nl);
+          r2f = fmaf(Rh, Rh, r2f);
+          z2f = fmaf(zmh, zmh, z2f);
         }
       }
     }
@@ -265,7 +279,24 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
       double acc = 0.0;
       if (m < n) {
         const int a = row_ptr[m], b = row_ptr[m + 1];
-        for (int q = a + gl; q < b; q += V) acc = fma((double)vals[q], z[col_idx[q]], acc);
+        int q = a + gl;
+        for (;; q += 4 * V) {
+          int c[4];
+          float v[4];
+          double zz[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int qq = q + u * V;
+            const bool ok = qq < b;
+            c[u] = ok ? col_idx[qq] : 0;
+            v[u] = ok ? vals[qq] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) zz[u] = z[c[u]];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc = fma((double)v[u], zz[u], acc);
+          if (q + 4 * V >= b) break;
+        }
       }
 #pragma unroll
       for (int o = V / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -285,6 +316,7 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
       }
     }
   }
+  if (FF) { r2 = (double)r2f; z2 = (double)z2f; }
   // block reduction, then the last block decides
   for (int o = 16; o > 0; o >>= 1) {
     r2 += __shfl_xor_sync(0xffffffffu, r2, o);
@@ -342,15 +374,18 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
 }
 
 // Output: z (float-float or FP64) of the assessed iterate -> FP64.
-__global__ void k_dom_out(int n, const float* __restrict__ zh0, const float* __restrict__ zl0,
-                          const float* __restrict__ zh1, const float* __restrict__ zl1,
+__global__ void k_dom_out(int n, const float2* __restrict__ z0, const float2* __restrict__ z1,
                           const double* __restrict__ z64_0, const double* __restrict__ z64_1,
                           int ff, double* __restrict__ out, const DomState* st) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n) return;
   const bool c1 = st->cur != 0;
-  if (ff) out[m] = c1 ? f2d_bits(zh1[m]) + f2d_bits(zl1[m]) : f2d_bits(zh0[m]) + f2d_bits(zl0[m]);
-  else out[m] = c1 ? z64_1[m] : z64_0[m];
+  if (ff) {
+    const float2 v = c1 ? z1[m] : z0[m];
+    out[m] = f2d_bits(v.x) + f2d_bits(v.y);
+  } else {
+    out[m] = c1 ? z64_1[m] : z64_0[m];
+  }
 }
 
 __global__ void k_dom_init64(int n, double* z, const DomState* st) {
@@ -392,27 +427,27 @@ cudaError_t launch_dom_setup(int n, const double* theta, const int32_t* row_ptr,
   return cudaGetLastError();
 }
 
-cudaError_t launch_dom_init(int n, float* zh, float* zl, double* z64, int ff, DomState* st,
+cudaError_t launch_dom_init(int n, float2* z, double* z64, int ff, DomState* st,
                             cudaStream_t s) {
   const int g = dom_grid(n);
-  k_dom_init<<<g, 256, 0, s>>>(n, zh, zl, st);
+  k_dom_init<<<g, 256, 0, s>>>(n, z, st);
   if (!ff) k_dom_init64<<<(n + 255) / 256, 256, 0, s>>>(n, z64, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dom_iter(int n, int vlanes, int ff, const int32_t* row_ptr,
                             const int32_t* col_idx, const float* vals, const float* th_hi,
-                            const float* th_lo, const double* theta, float* zh0, float* zl0,
-                            float* zh1, float* zl1, double* z64_0, double* z64_1, double* part,
-                            DomState* st, cudaStream_t s) {
+                            const float* th_lo, const double* theta, float2* z0, float2* z1,
+                            double* z64_0, double* z64_1, double* part, DomState* st,
+                            cudaStream_t s) {
   if (ff)
-    k_dom_ystar<true><<<1, 32, 0, s>>>(row_ptr, col_idx, vals, zh0, zl0, zh1, zl1, z64_0, z64_1, st);
+    k_dom_ystar<true><<<1, 32, 0, s>>>(row_ptr, col_idx, vals, z0, z1, z64_0, z64_1, st);
   else
-    k_dom_ystar<false><<<1, 32, 0, s>>>(row_ptr, col_idx, vals, zh0, zl0, zh1, zl1, z64_0, z64_1, st);
+    k_dom_ystar<false><<<1, 32, 0, s>>>(row_ptr, col_idx, vals, z0, z1, z64_0, z64_1, st);
   const int g = dom_grid(n);
 #define DOM_LAUNCH(FFV, VV)                                                                    \
-  k_dom_iter<FFV, VV><<<g, 256, 0, s>>>(n, row_ptr, col_idx, vals, th_hi, th_lo, theta, zh0, \
-                                        zl0, zh1, zl1, z64_0, z64_1, part, st)
+  k_dom_iter<FFV, VV><<<g, 256, 0, s>>>(n, row_ptr, col_idx, vals, th_hi, th_lo, theta, z0, z1, \
+                                        z64_0, z64_1, part, st)
   if (ff) {
     switch (vlanes) {
       case 4: DOM_LAUNCH(true, 4); break;
@@ -432,10 +467,10 @@ cudaError_t launch_dom_iter(int n, int vlanes, int ff, const int32_t* row_ptr,
   return cudaGetLastError();
 }
 
-cudaError_t launch_dom_out(int n, const float* zh0, const float* zl0, const float* zh1,
-                           const float* zl1, const double* z64_0, const double* z64_1, int ff,
-                           double* out, const DomState* st, cudaStream_t s) {
-  k_dom_out<<<(n + 255) / 256, 256, 0, s>>>(n, zh0, zl0, zh1, zl1, z64_0, z64_1, ff, out, st);
+cudaError_t launch_dom_out(int n, const float2* z0, const float2* z1, const double* z64_0,
+                           const double* z64_1, int ff, double* out, const DomState* st,
+                           cudaStream_t s) {
+  k_dom_out<<<(n + 255) / 256, 256, 0, s>>>(n, z0, z1, z64_0, z64_1, ff, out, st);
   return cudaGetLastError();
 }
 

@@ -173,15 +173,15 @@ cudaError_t launch_dom_check(int n, int64_t nnz, const int32_t* row_ptr, DomStat
 cudaError_t launch_dom_setup(int n, const double* theta, const int32_t* row_ptr,
                              const int32_t* col_idx, const float* vals, float* th_hi,
                              float* th_lo, DomState* st, cudaStream_t s);
-cudaError_t launch_dom_init(int n, float* zh, float* zl, double* z64, int ff, DomState* st,
+cudaError_t launch_dom_init(int n, float2* z, double* z64, int ff, DomState* st,
                             cudaStream_t s);
 cudaError_t launch_dom_iter(int n, int vlanes, int ff, const int32_t* row_ptr,
                             const int32_t* col_idx, const float* vals, const float* th_hi,
-                            const float* th_lo, const double* theta, float* zh0, float* zl0,
-                            float* zh1, float* zl1, double* z64_0, double* z64_1, double* part,
-                            DomState* st, cudaStream_t s);
-cudaError_t launch_dom_out(int n, const float* zh0, const float* zl0, const float* zh1,
-                           const float* zl1, const double* z64_0, const double* z64_1, int ff,
-                           double* out, const DomState* st, cudaStream_t s);
+                            const float* th_lo, const double* theta, float2* z0, float2* z1,
+                            double* z64_0, double* z64_1, double* part, DomState* st,
+                            cudaStream_t s);
+cudaError_t launch_dom_out(int n, const float2* z0, const float2* z1, const double* z64_0,
+                           const double* z64_1, int ff, double* out, const DomState* st,
+                           cudaStream_t s);
 
 }  // namespace dpt

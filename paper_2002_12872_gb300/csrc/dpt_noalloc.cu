@@ -117,10 +117,8 @@ extern "C" dpt_status dpt_solve_dominant_noalloc(int64_t n, const double* theta,
   float* f = reinterpret_cast<float*>(b + kStateBytes + kPartBytes);
   float* thh = f;
   float* thl = f + n;
-  float* zh0 = f + 2 * n;
-  float* zl0 = f + 3 * n;
-  float* zh1 = f + 4 * n;
-  float* zl1 = f + 5 * n;
+  float2* z0 = reinterpret_cast<float2*>(f + 2 * n);   // (hi, lo) pairs
+  float2* z1 = reinterpret_cast<float2*>(f + 4 * n);
 
 #define NA_CK(call)                                 \
   do {                                              \
@@ -158,20 +156,20 @@ extern "C" dpt_status dpt_solve_dominant_noalloc(int64_t n, const double* theta,
   NA_CK(cudaStreamSynchronize(s));
   if (h.bad_input) return done(DPT_ERR_ARG);
   if (h.ties != 1u) return done(DPT_ERR_DEGENERATE);
-  NA_CK(launch_dom_init(ni, zh0, zl0, nullptr, 1, st, s));
+  NA_CK(launch_dom_init(ni, z0, nullptr, 1, st, s));
   const double avg = (double)nnz32 / (double)n;
   const int V = avg < 24 ? 4 : (avg < 48 ? 8 : (avg < 96 ? 16 : 32));
   // plain launches (no graph: instantiating one may allocate), host check every 4
   const int per = 4;
   for (int c = 0; c <= max_iter / per + 1; ++c) {
     for (int q = 0; q < per; ++q)
-      NA_CK(launch_dom_iter(ni, V, 1, row_ptr, col_idx, vals, thh, thl, theta, zh0, zl0, zh1,
-                            zl1, nullptr, nullptr, part, st, s));
+      NA_CK(launch_dom_iter(ni, V, 1, row_ptr, col_idx, vals, thh, thl, theta, z0, z1, nullptr,
+                            nullptr, part, st, s));
     NA_CK(cudaMemcpyAsync(&h, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
     if (h.status != ST_RUNNING) break;
   }
-  NA_CK(launch_dom_out(ni, zh0, zl0, zh1, zl1, nullptr, nullptr, 1, z_out, st, s));
+  NA_CK(launch_dom_out(ni, z0, z1, nullptr, nullptr, 1, z_out, st, s));
   NA_CK(cudaMemcpyAsync(&h, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
   NA_CK(cudaStreamSynchronize(s));
   if (on_device(E_out)) NA_CK(cudaMemcpy(E_out, &h.E, sizeof(double), cudaMemcpyHostToDevice));
