@@ -122,7 +122,8 @@ DPT_API const char* dpt_status_string(dpt_status s);
 
 /* Full spectrum: all n eigenpairs of M = diag(theta) + lambda * Delta.
  *   n          matrix size, n >= 1
- *   dtype      DPT_R64 or DPT_C128 (the latter with DPT_PREC_FP64 or MIXED_BF16)
+ *   dtype      DPT_R64 or DPT_C128 (complex mixed solves run through the grouped path
+ *              of dpt_solve_batched with one problem)
  *   theta      n doubles, pairwise distinct and finite
  *   delta      n x n, column-major, leading dimension ld_delta >= n, finite
  *   lambda     real perturbation strength
@@ -142,6 +143,7 @@ DPT_API dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* thet
  * stage of an iteration is one launch over all problems' tiles, and each problem
  * stops at its own convergence (Sec. II.B: each problem is its own fixed-point
  * iteration).  Arrays of length count:
+ *   dtype        DPT_R64, or DPT_C128 (Delta, A, E interleaved complex; theta, lambda real)
  *   n[p]         size of problem p, 1 <= n[p] <= 65536
  *   theta[p]     device pointer, n[p] distinct finite doubles
  *   delta[p]     device pointer, column-major n[p] x n[p], leading dimension ld_delta[p]
@@ -152,11 +154,12 @@ DPT_API dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* thet
  * opt->prec == DPT_PREC_MIXED_BF16 without the Epstein-Nesbet shift is supported.
  * Returns DPT_OK when every problem converged, else the first failing problem's
  * status (infos[p] tells which).  Blocks until done. */
-DPT_API dpt_status dpt_solve_batched(int64_t count, const int64_t* n, const double* const* theta,
-                                     const double* const* delta, const int64_t* ld_delta,
-                                     const double* lambda, const dpt_options* opt,
-                                     double* const* A_out, const int64_t* ld_a,
-                                     double* const* E_out, dpt_info* infos, void* stream);
+DPT_API dpt_status dpt_solve_batched(int64_t count, dpt_dtype dtype, const int64_t* n,
+                                     const double* const* theta, const double* const* delta,
+                                     const int64_t* ld_delta, const double* lambda,
+                                     const dpt_options* opt, double* const* A_out,
+                                     const int64_t* ld_a, double* const* E_out,
+                                     dpt_info* infos, void* stream);
 
 /* Dominant eigenvector: the eigenpair continued from e_{n*}, by the single-vector
  * map of Eq. (single_line_dyn) (Sec. II.H; for a perturbative matrix this is the

@@ -676,10 +676,10 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
 // ---------------------------------------------------------------------------
 // Grouped solve of many independent real problems (mixed path)
 // ---------------------------------------------------------------------------
-// Tile width for a problem of size n: ceil(n / 256) column tiles, each the
-// smallest multiple of 32 covering its share.
-int group_tile_n(int n) {
-  const int ntn = (n + 255) / 256;
+// Tile width for a problem of size n: ceil(n / wmax) column tiles, each the
+// smallest multiple of 32 covering its share (wmax = 256 real, 128 complex).
+int group_tile_n(int n, int wmax) {
+  const int ntn = (n + wmax - 1) / wmax;
   const int w = (n + ntn - 1) / ntn;
   return (w + 31) / 32 * 32;
 }
@@ -687,24 +687,28 @@ int group_tile_n(int n) {
 struct GroupPlan {
   std::vector<GProb> probs;
   std::vector<int2> tiles;      // product kernel: (problem, tile)
-  std::vector<int4> prep;       // (problem, col block, row block) 32 x 32
-  std::vector<int4> blk128;     // (problem, col tile, row tile) 128 x 128
+  std::vector<int4> prep_r;     // real: (problem, col block, row block) 32 x 32
+  std::vector<int4> prep_c;     // complex: (problem, col block, row block) 16 x 16 complex
+  std::vector<int4> blk_r;      // real: (problem, col tile, row tile) 128 x 128
+  std::vector<int4> blk_c;      // complex: (problem, col tile, embedded-row tile) 128 x 128
   size_t bytes = 0;
 };
 
 // Lays out every problem's work arrays in one arena at `base` (nullptr: size only).
-void plan_group(GroupPlan& g, int count, const int64_t* n, const double* const* theta,
+void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const double* const* theta,
                 const double* const* delta, const int64_t* ld_delta, const double* lambda,
-                double* const* A_out, const int64_t* ld_a, double* const* E_out,
-                const dpt_options& o, char* base, IterState* states_dev) {
+                double* const* A_out, const int64_t* ld_a, double* const* E_out, char* base,
+                IterState* states_dev) {
   Carve c{base};
   g.probs.assign(count, GProb{});
-  g.tiles.clear(); g.prep.clear(); g.blk128.clear();
+  g.tiles.clear(); g.prep_r.clear(); g.prep_c.clear(); g.blk_r.clear(); g.blk_c.clear();
   for (int p = 0; p < count; ++p) {
     GProb& P = g.probs[p];
     const int np = (int)n[p];
-    const int ld = (int)round_up(np, 128);
-    P.n = np; P.ld = ld; P.ntm = (np + 127) / 128; P.bn = group_tile_n(np);
+    const int nr = cplx ? 2 * np : np;
+    const int ld = (int)round_up(nr, 128);
+    P.n = np; P.nr = nr; P.cplx = cplx; P.ld = ld; P.ntm = (nr + 127) / 128;
+    P.bn = group_tile_n(np, cplx ? 128 : 256);
     P.ntn = (np + P.bn - 1) / P.bn;
     P.lam = (float)lambda[p];
     P.lam_lo = (float)(lambda[p] - (double)P.lam);
@@ -716,41 +720,48 @@ void plan_group(GroupPlan& g, int count, const int64_t* n, const double* const* 
     P.ld_a = ld_a[p];
     P.E_out = E_out[p];
     P.st = states_dev + p;
+    const int w = cplx ? 2 : 1;     // values per column parameter (re, im)
     P.th_hi = c.take<float>(ld); P.th_lo = c.take<float>(ld);
-    P.d = c.take<double>(ld); P.E = c.take<double>(ld);
-    P.e_col = c.take<float>(ld); P.dprev_col = c.take<float>(ld);
-    P.part = c.take<float>((size_t)4 * P.ntm * ld);
-    P.rowpart = c.take<float>((size_t)P.ntm * ld);
-    P.Dcat = c.take<__nv_bfloat16>((size_t)3 * ld * np);
+    P.d = c.take<double>(w * ld); P.E = c.take<double>(w * ld);
+    P.e_col = c.take<float>(w * ld); P.dprev_col = c.take<float>(w * ld);
+    P.part = c.take<float>((size_t)(2 + 2 * w) * P.ntm * ld);
+    P.rowpart = c.take<float>((size_t)((np + 127) / 128) * ld);
+    P.Dcat = c.take<__nv_bfloat16>((size_t)3 * ld * nr);
     P.cat_ld = (int64_t)3 * ld;
     for (int q = 0; q < 2; ++q) { P.A_hi[q] = c.take<float>((size_t)ld * np); P.A_lo[q] = c.take<float>((size_t)ld * np); }
     for (int q = 0; q < 2; ++q) P.dt[q] = c.take<__nv_bfloat16>((size_t)ld * np);
     P.L = c.take<float>((size_t)ld * np);
     for (int t = 0; t < P.ntm * P.ntn; ++t) g.tiles.push_back(make_int2(p, t));
-    for (int by = 0; by < (np + 31) / 32; ++by)
-      for (int bx = 0; bx < ld / 32; ++bx) g.prep.push_back(make_int4(p, bx, by, 0));
-    for (int tm = 0; tm < P.ntm; ++tm)
-      for (int tn = 0; tn < P.ntm; ++tn) g.blk128.push_back(make_int4(p, tn, tm, 0));
+    const int ntn128 = (np + 127) / 128;
+    if (cplx) {
+      for (int by = 0; by < (np + 15) / 16; ++by)
+        for (int bx = 0; bx < (ld / 2 + 15) / 16; ++bx) g.prep_c.push_back(make_int4(p, bx, by, 0));
+      for (int tm = 0; tm < P.ntm; ++tm)
+        for (int tn = 0; tn < ntn128; ++tn) g.blk_c.push_back(make_int4(p, tn, tm, 0));
+    } else {
+      for (int by = 0; by < (np + 31) / 32; ++by)
+        for (int bx = 0; bx < ld / 32; ++bx) g.prep_r.push_back(make_int4(p, bx, by, 0));
+      for (int tm = 0; tm < P.ntm; ++tm)
+        for (int tn = 0; tn < ntn128; ++tn) g.blk_r.push_back(make_int4(p, tn, tm, 0));
+    }
   }
-  (void)o;
   g.bytes = (size_t)round_up((int64_t)c.off, 256) + 256;
 }
 
-dpt_status solve_batched(int count, const int64_t* n, const double* const* theta,
+dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* const* theta,
                          const double* const* delta, const int64_t* ld_delta,
                          const double* lambda, const dpt_options& o, double* const* A_out,
                          const int64_t* ld_a, double* const* E_out, dpt_info* infos,
                          cudaStream_t user) {
-  // sizes of the tables and of the arena
   GroupPlan g;
-  plan_group(g, count, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, o, nullptr, nullptr);
+  plan_group(g, count, cplx, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, nullptr, nullptr);
   const size_t arena = g.bytes;
   auto layout = [&](Carve& c) {
     c.take<IterState>(count);
     c.take<GProb>(count);
     c.take<int2>(g.tiles.size());
-    c.take<int4>(g.prep.size());
-    c.take<int4>(g.blk128.size());
+    c.take<int4>(g.prep_r.size() + g.prep_c.size());
+    c.take<int4>(g.blk_r.size() + g.blk_c.size());
     c.take<int>(4);
     c.take<char>(arena);
   };
@@ -761,16 +772,15 @@ dpt_status solve_batched(int count, const int64_t* n, const double* const* theta
     IterState* st = c.take<IterState>(count);
     GProb* probs = c.take<GProb>(count);
     int2* tiles = c.take<int2>(g.tiles.size());
-    int4* prep = c.take<int4>(g.prep.size());
-    int4* blk = c.take<int4>(g.blk128.size());
+    int4* prep = c.take<int4>(g.prep_r.size() + g.prep_c.size());
+    int4* blk = c.take<int4>(g.blk_r.size() + g.blk_c.size());
     int* flags = c.take<int>(4);      // [0] running count, [1] timeout
     char* ar = c.take<char>(arena);
-    plan_group(g, count, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, o, ar, st);
-    // TMA descriptors per problem
+    plan_group(g, count, cplx, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, ar, st);
     for (int p = 0; p < count; ++p) {
       GProb& P = g.probs[p];
-      P.tmA = make_tmap_bf16(P.Dcat, (uint64_t)3 * P.ld, P.n, (uint64_t)3 * P.ld, 128);
-      for (int q = 0; q < 2; ++q) P.tmB[q] = make_tmap_bf16(P.dt[q], P.n, P.n, P.ld, P.bn);
+      P.tmA = make_tmap_bf16(P.Dcat, (uint64_t)3 * P.ld, P.nr, (uint64_t)3 * P.ld, 128);
+      for (int q = 0; q < 2; ++q) P.tmB[q] = make_tmap_bf16(P.dt[q], P.nr, P.n, P.ld, P.bn);
     }
     std::vector<IterState> hs(count);
     for (int p = 0; p < count; ++p) {
@@ -786,6 +796,11 @@ dpt_status solve_batched(int count, const int64_t* n, const double* const* theta
       h.best = INFINITY;
       h.theta_max = 0.0;   // set by the theta check on the device
     }
+    std::vector<int4> preps(g.prep_r), blks(g.blk_r);
+    preps.insert(preps.end(), g.prep_c.begin(), g.prep_c.end());
+    blks.insert(blks.end(), g.blk_c.begin(), g.blk_c.end());
+    const int n_prep_r = (int)g.prep_r.size(), n_prep_c = (int)g.prep_c.size();
+    const int n_blk_r = (int)g.blk_r.size(), n_blk_c = (int)g.blk_c.size();
     cudaStream_t s = b->stream;
     CK(cudaEventRecord(b->ev, user));
     CK(cudaStreamWaitEvent(s, b->ev, 0));
@@ -793,26 +808,33 @@ dpt_status solve_batched(int count, const int64_t* n, const double* const* theta
     CK(cudaMemcpyAsync(st, hs.data(), sizeof(IterState) * count, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(probs, g.probs.data(), sizeof(GProb) * count, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(tiles, g.tiles.data(), sizeof(int2) * g.tiles.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(prep, g.prep.data(), sizeof(int4) * g.prep.size(), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(blk, g.blk128.data(), sizeof(int4) * g.blk128.size(), cudaMemcpyHostToDevice, s));
+    if (!preps.empty())
+      CK(cudaMemcpyAsync(prep, preps.data(), sizeof(int4) * preps.size(), cudaMemcpyHostToDevice, s));
+    if (!blks.empty())
+      CK(cudaMemcpyAsync(blk, blks.data(), sizeof(int4) * blks.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(flags, hflags, sizeof(hflags), cudaMemcpyHostToDevice, s));
     CK(g_set_attributes());
     CK(launch_g_check_theta(probs, count, flags, s));
-    CK(launch_g_prep(probs, prep, (int)g.prep.size(), s));
-    CK(launch_g_iter0(probs, blk, (int)g.blk128.size(), s));
-    CK(launch_g_ctrl(probs, count, flags, s));
+    CK(launch_g_prep(probs, prep, n_prep_r, s));
+    CK(launch_gc_prep(probs, prep + n_prep_r, n_prep_c, s));
+    CK(launch_g_iter0(probs, blk, n_blk_r, s));
+    CK(launch_gc_iter0(probs, blk + n_blk_r, n_blk_c, s));
+    auto ctrl = [&]() {
+      if (!cplx) CK(launch_g_ctrl(probs, count, flags, s));
+      else CK(launch_gc_ctrl(probs, count, flags, s));
+    };
+    ctrl();
     Prof prof;
     prof.on = o.profile != 0;
-    prof.launches = 4;
-    // host loop: graph replays of G iterations, stop when no problem runs
+    prof.launches = 5;
     const int per = o.graph_iters > 0 ? o.graph_iters : 4;
     prof.make(per);
     cudaGraphExec_t exec = nullptr;
     auto iter = [&](int q) {
       prof.before(q, s);
-      CK(launch_g_gemm_epi(probs, tiles, (int)g.tiles.size(), (unsigned*)(flags + 1), s));
+      CK(launch_g_gemm_epi(probs, tiles, (int)g.tiles.size(), (unsigned*)(flags + 1), cplx != 0, s));
       prof.after(q, s);
-      CK(launch_g_ctrl(probs, count, flags, s));
+      ctrl();
     };
     if (o.graph_iters > 0) {
       cudaGraph_t gr;
@@ -831,8 +853,7 @@ dpt_status solve_batched(int count, const int64_t* n, const double* const* theta
         prof.launches += 2 * per;
         CK(cudaMemcpyAsync(hrun, flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        // product time of the launches that did work is not separable per problem
-        // here: all per launches are counted while any problem runs
+        // the product launches of a chunk all count while any problem runs
         prof.collect(per);
         if (hrun[0] <= 0 || hrun[1]) break;
       }
@@ -841,7 +862,8 @@ dpt_status solve_batched(int count, const int64_t* n, const double* const* theta
       throw;
     }
     if (exec) cudaGraphExecDestroy(exec);
-    CK(launch_g_finalize(probs, blk, (int)g.blk128.size(), s));
+    CK(launch_g_finalize(probs, blk, n_blk_r, s));
+    CK(launch_gc_finalize(probs, blk + n_blk_r, n_blk_c, s));
     prof.launches += 1;
     CK(cudaMemcpyAsync(hs.data(), st, sizeof(IterState) * count, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -864,6 +886,51 @@ dpt_status solve_batched(int count, const int64_t* n, const double* const* theta
     CK(cudaStreamWaitEvent(user, b->ev, 0));
   } catch (Fail f) {
     cudaStreamSynchronize(b->stream);
+    ret = f.st;
+  }
+  release(b);
+  return ret;
+}
+
+// Complex mixed full solve: one problem through the grouped path, host buffers
+// staged through a pool block.
+dpt_status solve_full_mixed_complex(int64_t n, const std::vector<double>& th,
+                                    const double* delta, bool d_dev, int64_t ld_delta,
+                                    double lambda, const dpt_options& o, double* A_out,
+                                    bool a_dev, int64_t ld_a, double* E_out, bool e_dev,
+                                    dpt_info* info, cudaStream_t user) {
+  auto layout = [&](Carve& c) {
+    c.take<double>(n);
+    c.take<double>((size_t)2 * n * n);
+    c.take<double>((size_t)2 * n * n);
+    c.take<double>((size_t)2 * n);
+  };
+  Block* b = acquire(measure(layout));
+  dpt_status ret = DPT_OK;
+  try {
+    Carve c{(char*)b->ptr};
+    double* thd = c.take<double>(n);
+    double* Dd = c.take<double>((size_t)2 * n * n);
+    double* Ad = c.take<double>((size_t)2 * n * n);
+    double* Ed = c.take<double>((size_t)2 * n);
+    CK(cudaMemcpyAsync(thd, th.data(), sizeof(double) * n, cudaMemcpyHostToDevice, user));
+    CK(cudaMemcpy2DAsync(Dd, sizeof(double) * 2 * n, delta, sizeof(double) * 2 * ld_delta,
+                         sizeof(double) * 2 * n, n,
+                         d_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, user));
+    const int64_t nn = n, ldd = n, lda = n;
+    const double* thp = thd;
+    const double* dp = Dd;
+    double* ap = Ad;
+    double* ep = Ed;
+    ret = solve_batched(1, 1, &nn, &thp, &dp, &ldd, &lambda, o, &ap, &lda, &ep, info, user);
+    CK(cudaMemcpy2DAsync(A_out, sizeof(double) * 2 * ld_a, Ad, sizeof(double) * 2 * n,
+                         sizeof(double) * 2 * n, n,
+                         a_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, user));
+    CK(cudaMemcpyAsync(E_out, Ed, sizeof(double) * 2 * n,
+                       e_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, user));
+    CK(cudaStreamSynchronize(user));
+  } catch (Fail f) {
+    cudaStreamSynchronize(user);
     ret = f.st;
   }
   release(b);
@@ -926,7 +993,8 @@ dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const
     return done(DPT_ERR_ARG);
   if (o.prec != DPT_PREC_FP64 && o.prec != DPT_PREC_MIXED_BF16) return done(DPT_ERR_ARG);
   if (o.max_slices < 1 || o.max_slices > 3) return done(DPT_ERR_ARG);
-  if (o.prec == DPT_PREC_MIXED_BF16 && dtype == DPT_C128) return done(DPT_ERR_UNSUPPORTED);
+  if (o.prec == DPT_PREC_MIXED_BF16 && dtype == DPT_C128 && o.epstein_nesbet)
+    return done(DPT_ERR_UNSUPPORTED);
   try {
     cudaStream_t s = (cudaStream_t)stream;
     const bool th_dev = is_device_ptr(theta), d_dev = is_device_ptr(delta),
@@ -950,7 +1018,10 @@ dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const
     }
     st = check_distinct(th);
     if (st != DPT_OK) return done(st);
-    if (o.prec == DPT_PREC_MIXED_BF16)
+    if (o.prec == DPT_PREC_MIXED_BF16 && dtype == DPT_C128)
+      st = solve_full_mixed_complex(n, th, (const double*)delta, d_dev, ld_delta, lambda, o,
+                                    (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info, s);
+    else if (o.prec == DPT_PREC_MIXED_BF16)
       st = solve_full_mixed_real(n, th, (const double*)delta, d_dev, ld_delta, lambda, o,
                                  (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info, s);
     else
@@ -992,10 +1063,10 @@ dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int32_t* row
   }
 }
 
-dpt_status dpt_solve_batched(int64_t count, const int64_t* n, const double* const* theta,
-                             const double* const* delta, const int64_t* ld_delta,
-                             const double* lambda, const dpt_options* opt,
-                             double* const* A_out, const int64_t* ld_a,
+dpt_status dpt_solve_batched(int64_t count, dpt_dtype dtype, const int64_t* n,
+                             const double* const* theta, const double* const* delta,
+                             const int64_t* ld_delta, const double* lambda,
+                             const dpt_options* opt, double* const* A_out, const int64_t* ld_a,
                              double* const* E_out, dpt_info* infos, void* stream) {
   dpt_options o;
   dpt_options_default(&o);
@@ -1004,6 +1075,7 @@ dpt_status dpt_solve_batched(int64_t count, const int64_t* n, const double* cons
       !A_out || !ld_a || !E_out || !(o.tol > 0) || o.max_iter < 0 || o.max_slices < 1 ||
       o.max_slices > 3)
     return DPT_ERR_ARG;
+  if (dtype != DPT_R64 && dtype != DPT_C128) return DPT_ERR_ARG;
   if (o.prec != DPT_PREC_MIXED_BF16 || o.epstein_nesbet) return DPT_ERR_UNSUPPORTED;
   for (int64_t p = 0; p < count; ++p) {
     if (n[p] < 1 || n[p] > 65536 || ld_delta[p] < n[p] || ld_a[p] < n[p] || !theta[p] ||
@@ -1014,8 +1086,8 @@ dpt_status dpt_solve_batched(int64_t count, const int64_t* n, const double* cons
     if (!is_device_ptr(theta[0]) || !is_device_ptr(delta[0]) || !is_device_ptr(A_out[0]) ||
         !is_device_ptr(E_out[0]))
       return DPT_ERR_UNSUPPORTED;
-    return solve_batched((int)count, n, theta, delta, ld_delta, lambda, o, A_out, ld_a, E_out,
-                         infos, (cudaStream_t)stream);
+    return solve_batched((int)count, dtype == DPT_C128 ? 1 : 0, n, theta, delta, ld_delta,
+                         lambda, o, A_out, ld_a, E_out, infos, (cudaStream_t)stream);
   } catch (Fail f) {
     return f.st;
   } catch (...) {

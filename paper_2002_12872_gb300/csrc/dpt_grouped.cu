@@ -237,6 +237,7 @@ __global__ void __launch_bounds__(256) k_g_ctrl(const GProb* __restrict__ probs,
   const int p = blockIdx.x;
   if (p >= count) return;
   const GProb* P = probs + p;
+  if (P->cplx) return;
   IterState* st = P->st;
   if (st->status != ST_RUNNING) return;
   const int n = P->n, ld = P->ld, ntm = P->ntm;
@@ -291,6 +292,280 @@ __global__ void __launch_bounds__(256) k_g_ctrl(const GProb* __restrict__ probs,
   const int S = ((double)dmax < vs->slice_tol) ? 1 : vs->max_slices;
   vs->slices = S;
   vs->slice_gemms = vs->slice_gemms + S;
+}
+
+
+// ===========================================================================
+// Complex problems.  The product is the real GEMM of the interleaved embedding:
+// embedded row 2j carries [Re D_jk, -Im D_jk] and row 2j+1 [Im D_jk, Re D_jk] at
+// K = (2k, 2k+1), and a complex increment column stored (re, im) interleaved is
+// the K-major B operand, so X rows (2j, 2j+1) = (Re, Im) of (Delta dt)_j.  Each
+// epilogue lane's four consecutive rows are two complex elements.  theta and
+// lambda are real.
+// ===========================================================================
+
+// Delta (complex, column-major, interleaved doubles) -> three BF16 slices of the
+// embedding; theta -> float-float.  Work item: (problem, 16 complex columns, 16
+// complex rows); block 16 x 16.
+__global__ void k_gc_prep(const GProb* __restrict__ probs, const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const GProb* P = probs + it.x;
+  if (!g_running(P)) return;
+  __shared__ double2 tile[16][17];
+  const int n = P->n, ld = P->ld;
+  const int bx = it.y * 16, by = it.z * 16;      // complex column k, complex row j
+  const double2* delta = reinterpret_cast<const double2*>(P->delta_in);
+  const int64_t ld_in = P->ld_in;
+  {
+    const int j = by + threadIdx.x, k = bx + threadIdx.y;
+    double2 v = make_double2(0.0, 0.0);
+    if (j < n && k < n) {
+      v = delta[(int64_t)k * ld_in + j];
+      if (!finite_bits(v.x) || !finite_bits(v.y)) atomicExch(&P->st->bad_input, 1u);
+    }
+    tile[threadIdx.y][threadIdx.x] = v;    // tile[k - bx][j - by]
+  }
+  if (bx == 0 && threadIdx.y == 0) {
+    const int j = by + threadIdx.x;
+    if (j < n) {
+      float h, l;
+      split_double(P->theta[j], h, l);
+      P->th_hi[j] = h;
+      P->th_lo[j] = l;
+    }
+  }
+  __syncthreads();
+  const int j = by + threadIdx.y, k = bx + threadIdx.x;   // write complex row j, column k
+  if (j >= n || 2 * k >= ld) return;
+  const double2 v = (k < n) ? tile[threadIdx.x][threadIdx.y] : make_double2(0.0, 0.0);
+  // the four entries of the 2 x 2 real block of element (j, k)
+  double e4[4] = {v.x, -v.y, v.y, v.x};    // (2j,2k) (2j,2k+1) (2j+1,2k) (2j+1,2k+1)
+  const int64_t cat_ld = P->cat_ld;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = 2 * j + (q >> 1), c = 2 * k + (q & 1);
+    float rh, rl;
+    split_double(e4[q], rh, rl);
+    for (int sl = 0; sl < G_NSLICE; ++sl) {
+      const __nv_bfloat16 b = __float2bfloat16_rn(rh);
+      P->Dcat[(int64_t)r * cat_ld + (int64_t)sl * ld + c] = b;
+      two_sum(rh - __bfloat162float(b), rl, rh, rl);
+    }
+  }
+}
+
+// complex product a * b in float
+__device__ __forceinline__ void cmulf(float ar, float ai, float br, float bi, float& rr, float& ri) {
+  rr = fmaf(ar, br, -ai * bi);
+  ri = fmaf(ar, bi, ai * br);
+}
+
+// Iteration 0 (A_0 = I) for a complex problem.  Work item (problem, 128-column
+// tile, 128-embedded-row tile); lane l owns complex rows jc, jc + 1.
+__global__ void __launch_bounds__(128) k_gc_iter0(const GProb* __restrict__ probs,
+                                                  const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const GProb* P = probs + it.x;
+  if (!g_running(P)) return;
+  __shared__ float rows[4][64];
+  const int n = P->n, ld = P->ld, ntm = P->ntm;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int n0 = it.y * 128, m0 = it.z * 128, tm = it.z;
+  const int r0 = 4 * lane, jc0 = (m0 + r0) / 2;   // embedded rows m0+r0.., complex rows jc0, jc0+1
+  const int64_t cat_ld = P->cat_ld;
+  const float lam_hi = P->lam, lam_lo = P->lam_lo;
+  const double2* delta = reinterpret_cast<const double2*>(P->delta_in);
+  const int64_t ld_in = P->ld_in;
+  float thj_h[2], thj_l[2];
+  for (int e = 0; e < 2; ++e) {
+    const int j = jc0 + e;
+    thj_h[e] = j < n ? P->th_hi[j] : 0.f;
+    thj_l[e] = j < n ? P->th_lo[j] : 0.f;
+  }
+  float rowabs[2] = {0.f, 0.f};
+  float mx = 0.f;
+  for (int c = 0; c < 32; ++c) {
+    const int i = n0 + 32 * w + c;
+    if (i >= n) break;
+    const float thi_h = P->th_hi[i], thi_l = P->th_lo[i];
+    // Delta(i, jc0..jc0+1) from embedded row 2i: (Re, -Im) pairs
+    const __nv_bfloat16* Drow = P->Dcat + (int64_t)(2 * i) * cat_ld + 2 * jc0;
+    uint2 D[3];
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+    float oh[4], oL[4];
+    uint32_t ob[4];
+    float r2 = 0.f, a2 = 0.f, erh = 0.f, erl = 0.f, eih = 0.f, eil = 0.f;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int j = jc0 + e;
+      float dn[2] = {0.f, 0.f}, L2[2] = {0.f, 0.f}, A2[2] = {0.f, 0.f};
+      if (j < n) {
+        const double2 v = delta[(int64_t)i * ld_in + j];
+        float vh[2], vl[2];
+        split_double(v.x, vh[0], vl[0]);
+        split_double(v.y, vh[1], vl[1]);
+        rowabs[e] += sqrtf(vh[0] * vh[0] + vh[1] * vh[1]);
+        if (j == i) {
+          A2[0] = 1.f;
+          a2 += 1.f;
+          P->d[2 * i] = v.x;
+          P->d[2 * i + 1] = v.y;
+        } else {
+          float gh, gl;
+          ff_sub(thi_h, thi_l, thj_h[e], thj_l[e], gh, gl);
+          const float g = __frcp_rn(gh);
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            float pr, pe;
+            two_prod(lam_hi, vh[q], pr, pe);
+            pe = fmaf(lam_hi, vl[q], fmaf(lam_lo, vh[q], pe));
+            float R0h, R0l;
+            fast_two_sum(pr, pe, R0h, R0l);
+            dn[q] = bf16_round(R0h * g);
+            float qq, qe;
+            two_prod(gh, dn[q], qq, qe);
+            qe = fmaf(gl, dn[q], qe);
+            L2[q] = (R0h - qq) + (R0l - qe);
+            A2[q] = dn[q];
+            r2 = fmaf(R0h, R0h, r2);
+          }
+          // e_1 partial: Delta(i, j) dt(j, i), slices exact
+          float pr1, pi1, pr2, pi2;
+          const float a1 = bf_at(D[0], 2 * e), b1 = bf_at(D[0], 2 * e + 1);
+          pr1 = fmaf(a1, dn[0], b1 * dn[1]);          // a x + b' y   (b' = -Im)
+          pi1 = fmaf(a1, dn[1], -b1 * dn[0]);         // a y - b' x
+          const float a2s = bf_at(D[1], 2 * e) + bf_at(D[2], 2 * e);
+          const float b2s = bf_at(D[1], 2 * e + 1) + bf_at(D[2], 2 * e + 1);
+          pr2 = fmaf(a2s, dn[0], b2s * dn[1]);
+          pi2 = fmaf(a2s, dn[1], -b2s * dn[0]);
+          float sh, se;
+          two_sum(erh, pr1, sh, se); se += erl + pr2; fast_two_sum(sh, se, erh, erl);
+          two_sum(eih, pi1, sh, se); se += eil + pi2; fast_two_sum(sh, se, eih, eil);
+          mx = fmaxf(mx, fmaxf(fabsf(dn[0]), fabsf(dn[1])));
+        }
+      }
+      oh[2 * e] = A2[0]; oh[2 * e + 1] = A2[1];
+      oL[2 * e] = L2[0]; oL[2 * e + 1] = L2[1];
+      ob[2 * e] = bf_bits(dn[0]); ob[2 * e + 1] = bf_bits(dn[1]);
+    }
+    const int64_t idx = (int64_t)i * ld + m0 + r0;
+    st4(P->A_hi[1] + idx, make_float4(oh[0], oh[1], oh[2], oh[3]));
+    st4(P->A_lo[1] + idx, make_float4(0.f, 0.f, 0.f, 0.f));
+    st4(P->L + idx, make_float4(oL[0], oL[1], oL[2], oL[3]));
+    *reinterpret_cast<uint2*>(P->dt[0] + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+    warp_sum_ff(r2, a2, erh, erl);
+    float z0 = 0.f, z1 = 0.f;
+    warp_sum_ff(z0, z1, eih, eil);
+    if (lane == 0) {
+      P->part[((int64_t)0 * ntm + tm) * ld + i] = r2;
+      P->part[((int64_t)1 * ntm + tm) * ld + i] = a2;
+      P->part[((int64_t)2 * ntm + tm) * ld + i] = erh;
+      P->part[((int64_t)3 * ntm + tm) * ld + i] = erl;
+      P->part[((int64_t)4 * ntm + tm) * ld + i] = eih;
+      P->part[((int64_t)5 * ntm + tm) * ld + i] = eil;
+    }
+  }
+  rows[w][2 * lane] = rowabs[0];
+  rows[w][2 * lane + 1] = rowabs[1];
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int r = threadIdx.x, j = m0 / 2 + r;
+    if (j < n)
+      P->rowpart[(int64_t)it.y * ld + j] = ((rows[0][r] + rows[1][r]) + rows[2][r]) + rows[3][r];
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0 && mx > 0.f) atomicMax(&P->st->dmax_bits, __float_as_uint(mx));
+}
+
+// Control for complex problems: as k_g_ctrl with complex d, E, e.
+__global__ void __launch_bounds__(256) k_gc_ctrl(const GProb* __restrict__ probs, int count,
+                                                 int* running) {
+  const int p = blockIdx.x;
+  if (p >= count) return;
+  const GProb* P = probs + p;
+  if (!P->cplx) return;
+  IterState* st = P->st;
+  if (st->status != ST_RUNNING) return;
+  const int n = P->n, ld = P->ld, ntm = P->ntm;
+  const int ntn128 = (n + 127) / 128;
+  const bool first = (st->k == 0);
+  float rmax = 0.f, rowmax = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    float r2 = 0.f, a2 = 0.f;
+    double er = 0.0, ei = 0.0;
+    for (int t = 0; t < ntm; ++t) {
+      r2 += P->part[((int64_t)0 * ntm + t) * ld + i];
+      a2 += P->part[((int64_t)1 * ntm + t) * ld + i];
+      er += (double)P->part[((int64_t)2 * ntm + t) * ld + i] + (double)P->part[((int64_t)3 * ntm + t) * ld + i];
+      ei += (double)P->part[((int64_t)4 * ntm + t) * ld + i] + (double)P->part[((int64_t)5 * ntm + t) * ld + i];
+    }
+    float rr = sqrtf(r2 / a2);
+    if (!(rr == rr) || isinf(rr)) rr = __int_as_float(0x7f800000);
+    rmax = fmaxf(rmax, rr);
+    const double dr = P->d[2 * i], di = P->d[2 * i + 1];
+    P->E[2 * i] = P->theta[i] + P->lam64 * dr;
+    P->E[2 * i + 1] = P->lam64 * di;
+    P->dprev_col[2 * i] = (float)dr;
+    P->dprev_col[2 * i + 1] = (float)di;
+    P->e_col[2 * i] = (float)er;
+    P->e_col[2 * i + 1] = (float)ei;
+    P->d[2 * i] = dr + er;
+    P->d[2 * i + 1] = di + ei;
+    if (first) {
+      float rs = 0.f;
+      for (int t = 0; t < ntn128; ++t) rs += P->rowpart[(int64_t)t * ld + i];
+      rowmax = fmaxf(rowmax, rs);
+    }
+  }
+  __shared__ float sm[2][8];
+  for (int o = 16; o > 0; o >>= 1) {
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    rowmax = fmaxf(rowmax, __shfl_xor_sync(0xffffffffu, rowmax, o));
+  }
+  if ((threadIdx.x & 31) == 0) { sm[0][threadIdx.x >> 5] = rmax; sm[1][threadIdx.x >> 5] = rowmax; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+    rmax = fmaxf(rmax, sm[0][q]);
+    rowmax = fmaxf(rowmax, sm[1][q]);
+  }
+  volatile IterState* vs = st;
+  if (first) vs->s = vs->theta_max + fabs(vs->lam) * (double)rowmax;
+  const float dmax = __uint_as_float(vs->dmax_bits);
+  vs->dmax_bits = 0;
+  if (!decide(vs, (double)rmax / vs->s)) {
+    atomicSub(running, 1);
+    return;
+  }
+  const int S = ((double)dmax < vs->slice_tol) ? 1 : vs->max_slices;
+  vs->slices = S;
+  vs->slice_gemms = vs->slice_gemms + S;
+}
+
+// Output of complex problems (interleaved FP64).
+__global__ void k_gc_finalize(const GProb* __restrict__ probs, const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const GProb* P = probs + it.x;
+  if (!P->cplx) return;
+  const IterState* st = P->st;
+  const int n = P->n, ld = P->ld;
+  const int k = st->k;
+  const bool c1 = st->cur != 0;
+  const float* hi = c1 ? P->A_hi[1] : P->A_hi[0];
+  const float* lo = c1 ? P->A_lo[1] : P->A_lo[0];
+  const int r = it.z * 128 + threadIdx.x;       // embedded row
+  const int j = r >> 1;
+  if (j >= n) return;
+  for (int c = 0; c < 128; ++c) {
+    const int i = it.y * 128 + c;
+    if (i >= n) break;
+    double v;
+    if (k == 0) v = (i == j && (r & 1) == 0) ? 1.0 : 0.0;
+    else v = f2d_bits(hi[(int64_t)i * ld + r]) + f2d_bits(lo[(int64_t)i * ld + r]);
+    P->A_out[2 * (int64_t)i * P->ld_a + r] = v;
+  }
+  if (it.y == 0) P->E_out[r] = P->E[r];
 }
 
 // ---------------------------------------------------------------------------
@@ -414,6 +689,125 @@ __device__ __forceinline__ void g_epilogue_columns(const GTileInfo& ti, GSmem* m
   }
 }
 
+
+// Complex column walk: lane l owns complex rows jc0, jc0+1 (embedded rows r0..r0+3).
+__device__ __forceinline__ void gc_epilogue_columns(const GTileInfo& ti, GSmem* ms, const float* Xs,
+                                                    int ew, int lane, int c0, float& mx) {
+  const GProb* P = ti.P;
+  const int n = P->n, ld = P->ld;
+  const bool c1 = (ti.cur != 0);
+  const float* __restrict__ Ahc = c1 ? P->A_hi[1] : P->A_hi[0];
+  const float* __restrict__ Alc = c1 ? P->A_lo[1] : P->A_lo[0];
+  float* __restrict__ Ahn = c1 ? P->A_hi[0] : P->A_hi[1];
+  float* __restrict__ Aln = c1 ? P->A_lo[0] : P->A_lo[1];
+  const __nv_bfloat16* __restrict__ dtp = c1 ? P->dt[0] : P->dt[1];
+  __nv_bfloat16* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
+  float* __restrict__ L = P->L;
+  const float lam = P->lam;
+  const int r0 = 4 * lane;
+  const int jc0 = (ti.m0 + r0) / 2;
+  float thj_h[2], thj_l[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int j = jc0 + e;
+    thj_h[e] = j < n ? P->th_hi[j] : 0.f;
+    thj_l[e] = j < n ? P->th_lo[j] : 0.f;
+  }
+  const int cb = c0 + 4 * ew;
+  if (cb >= ti.bn) return;
+  Col4 in[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = ti.n0 + cb + u;
+    if (i < n) {
+      const int64_t idx = (int64_t)i * ld + ti.m0 + r0;
+      in[u].ah = ld4(Ahc + idx);
+      in[u].al = ld4(Alc + idx);
+      in[u].L = ld4(L + idx);
+      in[u].dtp = *reinterpret_cast<const uint2*>(dtp + idx);
+      const __nv_bfloat16* Drow = P->Dcat + (int64_t)(2 * i) * P->cat_ld + 2 * jc0;
+#pragma unroll
+      for (int sl = 0; sl < 3; ++sl)
+        in[u].D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int cl = cb + u;
+    const int i = ti.n0 + cl;
+    if (i >= n) continue;
+    const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * G_BM + r0);
+    // complex e_i and d_{k-1,i} are stored as (re, im) in the parameter arrays
+    const float er = ms->e[2 * (cl & 127)], ei = ms->e[2 * (cl & 127) + 1];
+    const float dr = ms->dprev[2 * (cl & 127)], di = ms->dprev[2 * (cl & 127) + 1];
+    const float thh = ms->thh[cl], thl = ms->thl[cl];
+    float oh[4], ol[4], oL[4];
+    uint32_t ob[4];
+    float r2 = 0.f, a2 = 0.f, erh = 0.f, erl = 0.f, eih = 0.f, eil = 0.f;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int j = jc0 + e;
+      const float ar = f4(in[u].ah, 2 * e), ai = f4(in[u].ah, 2 * e + 1);
+      const float alr = f4(in[u].al, 2 * e), ali = f4(in[u].al, 2 * e + 1);
+      float nh[2] = {0.f, 0.f}, nl[2] = {0.f, 0.f}, Ln[2] = {0.f, 0.f}, dn[2] = {0.f, 0.f};
+      if (j == i) {
+        nh[0] = 1.f;
+        a2 += 1.f;
+      } else if (j < n) {
+        float aer, aei, pdr, pdi;
+        cmulf(ar, ai, er, ei, aer, aei);
+        cmulf(bf_at(in[u].dtp, 2 * e), bf_at(in[u].dtp, 2 * e + 1), dr, di, pdr, pdi);
+        float R[2];
+        R[0] = f4(in[u].L, 2 * e) + lam * (f4(x4, 2 * e) - aer - pdr);
+        R[1] = f4(in[u].L, 2 * e + 1) + lam * (f4(x4, 2 * e + 1) - aei - pdi);
+        float gh, gl;
+        ff_sub(thh, thl, thj_h[e], thj_l[e], gh, gl);
+        const float g = __frcp_rn(gh);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          dn[q] = bf16_round(R[q] * g);
+          Ln[q] = fmaf(-gh, dn[q], R[q]) - gl * dn[q];
+          r2 = fmaf(R[q], R[q], r2);
+        }
+        ff_add_f(ar, alr, dn[0], nh[0], nl[0]);
+        ff_add_f(ai, ali, dn[1], nh[1], nl[1]);
+        a2 = fmaf(ar, ar, fmaf(ai, ai, a2));
+        const float a1 = bf_at(in[u].D[0], 2 * e), b1 = bf_at(in[u].D[0], 2 * e + 1);
+        const float pr1 = fmaf(a1, dn[0], b1 * dn[1]), pi1 = fmaf(a1, dn[1], -b1 * dn[0]);
+        const float a2s = bf_at(in[u].D[1], 2 * e) + bf_at(in[u].D[2], 2 * e);
+        const float b2s = bf_at(in[u].D[1], 2 * e + 1) + bf_at(in[u].D[2], 2 * e + 1);
+        const float pr2 = fmaf(a2s, dn[0], b2s * dn[1]), pi2 = fmaf(a2s, dn[1], -b2s * dn[0]);
+        float sh, se;
+        two_sum(erh, pr1, sh, se); se += erl + pr2; fast_two_sum(sh, se, erh, erl);
+        two_sum(eih, pi1, sh, se); se += eil + pi2; fast_two_sum(sh, se, eih, eil);
+        mx = fmaxf(mx, fmaxf(fabsf(dn[0]), fabsf(dn[1])));
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        oh[2 * e + q] = nh[q]; ol[2 * e + q] = nl[q]; oL[2 * e + q] = Ln[q];
+        ob[2 * e + q] = bf_bits(dn[q]);
+      }
+    }
+    const int64_t idx = (int64_t)i * ld + ti.m0 + r0;
+    st4(Ahn + idx, make_float4(oh[0], oh[1], oh[2], oh[3]));
+    st4(Aln + idx, make_float4(ol[0], ol[1], ol[2], ol[3]));
+    st4(L + idx, make_float4(oL[0], oL[1], oL[2], oL[3]));
+    *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+    warp_sum_ff(r2, a2, erh, erl);
+    float z0 = 0.f, z1 = 0.f;
+    warp_sum_ff(z0, z1, eih, eil);
+    if (lane == 0) {
+      const int ntm = P->ntm;
+      P->part[((int64_t)0 * ntm + ti.tm) * ld + i] = r2;
+      P->part[((int64_t)1 * ntm + ti.tm) * ld + i] = a2;
+      P->part[((int64_t)2 * ntm + ti.tm) * ld + i] = erh;
+      P->part[((int64_t)3 * ntm + ti.tm) * ld + i] = erl;
+      P->part[((int64_t)4 * ntm + ti.tm) * ld + i] = eih;
+      P->part[((int64_t)5 * ntm + ti.tm) * ld + i] = eil;
+    }
+  }
+}
+
 __device__ __forceinline__ void g_epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ bool g_epi_bar_and(bool v) {
   uint32_t r;
@@ -428,6 +822,8 @@ __device__ __forceinline__ bool g_epi_bar_and(bool v) {
   return r != 0;
 }
 
+// CPLX: every problem of the launch is complex (the group is of one kind).
+template <bool CPLX>
 __global__ void __launch_bounds__(G_NTHREADS, 1)
 k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, int ntiles,
              unsigned* timeout) {
@@ -463,7 +859,9 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
       const CUtensorMap* tB = (ti.cur == 1) ? &ti.P->tmB[0] : &ti.P->tmB[1];
       const uint32_t bytes = G_A_TILE + (uint32_t)ti.bn * G_BK * 2;
       const int nk = ti.S * ti.kbs;
-      const int kb_last = min(ti.kbs - 1, (ti.n0 + ti.bn - 1) / G_BK);
+      // a complex problem's column i is dominated by embedded K near 2i
+      const int kdiag = CPLX ? 2 * (ti.n0 + ti.bn) - 1 : ti.n0 + ti.bn - 1;
+      const int kb_last = min(ti.kbs - 1, kdiag / G_BK);
       for (int q = 0; q < nk; ++q, ++it) {
         const int s = it % G_STAGES;
         const uint32_t ph = (it / G_STAGES) & 1;
@@ -535,7 +933,17 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
         mx = 0.f;
       }
       g_epi_bar();
-      {
+      if constexpr (CPLX) {
+        // e and d_{k-1} are complex: (re, im) of the tile's columns, bn <= 128
+        const int i = ti.n0 + (et >> 1);
+        const bool v = (et < 2 * ti.bn) && (i < ti.P->n);
+        ms->e[et] = v ? ti.P->e_col[2 * ti.n0 + et] : 0.f;
+        ms->dprev[et] = v ? ti.P->dprev_col[2 * ti.n0 + et] : 0.f;
+        const int ic = ti.n0 + et;
+        const bool vc = (et < ti.bn) && (ic < ti.P->n);
+        ms->thh[et] = vc ? ti.P->th_hi[ic] : 0.f;
+        ms->thl[et] = vc ? ti.P->th_lo[ic] : 0.f;
+      } else {
         const int i = ti.n0 + et;
         const bool v = (et < ti.bn) && (i < ti.P->n);
         ms->e[et] = v ? ti.P->e_col[i] : 0.f;
@@ -560,7 +968,8 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
         all_ok = g_epi_bar_and(ok);
         if (c0 + G_XCH >= ti.bn && et == 0) mbar_arrive(&ms->acc_empty[b]);
         if (!all_ok) break;
-        g_epilogue_columns(ti, ms, Xs, ew, lane, c0, mx);
+        if constexpr (CPLX) gc_epilogue_columns(ti, ms, Xs, ew, lane, c0, mx);
+        else g_epilogue_columns(ti, ms, Xs, ew, lane, c0, mx);
       }
       if (!all_ok) break;
     }
@@ -582,6 +991,7 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
 __global__ void k_g_finalize(const GProb* __restrict__ probs, const int4* __restrict__ items) {
   const int4 it = items[blockIdx.x];
   const GProb* P = probs + it.x;
+  if (P->cplx) return;
   const IterState* st = P->st;
   const int n = P->n, ld = P->ld;
   const int k = st->k;
@@ -605,7 +1015,10 @@ __global__ void k_g_finalize(const GProb* __restrict__ probs, const int4* __rest
 // host launchers
 // ---------------------------------------------------------------------------
 cudaError_t g_set_attributes() {
-  return cudaFuncSetAttribute(k_g_gemm_epi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_g_gemm_epi<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_g_gemm_epi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               G_SMEM_BYTES);
 }
 cudaError_t launch_g_check_theta(const GProb* probs, int count, int* running, cudaStream_t s) {
@@ -625,7 +1038,7 @@ cudaError_t launch_g_ctrl(const GProb* probs, int count, int* running, cudaStrea
   return cudaGetLastError();
 }
 cudaError_t launch_g_gemm_epi(const GProb* probs, const int2* tiles, int ntiles, unsigned* timeout,
-                              cudaStream_t s) {
+                              bool cplx, cudaStream_t s) {
   static int nsm = 0;
   if (nsm == 0) {
     int dev = 0;
@@ -634,7 +1047,26 @@ cudaError_t launch_g_gemm_epi(const GProb* probs, const int2* tiles, int ntiles,
     if (e != cudaSuccess) return e;
   }
   const int grid = ntiles < nsm ? ntiles : nsm;
-  if (grid > 0) k_g_gemm_epi<<<grid, G_NTHREADS, G_SMEM_BYTES, s>>>(probs, tiles, ntiles, timeout);
+  if (grid > 0) {
+    if (cplx) k_g_gemm_epi<true><<<grid, G_NTHREADS, G_SMEM_BYTES, s>>>(probs, tiles, ntiles, timeout);
+    else k_g_gemm_epi<false><<<grid, G_NTHREADS, G_SMEM_BYTES, s>>>(probs, tiles, ntiles, timeout);
+  }
+  return cudaGetLastError();
+}
+cudaError_t launch_gc_prep(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {
+  if (nitems) k_gc_prep<<<nitems, dim3(16, 16), 0, s>>>(probs, items);
+  return cudaGetLastError();
+}
+cudaError_t launch_gc_iter0(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {
+  if (nitems) k_gc_iter0<<<nitems, 128, 0, s>>>(probs, items);
+  return cudaGetLastError();
+}
+cudaError_t launch_gc_ctrl(const GProb* probs, int count, int* running, cudaStream_t s) {
+  k_gc_ctrl<<<count, 256, 0, s>>>(probs, count, running);
+  return cudaGetLastError();
+}
+cudaError_t launch_gc_finalize(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {
+  if (nitems) k_gc_finalize<<<nitems, 128, 0, s>>>(probs, items);
   return cudaGetLastError();
 }
 cudaError_t launch_g_finalize(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {

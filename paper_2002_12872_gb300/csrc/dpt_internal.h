@@ -80,7 +80,10 @@ struct DomState {
 struct alignas(128) GProb {
   CUtensorMap tmA;          // Delta slices (row-major BF16, 3 slices side by side)
   CUtensorMap tmB[2];       // increment buffers dt[0], dt[1]
-  int n, ld, ntm, ntn, bn, pad0;
+  // n: problem size; nr: rows of the real product (n, or 2n for a complex problem,
+  // whose rows and K index interleave real and imaginary parts); ld: row pitch of
+  // every work column (a multiple of 128, >= nr); ntm: 128-row tiles over nr
+  int n, ld, ntm, ntn, bn, cplx, nr, pad0;
   float lam, lam_lo;
   double lam64;
   float* A_hi[2];
@@ -96,10 +99,10 @@ struct alignas(128) GProb {
   double* E;
   float* e_col;
   float* dprev_col;
-  float* part;
+  float* part;              // column partials [6][ntm][n]: |R|^2, |a|^2, diag (hi, lo) x (re, im)
   float* rowpart;
   IterState* st;
-  const double* delta_in;   // input Delta (device, column-major)
+  const double* delta_in;   // input Delta (device, column-major; interleaved if complex)
   int64_t ld_in;
   double* A_out;            // outputs (device)
   int64_t ld_a;
@@ -112,8 +115,12 @@ cudaError_t launch_g_prep(const GProb* probs, const int4* items, int nitems, cud
 cudaError_t launch_g_iter0(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
 cudaError_t launch_g_ctrl(const GProb* probs, int count, int* running, cudaStream_t s);
 cudaError_t launch_g_gemm_epi(const GProb* probs, const int2* tiles, int ntiles,
-                              unsigned* timeout, cudaStream_t s);
+                              unsigned* timeout, bool cplx, cudaStream_t s);
 cudaError_t launch_g_finalize(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
+cudaError_t launch_gc_prep(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
+cudaError_t launch_gc_iter0(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
+cudaError_t launch_gc_ctrl(const GProb* probs, int count, int* running, cudaStream_t s);
+cudaError_t launch_gc_finalize(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
 
 // Arguments of the tensor-core iteration kernel (mixed path, real).
 struct GemmEpiParams {

@@ -76,8 +76,8 @@ def lib() -> ctypes.CDLL:
         L.dpt_solve_dominant_noalloc.argtypes = [i64, P, P, P, P, i64, dbl, dbl,
                                                  ctypes.c_int32, P, P, ctypes.POINTER(Info), P]
         L.dpt_solve_dominant_noalloc.restype = ctypes.c_int
-        L.dpt_solve_batched.argtypes = [i64, P, P, P, P, P, ctypes.POINTER(Options), P, P, P,
-                                        P, P]
+        L.dpt_solve_batched.argtypes = [i64, ctypes.c_int, P, P, P, P, P,
+                                        ctypes.POINTER(Options), P, P, P, P, P]
         L.dpt_solve_batched.restype = ctypes.c_int
         L.dpt_release_workspace.argtypes = []
         L.dpt_release_workspace.restype = None
@@ -215,35 +215,39 @@ def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
 def solve_batched(thetas, deltas, lams, *, tol=1e-12, max_iter=200, graph_iters=None,
                   max_slices=None, slice_tol=None, profile=False, A_outs=None, E_outs=None,
                   stream=None, check=True):
-    """Grouped solve of independent real problems (dpt_solve_batched).
+    """Grouped solve of independent problems (dpt_solve_batched), all real or all
+    complex (complex128 deltas; theta and lambda real).
 
     thetas / deltas: sequences of CUDA tensors (deltas column-major, e.g. from
     colmajor_tensor).  Returns (As, Es, infos)."""
     import torch
     count = len(thetas)
+    cplx = deltas[0].is_complex()
     ns = (ctypes.c_int64 * count)(*[int(t.shape[0]) for t in thetas])
     th = (ctypes.c_void_p * count)(*[t.data_ptr() for t in thetas])
     ds, ldd = [], []
     keep = []
     for d in deltas:
-        ptr, ld, k = _colmajor(d, False)
+        ptr, ld, k = _colmajor(d, cplx)
         ds.append(ptr); ldd.append(ld); keep.append(k)
     dp = (ctypes.c_void_p * count)(*ds)
     lddp = (ctypes.c_int64 * count)(*ldd)
     lam = (ctypes.c_double * count)(*[float(x) for x in lams])
+    dt = torch.complex128 if cplx else torch.float64
     if A_outs is None:
-        A_outs = [torch.empty((int(t.shape[0]),) * 2, dtype=torch.float64, device=t.device).t()
+        A_outs = [torch.empty((int(t.shape[0]),) * 2, dtype=dt, device=t.device).t()
                   for t in thetas]
     if E_outs is None:
-        E_outs = [torch.empty_like(t, dtype=torch.float64) for t in thetas]
+        E_outs = [torch.empty(t.shape, dtype=dt, device=t.device) for t in thetas]
     ap = (ctypes.c_void_p * count)(*[a.data_ptr() for a in A_outs])
     lda = (ctypes.c_int64 * count)(*[a.stride(1) for a in A_outs])
     ep = (ctypes.c_void_p * count)(*[e.data_ptr() for e in E_outs])
     infos = (Info * count)()
     o = options(tol=tol, max_iter=max_iter, prec="mixed", graph_iters=graph_iters,
                 max_slices=max_slices, slice_tol=slice_tol, profile=int(bool(profile)))
-    st = lib().dpt_solve_batched(count, ns, th, dp, lddp, lam, ctypes.byref(o), ap, lda, ep,
-                                 infos, _stream_of(thetas[0], stream))
+    st = lib().dpt_solve_batched(count, C128 if cplx else R64, ns, th, dp, lddp, lam,
+                                 ctypes.byref(o), ap, lda, ep, infos,
+                                 _stream_of(thetas[0], stream))
     res = (A_outs, E_outs, [i.as_dict() for i in infos])
     if check and st != OK:
         err = RuntimeError(f"dpt_solve_batched: {status_string(st)}")
