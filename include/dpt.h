@@ -61,7 +61,10 @@ typedef enum {
   DPT_ERR_CUDA = -6,          /* a CUDA runtime call failed */
   DPT_ERR_TIMEOUT = -7,       /* a bounded device-side wait expired */
   DPT_ERR_UNSUPPORTED = -8,   /* option combination not implemented */
-  DPT_ERR_TOO_LARGE = -9      /* problem larger than a fixed-size entry point accepts */
+  DPT_ERR_TOO_LARGE = -9,     /* problem larger than a fixed-size entry point or a
+                                 server's memory budget accepts */
+  DPT_ERR_BUSY = -10,         /* server queue full: the request was not taken */
+  DPT_ERR_CANCELLED = -11     /* server request cancelled before it finished */
 } dpt_status;
 
 typedef enum {
@@ -213,6 +216,95 @@ DPT_API dpt_status dpt_solve_dominant_noalloc(int64_t n, const double* theta,
                                               const float* vals, int64_t nstar, double lambda,
                                               double tol, int32_t max_iter, double* z_out,
                                               double* E_out, dpt_info* info, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Solve server: continuous batching of independent full-spectrum problems.
+ *
+ * A server owns one worker thread, one CUDA stream and a fixed budget of device
+ * memory on the device current at dpt_server_create.  Requests (dpt_problem)
+ * wait in a FIFO queue and are admitted while a slot is free and the budget holds
+ * their working set; the worker then advances every admitted problem by one map
+ * application per step (one grouped tcgen05 product launch over all of them, the
+ * machinery of dpt_solve_batched), and retires each problem at its own
+ * convergence (each problem is its own fixed-point iteration, Sec. II.B), writing
+ * its outputs and freeing its memory for the queue.  A problem's arithmetic does
+ * not depend on which other problems share its steps: its results are the same
+ * alone and in any mix.  Mixed precision (DPT_PREC_MIXED_BF16) only.
+ * ------------------------------------------------------------------------ */
+typedef struct dpt_server dpt_server;
+typedef int64_t dpt_req;
+
+typedef struct {
+  uint64_t hbm_budget;    /* device bytes for request working sets; 0 = 80% of the
+                             free device memory at creation.  Allocated once, at
+                             creation; admission never allocates. */
+  int32_t max_active;     /* problems on the GPU at once (default 64, at most 4096) */
+  int32_t max_queue;      /* queued requests beyond which dpt_submit returns
+                             DPT_ERR_BUSY (default 65536) */
+  dpt_options opt;        /* tol, max_iter, max_slices, slice_tol for requests that
+                             do not set their own; prec must be MIXED_BF16 */
+} dpt_server_cfg;
+
+typedef struct {
+  int64_t n;              /* size, 1 <= n <= 65536 */
+  int32_t dtype;          /* dpt_dtype */
+  const double* theta;    /* n distinct finite doubles, host or device */
+  const void* delta;      /* n x n column-major, leading dimension ld_delta, host or device */
+  int64_t ld_delta;
+  double lambda;          /* real perturbation strength */
+  double tol;             /* <= 0: the server's */
+  int32_t max_iter;       /* <= 0: the server's */
+  void* A_out;            /* n x n column-major output (ld_a), host or device */
+  int64_t ld_a;
+  void* E_out;            /* n outputs, host or device */
+} dpt_problem;
+
+typedef struct {
+  int64_t submitted, completed, failed, cancelled, rejected;
+  int32_t queued, active;        /* right now */
+  int32_t max_queued;            /* largest queue length seen */
+  int64_t steps;                 /* grouped product steps run */
+  uint64_t hbm_budget, hbm_in_use, hbm_peak;
+  double p50_s, p99_s;           /* submit-to-result latency of completed requests */
+} dpt_server_stats;
+
+/* Fill *cfg with the defaults listed above. */
+DPT_API void dpt_server_cfg_default(dpt_server_cfg* cfg);
+
+/* Create a server on the current device (cfg NULL = defaults).  DPT_ERR_NOMEM
+ * when the budget cannot be allocated; DPT_ERR_ARG for invalid settings. */
+DPT_API dpt_status dpt_server_create(const dpt_server_cfg* cfg, dpt_server** out);
+
+/* Queue one problem.  The descriptor is copied; the buffers it points to are not:
+ * theta and delta must stay valid and unchanged, and A_out / E_out valid, until
+ * dpt_poll or dpt_wait reports a final status.  Checks the arguments it can on the
+ * host (DPT_ERR_ARG), rejects a problem whose working set exceeds the whole budget
+ * (DPT_ERR_TOO_LARGE) and refuses when the queue is full (DPT_ERR_BUSY); nothing is
+ * queued then.  Non-finite Delta entries and equal theta values are found on the
+ * GPU and end only that request (DPT_ERR_ARG / DPT_ERR_DEGENERATE).  *id
+ * identifies the request.  Thread-safe. */
+DPT_API dpt_status dpt_submit(dpt_server* srv, const dpt_problem* prob, dpt_req* id);
+
+/* Non-blocking: DPT_PENDING while the request is queued or running, else its final
+ * status, with *info (optional) filled: iters, slice_gemms, residual, status, and
+ * seconds = submit-to-result latency.  Once a final status has been returned the
+ * request is forgotten and its id becomes invalid (DPT_ERR_ARG).  Thread-safe. */
+DPT_API dpt_status dpt_poll(dpt_server* srv, dpt_req id, dpt_info* info);
+
+/* As dpt_poll, but waits up to timeout_s seconds (< 0: no limit) for a final status. */
+DPT_API dpt_status dpt_wait(dpt_server* srv, dpt_req id, double timeout_s, dpt_info* info);
+
+/* Cancel a queued or running request: it ends with DPT_ERR_CANCELLED (outputs
+ * unspecified) at the worker's next step boundary, unless it finishes first.  DPT_OK when the cancel was
+ * recorded, DPT_ERR_ARG for an unknown or already finished id.  Thread-safe. */
+DPT_API dpt_status dpt_cancel(dpt_server* srv, dpt_req id);
+
+/* Counters and latency percentiles so far.  Thread-safe. */
+DPT_API dpt_status dpt_server_stats_get(dpt_server* srv, dpt_server_stats* stats);
+
+/* Stop the worker, end every unfinished request with DPT_ERR_CANCELLED, free the
+ * budget.  Requests not yet polled are forgotten. */
+DPT_API dpt_status dpt_server_destroy(dpt_server* srv);
 
 /* Free the scratch pool of the current device (no solve may be running). */
 DPT_API void dpt_release_workspace(void);

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/dpt.h"
+#include "dpt_host.h"
 #include "dpt_internal.h"
 
 namespace dpt {
@@ -28,27 +29,6 @@ using namespace dpt;
 // ---------------------------------------------------------------------------
 namespace {
 
-struct Fail {
-  dpt_status st;
-};
-
-#define CK(call)                                              \
-  do {                                                        \
-    cudaError_t e_ = (call);                                  \
-    if (e_ != cudaSuccess) throw Fail{DPT_ERR_CUDA};          \
-  } while (0)
-
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 constexpr size_t kPinnedBytes = 4096;   // pinned host scratch for state read-backs
 
@@ -108,24 +88,10 @@ void release(Block* b) {
   b->busy = false;
 }
 
-// Bump allocator over a scratch block (256-byte alignment).
-struct Carve {
-  char* base;
-  size_t off = 0;
-  template <class T>
-  T* take(size_t count) {
-    off = (size_t)round_up((int64_t)off, 256);
-    T* p = reinterpret_cast<T*>(base + off);
-    off += count * sizeof(T);
-    return p;
-  }
-};
-template <class F>
-size_t measure(F&& f) {
-  Carve c{nullptr};
-  f(c);
-  return (size_t)round_up((int64_t)c.off, 256) + 256;
-}
+
+}  // namespace
+
+namespace dpt {
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -167,9 +133,14 @@ dpt_status from_state(int s) {
     case ST_TIMEOUT: return DPT_ERR_TIMEOUT;
     case ST_BADINPUT: return DPT_ERR_ARG;
     case ST_DEGENERATE: return DPT_ERR_DEGENERATE;
+    case ST_CANCELLED: return DPT_ERR_CANCELLED;
     default: return DPT_ERR_CUDA;
   }
 }
+
+}  // namespace dpt
+
+namespace {
 
 // Validates theta on the host: finite, pairwise distinct (after the optional
 // Epstein-Nesbet shift).  Returns the shifted copy.
@@ -676,6 +647,10 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
 // ---------------------------------------------------------------------------
 // Grouped solve of many independent real problems (mixed path)
 // ---------------------------------------------------------------------------
+}  // namespace
+
+namespace dpt {
+
 // Tile width for a problem of size n: ceil(n / wmax) column tiles, each the
 // smallest multiple of 32 covering its share (wmax = 256 real, 128 complex).
 int group_tile_n(int n, int wmax) {
@@ -684,15 +659,6 @@ int group_tile_n(int n, int wmax) {
   return (w + 31) / 32 * 32;
 }
 
-struct GroupPlan {
-  std::vector<GProb> probs;
-  std::vector<int2> tiles;      // product kernel: (problem, tile)
-  std::vector<int4> prep_r;     // real: (problem, col block, row block) 32 x 32
-  std::vector<int4> prep_c;     // complex: (problem, col block, row block) 16 x 16 complex
-  std::vector<int4> blk_r;      // real: (problem, col tile, row tile) 128 x 128
-  std::vector<int4> blk_c;      // complex: (problem, col tile, embedded-row tile) 128 x 128
-  size_t bytes = 0;
-};
 
 // Lays out every problem's work arrays in one arena at `base` (nullptr: size only).
 void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const double* const* theta,
@@ -747,6 +713,10 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
   }
   g.bytes = (size_t)round_up((int64_t)c.off, 256) + 256;
 }
+
+}  // namespace dpt
+
+namespace {
 
 dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* const* theta,
                          const double* const* delta, const int64_t* ld_delta,
@@ -970,6 +940,8 @@ const char* dpt_status_string(dpt_status s) {
     case DPT_ERR_TIMEOUT: return "DPT_ERR_TIMEOUT";
     case DPT_ERR_UNSUPPORTED: return "DPT_ERR_UNSUPPORTED";
     case DPT_ERR_TOO_LARGE: return "DPT_ERR_TOO_LARGE";
+    case DPT_ERR_BUSY: return "DPT_ERR_BUSY";
+    case DPT_ERR_CANCELLED: return "DPT_ERR_CANCELLED";
   }
   return "DPT_UNKNOWN";
 }

@@ -1,0 +1,90 @@
+// Host-side helpers shared by the C-ABI translation units: error propagation,
+// pointer classification, workspace carving, TMA descriptor encoding and the
+// layout of a grouped (multi-problem) solve.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/dpt.h"
+#include "dpt_internal.h"
+
+namespace dpt {
+
+// Thrown inside the host runtime, caught at the C-ABI boundary.
+struct Fail {
+  dpt_status st;
+};
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) throw ::dpt::Fail{DPT_ERR_CUDA};   \
+  } while (0)
+
+inline bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Bump allocator over a scratch block (256-byte alignment); base == nullptr
+// only measures.
+struct Carve {
+  char* base;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (size_t)round_up((int64_t)off, 256);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+template <class F>
+size_t measure(F&& f) {
+  Carve c{nullptr};
+  f(c);
+  return (size_t)round_up((int64_t)c.off, 256) + 256;
+}
+
+// 2-D BF16 tensor map: inner extent `inner` (contiguous), outer extent `outer`,
+// row pitch `pitch_elems`, box 64 x box_rows, 128-byte swizzle.  Throws Fail.
+CUtensorMap make_tmap_bf16(const void* base, uint64_t inner, uint64_t outer,
+                           uint64_t pitch_elems, uint32_t box_rows);
+
+// dpt_status of a device-side ST_* code.
+dpt_status from_state(int s);
+
+// Column-tile width of the grouped product for a problem of n columns.
+int group_tile_n(int n, int wmax);
+
+// Layout of a grouped solve: per-problem tables and the flat work lists.
+struct GroupPlan {
+  std::vector<GProb> probs;
+  std::vector<int2> tiles;      // product kernel: (problem, tile)
+  std::vector<int4> prep_r;     // real: (problem, col block, row block) 32 x 32
+  std::vector<int4> prep_c;     // complex: (problem, col block, row block) 16 x 16 complex
+  std::vector<int4> blk_r;      // real: (problem, col tile, row tile) 128 x 128
+  std::vector<int4> blk_c;      // complex: (problem, col tile, embedded-row tile) 128 x 128
+  size_t bytes = 0;
+};
+
+// Lays out every problem's work arrays in one arena at `base` (nullptr: size
+// only) and fills g.  states_dev + p becomes problem p's IterState.
+void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const double* const* theta,
+                const double* const* delta, const int64_t* ld_delta, const double* lambda,
+                double* const* A_out, const int64_t* ld_a, double* const* E_out, char* base,
+                IterState* states_dev);
+
+}  // namespace dpt

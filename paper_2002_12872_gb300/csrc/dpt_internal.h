@@ -16,6 +16,8 @@ enum : int {
   ST_MAXITER = -3,
   ST_DIVERGED = -4,
   ST_TIMEOUT = -7,
+  ST_CANCELLED = -11,   // server request cancelled while on the GPU
+  ST_IDLE = 2,          // server slot without a problem
 };
 
 // Per-solve iteration state, resident in device memory.  The control kernels

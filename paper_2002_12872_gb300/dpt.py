@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libdpt.so")
 OK, PENDING = 0, 1
 STATUS = {0: "OK", 1: "PENDING", -1: "ERR_ARG", -2: "ERR_DEGENERATE", -3: "ERR_MAXITER",
           -4: "ERR_DIVERGED", -5: "ERR_NOMEM", -6: "ERR_CUDA", -7: "ERR_TIMEOUT",
-          -8: "ERR_UNSUPPORTED", -9: "ERR_TOO_LARGE"}
+          -8: "ERR_UNSUPPORTED", -9: "ERR_TOO_LARGE", -10: "ERR_BUSY", -11: "ERR_CANCELLED"}
 R64, C128 = 0, 1
 PREC = {"fp64": 0, "mixed": 1, "bf16": 1}
 
@@ -47,6 +47,33 @@ class Info(ctypes.Structure):
                 "code": self.status, "nstar": self.nstar, "seconds": self.seconds,
                 "launches": self.launches, "product_launches": self.product_launches,
                 "product_ms": self.product_ms}
+
+
+class ServerCfg(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_active", ctypes.c_int32),
+                ("max_queue", ctypes.c_int32), ("opt", Options)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("theta", ctypes.c_void_p), ("delta", ctypes.c_void_p),
+                ("ld_delta", ctypes.c_int64), ("lam", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("A_out", ctypes.c_void_p), ("ld_a", ctypes.c_int64),
+                ("E_out", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("queued", ctypes.c_int32),
+                ("active", ctypes.c_int32), ("max_queued", ctypes.c_int32),
+                ("steps", ctypes.c_int64), ("hbm_budget", ctypes.c_uint64),
+                ("hbm_in_use", ctypes.c_uint64), ("hbm_peak", ctypes.c_uint64),
+                ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -79,6 +106,22 @@ def lib() -> ctypes.CDLL:
         L.dpt_solve_batched.argtypes = [i64, ctypes.c_int, P, P, P, P, P,
                                         ctypes.POINTER(Options), P, P, P, P, P]
         L.dpt_solve_batched.restype = ctypes.c_int
+        L.dpt_server_cfg_default.argtypes = [ctypes.POINTER(ServerCfg)]
+        L.dpt_server_cfg_default.restype = None
+        L.dpt_server_create.argtypes = [ctypes.POINTER(ServerCfg), ctypes.POINTER(P)]
+        L.dpt_server_create.restype = ctypes.c_int
+        L.dpt_submit.argtypes = [P, ctypes.POINTER(Problem), ctypes.POINTER(i64)]
+        L.dpt_submit.restype = ctypes.c_int
+        L.dpt_poll.argtypes = [P, i64, ctypes.POINTER(Info)]
+        L.dpt_poll.restype = ctypes.c_int
+        L.dpt_wait.argtypes = [P, i64, dbl, ctypes.POINTER(Info)]
+        L.dpt_wait.restype = ctypes.c_int
+        L.dpt_cancel.argtypes = [P, i64]
+        L.dpt_cancel.restype = ctypes.c_int
+        L.dpt_server_stats_get.argtypes = [P, ctypes.POINTER(ServerStats)]
+        L.dpt_server_stats_get.restype = ctypes.c_int
+        L.dpt_server_destroy.argtypes = [P]
+        L.dpt_server_destroy.restype = ctypes.c_int
         L.dpt_release_workspace.argtypes = []
         L.dpt_release_workspace.restype = None
         _lib = L
@@ -307,3 +350,108 @@ def solve_dominant_noalloc(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, tol=
 
 def release_workspace():
     lib().dpt_release_workspace()
+
+
+# ---------------------------------------------------------------------------
+# solve server (continuous batching)
+# ---------------------------------------------------------------------------
+class ServerError(RuntimeError):
+    def __init__(self, where, code):
+        super().__init__(f"{where}: {status_string(code)}")
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+class Server:
+    """dpt_server_*: requests of mixed sizes admitted against a device-memory
+    budget, advanced together one map application per step, each retired at its
+    own convergence.  Buffers handed to submit() are kept referenced here until
+    the request's final status has been collected."""
+
+    def __init__(self, *, hbm_budget=0, max_active=64, max_queue=65536, tol=None,
+                 max_iter=None, max_slices=None, slice_tol=None):
+        cfg = ServerCfg()
+        lib().dpt_server_cfg_default(ctypes.byref(cfg))
+        cfg.hbm_budget = int(hbm_budget)
+        cfg.max_active = int(max_active)
+        cfg.max_queue = int(max_queue)
+        for k, v in (("tol", tol), ("max_iter", max_iter), ("max_slices", max_slices),
+                     ("slice_tol", slice_tol)):
+            if v is not None:
+                setattr(cfg.opt, k, v)
+        h = ctypes.c_void_p()
+        st = lib().dpt_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise ServerError("dpt_server_create", st)
+        self._h = h
+        self._keep = {}
+
+    def submit(self, theta, delta, lam, *, tol=0.0, max_iter=0, A_out=None, E_out=None):
+        """Queue one problem; returns its request id.  Raises ServerError when the
+        request is refused (ERR_ARG, ERR_TOO_LARGE, ERR_BUSY)."""
+        cplx = _iscomplex(delta)
+        n = int(theta.shape[0])
+        th_ptr, th_keep = _vec_ptr(theta, "float64")
+        d_ptr, ldd, d_keep = _colmajor(delta, cplx)
+        A = _empty_colmajor(n, delta, cplx) if A_out is None else A_out
+        E = _empty_vec(n, delta, cplx) if E_out is None else E_out
+        lda = A.stride(1) if _is_torch(A) else A.strides[1] // A.itemsize
+        p = Problem(n=n, dtype=C128 if cplx else R64, theta=th_ptr, delta=d_ptr, ld_delta=ldd,
+                    lam=float(lam), tol=float(tol), max_iter=int(max_iter), A_out=_ptr(A),
+                    ld_a=lda, E_out=_ptr(E))
+        rid = ctypes.c_int64()
+        st = lib().dpt_submit(self._h, ctypes.byref(p), ctypes.byref(rid))
+        if st != OK:
+            raise ServerError("dpt_submit", st)
+        self._keep[rid.value] = (th_keep, d_keep, A, E)
+        return rid.value
+
+    def _final(self, rid, st, info):
+        A, E = self._keep.pop(rid, (None, None, None, None))[2:]
+        return A, E, info.as_dict()
+
+    def poll(self, rid):
+        """None while pending, else (A, E, info); info['status'] is the outcome."""
+        info = Info()
+        st = lib().dpt_poll(self._h, int(rid), ctypes.byref(info))
+        if st == PENDING:
+            return None
+        if st == -1 and rid not in self._keep:
+            raise ServerError("dpt_poll", st)
+        return self._final(rid, st, info)
+
+    def wait(self, rid, timeout=-1.0):
+        """(A, E, info) once finished; None if the timeout expired first."""
+        info = Info()
+        st = lib().dpt_wait(self._h, int(rid), float(timeout), ctypes.byref(info))
+        if st == PENDING:
+            return None
+        if st == -1 and rid not in self._keep:
+            raise ServerError("dpt_wait", st)
+        return self._final(rid, st, info)
+
+    def cancel(self, rid):
+        return STATUS.get(lib().dpt_cancel(self._h, int(rid)))
+
+    def stats(self):
+        s = ServerStats()
+        lib().dpt_server_stats_get(self._h, ctypes.byref(s))
+        return s.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().dpt_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
