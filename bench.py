@@ -48,8 +48,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the dominant-CSR and batched workloads")
-    ap.add_argument("--only", default="all", choices=["all", "dominant", "batched"],
+                    help="skip the dominant-CSR, batched and served workloads")
+    ap.add_argument("--only", default="all", choices=["all", "dominant", "batched", "served"],
                     help="time one secondary workload alone and print its JSON object")
     return ap.parse_args()
 
@@ -300,6 +300,122 @@ def bench_batched(dpt, inputs, dev, steps=3, warmup=2):
             "all_converged": all(i["status"] == "OK" for i in infos)}
 
 
+def _run_stream(srv, stream, th, D, outs, wait_all=True):
+    """Open-loop submission at the scheduled arrival times; returns per-request
+    (info, lateness) and the wall time from the first arrival to the last result."""
+    arr, pool, lam = stream["arrival_s"], stream["pool"], stream["lam"]
+    ids, late = [], []
+    t0 = time.perf_counter()
+    for k in range(len(arr)):
+        while True:
+            now = time.perf_counter() - t0
+            if now >= arr[k]:
+                break
+            if arr[k] - now > 2e-3:
+                time.sleep(0.5e-3)
+        late.append(time.perf_counter() - t0 - arr[k])
+        A, E = outs(k)
+        ids.append(srv.submit(th[pool[k]], D[pool[k]], float(lam[k]), A_out=A, E_out=E))
+    infos = [srv.wait(i)[2] for i in ids]
+    wall = time.perf_counter() - t0
+    return infos, np.array(late), wall
+
+
+def bench_served(dpt, inputs, dev, rates=(250, 500, 1000, 2000), window_s=1.0, pool_size=48):
+    """Served complex Hermitian problems (n log-uniform in [64, 4096], theta_i = i,
+    Delta of variance 1/n, lambda U[0.02, 0.08]) arriving as Poisson streams; the
+    requests draw their matrices from a pool of 48 distinct problems at stratified
+    size quantiles (inputs resident in HBM; each request its own lambda and its
+    own outputs).  Per rate: goodput, p50/p99 submit-to-result latency, queue depth
+    and memory use of the solve server."""
+    import torch
+    pool = inputs.served_pool(pool_size)
+    th = [torch.tensor(p["theta"], device=dev) for p in pool]
+    D = [dpt.colmajor_tensor(p["delta"], dev) for p in pool]
+    ns = np.array([p["n"] for p in pool])
+    out = {"workload": "served complex Hermitian, n log-uniform [64, 4096] (pool of 48 at "
+                       "stratified quantiles), theta_i = i, Delta var 1/n, lambda U[0.02, 0.08], "
+                       "tol=1e-12, Poisson arrivals",
+           "budget_bytes": 96 << 30, "max_active": 256, "rates": {}}
+    srv = dpt.Server(hbm_budget=96 << 30, max_active=256)
+    try:
+        # warm-up: every pool entry once
+        warm = [srv.submit(th[q], D[q], 0.05) for q in range(pool_size)]
+        for i in warm:
+            srv.wait(i)
+        for rate in rates:
+            st = inputs.served_stream(int(rate * window_s), rate, pool_size, rep=int(rate))
+            cnt = len(st["pool"])
+            bufs = [(torch.empty((ns[q], ns[q]), dtype=torch.complex128, device=dev).t(),
+                     torch.empty(ns[q], dtype=torch.complex128, device=dev)) for q in st["pool"]]
+            torch.cuda.synchronize()
+            s0 = srv.stats()
+            infos, late, wall = _run_stream(srv, st, th, D, lambda k: bufs[k])
+            s1 = srv.stats()
+            lat = np.array([i["seconds"] for i in infos])
+            ok = sum(i["status"] == "OK" for i in infos)
+            flop = sum(8.0 * float(ns[q]) ** 3 * i["iters"] for q, i in zip(st["pool"], infos))
+            out["rates"][str(rate)] = {
+                "requests": cnt, "completed_ok": ok, "window_s": float(st["arrival_s"][-1]),
+                "goodput_per_s": ok / wall, "wall_s": wall,
+                "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                "max_ms": 1e3 * float(lat.max()),
+                "submit_lateness_max_ms": 1e3 * float(late.max()),
+                "max_queued": s1["max_queued"], "hbm_peak_gb": s1["hbm_peak"] / 1e9,
+                "steps": s1["steps"] - s0["steps"],
+                "iters_mean": float(np.mean([i["iters"] for i in infos])),
+                "algorithmic_tflops": flop / wall / 1e12}
+            if rate == rates[-1]:
+                # sampled requests equal their solo solves bit for bit
+                rng = np.random.Generator(np.random.PCG64(5))
+                same = []
+                for k in rng.choice(cnt, size=4, replace=False):
+                    q = st["pool"][k]
+                    A1, E1, _ = dpt.solve_full(th[q], D[q], float(st["lam"][k]))
+                    same.append(bool(torch.equal(A1, bufs[k][0]) and torch.equal(E1, bufs[k][1])))
+                out["sampled_equal_to_solo"] = same
+            del bufs
+        # end to end at the highest rate: pinned host inputs and outputs (requests on
+        # the same pool entry share their host output buffers)
+        rate = rates[-1]
+        th_h = [torch.tensor(p["theta"]).pin_memory() for p in pool]
+        D_h = [dpt.colmajor_tensor(p["delta"], pin=True) for p in pool]
+        ob = [(torch.empty((n, n), dtype=torch.complex128).pin_memory().t(),
+               torch.empty(n, dtype=torch.complex128).pin_memory()) for n in ns]
+        st = inputs.served_stream(int(rate * window_s / 2), rate, pool_size, rep=7)
+        infos, late, wall = _run_stream(srv, st, th_h, D_h, lambda k: ob[st["pool"][k]])
+        lat = np.array([i["seconds"] for i in infos])
+        nb = sum(16.0 * float(ns[q]) ** 2 for q in st["pool"])
+        out["e2e_host_buffers"] = {
+            "rate": rate, "requests": len(infos),
+            "goodput_per_s": sum(i["status"] == "OK" for i in infos) / wall,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "h2d_bytes_per_request": nb / len(infos), "d2h_bytes_per_request": nb / len(infos)}
+    finally:
+        srv.close()
+    # solo solves of a stratified sample of the pool: mixed vs plain FP64
+    samp = list(range(3, pool_size, 8))
+    t = {"mixed": [], "fp64": []}
+    for prec in ("mixed", "fp64"):
+        dpt.solve_full(th[samp[0]], D[samp[0]], 0.05, prec=prec)      # warm-up
+        for q in samp:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, info = dpt.solve_full(th[q], D[q], 0.05, prec=prec)
+            torch.cuda.synchronize()
+            t[prec].append(time.perf_counter() - t0)
+    out["solo_sample"] = {
+        "n": [int(ns[q]) for q in samp],
+        "mixed_s": t["mixed"], "fp64_s": t["fp64"],
+        "mixed_solves_per_s_est": 1.0 / float(np.mean(t["mixed"])),
+        "fp64_solves_per_s_est": 1.0 / float(np.mean(t["fp64"])),
+        "note": "one solo solve per sampled pool entry (every 8th of 48, stratified); "
+                "the mean over the sample estimates the mean over the size law"}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -413,6 +529,7 @@ def run_ours(args, world, rank, local):
     if not args.no_extra:
         extra["dominant_csr"] = bench_dominant(dpt, inputs, dev, pk)
         extra["batched"] = bench_batched(dpt, inputs, dev)
+        extra["served"] = bench_served(dpt, inputs, dev)
 
     if rank != 0:
         return
@@ -459,8 +576,12 @@ def main():
         build.build()
         dev = torch.device("cuda", local)
         pk, _ = peaks()
-        fn = bench_dominant if args.only == "dominant" else bench_batched
-        out = fn(dpt, inputs, dev, pk) if args.only == "dominant" else fn(dpt, inputs, dev)
+        if args.only == "dominant":
+            out = bench_dominant(dpt, inputs, dev, pk)
+        elif args.only == "batched":
+            out = bench_batched(dpt, inputs, dev)
+        else:
+            out = bench_served(dpt, inputs, dev)
         if rank == 0:
             print(json.dumps({args.only: out}), flush=True)
         return

@@ -674,7 +674,7 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
     const int nr = cplx ? 2 * np : np;
     const int ld = (int)round_up(nr, 128);
     P.n = np; P.nr = nr; P.cplx = cplx; P.ld = ld; P.ntm = (nr + 127) / 128;
-    P.bn = group_tile_n(np, cplx ? 128 : 256);
+    P.bn = group_tile_n(np, 256);
     P.ntn = (np + P.bn - 1) / P.bn;
     P.lam = (float)lambda[p];
     P.lam_lo = (float)(lambda[p] - (double)P.lam);
@@ -700,8 +700,8 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
     for (int t = 0; t < P.ntm * P.ntn; ++t) g.tiles.push_back(make_int2(p, t));
     const int ntn128 = (np + 127) / 128;
     if (cplx) {
-      for (int by = 0; by < (np + 15) / 16; ++by)
-        for (int bx = 0; bx < (ld / 2 + 15) / 16; ++bx) g.prep_c.push_back(make_int4(p, bx, by, 0));
+      for (int by = 0; by < (np + 31) / 32; ++by)
+        for (int bx = 0; bx < ld / 64; ++bx) g.prep_c.push_back(make_int4(p, bx, by, 0));
       for (int tm = 0; tm < P.ntm; ++tm)
         for (int tn = 0; tn < ntn128; ++tn) g.blk_c.push_back(make_int4(p, tn, tm, 0));
     } else {
@@ -712,6 +712,17 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
     }
   }
   g.bytes = (size_t)round_up((int64_t)c.off, 256) + 256;
+  sort_tiles(g.tiles, g.probs.data());
+}
+
+// Largest tiles first (cost ~ K extent x tile width), problems kept contiguous
+// among equal costs.
+void sort_tiles(std::vector<int2>& tiles, const GProb* probs) {
+  std::stable_sort(tiles.begin(), tiles.end(), [probs](int2 a, int2 b) {
+    const GProb& A = probs[a.x];
+    const GProb& B = probs[b.x];
+    return (int64_t)A.ld * A.bn > (int64_t)B.ld * B.bn;
+  });
 }
 
 }  // namespace dpt
@@ -784,15 +795,14 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
       CK(cudaMemcpyAsync(blk, blks.data(), sizeof(int4) * blks.size(), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(flags, hflags, sizeof(hflags), cudaMemcpyHostToDevice, s));
     CK(g_set_attributes());
-    CK(launch_g_check_theta(probs, count, flags, s));
+    int max_n = 0;
+    for (int p = 0; p < count; ++p) max_n = std::max(max_n, (int)n[p]);
+    CK(launch_g_check_theta(probs, count, max_n, flags, s));
     CK(launch_g_prep(probs, prep, n_prep_r, s));
     CK(launch_gc_prep(probs, prep + n_prep_r, n_prep_c, s));
     CK(launch_g_iter0(probs, blk, n_blk_r, s));
     CK(launch_gc_iter0(probs, blk + n_blk_r, n_blk_c, s));
-    auto ctrl = [&]() {
-      if (!cplx) CK(launch_g_ctrl(probs, count, flags, s));
-      else CK(launch_gc_ctrl(probs, count, flags, s));
-    };
+    auto ctrl = [&]() { CK(launch_g_ctrl(probs, count, max_n, cplx != 0, flags, s)); };
     ctrl();
     Prof prof;
     prof.on = o.profile != 0;

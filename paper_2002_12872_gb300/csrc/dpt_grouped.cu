@@ -10,9 +10,11 @@
 // Sec. II.B; the arithmetic per problem is that of the single-problem mixed path,
 // see dpt_full_mixed.cu).
 //
-// Tile shape per problem (chosen on the host from n, the "autotuned" width):
-// M = 128 rows, N = the smallest multiple of 32 that covers n in ceil(n / 256)
-// column tiles, so small problems do not pay for 256-wide tiles.
+// Tile shape per problem (chosen on the host from n): M = 128 rows, N = the
+// smallest multiple of 32 that covers n in ceil(n / 256) column tiles, so small
+// problems do not pay for 256-wide tiles.  The host orders the tile list by cost
+// (K extent x width, largest first) so that the round-robin assignment to the
+// persistent CTAs stays balanced across problems of very different size.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -42,8 +44,8 @@ struct __align__(16) GSmem {
   uint64_t acc_full[2];
   uint64_t acc_empty[2];
   uint32_t tmem_base;
-  float e[G_BNMAX];
-  float dprev[G_BNMAX];
+  float e[2 * G_BNMAX];       // e_i of the tile's columns ((re, im) pairs if complex)
+  float dprev[2 * G_BNMAX];   // d_{k-1,i}, likewise
   float thh[G_BNMAX];
   float thl[G_BNMAX];
 };
@@ -62,26 +64,31 @@ __device__ __forceinline__ void g_fail(const GProb* P, int code, int* running) {
   if (atomicCAS(&P->st->status, ST_RUNNING, code) == ST_RUNNING) atomicSub(running, 1);
 }
 
-__global__ void k_g_check_theta(const GProb* __restrict__ probs, int count, int* running) {
+// Grid (problems, chunks of 128 indices i); thread i compares theta_i with every
+// theta_j, j > i, and the chunk's max |theta| goes to the state by atomicMax on
+// the bits of a non-negative double (which order like the values).
+__global__ void __launch_bounds__(128) k_g_check_theta(const GProb* __restrict__ probs,
+                                                       int count, int* running) {
   const int p = blockIdx.x;
   if (p >= count) return;
   const GProb* P = probs + p;
   const int n = P->n;
-  const double* th = P->theta;
+  const int i = blockIdx.y * 128 + threadIdx.x;
+  if (blockIdx.y * 128 >= n) return;
+  const double* __restrict__ th = P->theta;
   double amax = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  if (i < n) {
     const double ti = th[i];
     if (!finite_bits(ti)) g_fail(P, ST_BADINPUT, running);
-    else amax = fmax(amax, fabs(ti));
-    for (int j = i + 1; j < n; ++j)
-      if (th[j] == ti) { g_fail(P, ST_DEGENERATE, running); break; }
+    else amax = fabs(ti);
+    bool dup = false;
+    for (int j = i + 1; j < n; ++j) dup |= (th[j] == ti);
+    if (dup) g_fail(P, ST_DEGENERATE, running);
   }
-  // max |theta| for the residual scale
   for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  __shared__ double sm[4];
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = amax;
-  __syncthreads();
-  if (threadIdx.x == 0) P->st->theta_max = fmax(fmax(sm[0], sm[1]), fmax(sm[2], sm[3]));
+  if ((threadIdx.x & 31) == 0 && amax > 0.0)
+    atomicMax(reinterpret_cast<unsigned long long*>(&P->st->theta_max),
+              (unsigned long long)__double_as_longlong(amax));
 }
 
 // ---------------------------------------------------------------------------
@@ -228,73 +235,6 @@ __global__ void __launch_bounds__(128) k_g_iter0(const GProb* __restrict__ probs
   if (lane == 0 && mx > 0.f) atomicMax(&P->st->dmax_bits, __float_as_uint(mx));
 }
 
-// ---------------------------------------------------------------------------
-// Control: one block per problem.  Reduces the problem's tile partials, reads out
-// E of the assessed iterate, advances d and takes the problem's decision.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_g_ctrl(const GProb* __restrict__ probs, int count,
-                                                int* running) {
-  const int p = blockIdx.x;
-  if (p >= count) return;
-  const GProb* P = probs + p;
-  if (P->cplx) return;
-  IterState* st = P->st;
-  if (st->status != ST_RUNNING) return;
-  const int n = P->n, ld = P->ld, ntm = P->ntm;
-  const int ntn128 = (n + 127) / 128;
-  const bool first = (st->k == 0);
-  float rmax = 0.f, rowmax = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float r2 = 0.f, a2 = 0.f;
-    double ep = 0.0;
-    for (int t = 0; t < ntm; ++t) {
-      r2 += P->part[((int64_t)0 * ntm + t) * ld + i];
-      a2 += P->part[((int64_t)1 * ntm + t) * ld + i];
-      ep += (double)P->part[((int64_t)2 * ntm + t) * ld + i] +
-            (double)P->part[((int64_t)3 * ntm + t) * ld + i];
-    }
-    float rr = sqrtf(r2 / a2);
-    if (!(rr == rr) || isinf(rr)) rr = __int_as_float(0x7f800000);
-    rmax = fmaxf(rmax, rr);
-    const double dk = P->d[i];
-    P->E[i] = P->theta[i] + P->lam64 * dk;
-    P->dprev_col[i] = (float)dk;
-    P->e_col[i] = (float)ep;
-    P->d[i] = dk + ep;
-    if (first) {
-      float rs = 0.f;
-      for (int t = 0; t < ntn128; ++t) rs += P->rowpart[(int64_t)t * ld + i];
-      rowmax = fmaxf(rowmax, rs);
-    }
-  }
-  __shared__ float sm[2][8];
-  for (int o = 16; o > 0; o >>= 1) {
-    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    rowmax = fmaxf(rowmax, __shfl_xor_sync(0xffffffffu, rowmax, o));
-  }
-  if ((threadIdx.x & 31) == 0) { sm[0][threadIdx.x >> 5] = rmax; sm[1][threadIdx.x >> 5] = rowmax; }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
-    rmax = fmaxf(rmax, sm[0][q]);
-    rowmax = fmaxf(rowmax, sm[1][q]);
-  }
-  rmax = fmaxf(rmax, sm[0][0]);
-  rowmax = fmaxf(rowmax, sm[1][0]);
-  volatile IterState* vs = st;
-  if (first) vs->s = vs->theta_max + fabs(vs->lam) * (double)rowmax;
-  const float dmax = __uint_as_float(vs->dmax_bits);
-  vs->dmax_bits = 0;
-  if (!decide(vs, (double)rmax / vs->s)) {
-    atomicSub(running, 1);
-    return;
-  }
-  const int S = ((double)dmax < vs->slice_tol) ? 1 : vs->max_slices;
-  vs->slices = S;
-  vs->slice_gemms = vs->slice_gemms + S;
-}
-
-
 // ===========================================================================
 // Complex problems.  The product is the real GEMM of the interleaved embedding:
 // embedded row 2j carries [Re D_jk, -Im D_jk] and row 2j+1 [Im D_jk, Re D_jk] at
@@ -305,25 +245,28 @@ __global__ void __launch_bounds__(256) k_g_ctrl(const GProb* __restrict__ probs,
 // ===========================================================================
 
 // Delta (complex, column-major, interleaved doubles) -> three BF16 slices of the
-// embedding; theta -> float-float.  Work item: (problem, 16 complex columns, 16
-// complex rows); block 16 x 16.
-__global__ void k_gc_prep(const GProb* __restrict__ probs, const int4* __restrict__ items) {
+// embedding; theta -> float-float.  Work item: (problem, 32 complex columns, 32
+// complex rows); block 32 x 8.  Each embedded row pair (2j, 2j+1) gets the two
+// BF16 pairs (Re, -Im) and (Im, Re) of element (j, k) at columns (2k, 2k+1), one
+// 4-byte store per row and slice, so a warp writes 128 contiguous bytes.
+__global__ void __launch_bounds__(256) k_gc_prep(const GProb* __restrict__ probs,
+                                                 const int4* __restrict__ items) {
   const int4 it = items[blockIdx.x];
   const GProb* P = probs + it.x;
   if (!g_running(P)) return;
-  __shared__ double2 tile[16][17];
+  __shared__ double2 tile[32][33];
   const int n = P->n, ld = P->ld;
-  const int bx = it.y * 16, by = it.z * 16;      // complex column k, complex row j
-  const double2* delta = reinterpret_cast<const double2*>(P->delta_in);
+  const int bx = it.y * 32, by = it.z * 32;      // complex column k, complex row j
+  const double2* __restrict__ delta = reinterpret_cast<const double2*>(P->delta_in);
   const int64_t ld_in = P->ld_in;
-  {
-    const int j = by + threadIdx.x, k = bx + threadIdx.y;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int j = by + threadIdx.x, k = bx + r;
     double2 v = make_double2(0.0, 0.0);
     if (j < n && k < n) {
       v = delta[(int64_t)k * ld_in + j];
       if (!finite_bits(v.x) || !finite_bits(v.y)) atomicExch(&P->st->bad_input, 1u);
     }
-    tile[threadIdx.y][threadIdx.x] = v;    // tile[k - bx][j - by]
+    tile[r][threadIdx.x] = v;    // tile[k - bx][j - by]
   }
   if (bx == 0 && threadIdx.y == 0) {
     const int j = by + threadIdx.x;
@@ -335,21 +278,26 @@ __global__ void k_gc_prep(const GProb* __restrict__ probs, const int4* __restric
     }
   }
   __syncthreads();
-  const int j = by + threadIdx.y, k = bx + threadIdx.x;   // write complex row j, column k
-  if (j >= n || 2 * k >= ld) return;
-  const double2 v = (k < n) ? tile[threadIdx.x][threadIdx.y] : make_double2(0.0, 0.0);
-  // the four entries of the 2 x 2 real block of element (j, k)
-  double e4[4] = {v.x, -v.y, v.y, v.x};    // (2j,2k) (2j,2k+1) (2j+1,2k) (2j+1,2k+1)
   const int64_t cat_ld = P->cat_ld;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int r = 2 * j + (q >> 1), c = 2 * k + (q & 1);
-    float rh, rl;
-    split_double(e4[q], rh, rl);
+  const int k = bx + threadIdx.x;                 // complex column written by this thread
+  if (2 * k >= ld) return;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int j = by + r;
+    if (j >= n) break;
+    const double2 v = (k < n) ? tile[threadIdx.x][r] : make_double2(0.0, 0.0);
+    float rh[2], rl[2], ih[2], il[2];
+    split_double(v.x, rh[0], rl[0]);
+    split_double(v.y, ih[0], il[0]);
+    __nv_bfloat16* row0 = P->Dcat + (int64_t)(2 * j) * cat_ld + 2 * k;
+    __nv_bfloat16* row1 = row0 + cat_ld;
     for (int sl = 0; sl < G_NSLICE; ++sl) {
-      const __nv_bfloat16 b = __float2bfloat16_rn(rh);
-      P->Dcat[(int64_t)r * cat_ld + (int64_t)sl * ld + c] = b;
-      two_sum(rh - __bfloat162float(b), rl, rh, rl);
+      const __nv_bfloat16 br = __float2bfloat16_rn(rh[0]);
+      const __nv_bfloat16 bi = __float2bfloat16_rn(ih[0]);
+      // -Im rounds to -bf16(Im): the slices of -Im are the negated slices of Im
+      *reinterpret_cast<__nv_bfloat162*>(row0 + (int64_t)sl * ld) = __halves2bfloat162(br, __hneg(bi));
+      *reinterpret_cast<__nv_bfloat162*>(row1 + (int64_t)sl * ld) = __halves2bfloat162(bi, br);
+      two_sum(rh[0] - __bfloat162float(br), rl[0], rh[0], rl[0]);
+      two_sum(ih[0] - __bfloat162float(bi), il[0], ih[0], il[0]);
     }
   }
 }
@@ -478,63 +426,108 @@ __global__ void __launch_bounds__(128) k_gc_iter0(const GProb* __restrict__ prob
   if (lane == 0 && mx > 0.f) atomicMax(&P->st->dmax_bits, __float_as_uint(mx));
 }
 
-// Control for complex problems: as k_g_ctrl with complex d, E, e.
-__global__ void __launch_bounds__(256) k_gc_ctrl(const GProb* __restrict__ probs, int count,
-                                                 int* running) {
+// ---------------------------------------------------------------------------
+// Control.  Grid (problems, chunks of 64 columns); 4 threads per column sum every
+// 4th tile partial.  Per column: the residual estimate of the assessed iterate,
+// its eigenvalue read-out E = theta + lambda d (Sec. II.B), and d advanced by the
+// new diagonal increment.  The chunk maxima of the residual (and, at the first
+// control, of the row sums of |Delta|) reach the state by atomicMax; the last
+// chunk of a problem to finish takes the problem's decision.
+// ---------------------------------------------------------------------------
+template <bool CPLX>
+__global__ void __launch_bounds__(256) k_g_ctrl(const GProb* __restrict__ probs, int count,
+                                                int* running) {
   const int p = blockIdx.x;
   if (p >= count) return;
   const GProb* P = probs + p;
-  if (!P->cplx) return;
+  if ((P->cplx != 0) != CPLX) return;
   IterState* st = P->st;
   if (st->status != ST_RUNNING) return;
   const int n = P->n, ld = P->ld, ntm = P->ntm;
+  const int nchunk = (n + 63) / 64;
+  if ((int)blockIdx.y >= nchunk) return;
   const int ntn128 = (n + 127) / 128;
   const bool first = (st->k == 0);
-  float rmax = 0.f, rowmax = 0.f;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    float r2 = 0.f, a2 = 0.f;
+  __shared__ float sh[3][4][64];
+  __shared__ double she[2][4][64];
+  const int c = threadIdx.x & 63, g = threadIdx.x >> 6;
+  const int i = blockIdx.y * 64 + c;
+  {
+    float r2 = 0.f, a2 = 0.f, rs = 0.f;
     double er = 0.0, ei = 0.0;
-    for (int t = 0; t < ntm; ++t) {
-      r2 += P->part[((int64_t)0 * ntm + t) * ld + i];
-      a2 += P->part[((int64_t)1 * ntm + t) * ld + i];
-      er += (double)P->part[((int64_t)2 * ntm + t) * ld + i] + (double)P->part[((int64_t)3 * ntm + t) * ld + i];
-      ei += (double)P->part[((int64_t)4 * ntm + t) * ld + i] + (double)P->part[((int64_t)5 * ntm + t) * ld + i];
+    if (i < n) {
+      const float* __restrict__ part = P->part;
+      for (int t = g; t < ntm; t += 4) {
+        r2 += part[((int64_t)0 * ntm + t) * ld + i];
+        a2 += part[((int64_t)1 * ntm + t) * ld + i];
+        er += (double)part[((int64_t)2 * ntm + t) * ld + i] +
+              (double)part[((int64_t)3 * ntm + t) * ld + i];
+        if (CPLX)
+          ei += (double)part[((int64_t)4 * ntm + t) * ld + i] +
+                (double)part[((int64_t)5 * ntm + t) * ld + i];
+      }
+      if (first)
+        for (int t = g; t < ntn128; t += 4) rs += P->rowpart[(int64_t)t * ld + i];
     }
-    float rr = sqrtf(r2 / a2);
-    if (!(rr == rr) || isinf(rr)) rr = __int_as_float(0x7f800000);
-    rmax = fmaxf(rmax, rr);
-    const double dr = P->d[2 * i], di = P->d[2 * i + 1];
-    P->E[2 * i] = P->theta[i] + P->lam64 * dr;
-    P->E[2 * i + 1] = P->lam64 * di;
-    P->dprev_col[2 * i] = (float)dr;
-    P->dprev_col[2 * i + 1] = (float)di;
-    P->e_col[2 * i] = (float)er;
-    P->e_col[2 * i + 1] = (float)ei;
-    P->d[2 * i] = dr + er;
-    P->d[2 * i + 1] = di + ei;
-    if (first) {
-      float rs = 0.f;
-      for (int t = 0; t < ntn128; ++t) rs += P->rowpart[(int64_t)t * ld + i];
-      rowmax = fmaxf(rowmax, rs);
-    }
+    sh[0][g][c] = r2; sh[1][g][c] = a2; sh[2][g][c] = rs;
+    she[0][g][c] = er; she[1][g][c] = ei;
   }
-  __shared__ float sm[2][8];
-  for (int o = 16; o > 0; o >>= 1) {
-    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-    rowmax = fmaxf(rowmax, __shfl_xor_sync(0xffffffffu, rowmax, o));
-  }
-  if ((threadIdx.x & 31) == 0) { sm[0][threadIdx.x >> 5] = rmax; sm[1][threadIdx.x >> 5] = rowmax; }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
-    rmax = fmaxf(rmax, sm[0][q]);
-    rowmax = fmaxf(rowmax, sm[1][q]);
+  float rr = 0.f, rsum = 0.f;
+  if (g == 0 && i < n) {
+    const float r2 = ((sh[0][0][c] + sh[0][1][c]) + sh[0][2][c]) + sh[0][3][c];
+    const float a2 = ((sh[1][0][c] + sh[1][1][c]) + sh[1][2][c]) + sh[1][3][c];
+    const double er = ((she[0][0][c] + she[0][1][c]) + she[0][2][c]) + she[0][3][c];
+    rr = sqrtf(r2 / a2);
+    if (!(rr == rr) || isinf(rr)) rr = __int_as_float(0x7f800000);
+    if (first) rsum = ((sh[2][0][c] + sh[2][1][c]) + sh[2][2][c]) + sh[2][3][c];
+    if (CPLX) {
+      const double ei = ((she[1][0][c] + she[1][1][c]) + she[1][2][c]) + she[1][3][c];
+      const double dr = P->d[2 * i], di = P->d[2 * i + 1];
+      P->E[2 * i] = P->theta[i] + P->lam64 * dr;
+      P->E[2 * i + 1] = P->lam64 * di;
+      P->dprev_col[2 * i] = (float)dr;
+      P->dprev_col[2 * i + 1] = (float)di;
+      P->e_col[2 * i] = (float)er;
+      P->e_col[2 * i + 1] = (float)ei;
+      P->d[2 * i] = dr + er;
+      P->d[2 * i + 1] = di + ei;
+    } else {
+      const double dk = P->d[i];
+      P->E[i] = P->theta[i] + P->lam64 * dk;
+      P->dprev_col[i] = (float)dk;
+      P->e_col[i] = (float)er;
+      P->d[i] = dk + er;
+    }
   }
+  float m = rr, mr = rsum;
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+  }
+  __shared__ float wm[2][8];
+  __shared__ bool last;
+  if ((threadIdx.x & 31) == 0) { wm[0][threadIdx.x >> 5] = m; wm[1][threadIdx.x >> 5] = mr; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float bm = 0.f, br = 0.f;
+    for (int q = 0; q < 8; ++q) { bm = fmaxf(bm, wm[0][q]); br = fmaxf(br, wm[1][q]); }
+    atomicMax(&st->rho_bits, __float_as_uint(bm));
+    if (first) atomicMax(&st->row_bits, __float_as_uint(br));
+    __threadfence();
+    last = (atomicAdd(&st->blocks_done, 1u) == (unsigned)nchunk - 1u);
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
   volatile IterState* vs = st;
-  if (first) vs->s = vs->theta_max + fabs(vs->lam) * (double)rowmax;
+  if (first) vs->s = vs->theta_max + fabs(vs->lam) * (double)__uint_as_float(vs->row_bits);
+  const double rho = (double)__uint_as_float(vs->rho_bits) / vs->s;
+  vs->blocks_done = 0;
+  vs->rho_bits = 0;
   const float dmax = __uint_as_float(vs->dmax_bits);
   vs->dmax_bits = 0;
-  if (!decide(vs, (double)rmax / vs->s)) {
+  if (!decide(vs, rho)) {
     atomicSub(running, 1);
     return;
   }
@@ -543,8 +536,10 @@ __global__ void __launch_bounds__(256) k_gc_ctrl(const GProb* __restrict__ probs
   vs->slice_gemms = vs->slice_gemms + S;
 }
 
-// Output of complex problems (interleaved FP64).
-__global__ void k_gc_finalize(const GProb* __restrict__ probs, const int4* __restrict__ items) {
+// Output of complex problems (interleaved FP64): thread r owns embedded row r of
+// a 128-column tile; the loads of eight columns are issued before their stores.
+__global__ void __launch_bounds__(128) k_gc_finalize(const GProb* __restrict__ probs,
+                                                     const int4* __restrict__ items) {
   const int4 it = items[blockIdx.x];
   const GProb* P = probs + it.x;
   if (!P->cplx) return;
@@ -552,18 +547,30 @@ __global__ void k_gc_finalize(const GProb* __restrict__ probs, const int4* __res
   const int n = P->n, ld = P->ld;
   const int k = st->k;
   const bool c1 = st->cur != 0;
-  const float* hi = c1 ? P->A_hi[1] : P->A_hi[0];
-  const float* lo = c1 ? P->A_lo[1] : P->A_lo[0];
+  const float* __restrict__ hi = c1 ? P->A_hi[1] : P->A_hi[0];
+  const float* __restrict__ lo = c1 ? P->A_lo[1] : P->A_lo[0];
+  double* __restrict__ out = P->A_out;
+  const int64_t lda2 = 2 * P->ld_a;
   const int r = it.z * 128 + threadIdx.x;       // embedded row
   const int j = r >> 1;
   if (j >= n) return;
-  for (int c = 0; c < 128; ++c) {
-    const int i = it.y * 128 + c;
-    if (i >= n) break;
-    double v;
-    if (k == 0) v = (i == j && (r & 1) == 0) ? 1.0 : 0.0;
-    else v = f2d_bits(hi[(int64_t)i * ld + r]) + f2d_bits(lo[(int64_t)i * ld + r]);
-    P->A_out[2 * (int64_t)i * P->ld_a + r] = v;
+  const int i0 = it.y * 128, i1 = min(n, i0 + 128);
+  if (k == 0) {
+    for (int i = i0; i < i1; ++i) out[(int64_t)i * lda2 + r] = (i == j && (r & 1) == 0) ? 1.0 : 0.0;
+  } else {
+    int i = i0;
+    for (; i + 8 <= i1; i += 8) {
+      float h[8], l[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        h[u] = hi[(int64_t)(i + u) * ld + r];
+        l[u] = lo[(int64_t)(i + u) * ld + r];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) out[(int64_t)(i + u) * lda2 + r] = f2d_bits(h[u]) + f2d_bits(l[u]);
+    }
+    for (; i < i1; ++i)
+      out[(int64_t)i * lda2 + r] = f2d_bits(hi[(int64_t)i * ld + r]) + f2d_bits(lo[(int64_t)i * ld + r]);
   }
   if (it.y == 0) P->E_out[r] = P->E[r];
 }
@@ -738,8 +745,8 @@ __device__ __forceinline__ void gc_epilogue_columns(const GTileInfo& ti, GSmem* 
     if (i >= n) continue;
     const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * G_BM + r0);
     // complex e_i and d_{k-1,i} are stored as (re, im) in the parameter arrays
-    const float er = ms->e[2 * (cl & 127)], ei = ms->e[2 * (cl & 127) + 1];
-    const float dr = ms->dprev[2 * (cl & 127)], di = ms->dprev[2 * (cl & 127) + 1];
+    const float er = ms->e[2 * cl], ei = ms->e[2 * cl + 1];
+    const float dr = ms->dprev[2 * cl], di = ms->dprev[2 * cl + 1];
     const float thh = ms->thh[cl], thl = ms->thl[cl];
     float oh[4], ol[4], oL[4];
     uint32_t ob[4];
@@ -934,11 +941,15 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
       }
       g_epi_bar();
       if constexpr (CPLX) {
-        // e and d_{k-1} are complex: (re, im) of the tile's columns, bn <= 128
-        const int i = ti.n0 + (et >> 1);
-        const bool v = (et < 2 * ti.bn) && (i < ti.P->n);
-        ms->e[et] = v ? ti.P->e_col[2 * ti.n0 + et] : 0.f;
-        ms->dprev[et] = v ? ti.P->dprev_col[2 * ti.n0 + et] : 0.f;
+        // e and d_{k-1} are complex: (re, im) of the tile's columns
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int q = et + 256 * h;
+          const int i = ti.n0 + (q >> 1);
+          const bool v = (q < 2 * ti.bn) && (i < ti.P->n);
+          ms->e[q] = v ? ti.P->e_col[2 * ti.n0 + q] : 0.f;
+          ms->dprev[q] = v ? ti.P->dprev_col[2 * ti.n0 + q] : 0.f;
+        }
         const int ic = ti.n0 + et;
         const bool vc = (et < ti.bn) && (ic < ti.P->n);
         ms->thh[et] = vc ? ti.P->th_hi[ic] : 0.f;
@@ -986,9 +997,12 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
 }
 
 // ---------------------------------------------------------------------------
-// Output: A (float-float -> FP64) and E; work item (problem, 128-col tile, 128-row tile).
+// Output: A (float-float -> FP64) and E; work item (problem, 128-col tile, 128-row
+// tile), thread j owns row j; the loads of eight columns are issued before their
+// stores.
 // ---------------------------------------------------------------------------
-__global__ void k_g_finalize(const GProb* __restrict__ probs, const int4* __restrict__ items) {
+__global__ void __launch_bounds__(128) k_g_finalize(const GProb* __restrict__ probs,
+                                                    const int4* __restrict__ items) {
   const int4 it = items[blockIdx.x];
   const GProb* P = probs + it.x;
   if (P->cplx) return;
@@ -996,17 +1010,29 @@ __global__ void k_g_finalize(const GProb* __restrict__ probs, const int4* __rest
   const int n = P->n, ld = P->ld;
   const int k = st->k;
   const bool c1 = st->cur != 0;
-  const float* hi = c1 ? P->A_hi[1] : P->A_hi[0];
-  const float* lo = c1 ? P->A_lo[1] : P->A_lo[0];
+  const float* __restrict__ hi = c1 ? P->A_hi[1] : P->A_hi[0];
+  const float* __restrict__ lo = c1 ? P->A_lo[1] : P->A_lo[0];
+  double* __restrict__ out = P->A_out;
+  const int64_t lda = P->ld_a;
   const int j = it.z * 128 + threadIdx.x;
   if (j >= n) return;
-  for (int c = 0; c < 128; ++c) {
-    const int i = it.y * 128 + c;
-    if (i >= n) break;
-    double v;
-    if (k == 0) v = (i == j) ? 1.0 : 0.0;
-    else v = f2d_bits(hi[(int64_t)i * ld + j]) + f2d_bits(lo[(int64_t)i * ld + j]);
-    P->A_out[(int64_t)i * P->ld_a + j] = v;
+  const int i0 = it.y * 128, i1 = min(n, i0 + 128);
+  if (k == 0) {
+    for (int i = i0; i < i1; ++i) out[(int64_t)i * lda + j] = (i == j) ? 1.0 : 0.0;
+  } else {
+    int i = i0;
+    for (; i + 8 <= i1; i += 8) {
+      float h[8], l[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        h[u] = hi[(int64_t)(i + u) * ld + j];
+        l[u] = lo[(int64_t)(i + u) * ld + j];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) out[(int64_t)(i + u) * lda + j] = f2d_bits(h[u]) + f2d_bits(l[u]);
+    }
+    for (; i < i1; ++i)
+      out[(int64_t)i * lda + j] = f2d_bits(hi[(int64_t)i * ld + j]) + f2d_bits(lo[(int64_t)i * ld + j]);
   }
   if (it.y == 0) P->E_out[j] = P->E[j];
 }
@@ -1021,8 +1047,10 @@ cudaError_t g_set_attributes() {
   return cudaFuncSetAttribute(k_g_gemm_epi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               G_SMEM_BYTES);
 }
-cudaError_t launch_g_check_theta(const GProb* probs, int count, int* running, cudaStream_t s) {
-  k_g_check_theta<<<count, 128, 0, s>>>(probs, count, running);
+cudaError_t launch_g_check_theta(const GProb* probs, int count, int max_n, int* running,
+                                 cudaStream_t s) {
+  if (count > 0 && max_n > 0)
+    k_g_check_theta<<<dim3(count, (max_n + 127) / 128), 128, 0, s>>>(probs, count, running);
   return cudaGetLastError();
 }
 cudaError_t launch_g_prep(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {
@@ -1033,8 +1061,12 @@ cudaError_t launch_g_iter0(const GProb* probs, const int4* items, int nitems, cu
   if (nitems) k_g_iter0<<<nitems, 128, 0, s>>>(probs, items);
   return cudaGetLastError();
 }
-cudaError_t launch_g_ctrl(const GProb* probs, int count, int* running, cudaStream_t s) {
-  k_g_ctrl<<<count, 256, 0, s>>>(probs, count, running);
+cudaError_t launch_g_ctrl(const GProb* probs, int count, int max_n, bool cplx, int* running,
+                          cudaStream_t s) {
+  if (count <= 0 || max_n <= 0) return cudaGetLastError();
+  const dim3 grid(count, (max_n + 63) / 64);
+  if (cplx) k_g_ctrl<true><<<grid, 256, 0, s>>>(probs, count, running);
+  else k_g_ctrl<false><<<grid, 256, 0, s>>>(probs, count, running);
   return cudaGetLastError();
 }
 cudaError_t launch_g_gemm_epi(const GProb* probs, const int2* tiles, int ntiles, unsigned* timeout,
@@ -1054,15 +1086,11 @@ cudaError_t launch_g_gemm_epi(const GProb* probs, const int2* tiles, int ntiles,
   return cudaGetLastError();
 }
 cudaError_t launch_gc_prep(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {
-  if (nitems) k_gc_prep<<<nitems, dim3(16, 16), 0, s>>>(probs, items);
+  if (nitems) k_gc_prep<<<nitems, dim3(32, 8), 0, s>>>(probs, items);
   return cudaGetLastError();
 }
 cudaError_t launch_gc_iter0(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {
   if (nitems) k_gc_iter0<<<nitems, 128, 0, s>>>(probs, items);
-  return cudaGetLastError();
-}
-cudaError_t launch_gc_ctrl(const GProb* probs, int count, int* running, cudaStream_t s) {
-  k_gc_ctrl<<<count, 256, 0, s>>>(probs, count, running);
   return cudaGetLastError();
 }
 cudaError_t launch_gc_finalize(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {

@@ -87,4 +87,7 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
                 double* const* A_out, const int64_t* ld_a, double* const* E_out, char* base,
                 IterState* states_dev);
 
+// Orders a product tile list (problem, tile) by decreasing cost.
+void sort_tiles(std::vector<int2>& tiles, const GProb* probs);
+
 }  // namespace dpt

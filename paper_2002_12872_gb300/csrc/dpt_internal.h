@@ -112,16 +112,18 @@ struct alignas(128) GProb {
 };
 
 cudaError_t g_set_attributes();
-cudaError_t launch_g_check_theta(const GProb* probs, int count, int* running, cudaStream_t s);
+// max_n: the largest problem size among the first `count` table entries
+cudaError_t launch_g_check_theta(const GProb* probs, int count, int max_n, int* running,
+                                 cudaStream_t s);
 cudaError_t launch_g_prep(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
 cudaError_t launch_g_iter0(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
-cudaError_t launch_g_ctrl(const GProb* probs, int count, int* running, cudaStream_t s);
+cudaError_t launch_g_ctrl(const GProb* probs, int count, int max_n, bool cplx, int* running,
+                          cudaStream_t s);
 cudaError_t launch_g_gemm_epi(const GProb* probs, const int2* tiles, int ntiles,
                               unsigned* timeout, bool cplx, cudaStream_t s);
 cudaError_t launch_g_finalize(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
 cudaError_t launch_gc_prep(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
 cudaError_t launch_gc_iter0(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
-cudaError_t launch_gc_ctrl(const GProb* probs, int count, int* running, cudaStream_t s);
 cudaError_t launch_gc_finalize(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
 
 // Arguments of the tensor-core iteration kernel (mixed path, real).

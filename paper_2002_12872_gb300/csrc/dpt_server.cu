@@ -24,6 +24,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -211,15 +212,15 @@ void admit(dpt_server* S, Request* r) {
                                 cudaMemcpyHostToDevice, S->s));
   if (r->nblk) CK(cudaMemcpyAsync(r->blk, r->items_h.data() + nprep, sizeof(int4) * r->nblk,
                                   cudaMemcpyHostToDevice, S->s));
-  CK(launch_g_check_theta(Pd, 1, S->flags_dev, S->s));
+  CK(launch_g_check_theta(Pd, 1, (int)n, S->flags_dev, S->s));
   if (r->cplx) {
     CK(launch_gc_prep(Pd, prep_dev, nprep, S->s));
     CK(launch_gc_iter0(Pd, r->blk, r->nblk, S->s));
-    CK(launch_gc_ctrl(Pd, 1, S->flags_dev, S->s));
+    CK(launch_g_ctrl(Pd, 1, (int)n, true, S->flags_dev, S->s));
   } else {
     CK(launch_g_prep(Pd, prep_dev, nprep, S->s));
     CK(launch_g_iter0(Pd, r->blk, r->nblk, S->s));
-    CK(launch_g_ctrl(Pd, 1, S->flags_dev, S->s));
+    CK(launch_g_ctrl(Pd, 1, (int)n, false, S->flags_dev, S->s));
   }
 }
 
@@ -227,11 +228,15 @@ void upload_tiles(dpt_server* S) {
   std::vector<int2>* t = S->tiles_h;     // kept until the stream has synchronised
   t[0].clear();
   t[1].clear();
+  std::vector<GProb> tab(S->slots.size());
   for (size_t q = 0; q < S->slots.size(); ++q) {
     const Request* r = S->slots[q];
     if (!r) continue;
+    tab[q] = r->P;
     for (int i = 0; i < r->tiles; ++i) t[r->cplx].push_back(make_int2((int)q, i));
   }
+  sort_tiles(t[0], tab.data());
+  sort_tiles(t[1], tab.data());
   for (int k = 0; k < 2; ++k) {
     S->ntiles[k] = (int)t[k].size();
     if (t[k].empty()) continue;
@@ -331,14 +336,18 @@ void worker_loop(dpt_server* S) {
       if (hi == 0) continue;
       if (S->tiles_dirty) upload_tiles(S);
       bool kind[2] = {false, false};
+      int max_n[2] = {0, 0};
       for (int q = 0; q < hi; ++q)
-        if (S->slots[q]) kind[S->slots[q]->cplx] = true;
+        if (const Request* r = S->slots[q]) {
+          kind[r->cplx] = true;
+          max_n[r->cplx] = std::max(max_n[r->cplx], (int)r->p.n);
+        }
       for (int k = 0; k < 2; ++k)
         if (S->ntiles[k])
           CK(launch_g_gemm_epi(S->probs_dev, S->tiles_dev[k], S->ntiles[k],
                                (unsigned*)(S->flags_dev + 1), k == 1, S->s));
-      if (kind[0]) CK(launch_g_ctrl(S->probs_dev, hi, S->flags_dev, S->s));
-      if (kind[1]) CK(launch_gc_ctrl(S->probs_dev, hi, S->flags_dev, S->s));
+      if (kind[0]) CK(launch_g_ctrl(S->probs_dev, hi, max_n[0], false, S->flags_dev, S->s));
+      if (kind[1]) CK(launch_g_ctrl(S->probs_dev, hi, max_n[1], true, S->flags_dev, S->s));
       CK(cudaMemcpyAsync(S->states_host, S->states_dev, sizeof(IterState) * hi,
                          cudaMemcpyDeviceToHost, S->s));
       CK(cudaMemcpyAsync(S->flags_host, S->flags_dev, sizeof(int) * 2, cudaMemcpyDeviceToHost,

@@ -25,6 +25,10 @@ sparse perturbations, Sec. II.G-H, are synthetic, so these stand in for them):
                      Hermitian Delta with E|x|^2 = 1/n (real N(0, 1/n) diagonal,
                      off-diagonal real and imaginary parts N(0, 1/(2n))),
                      lam ~ U[0.02, 0.08]
+  served_pool /      the same requests drawn from a pool of distinct Hermitian
+  served_stream      problems at stratified quantiles of the log-uniform size law
+                     (each request its own lambda), so that long streams need not
+                     hold one matrix per request
 """
 from __future__ import annotations
 
@@ -154,3 +158,25 @@ def served_hermitian(count: int, rate: float = 2000.0, rep: int = 0, lo: int = 6
                     "delta": hermitian_gaussian(n, 1.0 / n, rng),
                     "lam": float(lams[p]), "tol": 1e-12})
     return out
+
+
+def served_pool(size: int = 48, rep: int = 0, lo: int = 64, hi: int = 4096) -> list:
+    """Distinct served problems at the `size` stratified quantiles of the
+    log-uniform size law on [lo, hi]: n_q = round(exp(ln lo + (q + 1/2) / size *
+    ln(hi / lo))), theta_i = i, Hermitian Delta of variance 1/n."""
+    rng = rng_for(5, 100 + rep)
+    out = []
+    for q in range(size):
+        n = int(round(np.exp(np.log(lo) + (q + 0.5) / size * np.log(hi / lo))))
+        out.append({"n": n, "theta": np.arange(n, dtype=np.float64),
+                    "delta": hermitian_gaussian(n, 1.0 / n, rng)})
+    return out
+
+
+def served_stream(count: int, rate: float, pool_size: int, rep: int = 0) -> dict:
+    """Poisson arrivals at `rate` per second (exponential gaps), the pool entry of
+    each request (uniform over the pool) and its lambda ~ U[0.02, 0.08]."""
+    rng = rng_for(5, 200 + rep)
+    return {"arrival_s": np.cumsum(rng.exponential(1.0 / rate, size=count)),
+            "pool": rng.integers(0, pool_size, size=count),
+            "lam": rng.uniform(0.02, 0.08, size=count)}
