@@ -706,7 +706,7 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
         for (int tn = 0; tn < ntn128; ++tn) g.blk_c.push_back(make_int4(p, tn, tm, 0));
     } else {
       for (int by = 0; by < (np + 31) / 32; ++by)
-        for (int bx = 0; bx < ld / 32; ++bx) g.prep_r.push_back(make_int4(p, bx, by, 0));
+        for (int bx = 0; bx < ld / 64; ++bx) g.prep_r.push_back(make_int4(p, bx, by, 0));
       for (int tm = 0; tm < P.ntm; ++tm)
         for (int tn = 0; tn < ntn128; ++tn) g.blk_r.push_back(make_int4(p, tn, tm, 0));
     }

@@ -93,6 +93,55 @@ __device__ __forceinline__ double f2d_bits(float f) {
   return __longlong_as_double((long long)(sign | (de << 52) | m));
 }
 
+// One 32-row x 64-column tile of the Delta -> BF16-slice conversion, block (32, 8).
+// Reads Delta (FP64, column-major, rows j contiguous) at rows [by, by+32) and
+// columns [bx, bx+64) into shared memory, then writes row j of each of the three
+// slices (row-major, pitch ld inside a row of cat_ld = 3 ld elements) as BF16
+// pairs: D1 = bf16(v), D2 = bf16(v - D1), D3 = bf16(v - D1 - D2), the remainders
+// carried exactly in float-float, so D1 + D2 + D3 = v to 2^-24 relative.  Columns
+// in [n, ld) are written as zeros; en != 0 zeroes the diagonal.  A non-finite
+// entry sets *bad.
+__device__ __forceinline__ void slice_tile_32x64(const double* __restrict__ delta, int64_t ld_in,
+                                                 int n, int ld, int en, int bx, int by,
+                                                 __nv_bfloat16* __restrict__ Dcat, int64_t cat_ld,
+                                                 unsigned* bad, double (*tile)[65]) {
+  const int x = threadIdx.x, y = threadIdx.y;
+  {
+    const int j = by + x;
+#pragma unroll
+    for (int r = y; r < 64; r += 8) {
+      const int k = bx + r;
+      double v = 0.0;
+      if (j < n && k < n) {
+        v = delta[(int64_t)k * ld_in + j];
+        if (!finite_bits(v)) atomicExch(bad, 1u);
+        if (en && j == k) v = 0.0;
+      }
+      tile[x][r] = v;      // tile[j - by][k - bx]
+    }
+  }
+  __syncthreads();
+  const int k0 = bx + 2 * x;
+  if (k0 >= ld) return;
+#pragma unroll
+  for (int r = y; r < 32; r += 8) {
+    const int j = by + r;
+    if (j >= n) break;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    if (k0 < n) split_double(tile[r][2 * x], h0, l0);
+    if (k0 + 1 < n) split_double(tile[r][2 * x + 1], h1, l1);
+    __nv_bfloat16* row = Dcat + (int64_t)j * cat_ld + k0;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      const __nv_bfloat16 b0 = __float2bfloat16_rn(h0);
+      const __nv_bfloat16 b1 = __float2bfloat16_rn(h1);
+      *reinterpret_cast<__nv_bfloat162*>(row + (int64_t)sl * ld) = __halves2bfloat162(b0, b1);
+      two_sum(h0 - __bfloat162float(b0), l0, h0, l0);
+      two_sum(h1 - __bfloat162float(b1), l1, h1, l1);
+    }
+  }
+}
+
 __device__ __forceinline__ float bf16_round(float x) {
   return __bfloat162float(__float2bfloat16_rn(x));
 }

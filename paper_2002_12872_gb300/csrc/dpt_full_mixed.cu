@@ -66,36 +66,13 @@ constexpr int SMEM_BYTES = SMEM_TILES + SMEM_X + 1024 + (int)sizeof(GemmSmemMisc
 // the BF16 slices D1 + D2 + D3 (row-major, concatenated along K), zeroing the
 // diagonal when the Epstein-Nesbet partition is used.
 // ---------------------------------------------------------------------------
-__global__ void k_prep_delta(const double* __restrict__ delta, int64_t ld_in, int n, int ld,
-                             int en, __nv_bfloat16* __restrict__ Dcat, IterState* st) {
-  __shared__ double tile[32][33];
-  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;  // bx: column k, by: row j of Delta
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int j = by + threadIdx.x, k = bx + r;
-    double v = 0.0;
-    if (j < n && k < n) {
-      v = delta[(int64_t)k * ld_in + j];
-      if (!finite_bits(v)) atomicExch(&st->bad_input, 1u);
-      if (en && j == k) v = 0.0;
-    }
-    tile[r][threadIdx.x] = v;   // tile[k - bx][j - by]
-  }
-  __syncthreads();
-  const int64_t cat_ld = (int64_t)NSLICE * ld;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int j = by + r, k = bx + threadIdx.x;   // write row j, column k (row-major)
-    if (j < n && k < ld) {
-      float rh = 0.f, rl = 0.f;
-      if (k < n) split_double(tile[threadIdx.x][r], rh, rl);
-      // BF16 slices: D1 = bf16(v), D2 = bf16(v - D1), D3 = bf16(v - D1 - D2)
-      // (remainders carried exactly in float-float); D1 + D2 + D3 = v to 2^-24
-      for (int s = 0; s < NSLICE; ++s) {
-        const __nv_bfloat16 b = __float2bfloat16_rn(rh);
-        Dcat[(int64_t)j * cat_ld + (int64_t)s * ld + k] = b;
-        two_sum(rh - __bfloat162float(b), rl, rh, rl);
-      }
-    }
-  }
+__global__ void __launch_bounds__(256) k_prep_delta(const double* __restrict__ delta,
+                                                    int64_t ld_in, int n, int ld, int en,
+                                                    __nv_bfloat16* __restrict__ Dcat,
+                                                    IterState* st) {
+  __shared__ double tile[32][65];
+  slice_tile_32x64(delta, ld_in, n, ld, en, blockIdx.x * 64, blockIdx.y * 32, Dcat,
+                   (int64_t)NSLICE * ld, &st->bad_input, tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -578,24 +555,37 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 // ---------------------------------------------------------------------------
 // Output: A (float-float -> FP64) and E of the returned iterate.
 // ---------------------------------------------------------------------------
-__global__ void k_finalize(int n, int ld, const float* __restrict__ Ahi0,
-                           const float* __restrict__ Alo0, const float* __restrict__ Ahi1,
-                           const float* __restrict__ Alo1, double* __restrict__ Aout,
-                           int64_t ld_a, const IterState* st) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y;
-  if (j >= n || i >= n) return;
+// Output: grid (128-row tiles, 128-column tiles); thread j owns row j of the tile
+// and issues the loads of eight columns before their stores.
+__global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __restrict__ Ahi0,
+                                                  const float* __restrict__ Alo0,
+                                                  const float* __restrict__ Ahi1,
+                                                  const float* __restrict__ Alo1,
+                                                  double* __restrict__ Aout, int64_t ld_a,
+                                                  const IterState* st) {
+  const int j = blockIdx.x * 128 + threadIdx.x;
+  if (j >= n) return;
+  const int i0 = blockIdx.y * 128, i1 = min(n, i0 + 128);
   const int k = st->k;
-  double v;
   if (k == 0) {
-    v = (i == j) ? 1.0 : 0.0;
-  } else {
-    const float* hi = (st->cur == 0) ? Ahi0 : Ahi1;
-    const float* lo = (st->cur == 0) ? Alo0 : Alo1;
-    const int64_t idx = (int64_t)i * ld + j;
-    v = f2d_bits(hi[idx]) + f2d_bits(lo[idx]);
+    for (int i = i0; i < i1; ++i) Aout[(int64_t)i * ld_a + j] = (i == j) ? 1.0 : 0.0;
+    return;
   }
-  Aout[(int64_t)i * ld_a + j] = v;
+  const float* __restrict__ hi = (st->cur == 0) ? Ahi0 : Ahi1;
+  const float* __restrict__ lo = (st->cur == 0) ? Alo0 : Alo1;
+  int i = i0;
+  for (; i + 8 <= i1; i += 8) {
+    float h[8], l[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      h[u] = hi[(int64_t)(i + u) * ld + j];
+      l[u] = lo[(int64_t)(i + u) * ld + j];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) Aout[(int64_t)(i + u) * ld_a + j] = f2d_bits(h[u]) + f2d_bits(l[u]);
+  }
+  for (; i < i1; ++i)
+    Aout[(int64_t)i * ld_a + j] = f2d_bits(hi[(int64_t)i * ld + j]) + f2d_bits(lo[(int64_t)i * ld + j]);
 }
 
 __global__ void k_theta_ff(int n, const double* __restrict__ th, float* __restrict__ hi,
@@ -615,7 +605,7 @@ int mixed_tile_n() { return BN; }
 
 cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en,
                               __nv_bfloat16* Dcat, IterState* st, cudaStream_t s) {
-  dim3 grid((ld + 31) / 32, (n + 31) / 32), block(32, 8);
+  dim3 grid(ld / 64, (n + 31) / 32), block(32, 8);     // ld is a multiple of 128
   k_prep_delta<<<grid, block, 0, s>>>(delta, ld_in, n, ld, en, Dcat, st);
   return cudaGetLastError();
 }
@@ -670,8 +660,8 @@ cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
 cudaError_t launch_finalize(int n, int ld, const float* Ahi0, const float* Alo0,
                             const float* Ahi1, const float* Alo1, double* Aout, int64_t ld_a,
                             const IterState* st, cudaStream_t s) {
-  dim3 grid((n + 255) / 256, n);
-  k_finalize<<<grid, 256, 0, s>>>(n, ld, Ahi0, Alo0, Ahi1, Alo1, Aout, ld_a, st);
+  dim3 grid((n + 127) / 128, (n + 127) / 128);
+  k_finalize<<<grid, 128, 0, s>>>(n, ld, Ahi0, Alo0, Ahi1, Alo1, Aout, ld_a, st);
   return cudaGetLastError();
 }
 

@@ -93,27 +93,17 @@ __global__ void __launch_bounds__(128) k_g_check_theta(const GProb* __restrict__
 
 // ---------------------------------------------------------------------------
 // Delta -> three BF16 slices (row-major) and theta -> float-float.
-// Work item: (problem, 32-column block, 32-row block).
+// Work item: (problem, 64-column block, 32-row block); block 32 x 8.
 // ---------------------------------------------------------------------------
-__global__ void k_g_prep(const GProb* __restrict__ probs, const int4* __restrict__ items) {
+__global__ void __launch_bounds__(256) k_g_prep(const GProb* __restrict__ probs,
+                                                const int4* __restrict__ items) {
   const int4 it = items[blockIdx.x];
   const GProb* P = probs + it.x;
   if (!g_running(P)) return;
-  __shared__ double tile[32][33];
+  __shared__ double tile[32][65];
   const int n = P->n, ld = P->ld;
-  const int bx = it.y * 32, by = it.z * 32;
-  const double* delta = P->delta_in;
-  const int64_t ld_in = P->ld_in;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int j = by + threadIdx.x, k = bx + r;
-    double v = 0.0;
-    if (j < n && k < n) {
-      v = delta[(int64_t)k * ld_in + j];
-      if (!finite_bits(v)) atomicExch(&P->st->bad_input, 1u);
-    }
-    tile[r][threadIdx.x] = v;
-  }
-  if (bx == 0 && threadIdx.y == 0) {   // theta split, rows by..by+31
+  const int by = it.z * 32;
+  if (it.y == 0 && threadIdx.y == 0) {   // theta split, rows by..by+31
     const int j = by + threadIdx.x;
     if (j < ld) {
       float h = 0.f, l = 0.f;
@@ -122,20 +112,8 @@ __global__ void k_g_prep(const GProb* __restrict__ probs, const int4* __restrict
       P->th_lo[j] = l;
     }
   }
-  __syncthreads();
-  const int64_t cat_ld = P->cat_ld;
-  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    const int j = by + r, k = bx + threadIdx.x;
-    if (j < n && k < ld) {
-      float rh = 0.f, rl = 0.f;
-      if (k < n) split_double(tile[threadIdx.x][r], rh, rl);
-      for (int s = 0; s < G_NSLICE; ++s) {
-        const __nv_bfloat16 b = __float2bfloat16_rn(rh);
-        P->Dcat[(int64_t)j * cat_ld + (int64_t)s * ld + k] = b;
-        two_sum(rh - __bfloat162float(b), rl, rh, rl);
-      }
-    }
-  }
+  slice_tile_32x64(P->delta_in, P->ld_in, n, ld, 0, it.y * 64, by, P->Dcat, P->cat_ld,
+                   &P->st->bad_input, tile);
 }
 
 // ---------------------------------------------------------------------------

@@ -73,8 +73,8 @@ int group_tile_n(int n, int wmax);
 struct GroupPlan {
   std::vector<GProb> probs;
   std::vector<int2> tiles;      // product kernel: (problem, tile)
-  std::vector<int4> prep_r;     // real: (problem, col block, row block) 32 x 32
-  std::vector<int4> prep_c;     // complex: (problem, col block, row block) 16 x 16 complex
+  std::vector<int4> prep_r;     // real: (problem, col block, row block) 64 x 32
+  std::vector<int4> prep_c;     // complex: (problem, col block, row block) 32 x 32 complex
   std::vector<int4> blk_r;      // real: (problem, col tile, row tile) 128 x 128
   std::vector<int4> blk_c;      // complex: (problem, col tile, embedded-row tile) 128 x 128
   size_t bytes = 0;
