@@ -49,8 +49,11 @@ def parse_args():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the dominant-CSR, batched and served workloads")
-    ap.add_argument("--only", default="all", choices=["all", "dominant", "batched", "served"],
+    ap.add_argument("--only", default="all",
+                    choices=["all", "dominant", "batched", "served", "served_pool"],
                     help="time one secondary workload alone and print its JSON object")
+    ap.add_argument("--pool-max-n", type=int, default=None,
+                    help="served_pool: keep pool entries with n up to this size")
     return ap.parse_args()
 
 
@@ -315,6 +318,44 @@ def bench_batched(dpt, inputs, dev, steps=3, warmup=2):
             "all_converged": all(i["status"] == "OK" for i in infos)}
 
 
+def bench_served_pool(dpt, inputs, dev, steps=3, warmup=2, max_n=None):
+    """The served problem mix (the 48-entry pool of complex Hermitian problems,
+    lambda = 0.05) as one grouped solve: the complex tcgen05 product's throughput
+    without the request loop.  max_n keeps only pool entries up to that size."""
+    import torch
+    pool = [p for p in inputs.served_pool(48) if max_n is None or p["n"] <= max_n]
+    th = [torch.tensor(p["theta"], device=dev) for p in pool]
+    D = [dpt.colmajor_tensor(p["delta"], dev) for p in pool]
+    lams = [0.05] * len(pool)
+    As = [torch.empty((p["n"], p["n"]), dtype=torch.complex128, device=dev).t() for p in pool]
+    Es = [torch.empty(p["n"], dtype=torch.complex128, device=dev) for p in pool]
+    for _ in range(warmup):
+        dpt.solve_batched(th, D, lams, A_outs=As, E_outs=Es)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pm, pl = 0.0, 0
+    e0.record(stream)
+    for _ in range(steps):
+        _, _, infos = dpt.solve_batched(th, D, lams, A_outs=As, E_outs=Es, profile=True)
+        pm += infos[0]["product_ms"]
+        pl += infos[0]["product_launches"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ns = np.array([p["n"] for p in pool], dtype=float)
+    it = np.array([i["iters"] for i in infos])
+    sl = np.array([i["slice_gemms"] for i in infos])
+    prod_ms = pm / steps
+    return {"workload": f"{len(pool)} served complex Hermitian problems (pool entries"
+                        f"{'' if max_n is None else f' with n <= {max_n}'}), lambda 0.05, one grouped solve",
+            "solves_per_s": len(pool) * 1e3 / ms, "ms_per_batch": ms,
+            "product_ms_per_batch": prod_ms, "product_launches": pl // steps,
+            "executed_tflops_in_product": float(np.sum(8 * ns**3 * sl)) / (prod_ms * 1e-3) / 1e12,
+            "algorithmic_tflops_in_product": float(np.sum(8 * ns**3 * it)) / (prod_ms * 1e-3) / 1e12,
+            "iters_max": int(it.max()), "all_converged": all(i["status"] == "OK" for i in infos)}
+
+
 def _run_stream(srv, stream, th, D, outs, wait_all=True):
     """Open-loop submission at the scheduled arrival times; returns per-request
     (info, lateness) and the wall time from the first arrival to the last result."""
@@ -545,6 +586,7 @@ def run_ours(args, world, rank, local):
         extra["dominant_csr"] = bench_dominant(dpt, inputs, dev, pk)
         extra["batched"] = bench_batched(dpt, inputs, dev)
         extra["served"] = bench_served(dpt, inputs, dev)
+        extra["served_pool"] = bench_served_pool(dpt, inputs, dev)
 
     if rank != 0:
         return
@@ -595,6 +637,9 @@ def main():
             out = bench_dominant(dpt, inputs, dev, pk)
         elif args.only == "batched":
             out = bench_batched(dpt, inputs, dev)
+        elif args.only == "served_pool":
+            out = bench_served_pool(dpt, inputs, dev, steps=max(1, min(args.steps, 10)),
+                                    warmup=max(1, min(args.warmup, 3)), max_n=args.pool_max_n)
         else:
             out = bench_served(dpt, inputs, dev)
         if rank == 0:

@@ -341,11 +341,15 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
 
     const CUtensorMap tA = make_tmap_bf16(Dcat, (uint64_t)3 * ld, n, (uint64_t)3 * ld, 128);
-    const CUtensorMap tB0 = make_tmap_bf16(dtb[0], n, n, ld, mixed_tile_n());
-    const CUtensorMap tB1 = make_tmap_bf16(dtb[1], n, n, ld, mixed_tile_n());
+    int nsm = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int bn = mixed_tile_n((int)n, nsm);
+    const CUtensorMap tB0 = make_tmap_bf16(dtb[0], n, n, ld, bn);
+    const CUtensorMap tB1 = make_tmap_bf16(dtb[1], n, n, ld, bn);
     CK(mixed_set_attributes());
     GemmEpiParams p{};
-    p.n = n; p.ld = ld; p.ntm = ntm; p.lam = (float)lambda;
+    p.n = n; p.ld = ld; p.ntm = ntm; p.bn = bn; p.lam = (float)lambda;
     for (int q = 0; q < 2; ++q) { p.A_hi[q] = Ahi[q]; p.A_lo[q] = Alo[q]; p.dt[q] = dtb[q]; }
     p.L = L; p.Dcat = Dcat; p.cat_ld = (int64_t)3 * ld; p.th_hi = thh; p.th_lo = thl; p.e_col = e_col; p.dprev_col = dprev;
     p.part = part; p.st = st;

@@ -30,7 +30,8 @@
 namespace dpt {
 
 constexpr int BM = 128;          // rows j per tile (TMEM lanes)
-constexpr int BN = 256;          // columns i per tile (TMEM columns per accumulator)
+constexpr int BN = 256;          // widest tile: columns i per tile (TMEM columns per accumulator);
+                                 // the launch's width p.bn is a multiple of 32 up to BN
 constexpr int BK = 64;           // K per stage: one 128-byte swizzle atom of BF16
 constexpr int UK = 16;           // K per tcgen05.mma (kind::f16)
 constexpr int STAGES = 4;        // operand ring depth (bytes in flight cover the L2 latency)
@@ -411,7 +412,8 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   float* Xs = reinterpret_cast<float*>(smem + SMEM_TILES);
   GemmSmemMisc* ms = (GemmSmemMisc*)(smem + SMEM_TILES + SMEM_X);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntn = (p.n + BN - 1) / BN;
+  const int bn = p.bn;
+  const int ntn = (p.n + bn - 1) / bn;
   const int ntiles = ntn * p.ntm;
 
   if (threadIdx.x == 0) {
@@ -444,13 +446,13 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     bool alive = true;
     for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
       const int tm = t / ntn, tn = t % ntn;
-      const int m0 = tm * BM, n0 = tn * BN;
-      const int kb_last = min(kb_per_slice - 1, (n0 + BN - 1) / BK);
+      const int m0 = tm * BM, n0 = tn * bn;
+      const int kb_last = min(kb_per_slice - 1, (n0 + bn - 1) / BK);
       for (int q = 0; q < nk; ++q, ++it) {
         const int s = it % STAGES;
         const uint32_t ph = (it / STAGES) & 1;
         if (!mbar_wait(&ms->empty[s], ph ^ 1, tflag)) { alive = false; break; }
-        mbar_arrive_expect_tx(&ms->full[s], A_TILE + B_TILE);
+        mbar_arrive_expect_tx(&ms->full[s], A_TILE + (uint32_t)bn * BK * 2);
         // Accumulation order.  The tensor core accumulates in FP32 and drops the
         // bits below the running sum at every step, so the error of a chain grows
         // with the size of the partial sums it carries.  Column i of Delta dt is
@@ -468,7 +470,7 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       mbar_wait(&ms->full[t % STAGES], (t / STAGES) & 1, tflag);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
-    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+    const uint32_t idesc = idesc_bf16_f32(BM, bn);
     uint32_t it = 0;
     int lt = 0;   // local tile counter
     bool alive = true;
@@ -505,11 +507,11 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     int lt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const int tm = t / ntn, tn = t % ntn;
-      const int m0 = tm * BM, n0 = tn * BN;
+      const int m0 = tm * BM, n0 = tn * bn;
       const int b = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
       epi_bar();   // the previous tile's column walk has finished with Xs and params
-      if (et < BN) {
+      if (et < bn) {
         const int i = n0 + et;
         const bool v = i < p.n;
         ms->e[et] = v ? p.e_col[i] : 0.f;
@@ -523,7 +525,7 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       const uint32_t src = tmem + (uint32_t)(b * BN) + ((uint32_t)(qd * 32) << 16);
       bool all_ok = true;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += XCH) {
+      for (int c0 = 0; c0 < bn; c0 += XCH) {
         if (c0 > 0) epi_bar();   // the previous chunk's column walk is done with Xs
         // phase 1: this warp's quadrant, 16 of the chunk's 32 columns
         if (ok) {
@@ -533,10 +535,10 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 #pragma unroll
           for (int c = 0; c < 16; ++c) Xs[(cc + c) * BM + qd * 32 + lane] = x[c];
         }
-        if (c0 + XCH == BN) tc_fence_before();
+        if (c0 + XCH == bn) tc_fence_before();
         all_ok = epi_bar_and(ok);   // Xs holds the chunk
         // after the last chunk is staged the TMEM buffer can be refilled
-        if (c0 + XCH == BN && et == 0) mbar_arrive(&ms->acc_empty[b]);
+        if (c0 + XCH == bn && et == 0) mbar_arrive(&ms->acc_empty[b]);
         if (!all_ok) break;
         epilogue_columns(p, ms, Xs, ew, lane, tm, m0, n0, c0, mx);
       }
@@ -601,7 +603,25 @@ __global__ void k_theta_ff(int n, const double* __restrict__ th, float* __restri
 // Host launchers
 // ---------------------------------------------------------------------------
 int mixed_smem_bytes() { return SMEM_BYTES; }
-int mixed_tile_n() { return BN; }
+// Tile width for an n x n product on nsm SMs.  Every CTA of the persistent kernel
+// takes tiles round-robin, so the launch lasts ceil(tiles / nsm) tile times; a
+// tile's time grows with its width plus a width-independent part (the A operand's
+// share of the TMA traffic and the epilogue's fixed work, about 64 columns' worth).
+// The width (a multiple of 32, at most 256) minimises that estimate, so that the
+// last wave is not left mostly idle (n = 4096 on 152 SMs: 224 -> 608 tiles = 4
+// full waves, against 512 tiles = 3.4 waves at 256).
+int mixed_tile_n(int n, int nsm) {
+  const int ntm = (n + BM - 1) / BM;
+  int best = BN;
+  long long best_cost = -1;
+  for (int w = BN; w >= 64; w -= 32) {
+    const long long tiles = (long long)ntm * ((n + w - 1) / w);
+    const long long waves = (tiles + nsm - 1) / nsm;
+    const long long cost = waves * (w + 64);
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = w; }
+  }
+  return best;
+}
 
 cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en,
                               __nv_bfloat16* Dcat, IterState* st, cudaStream_t s) {
@@ -651,7 +671,8 @@ cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
   }
-  const int ntiles = ((p.n + BN - 1) / BN) * p.ntm;
+  if (p.bn < 32 || p.bn > BN || p.bn % 32) return cudaErrorInvalidValue;
+  const int ntiles = ((p.n + p.bn - 1) / p.bn) * p.ntm;
   const int grid = ntiles < nsm ? ntiles : nsm;
   k_gemm_epi<<<grid, NTHREADS, SMEM_BYTES, s>>>(tmA, tmB0, tmB1, p);
   return cudaGetLastError();

@@ -131,6 +131,7 @@ struct GemmEpiParams {
   int n;               // matrix size
   int ld;              // padded leading dimension of every n x n work array (multiple of 128)
   int ntm;             // number of 128-row tiles
+  int bn;              // output tile width (columns), a multiple of 32 up to 256
   float lam;
   float* A_hi[2];      // float-float iterate, column-major, ping-pong by iteration parity
   float* A_lo[2];
@@ -147,7 +148,7 @@ struct GemmEpiParams {
 };
 
 int mixed_smem_bytes();
-int mixed_tile_n();      // columns per output tile of the product kernel
+int mixed_tile_n(int n, int nsm);   // columns per output tile of the product kernel
 cudaError_t mixed_set_attributes();   // once per device, before any capture
 cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en,
                               __nv_bfloat16* Dcat, IterState* st, cudaStream_t s);
