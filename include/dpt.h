@@ -306,6 +306,16 @@ DPT_API dpt_status dpt_server_stats_get(dpt_server* srv, dpt_server_stats* stats
  * budget.  Requests not yet polled are forgotten. */
 DPT_API dpt_status dpt_server_destroy(dpt_server* srv);
 
+/* Self-test of the bounded device waits (a deployment check; no counterpart in the
+ * paper).  Every wait inside the library's kernels gives up after a time limit, sets a
+ * flag the host reads and lets the kernel return, so a stalled pipeline ends as
+ * DPT_ERR_TIMEOUT with the device still usable.  This call runs one kernel whose wait
+ * can never complete (an mbarrier phase nobody arrives at) with a limit of `seconds`
+ * (0 < seconds <= 5).  Returns DPT_ERR_TIMEOUT when the wait expired and the kernel
+ * returned as designed (the expected result), DPT_ERR_ARG for a bad duration,
+ * DPT_ERR_CUDA otherwise.  Blocks until done. */
+DPT_API dpt_status dpt_selftest_bounded_wait(double seconds, void* stream);
+
 /* Free the scratch pool of the current device (no solve may be running). */
 DPT_API void dpt_release_workspace(void);
 

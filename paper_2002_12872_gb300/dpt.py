@@ -122,6 +122,8 @@ def lib() -> ctypes.CDLL:
         L.dpt_server_stats_get.restype = ctypes.c_int
         L.dpt_server_destroy.argtypes = [P]
         L.dpt_server_destroy.restype = ctypes.c_int
+        L.dpt_selftest_bounded_wait.argtypes = [dbl, P]
+        L.dpt_selftest_bounded_wait.restype = ctypes.c_int
         L.dpt_release_workspace.argtypes = []
         L.dpt_release_workspace.restype = None
         _lib = L
@@ -346,6 +348,13 @@ def solve_dominant_noalloc(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, tol=
         err.result = res
         raise err
     return res
+
+
+def selftest_bounded_wait(seconds=0.5, stream=None):
+    """dpt_selftest_bounded_wait: status name of a bounded device wait that is made to
+    expire ('ERR_TIMEOUT' is the expected outcome)."""
+    s = ctypes.c_void_p(0) if stream is None else ctypes.c_void_p(int(stream))
+    return STATUS.get(lib().dpt_selftest_bounded_wait(float(seconds), s))
 
 
 def release_workspace():

@@ -65,3 +65,23 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.dpt_solve_full(4, 0, p(th), p(d), 4, 0.1, ctypes.byref(o2), p(A), 4, p(E),
                               ctypes.byref(info), None) == -1
     assert info.status == -1
+
+
+def test_selftest_and_server_arguments_rejected_without_gpu(lib):
+    from paper_2002_12872_gb300 import dpt
+    assert lib.dpt_selftest_bounded_wait(0.0, None) == -1
+    assert lib.dpt_selftest_bounded_wait(10.0, None) == -1
+    cfg = dpt.ServerCfg()
+    lib.dpt_server_cfg_default(ctypes.byref(cfg))
+    assert cfg.max_active == 64 and cfg.max_queue == 65536 and cfg.opt.tol == 1e-12
+    h = ctypes.c_void_p()
+    bad = dpt.ServerCfg()
+    lib.dpt_server_cfg_default(ctypes.byref(bad))
+    bad.max_active = 0
+    assert lib.dpt_server_create(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad.max_active = 8
+    bad.opt.prec = 0                       # the server runs the mixed path only
+    assert lib.dpt_server_create(ctypes.byref(bad), ctypes.byref(h)) == -1
+    assert lib.dpt_submit(None, None, None) == -1
+    assert lib.dpt_poll(None, 1, None) == -1
+    assert lib.dpt_server_destroy(None) == -1
