@@ -98,9 +98,14 @@ typedef struct {
   int32_t max_slices;      /* BF16 slices of Delta in the mixed path, 1..3 (default 3) */
   int32_t profile;         /* nonzero: time every product kernel with CUDA events on
                               the stream it runs on (reported in dpt_info) */
-  double slice_tol;        /* mixed path: after an iteration whose largest increment
-                              |delta A| is below slice_tol, the next product uses one
-                              slice (default 1e-8) */
+  double slice_tol;        /* mixed path: the first product uses max_slices slices; a
+                              later product uses two once its increment's largest entry
+                              is below 2^-8 of the first increment's, one once below
+                              2^-16 of it or below slice_tol (default 1e-8) */
+  int32_t cta_pair;        /* real mixed full solve: nonzero runs the product as CTA
+                              pairs (tcgen05 cta_group::2, 256-row tiles split over two
+                              SMs) where clusters of two can be resident; 0 (default)
+                              one CTA per 128-row tile */
 } dpt_options;
 
 typedef struct {
@@ -115,6 +120,8 @@ typedef struct {
   int32_t product_launches;  /* product kernels that did work (one per iteration) */
   double product_ms;       /* with opt->profile: summed device time of those
                               product kernels, else 0 */
+  int32_t cta_pair;        /* real mixed full solve: 1 when the products ran in the
+                              CTA-pair form, else 0 */
 } dpt_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -344,10 +344,14 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     int nsm = 0, dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int bn = mixed_tile_n((int)n, nsm);
-    const CUtensorMap tB0 = make_tmap_bf16(dtb[0], n, n, ld, bn);
-    const CUtensorMap tB1 = make_tmap_bf16(dtb[1], n, n, ld, bn);
     CK(mixed_set_attributes());
+    // CTA-pair form when asked for and clusters of two can be resident
+    int npairs = 0;
+    if (o.cta_pair) npairs = std::min(nsm / 2, mixed_pair_clusters());
+    const bool pair = npairs > 0;
+    const int bn = pair ? mixed_pair_tile_n((int)n, npairs) : mixed_tile_n((int)n, nsm);
+    const CUtensorMap tB0 = make_tmap_bf16(dtb[0], n, n, ld, pair ? bn / 2 : bn);
+    const CUtensorMap tB1 = make_tmap_bf16(dtb[1], n, n, ld, pair ? bn / 2 : bn);
     GemmEpiParams p{};
     p.n = n; p.ld = ld; p.ntm = ntm; p.bn = bn; p.lam = (float)lambda;
     for (int q = 0; q < 2; ++q) { p.A_hi[q] = Ahi[q]; p.A_lo[q] = Alo[q]; p.dt[q] = dtb[q]; }
@@ -362,7 +366,8 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     if (b->host_state->status == ST_RUNNING)
       run_loop(b, st, o.graph_iters, o.max_iter, 2, prof, [&](int q) {
         prof.before(q, s);
-        CK(launch_gemm_epi(tA, tB0, tB1, p, s));
+        if (pair) CK(launch_gemm_epi_pair(tA, tB0, tB1, p, npairs, s));
+        else CK(launch_gemm_epi(tA, tB0, tB1, p, s));
         prof.after(q, s);
         CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
       });
@@ -385,6 +390,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
       info->launches = prof.launches;
       info->product_launches = prof.live;
       info->product_ms = prof.ms;
+      info->cta_pair = pair ? 1 : 0;
     }
     CK(cudaEventRecord(b->ev, s));
     CK(cudaStreamWaitEvent(user, b->ev, 0));
@@ -939,6 +945,7 @@ void dpt_options_default(dpt_options* o) {
   o->max_slices = 3;
   o->slice_tol = 1e-8;
   o->profile = 0;
+  o->cta_pair = 0;
 }
 
 const char* dpt_status_string(dpt_status s) {

@@ -209,6 +209,17 @@ __device__ __forceinline__ bool mbar_wait_ns(uint64_t* bar, uint32_t parity, uns
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* timeout) {
   return mbar_wait_ns(bar, parity, timeout, kWaitNs);
 }
+// Bounded wait that ignores (and never sets) the launch's timeout flag: used at the
+// end of a kernel to let asynchronous arrivals land before the CTA exits, also
+// after another wait has given up.
+__device__ __forceinline__ bool mbar_wait_quiet(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (global_ns() - t0 <= limit_ns)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+constexpr uint64_t kTailWaitNs = 100000000ull;   // 100 ms
 
 // ---------------------------------------------------------------------------
 // TMA: 2-D tiled bulk tensor load into shared memory, completion on an mbarrier
@@ -284,6 +295,73 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, float (&v)[16]) {
                : "memory");
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------------------
+// CTA pairs (clusters of two): cluster rank, cluster-wide barrier, peer shared
+// addresses, and the cta_group::2 forms of the TMEM, TMA and MMA instructions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// every thread of both CTAs
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+// shared::cluster address of the variable at `p` in the CTA of cluster rank `rank`
+__device__ __forceinline__ uint32_t mapa_shared(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster)
+               : "memory");
+}
+// one warp of each CTA of the pair, collectively
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish_pair() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+// TMA load into this CTA's shared memory, completing on an mbarrier that may live
+// in either CTA of the pair (given as a shared::cluster address)
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const void* tmap, uint32_t bar_cluster,
+                                                 int32_t x, int32_t y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(bar_cluster), "r"(x), "r"(y)
+      : "memory");
+}
+// D[tmem of both CTAs] (+)= A[smem of both CTAs, M halves] * B[smem of both CTAs, N halves]
+__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                               uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on `bar` (same offset) in every CTA of `mask` once this thread's MMAs completed
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
+      : "memory");
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile stored with the
@@ -421,6 +499,24 @@ __device__ __forceinline__ bool decide(volatile IterState* vs, double rho) {
   vs->k = vs->k + 1;
   vs->cur = vs->k & 1;
   return true;
+}
+
+// ---------------------------------------------------------------------------
+// Slices of Delta for the next product, from the largest increment dmax it will
+// multiply.  With S BF16 slices the truncation of Delta is about 2^(-8S) relative,
+// so a product's truncation error is about 2^(-8S) |Delta| dmax.  The first product
+// (three slices on the increment dt_0 of size dmax1) sets the error the solve
+// accepts; later products take the fewest slices that stay below it: two once
+// dmax <= 2^-8 dmax1, one once dmax <= 2^-16 dmax1 (or below slice_tol).  The
+// carried remainder makes the fixed point that of the full Delta either way.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int next_slices(volatile IterState* vs, float dmax, bool first) {
+  if (first) vs->dmax1 = dmax;
+  const float d1 = vs->dmax1;
+  int S = vs->max_slices;
+  if ((double)dmax < vs->slice_tol || dmax <= d1 * 0x1p-16f) S = 1;
+  else if (dmax <= d1 * 0x1p-8f) S = 2;
+  return S < vs->max_slices ? S : vs->max_slices;
 }
 
 }  // namespace dpt

@@ -35,6 +35,7 @@ constexpr int BN = 256;          // widest tile: columns i per tile (TMEM column
 constexpr int BK = 64;           // K per stage: one 128-byte swizzle atom of BF16
 constexpr int UK = 16;           // K per tcgen05.mma (kind::f16)
 constexpr int STAGES = 4;        // operand ring depth (bytes in flight cover the L2 latency)
+constexpr int MAX_STAGES = 8;    // barrier slots; the CTA-pair kernel fits more, smaller stages
 constexpr int NACC = 2;          // TMEM accumulators (double buffer)
 constexpr int IT0 = 128;         // columns (and rows) per block of iteration 0
 constexpr int NSLICE = 3;        // BF16 slices of Delta kept (the product uses the first S)
@@ -47,8 +48,8 @@ constexpr int XCH = 32;                         // accumulator columns staged pe
 constexpr int SMEM_X = BM * XCH * 4;            // accumulator staging (FP32, column-major)
 
 struct __align__(16) GemmSmemMisc {
-  uint64_t full[STAGES];
-  uint64_t empty[STAGES];
+  uint64_t full[MAX_STAGES];
+  uint64_t empty[MAX_STAGES];
   uint64_t acc_full[NACC];
   uint64_t acc_empty[NACC];
   uint32_t tmem_base;
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
   const float dmax = __uint_as_float(vs->dmax_bits);
   vs->dmax_bits = 0;
   if (!decide(vs, rho)) return;
-  const int S = ((double)dmax < vs->slice_tol) ? 1 : vs->max_slices;
+  const int S = next_slices(vs, dmax, first);
   vs->slices = S;
   vs->slice_gemms = vs->slice_gemms + S;
 }
@@ -555,6 +556,188 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 }
 
 // ---------------------------------------------------------------------------
+// CTA-pair form of the product kernel (tcgen05 cta_group::2).  The two CTAs of a
+// cluster compute one 256 x bn output tile: each loads its own 128 rows of the A
+// operand (Delta slices) and half of the B operand (bn/2 increment columns) into
+// its own shared memory; the MMA, issued by the pair's leader (cluster rank 0),
+// reads both halves of both operands and leaves each CTA's 128 rows of the
+// accumulator in that CTA's tensor memory.  Per SM a K-block stage is then A + B/2
+// instead of A + B, so the same shared memory holds six stages instead of four and
+// each SM fetches a third fewer operand bytes per flop.  Each CTA runs the fused
+// epilogue on its own rows; the arithmetic per element, the slice order and the K
+// rotation are those of k_gemm_epi.
+// Barriers: the leader's full[s] collects the transaction bytes of both CTAs'
+// loads (the leader posts the expectation for both); the MMA commits arrive on
+// empty[s] and acc_full[b] of both CTAs (multicast); both epilogues arrive on the
+// leader's acc_empty[b] (count 2).  Every thread of both CTAs reaches the final
+// cluster barrier, also when a bounded wait has given up.
+// ---------------------------------------------------------------------------
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
+                const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  IterState* st = p.st;
+  // read before any cluster barrier; nothing changes it during the launch, so both
+  // CTAs of a pair take the same branch
+  if (*((volatile int*)&st->status) != ST_RUNNING) return;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* Xs = reinterpret_cast<float*>(smem + SMEM_TILES);
+  GemmSmemMisc* ms = (GemmSmemMisc*)(smem + SMEM_TILES + SMEM_X);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int bn = p.bn, bh = bn / 2;
+  const int ntn = (p.n + bn - 1) / bn;
+  const int ntm2 = (p.n + 2 * BM - 1) / (2 * BM);
+  const int ntiles = ntn * ntm2;
+  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+
+  if (threadIdx.x == 0) {
+    ms->k = st->k;
+    ms->slices = st->slices;
+    ms->cur = st->cur;
+    for (int s = 0; s < MAX_STAGES; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], 1); }
+    for (int b = 0; b < NACC; ++b) { mbar_init(&ms->acc_full[b], 1); mbar_init(&ms->acc_empty[b], 2); }
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc_pair(&ms->tmem_base, NACC * BN);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  cluster_sync();      // both CTAs' barriers initialised and their TMEM allocated
+  tc_fence_after();
+  const uint32_t tmem = ms->tmem_base;
+  const int S = ms->slices;
+  const int kb_per_slice = p.ld / BK;
+  const int nk = S * kb_per_slice;
+  const uint32_t stage_bytes = (uint32_t)A_TILE + (uint32_t)bh * BK * 2;   // multiple of 1024
+  const int nst = min(MAX_STAGES, (int)(SMEM_TILES / stage_bytes));
+  const CUtensorMap* tmB = (ms->cur == 1) ? &tmB0 : &tmB1;
+  unsigned* tflag = &st->timeout;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer (both CTAs): completions go to the leader's full[s] ----
+    prefetch_tmap(&tmA);
+    prefetch_tmap(tmB);
+    const uint32_t full_leader = mapa_shared(&ms->full[0], 0);
+    uint32_t it = 0;
+    bool alive = true;
+    for (int t = pair; t < ntiles && alive; t += npairs) {
+      const int tm2 = t / ntn, tn = t % ntn;
+      const int m0 = tm2 * 2 * BM + (int)rank * BM, n0 = tn * bn;
+      const int kb_last = min(kb_per_slice - 1, (n0 + bn - 1) / BK);
+      for (int q = 0; q < nk; ++q, ++it) {
+        const int s = it % nst;
+        const uint32_t ph = (it / nst) & 1;
+        if (!mbar_wait(&ms->empty[s], ph ^ 1, tflag)) { alive = false; break; }
+        if (rank == 0) mbar_arrive_expect_tx(&ms->full[s], 2 * stage_bytes);
+        // small slices first, the tile's diagonal K-blocks last (see k_gemm_epi)
+        const int sl = S - 1 - q / kb_per_slice;
+        const int kb = (kb_last + 1 + q % kb_per_slice) % kb_per_slice;
+        uint8_t* slot = smem + (size_t)s * stage_bytes;
+        const uint32_t fb = full_leader + (uint32_t)s * 8u;
+        tma_load_2d_pair(slot, &tmA, fb, sl * p.ld + kb * BK, m0);
+        tma_load_2d_pair(slot + A_TILE, tmB, fb, kb * BK, n0 + (int)rank * bh);
+      }
+    }
+    // the MMA's last commits have arrived on this CTA's empty barriers
+    for (uint32_t u = (it > (uint32_t)nst ? it - nst : 0); u < it; ++u)
+      mbar_wait_quiet(&ms->empty[u % nst], (u / nst) & 1, kTailWaitNs);
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ---- MMA issuer (leader only) ----
+    const uint32_t idesc = idesc_bf16_f32(2 * BM, bn);
+    uint32_t it = 0;
+    int lt = 0;
+    bool alive = true;
+    for (int t = pair; t < ntiles && alive; t += npairs, ++lt) {
+      const int b = lt & 1;
+      const uint32_t use = (uint32_t)(lt >> 1);
+      if (!mbar_wait(&ms->acc_empty[b], (use & 1) ^ 1, tflag)) break;
+      tc_fence_after();
+      const uint32_t dacc = tmem + (uint32_t)(b * BN);
+      for (int q = 0; q < nk; ++q, ++it) {
+        const int s = it % nst;
+        const uint32_t ph = (it / nst) & 1;
+        if (!mbar_wait(&ms->full[s], ph, tflag)) { alive = false; break; }
+        tc_fence_after();
+        uint8_t* slot = smem + (size_t)s * stage_bytes;
+        const uint64_t da = smem_desc_sw128(slot);
+        const uint64_t db = smem_desc_sw128(slot + A_TILE);
+#pragma unroll
+        for (int kk = 0; kk < BK / UK; ++kk)
+          umma_bf16_pair(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                         (q > 0 || kk > 0) ? 1u : 0u);
+        umma_commit_pair(&ms->empty[s], (uint16_t)3);
+      }
+      umma_commit_pair(&ms->acc_full[b], (uint16_t)3);
+    }
+    // both epilogues have released the last accumulators: their arrivals on this
+    // CTA's acc_empty have landed before it can exit
+    for (int u = (lt > NACC ? lt - NACC : 0); u < lt; ++u)
+      mbar_wait_quiet(&ms->acc_empty[u & 1], (uint32_t)((u >> 1) & 1), kTailWaitNs);
+  } else if (warp >= 2) {
+    // ---- epilogue (both CTAs, each on its own 128 rows) ----
+    const int ew = warp - 2;
+    const int qd = warp & 3;
+    const int half = ew >> 2;
+    const int et = threadIdx.x - 64;
+    const uint32_t acc_empty_leader = mapa_shared(&ms->acc_empty[0], 0);
+    float mx = 0.f;
+    int lt = 0;
+    for (int t = pair; t < ntiles; t += npairs, ++lt) {
+      const int tm2 = t / ntn, tn = t % ntn;
+      const int tm = 2 * tm2 + (int)rank;
+      const int m0 = tm * BM, n0 = tn * bn;
+      const int b = lt & 1;
+      const uint32_t use = (uint32_t)(lt >> 1);
+      epi_bar();
+      if (et < bn) {
+        const int i = n0 + et;
+        const bool v = i < p.n;
+        ms->e[et] = v ? p.e_col[i] : 0.f;
+        ms->dprev[et] = v ? p.dprev_col[i] : 0.f;
+        ms->thh[et] = v ? p.th_hi[i] : 0.f;
+        ms->thl[et] = v ? p.th_lo[i] : 0.f;
+      }
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&ms->acc_full[b], use & 1, tflag));
+      tc_fence_after();
+      const uint32_t src = tmem + (uint32_t)(b * BN) + ((uint32_t)(qd * 32) << 16);
+      bool all_ok = true;
+#pragma unroll 1
+      for (int c0 = 0; c0 < bn; c0 += XCH) {
+        if (c0 > 0) epi_bar();
+        if (ok) {
+          float x[16];
+          const int cc = half * 16;
+          tmem_ld_x16(src + (uint32_t)(c0 + cc), x);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) Xs[(cc + c) * BM + qd * 32 + lane] = x[c];
+        }
+        if (c0 + XCH == bn) tc_fence_before();
+        all_ok = epi_bar_and(ok);
+        if (c0 + XCH == bn && et == 0) {
+          if (rank == 0) mbar_arrive(&ms->acc_empty[b]);
+          else mbar_arrive_remote(acc_empty_leader + (uint32_t)b * 8u);
+        }
+        if (!all_ok) break;
+        // rows of a pair tile beyond the padded matrix hold no work
+        if (tm < p.ntm) epilogue_columns(p, ms, Xs, ew, lane, tm, m0, n0, c0, mx);
+      }
+      if (!all_ok) break;
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0 && mx > 0.f) atomicMax(&p.st->dmax_bits, __float_as_uint(mx));
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();      // no MMA, load or remote arrival of the pair is still in flight
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, NACC * BN);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Output: A (float-float -> FP64) and E of the returned iterate.
 // ---------------------------------------------------------------------------
 // Output: grid (128-row tiles, 128-column tiles); thread j owns row j of the tile
@@ -658,8 +841,63 @@ cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
 }
 
 cudaError_t mixed_set_attributes() {
-  return cudaFuncSetAttribute(k_gemm_epi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_epi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_gemm_epi_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               SMEM_BYTES);
+}
+
+// Clusters of two that can be resident at once (0: the pair form cannot run).  The
+// kernel declares its cluster shape at compile time, so the query passes none.
+int mixed_pair_clusters() {
+  static int cached[64];
+  static bool known[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (known[dev]) return cached[dev];
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2, 1, 1);
+  cfg.blockDim = dim3(NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.attrs = nullptr;
+  cfg.numAttrs = 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_gemm_epi_pair, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cached[dev] = n;
+  known[dev] = true;
+  return n;
+}
+
+// Tile width for the pair form: as mixed_tile_n with 256-row tiles over `npairs`
+// CTA pairs; half of the width (a multiple of 16) goes to each CTA.
+int mixed_pair_tile_n(int n, int npairs) {
+  const int ntm2 = (n + 2 * BM - 1) / (2 * BM);
+  int best = BN;
+  long long best_cost = -1;
+  for (int w = BN; w >= 64; w -= 32) {
+    const long long tiles = (long long)ntm2 * ((n + w - 1) / w);
+    const long long waves = (tiles + npairs - 1) / npairs;
+    const long long cost = waves * (w + 64);
+    if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = w; }
+  }
+  return best;
+}
+
+cudaError_t launch_gemm_epi_pair(const CUtensorMap& tmA, const CUtensorMap& tmB0,
+                                 const CUtensorMap& tmB1, const GemmEpiParams& p, int npairs,
+                                 cudaStream_t s) {
+  if (p.bn < 64 || p.bn > BN || p.bn % 32 || npairs < 1) return cudaErrorInvalidValue;
+  const int ntiles = ((p.n + p.bn - 1) / p.bn) * ((p.n + 2 * BM - 1) / (2 * BM));
+  const int pairs = ntiles < npairs ? ntiles : npairs;
+  k_gemm_epi_pair<<<2 * pairs, NTHREADS, SMEM_BYTES, s>>>(tmA, tmB0, tmB1, p);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,

@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(256) k_g_ctrl(const GProb* __restrict__ probs,
     atomicSub(running, 1);
     return;
   }
-  const int S = ((double)dmax < vs->slice_tol) ? 1 : vs->max_slices;
+  const int S = next_slices(vs, dmax, first);
   vs->slices = S;
   vs->slice_gemms = vs->slice_gemms + S;
 }

@@ -47,6 +47,7 @@ struct IterState {
   double rho;          // normalised max residual of A_k
   double best;
   double rho_last;
+  float dmax1;         // max |dt_0|: the increment fed to the first product
 };
 
 // State of a dominant-eigenvector solve (single-vector map), device resident.
@@ -149,6 +150,11 @@ struct GemmEpiParams {
 
 int mixed_smem_bytes();
 int mixed_tile_n(int n, int nsm);   // columns per output tile of the product kernel
+int mixed_pair_clusters();          // resident clusters of two for the CTA-pair form
+int mixed_pair_tile_n(int n, int npairs);
+cudaError_t launch_gemm_epi_pair(const CUtensorMap& tmA, const CUtensorMap& tmB0,
+                                 const CUtensorMap& tmB1, const GemmEpiParams& p, int npairs,
+                                 cudaStream_t s);
 cudaError_t mixed_set_attributes();   // once per device, before any capture
 cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en,
                               __nv_bfloat16* Dcat, IterState* st, cudaStream_t s);

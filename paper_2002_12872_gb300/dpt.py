@@ -31,7 +31,8 @@ class Options(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("epstein_nesbet", ctypes.c_int32),
                 ("graph_iters", ctypes.c_int32), ("max_slices", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("slice_tol", ctypes.c_double)]
+                ("profile", ctypes.c_int32), ("slice_tol", ctypes.c_double),
+                ("cta_pair", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -39,14 +40,14 @@ class Info(ctypes.Structure):
                 ("residual", ctypes.c_double), ("status", ctypes.c_int32),
                 ("nstar", ctypes.c_int32), ("seconds", ctypes.c_double),
                 ("launches", ctypes.c_int32), ("product_launches", ctypes.c_int32),
-                ("product_ms", ctypes.c_double)]
+                ("product_ms", ctypes.c_double), ("cta_pair", ctypes.c_int32)]
 
     def as_dict(self):
         return {"iters": self.iters, "slice_gemms": self.slice_gemms,
                 "residual": self.residual, "status": STATUS.get(self.status, str(self.status)),
                 "code": self.status, "nstar": self.nstar, "seconds": self.seconds,
                 "launches": self.launches, "product_launches": self.product_launches,
-                "product_ms": self.product_ms}
+                "product_ms": self.product_ms, "cta_pair": self.cta_pair}
 
 
 class ServerCfg(ctypes.Structure):
@@ -228,7 +229,7 @@ def _iscomplex(x) -> bool:
 # ---------------------------------------------------------------------------
 def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
                epstein_nesbet=False, graph_iters=None, max_slices=None, slice_tol=None,
-               profile=False, A_out=None, E_out=None, stream=None, check=True):
+               profile=False, cta_pair=None, A_out=None, E_out=None, stream=None, check=True):
     """All eigenpairs of M = diag(theta) + lam * Delta by the DPT map (dpt_solve_full).
 
     Returns (A, E, info): A[:, i] is eigenvector i with A[i, i] = 1 and
@@ -244,7 +245,7 @@ def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
     lda = A.stride(1) if _is_torch(A) else A.strides[1] // A.itemsize
     o = options(tol=tol, max_iter=max_iter, prec=prec, epstein_nesbet=int(bool(epstein_nesbet)),
                 graph_iters=graph_iters, max_slices=max_slices, slice_tol=slice_tol,
-                profile=int(bool(profile)))
+                profile=int(bool(profile)), cta_pair=None if cta_pair is None else int(cta_pair))
     info = Info()
     st = lib().dpt_solve_full(n, C128 if cplx else R64, th_ptr, d_ptr, ldd, float(lam),
                               ctypes.byref(o), _ptr(A), lda, _ptr(E), ctypes.byref(info),
