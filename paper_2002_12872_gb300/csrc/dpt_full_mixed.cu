@@ -304,6 +304,7 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
                                                  const float* Xs, int ew, int lane, int tm,
                                                  int m0, int n0, int c0, float& mx) {
   const int n = p.n, ld = p.ld;
+  const int S = ms->slices;
   const bool c1 = (ms->cur != 0);
   // explicit selects: indexing the parameter arrays with a runtime value would
   // copy the parameter block to local memory
@@ -334,11 +335,13 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
         in[u].al = ld4(Alc + idx);
         in[u].L = ld4(L + idx);
         in[u].dtp = *reinterpret_cast<const uint2*>(dtp + idx);
-        // Delta_ij for j = j0..j0+3: row i of the row-major slices
+        // Delta_ij for j = j0..j0+3: row i of the row-major slices.  The diagonal
+        // partial uses as many slices as this product: its truncation error then
+        // obeys the same bound as the product's (see next_slices)
         const __nv_bfloat16* Drow = p.Dcat + (int64_t)i * p.cat_ld + j0;
-#pragma unroll
-        for (int sl = 0; sl < 3; ++sl)
-          in[u].D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+        in[u].D[0] = *reinterpret_cast<const uint2*>(Drow);
+        in[u].D[1] = S > 1 ? *reinterpret_cast<const uint2*>(Drow + ld) : make_uint2(0u, 0u);
+        in[u].D[2] = S > 2 ? *reinterpret_cast<const uint2*>(Drow + 2 * (int64_t)ld) : make_uint2(0u, 0u);
       }
     }
 #pragma unroll

@@ -610,10 +610,11 @@ __device__ __forceinline__ void g_epilogue_columns(const GTileInfo& ti, GSmem* m
       in[u].al = ld4(Alc + idx);
       in[u].L = ld4(L + idx);
       in[u].dtp = *reinterpret_cast<const uint2*>(dtp + idx);
+      // as many slices as this product (the bound of next_slices)
       const __nv_bfloat16* Drow = P->Dcat + (int64_t)i * P->cat_ld + j0;
-#pragma unroll
-      for (int sl = 0; sl < 3; ++sl)
-        in[u].D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+      in[u].D[0] = *reinterpret_cast<const uint2*>(Drow);
+      in[u].D[1] = ti.S > 1 ? *reinterpret_cast<const uint2*>(Drow + ld) : make_uint2(0u, 0u);
+      in[u].D[2] = ti.S > 2 ? *reinterpret_cast<const uint2*>(Drow + 2 * (int64_t)ld) : make_uint2(0u, 0u);
     }
   }
 #pragma unroll
@@ -711,9 +712,9 @@ __device__ __forceinline__ void gc_epilogue_columns(const GTileInfo& ti, GSmem* 
       in[u].L = ld4(L + idx);
       in[u].dtp = *reinterpret_cast<const uint2*>(dtp + idx);
       const __nv_bfloat16* Drow = P->Dcat + (int64_t)(2 * i) * P->cat_ld + 2 * jc0;
-#pragma unroll
-      for (int sl = 0; sl < 3; ++sl)
-        in[u].D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+      in[u].D[0] = *reinterpret_cast<const uint2*>(Drow);
+      in[u].D[1] = ti.S > 1 ? *reinterpret_cast<const uint2*>(Drow + ld) : make_uint2(0u, 0u);
+      in[u].D[2] = ti.S > 2 ? *reinterpret_cast<const uint2*>(Drow + 2 * (int64_t)ld) : make_uint2(0u, 0u);
     }
   }
 #pragma unroll
