@@ -6,10 +6,14 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
+#include <functional>
 #include <mutex>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -671,6 +675,32 @@ int group_tile_n(int n, int wmax) {
 
 
 // Lays out every problem's work arrays in one arena at `base` (nullptr: size only).
+// One problem's work arrays, in a fixed order, from the carve position c.
+static void carve_problem(GProb& P, Carve& c) {
+  const int np = P.n, nr = P.nr, ld = P.ld;
+  const int w = P.cplx ? 2 : 1;     // values per column parameter (re, im)
+  P.th_hi = c.take<float>(ld); P.th_lo = c.take<float>(ld);
+  P.d = c.take<double>(w * ld); P.E = c.take<double>(w * ld);
+  P.e_col = c.take<float>(w * ld); P.dprev_col = c.take<float>(w * ld);
+  P.part = c.take<float>((size_t)(2 + 2 * w) * P.ntm * ld);
+  P.rowpart = c.take<float>((size_t)((np + 127) / 128) * ld);
+  P.Dcat = c.take<__nv_bfloat16>((size_t)3 * ld * nr);
+  P.cat_ld = (int64_t)3 * ld;
+  for (int q = 0; q < 2; ++q) { P.A_hi[q] = c.take<float>((size_t)ld * np); P.A_lo[q] = c.take<float>((size_t)ld * np); }
+  for (int q = 0; q < 2; ++q) P.dt[q] = c.take<__nv_bfloat16>((size_t)ld * np);
+  P.L = c.take<float>((size_t)ld * np);
+}
+
+// Lays the planned problems' arrays out in the arena at `base` (a plan made with
+// base == nullptr keeps its work lists; only the pointers change).
+void place_group(GroupPlan& g, char* base, IterState* states_dev) {
+  Carve c{base};
+  for (size_t p = 0; p < g.probs.size(); ++p) {
+    g.probs[p].st = states_dev + p;
+    carve_problem(g.probs[p], c);
+  }
+}
+
 void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const double* const* theta,
                 const double* const* delta, const int64_t* ld_delta, const double* lambda,
                 double* const* A_out, const int64_t* ld_a, double* const* E_out, char* base,
@@ -696,17 +726,7 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
     P.ld_a = ld_a[p];
     P.E_out = E_out[p];
     P.st = states_dev + p;
-    const int w = cplx ? 2 : 1;     // values per column parameter (re, im)
-    P.th_hi = c.take<float>(ld); P.th_lo = c.take<float>(ld);
-    P.d = c.take<double>(w * ld); P.E = c.take<double>(w * ld);
-    P.e_col = c.take<float>(w * ld); P.dprev_col = c.take<float>(w * ld);
-    P.part = c.take<float>((size_t)(2 + 2 * w) * P.ntm * ld);
-    P.rowpart = c.take<float>((size_t)((np + 127) / 128) * ld);
-    P.Dcat = c.take<__nv_bfloat16>((size_t)3 * ld * nr);
-    P.cat_ld = (int64_t)3 * ld;
-    for (int q = 0; q < 2; ++q) { P.A_hi[q] = c.take<float>((size_t)ld * np); P.A_lo[q] = c.take<float>((size_t)ld * np); }
-    for (int q = 0; q < 2; ++q) P.dt[q] = c.take<__nv_bfloat16>((size_t)ld * np);
-    P.L = c.take<float>((size_t)ld * np);
+    carve_problem(P, c);
     for (int t = 0; t < P.ntm * P.ntn; ++t) g.tiles.push_back(make_int2(p, t));
     const int ntn128 = (np + 127) / 128;
     if (cplx) {
@@ -723,6 +743,38 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
   }
   g.bytes = (size_t)round_up((int64_t)c.off, 256) + 256;
   sort_tiles(g.tiles, g.probs.data());
+}
+
+// Runs enc(p) for p in [0, count) on up to 16 host threads (TMA descriptor encoding
+// is a pure host computation of about a microsecond each); rethrows the first Fail.
+void encode_group_maps(const GProb* probs, int count, const std::function<void(int)>& enc) {
+  (void)probs;
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nt = (int)std::min<unsigned>(std::min(16u, hw), (unsigned)std::max(1, count / 256));
+  if (nt <= 1) {
+    for (int p = 0; p < count; ++p) enc(p);
+    return;
+  }
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::atomic<int> err{0};
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&, t] {
+      try {
+        // a new host thread has no current context until it names the device
+        CK(cudaSetDevice(dev));
+        for (int p = t; p < count; p += nt) enc(p);
+      } catch (Fail f) {
+        int z = 0;
+        err.compare_exchange_strong(z, (int)f.st);
+      } catch (...) {
+        int z = 0;
+        err.compare_exchange_strong(z, (int)DPT_ERR_CUDA);
+      }
+    });
+  for (auto& x : th) x.join();
+  if (err.load()) throw Fail{(dpt_status)err.load()};
 }
 
 // Largest tiles first (cost ~ K extent x tile width), problems kept contiguous
@@ -767,12 +819,7 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
     int4* blk = c.take<int4>(g.blk_r.size() + g.blk_c.size());
     int* flags = c.take<int>(4);      // [0] running count, [1] timeout
     char* ar = c.take<char>(arena);
-    plan_group(g, count, cplx, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, ar, st);
-    for (int p = 0; p < count; ++p) {
-      GProb& P = g.probs[p];
-      P.tmA = make_tmap_bf16(P.Dcat, (uint64_t)3 * P.ld, P.nr, (uint64_t)3 * P.ld, 128);
-      for (int q = 0; q < 2; ++q) P.tmB[q] = make_tmap_bf16(P.dt[q], P.nr, P.n, P.ld, P.bn);
-    }
+    place_group(g, ar, st);
     std::vector<IterState> hs(count);
     for (int p = 0; p < count; ++p) {
       IterState& h = hs[p];
@@ -814,6 +861,20 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
     CK(launch_gc_iter0(probs, blk + n_blk_r, n_blk_c, s));
     auto ctrl = [&]() { CK(launch_g_ctrl(probs, count, max_n, cplx != 0, flags, s)); };
     ctrl();
+    // The product needs each problem's three TMA descriptors (tmA, tmB[2], the first
+    // 384 bytes of its table entry): encoded on host threads while the device runs the
+    // preparation above, then written into the table with one strided copy.
+    struct Maps { CUtensorMap m[3]; };
+    std::vector<Maps> maps(count);
+    encode_group_maps(g.probs.data(), count, [&](int p) {
+      const GProb& P = g.probs[p];
+      maps[p].m[0] = make_tmap_bf16(P.Dcat, (uint64_t)3 * P.ld, P.nr, (uint64_t)3 * P.ld, 128);
+      for (int q = 0; q < 2; ++q) maps[p].m[1 + q] = make_tmap_bf16(P.dt[q], P.nr, P.n, P.ld, P.bn);
+    });
+    static_assert(offsetof(GProb, tmA) == 0 && offsetof(GProb, tmB) == sizeof(CUtensorMap),
+                  "descriptors lead the table entry");
+    CK(cudaMemcpy2DAsync(probs, sizeof(GProb), maps.data(), sizeof(Maps), sizeof(Maps), count,
+                         cudaMemcpyHostToDevice, s));
     Prof prof;
     prof.on = o.profile != 0;
     prof.launches = 5;

@@ -8,6 +8,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 #include "../../include/dpt.h"
@@ -86,6 +87,13 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
                 const double* const* delta, const int64_t* ld_delta, const double* lambda,
                 double* const* A_out, const int64_t* ld_a, double* const* E_out, char* base,
                 IterState* states_dev);
+
+// Re-lays a plan's arrays out at `base` (same order as plan_group), states at
+// states_dev + p; the work lists are unchanged.
+void place_group(GroupPlan& g, char* base, IterState* states_dev);
+
+// Runs enc(p) for every problem on a few host threads (descriptor encoding).
+void encode_group_maps(const GProb* probs, int count, const std::function<void(int)>& enc);
 
 // Orders a product tile list (problem, tile) by decreasing cost.
 void sort_tiles(std::vector<int2>& tiles, const GProb* probs);

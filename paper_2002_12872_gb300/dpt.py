@@ -258,6 +258,67 @@ def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
     return res
 
 
+class Batch:
+    """A grouped solve (dpt_solve_batched) with its argument arrays built once.
+
+    thetas / deltas: sequences of CUDA tensors, deltas column-major (e.g. from
+    colmajor_tensor), all real or all complex128 (theta and lambda real).  The
+    outputs A_outs / E_outs are allocated here unless given.  solve() can be called
+    repeatedly; it writes the outputs in place."""
+
+    def __init__(self, thetas, deltas, lams, *, A_outs=None, E_outs=None):
+        import torch
+        count = len(thetas)
+        cplx = deltas[0].is_complex()
+        want = torch.complex128 if cplx else torch.float64
+        self.count, self.cplx = count, cplx
+        ns, th, ds, ldd, keep = [], [], [], [], []
+        for t, d in zip(thetas, deltas):
+            if t.dtype != torch.float64:
+                t = t.to(torch.float64)
+            if d.dtype != want:
+                d = d.to(want)
+            n0 = d.shape[0]
+            if not (d.stride(0) == 1 and d.stride(1) >= n0):
+                d = d.t().contiguous().t()
+            ns.append(int(t.shape[0]))
+            th.append(t.data_ptr())
+            ds.append(d.data_ptr())
+            ldd.append(d.stride(1))
+            keep.append((t, d))
+        if A_outs is None:
+            A_outs = [torch.empty((n, n), dtype=want, device=thetas[0].device).t() for n in ns]
+        if E_outs is None:
+            E_outs = [torch.empty(n, dtype=want, device=thetas[0].device) for n in ns]
+        self.A_outs, self.E_outs, self._keep = A_outs, E_outs, keep
+        P = ctypes.c_void_p
+        self._n = (ctypes.c_int64 * count)(*ns)
+        self._th = (P * count)(*th)
+        self._d = (P * count)(*ds)
+        self._ldd = (ctypes.c_int64 * count)(*ldd)
+        self._lam = (ctypes.c_double * count)(*[float(x) for x in lams])
+        self._a = (P * count)(*[a.data_ptr() for a in A_outs])
+        self._lda = (ctypes.c_int64 * count)(*[a.stride(1) for a in A_outs])
+        self._e = (P * count)(*[e.data_ptr() for e in E_outs])
+        self._dev = thetas[0]
+
+    def solve(self, *, tol=1e-12, max_iter=200, graph_iters=None, max_slices=None,
+              slice_tol=None, profile=False, stream=None, check=True):
+        """Returns (A_outs, E_outs, infos)."""
+        infos = (Info * self.count)()
+        o = options(tol=tol, max_iter=max_iter, prec="mixed", graph_iters=graph_iters,
+                    max_slices=max_slices, slice_tol=slice_tol, profile=int(bool(profile)))
+        st = lib().dpt_solve_batched(self.count, C128 if self.cplx else R64, self._n, self._th,
+                                     self._d, self._ldd, self._lam, ctypes.byref(o), self._a,
+                                     self._lda, self._e, infos, _stream_of(self._dev, stream))
+        res = (self.A_outs, self.E_outs, [i.as_dict() for i in infos])
+        if check and st != OK:
+            err = RuntimeError(f"dpt_solve_batched: {status_string(st)}")
+            err.result = res
+            raise err
+        return res
+
+
 def solve_batched(thetas, deltas, lams, *, tol=1e-12, max_iter=200, graph_iters=None,
                   max_slices=None, slice_tol=None, profile=False, A_outs=None, E_outs=None,
                   stream=None, check=True):
@@ -265,41 +326,11 @@ def solve_batched(thetas, deltas, lams, *, tol=1e-12, max_iter=200, graph_iters=
     complex (complex128 deltas; theta and lambda real).
 
     thetas / deltas: sequences of CUDA tensors (deltas column-major, e.g. from
-    colmajor_tensor).  Returns (As, Es, infos)."""
-    import torch
-    count = len(thetas)
-    cplx = deltas[0].is_complex()
-    ns = (ctypes.c_int64 * count)(*[int(t.shape[0]) for t in thetas])
-    th = (ctypes.c_void_p * count)(*[t.data_ptr() for t in thetas])
-    ds, ldd = [], []
-    keep = []
-    for d in deltas:
-        ptr, ld, k = _colmajor(d, cplx)
-        ds.append(ptr); ldd.append(ld); keep.append(k)
-    dp = (ctypes.c_void_p * count)(*ds)
-    lddp = (ctypes.c_int64 * count)(*ldd)
-    lam = (ctypes.c_double * count)(*[float(x) for x in lams])
-    dt = torch.complex128 if cplx else torch.float64
-    if A_outs is None:
-        A_outs = [torch.empty((int(t.shape[0]),) * 2, dtype=dt, device=t.device).t()
-                  for t in thetas]
-    if E_outs is None:
-        E_outs = [torch.empty(t.shape, dtype=dt, device=t.device) for t in thetas]
-    ap = (ctypes.c_void_p * count)(*[a.data_ptr() for a in A_outs])
-    lda = (ctypes.c_int64 * count)(*[a.stride(1) for a in A_outs])
-    ep = (ctypes.c_void_p * count)(*[e.data_ptr() for e in E_outs])
-    infos = (Info * count)()
-    o = options(tol=tol, max_iter=max_iter, prec="mixed", graph_iters=graph_iters,
-                max_slices=max_slices, slice_tol=slice_tol, profile=int(bool(profile)))
-    st = lib().dpt_solve_batched(count, C128 if cplx else R64, ns, th, dp, lddp, lam,
-                                 ctypes.byref(o), ap, lda, ep, infos,
-                                 _stream_of(thetas[0], stream))
-    res = (A_outs, E_outs, [i.as_dict() for i in infos])
-    if check and st != OK:
-        err = RuntimeError(f"dpt_solve_batched: {status_string(st)}")
-        err.result = res
-        raise err
-    return res
+    colmajor_tensor).  Returns (As, Es, infos).  For repeated solves of the same
+    problems build a Batch once and call its solve()."""
+    return Batch(thetas, deltas, lams, A_outs=A_outs, E_outs=E_outs).solve(
+        tol=tol, max_iter=max_iter, graph_iters=graph_iters, max_slices=max_slices,
+        slice_tol=slice_tol, profile=profile, stream=stream, check=check)
 
 
 def solve_dominant(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, prec="mixed", tol=1e-12,
