@@ -102,10 +102,11 @@ typedef struct {
                               later product uses two once its increment's largest entry
                               is below 2^-8 of the first increment's, one once below
                               2^-16 of it or below slice_tol (default 1e-8) */
-  int32_t cta_pair;        /* real mixed full solve: nonzero runs the product as CTA
-                              pairs (tcgen05 cta_group::2, 256-row tiles split over two
-                              SMs) where clusters of two can be resident; 0 (default)
-                              one CTA per 128-row tile */
+  int32_t cta_pair;        /* real mixed full solve: nonzero (default) runs the product
+                              as CTA pairs (tcgen05 cta_group::2, 256-row tiles split
+                              over two SMs, epilogue inputs staged in the shared memory
+                              this frees) where clusters of two can be resident; 0 one
+                              CTA per 128-row tile */
 } dpt_options;
 
 typedef struct {

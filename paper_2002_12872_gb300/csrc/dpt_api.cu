@@ -1006,7 +1006,7 @@ void dpt_options_default(dpt_options* o) {
   o->max_slices = 3;
   o->slice_tol = 1e-8;
   o->profile = 0;
-  o->cta_pair = 0;
+  o->cta_pair = 1;
 }
 
 const char* dpt_status_string(dpt_status s) {

@@ -63,6 +63,20 @@ struct __align__(16) GemmSmemMisc {
 };
 constexpr int SMEM_BYTES = SMEM_TILES + SMEM_X + 1024 + (int)sizeof(GemmSmemMisc);
 
+// CTA-pair layout: a smaller operand ring (a stage holds A and half of B: 30 KB at
+// bn = 224, four stages), the accumulator staging, and two buffers of epilogue
+// inputs filled by per-thread asynchronous copies one sub-chunk (16 columns) ahead.
+// The pair kernel's epilogue has 16 warps (its inputs sit in shared memory, not in
+// registers, so 576 threads fit the register file); each warp updates one column
+// of every 16-column sub-chunk.
+constexpr int P_RING = 4 * (A_TILE + 112 * BK * 2);     // 122880 B
+constexpr int P_EPI_WARPS = 16;
+constexpr int P_NTHREADS = 64 + 32 * P_EPI_WARPS;       // 576
+constexpr int EB_COL = 80;                              // bytes per lane and column
+constexpr int EB_BYTES = P_EPI_WARPS * 32 * EB_COL;     // one column per warp: 40960 B
+constexpr int P_SMEM_BYTES = P_RING + SMEM_X + 2 * EB_BYTES + 1024 + (int)sizeof(GemmSmemMisc);
+static_assert(P_SMEM_BYTES <= 232448, "CTA-pair shared memory over the per-block limit");
+
 // ---------------------------------------------------------------------------
 // Preparation: transpose Delta (column-major FP64) into row-major FP32 and into
 // the BF16 slices D1 + D2 + D3 (row-major, concatenated along K), zeroing the
@@ -559,6 +573,143 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 }
 
 // ---------------------------------------------------------------------------
+// Staged epilogue (CTA-pair kernel).  The column walk of k_gemm_epi, with its
+// global inputs brought into shared memory by the lane that will use them, with
+// cp.async one sub-chunk ahead, so that their latency overlaps the arithmetic of
+// the previous sub-chunk (and, for a tile's first sub-chunk, the wait for its
+// accumulator).  A sub-chunk is 16 columns, one per warp.  Each lane keeps its own
+// slots (80 B per column: A_hi, A_lo, L as float4, then dt_{k-1} and the Delta
+// slices as BF16 quadruples), so no barrier guards them.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint8_t* eb_f4(uint8_t* eb, int ew, int u, int f, int lane) {
+  return eb + ((ew + u) * 3 + f) * 512 + lane * 16;
+}
+__device__ __forceinline__ uint8_t* eb_u2(uint8_t* eb, int ew, int u, int g, int lane) {
+  return eb + P_EPI_WARPS * 3 * 512 + ((ew + u) * 4 + g) * 256 + lane * 8;
+}
+__device__ __forceinline__ void p_epi_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * P_EPI_WARPS) : "memory");
+}
+__device__ __forceinline__ bool p_epi_bar_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.and.pred po, 1, %2, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(32 * P_EPI_WARPS)
+      : "memory");
+  return r != 0;
+}
+
+// Issue the copies of sub-chunk sc (columns 16 sc .. 16 sc + 15) of tile (m0, n0).
+__device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, int S, uint8_t* eb,
+                                             int ew, int lane, int m0, int n0, int sc) {
+  const float* Ahc = c1 ? p.A_hi[1] : p.A_hi[0];
+  const float* Alc = c1 ? p.A_lo[1] : p.A_lo[0];
+  const __nv_bfloat16* dtp = c1 ? p.dt[0] : p.dt[1];
+  const int j0 = m0 + 4 * lane;
+#pragma unroll
+  for (int u = 0; u < 1; ++u) {
+    const int i = n0 + 16 * sc + ew + u;
+    if (i >= p.n) continue;
+    const int64_t idx = (int64_t)i * p.ld + j0;
+    cp_async16(eb_f4(eb, ew, u, 0, lane), Ahc + idx);
+    cp_async16(eb_f4(eb, ew, u, 1, lane), Alc + idx);
+    cp_async16(eb_f4(eb, ew, u, 2, lane), p.L + idx);
+    cp_async8(eb_u2(eb, ew, u, 0, lane), dtp + idx);
+    const __nv_bfloat16* Drow = p.Dcat + (int64_t)i * p.cat_ld + j0;
+    for (int sl = 0; sl < S; ++sl)
+      cp_async8(eb_u2(eb, ew, u, 1 + sl, lane), Drow + (int64_t)sl * p.ld);
+  }
+}
+
+// Update this warp's column of sub-chunk sc from the staged inputs in eb and
+// the accumulator chunk in Xs (which holds columns c0 .. c0 + 31, c0 = 32 (sc / 2)).
+__device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc* ms,
+                                            const float* Xs, const uint8_t* eb, int S, int ew,
+                                            int lane, int tm, int m0, int n0, int sc, float& mx) {
+  const int n = p.n, ld = p.ld;
+  const bool c1 = (ms->cur != 0);
+  float* __restrict__ Ahn = c1 ? p.A_hi[0] : p.A_hi[1];
+  float* __restrict__ Aln = c1 ? p.A_lo[0] : p.A_lo[1];
+  __nv_bfloat16* __restrict__ dtn_out = c1 ? p.dt[1] : p.dt[0];
+  float* __restrict__ L = p.L;
+  const float lam = p.lam;
+  const int r0 = 4 * lane;
+  const int j0 = m0 + r0;
+  const float4 thj_h = ld4(p.th_hi + j0);
+  const float4 thj_l = ld4(p.th_lo + j0);
+  const int c0 = 32 * (sc >> 1);
+#pragma unroll
+  for (int u = 0; u < 1; ++u) {
+    const int cl = 16 * sc + ew + u;
+    const int i = n0 + cl;
+    if (i >= n) continue;   // uniform across the warp
+    uint8_t* e8 = const_cast<uint8_t*>(eb);
+    const float4 ah4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 0, lane));
+    const float4 al4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 1, lane));
+    const float4 L4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 2, lane));
+    const uint2 dtp = *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 0, lane));
+    uint2 D[3];
+    D[0] = *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 1, lane));
+    D[1] = S > 1 ? *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 2, lane)) : make_uint2(0u, 0u);
+    D[2] = S > 2 ? *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 3, lane)) : make_uint2(0u, 0u);
+    const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * BM + r0);
+    const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
+    const float thh = ms->thh[cl], thl = ms->thl[cl];
+    float4 oh, ol, oL;
+    uint32_t ob[4];
+    float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = j0 + e;
+      const float ah = f4(ah4, e), al = f4(al4, e);
+      float nh = 0.f, nl = 0.f, Ln = 0.f, dnew = 0.f;
+      if (j == i) {
+        nh = 1.f;
+        a2 += 1.f;
+      } else if (j < n) {
+        const float R = f4(L4, e) + lam * (f4(x4, e) - ah * e_i - bf_at(dtp, e) * dp_i);
+        float gh, gl;
+        ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
+        // the increment is rounded to BF16 and the remainder keeps R - Gap dnew
+        // exactly, so any reciprocal close to 1/gap serves
+        dnew = bf16_round(R * rcp_approx(gh));
+        Ln = fmaf(-gh, dnew, R) - gl * dnew;
+        ff_add_f(ah, al, dnew, nh, nl);
+        r2 = fmaf(R, R, r2);
+        a2 = fmaf(ah, ah, a2);
+        const float p1 = bf_at(D[0], e) * dnew;
+        const float p23 = fmaf(bf_at(D[1], e), dnew, bf_at(D[2], e) * dnew);
+        float sh, se;
+        two_sum(eh, p1, sh, se);
+        se += el + p23;
+        fast_two_sum(sh, se, eh, el);
+        mx = fmaxf(mx, fabsf(dnew));
+      }
+      f4set(oh, e, nh);
+      f4set(ol, e, nl);
+      f4set(oL, e, Ln);
+      ob[e] = bf_bits(dnew);
+    }
+    const int64_t idx = (int64_t)i * ld + j0;
+    st4(Ahn + idx, oh);
+    st4(Aln + idx, ol);
+    st4(L + idx, oL);
+    *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+    warp_sum_ff(r2, a2, eh, el);
+    if (lane == 0) {
+      p.part[((int64_t)0 * p.ntm + tm) * ld + i] = r2;
+      p.part[((int64_t)1 * p.ntm + tm) * ld + i] = a2;
+      p.part[((int64_t)2 * p.ntm + tm) * ld + i] = eh;
+      p.part[((int64_t)3 * p.ntm + tm) * ld + i] = el;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // CTA-pair form of the product kernel (tcgen05 cta_group::2).  The two CTAs of a
 // cluster compute one 256 x bn output tile: each loads its own 128 rows of the A
 // operand (Delta slices) and half of the B operand (bn/2 increment columns) into
@@ -575,7 +726,7 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 // leader's acc_empty[b] (count 2).  Every thread of both CTAs reaches the final
 // cluster barrier, also when a bounded wait has given up.
 // ---------------------------------------------------------------------------
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(NTHREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
 k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
                 const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -584,8 +735,9 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   // CTAs of a pair take the same branch
   if (*((volatile int*)&st->status) != ST_RUNNING) return;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* Xs = reinterpret_cast<float*>(smem + SMEM_TILES);
-  GemmSmemMisc* ms = (GemmSmemMisc*)(smem + SMEM_TILES + SMEM_X);
+  float* Xs = reinterpret_cast<float*>(smem + P_RING);
+  uint8_t* EB = smem + P_RING + SMEM_X;                       // two epilogue input buffers
+  GemmSmemMisc* ms = (GemmSmemMisc*)(smem + P_RING + SMEM_X + 2 * EB_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_ctarank();
   const int bn = p.bn, bh = bn / 2;
@@ -614,7 +766,7 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   const int kb_per_slice = p.ld / BK;
   const int nk = S * kb_per_slice;
   const uint32_t stage_bytes = (uint32_t)A_TILE + (uint32_t)bh * BK * 2;   // multiple of 1024
-  const int nst = min(MAX_STAGES, (int)(SMEM_TILES / stage_bytes));
+  const int nst = min(MAX_STAGES, (int)(P_RING / stage_bytes));
   const CUtensorMap* tmB = (ms->cur == 1) ? &tmB0 : &tmB1;
   unsigned* tflag = &st->timeout;
 
@@ -682,18 +834,27 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     // ---- epilogue (both CTAs, each on its own 128 rows) ----
     const int ew = warp - 2;
     const int qd = warp & 3;
-    const int half = ew >> 2;
+    const int q4 = ew >> 2;                // which 8 of a chunk's 32 columns this warp stages
     const int et = threadIdx.x - 64;
     const uint32_t acc_empty_leader = mapa_shared(&ms->acc_empty[0], 0);
+    const bool c1 = (ms->cur != 0);
+    const int nsub = bn / 16;              // sub-chunks per tile (even: bn is a multiple of 32)
     float mx = 0.f;
     int lt = 0;
+    // the first tile's first sub-chunk, while its products run
+    if (pair < ntiles) {
+      const int tm = 2 * (pair / ntn) + (int)rank;
+      if (tm < p.ntm) epi_prefetch(p, c1, S, EB, ew, lane, tm * BM, (pair % ntn) * bn, 0);
+    }
+    cp_async_commit();
     for (int t = pair; t < ntiles; t += npairs, ++lt) {
       const int tm2 = t / ntn, tn = t % ntn;
       const int tm = 2 * tm2 + (int)rank;
       const int m0 = tm * BM, n0 = tn * bn;
       const int b = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
-      epi_bar();
+      const bool work = tm < p.ntm;        // rows of a pair tile beyond the padded matrix
+      p_epi_bar();
       if (et < bn) {
         const int i = n0 + et;
         const bool v = i < p.n;
@@ -708,26 +869,41 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       bool all_ok = true;
 #pragma unroll 1
       for (int c0 = 0; c0 < bn; c0 += XCH) {
-        if (c0 > 0) epi_bar();
+        if (c0 > 0) p_epi_bar();
         if (ok) {
-          float x[16];
-          const int cc = half * 16;
-          tmem_ld_x16(src + (uint32_t)(c0 + cc), x);
+          float x[8];
+          const int cc = q4 * 8;
+          tmem_ld_x8(src + (uint32_t)(c0 + cc), x);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) Xs[(cc + c) * BM + qd * 32 + lane] = x[c];
+          for (int c = 0; c < 8; ++c) Xs[(cc + c) * BM + qd * 32 + lane] = x[c];
         }
         if (c0 + XCH == bn) tc_fence_before();
-        all_ok = epi_bar_and(ok);
+        all_ok = p_epi_bar_and(ok);
         if (c0 + XCH == bn && et == 0) {
           if (rank == 0) mbar_arrive(&ms->acc_empty[b]);
           else mbar_arrive_remote(acc_empty_leader + (uint32_t)b * 8u);
         }
         if (!all_ok) break;
-        // rows of a pair tile beyond the padded matrix hold no work
-        if (tm < p.ntm) epilogue_columns(p, ms, Xs, ew, lane, tm, m0, n0, c0, mx);
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          const int sc = c0 / 16 + h;
+          // copies of the next sub-chunk: this tile's, or the next tile's first
+          uint8_t* nb = EB + ((sc + 1) & 1) * EB_BYTES;
+          if (sc + 1 < nsub) {
+            if (work) epi_prefetch(p, c1, S, nb, ew, lane, m0, n0, sc + 1);
+          } else if (t + npairs < ntiles) {
+            const int tn2 = 2 * ((t + npairs) / ntn) + (int)rank;
+            if (tn2 < p.ntm)
+              epi_prefetch(p, c1, S, nb, ew, lane, tn2 * BM, ((t + npairs) % ntn) * bn, 0);
+          }
+          cp_async_commit();
+          cp_async_wait<1>();              // this lane's copies of sub-chunk sc have landed
+          if (work) epi_compute(p, ms, Xs, EB + (sc & 1) * EB_BYTES, S, ew, lane, tm, m0, n0, sc, mx);
+        }
       }
       if (!all_ok) break;
     }
+    cp_async_wait<0>();                    // no copy into shared memory outlives the walk
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0 && mx > 0.f) atomicMax(&p.st->dmax_bits, __float_as_uint(mx));
   }
@@ -848,7 +1024,7 @@ cudaError_t mixed_set_attributes() {
                                        SMEM_BYTES);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_gemm_epi_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              SMEM_BYTES);
+                              P_SMEM_BYTES);
 }
 
 // Clusters of two that can be resident at once (0: the pair form cannot run).  The
@@ -864,8 +1040,8 @@ int mixed_pair_clusters() {
   if (known[dev]) return cached[dev];
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2, 1, 1);
-  cfg.blockDim = dim3(NTHREADS, 1, 1);
-  cfg.dynamicSmemBytes = SMEM_BYTES;
+  cfg.blockDim = dim3(P_NTHREADS, 1, 1);
+  cfg.dynamicSmemBytes = P_SMEM_BYTES;
   cfg.attrs = nullptr;
   cfg.numAttrs = 0;
   int n = 0;
@@ -899,7 +1075,7 @@ cudaError_t launch_gemm_epi_pair(const CUtensorMap& tmA, const CUtensorMap& tmB0
   if (p.bn < 64 || p.bn > BN || p.bn % 32 || npairs < 1) return cudaErrorInvalidValue;
   const int ntiles = ((p.n + p.bn - 1) / p.bn) * ((p.n + 2 * BM - 1) / (2 * BM));
   const int pairs = ntiles < npairs ? ntiles : npairs;
-  k_gemm_epi_pair<<<2 * pairs, NTHREADS, SMEM_BYTES, s>>>(tmA, tmB0, tmB1, p);
+  k_gemm_epi_pair<<<2 * pairs, P_NTHREADS, P_SMEM_BYTES, s>>>(tmA, tmB0, tmB1, p);
   return cudaGetLastError();
 }
 

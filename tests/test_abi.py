@@ -38,6 +38,7 @@ def test_defaults_and_status_strings(lib):
     from paper_2002_12872_gb300 import dpt
     o = dpt.options()
     assert o.tol == 1e-12 and o.max_iter == 200 and o.prec == 1 and o.max_slices == 3
+    assert o.cta_pair == 1
     assert dpt.status_string(-2) == "DPT_ERR_DEGENERATE"
     assert dpt.status_string(0) == "DPT_OK"
 
