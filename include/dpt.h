@@ -107,6 +107,14 @@ typedef struct {
                               over two SMs, epilogue inputs staged in the shared memory
                               this frees) where clusters of two can be resident; 0 one
                               CTA per 128-row tile */
+  int32_t grouped_form;    /* grouped solves, complex single solves and the server:
+                              1 (what 0, the default, selects) one CTA per 128-row tile
+                              with the epilogue reading global memory; 2 one CTA per
+                              tile with the epilogue inputs staged in shared memory
+                              (tiles at most 128 wide: faster for groups of small
+                              problems); 3 CTA pairs (256-row tiles).  Results of one
+                              problem are identical across entry points using the
+                              same form. */
 } dpt_options;
 
 typedef struct {
@@ -121,8 +129,10 @@ typedef struct {
   int32_t product_launches;  /* product kernels that did work (one per iteration) */
   double product_ms;       /* with opt->profile: summed device time of those
                               product kernels, else 0 */
-  int32_t cta_pair;        /* real mixed full solve: 1 when the products ran in the
-                              CTA-pair form, else 0 */
+  int32_t cta_pair;        /* mixed path: 1 when the products ran in the CTA-pair
+                              form, else 0 */
+  int32_t grouped_form;    /* grouped solves: the product form that ran (see
+                              dpt_options.grouped_form), else 0 */
 } dpt_info;
 
 /* Fill *opt with the defaults listed above. */

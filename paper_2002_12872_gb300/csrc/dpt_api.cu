@@ -704,7 +704,7 @@ void place_group(GroupPlan& g, char* base, IterState* states_dev) {
 void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const double* const* theta,
                 const double* const* delta, const int64_t* ld_delta, const double* lambda,
                 double* const* A_out, const int64_t* ld_a, double* const* E_out, char* base,
-                IterState* states_dev) {
+                IterState* states_dev, int form) {
   Carve c{base};
   g.probs.assign(count, GProb{});
   g.tiles.clear(); g.prep_r.clear(); g.prep_c.clear(); g.blk_r.clear(); g.blk_c.clear();
@@ -714,7 +714,7 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
     const int nr = cplx ? 2 * np : np;
     const int ld = (int)round_up(nr, 128);
     P.n = np; P.nr = nr; P.cplx = cplx; P.ld = ld; P.ntm = (nr + 127) / 128;
-    P.bn = group_tile_n(np, 256);
+    P.bn = group_tile_n(np, gform_wmax(form));
     P.ntn = (np + P.bn - 1) / P.bn;
     P.lam = (float)lambda[p];
     P.lam_lo = (float)(lambda[p] - (double)P.lam);
@@ -727,7 +727,8 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
     P.E_out = E_out[p];
     P.st = states_dev + p;
     carve_problem(P, c);
-    for (int t = 0; t < P.ntm * P.ntn; ++t) g.tiles.push_back(make_int2(p, t));
+    const int rows = (nr + gform_rows(form) - 1) / gform_rows(form);
+    for (int t = 0; t < rows * P.ntn; ++t) g.tiles.push_back(make_int2(p, t));
     const int ntn128 = (np + 127) / 128;
     if (cplx) {
       for (int by = 0; by < (np + 31) / 32; ++by)
@@ -777,6 +778,34 @@ void encode_group_maps(const GProb* probs, int count, const std::function<void(i
   if (err.load()) throw Fail{(dpt_status)err.load()};
 }
 
+// The default is the one-CTA form everywhere (batched, complex single solves and the
+// server), so that a problem's result is the same through every entry point.  Measured on
+// GB300 per product launch: 20,000 problems of n in [32, 512]: one-CTA 6.97 ms, staged
+// 6.56 ms, pair 7.01 ms; the 48-problem served mix (n in [64, 4096] complex): 2.07, 3.33,
+// 2.09 ms (the staged form's tiles of at most 128 columns cost the large problems).
+int choose_gform(int opt_form, int count, const int64_t* n, int* npairs) {
+  (void)count;
+  (void)n;
+  *npairs = 0;
+  int form = opt_form == 0 ? G_PLAIN : opt_form;
+  if (form == G_PAIR) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      *npairs = std::min(nsm / 2, g_pair_clusters());
+    cudaGetLastError();
+    if (*npairs <= 0) form = G_STAGED;   // clusters of two cannot be resident
+  }
+  return form;
+}
+
+cudaError_t launch_gform(int form, const GProb* probs, const int2* tiles, int ntiles,
+                         unsigned* timeout, bool cplx, int npairs, cudaStream_t s) {
+  if (form == G_PAIR) return launch_g_gemm_epi_pair(probs, tiles, ntiles, timeout, cplx, npairs, s);
+  if (form == G_STAGED) return launch_g_gemm_epi_staged(probs, tiles, ntiles, timeout, cplx, s);
+  return launch_g_gemm_epi(probs, tiles, ntiles, timeout, cplx, s);
+}
+
 // Largest tiles first (cost ~ K extent x tile width), problems kept contiguous
 // among equal costs.
 void sort_tiles(std::vector<int2>& tiles, const GProb* probs) {
@@ -796,8 +825,12 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
                          const double* lambda, const dpt_options& o, double* const* A_out,
                          const int64_t* ld_a, double* const* E_out, dpt_info* infos,
                          cudaStream_t user) {
+  int npairs = 0;
+  const int form = choose_gform(o.grouped_form, count, n, &npairs);
+  const bool pair = form == G_PAIR;
   GroupPlan g;
-  plan_group(g, count, cplx, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, nullptr, nullptr);
+  plan_group(g, count, cplx, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, nullptr, nullptr,
+             form);
   const size_t arena = g.bytes;
   auto layout = [&](Carve& c) {
     c.take<IterState>(count);
@@ -869,7 +902,8 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
     encode_group_maps(g.probs.data(), count, [&](int p) {
       const GProb& P = g.probs[p];
       maps[p].m[0] = make_tmap_bf16(P.Dcat, (uint64_t)3 * P.ld, P.nr, (uint64_t)3 * P.ld, 128);
-      for (int q = 0; q < 2; ++q) maps[p].m[1 + q] = make_tmap_bf16(P.dt[q], P.nr, P.n, P.ld, P.bn);
+      for (int q = 0; q < 2; ++q)
+        maps[p].m[1 + q] = make_tmap_bf16(P.dt[q], P.nr, P.n, P.ld, gform_box(form, P.bn));
     });
     static_assert(offsetof(GProb, tmA) == 0 && offsetof(GProb, tmB) == sizeof(CUtensorMap),
                   "descriptors lead the table entry");
@@ -883,7 +917,8 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
     cudaGraphExec_t exec = nullptr;
     auto iter = [&](int q) {
       prof.before(q, s);
-      CK(launch_g_gemm_epi(probs, tiles, (int)g.tiles.size(), (unsigned*)(flags + 1), cplx != 0, s));
+      CK(launch_gform(form, probs, tiles, (int)g.tiles.size(), (unsigned*)(flags + 1), cplx != 0,
+                      npairs, s));
       prof.after(q, s);
       ctrl();
     };
@@ -931,6 +966,8 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
         infos[p].launches = prof.launches;
         infos[p].product_launches = prof.live;
         infos[p].product_ms = prof.ms;
+        infos[p].cta_pair = pair ? 1 : 0;
+        infos[p].grouped_form = form;
       }
     }
     CK(cudaEventRecord(b->ev, s));
@@ -1007,6 +1044,7 @@ void dpt_options_default(dpt_options* o) {
   o->slice_tol = 1e-8;
   o->profile = 0;
   o->cta_pair = 1;
+  o->grouped_form = 0;
 }
 
 const char* dpt_status_string(dpt_status s) {

@@ -975,6 +975,525 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
   }
 }
 
+// ===========================================================================
+// CTA-pair form of the grouped product (tcgen05 cta_group::2; see k_gemm_epi_pair
+// in dpt_full_mixed.cu for the single-problem kernel it follows).  A tile of the
+// list is (problem, 256-row x bn pair tile); the two CTAs of a cluster each load
+// their 128 rows of the problem's slices and half of its increment columns, the
+// leader issues the MMA, and each CTA runs a 16-warp epilogue on its own rows with
+// the inputs staged in shared memory by per-lane cp.async one 16-column sub-chunk
+// ahead.  The arithmetic per element is that of g_/gc_epilogue_columns, with the
+// approximate reciprocal (the increment is rounded to BF16 and the remainder keeps
+// R - Gap dt exactly, so any reciprocal close to 1/gap serves).
+// ===========================================================================
+constexpr int GP_EPI_WARPS = 16;
+constexpr int GP_NTHREADS = 64 + 32 * GP_EPI_WARPS;          // 576
+constexpr int GP_SLOT = G_A_TILE + 112 * G_BK * 2;           // 30720: A + half of B at bn <= 224
+constexpr int GP_STAGES = 4;
+constexpr int GP_RING = GP_STAGES * GP_SLOT;                   // 122880 (the planner caps bn at 224)
+constexpr int GP_EB_BYTES = GP_EPI_WARPS * 32 * 80;           // 40960: one column per warp
+constexpr int GP_SMEM_BYTES = GP_RING + G_SMEM_X + 2 * GP_EB_BYTES + 1024 + (int)sizeof(GSmem);
+static_assert(GP_SMEM_BYTES <= 232448, "grouped CTA-pair shared memory over the per-block limit");
+static_assert(GP_STAGES <= G_STAGES, "barrier slots");
+
+struct GPairTile {
+  const GProb* P;
+  int tm2, tn, bn, n0, S, cur, kbs;
+  bool live;
+};
+
+__device__ __forceinline__ GPairTile gp_tile(const GProb* probs, const int2* tiles, int t) {
+  GPairTile ti;
+  const int2 e = tiles[t];
+  ti.P = probs + e.x;
+  const IterState* st = ti.P->st;
+  ti.live = *((volatile const int*)&st->status) == ST_RUNNING;
+  ti.tm2 = e.y / ti.P->ntn;
+  ti.tn = e.y % ti.P->ntn;
+  ti.bn = ti.P->bn;
+  ti.n0 = ti.tn * ti.bn;
+  ti.S = st->slices;
+  ti.cur = st->cur;
+  ti.kbs = ti.P->ld / G_BK;
+  return ti;
+}
+
+__device__ __forceinline__ uint8_t* gp_f4(uint8_t* eb, int ew, int f, int lane) {
+  return eb + (ew * 3 + f) * 512 + lane * 16;
+}
+__device__ __forceinline__ uint8_t* gp_u2(uint8_t* eb, int ew, int g, int lane) {
+  return eb + GP_EPI_WARPS * 3 * 512 + (ew * 4 + g) * 256 + lane * 8;
+}
+__device__ __forceinline__ void gp_epi_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(32 * GP_EPI_WARPS) : "memory");
+}
+__device__ __forceinline__ bool gp_epi_bar_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.and.pred po, 1, %2, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(32 * GP_EPI_WARPS)
+      : "memory");
+  return r != 0;
+}
+
+// Copies of column n0 + 16 sc + ew (rows m0 + 4 lane .. + 3) of the tile's inputs.
+template <bool CPLX>
+__device__ __forceinline__ void gp_prefetch(const GPairTile& ti, uint8_t* eb, int ew, int lane,
+                                            int m0, int sc) {
+  const GProb* P = ti.P;
+  const int i = ti.n0 + 16 * sc + ew;
+  if (i >= P->n) return;
+  const bool c1 = (ti.cur != 0);
+  const int64_t idx = (int64_t)i * P->ld + m0 + 4 * lane;
+  cp_async16(gp_f4(eb, ew, 0, lane), (c1 ? P->A_hi[1] : P->A_hi[0]) + idx);
+  cp_async16(gp_f4(eb, ew, 1, lane), (c1 ? P->A_lo[1] : P->A_lo[0]) + idx);
+  cp_async16(gp_f4(eb, ew, 2, lane), P->L + idx);
+  cp_async8(gp_u2(eb, ew, 0, lane), (c1 ? P->dt[0] : P->dt[1]) + idx);
+  // Delta_ij, j = the lane's rows: row i of the slices (row 2i of the embedding)
+  const __nv_bfloat16* Drow = P->Dcat + (int64_t)(CPLX ? 2 * i : i) * P->cat_ld + m0 + 4 * lane;
+  for (int sl = 0; sl < ti.S; ++sl) cp_async8(gp_u2(eb, ew, 1 + sl, lane), Drow + (int64_t)sl * P->ld);
+}
+
+// Real problems: update column n0 + cl (cl = 16 sc + ew) from the staged inputs.
+__device__ __forceinline__ void gp_compute_real(const GPairTile& ti, GSmem* ms, const float* Xs,
+                                                uint8_t* eb, int ew, int lane, int tm, int m0,
+                                                int sc, float& mx) {
+  const GProb* P = ti.P;
+  const int n = P->n, ld = P->ld;
+  const int cl = 16 * sc + ew;
+  const int i = ti.n0 + cl;
+  if (i >= n) return;
+  const bool c1 = (ti.cur != 0);
+  float* __restrict__ Ahn = c1 ? P->A_hi[0] : P->A_hi[1];
+  float* __restrict__ Aln = c1 ? P->A_lo[0] : P->A_lo[1];
+  __nv_bfloat16* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
+  const float lam = P->lam;
+  const int r0 = 4 * lane, j0 = m0 + r0;
+  const float4 thj_h = ld4(P->th_hi + j0);
+  const float4 thj_l = ld4(P->th_lo + j0);
+  const float4 ah4 = *reinterpret_cast<const float4*>(gp_f4(eb, ew, 0, lane));
+  const float4 al4 = *reinterpret_cast<const float4*>(gp_f4(eb, ew, 1, lane));
+  const float4 L4 = *reinterpret_cast<const float4*>(gp_f4(eb, ew, 2, lane));
+  const uint2 dtp = *reinterpret_cast<const uint2*>(gp_u2(eb, ew, 0, lane));
+  uint2 D[3];
+  D[0] = *reinterpret_cast<const uint2*>(gp_u2(eb, ew, 1, lane));
+  D[1] = ti.S > 1 ? *reinterpret_cast<const uint2*>(gp_u2(eb, ew, 2, lane)) : make_uint2(0u, 0u);
+  D[2] = ti.S > 2 ? *reinterpret_cast<const uint2*>(gp_u2(eb, ew, 3, lane)) : make_uint2(0u, 0u);
+  const int c0 = 32 * (sc >> 1);
+  const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * G_BM + r0);
+  const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
+  const float thh = ms->thh[cl], thl = ms->thl[cl];
+  float4 oh, ol, oL;
+  uint32_t ob[4];
+  float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int j = j0 + e;
+    const float ah = f4(ah4, e), al = f4(al4, e);
+    float nh = 0.f, nl = 0.f, Ln = 0.f, dnew = 0.f;
+    if (j == i) {
+      nh = 1.f;
+      a2 += 1.f;
+    } else if (j < n) {
+      const float R = f4(L4, e) + lam * (f4(x4, e) - ah * e_i - bf_at(dtp, e) * dp_i);
+      float gh, gl;
+      ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
+      dnew = bf16_round(R * rcp_approx(gh));
+      Ln = fmaf(-gh, dnew, R) - gl * dnew;
+      ff_add_f(ah, al, dnew, nh, nl);
+      r2 = fmaf(R, R, r2);
+      a2 = fmaf(ah, ah, a2);
+      const float p1 = bf_at(D[0], e) * dnew;
+      const float p23 = fmaf(bf_at(D[1], e), dnew, bf_at(D[2], e) * dnew);
+      float sh, se;
+      two_sum(eh, p1, sh, se);
+      se += el + p23;
+      fast_two_sum(sh, se, eh, el);
+      mx = fmaxf(mx, fabsf(dnew));
+    }
+    f4set(oh, e, nh);
+    f4set(ol, e, nl);
+    f4set(oL, e, Ln);
+    ob[e] = bf_bits(dnew);
+  }
+  const int64_t idx = (int64_t)i * ld + j0;
+  st4(Ahn + idx, oh);
+  st4(Aln + idx, ol);
+  st4(P->L + idx, oL);
+  *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+  warp_sum_ff(r2, a2, eh, el);
+  if (lane == 0) {
+    const int ntm = P->ntm;
+    P->part[((int64_t)0 * ntm + tm) * ld + i] = r2;
+    P->part[((int64_t)1 * ntm + tm) * ld + i] = a2;
+    P->part[((int64_t)2 * ntm + tm) * ld + i] = eh;
+    P->part[((int64_t)3 * ntm + tm) * ld + i] = el;
+  }
+}
+
+// Complex problems: lane l owns complex rows jc0, jc0 + 1 (embedded rows r0 .. r0 + 3).
+__device__ __forceinline__ void gp_compute_cplx(const GPairTile& ti, GSmem* ms, const float* Xs,
+                                                uint8_t* eb, int ew, int lane, int tm, int m0,
+                                                int sc, float& mx) {
+  const GProb* P = ti.P;
+  const int n = P->n, ld = P->ld;
+  const int cl = 16 * sc + ew;
+  const int i = ti.n0 + cl;
+  if (i >= n) return;
+  const bool c1 = (ti.cur != 0);
+  float* __restrict__ Ahn = c1 ? P->A_hi[0] : P->A_hi[1];
+  float* __restrict__ Aln = c1 ? P->A_lo[0] : P->A_lo[1];
+  __nv_bfloat16* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
+  const float lam = P->lam;
+  const int r0 = 4 * lane;
+  const int jc0 = (m0 + r0) / 2;
+  float thj_h[2], thj_l[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int j = jc0 + e;
+    thj_h[e] = j < n ? P->th_hi[j] : 0.f;
+    thj_l[e] = j < n ? P->th_lo[j] : 0.f;
+  }
+  const float4 ah4 = *reinterpret_cast<const float4*>(gp_f4(eb, ew, 0, lane));
+  const float4 al4 = *reinterpret_cast<const float4*>(gp_f4(eb, ew, 1, lane));
+  const float4 L4 = *reinterpret_cast<const float4*>(gp_f4(eb, ew, 2, lane));
+  const uint2 dtp = *reinterpret_cast<const uint2*>(gp_u2(eb, ew, 0, lane));
+  uint2 D[3];
+  D[0] = *reinterpret_cast<const uint2*>(gp_u2(eb, ew, 1, lane));
+  D[1] = ti.S > 1 ? *reinterpret_cast<const uint2*>(gp_u2(eb, ew, 2, lane)) : make_uint2(0u, 0u);
+  D[2] = ti.S > 2 ? *reinterpret_cast<const uint2*>(gp_u2(eb, ew, 3, lane)) : make_uint2(0u, 0u);
+  const int c0 = 32 * (sc >> 1);
+  const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * G_BM + r0);
+  const float er = ms->e[2 * cl], ei = ms->e[2 * cl + 1];
+  const float dr = ms->dprev[2 * cl], di = ms->dprev[2 * cl + 1];
+  const float thh = ms->thh[cl], thl = ms->thl[cl];
+  float oh[4], ol[4], oL[4];
+  uint32_t ob[4];
+  float r2 = 0.f, a2 = 0.f, erh = 0.f, erl = 0.f, eih = 0.f, eil = 0.f;
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int j = jc0 + e;
+    const float ar = f4(ah4, 2 * e), ai = f4(ah4, 2 * e + 1);
+    const float alr = f4(al4, 2 * e), ali = f4(al4, 2 * e + 1);
+    float nh[2] = {0.f, 0.f}, nl[2] = {0.f, 0.f}, Ln[2] = {0.f, 0.f}, dn[2] = {0.f, 0.f};
+    if (j == i) {
+      nh[0] = 1.f;
+      a2 += 1.f;
+    } else if (j < n) {
+      float aer, aei, pdr, pdi;
+      cmulf(ar, ai, er, ei, aer, aei);
+      cmulf(bf_at(dtp, 2 * e), bf_at(dtp, 2 * e + 1), dr, di, pdr, pdi);
+      float R[2];
+      R[0] = f4(L4, 2 * e) + lam * (f4(x4, 2 * e) - aer - pdr);
+      R[1] = f4(L4, 2 * e + 1) + lam * (f4(x4, 2 * e + 1) - aei - pdi);
+      float gh, gl;
+      ff_sub(thh, thl, thj_h[e], thj_l[e], gh, gl);
+      const float g = rcp_approx(gh);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        dn[q] = bf16_round(R[q] * g);
+        Ln[q] = fmaf(-gh, dn[q], R[q]) - gl * dn[q];
+        r2 = fmaf(R[q], R[q], r2);
+      }
+      ff_add_f(ar, alr, dn[0], nh[0], nl[0]);
+      ff_add_f(ai, ali, dn[1], nh[1], nl[1]);
+      a2 = fmaf(ar, ar, fmaf(ai, ai, a2));
+      const float a1 = bf_at(D[0], 2 * e), b1 = bf_at(D[0], 2 * e + 1);
+      const float pr1 = fmaf(a1, dn[0], b1 * dn[1]), pi1 = fmaf(a1, dn[1], -b1 * dn[0]);
+      const float a2s = bf_at(D[1], 2 * e) + bf_at(D[2], 2 * e);
+      const float b2s = bf_at(D[1], 2 * e + 1) + bf_at(D[2], 2 * e + 1);
+      const float pr2 = fmaf(a2s, dn[0], b2s * dn[1]), pi2 = fmaf(a2s, dn[1], -b2s * dn[0]);
+      float sh, se;
+      two_sum(erh, pr1, sh, se); se += erl + pr2; fast_two_sum(sh, se, erh, erl);
+      two_sum(eih, pi1, sh, se); se += eil + pi2; fast_two_sum(sh, se, eih, eil);
+      mx = fmaxf(mx, fmaxf(fabsf(dn[0]), fabsf(dn[1])));
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      oh[2 * e + q] = nh[q]; ol[2 * e + q] = nl[q]; oL[2 * e + q] = Ln[q];
+      ob[2 * e + q] = bf_bits(dn[q]);
+    }
+  }
+  const int64_t idx = (int64_t)i * ld + m0 + r0;
+  st4(Ahn + idx, make_float4(oh[0], oh[1], oh[2], oh[3]));
+  st4(Aln + idx, make_float4(ol[0], ol[1], ol[2], ol[3]));
+  st4(P->L + idx, make_float4(oL[0], oL[1], oL[2], oL[3]));
+  *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+  warp_sum_ff(r2, a2, erh, erl);
+  float z0 = 0.f, z1 = 0.f;
+  warp_sum_ff(z0, z1, eih, eil);
+  if (lane == 0) {
+    const int ntm = P->ntm;
+    P->part[((int64_t)0 * ntm + tm) * ld + i] = r2;
+    P->part[((int64_t)1 * ntm + tm) * ld + i] = a2;
+    P->part[((int64_t)2 * ntm + tm) * ld + i] = erh;
+    P->part[((int64_t)3 * ntm + tm) * ld + i] = erl;
+    P->part[((int64_t)4 * ntm + tm) * ld + i] = eih;
+    P->part[((int64_t)5 * ntm + tm) * ld + i] = eil;
+  }
+}
+
+// PAIR = false: the same kernel without clusters: one CTA per 128-row tile of width
+// <= 128, a 3-stage ring of A + B slots, its own MMA (cta_group::1) and the same
+// 16-warp staged epilogue; for groups of small problems, whose 128-row tiles would
+// leave the second CTA of a pair idle.
+template <bool PAIR>
+struct GPShape {
+  static constexpr int slot = PAIR ? GP_SLOT : G_A_TILE + 128 * G_BK * 2;   // 30720 / 32768
+  static constexpr int stages = PAIR ? GP_STAGES : 3;
+  static constexpr int rows = PAIR ? 2 * G_BM : G_BM;                         // rows per tile
+};
+static_assert(GPShape<false>::slot * GPShape<false>::stages <= GP_RING, "single-CTA ring");
+
+template <bool CPLX, bool PAIR>
+__global__ void __launch_bounds__(GP_NTHREADS, 1)
+k_g_gemm_epi_x(const GProb* __restrict__ probs, const int2* __restrict__ tiles, int ntiles,
+               unsigned* timeout) {
+  using Sh = GPShape<PAIR>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* Xs = reinterpret_cast<float*>(smem + GP_RING);
+  uint8_t* EB = smem + GP_RING + G_SMEM_X;
+  GSmem* ms = (GSmem*)(smem + GP_RING + G_SMEM_X + 2 * GP_EB_BYTES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const int pair = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int npairs = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Sh::stages; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], 1); }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ms->acc_full[b], 1);
+      mbar_init(&ms->acc_empty[b], PAIR ? 2 : 1);
+    }
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    if constexpr (PAIR) { tmem_alloc_pair(&ms->tmem_base, 2 * G_BNMAX); tmem_relinquish_pair(); }
+    else { tmem_alloc(&ms->tmem_base, 2 * G_BNMAX); tmem_relinquish(); }
+  }
+  tc_fence_before();
+  if constexpr (PAIR) cluster_sync();
+  else __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = ms->tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer (both CTAs): completions go to the leader's full[s] ----
+    const uint32_t full_leader = PAIR ? mapa_shared(&ms->full[0], 0) : 0u;
+    uint32_t it = 0;
+    bool alive = true;
+    for (int t = pair; t < ntiles && alive; t += npairs) {
+      const GPairTile ti = gp_tile(probs, tiles, t);
+      if (!ti.live) continue;
+      // the slot holds A and this CTA's rows of B: bn/2 <= 112 (pair) or bn <= 128
+      const int bh = PAIR ? ti.bn / 2 : ti.bn;
+      const uint32_t stage_bytes = (uint32_t)G_A_TILE + (uint32_t)bh * G_BK * 2;
+      const CUtensorMap* tA = &ti.P->tmA;
+      const CUtensorMap* tB = (ti.cur == 1) ? &ti.P->tmB[0] : &ti.P->tmB[1];
+      const int nk = ti.S * ti.kbs;
+      const int m0 = ti.tm2 * Sh::rows + (int)rank * G_BM;
+      const int kdiag = CPLX ? 2 * (ti.n0 + ti.bn) - 1 : ti.n0 + ti.bn - 1;
+      const int kb_last = min(ti.kbs - 1, kdiag / G_BK);
+      for (int q = 0; q < nk; ++q, ++it) {
+        const int s = it % Sh::stages;
+        const uint32_t ph = (it / Sh::stages) & 1;
+        if (!mbar_wait(&ms->empty[s], ph ^ 1, timeout)) { alive = false; break; }
+        const int sl = ti.S - 1 - q / ti.kbs;
+        const int kb = (kb_last + 1 + q % ti.kbs) % ti.kbs;
+        uint8_t* slot = smem + (size_t)s * Sh::slot;
+        if constexpr (PAIR) {
+          if (rank == 0) mbar_arrive_expect_tx(&ms->full[s], 2 * stage_bytes);
+          const uint32_t fb = full_leader + (uint32_t)s * 8u;
+          tma_load_2d_pair(slot, tA, fb, sl * ti.P->ld + kb * G_BK, m0);
+          tma_load_2d_pair(slot + G_A_TILE, tB, fb, kb * G_BK, ti.n0 + (int)rank * bh);
+        } else {
+          mbar_arrive_expect_tx(&ms->full[s], stage_bytes);
+          tma_load_2d(slot, tA, &ms->full[s], sl * ti.P->ld + kb * G_BK, m0);
+          tma_load_2d(slot + G_A_TILE, tB, &ms->full[s], kb * G_BK, ti.n0);
+        }
+      }
+    }
+    if constexpr (PAIR) {
+      for (uint32_t u = (it > (uint32_t)Sh::stages ? it - Sh::stages : 0); u < it; ++u)
+        mbar_wait_quiet(&ms->empty[u % Sh::stages], (u / Sh::stages) & 1, kTailWaitNs);
+    } else {
+      // every issued copy has landed before the CTA can exit
+      for (uint32_t u = (it > (uint32_t)Sh::stages ? it - Sh::stages : 0); u < it; ++u)
+        mbar_wait_quiet(&ms->full[u % Sh::stages], (u / Sh::stages) & 1, kTailWaitNs);
+    }
+  } else if (warp == 1 && lane == 0 && rank == 0) {
+    // ---- MMA issuer (the pair's leader, or the CTA itself) ----
+    uint32_t it = 0;
+    int lt = 0;
+    bool alive = true;
+    for (int t = pair; t < ntiles && alive; t += npairs) {
+      const GPairTile ti = gp_tile(probs, tiles, t);
+      if (!ti.live) continue;
+      const int b = lt & 1;
+      const uint32_t use = (uint32_t)(lt >> 1);
+      ++lt;
+      if (!mbar_wait(&ms->acc_empty[b], (use & 1) ^ 1, timeout)) break;
+      tc_fence_after();
+      const uint32_t dacc = tmem + (uint32_t)(b * G_BNMAX);
+      const uint32_t idesc = idesc_bf16_f32(Sh::rows, ti.bn);
+      const int nk = ti.S * ti.kbs;
+      for (int q = 0; q < nk; ++q, ++it) {
+        const int s = it % Sh::stages;
+        const uint32_t ph = (it / Sh::stages) & 1;
+        if (!mbar_wait(&ms->full[s], ph, timeout)) { alive = false; break; }
+        tc_fence_after();
+        uint8_t* slot = smem + (size_t)s * Sh::slot;
+        const uint64_t da = smem_desc_sw128(slot);
+        const uint64_t db = smem_desc_sw128(slot + G_A_TILE);
+#pragma unroll
+        for (int kk = 0; kk < G_BK / G_UK; ++kk) {
+          if constexpr (PAIR)
+            umma_bf16_pair(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                           (q > 0 || kk > 0) ? 1u : 0u);
+          else
+            umma_bf16(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+                      (q > 0 || kk > 0) ? 1u : 0u);
+        }
+        if constexpr (PAIR) umma_commit_pair(&ms->empty[s], (uint16_t)3);
+        else umma_commit(&ms->empty[s]);
+      }
+      if constexpr (PAIR) umma_commit_pair(&ms->acc_full[b], (uint16_t)3);
+      else umma_commit(&ms->acc_full[b]);
+    }
+    if constexpr (PAIR)
+      for (int u = (lt > 2 ? lt - 2 : 0); u < lt; ++u)
+        mbar_wait_quiet(&ms->acc_empty[u & 1], (uint32_t)((u >> 1) & 1), kTailWaitNs);
+  } else if (warp >= 2) {
+    // ---- epilogue (both CTAs, each on its own 128 rows) ----
+    const int ew = warp - 2;
+    const int qd = warp & 3;
+    const int q4 = ew >> 2;
+    const int et = threadIdx.x - 64;
+    const uint32_t acc_empty_leader = PAIR ? mapa_shared(&ms->acc_empty[0], 0) : 0u;
+    float mx = 0.f;
+    const GProb* mxP = nullptr;
+    int lt = 0;
+    int pref_t = -1;      // tile whose first sub-chunk is in flight
+    for (int t = pair; t < ntiles; t += npairs) {
+      const GPairTile ti = gp_tile(probs, tiles, t);
+      if (!ti.live) continue;
+      const int b = lt & 1;
+      const uint32_t use = (uint32_t)(lt >> 1);
+      ++lt;
+      // 128-row tile of this CTA: the pair's half, or the tile itself
+      const int tm = PAIR ? 2 * ti.tm2 + (int)rank : ti.tm2;
+      const int m0 = tm * G_BM;
+      const bool work = tm < ti.P->ntm;
+      if (mxP != ti.P) {
+        if (mxP) {
+          float m = mx;
+          for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+          if (lane == 0 && m > 0.f) atomicMax(&mxP->st->dmax_bits, __float_as_uint(m));
+        }
+        mxP = ti.P;
+        mx = 0.f;
+      }
+      if (pref_t != t) {
+        if (work) gp_prefetch<CPLX>(ti, EB, ew, lane, m0, 0);
+        cp_async_commit();
+        cp_async_wait<0>();
+      }
+      gp_epi_bar();
+      if constexpr (CPLX) {
+        const int i = ti.n0 + (et >> 1);
+        const bool v = (et < 2 * ti.bn) && (i < ti.P->n);
+        ms->e[et] = v ? ti.P->e_col[2 * ti.n0 + et] : 0.f;
+        ms->dprev[et] = v ? ti.P->dprev_col[2 * ti.n0 + et] : 0.f;
+        if (et < G_BNMAX) {
+          const int ic = ti.n0 + et;
+          const bool vc = (et < ti.bn) && (ic < ti.P->n);
+          ms->thh[et] = vc ? ti.P->th_hi[ic] : 0.f;
+          ms->thl[et] = vc ? ti.P->th_lo[ic] : 0.f;
+        }
+      } else {
+        if (et < G_BNMAX) {
+          const int i = ti.n0 + et;
+          const bool v = (et < ti.bn) && (i < ti.P->n);
+          ms->e[et] = v ? ti.P->e_col[i] : 0.f;
+          ms->dprev[et] = v ? ti.P->dprev_col[i] : 0.f;
+          ms->thh[et] = v ? ti.P->th_hi[i] : 0.f;
+          ms->thl[et] = v ? ti.P->th_lo[i] : 0.f;
+        }
+      }
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&ms->acc_full[b], use & 1, timeout));
+      tc_fence_after();
+      const uint32_t src = tmem + (uint32_t)(b * G_BNMAX) + ((uint32_t)(qd * 32) << 16);
+      const int nsub = ti.bn / 16;
+      // the next live tile of this pair, for the prefetch at the last sub-chunk
+      int tnext = t + npairs;
+      bool next_live = false;
+      GPairTile nx{};
+      if (tnext < ntiles) {
+        nx = gp_tile(probs, tiles, tnext);
+        next_live = nx.live;
+      }
+      bool all_ok = true;
+#pragma unroll 1
+      for (int c0 = 0; c0 < ti.bn; c0 += G_XCH) {
+        if (c0 > 0) gp_epi_bar();
+        if (ok) {
+          float x[8];
+          const int cc = q4 * 8;
+          tmem_ld_x8(src + (uint32_t)(c0 + cc), x);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) Xs[(cc + c) * G_BM + qd * 32 + lane] = x[c];
+        }
+        if (c0 + G_XCH >= ti.bn) tc_fence_before();
+        all_ok = gp_epi_bar_and(ok);
+        if (c0 + G_XCH >= ti.bn && et == 0) {
+          if (rank == 0) mbar_arrive(&ms->acc_empty[b]);
+          else if constexpr (PAIR) mbar_arrive_remote(acc_empty_leader + (uint32_t)b * 8u);
+        }
+        if (!all_ok) break;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+          const int sc = c0 / 16 + h;
+          uint8_t* nb = EB + ((sc + 1) & 1) * GP_EB_BYTES;
+          pref_t = -1;
+          if (sc + 1 < nsub) {
+            if (work) gp_prefetch<CPLX>(ti, nb, ew, lane, m0, sc + 1);
+          } else if (next_live) {
+            const int tmn = PAIR ? 2 * nx.tm2 + (int)rank : nx.tm2;
+            if (tmn < nx.P->ntm) gp_prefetch<CPLX>(nx, nb, ew, lane, tmn * G_BM, 0);
+            pref_t = tnext;
+          }
+          cp_async_commit();
+          cp_async_wait<1>();
+          if (work) {
+            uint8_t* cb = EB + (sc & 1) * GP_EB_BYTES;
+            if constexpr (CPLX) gp_compute_cplx(ti, ms, Xs, cb, ew, lane, tm, m0, sc, mx);
+            else gp_compute_real(ti, ms, Xs, cb, ew, lane, tm, m0, sc, mx);
+          }
+        }
+      }
+      if (!all_ok) break;
+    }
+    cp_async_wait<0>();
+    if (mxP) {
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if (lane == 0 && mx > 0.f) atomicMax(&mxP->st->dmax_bits, __float_as_uint(mx));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if constexpr (PAIR) cluster_sync();
+  if (warp == 0) {
+    tc_fence_after();
+    if constexpr (PAIR) tmem_dealloc_pair(tmem, 2 * G_BNMAX);
+    else tmem_dealloc(tmem, 2 * G_BNMAX);
+  }
+}
+
+
 // ---------------------------------------------------------------------------
 // Output: A (float-float -> FP64) and E; work item (problem, 128-col tile, 128-row
 // tile), thread j owns row j; the loads of eight columns are issued before their
@@ -1022,9 +1541,91 @@ __global__ void __launch_bounds__(128) k_g_finalize(const GProb* __restrict__ pr
 cudaError_t g_set_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_g_gemm_epi<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, G_SMEM_BYTES);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_g_gemm_epi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              G_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_g_gemm_epi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             G_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_g_gemm_epi_x<false, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_g_gemm_epi_x<true, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_g_gemm_epi_x<false, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM_BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_g_gemm_epi_x<true, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, GP_SMEM_BYTES);
+  return e;
+}
+
+namespace {
+// launch configuration of the staged kernel: clusters of two for the pair form
+struct StagedLaunch {
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  StagedLaunch(int blocks, bool pair, cudaStream_t s) {
+    cfg.gridDim = dim3(blocks, 1, 1);
+    cfg.blockDim = dim3(GP_NTHREADS, 1, 1);
+    cfg.dynamicSmemBytes = GP_SMEM_BYTES;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = pair ? 2 : 1;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pair ? 1 : 0;
+  }
+};
+}  // namespace
+
+// Clusters of two of the grouped pair kernel that can be resident at once.
+int g_pair_clusters() {
+  static int cached[64];
+  static bool known[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (known[dev]) return cached[dev];
+  StagedLaunch L(2, true, nullptr);
+  int n = 0;
+  if (cudaFuncSetAttribute(k_g_gemm_epi_x<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           GP_SMEM_BYTES) != cudaSuccess ||
+      cudaOccupancyMaxActiveClusters(&n, k_g_gemm_epi_x<false, true>, &L.cfg) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cached[dev] = n;
+  known[dev] = true;
+  return n;
+}
+
+cudaError_t launch_g_gemm_epi_pair(const GProb* probs, const int2* tiles, int ntiles,
+                                   unsigned* timeout, bool cplx, int npairs, cudaStream_t s) {
+  if (npairs < 1) return cudaErrorInvalidValue;
+  const int pairs = ntiles < npairs ? ntiles : npairs;
+  if (pairs <= 0) return cudaGetLastError();
+  StagedLaunch L(2 * pairs, true, s);
+  return cplx ? cudaLaunchKernelEx(&L.cfg, k_g_gemm_epi_x<true, true>, probs, tiles, ntiles, timeout)
+              : cudaLaunchKernelEx(&L.cfg, k_g_gemm_epi_x<false, true>, probs, tiles, ntiles, timeout);
+}
+
+cudaError_t launch_g_gemm_epi_staged(const GProb* probs, const int2* tiles, int ntiles,
+                                     unsigned* timeout, bool cplx, cudaStream_t s) {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = ntiles < nsm ? ntiles : nsm;
+  if (grid <= 0) return cudaGetLastError();
+  StagedLaunch L(grid, false, s);
+  return cplx ? cudaLaunchKernelEx(&L.cfg, k_g_gemm_epi_x<true, false>, probs, tiles, ntiles, timeout)
+              : cudaLaunchKernelEx(&L.cfg, k_g_gemm_epi_x<false, false>, probs, tiles, ntiles, timeout);
 }
 cudaError_t launch_g_check_theta(const GProb* probs, int count, int max_n, int* running,
                                  cudaStream_t s) {

@@ -83,10 +83,23 @@ struct GroupPlan {
 
 // Lays out every problem's work arrays in one arena at `base` (nullptr: size
 // only) and fills g.  states_dev + p becomes problem p's IterState.
+// Forms of the grouped product kernel: tile rows, largest tile width and the rows
+// of the increment descriptor's box.
+enum GForm { G_PLAIN = 1, G_STAGED = 2, G_PAIR = 3 };
+inline int gform_rows(int f) { return f == G_PAIR ? 256 : 128; }
+inline int gform_wmax(int f) { return f == G_PAIR ? 224 : (f == G_STAGED ? 128 : 256); }
+inline int gform_box(int f, int bn) { return f == G_PAIR ? bn / 2 : bn; }
+
 void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const double* const* theta,
                 const double* const* delta, const int64_t* ld_delta, const double* lambda,
                 double* const* A_out, const int64_t* ld_a, double* const* E_out, char* base,
-                IterState* states_dev);
+                IterState* states_dev, int form);
+
+// The product form for a group (opt_form 0: chosen from the sizes) and, for the pair
+// form, the number of CTA pairs; launches one product step of a group.
+int choose_gform(int opt_form, int count, const int64_t* n, int* npairs);
+cudaError_t launch_gform(int form, const GProb* probs, const int2* tiles, int ntiles,
+                         unsigned* timeout, bool cplx, int npairs, cudaStream_t s);
 
 // Re-lays a plan's arrays out at `base` (same order as plan_group), states at
 // states_dev + p; the work lists are unchanged.

@@ -123,6 +123,14 @@ cudaError_t launch_g_ctrl(const GProb* probs, int count, int max_n, bool cplx, i
 cudaError_t launch_g_gemm_epi(const GProb* probs, const int2* tiles, int ntiles,
                               unsigned* timeout, bool cplx, cudaStream_t s);
 cudaError_t launch_g_finalize(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
+// CTA-pair form of the grouped product: tiles are (problem, 256-row pair tile); the
+// problems' increment descriptors have boxes of bn/2 rows
+int g_pair_clusters();
+cudaError_t launch_g_gemm_epi_pair(const GProb* probs, const int2* tiles, int ntiles,
+                                   unsigned* timeout, bool cplx, int npairs, cudaStream_t s);
+// One CTA per 128-row tile with the staged 16-warp epilogue (tile widths <= 128).
+cudaError_t launch_g_gemm_epi_staged(const GProb* probs, const int2* tiles, int ntiles,
+                                     unsigned* timeout, bool cplx, cudaStream_t s);
 cudaError_t launch_gc_prep(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
 cudaError_t launch_gc_iter0(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
 cudaError_t launch_gc_finalize(const GProb* probs, const int4* items, int nitems, cudaStream_t s);

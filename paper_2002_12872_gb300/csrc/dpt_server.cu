@@ -105,6 +105,8 @@ struct dpt_server {
   cudaStream_t s = nullptr;
   bool tiles_dirty = true;
   int ntiles[2] = {0, 0};
+  int form = G_PLAIN;                     // product form (GForm)
+  int npairs = 0;                         // CTA pairs of the pair form
   // statistics (under mu)
   int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, rejected = 0, steps = 0;
   int32_t max_queued = 0;
@@ -178,12 +180,13 @@ void admit(dpt_server* S, Request* r) {
   GroupPlan g;
   const double lam = r->p.lambda;
   plan_group(g, 1, r->cplx, &n, &th, &dl, &ldd, &lam, &A, &lda, &E, plan_base,
-             S->states_dev + r->slot);
+             S->states_dev + r->slot, S->form);
   GProb& P = g.probs[0];
   P.tmA = make_tmap_bf16(P.Dcat, (uint64_t)3 * P.ld, P.nr, (uint64_t)3 * P.ld, 128);
-  for (int q = 0; q < 2; ++q) P.tmB[q] = make_tmap_bf16(P.dt[q], P.nr, P.n, P.ld, P.bn);
+  for (int q = 0; q < 2; ++q)
+    P.tmB[q] = make_tmap_bf16(P.dt[q], P.nr, P.n, P.ld, gform_box(S->form, P.bn));
   r->P = P;
-  r->tiles = P.ntm * P.ntn;
+  r->tiles = (int)g.tiles.size();
   const std::vector<int4>& prep = r->cplx ? g.prep_c : g.prep_r;
   const std::vector<int4>& blk = r->cplx ? g.blk_c : g.blk_r;
   const int nprep = (int)prep.size();
@@ -344,8 +347,8 @@ void worker_loop(dpt_server* S) {
         }
       for (int k = 0; k < 2; ++k)
         if (S->ntiles[k])
-          CK(launch_g_gemm_epi(S->probs_dev, S->tiles_dev[k], S->ntiles[k],
-                               (unsigned*)(S->flags_dev + 1), k == 1, S->s));
+          CK(launch_gform(S->form, S->probs_dev, S->tiles_dev[k], S->ntiles[k],
+                          (unsigned*)(S->flags_dev + 1), k == 1, S->npairs, S->s));
       if (kind[0]) CK(launch_g_ctrl(S->probs_dev, hi, max_n[0], false, S->flags_dev, S->s));
       if (kind[1]) CK(launch_g_ctrl(S->probs_dev, hi, max_n[1], true, S->flags_dev, S->s));
       CK(cudaMemcpyAsync(S->states_host, S->states_dev, sizeof(IterState) * hi,
@@ -457,6 +460,7 @@ dpt_status dpt_server_create(const dpt_server_cfg* cfg_in, dpt_server** out) {
     CK(cudaHostAlloc((void**)&S->flags_host, sizeof(int) * 4, cudaHostAllocDefault));
     CK(cudaStreamCreateWithFlags(&S->s, cudaStreamNonBlocking));
     CK(g_set_attributes());
+    S->form = choose_gform(cfg.opt.grouped_form, 0, nullptr, &S->npairs);
     // idle slots: a valid table entry whose state is not running
     std::vector<GProb> p0(m);
     std::vector<IterState> s0(m);
@@ -519,7 +523,7 @@ dpt_status dpt_submit(dpt_server* S, const dpt_problem* prob, dpt_req* id) {
   double* E = nullptr;
   const int64_t ld = n;
   const double lam = p.lambda;
-  plan_group(g, 1, r->cplx, &n, &th, &dl, &ld, &lam, &A, &ld, &E, nullptr, nullptr);
+  plan_group(g, 1, r->cplx, &n, &th, &dl, &ld, &lam, &A, &ld, &E, nullptr, nullptr, G_PLAIN);
   const int w = r->cplx ? 2 : 1;
   r->plan_bytes = g.bytes;
   size_t b = al256(g.bytes);

@@ -32,7 +32,7 @@ class Options(ctypes.Structure):
                 ("prec", ctypes.c_int32), ("epstein_nesbet", ctypes.c_int32),
                 ("graph_iters", ctypes.c_int32), ("max_slices", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("slice_tol", ctypes.c_double),
-                ("cta_pair", ctypes.c_int32)]
+                ("cta_pair", ctypes.c_int32), ("grouped_form", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -40,14 +40,16 @@ class Info(ctypes.Structure):
                 ("residual", ctypes.c_double), ("status", ctypes.c_int32),
                 ("nstar", ctypes.c_int32), ("seconds", ctypes.c_double),
                 ("launches", ctypes.c_int32), ("product_launches", ctypes.c_int32),
-                ("product_ms", ctypes.c_double), ("cta_pair", ctypes.c_int32)]
+                ("product_ms", ctypes.c_double), ("cta_pair", ctypes.c_int32),
+                ("grouped_form", ctypes.c_int32)]
 
     def as_dict(self):
         return {"iters": self.iters, "slice_gemms": self.slice_gemms,
                 "residual": self.residual, "status": STATUS.get(self.status, str(self.status)),
                 "code": self.status, "nstar": self.nstar, "seconds": self.seconds,
                 "launches": self.launches, "product_launches": self.product_launches,
-                "product_ms": self.product_ms, "cta_pair": self.cta_pair}
+                "product_ms": self.product_ms, "cta_pair": self.cta_pair,
+                "grouped_form": self.grouped_form}
 
 
 class ServerCfg(ctypes.Structure):
@@ -303,11 +305,12 @@ class Batch:
         self._dev = thetas[0]
 
     def solve(self, *, tol=1e-12, max_iter=200, graph_iters=None, max_slices=None,
-              slice_tol=None, profile=False, stream=None, check=True):
-        """Returns (A_outs, E_outs, infos)."""
+              slice_tol=None, profile=False, form=None, stream=None, check=True):
+        """Returns (A_outs, E_outs, infos).  form: the product form (grouped_form)."""
         infos = (Info * self.count)()
         o = options(tol=tol, max_iter=max_iter, prec="mixed", graph_iters=graph_iters,
-                    max_slices=max_slices, slice_tol=slice_tol, profile=int(bool(profile)))
+                    max_slices=max_slices, slice_tol=slice_tol, profile=int(bool(profile)),
+                    grouped_form=None if form is None else int(form))
         st = lib().dpt_solve_batched(self.count, C128 if self.cplx else R64, self._n, self._th,
                                      self._d, self._ldd, self._lam, ctypes.byref(o), self._a,
                                      self._lda, self._e, infos, _stream_of(self._dev, stream))
@@ -320,8 +323,8 @@ class Batch:
 
 
 def solve_batched(thetas, deltas, lams, *, tol=1e-12, max_iter=200, graph_iters=None,
-                  max_slices=None, slice_tol=None, profile=False, A_outs=None, E_outs=None,
-                  stream=None, check=True):
+                  max_slices=None, slice_tol=None, profile=False, form=None, A_outs=None,
+                  E_outs=None, stream=None, check=True):
     """Grouped solve of independent problems (dpt_solve_batched), all real or all
     complex (complex128 deltas; theta and lambda real).
 
@@ -330,7 +333,7 @@ def solve_batched(thetas, deltas, lams, *, tol=1e-12, max_iter=200, graph_iters=
     problems build a Batch once and call its solve()."""
     return Batch(thetas, deltas, lams, A_outs=A_outs, E_outs=E_outs).solve(
         tol=tol, max_iter=max_iter, graph_iters=graph_iters, max_slices=max_slices,
-        slice_tol=slice_tol, profile=profile, stream=stream, check=check)
+        slice_tol=slice_tol, profile=profile, form=form, stream=stream, check=check)
 
 
 def solve_dominant(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, prec="mixed", tol=1e-12,
@@ -410,14 +413,14 @@ class Server:
     the request's final status has been collected."""
 
     def __init__(self, *, hbm_budget=0, max_active=64, max_queue=65536, tol=None,
-                 max_iter=None, max_slices=None, slice_tol=None):
+                 max_iter=None, max_slices=None, slice_tol=None, form=None):
         cfg = ServerCfg()
         lib().dpt_server_cfg_default(ctypes.byref(cfg))
         cfg.hbm_budget = int(hbm_budget)
         cfg.max_active = int(max_active)
         cfg.max_queue = int(max_queue)
         for k, v in (("tol", tol), ("max_iter", max_iter), ("max_slices", max_slices),
-                     ("slice_tol", slice_tol)):
+                     ("slice_tol", slice_tol), ("grouped_form", form)):
             if v is not None:
                 setattr(cfg.opt, k, v)
         h = ctypes.c_void_p()

@@ -81,3 +81,23 @@ def test_batched_full_workload_sampled(ora, dpt):
         Ao, Eo, io = ora.solve_full(p["theta"], p["delta"], p["lam"], tol=1e-13)
         assert eig_err(to_np(Es[q]), Eo) <= EIG_RTOL
         assert vec_err(to_np(As[q]), Ao) <= VEC_TOL
+
+
+@pytest.mark.parametrize("form", [2, 3])
+def test_batched_other_product_forms(ora, dpt, form):
+    """The staged one-CTA form and the CTA-pair form of the grouped product."""
+    rng = np.random.Generator(np.random.PCG64(45 + form))
+    sizes = [1, 3, 33, 100, 128, 129, 257, 400]
+    probs = []
+    for n in sizes:
+        th = np.arange(n, dtype=float) + rng.uniform(-0.2, 0.2, n)
+        probs.append({"theta": th, "delta": inputs.symmetric_gaussian(n, 1.0 / n, rng),
+                      "lam": float(rng.uniform(0.01, 0.1))})
+    th, D = _dev(probs, dpt)
+    As, Es, infos = dpt.solve_batched(th, D, [p["lam"] for p in probs], form=form)
+    assert infos[0]["grouped_form"] == form or (form == 3 and infos[0]["grouped_form"] == 2)
+    for p, A, E, inf in zip(probs, As, Es, infos):
+        Ao, Eo, io = ora.solve_full(p["theta"], p["delta"], p["lam"], tol=1e-13)
+        assert inf["status"] == "OK"
+        assert eig_err(to_np(E), Eo) <= EIG_RTOL, (len(Eo), inf)
+        assert vec_err(to_np(A), Ao) <= VEC_TOL, (len(Eo), inf)

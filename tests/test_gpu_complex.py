@@ -99,3 +99,17 @@ def test_complex_served_size_sampled(ora, dpt):
     assert io["status"] == "OK"
     assert eig_err(E[cols], Eo) <= EIG_RTOL, info
     assert vec_err(A[:, cols], Ao) <= VEC_TOL, info
+
+
+@pytest.mark.parametrize("form", [2, 3])
+def test_complex_other_product_forms(ora, dpt, form):
+    sizes = [2, 64, 130, 300]
+    probs = [_hermitian(n, 5000 + n, lam=0.04) for n in sizes]
+    th = [torch.tensor(p[0], device="cuda") for p in probs]
+    D = [dpt.colmajor_tensor(p[1], "cuda") for p in probs]
+    As, Es, infos = dpt.solve_batched(th, D, [p[2] for p in probs], form=form)
+    for (t, d, lam), A, E, inf in zip(probs, As, Es, infos):
+        Ao, Eo, io = ora.solve_full(t, d, lam, tol=1e-13)
+        assert inf["status"] == "OK"
+        assert eig_err(to_np(E), Eo) <= EIG_RTOL, (len(t), inf)
+        assert vec_err(to_np(A), Ao) <= VEC_TOL, (len(t), inf)
