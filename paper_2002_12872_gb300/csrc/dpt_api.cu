@@ -197,6 +197,7 @@ struct Prof {
   void collect(int nlive) {
     live += nlive;
     if (!on) return;
+    nlive = std::min(nlive, (int)(ev.size() / 2));   // never past the recorded slots
     for (int q = 0; q < nlive; ++q) {
       float t = 0.f;
       CK(cudaEventElapsedTime(&t, ev[2 * q], ev[2 * q + 1]));
@@ -212,9 +213,11 @@ struct Prof {
 // epilogue / control launches, `kernels_per_iter` in all) `per` times per chunk,
 // as CUDA-graph replays when graph_iters > 0, until the device state leaves
 // ST_RUNNING.  One small device-to-host read of the state per chunk.
+// k_first: the iteration count at the start of the first chunk when the caller has
+// not read the state back (-1: read it from b->host_state).
 template <class F>
 void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kernels_per_iter,
-              Prof& prof, F&& iter, size_t state_bytes = sizeof(IterState)) {
+              Prof& prof, F&& iter, size_t state_bytes = sizeof(IterState), int k_first = -1) {
   cudaStream_t s = b->stream;
   const int per = graph_iters > 0 ? graph_iters : 4;
   prof.make(per);
@@ -231,7 +234,7 @@ void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kerne
   const int max_chunks = max_iter / per + 2;
   try {
     for (int c = 0; c < max_chunks; ++c) {
-      const int k0 = b->host_state->k;
+      const int k0 = (c == 0 && k_first >= 0) ? k_first : b->host_state->k;
       if (exec) {
         CK(cudaGraphLaunch(exec, s));
       } else {
@@ -241,7 +244,7 @@ void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kerne
       CK(cudaMemcpyAsync(b->host_state, dst, state_bytes, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       const bool running = b->host_state->status == ST_RUNNING;
-      prof.collect(running ? per : std::max(0, b->host_state->k - k0 + 1));
+      prof.collect(running ? per : std::min(per, std::max(0, b->host_state->k - k0 + 1)));
       if (!running) break;
     }
   } catch (...) {
@@ -261,11 +264,13 @@ struct Timer {
 // ---------------------------------------------------------------------------
 // Full solve, mixed precision (real)
 // ---------------------------------------------------------------------------
+// th: theta checked on the host (host input or Epstein-Nesbet shift); or, when it is
+// empty, theta_dev: the caller's device theta, checked on the device.
 dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
-                                 const double* delta_in, bool delta_dev, int64_t ld_delta,
-                                 double lambda, const dpt_options& o, double* A_out,
-                                 bool a_dev, int64_t ld_a, double* E_out, bool e_dev,
-                                 dpt_info* info, cudaStream_t user) {
+                                 const double* theta_dev, const double* delta_in, bool delta_dev,
+                                 int64_t ld_delta, double lambda, const dpt_options& o,
+                                 double* A_out, bool a_dev, int64_t ld_a, double* E_out,
+                                 bool e_dev, dpt_info* info, cudaStream_t user) {
   const int n = (int)n64;
   // a multiple of the 128-row tile: the epilogue's vector accesses cover whole
   // tiles, so every row of every tile must lie inside its own column
@@ -333,10 +338,15 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     h.best = INFINITY;
     double tm = 0;
     for (double v : th) tm = std::max(tm, std::fabs(v));
-    h.theta_max = tm;
+    h.theta_max = tm;                  // 0 for a device theta: set by the check kernel
     *b->host_state = h;
     CK(cudaMemcpyAsync(st, b->host_state, sizeof(IterState), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(thd, th.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    if (th.empty()) {
+      thd = const_cast<double*>(theta_dev);   // read in place, never written
+      CK(launch_check_theta(n, thd, st, s));
+    } else {
+      CK(cudaMemcpyAsync(thd, th.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    }
     CK(cudaMemsetAsync(dtb[0], 0, sizeof(__nv_bfloat16) * (size_t)ld * n * 2, s));
     CK(launch_theta_ff(n, thd, thh, thl, s));
     CK(launch_prep_delta(delta, ldd, n, ld, o.epstein_nesbet, Dcat, st, s));
@@ -361,20 +371,21 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     for (int q = 0; q < 2; ++q) { p.A_hi[q] = Ahi[q]; p.A_lo[q] = Alo[q]; p.dt[q] = dtb[q]; }
     p.L = L; p.Dcat = Dcat; p.cat_ld = (int64_t)3 * ld; p.th_hi = thh; p.th_lo = thl; p.e_col = e_col; p.dprev_col = dprev;
     p.part = part; p.st = st;
-    // the state read after iteration 0 seeds the per-chunk iteration count
-    CK(cudaMemcpyAsync(b->host_state, st, sizeof(IterState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    // no host round trip here: the loop's kernels return at once if the iteration
+    // stopped at iteration 0, and the loop reads the state after each chunk (the pinned
+    // state buffer may still be the source of the pending upload above: not touched)
     Prof prof;
     prof.on = o.profile != 0;
-    prof.launches = 4;   // theta split, Delta preparation, iteration 0, control
-    if (b->host_state->status == ST_RUNNING)
+    prof.launches = th.empty() ? 5 : 4;   // (theta check,) theta split, slicing, iteration 0, control
+    {
       run_loop(b, st, o.graph_iters, o.max_iter, 2, prof, [&](int q) {
         prof.before(q, s);
         if (pair) CK(launch_gemm_epi_pair(tA, tB0, tB1, p, npairs, s));
         else CK(launch_gemm_epi(tA, tB0, tB1, p, s));
         prof.after(q, s);
         CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
-      });
+      }, sizeof(IterState), /*k_first=*/1);   // the control after iteration 0 set k = 1
+    }
     prof.launches += 1;  // finalize
     CK(launch_finalize(n, ld, Ahi[0], Alo[0], Ahi[1], Alo[1], Astage, lda_dev, st, s));
     if (!a_dev)
@@ -1092,6 +1103,11 @@ dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const
     const bool th_dev = is_device_ptr(theta), d_dev = is_device_ptr(delta),
                a_dev = is_device_ptr(A_out), e_dev = is_device_ptr(E_out);
     std::vector<double> th;
+    if (o.prec == DPT_PREC_MIXED_BF16 && dtype == DPT_R64 && th_dev && !o.epstein_nesbet)
+      // theta stays on the device: checked there (finite, distinct, max) by the solve
+      return done(solve_full_mixed_real(n, th, theta, (const double*)delta, d_dev, ld_delta,
+                                        lambda, o, (double*)A_out, a_dev, ld_a, (double*)E_out,
+                                        e_dev, info, s));
     dpt_status st = host_theta(n, theta, th_dev, th);
     if (st != DPT_OK) return done(st);
     if (o.epstein_nesbet) {
@@ -1114,8 +1130,8 @@ dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const
       st = solve_full_mixed_complex(n, th, (const double*)delta, d_dev, ld_delta, lambda, o,
                                     (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info, s);
     else if (o.prec == DPT_PREC_MIXED_BF16)
-      st = solve_full_mixed_real(n, th, (const double*)delta, d_dev, ld_delta, lambda, o,
-                                 (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info, s);
+      st = solve_full_mixed_real(n, th, nullptr, (const double*)delta, d_dev, ld_delta, lambda,
+                                 o, (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info, s);
     else
       st = solve_full_fp64(n, dtype == DPT_C128, th, (const double*)delta, d_dev, ld_delta,
                            lambda, o, (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info,

@@ -952,6 +952,38 @@ __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __
     Aout[(int64_t)i * ld_a + j] = f2d_bits(hi[(int64_t)i * ld + j]) + f2d_bits(lo[(int64_t)i * ld + j]);
 }
 
+// Checks of a device-resident theta: finite, pairwise distinct (Sec. II.B: simple
+// unperturbed levels), and max |theta| into the state (the residual scale), by
+// atomicMax on the bits of a non-negative double.  Grid (256-blocks of i, 256-blocks
+// of j), upper triangle only: each block stages its 256 theta_j in shared memory and
+// thread i compares theta_i with those j > i.
+__global__ void __launch_bounds__(256) k_check_theta(int n, const double* __restrict__ th,
+                                                     IterState* st) {
+  if (blockIdx.y < blockIdx.x) return;
+  __shared__ double tj[256];
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  const int j0 = blockIdx.y * 256;
+  tj[threadIdx.x] = (j0 + (int)threadIdx.x < n) ? th[j0 + threadIdx.x] : 0.0;
+  __syncthreads();
+  double amax = 0.0;
+  if (i < n) {
+    const double ti = th[i];
+    if (!finite_bits(ti)) {
+      if (blockIdx.y == blockIdx.x) atomicCAS(&st->status, ST_RUNNING, ST_BADINPUT);
+    } else {
+      if (blockIdx.y == blockIdx.x) amax = fabs(ti);
+      const int jend = min(256, n - j0);
+      bool dup = false;
+      for (int q = max(0, i + 1 - j0); q < jend; ++q) dup |= (tj[q] == ti);
+      if (dup) atomicCAS(&st->status, ST_RUNNING, ST_DEGENERATE);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0 && amax > 0.0)
+    atomicMax(reinterpret_cast<unsigned long long*>(&st->theta_max),
+              (unsigned long long)__double_as_longlong(amax));
+}
+
 __global__ void k_theta_ff(int n, const double* __restrict__ th, float* __restrict__ hi,
                            float* __restrict__ lo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -989,6 +1021,11 @@ cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld,
                               __nv_bfloat16* Dcat, IterState* st, cudaStream_t s) {
   dim3 grid(ld / 64, (n + 31) / 32), block(32, 8);     // ld is a multiple of 128
   k_prep_delta<<<grid, block, 0, s>>>(delta, ld_in, n, ld, en, Dcat, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_theta(int n, const double* th, IterState* st, cudaStream_t s) {
+  k_check_theta<<<dim3((n + 255) / 256, (n + 255) / 256), 256, 0, s>>>(n, th, st);
   return cudaGetLastError();
 }
 

@@ -167,6 +167,8 @@ cudaError_t mixed_set_attributes();   // once per device, before any capture
 cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en,
                               __nv_bfloat16* Dcat, IterState* st, cudaStream_t s);
 cudaError_t launch_theta_ff(int n, const double* th, float* hi, float* lo, cudaStream_t s);
+// finite and pairwise distinct theta (status ST_BADINPUT / ST_DEGENERATE), max |theta|
+cudaError_t launch_check_theta(int n, const double* th, IterState* st, cudaStream_t s);
 cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
                          const float* th_lo, double lam, int n, int ld, int en,
                          const __nv_bfloat16* Dcat, float* Ahi1, float* Alo1,

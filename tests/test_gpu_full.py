@@ -204,3 +204,16 @@ def test_repeated_solves_identical(dpt):
     dpt.solve_full(*_dev(other), other["lam"])
     A2, E2, _ = dpt.solve_full(th, D, cfg["lam"])
     assert torch.equal(A1, A2) and torch.equal(E1, E2)
+
+
+@pytest.mark.parametrize("graph_iters", [0, 1, 2, 3, 4, 5, 7])
+def test_profiled_solves_any_chunk_size(dpt, graph_iters):
+    """Per-launch profiling with every chunk size, including chunks that end exactly at
+    convergence: the counted product launches equal the iterations."""
+    cfg = inputs.full_unsymmetric(n=512, rep=21)
+    th = torch.tensor(cfg["theta"], device="cuda")
+    D = dpt.colmajor_tensor(cfg["delta"], "cuda")
+    _, _, info = dpt.solve_full(th, D, cfg["lam"], profile=True, graph_iters=graph_iters)
+    assert info["status"] == "OK"
+    assert info["product_launches"] == info["iters"]
+    assert info["product_ms"] > 0
