@@ -957,13 +957,21 @@ __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __
 // atomicMax on the bits of a non-negative double.  Grid (256-blocks of i, 256-blocks
 // of j), upper triangle only: each block stages its 256 theta_j in shared memory and
 // thread i compares theta_i with those j > i.
+// Finite doubles are equal exactly when their bit patterns are, once -0 is read as +0:
+// the comparisons run as 64-bit integer compares (the FP64 pipe of GB300 is slow).
+__device__ __forceinline__ unsigned long long eq_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return b == 0x8000000000000000ull ? 0ull : b;
+}
+
 __global__ void __launch_bounds__(256) k_check_theta(int n, const double* __restrict__ th,
                                                      IterState* st) {
   if (blockIdx.y < blockIdx.x) return;
-  __shared__ double tj[256];
+  __shared__ unsigned long long tj[256];
   const int i = blockIdx.x * 256 + threadIdx.x;
   const int j0 = blockIdx.y * 256;
-  tj[threadIdx.x] = (j0 + (int)threadIdx.x < n) ? th[j0 + threadIdx.x] : 0.0;
+  // entries past n hold a pattern no finite value has
+  tj[threadIdx.x] = (j0 + (int)threadIdx.x < n) ? eq_key(th[j0 + threadIdx.x]) : ~0ull;
   __syncthreads();
   double amax = 0.0;
   if (i < n) {
@@ -972,9 +980,12 @@ __global__ void __launch_bounds__(256) k_check_theta(int n, const double* __rest
       if (blockIdx.y == blockIdx.x) atomicCAS(&st->status, ST_RUNNING, ST_BADINPUT);
     } else {
       if (blockIdx.y == blockIdx.x) amax = fabs(ti);
-      const int jend = min(256, n - j0);
+      const unsigned long long ki = eq_key(ti);
+      // diagonal block: only j > i; blocks to the right: all 256
+      const int q0 = (blockIdx.y == blockIdx.x) ? (int)threadIdx.x + 1 : 0;
       bool dup = false;
-      for (int q = max(0, i + 1 - j0); q < jend; ++q) dup |= (tj[q] == ti);
+#pragma unroll 8
+      for (int q = 0; q < 256; ++q) dup |= (q >= q0) & (tj[q] == ki);
       if (dup) atomicCAS(&st->status, ST_RUNNING, ST_DEGENERATE);
     }
   }
