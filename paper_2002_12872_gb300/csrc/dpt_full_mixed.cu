@@ -211,33 +211,36 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
                                               float* __restrict__ e_col,
                                               float* __restrict__ dprev_col, IterState* st) {
   if (st->status != ST_RUNNING) return;
-  // 64 columns per block, 4 threads per column each summing every 4th tile partial
-  __shared__ float sh[3][4][64];
-  __shared__ double she[4][64];
-  const int c = threadIdx.x & 63, g = threadIdx.x >> 6;
-  const int i = blockIdx.x * 64 + c;
+  // 32 columns per block, 8 threads per column each summing every 8th tile partial
+  // (short chains of independent loads: the partials were just written, in L2)
+  __shared__ float sh[3][8][32];
+  __shared__ double she[8][32];
+  const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int i = blockIdx.x * 32 + c;
   const bool first = (st->k == 0);
   {
     float r2 = 0.f, a2 = 0.f, rs = 0.f;
     double ep = 0.0;
     if (i < n) {
-      for (int t = g; t < ntm; t += 4) {
+#pragma unroll 4
+      for (int t = g; t < ntm; t += 8) {
         r2 += part[((int64_t)0 * ntm + t) * ld + i];
         a2 += part[((int64_t)1 * ntm + t) * ld + i];
         ep += (double)part[((int64_t)2 * ntm + t) * ld + i] +
               (double)part[((int64_t)3 * ntm + t) * ld + i];
       }
       if (first)
-        for (int t = g; t < ntn; t += 4) rs += rowpart[(int64_t)t * ld + i];
+        for (int t = g; t < ntn; t += 8) rs += rowpart[(int64_t)t * ld + i];
     }
     sh[0][g][c] = r2; sh[1][g][c] = a2; sh[2][g][c] = rs; she[g][c] = ep;
   }
   __syncthreads();
   float rho_raw = 0.f;
   if (g == 0 && i < n) {
-    const float r2 = ((sh[0][0][c] + sh[0][1][c]) + sh[0][2][c]) + sh[0][3][c];
-    const float a2 = ((sh[1][0][c] + sh[1][1][c]) + sh[1][2][c]) + sh[1][3][c];
-    const double ep = ((she[0][c] + she[1][c]) + she[2][c]) + she[3][c];
+    float r2 = 0.f, a2 = 0.f;
+    double ep = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) { r2 += sh[0][q][c]; a2 += sh[1][q][c]; ep += she[q][c]; }
     rho_raw = sqrtf(r2 / a2);
     if (!(rho_raw == rho_raw) || isinf(rho_raw)) rho_raw = __int_as_float(0x7f800000);
     const double dk = d[i];
@@ -246,7 +249,9 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
     e_col[i] = (float)ep;
     d[i] = dk + ep;
     if (first) {
-      const float rs = ((sh[2][0][c] + sh[2][1][c]) + sh[2][2][c]) + sh[2][3][c];
+      float rs = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) rs += sh[2][q][c];
       atomicMax(&st->row_bits, __float_as_uint(rs));
     }
   }
@@ -1062,7 +1067,7 @@ cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,
                         float* dprev_col, IterState* st, cudaStream_t s) {
   const int ntm = (n + BM - 1) / BM, ntn = (n + IT0 - 1) / IT0;   // row partials: 128-wide blocks
-  k_ctrl<<<(n + 63) / 64, 256, 0, s>>>(n, ld, ntm, ntn, part, rowpart, theta, d, E, e_col,
+  k_ctrl<<<(n + 31) / 32, 256, 0, s>>>(n, ld, ntm, ntn, part, rowpart, theta, d, E, e_col,
                                        dprev_col, st);
   return cudaGetLastError();
 }
