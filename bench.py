@@ -48,10 +48,13 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the dominant-CSR, batched and served workloads")
+                    help="skip the dominant (CSR and dense), batched and served workloads")
     ap.add_argument("--only", default="all",
-                    choices=["all", "dominant", "batched", "served", "served_pool"],
+                    choices=["all", "dominant", "dominant_dense", "batched", "served",
+                             "served_pool"],
                     help="time one secondary workload alone and print its JSON object")
+    ap.add_argument("--dense-n", type=int, default=32768,
+                    help="dominant_dense: problem size")
     ap.add_argument("--pool-max-n", type=int, default=None,
                     help="served_pool: keep pool entries with n up to this size")
     return ap.parse_args()
@@ -289,6 +292,47 @@ def bench_dominant(dpt, inputs, dev, pk, steps=20, warmup=3):
                        "achieved": out["mixed"]["achieved_GBs"], "peak": pk["hbm_gbs"],
                        "unit": "GB/s", "frac": out["mixed"]["hbm_frac"],
                        "algorithmic_bytes_per_pass": bytes_iter}
+    return out
+
+
+def bench_dominant_dense(dpt, inputs, dev, pk, steps=10, warmup=3, n=32768):
+    """Dominant eigenvector with a dense FP64 Delta (GEMV form), n = 32768, lambda =
+    0.1.  Algorithmic bytes per GEMV pass: Delta once (8 n^2) and z (8 n).  Delta
+    (8.6 GB) is far larger than L2, so no flush is needed between passes."""
+    import torch
+    cfg = inputs.dominant_dense_device(n=n, device=dev)
+    th, D, lam = cfg["theta"], cfg["delta"], cfg["lam"]
+    z = torch.empty(n, dtype=torch.float64, device=dev)
+    bytes_pass = 8.0 * n * n + 8.0 * n
+    out = {"workload": f"dominant eigenvector, dense FP64 n={n}, Delta iid N(0,1/n), "
+                       f"theta U[0,1] with theta_0=2, lambda={lam}, tol=1e-12"}
+    for prec in ("mixed", "fp64"):
+        for _ in range(warmup):
+            dpt.solve_dominant_dense(th, D, lam, prec=prec, z_out=z, profile=True)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pm, pl, its = 0.0, 0, []
+        e0.record(stream)
+        for _ in range(steps):
+            _, E, info = dpt.solve_dominant_dense(th, D, lam, prec=prec, z_out=z, profile=True)
+            pm += info["product_ms"]
+            pl += info["product_launches"]
+            its.append(info["iters"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        per_pass = pm / max(1, pl)
+        gbs = bytes_pass / (per_pass * 1e-3) / 1e9
+        out[prec] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iters": float(np.mean(its)),
+                     "gemv_ms_per_pass": per_pass, "achieved_GBs": gbs,
+                     "hbm_frac": gbs / pk["hbm_gbs"], "E": E}
+    out["roofline"] = {"bound": "hbm", "kernel": "k_dd_gemv (float-float GEMV)",
+                       "achieved": out["mixed"]["achieved_GBs"], "peak": pk["hbm_gbs"],
+                       "unit": "GB/s", "frac": out["mixed"]["hbm_frac"],
+                       "algorithmic_bytes_per_pass": bytes_pass}
+    del D, cfg
+    torch.cuda.empty_cache()
     return out
 
 
@@ -590,6 +634,7 @@ def run_ours(args, world, rank, local):
     extra = {}
     if not args.no_extra:
         extra["dominant_csr"] = bench_dominant(dpt, inputs, dev, pk)
+        extra["dominant_dense"] = bench_dominant_dense(dpt, inputs, dev, pk)
         extra["batched"] = bench_batched(dpt, inputs, dev)
         extra["served"] = bench_served(dpt, inputs, dev)
         extra["served_pool"] = bench_served_pool(dpt, inputs, dev)
@@ -642,6 +687,9 @@ def main():
         pk, _ = peaks()
         if args.only == "dominant":
             out = bench_dominant(dpt, inputs, dev, pk)
+        elif args.only == "dominant_dense":
+            out = bench_dominant_dense(dpt, inputs, dev, pk, steps=max(1, min(args.steps, 10)),
+                                       warmup=max(1, min(args.warmup, 3)), n=args.dense_n)
         elif args.only == "batched":
             out = bench_batched(dpt, inputs, dev)
         elif args.only == "served_pool":

@@ -203,6 +203,28 @@ DPT_API dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int3
                                       double lambda, const dpt_options* opt, double* z_out,
                                       double* E_out, dpt_info* info, void* stream);
 
+/* Dominant eigenvector with a dense perturbation: the map of dpt_solve_dominant
+ * (Eq. (single_line_dyn), Sec. II.H) with y = Delta z formed by a GEMV.  Every
+ * iteration streams Delta from device memory once (8 bytes per entry), so the
+ * solve is bound by memory bandwidth.
+ *   n          size, 1 <= n <= 2^20 (Delta must fit in device memory)
+ *   theta      n doubles, finite; theta_m != theta_{n*} for every m != n*
+ *   delta      column-major n x n FP64 (entry (m, k) at delta[m + k ld_delta]),
+ *              host or device; a host matrix is first copied to the device
+ *   ld_delta   leading dimension, >= n
+ *   nstar, lambda, opt, z_out, E_out, info   as for dpt_solve_dominant
+ *              (prec DPT_PREC_MIXED_BF16: each FP64 entry is split exactly enough
+ *              into two floats and the products summed in float-float on the FP32
+ *              pipes; DPT_PREC_FP64: plain FP64 arithmetic)
+ * A non-finite entry of Delta gives DPT_ERR_ARG (detected during the first pass,
+ * before any result is returned), and so does, in the float-float form only, an
+ * entry of magnitude 2^128 or more (beyond the FP32 exponent range).  Blocks until
+ * done. */
+DPT_API dpt_status dpt_solve_dominant_dense(int64_t n, const double* theta, const double* delta,
+                                            int64_t ld_delta, int64_t nstar, double lambda,
+                                            const dpt_options* opt, double* z_out,
+                                            double* E_out, dpt_info* info, void* stream);
+
 /* dpt_solve_dominant for callers that cannot allocate device memory.  (This entry
  * point has no counterpart in the paper; it is a deployment variant of
  * dpt_solve_dominant.)

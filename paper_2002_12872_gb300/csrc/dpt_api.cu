@@ -670,6 +670,152 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
 }
 
 // ---------------------------------------------------------------------------
+// Dominant eigenvector, dense perturbation (GEMV)
+// ---------------------------------------------------------------------------
+dpt_status solve_dominant_dense(int64_t n64, const double* theta, const double* delta,
+                                int64_t ld_delta, int64_t nstar, double lambda,
+                                const dpt_options& o, double* z_out, double* E_out,
+                                dpt_info* info, cudaStream_t user) {
+  const int n = (int)n64;
+  const bool th_dev = is_device_ptr(theta), d_dev = is_device_ptr(delta),
+             z_dev = is_device_ptr(z_out), e_dev = is_device_ptr(E_out);
+  const bool ff = o.prec != DPT_PREC_FP64;
+  DDParams p{};
+  p.n = n;
+  p.ld = d_dev ? ld_delta : round_up(n, 2);
+  const bool al16 = d_dev ? ((uintptr_t)delta % 16 == 0) : true;
+  dd_plan(p, al16);
+  const int G = dd_update_blocks(n);
+  const size_t parts = (size_t)p.nslices * n;
+  auto layout = [&](Carve& c) {
+    c.take<DomState>(1);
+    c.take<float>(n); c.take<float>(n);                 // theta float-float
+    for (int q = 0; q < 2; ++q) c.take<float2>(n);      // z float-float ping-pong
+    if (!ff) { c.take<double>(n); c.take<double>(n); }  // z FP64 ping-pong
+    if (ff) c.take<float2>(parts); else c.take<double>(parts);   // y slice partials
+    c.take<float>(parts);                               // |Delta| row-sum partials
+    c.take<double>((size_t)2 * G);                      // block partials
+    if (!th_dev) c.take<double>(n);
+    if (!d_dev) c.take<double>((size_t)p.ld * n);
+    if (!z_dev) c.take<double>(n);
+  };
+  Block* b = acquire(measure(layout));
+  dpt_status ret = DPT_OK;
+  try {
+    Carve c{(char*)b->ptr};
+    DomState* st = c.take<DomState>(1);
+    float* thh = c.take<float>(n);
+    float* thl = c.take<float>(n);
+    p.z0 = c.take<float2>(n);
+    p.z1 = c.take<float2>(n);
+    if (!ff) { p.z64_0 = c.take<double>(n); p.z64_1 = c.take<double>(n); }
+    if (ff) p.ypart = c.take<float2>(parts); else p.ypart64 = c.take<double>(parts);
+    p.rowabs = c.take<float>(parts);
+    p.part = c.take<double>((size_t)2 * G);
+    cudaStream_t s = b->stream;
+    CK(cudaEventRecord(b->ev, user));
+    CK(cudaStreamWaitEvent(s, b->ev, 0));
+    const double* thd = theta;
+    if (!th_dev) {
+      double* t = c.take<double>(n);
+      CK(cudaMemcpyAsync(t, theta, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      thd = t;
+    }
+    const double* Dd = delta;
+    if (!d_dev) {
+      double* t = c.take<double>((size_t)p.ld * n);
+      CK(cudaMemcpy2DAsync(t, sizeof(double) * p.ld, delta, sizeof(double) * ld_delta,
+                           sizeof(double) * n, n, cudaMemcpyHostToDevice, s));
+      Dd = t;
+    }
+    double* zstage = z_dev ? z_out : c.take<double>(n);
+    p.delta = Dd;
+    p.th_hi = thh;
+    p.th_lo = thl;
+    p.theta = thd;
+    p.st = st;
+
+    DomState h{};
+    h.status = ST_RUNNING;
+    h.max_iter = o.max_iter;
+    h.nstar_req = (int)nstar;
+    h.nstar_min = 0x7fffffff;
+    h.lam = lambda;
+    h.lam_hi = (float)lambda;
+    h.lam_lo = (float)(lambda - (double)h.lam_hi);
+    h.tol = o.tol;
+    h.best = INFINITY;
+    DomState* hs = reinterpret_cast<DomState*>(b->host_state);
+    *hs = h;
+    CK(cudaMemcpyAsync(st, hs, sizeof(DomState), cudaMemcpyHostToDevice, s));
+    CK(launch_dd_setup(n, thd, thh, thl, st, s));
+    CK(cudaMemcpyAsync(hs, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hs->bad_input) throw Fail{DPT_ERR_ARG};
+    if (hs->ties != 1u) throw Fail{DPT_ERR_DEGENERATE};
+    const int nst = hs->nstar;
+    // z_0 = e_{n*}; the residual scale is formed by the first pass
+    CK(launch_dom_init(n, p.z0, p.z64_0, ff, st, s));
+    Prof prof;
+    prof.on = o.profile != 0;
+    // theta set-up, n* selection (3), z_0 (1, or 2 for FP64), the first pass (2)
+    prof.launches = ff ? 7 : 8;
+    // The first pass (it also checks Delta and forms the residual scale) has its
+    // own kernel instances and event pair; the state is read back with the loop's.
+    struct EvPair {
+      cudaEvent_t e[2] = {nullptr, nullptr};
+      ~EvPair() { for (auto x : e) if (x) cudaEventDestroy(x); }
+    } fp;
+    if (prof.on) {
+      CK(cudaEventCreate(&fp.e[0]));
+      CK(cudaEventCreate(&fp.e[1]));
+      CK(cudaEventRecord(fp.e[0], s));
+    }
+    CK(launch_dd_gemv(p, ff, 1, s));
+    if (prof.on) CK(cudaEventRecord(fp.e[1], s));
+    CK(launch_dd_update(p, ff, 1, s));
+    run_loop(b, reinterpret_cast<IterState*>(st), o.graph_iters, o.max_iter, 2, prof,
+             [&](int q) {
+               prof.before(q, s);
+               CK(launch_dd_gemv(p, ff, 0, s));
+               prof.after(q, s);
+               CK(launch_dd_update(p, ff, 0, s));
+             },
+             sizeof(DomState), 1);
+    prof.live += 1;
+    if (prof.on) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, fp.e[0], fp.e[1]));
+      prof.ms += t;
+    }
+    CK(launch_dom_out(n, p.z0, p.z1, p.z64_0, p.z64_1, ff, zstage, st, s));
+    prof.launches += 1;
+    if (!z_dev) CK(cudaMemcpyAsync(z_out, zstage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hs, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ret = from_state(hs->status);
+    if (e_dev) CK(cudaMemcpy(E_out, &hs->E, sizeof(double), cudaMemcpyHostToDevice));
+    else *E_out = hs->E;
+    if (info) {
+      info->iters = hs->k;
+      info->residual = hs->rho;
+      info->status = ret;
+      info->nstar = nst;
+      info->launches = prof.launches;
+      info->product_launches = prof.live;
+      info->product_ms = prof.ms;
+    }
+    CK(cudaEventRecord(b->ev, s));
+    CK(cudaStreamWaitEvent(user, b->ev, 0));
+  } catch (Fail f) {
+    cudaStreamSynchronize(b->stream);
+    ret = f.st;
+  }
+  release(b);
+  return ret;
+}
+
+// ---------------------------------------------------------------------------
 // Grouped solve of many independent real problems (mixed path)
 // ---------------------------------------------------------------------------
 }  // namespace
@@ -1164,6 +1310,33 @@ dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int32_t* row
   try {
     return done(solve_dominant(n, theta, row_ptr, col_idx, vals, nstar < 0 ? -1 : nstar, lambda,
                                o, z_out, E_out, info, (cudaStream_t)stream));
+  } catch (Fail f) {
+    return done(f.st);
+  } catch (...) {
+    return done(DPT_ERR_CUDA);
+  }
+}
+
+dpt_status dpt_solve_dominant_dense(int64_t n, const double* theta, const double* delta,
+                                    int64_t ld_delta, int64_t nstar, double lambda,
+                                    const dpt_options* opt, double* z_out, double* E_out,
+                                    dpt_info* info, void* stream) {
+  Timer timer;
+  if (info) { std::memset(info, 0, sizeof(*info)); info->status = DPT_ERR_ARG; info->nstar = -1; }
+  dpt_options o;
+  dpt_options_default(&o);
+  if (opt) o = *opt;
+  auto done = [&](dpt_status st) {
+    if (info) { info->status = st; info->seconds = timer.sec(); }
+    return st;
+  };
+  if (n < 1 || n > (1 << 20) || !theta || !delta || ld_delta < n || !z_out || !E_out ||
+      nstar >= n || !std::isfinite(lambda) || !(o.tol > 0) || o.max_iter < 0 ||
+      (o.prec != DPT_PREC_FP64 && o.prec != DPT_PREC_MIXED_BF16))
+    return done(DPT_ERR_ARG);
+  try {
+    return done(solve_dominant_dense(n, theta, delta, ld_delta, nstar < 0 ? -1 : nstar, lambda,
+                                     o, z_out, E_out, info, (cudaStream_t)stream));
   } catch (Fail f) {
     return done(f.st);
   } catch (...) {

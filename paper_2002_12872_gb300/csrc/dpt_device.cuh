@@ -78,6 +78,13 @@ __device__ __forceinline__ bool finite_bits(double v) {
   return ((unsigned)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FFu) != 0x7FFu;
 }
 
+// Order-preserving integer key of a double (larger key <=> larger value, for
+// non-NaN values), so that maxima can be taken with integer atomics.
+__device__ __forceinline__ unsigned long long ordered_bits(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
 // Exact float -> double by bit construction (zero and normal floats; subnormal
 // floats, which this library never produces, fall back to the conversion).
 __device__ __forceinline__ double f2d_bits(float f) {

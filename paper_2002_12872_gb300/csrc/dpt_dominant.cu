@@ -47,11 +47,6 @@ __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, f
 // ---------------------------------------------------------------------------
 // Set-up: theta -> float-float, residual scale row sums, CSR validity, argmax.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long ordered_bits(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-
 __global__ void k_dom_setup(int n, const double* __restrict__ theta,
                             const int32_t* __restrict__ row_ptr,
                             const int32_t* __restrict__ col_idx, const float* __restrict__ vals,
@@ -419,8 +414,12 @@ cudaError_t launch_dom_check(int n, int64_t nnz, const int32_t* row_ptr, DomStat
 cudaError_t launch_dom_setup(int n, const double* theta, const int32_t* row_ptr,
                              const int32_t* col_idx, const float* vals, float* th_hi,
                              float* th_lo, DomState* st, cudaStream_t s) {
+  k_dom_setup<<<dom_grid(n), 256, 0, s>>>(n, theta, row_ptr, col_idx, vals, th_hi, th_lo, st);
+  return launch_dom_select(n, theta, st, s);
+}
+
+cudaError_t launch_dom_select(int n, const double* theta, DomState* st, cudaStream_t s) {
   const int g = dom_grid(n);
-  k_dom_setup<<<g, 256, 0, s>>>(n, theta, row_ptr, col_idx, vals, th_hi, th_lo, st);
   k_dom_argmax<<<g, 256, 0, s>>>(n, theta, st);
   k_dom_pick<<<1, 1, 0, s>>>(st);
   k_dom_ties<<<g, 256, 0, s>>>(n, theta, st);

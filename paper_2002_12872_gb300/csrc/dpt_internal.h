@@ -208,6 +208,33 @@ cudaError_t launch_dom_iter(int n, int vlanes, int ff, const int32_t* row_ptr,
                             const float* th_lo, const double* theta, float2* z0, float2* z1,
                             double* z64_0, double* z64_1, double* part, DomState* st,
                             cudaStream_t s);
+cudaError_t launch_dom_select(int n, const double* theta, DomState* st, cudaStream_t s);
+
+// Dense dominant form (GEMV): arguments of one iteration's two kernels.
+struct DDParams {
+  int n, vec, slice, nslices;      // size, rows per thread, columns per slice, slices
+  int64_t ld;                      // leading dimension of Delta (elements)
+  const double* delta;             // column-major FP64
+  float2* z0;                      // z ping-pong, float-float
+  float2* z1;
+  double* z64_0;                   // z ping-pong, FP64 (comparator)
+  double* z64_1;
+  float2* ypart;                   // slice partials of y, [nslices][n]
+  double* ypart64;
+  float* rowabs;                   // slice partials of sum_k |Delta_mk| (first pass)
+  const float* th_hi;
+  const float* th_lo;
+  const double* theta;
+  double* part;                    // per-block norm partials of the update kernel
+  DomState* st;
+};
+int dd_slice(int n, int vec, int nsm);
+void dd_plan(DDParams& p, bool aligned16);
+int dd_update_blocks(int n);
+cudaError_t launch_dd_setup(int n, const double* theta, float* th_hi, float* th_lo, DomState* st,
+                            cudaStream_t s);
+cudaError_t launch_dd_gemv(const DDParams& p, int ff, int first, cudaStream_t s);
+cudaError_t launch_dd_update(const DDParams& p, int ff, int first, cudaStream_t s);
 cudaError_t launch_dom_out(int n, const float2* z0, const float2* z1, const double* z64_0,
                            const double* z64_1, int ff, double* out, const DomState* st,
                            cudaStream_t s);

@@ -103,6 +103,10 @@ def lib() -> ctypes.CDLL:
         L.dpt_solve_dominant.argtypes = [i64, P, P, P, P, i64, dbl, ctypes.POINTER(Options),
                                          P, P, ctypes.POINTER(Info), P]
         L.dpt_solve_dominant.restype = ctypes.c_int
+        L.dpt_solve_dominant_dense.argtypes = [i64, P, P, i64, i64, dbl,
+                                               ctypes.POINTER(Options), P, P,
+                                               ctypes.POINTER(Info), P]
+        L.dpt_solve_dominant_dense.restype = ctypes.c_int
         L.dpt_solve_dominant_noalloc.argtypes = [i64, P, P, P, P, i64, dbl, dbl,
                                                  ctypes.c_int32, P, P, ctypes.POINTER(Info), P]
         L.dpt_solve_dominant_noalloc.restype = ctypes.c_int
@@ -359,6 +363,31 @@ def solve_dominant(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, prec="mixed"
     res = (z_out, float(E[0]), info.as_dict())
     if check and st != OK:
         err = RuntimeError(f"dpt_solve_dominant: {status_string(st)}")
+        err.result = res
+        raise err
+    return res
+
+
+def solve_dominant_dense(theta, delta, lam, *, nstar=-1, prec="mixed", tol=1e-12, max_iter=200,
+                         graph_iters=None, profile=False, z_out=None, stream=None, check=True):
+    """Dominant eigenpair by the single-vector map with a dense FP64 perturbation
+    (dpt_solve_dominant_dense, a GEMV per iteration).  Returns (z, E, info) with
+    z[n*] = 1."""
+    n = int(theta.shape[0])
+    th_ptr, k1 = _vec_ptr(theta, "float64")
+    d_ptr, ldd, k2 = _colmajor(delta, False)
+    if z_out is None:
+        z_out = _empty_vec(n, theta, False)
+    E = np.zeros(1)
+    o = options(tol=tol, max_iter=max_iter, prec=prec, graph_iters=graph_iters,
+                profile=int(bool(profile)))
+    info = Info()
+    st = lib().dpt_solve_dominant_dense(n, th_ptr, d_ptr, ldd, int(nstar), float(lam),
+                                        ctypes.byref(o), _ptr(z_out), E.ctypes.data,
+                                        ctypes.byref(info), _stream_of(theta, stream))
+    res = (z_out, float(E[0]), info.as_dict())
+    if check and st != OK:
+        err = RuntimeError(f"dpt_solve_dominant_dense: {status_string(st)}")
         err.result = res
         raise err
     return res

@@ -19,6 +19,9 @@ sparse perturbations, Sec. II.G-H, are synthetic, so these stand in for them):
   dominant_csr       theta_m ~ U[0, 1] with theta_0 = 2, 16 distinct sorted column
                      indices per row drawn uniformly, values N(0, 1) in FP32,
                      lam 0.01
+  dominant_dense     theta_m ~ U[0, 1] with theta_0 = 2, Delta iid N(0, 1/n)
+                     dense FP64, lam 0.1 (the GEMV form; drawn on the device
+                     by torch's seeded generator at sizes beyond a few thousand)
   batched_symmetric  n log-uniform in [32, 512], theta_i = i + U(-0.2, 0.2),
                      symmetric Delta as above, lam ~ U[0.01, 0.1]
   served_hermitian   Poisson arrivals, n log-uniform in [64, 4096], theta_i = i,
@@ -110,6 +113,31 @@ def dominant_csr(n: int = 2_000_000, nnz_per_row: int = 16, rep: int = 0,
     vals = rng.standard_normal(n * k).astype(np.float32)
     return {"n": n, "theta": theta, "row_ptr": row_ptr, "col_idx": col_idx,
             "vals": vals, "lam": lam, "nstar": 0, "tol": 1e-12}
+
+
+def dominant_dense(n: int = 32768, rep: int = 0, lam: float = 0.1) -> dict:
+    """Dense unsymmetric workload for the dominant-eigenvector form (GEMV):
+    theta_m ~ U[0, 1] with theta_0 = 2 set apart, Delta iid N(0, 1/n) (column-major
+    FP64)."""
+    rng = rng_for(6, rep)
+    theta = rng.uniform(0.0, 1.0, size=n)
+    theta[0] = 2.0
+    delta = np.asfortranarray(rng.standard_normal((n, n)) / np.sqrt(n))
+    return {"n": n, "theta": theta, "delta": delta, "lam": lam, "nstar": 0, "tol": 1e-12}
+
+
+def dominant_dense_device(n: int = 32768, rep: int = 0, lam: float = 0.1, device="cuda"):
+    """dominant_dense's recipe drawn on the device with torch's seeded generator
+    (sizes whose host generation would dominate a run).  Returns theta (n) and the
+    column-major Delta as the transpose view of a row-major tensor."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed_for(6, rep))
+    theta = torch.rand(n, generator=g, device=device, dtype=torch.float64)
+    theta[0] = 2.0
+    rows = torch.randn(n, n, generator=g, device=device, dtype=torch.float64)
+    rows.mul_(1.0 / np.sqrt(n))
+    return {"n": n, "theta": theta, "delta": rows.t(), "lam": lam, "nstar": 0, "tol": 1e-12}
 
 
 def csr_to_dense(row_ptr, col_idx, vals, n) -> np.ndarray:

@@ -66,6 +66,19 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.dpt_solve_full(4, 0, p(th), p(d), 4, 0.1, ctypes.byref(o2), p(A), 4, p(E),
                               ctypes.byref(info), None) == -1
     assert info.status == -1
+    # dense dominant form: n < 1, ld_delta < n, nstar >= n, non-finite lambda
+    z = np.zeros(4)
+    Eo = np.zeros(1)
+    dd = lib.dpt_solve_dominant_dense
+    assert dd(0, p(th), p(d), 4, -1, 0.1, ctypes.byref(o), p(z), p(Eo),
+              ctypes.byref(info), None) == -1
+    assert dd(4, p(th), p(d), 3, -1, 0.1, ctypes.byref(o), p(z), p(Eo),
+              ctypes.byref(info), None) == -1
+    assert dd(4, p(th), p(d), 4, 4, 0.1, ctypes.byref(o), p(z), p(Eo),
+              ctypes.byref(info), None) == -1
+    assert dd(4, p(th), p(d), 4, -1, float("nan"), ctypes.byref(o), p(z), p(Eo),
+              ctypes.byref(info), None) == -1
+    assert info.status == -1 and info.nstar == -1
 
 
 def test_selftest_and_server_arguments_rejected_without_gpu(lib):
