@@ -210,7 +210,9 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     from paper_2002_12872_gb300 import inputs
-    cores = os.cpu_count() or 1
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
     cfg = inputs.full_unsymmetric(n=N)
     _, t1, _ = cpu_oracle(cfg, 1, seed=12345)            # calibration, not timed
     budget = 150.0 / max(1, args.steps + args.warmup)   # seconds per step
@@ -235,15 +237,25 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_sized(cfg, target_s=15.0):
-    """The oracle on a column sample sized to about target_s seconds of work."""
-    cores = os.cpu_count() or 1
+def cpu_baseline_sized(cfg, target_s=15.0, single_s=8.0):
+    """The oracle on a column sample sized to about target_s seconds of work on all
+    host threads, and on a smaller sample (about single_s seconds) on one thread."""
+    import oracle
+    oracle.build()
+    cores = oracle.set_threads(os.cpu_count() or 1)
     _, t, _ = cpu_oracle(cfg, cores, seed=1)             # calibration
     ncols = int(min(cfg["n"], max(1, cores * max(1, round(target_s / max(t, 1e-3))))))
     v, dt, info = cpu_oracle(cfg, ncols, seed=2)
+    oracle.set_threads(1)
+    n1 = int(min(cfg["n"], max(1, round(single_s / max(t, 1e-3)))))
+    v1, dt1, info1 = cpu_oracle(cfg, n1, seed=3)
+    oracle.set_threads(cores)
     return {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
             "sample": f"{ncols} of {cfg['n']} columns ({dt:.1f} s on {cores} threads), "
-                      f"scaled by n/{ncols}; status {info['status']}"}
+                      f"scaled by n/{ncols}; status {info['status']}",
+            "single_core": {"value": v1, "unit": "solves/s", "cores": 1,
+                            "sample": f"{n1} of {cfg['n']} columns ({dt1:.1f} s on 1 thread), "
+                                      f"scaled by n/{n1}; status {info1['status']}"}}
 
 
 # ---------------------------------------------------------------------------

@@ -182,6 +182,17 @@ DPT_API dpt_status dpt_solve_batched(int64_t count, dpt_dtype dtype, const int64
                                      const int64_t* ld_a, double* const* E_out,
                                      dpt_info* infos, void* stream);
 
+/* Device workspace, in bytes, that one dpt_solve_full call of size n takes from the
+ * library's pool with the default options and with theta, Delta, A and E in device
+ * memory (host buffers add their staging copies: about 8 n^2 bytes each for Delta
+ * and A, twice that for DPT_C128).  The pool keeps its blocks, grown to the largest
+ * request so far, until dpt_release_workspace.  Mixed real: about 30 bytes per matrix
+ * element (BF16 slices of Delta, float-float A and its ping-pong copy, BF16
+ * increments, the carried remainder); plain FP64: 3 n^2 doubles (A, its ping-pong
+ * copy and the product) per real component.  Host-only computation (no CUDA call);
+ * -1 for n outside [1, 2^20] or an unknown dtype or prec. */
+DPT_API int64_t dpt_workspace_bytes(int64_t n, dpt_dtype dtype, dpt_prec prec);
+
 /* Dominant eigenvector: the eigenpair continued from e_{n*}, by the single-vector
  * map of Eq. (single_line_dyn) (Sec. II.H; for a perturbative matrix this is the
  * eigenvector of the largest eigenvalue when n* = argmax theta).

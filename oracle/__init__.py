@@ -144,6 +144,15 @@ def residual(theta, delta, lam, A, E):
     return m, rho
 
 
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's column-parallel loops (n <= 0: unchanged); returns
+    the count in effect."""
+    f = lib().ora_set_threads
+    f.argtypes = [ctypes.c_int]
+    f.restype = ctypes.c_int
+    return int(f(int(n)))
+
+
 def solve_full(theta, delta, lam, tol=1e-12, max_iter=1000, cols=None,
                epstein_nesbet=False):
     """Full-spectrum DPT solve from A_0 = I (Sec. II.B) on the listed columns.

@@ -28,6 +28,21 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads for the parallel loops over independent columns (n <= 0 leaves the
+ * setting unchanged); returns the number in effect (1 without OpenMP). */
+int ora_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 /* ---- real FP64 instance ------------------------------------------------- */
 #define T double

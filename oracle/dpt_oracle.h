@@ -52,6 +52,11 @@ int ora_rs_series_r(int64_t n, const double* theta, const double* delta,
 
 int ora_jacobi_sym(int64_t n, const double* S, double* w, double* V);
 
+/* Threads for the column-parallel loops (n <= 0: unchanged); returns the count in
+ * effect.  Timing control only: no result depends on it beyond the summation
+ * order of the residual norms. */
+int ora_set_threads(int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -266,6 +266,25 @@ struct Timer {
 // ---------------------------------------------------------------------------
 // th: theta checked on the host (host input or Epstein-Nesbet shift); or, when it is
 // empty, theta_dev: the caller's device theta, checked on the device.
+// Workspace of one mixed real full solve (the carve order of solve_full_mixed_real).
+void layout_full_mixed_real(Carve& c, int n, bool delta_dev, bool a_dev) {
+  const int ld = (int)round_up(n, 128);
+  const int ntm = (n + 127) / 128, ntn = (n + 127) / 128;
+  c.take<IterState>(1);
+  c.take<double>(ld);                        // theta (shifted)
+  c.take<float>(ld); c.take<float>(ld);      // theta hi/lo
+  c.take<double>(ld); c.take<double>(ld);    // d, E
+  c.take<float>(ld); c.take<float>(ld);      // e_col, dprev_col
+  c.take<float>((size_t)4 * ntm * ld);       // column partials
+  c.take<float>((size_t)ntn * ld);           // row partials
+  c.take<__nv_bfloat16>((size_t)3 * ld * n); // Dcat (three BF16 slices)
+  for (int q = 0; q < 2; ++q) { c.take<float>((size_t)ld * n); c.take<float>((size_t)ld * n); }
+  for (int q = 0; q < 2; ++q) c.take<__nv_bfloat16>((size_t)ld * n);
+  c.take<float>((size_t)ld * n);             // L
+  if (!delta_dev) c.take<double>((size_t)ld * n);
+  if (!a_dev) c.take<double>((size_t)ld * n);
+}
+
 dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
                                  const double* theta_dev, const double* delta_in, bool delta_dev,
                                  int64_t ld_delta, double lambda, const dpt_options& o,
@@ -277,21 +296,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
   const int ld = (int)round_up(n64, 128);
   const int S = o.max_slices;
   const int ntm = (n + 127) / 128, ntn = (n + 127) / 128;
-  auto layout = [&](Carve& c) {
-    c.take<IterState>(1);
-    c.take<double>(ld);                        // theta (shifted)
-    c.take<float>(ld); c.take<float>(ld);      // theta hi/lo
-    c.take<double>(ld); c.take<double>(ld);    // d, E
-    c.take<float>(ld); c.take<float>(ld);      // e_col, dprev_col
-    c.take<float>((size_t)4 * ntm * ld);       // column partials
-    c.take<float>((size_t)ntn * ld);           // row partials
-    c.take<__nv_bfloat16>((size_t)3 * ld * n); // Dcat (three BF16 slices)
-    for (int q = 0; q < 2; ++q) { c.take<float>((size_t)ld * n); c.take<float>((size_t)ld * n); }
-    for (int q = 0; q < 2; ++q) c.take<__nv_bfloat16>((size_t)ld * n);
-    c.take<float>((size_t)ld * n);             // L
-    if (!delta_dev) c.take<double>((size_t)ld * n);
-    if (!a_dev) c.take<double>((size_t)ld * n);
-  };
+  auto layout = [&](Carve& c) { layout_full_mixed_real(c, n, delta_dev, a_dev); };
   Block* b = acquire(measure(layout));
   dpt_status ret = DPT_OK;
   try {
@@ -420,6 +425,18 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
 // ---------------------------------------------------------------------------
 // Full solve, plain FP64 (real or complex)
 // ---------------------------------------------------------------------------
+// Workspace of one plain FP64 full solve (the carve order of solve_full_fp64).
+void layout_full_fp64(Carve& c, int n, bool cplx, bool copy_delta) {
+  const int ld = (int)round_up(n, 64);
+  const int w = cplx ? 2 : 1;
+  c.take<IterState>(1);
+  c.take<double>(ld);                          // theta
+  c.take<double>((size_t)w * ld);              // E
+  for (int q = 0; q < 2; ++q) c.take<double>((size_t)w * ld * n);   // A ping-pong
+  c.take<double>((size_t)w * ld * n);          // P
+  if (copy_delta) c.take<double>((size_t)w * ld * n);
+}
+
 dpt_status solve_full_fp64(int64_t n64, bool cplx, const std::vector<double>& th,
                            const double* delta_in, bool delta_dev, int64_t ld_delta,
                            double lambda, const dpt_options& o, double* A_out, bool a_dev,
@@ -429,14 +446,7 @@ dpt_status solve_full_fp64(int64_t n64, bool cplx, const std::vector<double>& th
   const int ld = (int)round_up(n64, 64);
   const int w = cplx ? 2 : 1;   // doubles per element
   const bool copy_delta = !delta_dev || o.epstein_nesbet;
-  auto layout = [&](Carve& c) {
-    c.take<IterState>(1);
-    c.take<double>(ld);                          // theta
-    c.take<double>((size_t)w * ld);              // E
-    for (int q = 0; q < 2; ++q) c.take<double>((size_t)w * ld * n);   // A ping-pong
-    c.take<double>((size_t)w * ld * n);          // P
-    if (copy_delta) c.take<double>((size_t)w * ld * n);
-  };
+  auto layout = [&](Carve& c) { layout_full_fp64(c, n, cplx, copy_delta); };
   Block* b = acquire(measure(layout));
   dpt_status ret = DPT_OK;
   try {
@@ -977,6 +987,17 @@ void sort_tiles(std::vector<int2>& tiles, const GProb* probs) {
 
 namespace {
 
+// Workspace of one grouped solve of a planned group (the carve order of solve_batched).
+void layout_batched(Carve& c, int count, const GroupPlan& g) {
+  c.take<IterState>(count);
+  c.take<GProb>(count);
+  c.take<int2>(g.tiles.size());
+  c.take<int4>(g.prep_r.size() + g.prep_c.size());
+  c.take<int4>(g.blk_r.size() + g.blk_c.size());
+  c.take<int>(4);
+  c.take<char>(g.bytes);
+}
+
 dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* const* theta,
                          const double* const* delta, const int64_t* ld_delta,
                          const double* lambda, const dpt_options& o, double* const* A_out,
@@ -989,15 +1010,7 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
   plan_group(g, count, cplx, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, nullptr, nullptr,
              form);
   const size_t arena = g.bytes;
-  auto layout = [&](Carve& c) {
-    c.take<IterState>(count);
-    c.take<GProb>(count);
-    c.take<int2>(g.tiles.size());
-    c.take<int4>(g.prep_r.size() + g.prep_c.size());
-    c.take<int4>(g.blk_r.size() + g.blk_c.size());
-    c.take<int>(4);
-    c.take<char>(arena);
-  };
+  auto layout = [&](Carve& c) { layout_batched(c, count, g); };
   Block* b = acquire(measure(layout));
   dpt_status ret = DPT_OK;
   try {
@@ -1137,6 +1150,14 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
   return ret;
 }
 
+// Staging block of the complex mixed full solve: theta, Delta, A and E, contiguous.
+void layout_full_mixed_complex_stage(Carve& c, int n) {
+  c.take<double>(n);
+  c.take<double>((size_t)2 * n * n);
+  c.take<double>((size_t)2 * n * n);
+  c.take<double>((size_t)2 * n);
+}
+
 // Complex mixed full solve: one problem through the grouped path, host buffers
 // staged through a pool block.
 dpt_status solve_full_mixed_complex(int64_t n, const std::vector<double>& th,
@@ -1144,12 +1165,7 @@ dpt_status solve_full_mixed_complex(int64_t n, const std::vector<double>& th,
                                     double lambda, const dpt_options& o, double* A_out,
                                     bool a_dev, int64_t ld_a, double* E_out, bool e_dev,
                                     dpt_info* info, cudaStream_t user) {
-  auto layout = [&](Carve& c) {
-    c.take<double>(n);
-    c.take<double>((size_t)2 * n * n);
-    c.take<double>((size_t)2 * n * n);
-    c.take<double>((size_t)2 * n);
-  };
+  auto layout = [&](Carve& c) { layout_full_mixed_complex_stage(c, (int)n); };
   Block* b = acquire(measure(layout));
   dpt_status ret = DPT_OK;
   try {
@@ -1202,6 +1218,31 @@ void dpt_options_default(dpt_options* o) {
   o->profile = 0;
   o->cta_pair = 1;
   o->grouped_form = 0;
+}
+
+int64_t dpt_workspace_bytes(int64_t n, dpt_dtype dtype, dpt_prec prec) {
+  if (n < 1 || n > (1 << 20) || (dtype != DPT_R64 && dtype != DPT_C128) ||
+      (prec != DPT_PREC_FP64 && prec != DPT_PREC_MIXED_BF16))
+    return -1;
+  try {
+    const int ni = (int)n;
+    const bool cplx = dtype == DPT_C128;
+    if (prec == DPT_PREC_FP64)
+      return (int64_t)measure([&](Carve& c) { layout_full_fp64(c, ni, cplx, false); });
+    if (!cplx)
+      return (int64_t)measure([&](Carve& c) { layout_full_mixed_real(c, ni, true, true); });
+    // the complex solve holds its staging block and the grouped solve's block at once
+    GroupPlan g;
+    const int64_t nn = n;
+    const double lam = 0.0;
+    const double* nul = nullptr;
+    double* nulw = nullptr;
+    plan_group(g, 1, 1, &nn, &nul, &nul, &nn, &lam, &nulw, &nn, &nulw, nullptr, nullptr, G_PLAIN);
+    return (int64_t)(measure([&](Carve& c) { layout_full_mixed_complex_stage(c, ni); }) +
+                     measure([&](Carve& c) { layout_batched(c, 1, g); }));
+  } catch (...) {
+    return -1;
+  }
 }
 
 const char* dpt_status_string(dpt_status s) {

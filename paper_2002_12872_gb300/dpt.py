@@ -131,6 +131,8 @@ def lib() -> ctypes.CDLL:
         L.dpt_server_destroy.restype = ctypes.c_int
         L.dpt_selftest_bounded_wait.argtypes = [dbl, P]
         L.dpt_selftest_bounded_wait.restype = ctypes.c_int
+        L.dpt_workspace_bytes.argtypes = [i64, ctypes.c_int, ctypes.c_int]
+        L.dpt_workspace_bytes.restype = i64
         L.dpt_release_workspace.argtypes = []
         L.dpt_release_workspace.restype = None
         _lib = L
@@ -419,6 +421,12 @@ def selftest_bounded_wait(seconds=0.5, stream=None):
     expire ('ERR_TIMEOUT' is the expected outcome)."""
     s = ctypes.c_void_p(0) if stream is None else ctypes.c_void_p(int(stream))
     return STATUS.get(lib().dpt_selftest_bounded_wait(float(seconds), s))
+
+
+def workspace_bytes(n, complex_=False, prec="mixed"):
+    """dpt_workspace_bytes: device workspace of one dpt_solve_full of size n (device
+    inputs and outputs, default options); -1 for invalid arguments."""
+    return int(lib().dpt_workspace_bytes(int(n), C128 if complex_ else R64, PREC[prec]))
 
 
 def release_workspace():

@@ -99,3 +99,24 @@ def test_selftest_and_server_arguments_rejected_without_gpu(lib):
     assert lib.dpt_submit(None, None, None) == -1
     assert lib.dpt_poll(None, 1, None) == -1
     assert lib.dpt_server_destroy(None) == -1
+
+
+def test_workspace_bytes_without_gpu(lib):
+    """dpt_workspace_bytes is host arithmetic over the solves' carve layouts: about
+    30 B per element for the mixed real solve (BF16 slices 6, float-float A and its
+    copy 16, BF16 increments 4, remainder 4), 3 n^2 doubles per real component for
+    the FP64 map, and -1 outside its domain."""
+    from paper_2002_12872_gb300 import dpt
+    for n in (256, 4096, 8192):
+        nn = float(n) * n
+        assert 30.0 <= dpt.workspace_bytes(n) / nn <= 30.5
+        assert 24.0 <= dpt.workspace_bytes(n, prec="fp64") / nn <= 24.2
+        assert 48.0 <= dpt.workspace_bytes(n, True, "fp64") / nn <= 48.2
+        # complex mixed: staging copies of Delta and A (32 B) plus the grouped solve
+        assert 100.0 <= dpt.workspace_bytes(n, True) / nn <= 110.0
+    sizes = [dpt.workspace_bytes(n) for n in (1, 100, 1000, 5000)]
+    assert sizes == sorted(sizes) and sizes[0] > 0
+    assert lib.dpt_workspace_bytes(0, 0, 1) == -1
+    assert lib.dpt_workspace_bytes((1 << 20) + 1, 0, 1) == -1
+    assert lib.dpt_workspace_bytes(16, 7, 1) == -1
+    assert lib.dpt_workspace_bytes(16, 0, 9) == -1

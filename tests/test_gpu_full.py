@@ -217,3 +217,25 @@ def test_profiled_solves_any_chunk_size(dpt, graph_iters):
     assert info["status"] == "OK"
     assert info["product_launches"] == info["iters"]
     assert info["product_ms"] > 0
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_workspace_bytes_matches_pool_growth(dpt, prec):
+    """dpt_workspace_bytes equals what a solve with device buffers takes from the
+    pool: device memory drops by that figure (up to allocation granularity) when an
+    empty pool serves one solve."""
+    n = 2048
+    cfg = inputs.full_unsymmetric(n=n)
+    th, D = _dev(cfg)
+    A = torch.empty((n, n), dtype=torch.float64, device="cuda").t()
+    E = torch.empty(n, dtype=torch.float64, device="cuda")
+    dpt.solve_full(th, D, cfg["lam"], prec=prec, A_out=A, E_out=E)   # modules loaded
+    torch.cuda.synchronize()
+    dpt.release_workspace()
+    free0 = torch.cuda.mem_get_info()[0]
+    dpt.solve_full(th, D, cfg["lam"], prec=prec, A_out=A, E_out=E)
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    ws = dpt.workspace_bytes(n, prec=prec)
+    assert ws > 0 and abs(used - ws) <= 8 * 2**20, (used, ws)
+    dpt.release_workspace()
