@@ -17,13 +17,17 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ORA = os.path.join(os.path.dirname(HERE), "oracle")
 
 MUTANTS = {
-    "drop_d_a_term": ("an[j] = lambda * g * (p[j] - d * a[j]);", "an[j] = lambda * g * (p[j]);"),
+    "drop_d_a_term": ("an[j] = lam_map * g * (p[j] - d * a[j]);", "an[j] = lam_map * g * (p[j]);"),
     "flip_gap_sign": ("const T g = 1.0 / (theta[i] - theta[j]);",
                       "const T g = 1.0 / (theta[j] - theta[i]);"),
     "transpose_delta": ("for (int64_t j = 0; j < n; ++j) p[j] += dk[j] * akc;",
                         "for (int64_t j = 0; j < n; ++j) p[j] += delta[k + j * n] * akc;"),
     "eigenvalue_without_lambda": ("E[c] = theta[i] + lambda * d;", "E[c] = theta[i] + d;"),
     "diagonal_not_pinned": ("an[j] = 1;  ", "an[j] = a[j] + lambda * d;  "),
+    "ramp_exponent_off_by_one": (
+        "const T lam_map = ramp_alpha > 0.0 ? lambda * (1.0 - pw) : lambda;\n      pw *= ramp_alpha;",
+        "pw *= ramp_alpha;\n      const T lam_map = ramp_alpha > 0.0 ? lambda * (1.0 - pw) : lambda;"),
+    "ramp_in_eigenvalue": ("E[c] = theta[i] + lambda * d;", "E[c] = theta[i] + lam_map * d;"),
 }
 
 
@@ -42,7 +46,23 @@ def _build(tmp, name, old, new):
     lib = ctypes.CDLL(so)
     P, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
     lib.ora_step_r.argtypes = [i64, P, P, dbl, P, P, P]
+    lib.ora_solve_full_r.argtypes = [i64, P, P, dbl, i64, P, dbl, i64, ctypes.c_int, dbl,
+                                     P, P, P]
     return lib
+
+
+def _solve_ramp(lib, th, D, lam, alpha, max_iter):
+    """(A_k, E) returned by the ramped full solve after max_iter map applications."""
+    n = len(th)
+    th = np.ascontiguousarray(th, float)
+    D = np.asfortranarray(D, float)
+    A = np.zeros((n, n), order="F")
+    E = np.zeros(n)
+    info = ctypes.create_string_buffer(64)   # iterations, residual, status (unused here)
+    p = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    lib.ora_solve_full_r(n, p(th), p(D), lam, n, None, 1e-300, max_iter, 0, alpha,
+                         p(A), p(E), ctypes.cast(info, ctypes.c_void_p))
+    return A, E
 
 
 def _step(lib, th, D, lam, A):
@@ -58,6 +78,17 @@ def _step(lib, th, D, lam, A):
 
 
 def _pins_pass(lib):
+    # 0. the non-autonomous iteration's A_2 in closed form: I + lam (1 - alpha) G o Delta
+    #    (zero-diagonal Delta), and E of the iterate read out at the full lambda
+    th0 = np.array([0.0, 1.0, 3.0])
+    D0 = np.array([[0.0, 1.0, 2.0], [1.0, 0.0, 3.0], [2.0, 3.0, 0.0]])
+    G0 = np.array([[0.0 if i == j else 1.0 / (th0[i] - th0[j]) for i in range(3)]
+                   for j in range(3)])
+    A2, E2 = _solve_ramp(lib, th0, D0, 0.1, 0.5, 2)
+    if not np.allclose(A2, np.eye(3) + 0.1 * 0.5 * G0 * D0, atol=1e-15, rtol=0):
+        return False
+    if not np.allclose(E2, th0 + 0.1 * np.diag(D0 @ A2), atol=1e-15, rtol=0):
+        return False
     # 1. exact 2x2 iterates, column form [[1, -x], [x, 1]]
     th2, D2 = np.array([0.0, 1.0]), np.array([[0.0, 1.0], [1.0, 0.0]])
     A, x, lam = np.eye(2), 0.0, 0.3
