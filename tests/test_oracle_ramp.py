@@ -104,4 +104,4 @@ def test_ramp_reaches_the_autonomous_fixed_point(ora):
 def test_ramp_alpha_out_of_range_rejected(ora):
     for a in (-0.1, 1.0, 2.0):
         _, _, info = ora.solve_full(TH3, D3, 0.1, ramp_alpha=a)
-        assert info["status"] == "ERR_ARG"
+        assert info["status"] == "ARG"
