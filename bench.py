@@ -339,6 +339,19 @@ def bench_dominant_dense(dpt, inputs, dev, pk, steps=10, warmup=3, n=32768):
         out[prec] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "iters": float(np.mean(its)),
                      "gemv_ms_per_pass": per_pass, "achieved_GBs": gbs,
                      "hbm_frac": gbs / pk["hbm_gbs"], "E": E}
+    # the non-autonomous iteration (lambda (1 - 0.5^k)) on the same problem: same fixed
+    # point, more steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    dpt.solve_dominant_dense(th, D, lam, z_out=z, ramp_alpha=0.5)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    _, Er, infor = dpt.solve_dominant_dense(th, D, lam, z_out=z, ramp_alpha=0.5)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    msr = e0.elapsed_time(e1)
+    out["ramp_alpha_0.5"] = {"solves_per_s": 1e3 / msr, "ms_per_solve": msr,
+                             "iters": infor["iters"], "status": infor["status"],
+                             "E_minus_autonomous": Er - out["mixed"]["E"]}
     out["roofline"] = {"bound": "hbm", "kernel": "k_dd_gemv (float-float GEMV)",
                        "achieved": out["mixed"]["achieved_GBs"], "peak": pk["hbm_gbs"],
                        "unit": "GB/s", "frac": out["mixed"]["hbm_frac"],

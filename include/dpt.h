@@ -115,6 +115,16 @@ typedef struct {
                               problems); 3 CTA pairs (256-row tiles).  Results of one
                               problem are identical across entry points using the
                               same form. */
+  double ramp_alpha;       /* 0 (default): the autonomous map.  In (0, 1): the
+                              non-autonomous iteration of the Supplement's explicit
+                              3x3 example, step k applying the map at
+                              lambda (1 - ramp_alpha^k) (step 0 at strength 0), which
+                              can reach fixed points the autonomous iteration from
+                              the unperturbed vectors misses near the boundary of its
+                              convergence domain; E, the residual and the stopping test
+                              always refer to lambda.  Supported by both dominant
+                              forms and by the plain-FP64 full solve; mixed full,
+                              batched and served solves return DPT_ERR_UNSUPPORTED. */
 } dpt_options;
 
 typedef struct {
@@ -293,7 +303,8 @@ typedef struct {
   int32_t max_queue;      /* queued requests beyond which dpt_submit returns
                              DPT_ERR_BUSY (default 65536) */
   dpt_options opt;        /* tol, max_iter, max_slices, slice_tol for requests that
-                             do not set their own; prec must be MIXED_BF16 */
+                             do not set their own; prec must be MIXED_BF16 and
+                             ramp_alpha 0 */
 } dpt_server_cfg;
 
 typedef struct {

@@ -481,6 +481,9 @@ dpt_status solve_full_fp64(int64_t n64, bool cplx, const std::vector<double>& th
     h.max_iter = o.max_iter;
     h.lam = lambda;
     h.tol = o.tol;
+    h.ramp_alpha = o.ramp_alpha;
+    h.ramp_pow = 1.0;
+    h.lam_k = o.ramp_alpha > 0.0 ? 0.0 : lambda;   // step 0 of the ramp applies strength 0
     h.best = INFINITY;
     double tm = 0;
     for (double v : th) tm = std::max(tm, std::fabs(v));
@@ -620,6 +623,13 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
     h.lam_lo = (float)(lambda - (double)h.lam_hi);
     h.tol = o.tol;
     h.best = INFINITY;
+    h.ramp_alpha = o.ramp_alpha;
+    h.ramp_pow = 1.0;
+    if (o.ramp_alpha > 0.0) {   // step 0 of the ramp applies strength 0: dlam = lambda
+      h.dlam = lambda;
+      h.dlam_hi = (float)lambda;
+      h.dlam_lo = (float)(lambda - (double)h.dlam_hi);
+    }
     DomState* hs = reinterpret_cast<DomState*>(b->host_state);   // pinned scratch (large enough)
     static_assert(sizeof(DomState) <= kPinnedBytes, "pinned scratch size");
     *hs = h;
@@ -755,6 +765,13 @@ dpt_status solve_dominant_dense(int64_t n64, const double* theta, const double* 
     h.lam_lo = (float)(lambda - (double)h.lam_hi);
     h.tol = o.tol;
     h.best = INFINITY;
+    h.ramp_alpha = o.ramp_alpha;
+    h.ramp_pow = 1.0;
+    if (o.ramp_alpha > 0.0) {   // step 0 of the ramp applies strength 0: dlam = lambda
+      h.dlam = lambda;
+      h.dlam_hi = (float)lambda;
+      h.dlam_lo = (float)(lambda - (double)h.dlam_hi);
+    }
     DomState* hs = reinterpret_cast<DomState*>(b->host_state);
     *hs = h;
     CK(cudaMemcpyAsync(st, hs, sizeof(DomState), cudaMemcpyHostToDevice, s));
@@ -1218,6 +1235,7 @@ void dpt_options_default(dpt_options* o) {
   o->profile = 0;
   o->cta_pair = 1;
   o->grouped_form = 0;
+  o->ramp_alpha = 0.0;
 }
 
 int64_t dpt_workspace_bytes(int64_t n, dpt_dtype dtype, dpt_prec prec) {
@@ -1285,6 +1303,9 @@ dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const
   if (o.max_slices < 1 || o.max_slices > 3) return done(DPT_ERR_ARG);
   if (o.prec == DPT_PREC_MIXED_BF16 && dtype == DPT_C128 && o.epstein_nesbet)
     return done(DPT_ERR_UNSUPPORTED);
+  if (!(o.ramp_alpha >= 0.0 && o.ramp_alpha < 1.0)) return done(DPT_ERR_ARG);
+  // the mixed path carries the residual across steps at one lambda
+  if (o.ramp_alpha > 0.0 && o.prec != DPT_PREC_FP64) return done(DPT_ERR_UNSUPPORTED);
   try {
     cudaStream_t s = (cudaStream_t)stream;
     const bool th_dev = is_device_ptr(theta), d_dev = is_device_ptr(delta),
@@ -1346,7 +1367,8 @@ dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int32_t* row
   };
   if (n < 1 || n > 0x7ffffffe || !theta || !row_ptr || !col_idx || !vals || !z_out || !E_out ||
       nstar >= n || !std::isfinite(lambda) || !(o.tol > 0) || o.max_iter < 0 ||
-      (o.prec != DPT_PREC_FP64 && o.prec != DPT_PREC_MIXED_BF16))
+      (o.prec != DPT_PREC_FP64 && o.prec != DPT_PREC_MIXED_BF16) ||
+      !(o.ramp_alpha >= 0.0 && o.ramp_alpha < 1.0))
     return done(DPT_ERR_ARG);
   try {
     return done(solve_dominant(n, theta, row_ptr, col_idx, vals, nstar < 0 ? -1 : nstar, lambda,
@@ -1373,7 +1395,8 @@ dpt_status dpt_solve_dominant_dense(int64_t n, const double* theta, const double
   };
   if (n < 1 || n > (1 << 20) || !theta || !delta || ld_delta < n || !z_out || !E_out ||
       nstar >= n || !std::isfinite(lambda) || !(o.tol > 0) || o.max_iter < 0 ||
-      (o.prec != DPT_PREC_FP64 && o.prec != DPT_PREC_MIXED_BF16))
+      (o.prec != DPT_PREC_FP64 && o.prec != DPT_PREC_MIXED_BF16) ||
+      !(o.ramp_alpha >= 0.0 && o.ramp_alpha < 1.0))
     return done(DPT_ERR_ARG);
   try {
     return done(solve_dominant_dense(n, theta, delta, ld_delta, nstar < 0 ? -1 : nstar, lambda,
@@ -1398,7 +1421,9 @@ dpt_status dpt_solve_batched(int64_t count, dpt_dtype dtype, const int64_t* n,
       o.max_slices > 3)
     return DPT_ERR_ARG;
   if (dtype != DPT_R64 && dtype != DPT_C128) return DPT_ERR_ARG;
-  if (o.prec != DPT_PREC_MIXED_BF16 || o.epstein_nesbet) return DPT_ERR_UNSUPPORTED;
+  if (!(o.ramp_alpha >= 0.0 && o.ramp_alpha < 1.0)) return DPT_ERR_ARG;
+  if (o.prec != DPT_PREC_MIXED_BF16 || o.epstein_nesbet || o.ramp_alpha > 0.0)
+    return DPT_ERR_UNSUPPORTED;
   for (int64_t p = 0; p < count; ++p) {
     if (n[p] < 1 || n[p] > 65536 || ld_delta[p] < n[p] || ld_a[p] < n[p] || !theta[p] ||
         !delta[p] || !A_out[p] || !E_out[p] || !std::isfinite(lambda[p]))

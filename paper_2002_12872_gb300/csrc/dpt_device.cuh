@@ -543,7 +543,27 @@ __device__ __forceinline__ bool decide(volatile IterState* vs, double rho) {
   if (vs->k >= vs->max_iter) { vs->status = ST_MAXITER; return false; }
   vs->k = vs->k + 1;
   vs->cur = vs->k & 1;
+  if (vs->ramp_alpha > 0.0) {   // strength lambda (1 - alpha^k) for the next step
+    double pw = vs->ramp_pow * vs->ramp_alpha;
+    if (pw < 0x1p-60) pw = 0.0;
+    vs->ramp_pow = pw;
+    vs->lam_k = vs->lam * (1.0 - pw);
+  }
   return true;
+}
+
+// The same for a single-vector solve: the next step applies lambda - dlam with
+// dlam = lambda alpha^k (carried in FP64 and as a float pair).
+__device__ __forceinline__ void dom_ramp_advance(volatile DomState* vs) {
+  if (!(vs->ramp_alpha > 0.0)) return;
+  double pw = vs->ramp_pow * vs->ramp_alpha;
+  if (pw < 0x1p-60) pw = 0.0;
+  vs->ramp_pow = pw;
+  const double dl = vs->lam * pw;
+  vs->dlam = dl;
+  const float h = (float)dl;
+  vs->dlam_hi = h;
+  vs->dlam_lo = (float)(dl - (double)h);
 }
 
 // ---------------------------------------------------------------------------

@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
     float2* nz = c1 ? z0 : z1;
     const float ysh = st->ys_hi, ysl = st->ys_lo;
     const float tsh = th_hi[nstar], tsl = th_lo[nstar];
+    const float dlh = st->dlam_hi, dll = st->dlam_lo;   // non-autonomous step (0: off)
     // rows are visited in rounds; every lane runs the same number of rounds
     const int rounds = (n + gstride - 1) / gstride;
     for (int rd = 0; rd < rounds; ++rd) {
@@ -253,7 +254,14 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
           ff_sub(tsh, tsl, th_hi[m], th_lo[m], gh, gl2);
           ff_mul(gh, gl2, zmh, zml, vh, vl);
           ff_add(uh, ul, -vh, -vl, Rh, Rl);
-          const float dlt = Rh * __frcp_rn(gh);
+          // the step applies lambda - dlam: R_step = R - dlam (y - y* z)
+          float Sh = Rh;
+          if (dlh != 0.f) {
+            float wh, wl, sl;
+            ff_mul(dlh, dll, t2h, t2l, wh, wl);
+            ff_add(Rh, Rl, -wh, -wl, Sh, sl);
+          }
+          const float dlt = Sh * __frcp_rn(gh);
           float nh, nl;
           ff_add(zmh, zml, dlt, 0.f, nh, nl);
           nz[m] = make_float2(nh, nl);
@@ -268,6 +276,7 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
     const double ys = st->ys64;
     const double ts = theta[nstar];
     const double lam = st->lam;
+    const double dlam = st->dlam;   // non-autonomous step (0: off)
     const int rounds = (n + gstride - 1) / gstride;
     for (int rd = 0; rd < rounds; ++rd) {
       const int m = g0 + rd * gstride;
@@ -304,7 +313,7 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
           const double gap = ts - theta[m];
           const double t = acc - ys * zm;
           const double R = lam * t - gap * zm;
-          nz[m] = lam * t / gap;
+          nz[m] = (lam - dlam) * t / gap;
           r2 += R * R;
           z2 += zm * zm;
         }
@@ -366,6 +375,7 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
   if (vs->k >= vs->max_iter) { vs->status = ST_MAXITER; return; }
   vs->k = vs->k + 1;
   vs->cur = vs->k & 1;
+  dom_ramp_advance(vs);
 }
 
 // Output: z (float-float or FP64) of the assessed iterate -> FP64.

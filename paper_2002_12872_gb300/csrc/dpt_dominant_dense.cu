@@ -289,7 +289,15 @@ __global__ void __launch_bounds__(DD_THREADS) k_dd_update(DDParams p) {
         ff_sub(p.th_hi[nstar], p.th_lo[nstar], p.th_hi[m], p.th_lo[m], gh, gl);
         dd_mul(gh, gl, zmh, zml, vh, vl);
         dd_add(uh, ul, -vh, -vl, Rh, Rl);
-        const float dlt = Rh * __frcp_rn(gh);
+        // the step applies lambda - dlam: R_step = R - dlam (y - y* z)
+        float Sh = Rh;
+        const float dlh = st->dlam_hi;
+        if (dlh != 0.f) {
+          float wh, wl, sl;
+          dd_mul(dlh, st->dlam_lo, t2h, t2l, wh, wl);
+          dd_add(Rh, Rl, -wh, -wl, Sh, sl);
+        }
+        const float dlt = Sh * __frcp_rn(gh);
         float nh, nl;
         dd_add(zmh, zml, dlt, 0.f, nh, nl);
         nz[m] = make_float2(nh, nl);
@@ -307,7 +315,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_dd_update(DDParams p) {
         const double gap = p.theta[nstar] - p.theta[m];
         const double t = y64 - ys_64 * zm;
         const double R = st->lam * t - gap * zm;
-        nz[m] = st->lam * t / gap;
+        nz[m] = (st->lam - st->dlam) * t / gap;
         r2 = R * R;
         z2 = zm * zm;
       }
@@ -384,6 +392,7 @@ __global__ void __launch_bounds__(DD_THREADS) k_dd_update(DDParams p) {
   if (vs->k >= vs->max_iter) { vs->status = ST_MAXITER; return; }
   vs->k = vs->k + 1;
   vs->cur = vs->k & 1;
+  dom_ramp_advance(vs);
 }
 
 // ---------------------------------------------------------------------------

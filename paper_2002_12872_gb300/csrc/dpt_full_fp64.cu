@@ -149,6 +149,9 @@ __global__ void __launch_bounds__(256) k_epi_f64(int n, int ld, const double* __
   if (st->status != ST_RUNNING) return;
   const int i = blockIdx.x;
   const double thi = theta[i];
+  // strength of this map application: lambda, or lambda (1 - alpha^k) for the
+  // non-autonomous iteration (E and the residual R stay at lambda)
+  const double lam_map = st->lam_k;
   double r2 = 0.0, a2 = 0.0, rowabs = 0.0;
   if (CPLX) {
     const double2* P = (const double2*)Pv;
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(256) k_epi_f64(int n, int ld, const double* __
         const double2 tt = make_double2(P[idx].x - da.x, P[idx].y - da.y);
         const double2 R = make_double2(lam * tt.x - gap * a.x, lam * tt.y - gap * a.y);
         r2 += R.x * R.x + R.y * R.y;
-        An[idx] = make_double2(lam * tt.x / gap, lam * tt.y / gap);
+        An[idx] = make_double2(lam_map * tt.x / gap, lam_map * tt.y / gap);
       }
       if (first) {   // row sums of |Delta| for the residual scale (row j = i here)
         const double2* D2 = (const double2*)Dl;
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(256) k_epi_f64(int n, int ld, const double* __
         const double tt = Pv[idx] - d * a;
         const double R = lam * tt - gap * a;
         r2 += R * R;
-        Anv[idx] = lam * tt / gap;
+        Anv[idx] = lam_map * tt / gap;
       }
       if (first) rowabs += fabs(Dl[(int64_t)j * ldd + i]);
     }

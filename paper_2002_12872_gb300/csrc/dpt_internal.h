@@ -48,6 +48,9 @@ struct IterState {
   double best;
   double rho_last;
   float dmax1;         // max |dt_0|: the increment fed to the first product
+  double ramp_alpha;   // non-autonomous iteration (0: off)
+  double ramp_pow;     // ramp_alpha^k
+  double lam_k;        // strength the next map application uses (FP64 path)
 };
 
 // State of a dominant-eigenvector solve (single-vector map), device resident.
@@ -76,6 +79,10 @@ struct DomState {
   double rho;
   double best;
   double E;              // eigenvalue of the assessed iterate
+  double ramp_alpha;     // non-autonomous iteration (0: off)
+  double ramp_pow;       // ramp_alpha^k
+  double dlam;           // lambda minus the strength of the next map application
+  float dlam_hi, dlam_lo;
 };
 
 // One problem of a grouped (batched / served) solve: a device-resident table entry
