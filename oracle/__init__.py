@@ -60,15 +60,15 @@ def lib() -> ctypes.CDLL:
         _lib.ora_step_r.argtypes = [i64, P, P, dbl, P, P, P]
         _lib.ora_residual_r.argtypes = [i64, P, P, dbl, P, P, P]
         _lib.ora_residual_r.restype = dbl
-        _lib.ora_solve_full_r.argtypes = [i64, P, P, dbl, i64, P, dbl, i64, cint, dbl,
+        _lib.ora_solve_full_r.argtypes = [i64, P, P, dbl, i64, P, dbl, i64, cint, dbl, P,
                                           P, P, ctypes.POINTER(_Info)]
         # complex lambda crosses the boundary as (re, im)
         _lib.ora_step_c.argtypes = [i64, P, P, dbl, dbl, P, P, P]
         _lib.ora_residual_c.argtypes = [i64, P, P, dbl, dbl, P, P, P]
         _lib.ora_residual_c.restype = dbl
-        _lib.ora_solve_full_c.argtypes = [i64, P, P, dbl, dbl, i64, P, dbl, i64, cint, dbl,
+        _lib.ora_solve_full_c.argtypes = [i64, P, P, dbl, dbl, i64, P, dbl, i64, cint, dbl, P,
                                           P, P, ctypes.POINTER(_Info)]
-        _lib.ora_solve_dominant_csr.argtypes = [i64, P, P, P, P, i64, dbl, dbl, i64, dbl,
+        _lib.ora_solve_dominant_csr.argtypes = [i64, P, P, P, P, i64, dbl, dbl, i64, dbl, P,
                                                 P, P, ctypes.POINTER(_Info)]
         _lib.ora_rs_series_r.argtypes = [i64, P, P, dbl, i64, P, P]
         _lib.ora_jacobi_sym.argtypes = [i64, P, P, P]
@@ -154,10 +154,11 @@ def set_threads(n: int = 0) -> int:
 
 
 def solve_full(theta, delta, lam, tol=1e-12, max_iter=1000, cols=None,
-               epstein_nesbet=False, ramp_alpha=0.0):
+               epstein_nesbet=False, ramp_alpha=0.0, start=None):
     """Full-spectrum DPT solve from A_0 = I (Sec. II.B) on the listed columns.
     ramp_alpha in (0, 1) runs the non-autonomous iteration of the Supplement's 3x3
-    example (step k at lambda (1 - alpha^k)); 0 is the autonomous map.
+    example (step k at lambda (1 - alpha^k)); 0 is the autonomous map.  start
+    (n x len(cols)) replaces A_0, each column scaled to its chart entry 1.
 
     Returns (A, E, info): A is n x len(cols), E has len(cols) entries, info is a
     dict with 'iters', 'residual', 'status' (name) and 'code'."""
@@ -172,8 +173,11 @@ def solve_full(theta, delta, lam, tol=1e-12, max_iter=1000, cols=None,
     E = np.zeros(ncols, dtype=dt)
     info = _Info()
     args = (n, _ptr(theta), _ptr(delta))
+    st_arr = None if start is None else np.asfortranarray(start, dtype=dt).reshape(n, ncols,
+                                                                                 order="F")
     tail = (ncols, cptr, float(tol), int(max_iter), int(bool(epstein_nesbet)),
-            float(ramp_alpha), _ptr(A), _ptr(E), ctypes.byref(info))
+            float(ramp_alpha), None if st_arr is None else _ptr(st_arr), _ptr(A), _ptr(E),
+            ctypes.byref(info))
     if cplx:
         st = lib().ora_solve_full_c(*args, *_c128(lam), *tail)
     else:
@@ -183,20 +187,22 @@ def solve_full(theta, delta, lam, tol=1e-12, max_iter=1000, cols=None,
 
 
 def solve_dominant_csr(theta, row_ptr, col_idx, vals, lam, nstar=-1, tol=1e-12,
-                       max_iter=1000, ramp_alpha=0.0):
+                       max_iter=1000, ramp_alpha=0.0, start=None):
     """Dominant eigenvector by the single-vector map F_{n*} (Sec. II.H); ramp_alpha
-    as for solve_full."""
+    and start (n values) as for solve_full."""
     theta = np.ascontiguousarray(theta, dtype=np.float64)
     row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
     col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
     vals = np.ascontiguousarray(vals, dtype=np.float32)
     n = theta.shape[0]
+    st_arr = None if start is None else np.ascontiguousarray(start, dtype=np.float64)
     z = np.zeros(n)
     E = np.zeros(1)
     info = _Info()
     st = lib().ora_solve_dominant_csr(n, _ptr(theta), _ptr(row_ptr), _ptr(col_idx),
                                       _ptr(vals), int(nstar), float(lam), float(tol),
-                                      int(max_iter), float(ramp_alpha), _ptr(z), _ptr(E),
+                                      int(max_iter), float(ramp_alpha),
+                                      None if start is None else _ptr(st_arr), _ptr(z), _ptr(E),
                                       ctypes.byref(info))
     return z, float(E[0]), {"iters": int(info.iters), "residual": float(info.residual),
                             "status": STATUS_NAMES.get(st, str(st)), "code": int(st)}

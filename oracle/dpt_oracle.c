@@ -80,9 +80,9 @@ double ora_residual_r(int64_t n, const double* theta, const double* delta,
 int ora_solve_full_r(int64_t n, const double* theta, const double* delta,
                      double lambda, int64_t ncols, const int64_t* cols, double tol,
                      int64_t max_iter, int epstein_nesbet, double ramp_alpha,
-                     double* A_out, double* E_out, ora_info* info) {
+                     const double* start, double* A_out, double* E_out, ora_info* info) {
   return solve_full_r(n, theta, delta, lambda, ncols, cols, tol, max_iter,
-                      epstein_nesbet, ramp_alpha, A_out, E_out, info);
+                      epstein_nesbet, ramp_alpha, start, A_out, E_out, info);
 }
 int ora_step_c(int64_t n, const double _Complex* theta, const double _Complex* delta,
                double lambda_re, double lambda_im, const double _Complex* A,
@@ -97,10 +97,10 @@ double ora_residual_c(int64_t n, const double _Complex* theta,
 int ora_solve_full_c(int64_t n, const double _Complex* theta,
                      const double _Complex* delta, double lambda_re, double lambda_im,
                      int64_t ncols, const int64_t* cols, double tol, int64_t max_iter,
-                     int epstein_nesbet, double ramp_alpha, double _Complex* A_out,
-                     double _Complex* E_out, ora_info* info) {
+                     int epstein_nesbet, double ramp_alpha, const double _Complex* start,
+                     double _Complex* A_out, double _Complex* E_out, ora_info* info) {
   return solve_full_c(n, theta, delta, CMPLX(lambda_re, lambda_im), ncols, cols, tol,
-                      max_iter, epstein_nesbet, ramp_alpha, A_out, E_out, info);
+                      max_iter, epstein_nesbet, ramp_alpha, start, A_out, E_out, info);
 }
 
 /* ---- dominant eigenvector, CSR perturbation ------------------------------ */
@@ -119,15 +119,15 @@ int ora_solve_full_c(int64_t n, const double _Complex* theta,
  * residual ||M z - E z||_2 / (s ||z||_2), with M z = theta o z + lambda Delta z
  * evaluated by a second pass over the matrix and
  * s = max_m |theta_m| + |lambda| * max_m sum_k |Delta_mk|.
- * nstar < 0 selects argmax_m theta_m (first index on ties).  ramp_alpha as for
- * ora_solve_full_r (0: autonomous; in (0, 1): step k applies lambda (1 - alpha^k)).
+ * nstar < 0 selects argmax_m theta_m (first index on ties).  ramp_alpha and start
+ * (n values, or NULL for e_{n*}) as for ora_solve_full_r.
  * Returns the statuses of ora_solve_full_r; the degeneracy test concerns the
  * gaps theta_{n*} - theta_m only, the only ones this map divides by. */
 int ora_solve_dominant_csr(int64_t n, const double* theta, const int32_t* row_ptr,
                            const int32_t* col_idx, const float* vals,
                            int64_t nstar, double lambda, double tol,
-                           int64_t max_iter, double ramp_alpha, double* z_out,
-                           double* E_out, ora_info* info) {
+                           int64_t max_iter, double ramp_alpha, const double* start,
+                           double* z_out, double* E_out, ora_info* info) {
   if (info) { info->iters = 0; info->residual = NAN; info->status = ORA_ERR_ARG; }
   if (n <= 0 || !theta || !row_ptr || !col_idx || !vals || !z_out || !E_out ||
       max_iter < 0 || nstar >= n || !(ramp_alpha >= 0.0 && ramp_alpha < 1.0))
@@ -162,7 +162,19 @@ int ora_solve_dominant_csr(int64_t n, const double* theta, const int32_t* row_pt
   double* zn = (double*)malloc(sizeof(double) * (size_t)n);
   double* y = (double*)malloc(sizeof(double) * (size_t)n);
   if (!z || !zn || !y) { free(z); free(zn); free(y); return ORA_ERR_ARG; }
-  for (int64_t m = 0; m < n; ++m) z[m] = (m == nstar) ? 1.0 : 0.0;
+  /* z_0 = e_{n*}, or the given start scaled to the chart z_{n*} = 1 */
+  if (start) {
+    const double piv = start[nstar];
+    int ok = piv != 0.0 && isfinite(piv);
+    for (int64_t m = 0; m < n; ++m) ok = ok && isfinite(start[m]);
+    if (!ok) {
+      free(z); free(zn); free(y);
+      return ORA_ERR_ARG;
+    }
+    for (int64_t m = 0; m < n; ++m) z[m] = (m == nstar) ? 1.0 : start[m] / piv;
+  } else {
+    for (int64_t m = 0; m < n; ++m) z[m] = (m == nstar) ? 1.0 : 0.0;
+  }
 
   int status = ORA_ERR_MAXITER;
   double best = INFINITY, rho = INFINITY, E = 0.0;

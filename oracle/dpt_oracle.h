@@ -28,7 +28,7 @@ double ora_residual_r(int64_t n, const double* theta, const double* delta,
 int ora_solve_full_r(int64_t n, const double* theta, const double* delta,
                      double lambda, int64_t ncols, const int64_t* cols, double tol,
                      int64_t max_iter, int epstein_nesbet, double ramp_alpha,
-                     double* A_out, double* E_out, ora_info* info);
+                     const double* start, double* A_out, double* E_out, ora_info* info);
 
 int ora_step_c(int64_t n, const double _Complex* theta, const double _Complex* delta,
                double lambda_re, double lambda_im, const double _Complex* A,
@@ -39,14 +39,14 @@ double ora_residual_c(int64_t n, const double _Complex* theta,
 int ora_solve_full_c(int64_t n, const double _Complex* theta,
                      const double _Complex* delta, double lambda_re, double lambda_im,
                      int64_t ncols, const int64_t* cols, double tol, int64_t max_iter,
-                     int epstein_nesbet, double ramp_alpha, double _Complex* A_out,
-                     double _Complex* E_out, ora_info* info);
+                     int epstein_nesbet, double ramp_alpha, const double _Complex* start,
+                     double _Complex* A_out, double _Complex* E_out, ora_info* info);
 
 int ora_solve_dominant_csr(int64_t n, const double* theta, const int32_t* row_ptr,
                            const int32_t* col_idx, const float* vals, int64_t nstar,
                            double lambda, double tol, int64_t max_iter,
-                           double ramp_alpha, double* z_out, double* E_out,
-                           ora_info* info);
+                           double ramp_alpha, const double* start, double* z_out,
+                           double* E_out, ora_info* info);
 
 int ora_rs_series_r(int64_t n, const double* theta, const double* delta,
                     double lambda, int64_t k, double* A_out, double* E_out);

@@ -47,7 +47,7 @@ def _build(tmp, name, old, new):
     P, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
     lib.ora_step_r.argtypes = [i64, P, P, dbl, P, P, P]
     lib.ora_solve_full_r.argtypes = [i64, P, P, dbl, i64, P, dbl, i64, ctypes.c_int, dbl,
-                                     P, P, P]
+                                     P, P, P, P]
     return lib
 
 
@@ -60,7 +60,7 @@ def _solve_ramp(lib, th, D, lam, alpha, max_iter):
     E = np.zeros(n)
     info = ctypes.create_string_buffer(64)   # iterations, residual, status (unused here)
     p = lambda x: x.ctypes.data_as(ctypes.c_void_p)
-    lib.ora_solve_full_r(n, p(th), p(D), lam, n, None, 1e-300, max_iter, 0, alpha,
+    lib.ora_solve_full_r(n, p(th), p(D), lam, n, None, 1e-300, max_iter, 0, alpha, None,
                          p(A), p(E), ctypes.cast(info, ctypes.c_void_p))
     return A, E
 
