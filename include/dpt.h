@@ -125,6 +125,23 @@ typedef struct {
                               always refer to lambda.  Supported by both dominant
                               forms and by the plain-FP64 full solve; mixed full,
                               batched and served solves return DPT_ERR_UNSUPPORTED. */
+  const double* start;     /* NULL (default): iterate from the unperturbed vectors
+                              (A_0 = I, z_0 = e_{n*}).  Otherwise the starting iterate,
+                              host or device: for the dominant forms n doubles; for
+                              the full solve an n x n column-major matrix (complex
+                              interleaved for DPT_C128) with leading dimension
+                              ld_start.  Each vector is divided by its chart entry
+                              (a_i[i], z[n*]), so any nonzero multiple of an
+                              eigenvector estimate will do; a zero or non-finite
+                              chart entry or a non-finite value gives DPT_ERR_ARG.
+                              This is the polisher use of the closing remark of
+                              Sec. II.H: approximate eigenvectors from another
+                              method, refined by the map's final convergent steps.
+                              Supported by both dominant forms and the plain-FP64
+                              full solve; mixed full, batched and served solves
+                              return DPT_ERR_UNSUPPORTED (their first step is exact
+                              only from A_0 = I). */
+  int64_t ld_start;        /* leading dimension of a full-solve start (>= n) */
 } dpt_options;
 
 typedef struct {

@@ -492,7 +492,15 @@ dpt_status solve_full_fp64(int64_t n64, bool cplx, const std::vector<double>& th
     CK(cudaMemcpyAsync(st, b->host_state, sizeof(IterState), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(thd, th.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     CK(launch_check_finite(n, Dl, ldd, cplx, st, s));
-    CK(launch_fp64_init(n, ld, cplx, A[0], s));
+    if (o.start) {   // A_0 from the caller's start, each column scaled to its chart entry
+      CK(cudaMemcpy2DAsync(A[0], sizeof(double) * w * ld, o.start, sizeof(double) * w * o.ld_start,
+                           sizeof(double) * w * n, n,
+                           is_device_ptr(o.start) ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyHostToDevice, s));
+      CK(launch_fp64_start(n, ld, cplx, A[0], st, s));
+    } else {
+      CK(launch_fp64_init(n, ld, cplx, A[0], s));
+    }
     // iteration 0 outside the graph (it also forms the residual scale)
     Prof prof;
     prof.on = o.profile != 0;
@@ -573,6 +581,7 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
   const int64_t nnz = nnz32;
   const bool ff = o.prec != DPT_PREC_FP64;
   const int G = dom_blocks(n);
+  const bool start_host = o.start && !is_device_ptr(o.start);
   auto layout = [&](Carve& c) {
     c.take<DomState>(1);
     c.take<float>(n); c.take<float>(n);                 // theta float-float
@@ -584,6 +593,7 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
     if (!ci_dev) c.take<int32_t>(nnz > 0 ? nnz : 1);
     if (!va_dev) c.take<float>(nnz > 0 ? nnz : 1);
     if (!z_dev) c.take<double>(n);
+    if (start_host) c.take<double>(n);
   };
   Block* b = acquire(measure(layout));
   dpt_status ret = DPT_OK;
@@ -645,7 +655,17 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
     if (hs->bad_input) throw Fail{DPT_ERR_ARG};
     if (hs->ties != 1u) throw Fail{DPT_ERR_DEGENERATE};
     const int nst = hs->nstar;
-    CK(launch_dom_init(n, zf[0], z64[0], ff, st, s));
+    if (o.start) {   // z_0 from the caller's start vector (chart z_{n*} = 1)
+      const double* v = o.start;
+      if (start_host) {
+        double* t = c.take<double>(n);
+        CK(cudaMemcpyAsync(t, o.start, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        v = t;
+      }
+      CK(launch_dom_start(n, v, zf[0], z64[0], st, s));
+    } else {
+      CK(launch_dom_init(n, zf[0], z64[0], ff, st, s));
+    }
     const double avg = n > 0 ? (double)nnz / n : 0.0;
     const int V = avg < 24 ? 4 : (avg < 48 ? 8 : (avg < 96 ? 16 : 32));
     Prof prof;
@@ -707,6 +727,7 @@ dpt_status solve_dominant_dense(int64_t n64, const double* theta, const double* 
   dd_plan(p, al16);
   const int G = dd_update_blocks(n);
   const size_t parts = (size_t)p.nslices * n;
+  const bool start_host = o.start && !is_device_ptr(o.start);
   auto layout = [&](Carve& c) {
     c.take<DomState>(1);
     c.take<float>(n); c.take<float>(n);                 // theta float-float
@@ -718,6 +739,7 @@ dpt_status solve_dominant_dense(int64_t n64, const double* theta, const double* 
     if (!th_dev) c.take<double>(n);
     if (!d_dev) c.take<double>((size_t)p.ld * n);
     if (!z_dev) c.take<double>(n);
+    if (start_host) c.take<double>(n);
   };
   Block* b = acquire(measure(layout));
   dpt_status ret = DPT_OK;
@@ -782,7 +804,17 @@ dpt_status solve_dominant_dense(int64_t n64, const double* theta, const double* 
     if (hs->ties != 1u) throw Fail{DPT_ERR_DEGENERATE};
     const int nst = hs->nstar;
     // z_0 = e_{n*}; the residual scale is formed by the first pass
-    CK(launch_dom_init(n, p.z0, p.z64_0, ff, st, s));
+    if (o.start) {   // z_0 from the caller's start vector (chart z_{n*} = 1)
+      const double* v = o.start;
+      if (start_host) {
+        double* t = c.take<double>(n);
+        CK(cudaMemcpyAsync(t, o.start, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        v = t;
+      }
+      CK(launch_dom_start(n, v, p.z0, p.z64_0, st, s));
+    } else {
+      CK(launch_dom_init(n, p.z0, p.z64_0, ff, st, s));
+    }
     Prof prof;
     prof.on = o.profile != 0;
     // theta set-up, n* selection (3), z_0 (1, or 2 for FP64), the first pass (2)
@@ -1236,6 +1268,8 @@ void dpt_options_default(dpt_options* o) {
   o->cta_pair = 1;
   o->grouped_form = 0;
   o->ramp_alpha = 0.0;
+  o->start = nullptr;
+  o->ld_start = 0;
 }
 
 int64_t dpt_workspace_bytes(int64_t n, dpt_dtype dtype, dpt_prec prec) {
@@ -1306,6 +1340,9 @@ dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const
   if (!(o.ramp_alpha >= 0.0 && o.ramp_alpha < 1.0)) return done(DPT_ERR_ARG);
   // the mixed path carries the residual across steps at one lambda
   if (o.ramp_alpha > 0.0 && o.prec != DPT_PREC_FP64) return done(DPT_ERR_UNSUPPORTED);
+  if (o.start && o.ld_start < n) return done(DPT_ERR_ARG);
+  // the mixed path's first step is exact only from A_0 = I
+  if (o.start && o.prec != DPT_PREC_FP64) return done(DPT_ERR_UNSUPPORTED);
   try {
     cudaStream_t s = (cudaStream_t)stream;
     const bool th_dev = is_device_ptr(theta), d_dev = is_device_ptr(delta),
@@ -1422,7 +1459,7 @@ dpt_status dpt_solve_batched(int64_t count, dpt_dtype dtype, const int64_t* n,
     return DPT_ERR_ARG;
   if (dtype != DPT_R64 && dtype != DPT_C128) return DPT_ERR_ARG;
   if (!(o.ramp_alpha >= 0.0 && o.ramp_alpha < 1.0)) return DPT_ERR_ARG;
-  if (o.prec != DPT_PREC_MIXED_BF16 || o.epstein_nesbet || o.ramp_alpha > 0.0)
+  if (o.prec != DPT_PREC_MIXED_BF16 || o.epstein_nesbet || o.ramp_alpha > 0.0 || o.start)
     return DPT_ERR_UNSUPPORTED;
   for (int64_t p = 0; p < count; ++p) {
     if (n[p] < 1 || n[p] > 65536 || ld_delta[p] < n[p] || ld_a[p] < n[p] || !theta[p] ||

@@ -393,6 +393,31 @@ __global__ void k_dom_out(int n, const float2* __restrict__ z0, const float2* __
   }
 }
 
+// z_0 from a caller's start vector v: z_m = v_m / v_{n*} (the chart z_{n*} = 1) in
+// FP64 and as float pairs, and the residual scale as k_dom_init forms it.  A zero or
+// non-finite v_{n*}, or any non-finite v_m, marks the input bad (the first decision
+// then ends the solve with DPT_ERR_ARG).
+__global__ void k_dom_start(int n, const double* __restrict__ v, float2* __restrict__ z,
+                            double* __restrict__ z64, DomState* st) {
+  const int nstar = st->nstar;
+  const double piv = v[nstar];
+  const bool piv_ok = piv != 0.0 && finite_bits(piv);
+  bool bad = !piv_ok;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    const double vm = v[m];
+    if (!finite_bits(vm)) bad = true;
+    const double q = (m == nstar) ? 1.0 : (piv_ok ? vm / piv : 0.0);
+    float h, l;
+    split_double(q, h, l);
+    z[m] = make_float2(h, l);
+    if (z64) z64[m] = q;
+  }
+  if (bad) atomicExch(&st->bad_input, 1u);
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    st->s = (double)__uint_as_float(st->absmax_bits) +
+            fabs(st->lam) * (double)__uint_as_float(st->row_bits);
+}
+
 __global__ void k_dom_init64(int n, double* z, const DomState* st) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m < n) z[m] = (m == st->nstar) ? 1.0 : 0.0;
@@ -433,6 +458,12 @@ cudaError_t launch_dom_select(int n, const double* theta, DomState* st, cudaStre
   k_dom_argmax<<<g, 256, 0, s>>>(n, theta, st);
   k_dom_pick<<<1, 1, 0, s>>>(st);
   k_dom_ties<<<g, 256, 0, s>>>(n, theta, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dom_start(int n, const double* v, float2* z, double* z64, DomState* st,
+                             cudaStream_t s) {
+  k_dom_start<<<dom_grid(n), 256, 0, s>>>(n, v, z, z64, st);
   return cudaGetLastError();
 }
 

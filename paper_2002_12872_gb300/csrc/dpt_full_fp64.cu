@@ -27,6 +27,41 @@ __global__ void k_fp64_init(int n, int ld, int cplx, double* A) {
   }
 }
 
+// A_0 from a caller's start (already copied into A): column i divided by its entry
+// i (the chart a_i = 1).  One block per column; a zero or non-finite chart entry or
+// any non-finite value marks the input bad.
+__global__ void k_fp64_start(int n, int ld, int cplx, double* A, IterState* st) {
+  const int i = blockIdx.x;
+  bool bad = false;
+  if (cplx) {
+    double2* col = reinterpret_cast<double2*>(A) + (int64_t)i * ld;
+    const double2 p = col[i];
+    const double den = p.x * p.x + p.y * p.y;
+    if (!(den > 0.0) || !finite_bits(den)) bad = true;
+    __syncthreads();   // every thread has read the pivot before it is overwritten
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double2 v = col[j];
+      if (!finite_bits(v.x) || !finite_bits(v.y)) bad = true;
+      double2 q = make_double2(1.0, 0.0);
+      if (j != i) q = bad ? make_double2(0.0, 0.0)
+                          : make_double2((v.x * p.x + v.y * p.y) / den,
+                                         (v.y * p.x - v.x * p.y) / den);
+      col[j] = q;
+    }
+  } else {
+    double* col = A + (int64_t)i * ld;
+    const double p = col[i];
+    if (p == 0.0 || !finite_bits(p)) bad = true;
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double v = col[j];
+      if (!finite_bits(v)) bad = true;
+      col[j] = (j == i) ? 1.0 : (bad ? 0.0 : v / p);
+    }
+  }
+  if (bad) atomicExch(&st->bad_input, 1u);
+}
+
 // ---------------------------------------------------------------------------
 // P = Delta * A, FP64 SIMT GEMM.  64 x 64 tile per block, BK = 16, 256 threads,
 // 4 x 4 outputs per thread (rows tm + 16 r, columns tn + 16 c).
@@ -245,6 +280,12 @@ __global__ void k_check_finite(int n, const double* __restrict__ D, int64_t ldd,
 cudaError_t launch_fp64_init(int n, int ld, int cplx, void* A0, cudaStream_t s) {
   dim3 grid((ld + 255) / 256, n);
   k_fp64_init<<<grid, 256, 0, s>>>(n, ld, cplx, (double*)A0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp64_start(int n, int ld, int cplx, double* A, IterState* st,
+                              cudaStream_t s) {
+  k_fp64_start<<<n, 256, 0, s>>>(n, ld, cplx, A, st);
   return cudaGetLastError();
 }
 

@@ -216,6 +216,9 @@ cudaError_t launch_dom_iter(int n, int vlanes, int ff, const int32_t* row_ptr,
                             double* z64_0, double* z64_1, double* part, DomState* st,
                             cudaStream_t s);
 cudaError_t launch_dom_select(int n, const double* theta, DomState* st, cudaStream_t s);
+cudaError_t launch_dom_start(int n, const double* v, float2* z, double* z64, DomState* st,
+                             cudaStream_t s);
+cudaError_t launch_fp64_start(int n, int ld, int cplx, double* A, IterState* st, cudaStream_t s);
 
 // Dense dominant form (GEMV): arguments of one iteration's two kernels.
 struct DDParams {

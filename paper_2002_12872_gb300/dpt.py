@@ -33,7 +33,8 @@ class Options(ctypes.Structure):
                 ("graph_iters", ctypes.c_int32), ("max_slices", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("slice_tol", ctypes.c_double),
                 ("cta_pair", ctypes.c_int32), ("grouped_form", ctypes.c_int32),
-                ("ramp_alpha", ctypes.c_double)]
+                ("ramp_alpha", ctypes.c_double), ("start", ctypes.c_void_p),
+                ("ld_start", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -238,8 +239,8 @@ def _iscomplex(x) -> bool:
 # ---------------------------------------------------------------------------
 def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
                epstein_nesbet=False, graph_iters=None, max_slices=None, slice_tol=None,
-               profile=False, cta_pair=None, ramp_alpha=None, A_out=None, E_out=None,
-               stream=None, check=True):
+               profile=False, cta_pair=None, ramp_alpha=None, start=None, A_out=None,
+               E_out=None, stream=None, check=True):
     """All eigenpairs of M = diag(theta) + lam * Delta by the DPT map (dpt_solve_full).
 
     Returns (A, E, info): A[:, i] is eigenvector i with A[i, i] = 1 and
@@ -257,6 +258,10 @@ def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
                 graph_iters=graph_iters, max_slices=max_slices, slice_tol=slice_tol,
                 profile=int(bool(profile)), cta_pair=None if cta_pair is None else int(cta_pair),
                 ramp_alpha=ramp_alpha)
+    s_keep = None
+    if start is not None:
+        s_ptr, s_ld, s_keep = _colmajor(start, cplx)
+        o.start, o.ld_start = s_ptr, s_ld
     info = Info()
     st = lib().dpt_solve_full(n, C128 if cplx else R64, th_ptr, d_ptr, ldd, float(lam),
                               ctypes.byref(o), _ptr(A), lda, _ptr(E), ctypes.byref(info),
@@ -346,8 +351,8 @@ def solve_batched(thetas, deltas, lams, *, tol=1e-12, max_iter=200, graph_iters=
 
 
 def solve_dominant(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, prec="mixed", tol=1e-12,
-                   max_iter=200, graph_iters=None, profile=False, ramp_alpha=None, z_out=None,
-                   stream=None, check=True):
+                   max_iter=200, graph_iters=None, profile=False, ramp_alpha=None, start=None,
+                   z_out=None, stream=None, check=True):
     """Dominant eigenpair by the single-vector map (dpt_solve_dominant) for a CSR
     perturbation (int32 row_ptr / col_idx, FP32 values).  Returns (z, E, info)
     with z[n*] = 1."""
@@ -361,6 +366,9 @@ def solve_dominant(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, prec="mixed"
     E = np.zeros(1)
     o = options(tol=tol, max_iter=max_iter, prec=prec, graph_iters=graph_iters,
                 profile=int(bool(profile)), ramp_alpha=ramp_alpha)
+    s_keep = None
+    if start is not None:
+        o.start, s_keep = _vec_ptr(start, "float64")
     info = Info()
     st = lib().dpt_solve_dominant(n, th_ptr, rp_ptr, ci_ptr, va_ptr, int(nstar), float(lam),
                                   ctypes.byref(o), _ptr(z_out), E.ctypes.data,
@@ -374,8 +382,8 @@ def solve_dominant(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, prec="mixed"
 
 
 def solve_dominant_dense(theta, delta, lam, *, nstar=-1, prec="mixed", tol=1e-12, max_iter=200,
-                         graph_iters=None, profile=False, ramp_alpha=None, z_out=None,
-                         stream=None, check=True):
+                         graph_iters=None, profile=False, ramp_alpha=None, start=None,
+                         z_out=None, stream=None, check=True):
     """Dominant eigenpair by the single-vector map with a dense FP64 perturbation
     (dpt_solve_dominant_dense, a GEMV per iteration).  Returns (z, E, info) with
     z[n*] = 1."""
@@ -387,6 +395,9 @@ def solve_dominant_dense(theta, delta, lam, *, nstar=-1, prec="mixed", tol=1e-12
     E = np.zeros(1)
     o = options(tol=tol, max_iter=max_iter, prec=prec, graph_iters=graph_iters,
                 profile=int(bool(profile)), ramp_alpha=ramp_alpha)
+    s_keep = None
+    if start is not None:
+        o.start, s_keep = _vec_ptr(start, "float64")
     info = Info()
     st = lib().dpt_solve_dominant_dense(n, th_ptr, d_ptr, ldd, int(nstar), float(lam),
                                         ctypes.byref(o), _ptr(z_out), E.ctypes.data,
