@@ -208,6 +208,54 @@ def solve_dominant_csr(theta, row_ptr, col_idx, vals, lam, nstar=-1, tol=1e-12,
                             "status": STATUS_NAMES.get(st, str(st)), "code": int(st)}
 
 
+def homotopy(theta, delta, lam, stages, tol=1e-12, max_iter=1000):
+    """Homotopy continuation of the Discussion (Sec. III): lambda is split into
+    `stages` equal steps; after each step the problem is re-expressed in the
+    eigenbasis just computed (the diagonal matrix of its eigenvalues becomes the
+    next unperturbed matrix) and the map is iterated again from the identity.
+
+    With right eigenvectors V and left eigenvectors W of M_q = D + q (lam/Q) Delta
+    (W^T V = I), M_{q+1} = M_q + (lam/Q) Delta becomes, in that basis,
+        W^T M_{q+1} V = diag(E_q) + (lam/Q) W^T Delta V,
+    a perturbation problem of the form DPT solves.  Each stage solves it for the
+    right eigenvectors A' (columns with A'_ii = 1) and, on the transposed problem,
+    the left ones B' (scaled so that B'^T A' = I); then V <- V A', W <- W B'.
+    Stage solves use solve_full (FP64, from the identity); the basis changes are
+    plain matrix products.  Real theta / Delta.
+
+    Returns (A, E, info): A = V with each column scaled to its chart entry
+    A[i, i] = 1 (the chart of the original problem), E the eigenvalues, info with
+    'status' (of the first failing stage, else 'OK'), 'stages', 'iters' (summed)."""
+    theta = np.asarray(theta, dtype=np.float64)
+    D = np.asarray(delta, dtype=np.float64)
+    n = theta.shape[0]
+    Q = int(stages)
+    if Q < 1:
+        raise ValueError("stages must be >= 1")
+    step_lam = float(lam) / Q
+    V = np.eye(n)
+    W = np.eye(n)
+    th = theta.copy()
+    iters = 0
+    for q in range(Q):
+        Dq = W.T @ D @ V
+        Ar, E, ir = solve_full(th, Dq, step_lam, tol=tol, max_iter=max_iter)
+        iters += ir["iters"]
+        if ir["status"] != "OK":
+            return V, th, {"status": ir["status"], "stages": q, "iters": iters}
+        if q + 1 < Q:
+            Bl, _, il = solve_full(th, Dq.T, step_lam, tol=tol, max_iter=max_iter)
+            iters += il["iters"]
+            if il["status"] != "OK":
+                return V, th, {"status": il["status"], "stages": q, "iters": iters}
+            Bl = Bl / np.sum(Bl * Ar, axis=0)[None, :]      # b_i^T a_i = 1
+            W = W @ Bl
+        V = V @ Ar
+        th = np.real(E).astype(np.float64)
+    V = V / np.diag(V)[None, :]
+    return V, th, {"status": "OK", "stages": Q, "iters": iters}
+
+
 def rs_series(theta, delta, lam, k):
     """Rayleigh-Schroedinger partial sums A_RS^(k), E_RS^(k) of Eq. (ARS-alpha)."""
     theta = np.ascontiguousarray(theta, dtype=np.float64)
