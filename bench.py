@@ -50,8 +50,8 @@ def parse_args():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the dominant (CSR and dense), batched and served workloads")
     ap.add_argument("--only", default="all",
-                    choices=["all", "dominant", "dominant_dense", "batched", "served",
-                             "served_pool"],
+                    choices=["all", "dominant", "dominant_dense", "homotopy", "batched",
+                             "served", "served_pool"],
                     help="time one secondary workload alone and print its JSON object")
     ap.add_argument("--dense-n", type=int, default=32768,
                     help="dominant_dense: problem size")
@@ -375,6 +375,42 @@ def bench_dominant_dense(dpt, inputs, dev, pk, steps=10, warmup=3, n=32768):
     return out
 
 
+def bench_homotopy(dpt, dev, n=2048, lam=2.5, stages=3, steps=3):
+    """Homotopy continuation (lambda in `stages` steps with a change of basis) on a
+    seeded symmetric problem, theta_i = i, Delta = (S + S^T)/sqrt(2) with S iid
+    N(0, 1/n), beside the direct solve of the same problem.  The basis changes are
+    FP64 matrix products (2 n^3 flop each, 4 per stage but one less in the last)."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(2002_12872 + 7000))
+    th_h = np.arange(n, dtype=float)
+    S = rng.standard_normal((n, n)) / np.sqrt(n)
+    D_h = (S + S.T) / np.sqrt(2)
+    th = torch.tensor(th_h, device=dev)
+    D = dpt.colmajor_tensor(D_h, dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": f"homotopy continuation, symmetric n={n}, theta_i=i, "
+                       f"Delta GOE-like N(0,1/n), lambda={lam}, {stages} stages, tol=1e-12"}
+    for name, fn in (("direct", lambda: dpt.solve_full(th, D, lam, max_iter=2000, check=False)),
+                     ("homotopy", lambda: dpt.solve_homotopy(th, D, lam, stages, max_iter=2000,
+                                                             check=False))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            _, E, info = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_solve": ms, "solves_per_s": 1e3 / ms, "iters": info["iters"],
+                     "status": info["status"]}
+    gemms = 4 * stages - 1
+    out["homotopy"]["fp64_gemm_tflop"] = gemms * 2.0 * n**3 / 1e12
+    del D
+    torch.cuda.empty_cache()
+    return out
+
+
 def bench_batched(dpt, inputs, dev, steps=3, warmup=2):
     """20,000 independent symmetric problems, n log-uniform in [32, 512], one
     grouped solve per step (inputs resident in HBM; the pointer arrays of the call
@@ -674,6 +710,7 @@ def run_ours(args, world, rank, local):
     if not args.no_extra:
         extra["dominant_csr"] = bench_dominant(dpt, inputs, dev, pk)
         extra["dominant_dense"] = bench_dominant_dense(dpt, inputs, dev, pk)
+        extra["homotopy"] = bench_homotopy(dpt, dev)
         extra["batched"] = bench_batched(dpt, inputs, dev)
         extra["served"] = bench_served(dpt, inputs, dev)
         extra["served_pool"] = bench_served_pool(dpt, inputs, dev)
@@ -729,6 +766,8 @@ def main():
         elif args.only == "dominant_dense":
             out = bench_dominant_dense(dpt, inputs, dev, pk, steps=max(1, min(args.steps, 10)),
                                        warmup=max(1, min(args.warmup, 3)), n=args.dense_n)
+        elif args.only == "homotopy":
+            out = bench_homotopy(dpt, dev)
         elif args.only == "batched":
             out = bench_batched(dpt, inputs, dev)
         elif args.only == "served_pool":

@@ -241,6 +241,34 @@ DPT_API dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int3
                                       double lambda, const dpt_options* opt, double* z_out,
                                       double* E_out, dpt_info* info, void* stream);
 
+/* Homotopy continuation (the Discussion's extension of the convergence domain):
+ * lambda is reached in `stages` equal steps.  After each step the problem is
+ * re-expressed in the eigenbasis just found,
+ *     W^T (M_q + (lambda/Q) Delta) V = diag(E_q) + (lambda/Q) W^T Delta V,
+ * (V right and W left eigenvectors of M_q = diag(theta) + q (lambda/Q) Delta,
+ * W^T V = I), and the map is iterated again from the identity: each stage is a
+ * perturbation problem of strength lambda/Q around the previous eigenvalues, so
+ * a lambda beyond the direct iteration's domain can be reached.  A stage is one
+ * full solve for the right eigenvectors (opt->prec: mixed or plain FP64) and,
+ * except in the last stage, one on the transposed problem for the left ones; the
+ * basis changes are FP64 matrix products (four per stage).
+ *   n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out   as for dpt_solve_full,
+ *              real (DPT_R64) only, all four arrays device pointers
+ *              (DPT_ERR_UNSUPPORTED otherwise), 1 <= n <= 65536
+ *   stages     Q, 1..1024 (1 is the direct solve)
+ *   opt        tol, max_iter, prec, max_slices, slice_tol, graph_iters apply to every
+ *              stage solve; start, ramp_alpha and epstein_nesbet must be unset
+ *              (DPT_ERR_UNSUPPORTED)
+ * A_out columns are scaled to the chart of the original problem (A_ii = 1).  The
+ * status is that of the first failing stage solve (DPT_ERR_DEGENERATE when two
+ * eigenvalues of a stage coincide); DPT_ERR_DIVERGED when a basis vector has a
+ * zero chart entry.  info->iters sums the iterations of all stage solves and
+ * info->residual is the last stage's.  Blocks until done. */
+DPT_API dpt_status dpt_solve_homotopy(int64_t n, const double* theta, const double* delta,
+                                      int64_t ld_delta, double lambda, int32_t stages,
+                                      const dpt_options* opt, double* A_out, int64_t ld_a,
+                                      double* E_out, dpt_info* info, void* stream);
+
 /* Dominant eigenvector with a dense perturbation: the map of dpt_solve_dominant
  * (Eq. (single_line_dyn), Sec. II.H) with y = Delta z formed by a GEMV.  Every
  * iteration streams Delta from device memory once (8 bytes per entry), so the

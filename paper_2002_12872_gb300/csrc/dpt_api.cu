@@ -710,6 +710,118 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
 }
 
 // ---------------------------------------------------------------------------
+// Homotopy continuation (Discussion): lambda in `stages` steps, each re-expressed
+// in the eigenbasis of the previous one and solved from the identity.
+// ---------------------------------------------------------------------------
+void layout_homotopy(Carve& c, int n) {
+  c.take<IterState>(1);
+  for (int q = 0; q < 7; ++q) c.take<double>((size_t)n * n);   // V W T Dq X Ar Bl
+  for (int q = 0; q < 3; ++q) c.take<double>(n);               // theta_q, E, E (left)
+}
+
+dpt_status solve_homotopy(int64_t n64, const double* theta, const double* delta,
+                          int64_t ld_delta, double lambda, int stages, const dpt_options& o,
+                          double* A_out, int64_t ld_a, double* E_out, dpt_info* info,
+                          cudaStream_t user) {
+  const int n = (int)n64, ld = n;
+  Block* b = acquire(measure([&](Carve& c) { layout_homotopy(c, n); }));
+  dpt_status ret = DPT_OK;
+  try {
+    Carve c{(char*)b->ptr};
+    IterState* st = c.take<IterState>(1);
+    double* M[7];
+    for (int q = 0; q < 7; ++q) M[q] = c.take<double>((size_t)n * n);
+    double *V = M[0], *W = M[1], *T = M[2], *Dq = M[3], *X = M[4], *Ar = M[5], *Bl = M[6];
+    double* thq = c.take<double>(n);
+    double* Eq = c.take<double>(n);
+    double* El = c.take<double>(n);
+    cudaStream_t s = b->stream;
+    CK(cudaEventRecord(b->ev, user));
+    CK(cudaStreamWaitEvent(s, b->ev, 0));
+    IterState h{};
+    h.status = ST_RUNNING;   // lets the FP64 GEMM run; bad_input records a breakdown
+    *b->host_state = h;
+    CK(cudaMemcpyAsync(st, b->host_state, sizeof(IterState), cudaMemcpyHostToDevice, s));
+    CK(launch_fp64_init(n, ld, 0, V, s));
+    CK(launch_fp64_init(n, ld, 0, W, s));
+    CK(cudaMemcpyAsync(thq, theta, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    dpt_options so = o;            // stage solves: from the identity, autonomous
+    so.start = nullptr;
+    so.ramp_alpha = 0.0;
+    so.epstein_nesbet = 0;
+    const double step = lambda / stages;
+    auto stage = [&](const double* Dm, double* Aout, double* Eout, dpt_info* si) {
+      if (o.prec == DPT_PREC_FP64) {
+        std::vector<double> th((size_t)n);
+        CK(cudaMemcpyAsync(th.data(), thq, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (double v : th)
+          if (!std::isfinite(v)) return DPT_ERR_DIVERGED;
+        const dpt_status d = check_distinct(th);
+        if (d != DPT_OK) return d;
+        return solve_full_fp64(n, false, th, Dm, true, ld, step, so, Aout, true, ld, Eout, true,
+                               si, s);
+      }
+      return solve_full_mixed_real(n, {}, thq, Dm, true, ld, step, so, Aout, true, ld, Eout,
+                                   true, si, s);
+    };
+    int iters = 0, launches = 0;
+    double resid = 0.0;
+    for (int q = 0; q < stages && ret == DPT_OK; ++q) {
+      // the stage problem: theta_q = E_{q-1}, Delta_q = W^T Delta V
+      CK(launch_gemm_f64(n, delta, ld_delta, V, ld, T, st, s));
+      CK(launch_h_transpose(n, ld, W, X, s));
+      CK(launch_gemm_f64(n, X, ld, T, ld, Dq, st, s));
+      launches += 3;
+      dpt_info si{};
+      ret = stage(Dq, Ar, Eq, &si);
+      iters += si.iters;
+      launches += si.launches;
+      resid = si.residual;
+      if (ret != DPT_OK) break;
+      if (q + 1 < stages) {
+        // left eigenvectors of the stage problem (its transpose), scaled to B^T A = I
+        CK(launch_h_transpose(n, ld, Dq, X, s));
+        dpt_info sl{};
+        ret = stage(X, Bl, El, &sl);
+        iters += sl.iters;
+        launches += sl.launches + 1;
+        if (ret != DPT_OK) break;
+        CK(launch_h_biorth(n, ld, Ar, Bl, st, s));
+        CK(launch_gemm_f64(n, W, ld, Bl, ld, T, st, s));
+        std::swap(W, T);
+        launches += 2;
+      }
+      CK(launch_gemm_f64(n, V, ld, Ar, ld, T, st, s));
+      std::swap(V, T);
+      CK(cudaMemcpyAsync(thq, Eq, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      launches += 1;
+    }
+    if (ret == DPT_OK) {
+      CK(launch_h_chart(n, ld, V, A_out, ld_a, st, s));
+      CK(cudaMemcpyAsync(E_out, thq, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      launches += 1;
+    }
+    CK(cudaMemcpyAsync(b->host_state, st, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ret == DPT_OK && b->host_state->bad_input) ret = DPT_ERR_DIVERGED;   // zero pivot
+    if (info) {
+      info->iters = iters;
+      info->residual = resid;
+      info->status = ret;
+      info->launches = launches;
+    }
+    CK(cudaEventRecord(b->ev, s));
+    CK(cudaStreamWaitEvent(user, b->ev, 0));
+  } catch (Fail f) {
+    cudaStreamSynchronize(b->stream);
+    ret = f.st;
+  }
+  release(b);
+  return ret;
+}
+
+// ---------------------------------------------------------------------------
 // Dominant eigenvector, dense perturbation (GEMV)
 // ---------------------------------------------------------------------------
 dpt_status solve_dominant_dense(int64_t n64, const double* theta, const double* delta,
@@ -1410,6 +1522,38 @@ dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int32_t* row
   try {
     return done(solve_dominant(n, theta, row_ptr, col_idx, vals, nstar < 0 ? -1 : nstar, lambda,
                                o, z_out, E_out, info, (cudaStream_t)stream));
+  } catch (Fail f) {
+    return done(f.st);
+  } catch (...) {
+    return done(DPT_ERR_CUDA);
+  }
+}
+
+dpt_status dpt_solve_homotopy(int64_t n, const double* theta, const double* delta,
+                              int64_t ld_delta, double lambda, int32_t stages,
+                              const dpt_options* opt, double* A_out, int64_t ld_a,
+                              double* E_out, dpt_info* info, void* stream) {
+  Timer timer;
+  if (info) { std::memset(info, 0, sizeof(*info)); info->status = DPT_ERR_ARG; info->nstar = -1; }
+  dpt_options o;
+  dpt_options_default(&o);
+  if (opt) o = *opt;
+  auto done = [&](dpt_status st) {
+    if (info) { info->status = st; info->seconds = timer.sec(); }
+    return st;
+  };
+  if (n < 1 || n > (1 << 16) || !theta || !delta || !A_out || !E_out || ld_delta < n ||
+      ld_a < n || !std::isfinite(lambda) || stages < 1 || stages > 1024 || !(o.tol > 0) ||
+      o.max_iter < 0 || o.max_slices < 1 || o.max_slices > 3 ||
+      (o.prec != DPT_PREC_FP64 && o.prec != DPT_PREC_MIXED_BF16))
+    return done(DPT_ERR_ARG);
+  if (o.start || o.ramp_alpha != 0.0 || o.epstein_nesbet) return done(DPT_ERR_UNSUPPORTED);
+  try {
+    if (!is_device_ptr(theta) || !is_device_ptr(delta) || !is_device_ptr(A_out) ||
+        !is_device_ptr(E_out))
+      return done(DPT_ERR_UNSUPPORTED);
+    return done(solve_homotopy(n, theta, delta, ld_delta, lambda, stages, o, A_out, ld_a,
+                               E_out, info, (cudaStream_t)stream));
   } catch (Fail f) {
     return done(f.st);
   } catch (...) {

@@ -219,6 +219,11 @@ cudaError_t launch_dom_select(int n, const double* theta, DomState* st, cudaStre
 cudaError_t launch_dom_start(int n, const double* v, float2* z, double* z64, DomState* st,
                              cudaStream_t s);
 cudaError_t launch_fp64_start(int n, int ld, int cplx, double* A, IterState* st, cudaStream_t s);
+cudaError_t launch_h_transpose(int n, int ld, const double* X, double* Y, cudaStream_t s);
+cudaError_t launch_h_biorth(int n, int ld, const double* A, double* B, IterState* st,
+                            cudaStream_t s);
+cudaError_t launch_h_chart(int n, int ld, const double* V, double* out, int64_t ld_out,
+                           IterState* st, cudaStream_t s);
 
 // Dense dominant form (GEMV): arguments of one iteration's two kernels.
 struct DDParams {

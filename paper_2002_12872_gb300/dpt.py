@@ -105,6 +105,10 @@ def lib() -> ctypes.CDLL:
         L.dpt_solve_dominant.argtypes = [i64, P, P, P, P, i64, dbl, ctypes.POINTER(Options),
                                          P, P, ctypes.POINTER(Info), P]
         L.dpt_solve_dominant.restype = ctypes.c_int
+        L.dpt_solve_homotopy.argtypes = [i64, P, P, i64, dbl, ctypes.c_int32,
+                                         ctypes.POINTER(Options), P, i64, P,
+                                         ctypes.POINTER(Info), P]
+        L.dpt_solve_homotopy.restype = ctypes.c_int
         L.dpt_solve_dominant_dense.argtypes = [i64, P, P, i64, i64, dbl,
                                                ctypes.POINTER(Options), P, P,
                                                ctypes.POINTER(Info), P]
@@ -269,6 +273,32 @@ def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
     res = (A, E, info.as_dict())
     if check and st != OK:
         err = RuntimeError(f"dpt_solve_full: {status_string(st)}")
+        err.result = res
+        raise err
+    return res
+
+
+def solve_homotopy(theta, delta, lam, stages, *, prec="mixed", tol=1e-12, max_iter=200,
+                   graph_iters=None, max_slices=None, A_out=None, E_out=None, stream=None,
+                   check=True):
+    """Homotopy continuation (dpt_solve_homotopy): lambda in `stages` steps, each
+    solved in the eigenbasis of the previous one.  Real CUDA tensors only.  Returns
+    (A, E, info) as solve_full."""
+    n = int(theta.shape[0])
+    th_ptr, th_keep = _vec_ptr(theta, "float64")
+    d_ptr, ldd, d_keep = _colmajor(delta, False)
+    A = _empty_colmajor(n, delta, False) if A_out is None else A_out
+    E = _empty_vec(n, delta, False) if E_out is None else E_out
+    lda = A.stride(1) if _is_torch(A) else A.strides[1] // A.itemsize
+    o = options(tol=tol, max_iter=max_iter, prec=prec, graph_iters=graph_iters,
+                max_slices=max_slices)
+    info = Info()
+    st = lib().dpt_solve_homotopy(n, th_ptr, d_ptr, ldd, float(lam), int(stages),
+                                  ctypes.byref(o), _ptr(A), lda, _ptr(E), ctypes.byref(info),
+                                  _stream_of(delta, stream))
+    res = (A, E, info.as_dict())
+    if check and st != OK:
+        err = RuntimeError(f"dpt_solve_homotopy: {status_string(st)}")
         err.result = res
         raise err
     return res

@@ -79,6 +79,14 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert dd(4, p(th), p(d), 4, -1, float("nan"), ctypes.byref(o), p(z), p(Eo),
               ctypes.byref(info), None) == -1
     assert info.status == -1 and info.nstar == -1
+    # homotopy: stages outside 1..1024, n < 1, ld_a < n
+    hs = lib.dpt_solve_homotopy
+    for args in ((4, 0), (4, 1025), (0, 2)):
+        nn, Q = args
+        assert hs(nn, p(th), p(d), 4, 0.1, Q, ctypes.byref(o), p(A), 4, p(E),
+                  ctypes.byref(info), None) == -1
+    assert hs(4, p(th), p(d), 4, 0.1, 2, ctypes.byref(o), p(A), 3, p(E),
+              ctypes.byref(info), None) == -1
 
 
 def test_selftest_and_server_arguments_rejected_without_gpu(lib):
