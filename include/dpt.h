@@ -249,12 +249,16 @@ DPT_API dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int3
  * W^T V = I), and the map is iterated again from the identity: each stage is a
  * perturbation problem of strength lambda/Q around the previous eigenvalues, so
  * a lambda beyond the direct iteration's domain can be reached.  A stage is one
- * full solve for the right eigenvectors (opt->prec: mixed or plain FP64) and,
- * except in the last stage, one on the transposed problem for the left ones; the
- * basis changes are FP64 matrix products (four per stage).
+ * full solve for the right eigenvectors (opt->prec: mixed or plain FP64; a mixed
+ * last stage is refined by the plain FP64 map started from its result) and, except
+ * in the last stage, one on the transposed problem for the left ones.  The basis
+ * changes are FP64 matrix products (six per stage, three in the last): the stage
+ * matrix is the exact transform W^T M_{q+1} V, so errors of earlier stages enter
+ * the next stage's perturbation instead of being lost, and one Newton-Schulz step
+ * W <- W (2I - V^T W) keeps W^T V = I to working precision.
  *   n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out   as for dpt_solve_full,
  *              real (DPT_R64) only, all four arrays device pointers
- *              (DPT_ERR_UNSUPPORTED otherwise), 1 <= n <= 65536
+ *              (DPT_ERR_UNSUPPORTED otherwise), 1 <= n <= 32768
  *   stages     Q, 1..1024 (1 is the direct solve)
  *   opt        tol, max_iter, prec, max_slices, slice_tol, graph_iters apply to every
  *              stage solve; start, ramp_alpha and epstein_nesbet must be unset

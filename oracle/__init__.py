@@ -214,14 +214,18 @@ def homotopy(theta, delta, lam, stages, tol=1e-12, max_iter=1000):
     eigenbasis just computed (the diagonal matrix of its eigenvalues becomes the
     next unperturbed matrix) and the map is iterated again from the identity.
 
-    With right eigenvectors V and left eigenvectors W of M_q = D + q (lam/Q) Delta
-    (W^T V = I), M_{q+1} = M_q + (lam/Q) Delta becomes, in that basis,
-        W^T M_{q+1} V = diag(E_q) + (lam/Q) W^T Delta V,
-    a perturbation problem of the form DPT solves.  Each stage solves it for the
-    right eigenvectors A' (columns with A'_ii = 1) and, on the transposed problem,
-    the left ones B' (scaled so that B'^T A' = I); then V <- V A', W <- W B'.
-    Stage solves use solve_full (FP64, from the identity); the basis changes are
-    plain matrix products.  Real theta / Delta.
+    Reading of the basis change (the paper gives none): with V the accumulated
+    right eigenvectors and W^T = V^{-1}, step q + 1 solves the matrix
+        S = W^T M_{q+1} V = diag(E_q) + (lam/Q) Delta_q,
+        Delta_q = (W^T (diag(theta) V + lambda_{q+1} Delta V) - diag(E_q)) Q / lam,
+    i.e. the exact similarity transform of M_{q+1} = diag(theta) + lambda_{q+1}
+    Delta, lambda_{q+1} = (q + 1) lam / Q, so errors of earlier stages are carried
+    into the next stage's perturbation instead of being dropped.  Each stage solves
+    S for its right eigenvectors A' (A'_ii = 1) and, except in the last stage, its
+    transpose for the left ones B' (scaled so that B'^T A' = I); then V <- V A',
+    W <- W B', followed by one Newton-Schulz step W <- W (2 I - V^T W) that
+    restores W^T V = I to working precision.  Stage solves are solve_full (FP64,
+    from the identity); the basis changes are plain matrix products.  Real only.
 
     Returns (A, E, info): A = V with each column scaled to its chart entry
     A[i, i] = 1 (the chart of the original problem), E the eigenvalues, info with
@@ -235,25 +239,28 @@ def homotopy(theta, delta, lam, stages, tol=1e-12, max_iter=1000):
     step_lam = float(lam) / Q
     V = np.eye(n)
     W = np.eye(n)
-    th = theta.copy()
+    Eq = theta.copy()
     iters = 0
     for q in range(Q):
-        Dq = W.T @ D @ V
-        Ar, E, ir = solve_full(th, Dq, step_lam, tol=tol, max_iter=max_iter)
+        lam_next = (q + 1) * step_lam
+        S = W.T @ (theta[:, None] * V + lam_next * (D @ V))
+        Dq = (S - np.diag(Eq)) / step_lam
+        Ar, E, ir = solve_full(Eq, Dq, step_lam, tol=tol, max_iter=max_iter)
         iters += ir["iters"]
         if ir["status"] != "OK":
-            return V, th, {"status": ir["status"], "stages": q, "iters": iters}
+            return V, Eq, {"status": ir["status"], "stages": q, "iters": iters}
+        V = V @ Ar
         if q + 1 < Q:
-            Bl, _, il = solve_full(th, Dq.T, step_lam, tol=tol, max_iter=max_iter)
+            Bl, _, il = solve_full(Eq, Dq.T, step_lam, tol=tol, max_iter=max_iter)
             iters += il["iters"]
             if il["status"] != "OK":
-                return V, th, {"status": il["status"], "stages": q, "iters": iters}
+                return V, Eq, {"status": il["status"], "stages": q, "iters": iters}
             Bl = Bl / np.sum(Bl * Ar, axis=0)[None, :]      # b_i^T a_i = 1
             W = W @ Bl
-        V = V @ Ar
-        th = np.real(E).astype(np.float64)
+            W = W @ (2.0 * np.eye(n) - V.T @ W)             # Newton-Schulz: W^T V -> I
+        Eq = np.real(E).astype(np.float64)
     V = V / np.diag(V)[None, :]
-    return V, th, {"status": "OK", "stages": Q, "iters": iters}
+    return V, Eq, {"status": "OK", "stages": Q, "iters": iters}
 
 
 def rs_series(theta, delta, lam, k):

@@ -768,19 +768,42 @@ dpt_status solve_homotopy(int64_t n64, const double* theta, const double* delta,
     int iters = 0, launches = 0;
     double resid = 0.0;
     for (int q = 0; q < stages && ret == DPT_OK; ++q) {
-      // the stage problem: theta_q = E_{q-1}, Delta_q = W^T Delta V
-      CK(launch_gemm_f64(n, delta, ld_delta, V, ld, T, st, s));
+      const bool last = q + 1 == stages;
+      // the stage matrix W^T M_{q+1} V = diag(E_q) + step Delta_q, exactly transformed
+      CK(launch_gemm_f64(n, delta, ld_delta, V, ld, T, st, s));          // Delta V
+      CK(launch_h_mv(n, ld, theta, V, (q + 1) * step, T, s));           // M_{q+1} V
       CK(launch_h_transpose(n, ld, W, X, s));
-      CK(launch_gemm_f64(n, X, ld, T, ld, Dq, st, s));
-      launches += 3;
+      CK(launch_gemm_f64(n, X, ld, T, ld, Dq, st, s));                  // W^T M V
+      CK(launch_h_stage(n, ld, thq, step, Dq, s));                      // Delta_q
+      launches += 5;
       dpt_info si{};
       ret = stage(Dq, Ar, Eq, &si);
       iters += si.iters;
       launches += si.launches;
       resid = si.residual;
+      if (ret == DPT_OK && last && o.prec != DPT_PREC_FP64) {
+        // the last stage decides the accuracy: refine the mixed result with the plain
+        // FP64 map started from it (a few steps)
+        std::vector<double> th((size_t)n);
+        CK(cudaMemcpyAsync(th.data(), thq, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        dpt_options po = so;
+        po.prec = DPT_PREC_FP64;
+        po.start = Ar;
+        po.ld_start = ld;
+        dpt_info sp{};
+        ret = solve_full_fp64(n, false, th, Dq, true, ld, step, po, Ar, true, ld, Eq, true, &sp,
+                              s);
+        iters += sp.iters;
+        launches += sp.launches;
+        resid = sp.residual;
+      }
       if (ret != DPT_OK) break;
-      if (q + 1 < stages) {
-        // left eigenvectors of the stage problem (its transpose), scaled to B^T A = I
+      CK(launch_gemm_f64(n, V, ld, Ar, ld, T, st, s));                  // V <- V A'
+      std::swap(V, T);
+      launches += 1;
+      if (!last) {
+        // left eigenvectors of the stage matrix (its transpose), scaled to B^T A = I
         CK(launch_h_transpose(n, ld, Dq, X, s));
         dpt_info sl{};
         ret = stage(X, Bl, El, &sl);
@@ -788,14 +811,17 @@ dpt_status solve_homotopy(int64_t n64, const double* theta, const double* delta,
         launches += sl.launches + 1;
         if (ret != DPT_OK) break;
         CK(launch_h_biorth(n, ld, Ar, Bl, st, s));
-        CK(launch_gemm_f64(n, W, ld, Bl, ld, T, st, s));
+        CK(launch_gemm_f64(n, W, ld, Bl, ld, T, st, s));                // W <- W B'
         std::swap(W, T);
-        launches += 2;
+        // one Newton-Schulz step W <- W (2 I - V^T W) restores W^T V = I
+        CK(launch_h_transpose(n, ld, V, X, s));
+        CK(launch_gemm_f64(n, X, ld, W, ld, T, st, s));
+        CK(launch_h_two_minus(n, ld, T, s));
+        CK(launch_gemm_f64(n, W, ld, T, ld, Dq, st, s));
+        std::swap(W, Dq);
+        launches += 6;
       }
-      CK(launch_gemm_f64(n, V, ld, Ar, ld, T, st, s));
-      std::swap(V, T);
       CK(cudaMemcpyAsync(thq, Eq, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-      launches += 1;
     }
     if (ret == DPT_OK) {
       CK(launch_h_chart(n, ld, V, A_out, ld_a, st, s));
@@ -1542,7 +1568,7 @@ dpt_status dpt_solve_homotopy(int64_t n, const double* theta, const double* delt
     if (info) { info->status = st; info->seconds = timer.sec(); }
     return st;
   };
-  if (n < 1 || n > (1 << 16) || !theta || !delta || !A_out || !E_out || ld_delta < n ||
+  if (n < 1 || n > (1 << 15) || !theta || !delta || !A_out || !E_out || ld_delta < n ||
       ld_a < n || !std::isfinite(lambda) || stages < 1 || stages > 1024 || !(o.tol > 0) ||
       o.max_iter < 0 || o.max_slices < 1 || o.max_slices > 3 ||
       (o.prec != DPT_PREC_FP64 && o.prec != DPT_PREC_MIXED_BF16))

@@ -1,11 +1,12 @@
 // Homotopy continuation (arXiv:2002.12872, Discussion): lambda is reached in Q equal
 // steps; after each step the problem is re-expressed in the eigenbasis just found,
-//     W^T (M_q + (lambda/Q) Delta) V = diag(E_q) + (lambda/Q) W^T Delta V,
-// with V the right and W the left eigenvectors of M_q (W^T V = I), and the map is
-// iterated again from the identity.  The stage solves are the library's full
+//     W^T M_{q+1} V = diag(E_q) + (lambda/Q) Delta_q,
+// with V the accumulated right and W the left eigenvectors (W^T V = I), and the map
+// is iterated again from the identity.  The stage solves are the library's full
 // solves; this file holds the FP64 helpers of the basis changes (the products use
-// the FP64 GEMM of dpt_full_fp64.cu): a tiled transpose, the biorthogonal scaling
-// of the left eigenvectors and the final chart scaling.
+// the FP64 GEMM of dpt_full_fp64.cu): M V, the stage perturbation, a tiled
+// transpose, the biorthogonal scaling of the left eigenvectors, the Newton-Schulz
+// factor and the final chart scaling.
 #include <cuda_runtime.h>
 
 #include "dpt_device.cuh"
@@ -65,6 +66,50 @@ __global__ void k_h_chart(int n, int ld, const double* __restrict__ V, double* _
   }
   for (int j = threadIdx.x; j < n; j += blockDim.x)
     out[(int64_t)i * ld_out + j] = (j == i) ? 1.0 : v[j] / p;
+}
+
+// T <- diag(theta) V + c T  (column-major, leading dimension ld): with T = Delta V
+// on entry this is M V for M = diag(theta) + c Delta.
+__global__ void k_h_mv(int n, int ld, const double* __restrict__ theta,
+                       const double* __restrict__ V, double c, double* __restrict__ T) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (j >= n) return;
+  const int64_t idx = (int64_t)i * ld + j;
+  T[idx] = fma(c, T[idx], theta[j] * V[idx]);
+}
+
+// S <- (S - diag(e)) / step: the stage perturbation from the transformed matrix.
+__global__ void k_h_stage(int n, int ld, const double* __restrict__ e, double step,
+                          double* __restrict__ S) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (j >= n) return;
+  const int64_t idx = (int64_t)i * ld + j;
+  S[idx] = (j == i ? S[idx] - e[i] : S[idx]) / step;
+}
+
+// T <- 2 I - T (the Newton-Schulz factor).
+__global__ void k_h_two_minus(int n, int ld, double* __restrict__ T) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (j >= n) return;
+  const int64_t idx = (int64_t)i * ld + j;
+  T[idx] = (j == i ? 2.0 : 0.0) - T[idx];
+}
+
+cudaError_t launch_h_mv(int n, int ld, const double* theta, const double* V, double c, double* T,
+                        cudaStream_t s) {
+  k_h_mv<<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, ld, theta, V, c, T);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_h_stage(int n, int ld, const double* e, double step, double* S,
+                           cudaStream_t s) {
+  k_h_stage<<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, ld, e, step, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_h_two_minus(int n, int ld, double* T, cudaStream_t s) {
+  k_h_two_minus<<<dim3((n + 255) / 256, n), 256, 0, s>>>(n, ld, T);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_h_transpose(int n, int ld, const double* X, double* Y, cudaStream_t s) {

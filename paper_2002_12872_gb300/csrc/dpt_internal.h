@@ -220,6 +220,11 @@ cudaError_t launch_dom_start(int n, const double* v, float2* z, double* z64, Dom
                              cudaStream_t s);
 cudaError_t launch_fp64_start(int n, int ld, int cplx, double* A, IterState* st, cudaStream_t s);
 cudaError_t launch_h_transpose(int n, int ld, const double* X, double* Y, cudaStream_t s);
+cudaError_t launch_h_mv(int n, int ld, const double* theta, const double* V, double c, double* T,
+                        cudaStream_t s);
+cudaError_t launch_h_stage(int n, int ld, const double* e, double step, double* S,
+                           cudaStream_t s);
+cudaError_t launch_h_two_minus(int n, int ld, double* T, cudaStream_t s);
 cudaError_t launch_h_biorth(int n, int ld, const double* A, double* B, IterState* st,
                             cudaStream_t s);
 cudaError_t launch_h_chart(int n, int ld, const double* V, double* out, int64_t ld_out,

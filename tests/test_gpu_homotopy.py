@@ -60,13 +60,14 @@ def test_homotopy_parity(ora, dpt, prec, case):
     assert np.array_equal(np.diag(to_np(A)), np.ones(n))
 
 
-def test_one_stage_is_the_direct_solve(dpt):
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_one_stage_is_the_direct_solve(ora, dpt, prec):
     th, D = _sym(200, 3)
     thd, Dd = _dev(th, D)
-    A1, E1, i1 = dpt.solve_homotopy(thd, Dd, 0.3, 1)
-    A0, E0, i0 = dpt.solve_full(thd, Dd, 0.3)
-    assert i1["status"] == "OK" and i1["iters"] == i0["iters"]
-    assert torch.equal(E1, E0) and torch.equal(A1, A0)
+    A1, E1, i1 = dpt.solve_homotopy(thd, Dd, 0.3, 1, prec=prec, tol=1e-13)
+    Ao, Eo, io = ora.solve_full(th, D, 0.3, tol=1e-14)
+    assert i1["status"] == "OK" and io["status"] == "OK"
+    assert eig_err(to_np(E1), Eo) <= EIG_RTOL and vec_err(to_np(A1), Ao) <= VEC_TOL
 
 
 def test_homotopy_argument_errors(dpt):
