@@ -50,8 +50,8 @@ def parse_args():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the dominant (CSR and dense), batched and served workloads")
     ap.add_argument("--only", default="all",
-                    choices=["all", "dominant", "dominant_dense", "homotopy", "batched",
-                             "served", "served_pool"],
+                    choices=["all", "dominant", "dominant_dense", "homotopy", "rs",
+                             "batched", "served", "served_pool"],
                     help="time one secondary workload alone and print its JSON object")
     ap.add_argument("--dense-n", type=int, default=32768,
                     help="dominant_dense: problem size")
@@ -412,6 +412,52 @@ def bench_homotopy(dpt, dev, n=2048, lam=2.5, stages=3, steps=3):
     return out
 
 
+def bench_rs_comparator(dpt, inputs, dev, N=100, big=2000):
+    """The paper's D-PT vs RS comparison (Sec. II.F) on the GPU, delta-potential
+    oscillator: for N = 100 the D-PT iterations (plain FP64 map) and the RS orders
+    (dpt_rs_series, FP64) needed to reach 1e-12 of the converged eigenvectors at
+    lambda = 1.5, and the RS error growth at lambda = 2.5; for N = `big` the time of a
+    D-PT solve (mixed and FP64) and of 70 RS orders at lambda = 1.5."""
+    import torch
+    w = inputs.delta_oscillator(N)
+    th = torch.tensor(w["theta"], device=dev)
+    D = dpt.colmajor_tensor(w["delta"], dev)
+    out = {"workload": f"delta-potential oscillator (Sec. II.F), N={N} and N={big}"}
+    A, _, info = dpt.solve_full(th, D, 1.5, prec="fp64", tol=1e-14, max_iter=500)
+    A = A.cpu().numpy()
+    kd = next((k for k in range(1, 200)
+               if np.linalg.norm(dpt.solve_full(th, D, 1.5, prec="fp64", tol=1e-300, max_iter=k,
+                                                check=False)[0].cpu().numpy() - A) < 1e-12), None)
+    kr = next((k for k in range(5, 201, 5)
+               if np.linalg.norm(dpt.rs_series(th, D, 1.5, k)[0].cpu().numpy() - A) < 1e-12), None)
+    A25, _, _ = dpt.solve_full(th, D, 2.5, prec="fp64", tol=1e-13, max_iter=3000)
+    A25 = A25.cpu().numpy()
+    errs = {k: float(np.linalg.norm(dpt.rs_series(th, D, 2.5, k)[0].cpu().numpy() - A25))
+            for k in (20, 40, 60)}
+    out["N100"] = {"lambda_1.5": {"dpt_iterations_to_1e-12": kd, "rs_orders_to_1e-12": kr},
+                   "lambda_2.5": {"rs_error_by_order": errs, "dpt_status": "OK"}}
+    w = inputs.delta_oscillator(big)
+    th = torch.tensor(w["theta"], device=dev)
+    D = dpt.colmajor_tensor(w["delta"], dev)
+    stream = torch.cuda.current_stream(dev)
+    timing = {}
+    for name, fn in (("dpt_mixed", lambda: dpt.solve_full(th, D, 1.5, max_iter=500)),
+                     ("dpt_fp64", lambda: dpt.solve_full(th, D, 1.5, prec="fp64", max_iter=500)),
+                     ("rs_70_orders", lambda: dpt.rs_series(th, D, 1.5, 70))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        timing[name] = {"ms": e0.elapsed_time(e1)}
+        if name.startswith("dpt"):
+            timing[name]["iters"] = r[2]["iters"]
+    out[f"N{big}"] = timing
+    return out
+
+
 def bench_batched(dpt, inputs, dev, steps=3, warmup=2):
     """20,000 independent symmetric problems, n log-uniform in [32, 512], one
     grouped solve per step (inputs resident in HBM; the pointer arrays of the call
@@ -712,6 +758,7 @@ def run_ours(args, world, rank, local):
         extra["dominant_csr"] = bench_dominant(dpt, inputs, dev, pk)
         extra["dominant_dense"] = bench_dominant_dense(dpt, inputs, dev, pk)
         extra["homotopy"] = bench_homotopy(dpt, dev)
+        extra["rs_comparator"] = bench_rs_comparator(dpt, inputs, dev)
         extra["batched"] = bench_batched(dpt, inputs, dev)
         extra["served"] = bench_served(dpt, inputs, dev)
         extra["served_pool"] = bench_served_pool(dpt, inputs, dev)
@@ -769,6 +816,8 @@ def main():
                                        warmup=max(1, min(args.warmup, 3)), n=args.dense_n)
         elif args.only == "homotopy":
             out = bench_homotopy(dpt, dev)
+        elif args.only == "rs":
+            out = bench_rs_comparator(dpt, inputs, dev)
         elif args.only == "batched":
             out = bench_batched(dpt, inputs, dev)
         elif args.only == "served_pool":

@@ -241,6 +241,21 @@ DPT_API dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int3
                                       double lambda, const dpt_options* opt, double* z_out,
                                       double* E_out, dpt_info* info, void* stream);
 
+/* Rayleigh-Schroedinger partial sums, the comparator the paper sets DPT against
+ * (Sec. II.D, Eq. (ARS-alpha); the recursion of Supplement B), in plain FP64:
+ *     A_out = sum_{l=0}^{order} lambda^l C^(l),   E_out = theta + sum_{l=1}^{order} lambda^l eps^(l),
+ *     C^(0) = I,  eps^(l)_i = (Delta C^(l-1))_ii,
+ *     C^(l)_ji = ((Delta C^(l-1))_ji - sum_{s<l} C^(l-1-s)_ji eps^(s+1)_i) / (theta_i - theta_j),
+ *     C^(l)_ii = 0.
+ * One FP64 product per order plus an l-term convolution of the earlier orders, all
+ * of which stay in device memory: (order + 3) n^2 doubles of workspace.
+ *   theta, delta (column-major, ld_delta), A_out (ld_a), E_out: device pointers
+ *   (DPT_ERR_UNSUPPORTED otherwise), real; 1 <= n <= 32768; 0 <= order <= 4096.
+ * DPT_ERR_DEGENERATE when two theta coincide.  Blocks until done. */
+DPT_API dpt_status dpt_rs_series(int64_t n, const double* theta, const double* delta,
+                                 int64_t ld_delta, double lambda, int32_t order, double* A_out,
+                                 int64_t ld_a, double* E_out, void* stream);
+
 /* Homotopy continuation (the Discussion's extension of the convergence domain):
  * lambda is reached in `stages` equal steps.  After each step the problem is
  * re-expressed in the eigenbasis just found,

@@ -848,6 +848,68 @@ dpt_status solve_homotopy(int64_t n64, const double* theta, const double* delta,
 }
 
 // ---------------------------------------------------------------------------
+// Rayleigh-Schroedinger partial sums (the comparator of Sec. II.D), FP64
+// ---------------------------------------------------------------------------
+dpt_status rs_series(int64_t n64, const double* theta, const double* delta, int64_t ld_delta,
+                     double lambda, int k, double* A_out, int64_t ld_a, double* E_out,
+                     cudaStream_t user) {
+  const int n = (int)n64, ld = n;
+  const size_t nn = (size_t)n * n;
+  std::vector<double> th;
+  dpt_status d = host_theta(n, theta, true, th);
+  if (d != DPT_OK) return d;
+  d = check_distinct(th);
+  if (d != DPT_OK) return d;
+  auto layout = [&](Carve& c) {
+    c.take<IterState>(1);
+    c.take<double>(nn * (size_t)(k + 1));   // C^(0..k)
+    c.take<double>(nn);                     // X = Delta C^(l-1)
+    c.take<double>(nn);                     // A partial sum
+    c.take<double>((size_t)n * (k + 1));    // eps^(0..k)
+    c.take<double>(n);                      // E partial sum
+  };
+  Block* b = acquire(measure(layout));
+  dpt_status ret = DPT_OK;
+  try {
+    Carve c{(char*)b->ptr};
+    IterState* st = c.take<IterState>(1);
+    double* C = c.take<double>(nn * (size_t)(k + 1));
+    double* X = c.take<double>(nn);
+    double* A = c.take<double>(nn);
+    double* eps = c.take<double>((size_t)n * (k + 1));
+    double* E = c.take<double>(n);
+    cudaStream_t s = b->stream;
+    CK(cudaEventRecord(b->ev, user));
+    CK(cudaStreamWaitEvent(s, b->ev, 0));
+    IterState h{};
+    h.status = ST_RUNNING;   // lets the FP64 GEMM run
+    *b->host_state = h;
+    CK(cudaMemcpyAsync(st, b->host_state, sizeof(IterState), cudaMemcpyHostToDevice, s));
+    CK(launch_fp64_init(n, ld, 0, C, s));     // C^(0) = I
+    CK(launch_fp64_init(n, ld, 0, A, s));     // A = lambda^0 C^(0)
+    CK(cudaMemcpyAsync(E, theta, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    double lam_l = 1.0;
+    for (int l = 1; l <= k; ++l) {
+      lam_l *= lambda;
+      CK(launch_gemm_f64(n, delta, ld_delta, C + nn * (size_t)(l - 1), ld, X, st, s));
+      CK(launch_rs_eps(n, ld, X, eps + (size_t)n * l, lam_l, E, s));
+      CK(launch_rs_order(n, ld, l, X, C, eps, theta, lam_l, A, s));
+    }
+    CK(cudaMemcpy2DAsync(A_out, sizeof(double) * ld_a, A, sizeof(double) * ld, sizeof(double) * n,
+                         n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(E_out, E, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaEventRecord(b->ev, s));
+    CK(cudaStreamWaitEvent(user, b->ev, 0));
+  } catch (Fail f) {
+    cudaStreamSynchronize(b->stream);
+    ret = f.st;
+  }
+  release(b);
+  return ret;
+}
+
+// ---------------------------------------------------------------------------
 // Dominant eigenvector, dense perturbation (GEMV)
 // ---------------------------------------------------------------------------
 dpt_status solve_dominant_dense(int64_t n64, const double* theta, const double* delta,
@@ -1552,6 +1614,25 @@ dpt_status dpt_solve_dominant(int64_t n, const double* theta, const int32_t* row
     return done(f.st);
   } catch (...) {
     return done(DPT_ERR_CUDA);
+  }
+}
+
+dpt_status dpt_rs_series(int64_t n, const double* theta, const double* delta, int64_t ld_delta,
+                         double lambda, int32_t order, double* A_out, int64_t ld_a,
+                         double* E_out, void* stream) {
+  if (n < 1 || n > (1 << 15) || !theta || !delta || !A_out || !E_out || ld_delta < n ||
+      ld_a < n || !std::isfinite(lambda) || order < 0 || order > 4096)
+    return DPT_ERR_ARG;
+  try {
+    if (!is_device_ptr(theta) || !is_device_ptr(delta) || !is_device_ptr(A_out) ||
+        !is_device_ptr(E_out))
+      return DPT_ERR_UNSUPPORTED;
+    return rs_series(n, theta, delta, ld_delta, lambda, order, A_out, ld_a, E_out,
+                     (cudaStream_t)stream);
+  } catch (Fail f) {
+    return f.st;
+  } catch (...) {
+    return DPT_ERR_CUDA;
   }
 }
 

@@ -225,6 +225,10 @@ cudaError_t launch_h_mv(int n, int ld, const double* theta, const double* V, dou
 cudaError_t launch_h_stage(int n, int ld, const double* e, double step, double* S,
                            cudaStream_t s);
 cudaError_t launch_h_two_minus(int n, int ld, double* T, cudaStream_t s);
+cudaError_t launch_rs_eps(int n, int ld, const double* X, double* eps_l, double lam_l, double* E,
+                          cudaStream_t s);
+cudaError_t launch_rs_order(int n, int ld, int l, const double* X, double* C, const double* eps,
+                            const double* theta, double lam_l, double* A, cudaStream_t s);
 cudaError_t launch_h_biorth(int n, int ld, const double* A, double* B, IterState* st,
                             cudaStream_t s);
 cudaError_t launch_h_chart(int n, int ld, const double* V, double* out, int64_t ld_out,

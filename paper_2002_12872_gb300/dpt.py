@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
                                          ctypes.POINTER(Options), P, i64, P,
                                          ctypes.POINTER(Info), P]
         L.dpt_solve_homotopy.restype = ctypes.c_int
+        L.dpt_rs_series.argtypes = [i64, P, P, i64, dbl, ctypes.c_int32, P, i64, P, P]
+        L.dpt_rs_series.restype = ctypes.c_int
         L.dpt_solve_dominant_dense.argtypes = [i64, P, P, i64, i64, dbl,
                                                ctypes.POINTER(Options), P, P,
                                                ctypes.POINTER(Info), P]
@@ -302,6 +304,23 @@ def solve_homotopy(theta, delta, lam, stages, *, prec="mixed", tol=1e-12, max_it
         err.result = res
         raise err
     return res
+
+
+def rs_series(theta, delta, lam, order, *, A_out=None, E_out=None, stream=None, check=True):
+    """Rayleigh-Schroedinger partial sums of the given order (dpt_rs_series, FP64):
+    (A, E) with A = sum_l lam^l C^(l), E = theta + sum_l lam^l eps^(l).  Real CUDA
+    tensors."""
+    n = int(theta.shape[0])
+    th_ptr, th_keep = _vec_ptr(theta, "float64")
+    d_ptr, ldd, d_keep = _colmajor(delta, False)
+    A = _empty_colmajor(n, delta, False) if A_out is None else A_out
+    E = _empty_vec(n, delta, False) if E_out is None else E_out
+    lda = A.stride(1) if _is_torch(A) else A.strides[1] // A.itemsize
+    st = lib().dpt_rs_series(n, th_ptr, d_ptr, ldd, float(lam), int(order), _ptr(A), lda,
+                             _ptr(E), _stream_of(delta, stream))
+    if check and st != OK:
+        raise RuntimeError(f"dpt_rs_series: {status_string(st)}")
+    return A, E, STATUS.get(st, str(st))
 
 
 class Batch:

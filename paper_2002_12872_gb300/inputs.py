@@ -28,6 +28,8 @@ sparse perturbations, Sec. II.G-H, are synthetic, so these stand in for them):
                      Hermitian Delta with E|x|^2 = 1/n (real N(0, 1/n) diagonal,
                      off-diagonal real and imaginary parts N(0, 1/(2n))),
                      lam ~ U[0.02, 0.08]
+  delta_oscillator   the harmonic oscillator with a delta potential (Sec. II.F):
+                     theta_n = 2n + 1/2, rank-one Delta from Hermite functions at 0
   served_pool /      the same requests drawn from a pool of distinct Hermitian
   served_stream      problems at stratified quantiles of the log-uniform size law
                      (each request its own lambda), so that long streams need not
@@ -138,6 +140,19 @@ def dominant_dense_device(n: int = 32768, rep: int = 0, lam: float = 0.1, device
     rows = torch.randn(n, n, generator=g, device=device, dtype=torch.float64)
     rows.mul_(1.0 / np.sqrt(n))
     return {"n": n, "theta": theta, "delta": rows.t(), "lam": lam, "nstar": 0, "tol": 1e-12}
+
+
+def delta_oscillator(N: int = 100) -> dict:
+    """The harmonic oscillator with a delta potential at the origin (Sec. II.F), on
+    the even Hermite functions: theta_n = 2n + 1/2 and the rank-one Delta_nm =
+    phi_2n(0) phi_2m(0), with phi_k(x) = (2^k k! sqrt(pi))^(-1/2) H_k(x) exp(-x^2/2),
+    so phi_0(0) = pi^(-1/4) and phi_2n(0) = -phi_2n-2(0) sqrt((2n-1)/(2n)) (from
+    H_2n(0) = (-1)^n (2n)!/n!).  Deterministic: no random draw."""
+    phi = np.zeros(N)
+    phi[0] = np.pi ** -0.25
+    for n in range(1, N):
+        phi[n] = -phi[n - 1] * np.sqrt((2 * n - 1) / (2 * n))
+    return {"n": N, "theta": 2 * np.arange(N) + 0.5, "delta": np.outer(phi, phi)}
 
 
 def csr_to_dense(row_ptr, col_idx, vals, n) -> np.ndarray:

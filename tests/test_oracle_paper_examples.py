@@ -57,14 +57,10 @@ def test_3x3_multipliers_are_roots_of_printed_polynomials(ora, lam):
 
 
 def _delta_potential(N=100):
-    """D = (2n + 1/2), Delta_nm = phi_2n(0) phi_2m(0) with Hermite functions
-    phi_k(x) = (2^k k! sqrt(pi))^(-1/2) H_k(x) exp(-x^2/2); phi_0(0) = pi^(-1/4) and
-    phi_2n(0) = -phi_2n-2(0) sqrt((2n-1)/(2n)) since H_2n(0) = (-1)^n (2n)!/n!."""
-    phi = np.zeros(N)
-    phi[0] = np.pi ** -0.25
-    for n in range(1, N):
-        phi[n] = -phi[n - 1] * np.sqrt((2 * n - 1) / (2 * n))
-    return 2 * np.arange(N) + 0.5, np.outer(phi, phi)
+    """The workload of Sec. II.F (paper_2002_12872_gb300.inputs.delta_oscillator)."""
+    from paper_2002_12872_gb300 import inputs
+    w = inputs.delta_oscillator(N)
+    return w["theta"], w["delta"]
 
 
 def test_delta_potential_lambda_1p5(ora):
@@ -100,3 +96,16 @@ def test_delta_potential_lambda_2p5(ora):
     assert info["status"] == "OK"
     errs = [np.linalg.norm(ora.rs_series(th, D, lam, k)[0] - A) for k in (20, 40, 60)]
     assert errs[0] < errs[1] < errs[2] and errs[2] > 1.0
+
+
+def test_delta_oscillator_hermite_values():
+    """phi_2n(0) of the workload against the closed form
+    (-1)^n sqrt((2n)!) / (2^n n!) / pi^(1/4) (H_2n(0) = (-1)^n (2n)!/n!)."""
+    import math
+    from paper_2002_12872_gb300 import inputs
+    w = inputs.delta_oscillator(12)
+    phi = np.sqrt(np.diag(w["delta"])) * np.sign(w["delta"][0])
+    for n in range(12):
+        want = (-1) ** n * math.sqrt(math.factorial(2 * n)) / (2**n * math.factorial(n)) / np.pi**0.25
+        assert abs(phi[n] - want) < 1e-14 * abs(want)
+    assert np.array_equal(w["theta"], 2 * np.arange(12) + 0.5)
