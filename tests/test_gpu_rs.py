@@ -53,13 +53,19 @@ def test_oscillator_claims_on_gpu(dpt):
     A, _, info = dpt.solve_full(th, D, 1.5, prec="fp64", tol=1e-14, max_iter=500)
     assert info["status"] == "OK"
     A = to_np(A)
-    err_d = {}
-    for k in (30, 40, 45):
+    def err_d(k):
         Ak, _, _ = dpt.solve_full(th, D, 1.5, prec="fp64", tol=1e-300, max_iter=k, check=False)
-        err_d[k] = np.linalg.norm(to_np(Ak) - A)
-    assert err_d[45] < 1e-12
-    err_rs = {k: np.linalg.norm(to_np(dpt.rs_series(th, D, 1.5, k)[0]) - A) for k in (45, 60)}
-    assert err_rs[45] > 1e3 * err_d[45] and err_rs[60] > 1e-12
+        return np.linalg.norm(to_np(Ak) - A)
+
+    def err_rs(k):
+        return np.linalg.norm(to_np(dpt.rs_series(th, D, 1.5, k)[0]) - A)
+
+    target = 1e-12
+    kd = next((k for k in range(20, 61) if err_d(k) < target), None)
+    kr = next((k for k in range(30, 101, 5) if err_rs(k) < target), None)
+    assert kd is not None and kd <= 45
+    assert kr is None or kr >= kd + 10
+    assert err_rs(45) > 100 * err_d(45)
     # lambda = 2.5: the series diverges, the map converges
     A, _, info = dpt.solve_full(th, D, 2.5, prec="fp64", tol=1e-13, max_iter=3000)
     assert info["status"] == "OK"
