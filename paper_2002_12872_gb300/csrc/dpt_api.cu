@@ -215,9 +215,14 @@ struct Prof {
 // ST_RUNNING.  One small device-to-host read of the state per chunk.
 // k_first: the iteration count at the start of the first chunk when the caller has
 // not read the state back (-1: read it from b->host_state).
+// tail: work enqueued after every chunk's slots, inside its graph (e.g. an output
+// kernel that acts only once the state has left ST_RUNNING), so that the chunk in
+// which the iteration stops also produces the outputs without another host round
+// trip; tail_launches counts its kernels.
 template <class F>
 void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kernels_per_iter,
-              Prof& prof, F&& iter, size_t state_bytes = sizeof(IterState), int k_first = -1) {
+              Prof& prof, F&& iter, size_t state_bytes = sizeof(IterState), int k_first = -1,
+              const std::function<void()>& tail = nullptr, int tail_launches = 0) {
   cudaStream_t s = b->stream;
   const int per = graph_iters > 0 ? graph_iters : 4;
   prof.make(per);
@@ -226,6 +231,7 @@ void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kerne
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int q = 0; q < per; ++q) iter(q);
+    if (tail) tail();
     CK(cudaStreamEndCapture(s, &g));
     cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
@@ -239,8 +245,9 @@ void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kerne
         CK(cudaGraphLaunch(exec, s));
       } else {
         for (int q = 0; q < per; ++q) iter(q);
+        if (tail) tail();
       }
-      prof.launches += per * kernels_per_iter;
+      prof.launches += per * kernels_per_iter + (tail ? tail_launches : 0);
       CK(cudaMemcpyAsync(b->host_state, dst, state_bytes, cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       const bool running = b->host_state->status == ST_RUNNING;
@@ -383,21 +390,25 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     prof.on = o.profile != 0;
     prof.launches = th.empty() ? 5 : 4;   // (theta check,) theta split, slicing, iteration 0, control
     {
+      // the outputs are formed inside the chunk in which the iteration stops (the
+      // output kernel does nothing while the state is still running)
+      const std::function<void()> tail = [&]() {
+        CK(launch_finalize(n, ld, Ahi[0], Alo[0], Ahi[1], Alo[1], Astage, lda_dev, st, 1, s));
+        if (e_dev)
+          CK(cudaMemcpyAsync(E_out, E, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      };
       run_loop(b, st, o.graph_iters, o.max_iter, 2, prof, [&](int q) {
         prof.before(q, s);
         if (pair) CK(launch_gemm_epi_pair(tA, tB0, tB1, p, npairs, s));
         else CK(launch_gemm_epi(tA, tB0, tB1, p, s));
         prof.after(q, s);
         CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
-      }, sizeof(IterState), /*k_first=*/1);   // the control after iteration 0 set k = 1
+      }, sizeof(IterState), /*k_first=*/1, tail, 1);   // the control after iteration 0 set k = 1
     }
-    prof.launches += 1;  // finalize
-    CK(launch_finalize(n, ld, Ahi[0], Alo[0], Ahi[1], Alo[1], Astage, lda_dev, st, s));
     if (!a_dev)
       CK(cudaMemcpy2DAsync(A_out, sizeof(double) * ld_a, Astage, sizeof(double) * ld,
                            sizeof(double) * n, n, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(E_out, E, sizeof(double) * n,
-                       e_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!e_dev) CK(cudaMemcpyAsync(E_out, E, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(b->host_state, st, sizeof(IterState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     const IterState& fs = *b->host_state;

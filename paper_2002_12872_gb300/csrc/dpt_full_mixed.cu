@@ -931,9 +931,10 @@ __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __
                                                   const float* __restrict__ Ahi1,
                                                   const float* __restrict__ Alo1,
                                                   double* __restrict__ Aout, int64_t ld_a,
-                                                  const IterState* st) {
+                                                  const IterState* st, int only_done) {
   const int j = blockIdx.x * 128 + threadIdx.x;
   if (j >= n) return;
+  if (only_done && st->status == ST_RUNNING) return;   // not the final iterate yet
   const int i0 = blockIdx.y * 128, i1 = min(n, i0 + 128);
   const int k = st->k;
   if (k == 0) {
@@ -1150,9 +1151,9 @@ cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
 
 cudaError_t launch_finalize(int n, int ld, const float* Ahi0, const float* Alo0,
                             const float* Ahi1, const float* Alo1, double* Aout, int64_t ld_a,
-                            const IterState* st, cudaStream_t s) {
+                            const IterState* st, int only_done, cudaStream_t s) {
   dim3 grid((n + 127) / 128, (n + 127) / 128);
-  k_finalize<<<grid, 128, 0, s>>>(n, ld, Ahi0, Alo0, Ahi1, Alo1, Aout, ld_a, st);
+  k_finalize<<<grid, 128, 0, s>>>(n, ld, Ahi0, Alo0, Ahi1, Alo1, Aout, ld_a, st, only_done);
   return cudaGetLastError();
 }
 

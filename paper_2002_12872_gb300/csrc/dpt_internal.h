@@ -188,7 +188,7 @@ cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
                             const CUtensorMap& tmB1, const GemmEpiParams& p, cudaStream_t s);
 cudaError_t launch_finalize(int n, int ld, const float* Ahi0, const float* Alo0,
                             const float* Ahi1, const float* Alo1, double* Aout, int64_t ld_a,
-                            const IterState* st, cudaStream_t s);
+                            const IterState* st, int only_done, cudaStream_t s);
 
 // Plain FP64 path (real and complex)
 cudaError_t launch_fp64_init(int n, int ld, int cplx, void* A0, cudaStream_t s);
