@@ -359,7 +359,9 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     } else {
       CK(cudaMemcpyAsync(thd, th.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
     }
-    CK(cudaMemsetAsync(dtb[0], 0, sizeof(__nv_bfloat16) * (size_t)ld * n * 2, s));
+    // no clearing of the increment buffers: iteration 0 writes all ld rows of dt_0,
+    // every product writes all ld rows of its dt_k before any read, and the operand
+    // tensor maps stop at row n (rows beyond read as zero)
     CK(launch_theta_ff(n, thd, thh, thl, s));
     CK(launch_prep_delta(delta, ldd, n, ld, o.epstein_nesbet, Dcat, st, s));
     CK(launch_iter0(delta, ldd, thh, thl, lambda, n, ld, o.epstein_nesbet, Dcat, Ahi[1], Alo[1],
