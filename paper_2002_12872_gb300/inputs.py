@@ -93,6 +93,20 @@ def full_unsymmetric(n: int = 4096, rep: int = 0, lam: float = 0.1) -> dict:
     return {"n": n, "theta": theta, "delta": delta, "lam": lam, "tol": 1e-12}
 
 
+def full_unsymmetric_device(n: int = 32768, rep: int = 0, lam: float = 0.1, device="cuda"):
+    """full_unsymmetric's recipe at sizes whose host generation would dominate a run:
+    theta from the same NumPy draw, Delta iid N(0, 1/n) drawn on the device with
+    torch's seeded generator (column-major: the transpose view of a row-major
+    tensor)."""
+    import torch
+    theta = spaced_uniform(n, 0.5, rng_for(2, rep))
+    g = torch.Generator(device=device)
+    g.manual_seed(seed_for(2, rep))
+    rows = torch.randn(n, n, generator=g, device=device, dtype=torch.float64)
+    rows.mul_(1.0 / np.sqrt(n))
+    return {"n": n, "theta": theta, "delta": rows.t(), "lam": lam, "tol": 1e-12}
+
+
 def dominant_csr(n: int = 2_000_000, nnz_per_row: int = 16, rep: int = 0,
                  lam: float = 0.01) -> dict:
     """Sparse unsymmetric CSR workload for the dominant-eigenvector form."""

@@ -169,6 +169,41 @@ def test_full_size_unsymmetric_sampled_columns(ora, dpt):
     assert rho.max() <= 1e-10
 
 
+def test_full_max_size_sampled_columns(ora, dpt):
+    """n = 32768, the largest size whose full mixed solve fits comfortably in device
+    memory beside its input and output (32 GB of workspace, 8.6 GB each for Delta
+    and A): every 64-bit offset of the slices (3 n^2 elements), partials and tiles is
+    exercised.  Checked on sampled columns: the explicit FP64 residual M a - E a of
+    16 seeded columns, and the oracle's solution of two of them (each column is its
+    own map, Sec. II.B)."""
+    n = 32768
+    cfg = inputs.full_unsymmetric_device(n=n)
+    th = torch.tensor(cfg["theta"], device="cuda")
+    D, lam = cfg["delta"], cfg["lam"]
+    A = torch.empty((n, n), dtype=torch.float64, device="cuda").t()
+    E = torch.empty(n, dtype=torch.float64, device="cuda")
+    _, _, info = dpt.solve_full(th, D, lam, A_out=A, E_out=E)
+    assert info["status"] == "OK"
+    rng = np.random.Generator(np.random.PCG64(n))
+    cols = np.sort(np.concatenate([[0, n - 1], rng.choice(np.arange(1, n - 1), 14, replace=False)]))
+    ct = torch.tensor(cols, device="cuda")
+    Ac = A[:, ct]
+    R = th[:, None] * Ac + lam * (D @ Ac) - Ac * E[ct][None, :]
+    s = th.abs().max().item() + lam * D.abs().sum(1).max().item()
+    rho = (torch.linalg.vector_norm(R, dim=0) / (s * torch.linalg.vector_norm(Ac, dim=0))).max()
+    assert rho.item() <= 1e-10
+    assert torch.all(A[ct, ct] == 1.0)
+    Dh = D.t().contiguous().cpu().numpy().T          # column-major host copy
+    two = np.array([0, n - 1])
+    Ao, Eo, io = ora.solve_full(cfg["theta"], Dh, lam, tol=1e-13, cols=two)
+    assert io["status"] == "OK"
+    assert eig_err(to_np(E)[two], Eo) <= EIG_RTOL
+    assert vec_err(to_np(A[:, torch.tensor(two, device="cuda")]), Ao) <= VEC_TOL
+    del A, D, cfg, Dh
+    dpt.release_workspace()
+    torch.cuda.empty_cache()
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_profiled_solve_reports_product_time(dpt, prec):
     cfg = inputs.full_unsymmetric(n=300)
