@@ -73,6 +73,36 @@ __device__ __forceinline__ void split_double(double v, float& hi, float& lo) {
   lo = __uint_as_float(sign | __float_as_uint(__uint2float_rn(rem) * __uint_as_float((unsigned)le << 23)));
 }
 
+// Splits a double v into hi + lo floats with a few branch-free integer operations
+// (one per streamed entry: split_double's exponent cases cost several times more).
+// hi is v truncated to 24 significant bits, lo the next 23 bits truncated, so
+// |v - hi - lo| < 2^-46 |v|.  Valid for 2^-103 <= |v| < 2^128; below that lo is 0
+// and below 2^-126 hi is 0 as well (such terms are under 2^-103 of the unit-size
+// quantities they meet).  Callers reject |v| >= 2^128 and non-finite v with
+// beyond_float().
+__device__ __forceinline__ void split_double_fast(double v, float& hi, float& lo) {
+  const unsigned hb = (unsigned)__double2hiint(v);
+  const unsigned lb = (unsigned)__double2loint(v);
+  const unsigned e = (hb >> 20) & 0x7FFu;
+  // (hb:lb) << 3 puts the exponent's low 9 bits over the top 23 mantissa bits;
+  // subtracting 384 from that 9-bit field maps the FP64 bias onto the FP32 bias
+  // (e - 1023 + 127 = e - 896 = (e mod 512) - 384 for 897 <= e <= 1150)
+  const unsigned t = __funnelshift_l(lb, hb, 3) - (384u << 23);
+  const unsigned hib = (t & 0x7FFFFFFFu) | (hb & 0x80000000u);
+  // lo: the next 23 mantissa bits as the fraction of a float whose exponent is
+  // 23 below hi's, minus that float's leading one (exact, Sterbenz)
+  const unsigned base = (hib & 0xFF800000u) - (23u << 23);
+  const unsigned gb = base | ((lb >> 6) & 0x7FFFFFu);
+  const float l = __uint_as_float(gb) - __uint_as_float(base);
+  hi = (e >= 897u) ? __uint_as_float(hib) : __uint_as_float(hb & 0x80000000u);
+  lo = (e >= 920u) ? l : 0.f;
+}
+
+// True for values split_double_fast cannot represent: |v| >= 2^128, inf and NaN.
+__device__ __forceinline__ bool beyond_float(double v) {
+  return (((unsigned)__double2hiint(v) >> 20) & 0x7FFu) >= 1151u;
+}
+
 // True unless v is +-inf or NaN (integer test).
 __device__ __forceinline__ bool finite_bits(double v) {
   return ((unsigned)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7FFu) != 0x7FFu;
@@ -107,7 +137,8 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // pairs: D1 = bf16(v), D2 = bf16(v - D1), D3 = bf16(v - D1 - D2), the remainders
 // carried exactly in float-float, so D1 + D2 + D3 = v to 2^-24 relative.  Columns
 // in [n, ld) are written as zeros; en != 0 zeroes the diagonal.  A non-finite
-// entry sets *bad.
+// entry, or one of magnitude 2^128 or more (beyond the float range of the slices),
+// sets *bad.
 __device__ __forceinline__ void slice_tile_32x64(const double* __restrict__ delta, int64_t ld_in,
                                                  int n, int ld, int en, int bx, int by,
                                                  __nv_bfloat16* __restrict__ Dcat, int64_t cat_ld,
@@ -121,7 +152,7 @@ __device__ __forceinline__ void slice_tile_32x64(const double* __restrict__ delt
       double v = 0.0;
       if (j < n && k < n) {
         v = delta[(int64_t)k * ld_in + j];
-        if (!finite_bits(v)) atomicExch(bad, 1u);
+        if (beyond_float(v)) atomicExch(bad, 1u);   // non-finite, or beyond the float range
         if (en && j == k) v = 0.0;
       }
       tile[x][r] = v;      // tile[j - by][k - bx]
@@ -135,8 +166,8 @@ __device__ __forceinline__ void slice_tile_32x64(const double* __restrict__ delt
     const int j = by + r;
     if (j >= n) break;
     float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-    if (k0 < n) split_double(tile[r][2 * x], h0, l0);
-    if (k0 + 1 < n) split_double(tile[r][2 * x + 1], h1, l1);
+    if (k0 < n) split_double_fast(tile[r][2 * x], h0, l0);
+    if (k0 + 1 < n) split_double_fast(tile[r][2 * x + 1], h1, l1);
     __nv_bfloat16* row = Dcat + (int64_t)j * cat_ld + k0;
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) {

@@ -23,7 +23,7 @@
 //                every result, is deterministic), applies the map, reduces the
 //                norms; the last block takes the decision.
 // The first pass (on z_0, its own kernel instances) also tests every entry (finite;
-// below 2^128 in magnitude for the float-float split) and sums |Delta| per row for
+// below 2^128 in magnitude for the float-float split, split_double_fast) and sums |Delta| per row for
 // the residual scale s = max|theta| + |lambda| max_m sum_k |Delta_mk|.
 #include <cuda_runtime.h>
 
@@ -65,35 +65,6 @@ __device__ __forceinline__ void dd_mul(float ah, float al, float bh, float bl, f
   two_prod(ah, bh, p, pe);
   pe = fmaf(ah, bl, fmaf(al, bh, pe));
   fast_two_sum(p, pe, rh, rl);
-}
-
-// Splits a double v into hi + lo floats with a few integer operations (the FP64
-// pipe, conversions included, is far too slow for one operation per streamed
-// entry).  hi is v truncated to 24 significant bits, lo the next 23 bits truncated,
-// so |v - hi - lo| < 2^-46 |v|.  Valid for 2^-103 <= |v| < 2^128; below that lo is
-// 0 and below 2^-126 hi is 0 as well (the terms are then under 2^-103 |z|).  The
-// caller rejects |v| >= 2^128 and non-finite v through dd_exp_bad().
-__device__ __forceinline__ void dd_split(double v, float& hi, float& lo) {
-  const unsigned hb = (unsigned)__double2hiint(v);
-  const unsigned lb = (unsigned)__double2loint(v);
-  const unsigned e = (hb >> 20) & 0x7FFu;
-  // (hb:lb) << 3 puts the exponent's low 9 bits over the top 23 mantissa bits;
-  // subtracting 384 from that 9-bit field maps the FP64 bias onto the FP32 bias
-  // (e - 1023 + 127 = e - 896 = (e mod 512) - 384 for 897 <= e <= 1150)
-  const unsigned t = __funnelshift_l(lb, hb, 3) - (384u << 23);
-  const unsigned hib = (t & 0x7FFFFFFFu) | (hb & 0x80000000u);
-  // lo: the next 23 mantissa bits as the fraction of a float whose exponent is
-  // 23 below hi's, minus that float's leading one (exact, Sterbenz)
-  const unsigned base = (hib & 0xFF800000u) - (23u << 23);
-  const unsigned gb = base | ((lb >> 6) & 0x7FFFFFu);
-  const float l = __uint_as_float(gb) - __uint_as_float(base);
-  hi = (e >= 897u) ? __uint_as_float(hib) : __uint_as_float(hb & 0x80000000u);
-  lo = (e >= 920u) ? l : 0.f;
-}
-
-// True for entries dd_split cannot represent: |v| >= 2^128, inf and NaN.
-__device__ __forceinline__ bool dd_exp_bad(double v) {
-  return (((unsigned)__double2hiint(v) >> 20) & 0x7FFu) >= 1151u;
 }
 
 template <int VEC> struct DDVec;
@@ -173,10 +144,10 @@ __global__ void __launch_bounds__(DD_THREADS) k_dd_gemv(DDParams p) {
       const double d = DDVec<VEC>::get(dv, v);
       if (FF) {
         float dh, dl;
-        dd_split(d, dh, dl);
+        split_double_fast(d, dh, dl);
         const float2 zz = zs[kk];
         dd_fma(dh, dl, zz.x, zz.y, ah[v], al[v]);
-        if (FIRST) { ra[v] += fabsf(dh); bad |= dd_exp_bad(d); }
+        if (FIRST) { ra[v] += fabsf(dh); bad |= beyond_float(d); }
       } else {
         acc[v] = fma(d, zs64[kk], acc[v]);
         if (FIRST) { ra[v] += fabsf((float)d); bad |= !finite_bits(d); }

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta,
       if (j < n) {
         const double v = delta[(int64_t)i * ld_in + j];
         float vh, vl;
-        split_double(v, vh, vl);
+        split_double_fast(v, vh, vl);   // |v| < 2^128: checked by the slicing
         rowabs[e] += fabsf(vh);
         if (j == i) {
           nh = 1.f;
@@ -924,7 +924,7 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 // ---------------------------------------------------------------------------
 // Output: A (float-float -> FP64) and E of the returned iterate.
 // ---------------------------------------------------------------------------
-// Output: grid (128-row tiles, 128-column tiles); thread j owns row j of the tile
+// Output: grid (128-row tiles, 32-column tiles); thread j owns row j of the tile
 // and issues the loads of eight columns before their stores.
 __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __restrict__ Ahi0,
                                                   const float* __restrict__ Alo0,
@@ -935,7 +935,7 @@ __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __
   const int j = blockIdx.x * 128 + threadIdx.x;
   if (j >= n) return;
   if (only_done && st->status == ST_RUNNING) return;   // not the final iterate yet
-  const int i0 = blockIdx.y * 128, i1 = min(n, i0 + 128);
+  const int i0 = blockIdx.y * 32, i1 = min(n, i0 + 32);
   const int k = st->k;
   if (k == 0) {
     for (int i = i0; i < i1; ++i) Aout[(int64_t)i * ld_a + j] = (i == j) ? 1.0 : 0.0;
@@ -1152,7 +1152,7 @@ cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
 cudaError_t launch_finalize(int n, int ld, const float* Ahi0, const float* Alo0,
                             const float* Ahi1, const float* Alo1, double* Aout, int64_t ld_a,
                             const IterState* st, int only_done, cudaStream_t s) {
-  dim3 grid((n + 127) / 128, (n + 127) / 128);
+  dim3 grid((n + 127) / 128, (n + 31) / 32);   // 128 rows x 32 columns per block
   k_finalize<<<grid, 128, 0, s>>>(n, ld, Ahi0, Alo0, Ahi1, Alo1, Aout, ld_a, st, only_done);
   return cudaGetLastError();
 }
