@@ -134,8 +134,9 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // Reads Delta (FP64, column-major, rows j contiguous) at rows [by, by+32) and
 // columns [bx, bx+64) into shared memory, then writes row j of each of the three
 // slices (row-major, pitch ld inside a row of cat_ld = 3 ld elements) as BF16
-// pairs: D1 = bf16(v), D2 = bf16(v - D1), D3 = bf16(v - D1 - D2), the remainders
-// carried exactly in float-float, so D1 + D2 + D3 = v to 2^-24 relative.  Columns
+// pairs: with v = hi + lo (split_double_fast), D1 = bf16(hi), D2 = bf16(hi - D1),
+// D3 = bf16(hi - D1 - D2 + lo); the first two remainders are exact in float (hi has
+// 24 significant bits), so D1 + D2 + D3 = v to 2^-24 relative.  Columns
 // in [n, ld) are written as zeros; en != 0 zeroes the diagonal.  A non-finite
 // entry, or one of magnitude 2^128 or more (beyond the float range of the slices),
 // sets *bad.
@@ -169,14 +170,16 @@ __device__ __forceinline__ void slice_tile_32x64(const double* __restrict__ delt
     if (k0 < n) split_double_fast(tile[r][2 * x], h0, l0);
     if (k0 + 1 < n) split_double_fast(tile[r][2 * x + 1], h1, l1);
     __nv_bfloat16* row = Dcat + (int64_t)j * cat_ld + k0;
-#pragma unroll
-    for (int sl = 0; sl < 3; ++sl) {
-      const __nv_bfloat16 b0 = __float2bfloat16_rn(h0);
-      const __nv_bfloat16 b1 = __float2bfloat16_rn(h1);
-      *reinterpret_cast<__nv_bfloat162*>(row + (int64_t)sl * ld) = __halves2bfloat162(b0, b1);
-      two_sum(h0 - __bfloat162float(b0), l0, h0, l0);
-      two_sum(h1 - __bfloat162float(b1), l1, h1, l1);
-    }
+    // hi has 24 significant bits: D1 and D2 take 8 each with exact remainders, and
+    // the third slice rounds what is left together with lo
+    const __nv_bfloat16 a0 = __float2bfloat16_rn(h0), a1 = __float2bfloat16_rn(h1);
+    const float r0 = h0 - __bfloat162float(a0), r1 = h1 - __bfloat162float(a1);
+    const __nv_bfloat16 b0 = __float2bfloat16_rn(r0), b1 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 c0 = __float2bfloat16_rn((r0 - __bfloat162float(b0)) + l0);
+    const __nv_bfloat16 c1 = __float2bfloat16_rn((r1 - __bfloat162float(b1)) + l1);
+    *reinterpret_cast<__nv_bfloat162*>(row) = __halves2bfloat162(a0, a1);
+    *reinterpret_cast<__nv_bfloat162*>(row + ld) = __halves2bfloat162(b0, b1);
+    *reinterpret_cast<__nv_bfloat162*>(row + 2 * (int64_t)ld) = __halves2bfloat162(c0, c1);
   }
 }
 
