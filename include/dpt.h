@@ -169,11 +169,15 @@ DPT_API void dpt_options_default(dpt_options* opt);
 DPT_API const char* dpt_status_string(dpt_status s);
 
 /* Full spectrum: all n eigenpairs of M = diag(theta) + lambda * Delta.
- *   n          matrix size, n >= 1
+ *   n          matrix size, 1 <= n <= 2^20 (the mixed path's workspace, about 30
+ *              bytes per element, bounds it in practice; the plain FP64 path returns
+ *              DPT_ERR_TOO_LARGE beyond 65535)
  *   dtype      DPT_R64 or DPT_C128 (complex mixed solves run through the grouped path
  *              of dpt_solve_batched with one problem)
  *   theta      n doubles, pairwise distinct and finite
- *   delta      n x n, column-major, leading dimension ld_delta >= n, finite
+ *   delta      n x n, column-major, leading dimension ld_delta >= n, finite (the
+ *              mixed path also rejects entries of magnitude 2^128 or more: its slices
+ *              hold float-range values; DPT_ERR_ARG)
  *   lambda     real perturbation strength
  *   opt        options (NULL = defaults)
  *   A_out      n x n output, column-major, ld_a >= n: column i is the eigenvector

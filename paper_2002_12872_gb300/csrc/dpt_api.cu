@@ -1554,6 +1554,9 @@ dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const
   // the mixed path carries the residual across steps at one lambda
   if (o.ramp_alpha > 0.0 && o.prec != DPT_PREC_FP64) return done(DPT_ERR_UNSUPPORTED);
   if (o.start && o.ld_start < n) return done(DPT_ERR_ARG);
+  // the plain FP64 path launches one grid row per column (at most 65535); at that size
+  // each of its products would take minutes anyway
+  if (o.prec == DPT_PREC_FP64 && n > 65535) return done(DPT_ERR_TOO_LARGE);
   // the mixed path's first step is exact only from A_0 = I
   if (o.start && o.prec != DPT_PREC_FP64) return done(DPT_ERR_UNSUPPORTED);
   try {
