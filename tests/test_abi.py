@@ -79,6 +79,10 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert dd(4, p(th), p(d), 4, -1, float("nan"), ctypes.byref(o), p(z), p(Eo),
               ctypes.byref(info), None) == -1
     assert info.status == -1 and info.nstar == -1
+    # plain FP64 beyond 65535: refused before any work
+    o64 = dpt.options(prec="fp64")
+    assert lib.dpt_solve_full(70000, 0, p(th), p(d), 70000, 0.1, ctypes.byref(o64), p(A), 70000,
+                              p(E), ctypes.byref(info), None) == -9
     # homotopy: stages outside 1..1024, n < 1, ld_a < n
     hs = lib.dpt_solve_homotopy
     for args in ((4, 0), (4, 1025), (0, 2)):
