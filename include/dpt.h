@@ -142,6 +142,13 @@ typedef struct {
                               return DPT_ERR_UNSUPPORTED (their first step is exact
                               only from A_0 = I). */
   int64_t ld_start;        /* leading dimension of a full-solve start (>= n) */
+  int32_t certify;         /* mixed real full solve: nonzero (default) lets a product whose
+                              iterate is predicted to pass the tolerance (the residual
+                              falling geometrically below half of it) form only that
+                              residual, writing no next iterate; if the iterate does not
+                              pass after all, the same iteration runs again in full.
+                              Results and iteration counts are those of 0, which always
+                              runs the full map. */
 } dpt_options;
 
 typedef struct {

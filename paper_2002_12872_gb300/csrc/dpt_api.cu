@@ -348,6 +348,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     h.tol = o.tol;
     h.slice_tol = o.slice_tol;
     h.best = INFINITY;
+    h.certify_on = o.certify ? 1 : 0;
     double tm = 0;
     for (double v : th) tm = std::max(tm, std::fabs(v));
     h.theta_max = tm;                  // 0 for a device theta: set by the check kernel
@@ -1483,6 +1484,7 @@ void dpt_options_default(dpt_options* o) {
   o->ramp_alpha = 0.0;
   o->start = nullptr;
   o->ld_start = 0;
+  o->certify = 1;
 }
 
 int64_t dpt_workspace_bytes(int64_t n, dpt_dtype dtype, dpt_prec prec) {

@@ -586,6 +586,19 @@ __device__ __forceinline__ bool decide(volatile IterState* vs, double rho) {
   return true;
 }
 
+// Decision after a certifying pass (an assessment of A_k that produced no A_{k+1}):
+// the statuses of decide() when the iterate fails or passes; otherwise the state is
+// left as it is (k not advanced) so that the same iteration runs again in full.
+// Returns true when the iteration continues.
+__device__ __forceinline__ bool decide_final(volatile IterState* vs, double rho) {
+  vs->rho = rho;
+  if (vs->bad_input) { vs->status = ST_BADINPUT; return false; }
+  if (vs->timeout) { vs->status = ST_TIMEOUT; return false; }
+  if (!(rho == rho) || isinf(rho)) { vs->status = ST_DIVERGED; return false; }
+  if (rho <= vs->tol) { vs->status = ST_CONVERGED; return false; }
+  return true;
+}
+
 // The same for a single-vector solve: the next step applies lambda - dlam with
 // dlam = lambda alpha^k (carried in FP64 and as a float pair).
 __device__ __forceinline__ void dom_ramp_advance(volatile DomState* vs) {

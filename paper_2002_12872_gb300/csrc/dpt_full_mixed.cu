@@ -56,6 +56,7 @@ struct __align__(16) GemmSmemMisc {
   int k;
   int slices;
   int cur;
+  int certify;        // this product only assesses its iterate (IterState::certify)
   float e[BN];        // e_k for the tile's columns
   float dprev[BN];    // d_{k-1}
   float thh[BN];      // theta_i as float-float
@@ -218,6 +219,9 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
   const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + c;
   const bool first = (st->k == 0);
+  // after a certifying product only its residual norms are valid: the iterate, d and
+  // the column parameters of the next product stay as they are
+  const bool cert = st->certify != 0;
   {
     float r2 = 0.f, a2 = 0.f, rs = 0.f;
     double ep = 0.0;
@@ -245,9 +249,11 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
     if (!(rho_raw == rho_raw) || isinf(rho_raw)) rho_raw = __int_as_float(0x7f800000);
     const double dk = d[i];
     E[i] = theta[i] + st->lam * dk;
-    dprev_col[i] = (float)dk;
-    e_col[i] = (float)ep;
-    d[i] = dk + ep;
+    if (!cert) {
+      dprev_col[i] = (float)dk;
+      e_col[i] = (float)ep;
+      d[i] = dk + ep;
+    }
     if (first) {
       float rs = 0.f;
 #pragma unroll
@@ -279,10 +285,25 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
   vs->rho_bits = 0;
   const float dmax = __uint_as_float(vs->dmax_bits);
   vs->dmax_bits = 0;
+  if (cert) {
+    // the certifying pass assessed A_k: stop if it passed, else run the same
+    // iteration again in full (nothing it depends on was touched)
+    vs->certify = 0;
+    if (decide_final(vs, rho)) vs->slice_gemms = vs->slice_gemms + vs->slices;
+    return;
+  }
+  const double prev = vs->rho_last;
+  vs->rho_last = rho;
   if (!decide(vs, rho)) return;
   const int S = next_slices(vs, dmax, first);
   vs->slices = S;
   vs->slice_gemms = vs->slice_gemms + S;
+  // When the residual falls geometrically and the next one is predicted below half
+  // the tolerance, the next product only forms the residual of its iterate (no new
+  // iterate, increment or remainder is written): the last product of a converging
+  // solve then costs little more than its matrix product.
+  vs->certify = (vs->certify_on && vs->k >= 3 && prev > 0.0 && rho < prev &&
+                 rho * (rho / prev) <= 0.5 * vs->tol) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -325,6 +346,9 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
   const int n = p.n, ld = p.ld;
   const int S = ms->slices;
   const bool c1 = (ms->cur != 0);
+  // a certifying pass forms only the residual of the current iterate (nothing is
+  // written but its norms), see k_ctrl
+  const bool cert = ms->certify != 0;
   // explicit selects: indexing the parameter arrays with a runtime value would
   // copy the parameter block to local memory
   const float* __restrict__ Ahc = c1 ? p.A_hi[1] : p.A_hi[0];
@@ -351,16 +375,17 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
       if (i < n) {
         const int64_t idx = (int64_t)i * ld + j0;
         in[u].ah = ld4(Ahc + idx);
-        in[u].al = ld4(Alc + idx);
+        in[u].al = cert ? make_float4(0.f, 0.f, 0.f, 0.f) : ld4(Alc + idx);
         in[u].L = ld4(L + idx);
         in[u].dtp = *reinterpret_cast<const uint2*>(dtp + idx);
         // Delta_ij for j = j0..j0+3: row i of the row-major slices.  The diagonal
         // partial uses as many slices as this product: its truncation error then
         // obeys the same bound as the product's (see next_slices)
         const __nv_bfloat16* Drow = p.Dcat + (int64_t)i * p.cat_ld + j0;
-        in[u].D[0] = *reinterpret_cast<const uint2*>(Drow);
-        in[u].D[1] = S > 1 ? *reinterpret_cast<const uint2*>(Drow + ld) : make_uint2(0u, 0u);
-        in[u].D[2] = S > 2 ? *reinterpret_cast<const uint2*>(Drow + 2 * (int64_t)ld) : make_uint2(0u, 0u);
+        const int Se = cert ? 0 : S;
+        in[u].D[0] = Se > 0 ? *reinterpret_cast<const uint2*>(Drow) : make_uint2(0u, 0u);
+        in[u].D[1] = Se > 1 ? *reinterpret_cast<const uint2*>(Drow + ld) : make_uint2(0u, 0u);
+        in[u].D[2] = Se > 2 ? *reinterpret_cast<const uint2*>(Drow + 2 * (int64_t)ld) : make_uint2(0u, 0u);
       }
     }
 #pragma unroll
@@ -385,22 +410,24 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
         } else if (j < n) {
           const float R = f4(in[u].L, e) +
                           lam * (f4(x4, e) - ah * e_i - bf_at(in[u].dtp, e) * dp_i);
-          float gh, gl;
-          ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
-          dnew = bf16_round(R * __frcp_rn(gh));
-          Ln = fmaf(-gh, dnew, R) - gl * dnew;
-          ff_add_f(ah, al, dnew, nh, nl);
           r2 = fmaf(R, R, r2);
           a2 = fmaf(ah, ah, a2);
-          // e_{k+1} partial Delta_ij dt_ji: the slice products are exact (8-bit
-          // significands), summed in float-float
-          const float p1 = bf_at(in[u].D[0], e) * dnew;
-          const float p23 = fmaf(bf_at(in[u].D[1], e), dnew, bf_at(in[u].D[2], e) * dnew);
-          float sh, se;
-          two_sum(eh, p1, sh, se);
-          se += el + p23;
-          fast_two_sum(sh, se, eh, el);
-          mx = fmaxf(mx, fabsf(dnew));
+          if (!cert) {
+            float gh, gl;
+            ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
+            dnew = bf16_round(R * __frcp_rn(gh));
+            Ln = fmaf(-gh, dnew, R) - gl * dnew;
+            ff_add_f(ah, al, dnew, nh, nl);
+            // e_{k+1} partial Delta_ij dt_ji: the slice products are exact (8-bit
+            // significands), summed in float-float
+            const float p1 = bf_at(in[u].D[0], e) * dnew;
+            const float p23 = fmaf(bf_at(in[u].D[1], e), dnew, bf_at(in[u].D[2], e) * dnew);
+            float sh, se;
+            two_sum(eh, p1, sh, se);
+            se += el + p23;
+            fast_two_sum(sh, se, eh, el);
+            mx = fmaxf(mx, fabsf(dnew));
+          }
         }
         f4set(oh, e, nh);
         f4set(ol, e, nl);
@@ -408,16 +435,20 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
         ob[e] = bf_bits(dnew);
       }
       const int64_t idx = (int64_t)i * ld + j0;
-      st4(Ahn + idx, oh);
-      st4(Aln + idx, ol);
-      st4(L + idx, oL);
-      *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+      if (!cert) {
+        st4(Ahn + idx, oh);
+        st4(Aln + idx, ol);
+        st4(L + idx, oL);
+        *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+      }
       warp_sum_ff(r2, a2, eh, el);
       if (lane == 0) {
         p.part[((int64_t)0 * p.ntm + tm) * ld + i] = r2;
         p.part[((int64_t)1 * p.ntm + tm) * ld + i] = a2;
-        p.part[((int64_t)2 * p.ntm + tm) * ld + i] = eh;
-        p.part[((int64_t)3 * p.ntm + tm) * ld + i] = el;
+        if (!cert) {
+          p.part[((int64_t)2 * p.ntm + tm) * ld + i] = eh;
+          p.part[((int64_t)3 * p.ntm + tm) * ld + i] = el;
+        }
       }
     }
   }
@@ -442,6 +473,7 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
   if (threadIdx.x == 0) {
     ms->k = st->k;
     ms->slices = st->slices;
+    ms->certify = st->certify;
     ms->cur = st->cur;
     for (int s = 0; s < STAGES; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], 1); }
     for (int b = 0; b < NACC; ++b) { mbar_init(&ms->acc_full[b], 1); mbar_init(&ms->acc_empty[b], 1); }
@@ -609,8 +641,10 @@ __device__ __forceinline__ bool p_epi_bar_and(bool v) {
 }
 
 // Issue the copies of sub-chunk sc (columns 16 sc .. 16 sc + 15) of tile (m0, n0).
-__device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, int S, uint8_t* eb,
-                                             int ew, int lane, int m0, int n0, int sc) {
+// A certifying pass (cert) needs neither A_lo nor the slices.
+__device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, bool cert, int S,
+                                             uint8_t* eb, int ew, int lane, int m0, int n0,
+                                             int sc) {
   const float* Ahc = c1 ? p.A_hi[1] : p.A_hi[0];
   const float* Alc = c1 ? p.A_lo[1] : p.A_lo[0];
   const __nv_bfloat16* dtp = c1 ? p.dt[0] : p.dt[1];
@@ -621,9 +655,10 @@ __device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, in
     if (i >= p.n) continue;
     const int64_t idx = (int64_t)i * p.ld + j0;
     cp_async16(eb_f4(eb, ew, u, 0, lane), Ahc + idx);
-    cp_async16(eb_f4(eb, ew, u, 1, lane), Alc + idx);
+    if (!cert) cp_async16(eb_f4(eb, ew, u, 1, lane), Alc + idx);
     cp_async16(eb_f4(eb, ew, u, 2, lane), p.L + idx);
     cp_async8(eb_u2(eb, ew, u, 0, lane), dtp + idx);
+    if (cert) continue;
     const __nv_bfloat16* Drow = p.Dcat + (int64_t)i * p.cat_ld + j0;
     for (int sl = 0; sl < S; ++sl)
       cp_async8(eb_u2(eb, ew, u, 1 + sl, lane), Drow + (int64_t)sl * p.ld);
@@ -637,6 +672,7 @@ __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc
                                             int lane, int tm, int m0, int n0, int sc, float& mx) {
   const int n = p.n, ld = p.ld;
   const bool c1 = (ms->cur != 0);
+  const bool cert = ms->certify != 0;     // residual norms only, nothing written
   float* __restrict__ Ahn = c1 ? p.A_hi[0] : p.A_hi[1];
   float* __restrict__ Aln = c1 ? p.A_lo[0] : p.A_lo[1];
   __nv_bfloat16* __restrict__ dtn_out = c1 ? p.dt[1] : p.dt[0];
@@ -654,13 +690,15 @@ __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc
     if (i >= n) continue;   // uniform across the warp
     uint8_t* e8 = const_cast<uint8_t*>(eb);
     const float4 ah4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 0, lane));
-    const float4 al4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 1, lane));
+    const float4 al4 = cert ? make_float4(0.f, 0.f, 0.f, 0.f)
+                            : *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 1, lane));
     const float4 L4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 2, lane));
     const uint2 dtp = *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 0, lane));
+    const int Se = cert ? 0 : S;
     uint2 D[3];
-    D[0] = *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 1, lane));
-    D[1] = S > 1 ? *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 2, lane)) : make_uint2(0u, 0u);
-    D[2] = S > 2 ? *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 3, lane)) : make_uint2(0u, 0u);
+    D[0] = Se > 0 ? *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 1, lane)) : make_uint2(0u, 0u);
+    D[1] = Se > 1 ? *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 2, lane)) : make_uint2(0u, 0u);
+    D[2] = Se > 2 ? *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 3, lane)) : make_uint2(0u, 0u);
     const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * BM + r0);
     const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
     const float thh = ms->thh[cl], thl = ms->thl[cl];
@@ -677,22 +715,24 @@ __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc
         a2 += 1.f;
       } else if (j < n) {
         const float R = f4(L4, e) + lam * (f4(x4, e) - ah * e_i - bf_at(dtp, e) * dp_i);
-        float gh, gl;
-        ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
-        // the increment is rounded to BF16 and the remainder keeps R - Gap dnew
-        // exactly, so any reciprocal close to 1/gap serves
-        dnew = bf16_round(R * rcp_approx(gh));
-        Ln = fmaf(-gh, dnew, R) - gl * dnew;
-        ff_add_f(ah, al, dnew, nh, nl);
         r2 = fmaf(R, R, r2);
         a2 = fmaf(ah, ah, a2);
-        const float p1 = bf_at(D[0], e) * dnew;
-        const float p23 = fmaf(bf_at(D[1], e), dnew, bf_at(D[2], e) * dnew);
-        float sh, se;
-        two_sum(eh, p1, sh, se);
-        se += el + p23;
-        fast_two_sum(sh, se, eh, el);
-        mx = fmaxf(mx, fabsf(dnew));
+        if (!cert) {
+          float gh, gl;
+          ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
+          // the increment is rounded to BF16 and the remainder keeps R - Gap dnew
+          // exactly, so any reciprocal close to 1/gap serves
+          dnew = bf16_round(R * rcp_approx(gh));
+          Ln = fmaf(-gh, dnew, R) - gl * dnew;
+          ff_add_f(ah, al, dnew, nh, nl);
+          const float p1 = bf_at(D[0], e) * dnew;
+          const float p23 = fmaf(bf_at(D[1], e), dnew, bf_at(D[2], e) * dnew);
+          float sh, se;
+          two_sum(eh, p1, sh, se);
+          se += el + p23;
+          fast_two_sum(sh, se, eh, el);
+          mx = fmaxf(mx, fabsf(dnew));
+        }
       }
       f4set(oh, e, nh);
       f4set(ol, e, nl);
@@ -700,16 +740,20 @@ __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc
       ob[e] = bf_bits(dnew);
     }
     const int64_t idx = (int64_t)i * ld + j0;
-    st4(Ahn + idx, oh);
-    st4(Aln + idx, ol);
-    st4(L + idx, oL);
-    *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+    if (!cert) {
+      st4(Ahn + idx, oh);
+      st4(Aln + idx, ol);
+      st4(L + idx, oL);
+      *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+    }
     warp_sum_ff(r2, a2, eh, el);
     if (lane == 0) {
       p.part[((int64_t)0 * p.ntm + tm) * ld + i] = r2;
       p.part[((int64_t)1 * p.ntm + tm) * ld + i] = a2;
-      p.part[((int64_t)2 * p.ntm + tm) * ld + i] = eh;
-      p.part[((int64_t)3 * p.ntm + tm) * ld + i] = el;
+      if (!cert) {
+        p.part[((int64_t)2 * p.ntm + tm) * ld + i] = eh;
+        p.part[((int64_t)3 * p.ntm + tm) * ld + i] = el;
+      }
     }
   }
 }
@@ -754,6 +798,7 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   if (threadIdx.x == 0) {
     ms->k = st->k;
     ms->slices = st->slices;
+    ms->certify = st->certify;
     ms->cur = st->cur;
     for (int s = 0; s < MAX_STAGES; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], 1); }
     for (int b = 0; b < NACC; ++b) { mbar_init(&ms->acc_full[b], 1); mbar_init(&ms->acc_empty[b], 2); }
@@ -843,13 +888,14 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const int et = threadIdx.x - 64;
     const uint32_t acc_empty_leader = mapa_shared(&ms->acc_empty[0], 0);
     const bool c1 = (ms->cur != 0);
+    const bool cert = ms->certify != 0;
     const int nsub = bn / 16;              // sub-chunks per tile (even: bn is a multiple of 32)
     float mx = 0.f;
     int lt = 0;
     // the first tile's first sub-chunk, while its products run
     if (pair < ntiles) {
       const int tm = 2 * (pair / ntn) + (int)rank;
-      if (tm < p.ntm) epi_prefetch(p, c1, S, EB, ew, lane, tm * BM, (pair % ntn) * bn, 0);
+      if (tm < p.ntm) epi_prefetch(p, c1, cert, S, EB, ew, lane, tm * BM, (pair % ntn) * bn, 0);
     }
     cp_async_commit();
     for (int t = pair; t < ntiles; t += npairs, ++lt) {
@@ -895,11 +941,11 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           // copies of the next sub-chunk: this tile's, or the next tile's first
           uint8_t* nb = EB + ((sc + 1) & 1) * EB_BYTES;
           if (sc + 1 < nsub) {
-            if (work) epi_prefetch(p, c1, S, nb, ew, lane, m0, n0, sc + 1);
+            if (work) epi_prefetch(p, c1, cert, S, nb, ew, lane, m0, n0, sc + 1);
           } else if (t + npairs < ntiles) {
             const int tn2 = 2 * ((t + npairs) / ntn) + (int)rank;
             if (tn2 < p.ntm)
-              epi_prefetch(p, c1, S, nb, ew, lane, tn2 * BM, ((t + npairs) % ntn) * bn, 0);
+              epi_prefetch(p, c1, cert, S, nb, ew, lane, tn2 * BM, ((t + npairs) % ntn) * bn, 0);
           }
           cp_async_commit();
           cp_async_wait<1>();              // this lane's copies of sub-chunk sc have landed

@@ -46,11 +46,13 @@ struct IterState {
   double slice_tol;
   double rho;          // normalised max residual of A_k
   double best;
-  double rho_last;
+  double rho_last;     // normalised residual of the previous iterate
   float dmax1;         // max |dt_0|: the increment fed to the first product
   double ramp_alpha;   // non-autonomous iteration (0: off)
   double ramp_pow;     // ramp_alpha^k
   double lam_k;        // strength the next map application uses (FP64 path)
+  int certify;         // mixed single solve: the next product only assesses its iterate
+  int certify_on;      // whether such passes may be scheduled (dpt_options::certify)
 };
 
 // State of a dominant-eigenvector solve (single-vector map), device resident.
