@@ -454,6 +454,9 @@ def bench_rs_comparator(dpt, inputs, dev, N=100, big=2000):
         timing[name] = {"ms": e0.elapsed_time(e1)}
         if name.startswith("dpt"):
             timing[name]["iters"] = r[2]["iters"]
+            # the mixed solve of this strongly coupled problem ends with plain FP64
+            # map steps (its float recursion cannot vouch for 1e-12 here)
+            timing[name]["fp64_iters"] = r[2].get("fp64_iters", 0)
     out[f"N{big}"] = timing
     return out
 
@@ -728,6 +731,8 @@ def run_ours(args, world, rank, local):
     # roofline of the product kernel: algorithmic 2 n^3 flop per launch (one DPT
     # iteration's product) over its measured average launch duration
     pk, src = peaks()
+    # the products take FP16 operands: FP16 and BF16 have the same nominal dense
+    # tensor-core rate, so the measured BF16 peak times 1 is the FP16 peak
     peak = pk["bf16_tflops_sustained"]
     per_launch_ms = prod_ms / max(1, prod_launches)
     achieved = 2.0 * N**3 / (per_launch_ms * 1e-3) / 1e12
@@ -787,10 +792,10 @@ def run_ours(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N, "lambda": cfg["lam"], "tol": 1e-12,
-                   "prec": "mixed (BF16 tensor-core increments, FP32 accumulate, "
-                           "float-float state)",
+                   "prec": "mixed (FP16 tensor-core slices and increments with power-of-two "
+                           "scales, FP32 accumulate, float-float state)",
                    "l2": "flushed between steps (256 MB write)",
                    "parallelism": f"{world} independent solves (one per GPU)"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -803,7 +808,8 @@ def run_ours(args, world, rank, local):
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "kernel": ("k_gemm_epi_pair (tcgen05 cta_group::2 product + fused update)"
                                 if pair else "k_gemm_epi (tcgen05 product + fused update)"),
-                     "peak_source": f"bf16_tflops_sustained, {src}",
+                     "peak_source": f"bf16_tflops_sustained x 1 (FP16 nominal rate = "
+                                    f"BF16), {src}",
                      "algorithmic": "2 n^3 flop per launch (one DPT iteration's product)",
                      "executed_tflops": executed,
                      "ms_per_launch": per_launch_ms},

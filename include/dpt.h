@@ -77,9 +77,11 @@ typedef enum {
   DPT_PREC_FP64 = 0,        /* every product in FP64 on the CUDA cores: the map of
                                Eq. (dyn) applied literally */
   DPT_PREC_MIXED_BF16 = 1   /* tensor-core products: each iteration multiplies Delta,
-                               split into up to three BF16 slices, by the BF16
-                               increment of A, with FP32 accumulation; A, the
-                               residual and the eigenvalues are carried in extended
+                               split into 16-bit slices, by the 16-bit increment of
+                               A, with FP32 accumulation (real single solves: FP16
+                               slices and increments with power-of-two scales;
+                               complex and grouped solves: BF16); A, the residual
+                               and the eigenvalues are carried in extended
                                precision, so the iteration refines to the FP64
                                fixed point */
 } dpt_prec;
@@ -95,13 +97,17 @@ typedef struct {
                               (the partition of Sec. II.H); same eigenpairs */
   int32_t graph_iters;     /* iterations per captured CUDA graph replay between
                               host convergence checks (default 4; 0 = no graph) */
-  int32_t max_slices;      /* BF16 slices of Delta in the mixed path, 1..3 (default 3) */
+  int32_t max_slices;      /* slices of Delta in the mixed path, 1..3 (default 3): that
+                              many BF16 slices in grouped and complex solves; a real
+                              single solve uses FP16 slices (11 significant bits each),
+                              two for max_slices 2 or 3 and one for 1 */
   int32_t profile;         /* nonzero: time every product kernel with CUDA events on
                               the stream it runs on (reported in dpt_info) */
-  double slice_tol;        /* mixed path: the first product uses max_slices slices; a
-                              later product uses two once its increment's largest entry
-                              is below 2^-8 of the first increment's, one once below
-                              2^-16 of it or below slice_tol (default 1e-8) */
+  double slice_tol;        /* mixed path: the first product uses all its slices; a
+                              later one drops a slice for each factor 2^-8 (BF16) or
+                              2^-11 (FP16) by which its increment's largest entry
+                              is below the first increment's, and uses one below
+                              slice_tol (default 1e-8) */
   int32_t cta_pair;        /* real mixed full solve: nonzero (default) runs the product
                               as CTA pairs (tcgen05 cta_group::2, 256-row tiles split
                               over two SMs, epilogue inputs staged in the shared memory
@@ -167,6 +173,11 @@ typedef struct {
                               form, else 0 */
   int32_t grouped_form;    /* grouped solves: the product form that ran (see
                               dpt_options.grouped_form), else 0 */
+  int32_t fp64_iters;      /* mixed real full solve: plain FP64 map steps (included in
+                              iters) that finished a strongly coupled solve, whose
+                              float recursion could not vouch for the tolerance
+                              (2^-23 times the sum of its residuals above
+                              max(tol, 1e-11)); 0 otherwise */
 } dpt_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -225,8 +236,8 @@ DPT_API dpt_status dpt_solve_batched(int64_t count, dpt_dtype dtype, const int64
  * memory (host buffers add their staging copies: about 8 n^2 bytes each for Delta
  * and A, twice that for DPT_C128).  The pool keeps its blocks, grown to the largest
  * request so far, until dpt_release_workspace.  Mixed real: about 30 bytes per matrix
- * element (BF16 slices of Delta, float-float A and its ping-pong copy, BF16
- * increments, the carried remainder); plain FP64: 3 n^2 doubles (A, its ping-pong
+ * element (room for three FP16 slices of Delta, float-float A and its ping-pong copy,
+ * FP16 increments, the carried remainder); plain FP64: 3 n^2 doubles (A, its ping-pong
  * copy and the product) per real component.  Host-only computation (no CUDA call);
  * -1 for n outside [1, 2^20] or an unknown dtype or prec. */
 DPT_API int64_t dpt_workspace_bytes(int64_t n, dpt_dtype dtype, dpt_prec prec);

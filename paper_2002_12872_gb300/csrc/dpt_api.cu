@@ -114,7 +114,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // 2-D BF16 tensor map: inner extent `inner` (contiguous), outer extent `outer`,
 // row pitch `pitch_elems`, box 64 x box_rows, 128-byte swizzle.
 CUtensorMap make_tmap_bf16(const void* base, uint64_t inner, uint64_t outer,
-                           uint64_t pitch_elems, uint32_t box_rows) {
+                           uint64_t pitch_elems, uint32_t box_rows, bool f16) {
   CUtensorMap m;
   auto fn = encode_fn();
   if (!fn) throw Fail{DPT_ERR_CUDA};
@@ -122,7 +122,8 @@ CUtensorMap make_tmap_bf16(const void* base, uint64_t inner, uint64_t outer,
   cuuint64_t strides[1] = {pitch_elems * 2};
   cuuint32_t box[2] = {64, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims,
+  CUresult r = fn(&m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                  2, const_cast<void*>(base), dims,
                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Fail{DPT_ERR_CUDA};
@@ -284,24 +285,29 @@ void layout_full_mixed_real(Carve& c, int n, bool delta_dev, bool a_dev) {
   c.take<float>(ld); c.take<float>(ld);      // e_col, dprev_col
   c.take<float>((size_t)4 * ntm * ld);       // column partials
   c.take<float>((size_t)ntn * ld);           // row partials
-  c.take<__nv_bfloat16>((size_t)3 * ld * n); // Dcat (three BF16 slices)
+  c.take<__half>((size_t)3 * ld * n);        // Dcat (room for three FP16 slices)
   for (int q = 0; q < 2; ++q) { c.take<float>((size_t)ld * n); c.take<float>((size_t)ld * n); }
-  for (int q = 0; q < 2; ++q) c.take<__nv_bfloat16>((size_t)ld * n);
+  for (int q = 0; q < 2; ++q) c.take<__half>((size_t)ld * n);
   c.take<float>((size_t)ld * n);             // L
   if (!delta_dev) c.take<double>((size_t)ld * n);
   if (!a_dev) c.take<double>((size_t)ld * n);
 }
 
+// rho_sum (optional): the sum of the residuals rho_k (k >= 1) the float recursion
+// carried, whose rounding bounds how far its tracked residual may be from the exact one.
 dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
                                  const double* theta_dev, const double* delta_in, bool delta_dev,
                                  int64_t ld_delta, double lambda, const dpt_options& o,
                                  double* A_out, bool a_dev, int64_t ld_a, double* E_out,
-                                 bool e_dev, dpt_info* info, cudaStream_t user) {
+                                 bool e_dev, dpt_info* info, cudaStream_t user,
+                                 double* rho_sum = nullptr) {
   const int n = (int)n64;
   // a multiple of the 128-row tile: the epilogue's vector accesses cover whole
   // tiles, so every row of every tile must lie inside its own column
   const int ld = (int)round_up(n64, 128);
-  const int S = o.max_slices;
+  // FP16 slices of Delta: two (22 significant bits, against 24 for the three BF16
+  // slices of the grouped path) unless a single slice is asked for
+  const int S = o.max_slices <= 1 ? 1 : 2;
   const int ntm = (n + 127) / 128, ntn = (n + 127) / 128;
   auto layout = [&](Carve& c) { layout_full_mixed_real(c, n, delta_dev, a_dev); };
   Block* b = acquire(measure(layout));
@@ -318,11 +324,11 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     float* dprev = c.take<float>(ld);
     float* part = c.take<float>((size_t)4 * ntm * ld);
     float* rowpart = c.take<float>((size_t)ntn * ld);
-    __nv_bfloat16* Dcat = c.take<__nv_bfloat16>((size_t)3 * ld * n);
+    __half* Dcat = c.take<__half>((size_t)3 * ld * n);
     float *Ahi[2], *Alo[2];
     for (int q = 0; q < 2; ++q) { Ahi[q] = c.take<float>((size_t)ld * n); Alo[q] = c.take<float>((size_t)ld * n); }
-    __nv_bfloat16* dtb[2];
-    for (int q = 0; q < 2; ++q) dtb[q] = c.take<__nv_bfloat16>((size_t)ld * n);
+    __half* dtb[2];
+    for (int q = 0; q < 2; ++q) dtb[q] = c.take<__half>((size_t)ld * n);
     float* L = c.take<float>((size_t)ld * n);
     const double* delta = delta_in;
     int64_t ldd = ld_delta;
@@ -364,12 +370,13 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     // every product writes all ld rows of its dt_k before any read, and the operand
     // tensor maps stop at row n (rows beyond read as zero)
     CK(launch_theta_ff(n, thd, thh, thl, s));
-    CK(launch_prep_delta(delta, ldd, n, ld, o.epstein_nesbet, Dcat, st, s));
-    CK(launch_iter0(delta, ldd, thh, thl, lambda, n, ld, o.epstein_nesbet, Dcat, Ahi[1], Alo[1],
-                    dtb[0], L, d, part, rowpart, st, s));
+    CK(launch_delta_scales(delta, ldd, n, thh, thl, lambda, o.epstein_nesbet, st, s));
+    CK(launch_prep_delta(delta, ldd, n, ld, o.epstein_nesbet, S, Dcat, st, s));
+    CK(launch_iter0(delta, ldd, thh, thl, lambda, n, ld, o.epstein_nesbet, S, Dcat, Ahi[1],
+                    Alo[1], dtb[0], L, d, part, rowpart, st, s));
     CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
 
-    const CUtensorMap tA = make_tmap_bf16(Dcat, (uint64_t)3 * ld, n, (uint64_t)3 * ld, 128);
+    const CUtensorMap tA = make_tmap_bf16(Dcat, (uint64_t)3 * ld, n, (uint64_t)3 * ld, 128, true);
     int nsm = 0, dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -379,8 +386,8 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     if (o.cta_pair) npairs = std::min(nsm / 2, mixed_pair_clusters());
     const bool pair = npairs > 0;
     const int bn = pair ? mixed_pair_tile_n((int)n, npairs) : mixed_tile_n((int)n, nsm);
-    const CUtensorMap tB0 = make_tmap_bf16(dtb[0], n, n, ld, pair ? bn / 2 : bn);
-    const CUtensorMap tB1 = make_tmap_bf16(dtb[1], n, n, ld, pair ? bn / 2 : bn);
+    const CUtensorMap tB0 = make_tmap_bf16(dtb[0], n, n, ld, pair ? bn / 2 : bn, true);
+    const CUtensorMap tB1 = make_tmap_bf16(dtb[1], n, n, ld, pair ? bn / 2 : bn, true);
     GemmEpiParams p{};
     p.n = n; p.ld = ld; p.ntm = ntm; p.bn = bn; p.lam = (float)lambda;
     for (int q = 0; q < 2; ++q) { p.A_hi[q] = Ahi[q]; p.A_lo[q] = Alo[q]; p.dt[q] = dtb[q]; }
@@ -391,7 +398,8 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     // state buffer may still be the source of the pending upload above: not touched)
     Prof prof;
     prof.on = o.profile != 0;
-    prof.launches = th.empty() ? 5 : 4;   // (theta check,) theta split, slicing, iteration 0, control
+    prof.launches = th.empty() ? 6 : 5;   // (theta check,) theta split, scales, slicing,
+                                          // iteration 0, control
     {
       // the outputs are formed inside the chunk in which the iteration stops (the
       // output kernel does nothing while the state is still running)
@@ -416,6 +424,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     CK(cudaStreamSynchronize(s));
     const IterState& fs = *b->host_state;
     ret = from_state(fs.status);
+    if (rho_sum) *rho_sum = fs.rho_sum;
     if (info) {
       info->iters = fs.k;
       info->slice_gemms = fs.slice_gemms;
@@ -1461,6 +1470,52 @@ dpt_status solve_full_mixed_complex(int64_t n, const std::vector<double>& th,
   return ret;
 }
 
+// The mixed real full solve as the public entry runs it.  Its float recursion tracks
+// the residual to about 2^-23 of the residuals it carried (sum of rho_k, k >= 1; the
+// increments and the FP32 accumulation are rounded relative to them).  For weakly
+// coupled problems that is far below the tolerance; when a problem is strongly
+// coupled (the 2 x 2 of Sec. II.E at lambda = 0.3 carries rho_1 ~ 2e-2) it is not,
+// and the iterate it returns is refined by the plain FP64 map started from it, which
+// forms every residual anew (a few steps, the fixed point attracting).
+dpt_status mixed_real_finished(int64_t n, std::vector<double> th, const double* theta_dev,
+                               const double* delta, bool delta_dev, int64_t ld_delta,
+                               double lambda, const dpt_options& o, double* A_out, bool a_dev,
+                               int64_t ld_a, double* E_out, bool e_dev, dpt_info* info,
+                               cudaStream_t s) {
+  dpt_info mi{};
+  double rho_sum = 0.0;
+  dpt_status st = solve_full_mixed_real(n, th, theta_dev, delta, delta_dev, ld_delta, lambda, o,
+                                        A_out, a_dev, ld_a, E_out, e_dev, &mi, s, &rho_sum);
+  if (st == DPT_OK && rho_sum * 0x1p-23 > std::max(o.tol, 1e-11)) {
+    if (th.empty()) {   // device theta, already checked by the mixed solve
+      st = host_theta(n, theta_dev, true, th);
+      if (st != DPT_OK) return st;
+    }
+    dpt_options po = o;
+    po.prec = DPT_PREC_FP64;
+    po.start = A_out;
+    po.ld_start = ld_a;
+    dpt_info fi{};
+    st = solve_full_fp64(n, false, th, delta, delta_dev, ld_delta, lambda, po, A_out, a_dev,
+                         ld_a, E_out, e_dev, &fi, s);
+    mi.iters += fi.iters;
+    mi.fp64_iters = fi.iters;
+    mi.launches += fi.launches;
+    mi.product_launches += fi.product_launches;
+    mi.product_ms += fi.product_ms;
+    mi.residual = fi.residual;
+    mi.status = st;
+  }
+  if (info) {
+    const double sec = info->seconds;
+    const int32_t ns = info->nstar;
+    *info = mi;
+    info->seconds = sec;
+    info->nstar = ns;
+  }
+  return st;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1568,9 +1623,9 @@ dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const
     std::vector<double> th;
     if (o.prec == DPT_PREC_MIXED_BF16 && dtype == DPT_R64 && th_dev && !o.epstein_nesbet)
       // theta stays on the device: checked there (finite, distinct, max) by the solve
-      return done(solve_full_mixed_real(n, th, theta, (const double*)delta, d_dev, ld_delta,
-                                        lambda, o, (double*)A_out, a_dev, ld_a, (double*)E_out,
-                                        e_dev, info, s));
+      return done(mixed_real_finished(n, th, theta, (const double*)delta, d_dev, ld_delta,
+                                      lambda, o, (double*)A_out, a_dev, ld_a, (double*)E_out,
+                                      e_dev, info, s));
     dpt_status st = host_theta(n, theta, th_dev, th);
     if (st != DPT_OK) return done(st);
     if (o.epstein_nesbet) {
@@ -1593,8 +1648,8 @@ dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const
       st = solve_full_mixed_complex(n, th, (const double*)delta, d_dev, ld_delta, lambda, o,
                                     (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info, s);
     else if (o.prec == DPT_PREC_MIXED_BF16)
-      st = solve_full_mixed_real(n, th, nullptr, (const double*)delta, d_dev, ld_delta, lambda,
-                                 o, (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info, s);
+      st = mixed_real_finished(n, th, nullptr, (const double*)delta, d_dev, ld_delta, lambda,
+                               o, (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info, s);
     else
       st = solve_full_fp64(n, dtype == DPT_C128, th, (const double*)delta, d_dev, ld_delta,
                            lambda, o, (double*)A_out, a_dev, ld_a, (double*)E_out, e_dev, info,

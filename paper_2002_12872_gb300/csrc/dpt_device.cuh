@@ -468,6 +468,10 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
+// The same with FP16 A and B (type fields 0): both operands of one MMA are FP16.
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 // ---------------------------------------------------------------------------
 // Warp transpose-reduction: each lane holds v[0..15] (16 columns); afterwards
@@ -542,6 +546,24 @@ __device__ __forceinline__ float bf_at(uint2 u, int e) {
 }
 __device__ __forceinline__ uint32_t bf_bits(float x) {
   return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+// Element e (0..3) of four FP16 values packed in a uint2, as a float (exact).
+__device__ __forceinline__ float h_at(uint2 u, int e) {
+  const uint32_t w = (e < 2) ? u.x : u.y;
+  return __half2float(__ushort_as_half((unsigned short)((e & 1) ? (w >> 16) : (w & 0xFFFFu))));
+}
+// Two floats rounded to FP16 (nearest even) and packed (a in the low half); values
+// beyond the FP16 range become +-65504 instead of infinities.
+__device__ __forceinline__ uint32_t f16x2_sat(float a, float b) {
+  uint32_t r;
+  asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+  return r;
+}
+// 2^e as a float, for -126 <= e <= 127 (exact; bit construction).
+__device__ __forceinline__ float exp2i(int e) { return __uint_as_float((unsigned)(e + 127) << 23); }
+// floor(log2 |x|) of a nonzero finite double, from its bits (normal range).
+__device__ __forceinline__ int ilog2_bits(double x) {
+  return (int)(((unsigned)__double2hiint(x) >> 20) & 0x7FFu) - 1023;
 }
 // Warp reduction of the column sums: |R|^2 and |a|^2 in float, the diagonal
 // increment (eh, el) in float-float.
@@ -629,6 +651,34 @@ __device__ __forceinline__ int next_slices(volatile IterState* vs, float dmax, b
   if ((double)dmax < vs->slice_tol || dmax <= d1 * 0x1p-16f) S = 1;
   else if (dmax <= d1 * 0x1p-8f) S = 2;
   return S < vs->max_slices ? S : vs->max_slices;
+}
+
+// The same rule for FP16 slices (11 significant bits each, so about 2^(-11 S)
+// relative) of a solve whose first product used nsl of them: S slices once
+// dmax <= 2^(-11 (nsl - S)) dmax1, one below slice_tol.
+__device__ __forceinline__ int next_slices_f16(volatile IterState* vs, float dmax, bool first,
+                                               int nsl) {
+  if (first) vs->dmax1 = dmax;
+  const float d1 = vs->dmax1;
+  if ((double)dmax < vs->slice_tol) return 1;
+  int S = nsl;
+  while (S > 1 && dmax <= d1 * exp2i(-11 * (nsl - S + 1))) --S;
+  return S;
+}
+
+// Scale exponent s of an FP16 increment buffer (it holds dt * 2^s): the expected
+// largest |dt| `ref` lands in [2^top, 2^(top+1)), so FP16's 2^-14 .. 65504 keeps its
+// full 11 bits for entries down to 2^-(14+top) of it (the rest rounds; the carried
+// remainder keeps what rounding drops).  s is bounded so that lambda 2^-(sig + s),
+// the product's multiplier, stays a normal float.  Scaling (Delta, lambda) to
+// (2^p Delta, 2^-p lambda) shifts sig by -p and leaves s unchanged.
+__device__ __forceinline__ int dt_scale_exp(double ref, int top, int sig, double lam) {
+  int s = (ref > 0.0 && ref < 1e300) ? top - ilog2_bits(ref) : 0;
+  if (lam != 0.0 && fabs(lam) < 1e300) {
+    const int lg = ilog2_bits(lam);
+    s = max(lg - 120 - sig, min(lg + 120 - sig, s));
+  }
+  return max(-120, min(120, s));
 }
 
 }  // namespace dpt

@@ -5,17 +5,23 @@
 //     R_k     = lambda (Delta A_k - A_k diag(d_k)) - Gap o A_k,   d_k = diag(Delta A_k),
 // with Gap_ji = theta_i - theta_j and G = 1/Gap off the diagonal, is carried here
 // in increment form so that every product acts on a small quantity:
-//     X_k   = Delta dt_{k-1}                         (tensor-core GEMM, BF16 in, FP32 acc)
+//     X_k   = Delta dt_{k-1}                         (tensor-core GEMM, FP16 in, FP32 acc)
 //     e_k   = diag(Delta dt_{k-1}),   d_k = d_{k-1} + e_k
 //     R_k   = L_k + lambda (X_k - A_k diag(e_k) - dt_{k-1} diag(d_{k-1}))
-//     dt_k  = bf16(G o R_k)                          (the increment actually applied)
+//     dt_k  = f16(G o R_k)                           (the increment actually applied)
 //     L_{k+1} = R_k - Gap o dt_k                     (carried remainder: exact feedback)
 //     A_{k+1} = A_k + dt_k                           (float-float accumulation)
 // Substituting A_k = A_{k-1} + dt_{k-1} into R_k shows this is the same recursion
-// as the map; the remainder L makes the BF16 rounding of each increment re-enter
-// the next step instead of being lost, so the fixed point is the FP64 one.
-// Delta enters the product as up to three BF16 slices (Delta ~ D1 + D2 + D3),
-// concatenated along K, so one GEMM of depth S*n gives the sliced product.
+// as the map; the remainder L makes the FP16 rounding of each increment re-enter
+// the next step instead of being lost, so the fixed point is the FP64 one: any
+// rounding (or clamping) of dt_k is made good by the following steps.
+// Delta enters the product as FP16 slices (Delta 2^sig ~ D1 + D2, 11 significant
+// bits each; a third on request), concatenated along K, so one GEMM of depth S*n
+// gives the sliced product.  The increments dt are FP16 as well, each buffer with
+// its own power-of-two scale: FP16 has three more significand bits than BF16 but a
+// narrow exponent range, and the scales (exact in both directions) give it the
+// range of the data.  Two FP16 slices carry 22 bits where three BF16 slices carried
+// 24, so the first products need a third fewer tensor-core passes.
 // R_k is, to rounding, the eigen-residual M a_i - E_i a_i of the iterate A_k
 // (the residual identity: R = Gap o (F(A) - A)); its column norms give the
 // convergence test without a second product.
@@ -32,13 +38,14 @@ namespace dpt {
 constexpr int BM = 128;          // rows j per tile (TMEM lanes)
 constexpr int BN = 256;          // widest tile: columns i per tile (TMEM columns per accumulator);
                                  // the launch's width p.bn is a multiple of 32 up to BN
-constexpr int BK = 64;           // K per stage: one 128-byte swizzle atom of BF16
+constexpr int BK = 64;           // K per stage: one 128-byte swizzle atom of 16-bit elements
 constexpr int UK = 16;           // K per tcgen05.mma (kind::f16)
 constexpr int STAGES = 4;        // operand ring depth (bytes in flight cover the L2 latency)
 constexpr int MAX_STAGES = 8;    // barrier slots; the CTA-pair kernel fits more, smaller stages
 constexpr int NACC = 2;          // TMEM accumulators (double buffer)
 constexpr int IT0 = 128;         // columns (and rows) per block of iteration 0
-constexpr int NSLICE = 3;        // BF16 slices of Delta kept (the product uses the first S)
+constexpr int NSLICE = 3;        // FP16 slices of Delta the layout holds (the solve writes
+                                 // max_slices of them, the product uses the first S)
 constexpr int A_TILE = BM * BK * 2;
 constexpr int B_TILE = BN * BK * 2;
 constexpr int EPI_WARPS = 8;
@@ -57,8 +64,11 @@ struct __align__(16) GemmSmemMisc {
   int slices;
   int cur;
   int certify;        // this product only assesses its iterate (IterState::certify)
-  float e[BN];        // e_k for the tile's columns
-  float dprev[BN];    // d_{k-1}
+  int sig;            // the slices hold Delta 2^sig
+  int scur;           // dt_{k-1} (the B operand) is stored as dt_{k-1} 2^scur
+  int snew;           // dt_k is stored as dt_k 2^snew
+  float e[BN];        // e_k 2^sig 2^scur for the tile's columns
+  float dprev[BN];    // d_{k-1} 2^sig
   float thh[BN];      // theta_i as float-float
   float thl[BN];
 };
@@ -79,35 +89,166 @@ constexpr int P_SMEM_BYTES = P_RING + SMEM_X + 2 * EB_BYTES + 1024 + (int)sizeof
 static_assert(P_SMEM_BYTES <= 232448, "CTA-pair shared memory over the per-block limit");
 
 // ---------------------------------------------------------------------------
-// Preparation: transpose Delta (column-major FP64) into row-major FP32 and into
-// the BF16 slices D1 + D2 + D3 (row-major, concatenated along K), zeroing the
-// diagonal when the Epstein-Nesbet partition is used.
+// Scales of the FP16 operands.  One block per column i of Delta (rows j
+// contiguous): the high word of max |Delta_ji| (the FP64 bits without the sign;
+// with its low word filled with ones it bounds max |Delta|) and max_{j != i}
+// |Delta_ji| / |theta_i - theta_j| (float-float gaps), both by integer atomicMax.
+// The last block sets sig (max |Delta| 2^sig in [2^14, 2^15)) and the exponent of
+// the first increment: |dt_0| <= |lambda| max |Delta_ji / gap| lands at 2^13.
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__ delta,
+                                                      int64_t ld_in, int n,
+                                                      const float* __restrict__ th_hi,
+                                                      const float* __restrict__ th_lo, int en,
+                                                      IterState* st) {
+  const int i = blockIdx.x;
+  const float thh = th_hi[i], thl = th_lo[i];
+  const double* col = delta + (int64_t)i * ld_in;
+  unsigned hmax = 0u;
+  float gmax = 0.f;
+  // four independent loads in flight per thread (the column streams from HBM)
+  for (int jb = threadIdx.x; jb < n; jb += 1024) {
+    double v[4];
+    float tjh[4], tjl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = jb + 256 * u;
+      v[u] = j < n ? col[j] : 0.0;
+      tjh[u] = j < n ? th_hi[j] : 0.f;
+      tjl[u] = j < n ? th_lo[j] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = jb + 256 * u;
+      if (j >= n) break;
+      const unsigned hw = (unsigned)__double2hiint(v[u]) & 0x7FFFFFFFu;
+      if (j == i) {
+        if (!en) hmax = max(hmax, hw);
+        continue;
+      }
+      hmax = max(hmax, hw);
+      float vh, vl;
+      split_double_fast(v[u], vh, vl);
+      float gh, gl;
+      ff_sub(thh, thl, tjh[u], tjl[u], gh, gl);
+      // a scale bound: an approximate reciprocal serves (NaN never wins fmaxf)
+      gmax = fmaxf(gmax, fabsf(vh) * rcp_approx(fabsf(gh)));
+    }
+  }
+  hmax = __reduce_max_sync(0xffffffffu, hmax);
+  unsigned gb = __reduce_max_sync(0xffffffffu, __float_as_uint(gmax));   // gmax >= 0
+  __shared__ unsigned wh[8], wg[8];
+  __shared__ bool last;
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { wh[w] = hmax; wg[w] = gb; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned a = 0u, b = 0u;
+    for (int q = 0; q < 8; ++q) { a = max(a, wh[q]); b = max(b, wg[q]); }
+    atomicMax(&st->amax_bits, a);
+    atomicMax(&st->g0max_bits, b);
+    __threadfence();
+    last = (atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  volatile IterState* vs = st;
+  const unsigned hm = vs->amax_bits;
+  int sig = 0;
+  if (hm != 0u) sig = 14 - ((int)((hm >> 20) & 0x7FFu) - 1023);   // max |Delta| < 2^(e+1)
+  sig = max(-120, min(120, sig));
+  const double lam = vs->lam;
+  const double ref = fabs(lam) * (double)__uint_as_float(vs->g0max_bits);
+  const int s0 = dt_scale_exp(ref, 13, sig, lam);
+  vs->sig = sig;
+  vs->sexp[0] = s0;
+  vs->sexp[1] = s0;
+  vs->blocks_done = 0;
+}
+
+// One 32-row x 64-column tile of the Delta -> FP16-slice conversion, block (32, 8):
+// as slice_tile_32x64 (shared-memory transpose, row-major slices of pitch cat_ld),
+// with NSL FP16 slices of Delta 2^sig: D1 = f16(hi 2^sig), each further slice the
+// FP16 rounding of what is left (the remainders are exact in float), the last one
+// taking lo as well.
+template <int NSL>
+__device__ __forceinline__ void slice16_tile_32x64(const double* __restrict__ delta, int64_t ld_in,
+                                                   int n, int ld, int en, float sc, int bx,
+                                                   int by, __half* __restrict__ Dcat, int64_t cat_ld,
+                                                   unsigned* bad, double (*tile)[65]) {
+  const int x = threadIdx.x, y = threadIdx.y;
+  {
+    const int j = by + x;
+#pragma unroll
+    for (int r = y; r < 64; r += 8) {
+      const int k = bx + r;
+      double v = 0.0;
+      if (j < n && k < n) {
+        v = delta[(int64_t)k * ld_in + j];
+        if (beyond_float(v)) atomicExch(bad, 1u);   // non-finite, or beyond the float range
+        if (en && j == k) v = 0.0;
+      }
+      tile[x][r] = v;      // tile[j - by][k - bx]
+    }
+  }
+  __syncthreads();
+  const int k0 = bx + 2 * x;
+  if (k0 >= ld) return;
+#pragma unroll
+  for (int r = y; r < 32; r += 8) {
+    const int j = by + r;
+    if (j >= n) break;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    if (k0 < n) split_double_fast(tile[r][2 * x], h0, l0);
+    if (k0 + 1 < n) split_double_fast(tile[r][2 * x + 1], h1, l1);
+    __half* row = Dcat + (int64_t)j * cat_ld + k0;
+    float r0 = h0 * sc, r1 = h1 * sc;
+#pragma unroll
+    for (int sl = 0; sl < NSL; ++sl) {
+      const bool lastsl = (sl == NSL - 1);
+      const float t0 = lastsl ? r0 + l0 * sc : r0;
+      const float t1 = lastsl ? r1 + l1 * sc : r1;
+      const __half q0 = __float2half_rn(t0), q1 = __float2half_rn(t1);
+      r0 = t0 - __half2float(q0);
+      r1 = t1 - __half2float(q1);
+      *reinterpret_cast<__half2*>(row + (int64_t)sl * ld) = __halves2half2(q0, q1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Preparation: transpose Delta (column-major FP64) into the row-major FP16 slices
+// of Delta 2^sig (concatenated along K), zeroing the diagonal when the
+// Epstein-Nesbet partition is used.
+// ---------------------------------------------------------------------------
+template <int NSL>
 __global__ void __launch_bounds__(256) k_prep_delta(const double* __restrict__ delta,
                                                     int64_t ld_in, int n, int ld, int en,
-                                                    __nv_bfloat16* __restrict__ Dcat,
-                                                    IterState* st) {
+                                                    __half* __restrict__ Dcat, IterState* st) {
   __shared__ double tile[32][65];
-  slice_tile_32x64(delta, ld_in, n, ld, en, blockIdx.x * 64, blockIdx.y * 32, Dcat,
-                   (int64_t)NSLICE * ld, &st->bad_input, tile);
+  const float sc = exp2i(st->sig);
+  slice16_tile_32x64<NSL>(delta, ld_in, n, ld, en, sc, blockIdx.x * 64, blockIdx.y * 32, Dcat,
+                          (int64_t)NSLICE * ld, &st->bad_input, tile);
 }
 
 // ---------------------------------------------------------------------------
 // Iteration 0 (A_0 = I), computed from the FP64 input in float-float:
 //   R_0 = lambda Delta (off the diagonal), d_0 = diag(Delta),
-//   dt_0 = bf16(G o R_0), L_1 = R_0 - Gap o dt_0, A_1 = I + dt_0,
-// plus the column partials of |R_0|^2, |a|^2 = 1, e_1 = diag(Delta dt_0) (float-
-// float) and the row partials of sum_k |Delta_jk| for the residual scale.
-// One block per 128 x 128 tile, 4 warps; each warp walks 32 columns and lane l
-// owns rows 4l..4l+3 (vector loads along the contiguous row index).
+//   dt_0 = f16(G o R_0) (stored scaled by 2^sexp[0]), L_1 = R_0 - Gap o dt_0,
+//   A_1 = I + dt_0,
+// plus the column partials of |R_0|^2, |a|^2 = 1, e_1 2^sig = diag(Delta 2^sig dt_0)
+// from the FP16 slices (float-float) and the row partials of sum_k |Delta_jk| for the
+// residual scale.  One block per 128 x 128 tile, 4 warps; each warp walks 32 columns
+// and lane l owns rows 4l..4l+3 (vector loads along the contiguous row index).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta, int64_t ld_in,
                                                const float* __restrict__ th_hi,
                                                const float* __restrict__ th_lo, float lam_hi,
                                                float lam_lo, int n, int ld, int ntm, int en,
-                                               const __nv_bfloat16* __restrict__ Dcat,
+                                               int nsl, const __half* __restrict__ Dcat,
                                                float* __restrict__ Ahi1, float* __restrict__ Alo1,
-                                               __nv_bfloat16* __restrict__ dt0,
+                                               __half* __restrict__ dt0,
                                                float* __restrict__ L, double* __restrict__ d,
                                                float* __restrict__ part,
                                                float* __restrict__ rowpart, IterState* st) {
@@ -116,6 +257,7 @@ __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta,
   const int n0 = blockIdx.x * IT0, m0 = blockIdx.y * IT0, tm = blockIdx.y;
   const int r0 = 4 * lane, j0 = m0 + r0;
   const int64_t cat_ld = (int64_t)NSLICE * ld;
+  const float qs = exp2i(st->sexp[0]), iqs = exp2i(-st->sexp[0]);
   const float4 thj_h = *reinterpret_cast<const float4*>(th_hi + j0);
   const float4 thj_l = *reinterpret_cast<const float4*>(th_lo + j0);
   float rowabs[4] = {0.f, 0.f, 0.f, 0.f};
@@ -124,61 +266,72 @@ __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta,
     const int i = n0 + 32 * w + c;
     if (i >= n) break;   // uniform across the warp
     const float thi_h = th_hi[i], thi_l = th_lo[i];
-    const __nv_bfloat16* Drow = Dcat + (int64_t)i * cat_ld + j0;
+    const __half* Drow = Dcat + (int64_t)i * cat_ld + j0;
     uint2 D[3];
 #pragma unroll
-    for (int sl = 0; sl < 3; ++sl) D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
-    float4 oh, oL;
-    uint32_t ob[4];
-    float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
+    for (int sl = 0; sl < 3; ++sl)
+      D[sl] = sl < nsl ? *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld) : make_uint2(0u, 0u);
+    // first pass: R_0 and the scaled quotient of the four rows
+    float R0h[4], R0l[4], gh[4], gl[4], q[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int j = j0 + e;
-      float nh = 0.f, Ln = 0.f, dtn = 0.f;
+      R0h[e] = R0l[e] = gh[e] = gl[e] = q[e] = 0.f;
       if (j < n) {
         const double v = delta[(int64_t)i * ld_in + j];
         float vh, vl;
         split_double_fast(v, vh, vl);   // |v| < 2^128: checked by the slicing
         rowabs[e] += fabsf(vh);
         if (j == i) {
-          nh = 1.f;
-          a2 += 1.f;
           d[i] = en ? 0.0 : v;
         } else {
           // R_0 = lambda * Delta_ji as float-float
           float pr, pe;
           two_prod(lam_hi, vh, pr, pe);
           pe = fmaf(lam_hi, vl, fmaf(lam_lo, vh, pe));
-          float R0h, R0l;
-          fast_two_sum(pr, pe, R0h, R0l);
-          float gh, gl;
-          ff_sub(thi_h, thi_l, f4(thj_h, e), f4(thj_l, e), gh, gl);
-          dtn = bf16_round(R0h * __frcp_rn(gh));
-          // L_1 = R_0 - Gap * dt_0; R0h - q is exact (q is R0h to BF16 accuracy)
-          float q, qe;
-          two_prod(gh, dtn, q, qe);
-          qe = fmaf(gl, dtn, qe);
-          Ln = (R0h - q) + (R0l - qe);
-          nh = dtn;
-          r2 = fmaf(R0h, R0h, r2);
-          const float p1 = bf_at(D[0], e) * dtn;
-          const float p23 = fmaf(bf_at(D[1], e), dtn, bf_at(D[2], e) * dtn);
-          float sh, se;
-          two_sum(eh, p1, sh, se);
-          se += el + p23;
-          fast_two_sum(sh, se, eh, el);
-          mx = fmaxf(mx, fabsf(dtn));
+          fast_two_sum(pr, pe, R0h[e], R0l[e]);
+          ff_sub(thi_h, thi_l, f4(thj_h, e), f4(thj_l, e), gh[e], gl[e]);
+          q[e] = R0h[e] * __frcp_rn(gh[e]) * qs;
         }
+      }
+    }
+    const uint32_t ob01 = f16x2_sat(q[0], q[1]), ob23 = f16x2_sat(q[2], q[3]);
+    const uint2 ob = make_uint2(ob01, ob23);
+    float4 oh, oL;
+    float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = j0 + e;
+      float nh = 0.f, Ln = 0.f;
+      if (j == i) {
+        nh = 1.f;
+        a2 += 1.f;
+      } else if (j < n) {
+        const float dtn = h_at(ob, e) * iqs;
+        // L_1 = R_0 - Gap * dt_0; R0h - p is exact (p is R0h to FP16 accuracy)
+        float pp, pq;
+        two_prod(gh[e], dtn, pp, pq);
+        pq = fmaf(gl[e], dtn, pq);
+        Ln = (R0h[e] - pp) + (R0l[e] - pq);
+        nh = dtn;
+        r2 = fmaf(R0h[e], R0h[e], r2);
+        const float p1 = h_at(D[0], e) * dtn;
+        const float p23 = fmaf(h_at(D[1], e), dtn, h_at(D[2], e) * dtn);
+        float sh, se;
+        two_sum(eh, p1, sh, se);
+        se += el + p23;
+        fast_two_sum(sh, se, eh, el);
+        mx = fmaxf(mx, fabsf(dtn));
       }
       f4set(oh, e, nh);
       f4set(oL, e, Ln);
-      ob[e] = bf_bits(dtn);
     }
     const int64_t idx = (int64_t)i * ld + j0;
     st4(Ahi1 + idx, oh);
     st4(Alo1 + idx, make_float4(0.f, 0.f, 0.f, 0.f));
     st4(L + idx, oL);
-    *reinterpret_cast<uint2*>(dt0 + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+    // rows beyond n and the diagonal hold zero increments (q = 0 there)
+    *reinterpret_cast<uint2*>(dt0 + idx) = ob;
     warp_sum_ff(r2, a2, eh, el);
     if (lane == 0) {
       part[((int64_t)0 * ntm + tm) * ld + i] = r2;
@@ -193,7 +346,7 @@ __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta,
   const int r = threadIdx.x;
   if (m0 + r < n)
     rowpart[(int64_t)blockIdx.x * ld + m0 + r] = ((rows[0][r] + rows[1][r]) + rows[2][r]) + rows[3][r];
-  // the slice count of the first product depends on the size of dt_0
+  // the slice count and scale of the first product depend on the size of dt_0
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0 && mx > 0.f) atomicMax(&st->dmax_bits, __float_as_uint(mx));
 }
@@ -222,6 +375,8 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
   // after a certifying product only its residual norms are valid: the iterate, d and
   // the column parameters of the next product stay as they are
   const bool cert = st->certify != 0;
+  // the diagonal partials are of Delta 2^sig dt (FP16 slices): exact rescaling
+  const double isg = (double)exp2i(-st->sig);
   {
     float r2 = 0.f, a2 = 0.f, rs = 0.f;
     double ep = 0.0;
@@ -245,6 +400,7 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
     double ep = 0.0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) { r2 += sh[0][q][c]; a2 += sh[1][q][c]; ep += she[q][c]; }
+    ep *= isg;
     rho_raw = sqrtf(r2 / a2);
     if (!(rho_raw == rho_raw) || isinf(rho_raw)) rho_raw = __int_as_float(0x7f800000);
     const double dk = d[i];
@@ -285,6 +441,8 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
   vs->rho_bits = 0;
   const float dmax = __uint_as_float(vs->dmax_bits);
   vs->dmax_bits = 0;
+  // the rounding of the float recursion grows with the residuals it carried
+  if (!first) vs->rho_sum = vs->rho_sum + rho;
   if (cert) {
     // the certifying pass assessed A_k: stop if it passed, else run the same
     // iteration again in full (nothing it depends on was touched)
@@ -295,9 +453,14 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
   const double prev = vs->rho_last;
   vs->rho_last = rho;
   if (!decide(vs, rho)) return;
-  const int S = next_slices(vs, dmax, first);
+  const int S = next_slices_f16(vs, dmax, first, vs->max_slices);
   vs->slices = S;
   vs->slice_gemms = vs->slice_gemms + S;
+  // the next product writes dt_k into buffer cur: scaled so that the largest
+  // increment of the last step, dmax, would land at 2^10 (increments shrink as the
+  // iteration converges; 32-fold growth still fits, more is clamped and the
+  // remainder keeps the rest)
+  vs->sexp[vs->cur] = dt_scale_exp((double)dmax, 10, vs->sig, vs->lam);
   // When the residual falls geometrically and the next one is predicted below half
   // the tolerance, the next product only forms the residual of its iterate (no new
   // iterate, increment or remainder is written): the last product of a converging
@@ -355,10 +518,13 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
   const float* __restrict__ Alc = c1 ? p.A_lo[1] : p.A_lo[0];
   float* __restrict__ Ahn = c1 ? p.A_hi[0] : p.A_hi[1];
   float* __restrict__ Aln = c1 ? p.A_lo[0] : p.A_lo[1];
-  const __nv_bfloat16* __restrict__ dtp = c1 ? p.dt[0] : p.dt[1];   // dt_{k-1}
-  __nv_bfloat16* __restrict__ dtn_out = c1 ? p.dt[1] : p.dt[0];     // dt_k
+  const __half* __restrict__ dtp = c1 ? p.dt[0] : p.dt[1];   // dt_{k-1} 2^scur
+  __half* __restrict__ dtn_out = c1 ? p.dt[1] : p.dt[0];     // dt_k 2^snew
   float* __restrict__ L = p.L;
-  const float lam = p.lam;
+  // the accumulator holds 2^(sig + scur) Delta dt_{k-1}: lambda carries the inverse
+  // scale and the per-column parameters the matching ones (all exact)
+  const float lam = (p.lam * exp2i(-ms->sig)) * exp2i(-ms->scur);
+  const float qs = exp2i(ms->snew), iqs = exp2i(-ms->snew);
   const int r0 = 4 * lane;                // rows r0..r0+3 of the tile
   const int j0 = m0 + r0;
   // rows beyond n lie in the padded part of every work array (ld is a multiple of
@@ -378,10 +544,10 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
         in[u].al = cert ? make_float4(0.f, 0.f, 0.f, 0.f) : ld4(Alc + idx);
         in[u].L = ld4(L + idx);
         in[u].dtp = *reinterpret_cast<const uint2*>(dtp + idx);
-        // Delta_ij for j = j0..j0+3: row i of the row-major slices.  The diagonal
-        // partial uses as many slices as this product: its truncation error then
-        // obeys the same bound as the product's (see next_slices)
-        const __nv_bfloat16* Drow = p.Dcat + (int64_t)i * p.cat_ld + j0;
+        // Delta_ij 2^sig for j = j0..j0+3: row i of the row-major slices.  The
+        // diagonal partial uses as many slices as this product: its truncation error
+        // then obeys the same bound as the product's (see next_slices_f16)
+        const __half* Drow = p.Dcat + (int64_t)i * p.cat_ld + j0;
         const int Se = cert ? 0 : S;
         in[u].D[0] = Se > 0 ? *reinterpret_cast<const uint2*>(Drow) : make_uint2(0u, 0u);
         in[u].D[1] = Se > 1 ? *reinterpret_cast<const uint2*>(Drow + ld) : make_uint2(0u, 0u);
@@ -397,49 +563,64 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
       const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
       const float thh = ms->thh[cl], thl = ms->thl[cl];
       float4 oh, ol, oL;
-      uint32_t ob[4];
       float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
+      uint2 ob;
+      // two rows at a time: the residual and the scaled quotient R / Gap, one packed
+      // FP16 conversion (the increment as applied, so the remainder below keeps
+      // R - Gap dt exactly whatever the rounding or clamping did), then the rest
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int j = j0 + e;
-        const float ah = f4(in[u].ah, e), al = f4(in[u].al, e);
-        float nh = 0.f, nl = 0.f, Ln = 0.f, dnew = 0.f;
-        if (j == i) {
-          nh = 1.f;
-          a2 += 1.f;
-        } else if (j < n) {
-          const float R = f4(in[u].L, e) +
-                          lam * (f4(x4, e) - ah * e_i - bf_at(in[u].dtp, e) * dp_i);
-          r2 = fmaf(R, R, r2);
-          a2 = fmaf(ah, ah, a2);
-          if (!cert) {
-            float gh, gl;
-            ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
-            dnew = bf16_round(R * __frcp_rn(gh));
-            Ln = fmaf(-gh, dnew, R) - gl * dnew;
+      for (int hp = 0; hp < 2; ++hp) {
+        float R[2], gh[2], gl[2], q[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int e = 2 * hp + t, j = j0 + e;
+          R[t] = gh[t] = gl[t] = q[t] = 0.f;
+          if (j != i && j < n) {
+            const float ah = f4(in[u].ah, e);
+            R[t] = f4(in[u].L, e) + lam * (f4(x4, e) - ah * e_i - h_at(in[u].dtp, e) * dp_i);
+            r2 = fmaf(R[t], R[t], r2);
+            a2 = fmaf(ah, ah, a2);
+            if (!cert) {
+              ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh[t], gl[t]);
+              q[t] = R[t] * __frcp_rn(gh[t]) * qs;
+            }
+          }
+        }
+        const uint32_t w = f16x2_sat(q[0], q[1]);
+        if (hp == 0) ob.x = w; else ob.y = w;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int e = 2 * hp + t, j = j0 + e;
+          const float ah = f4(in[u].ah, e), al = f4(in[u].al, e);
+          float nh = 0.f, nl = 0.f, Ln = 0.f;
+          if (j == i) {
+            nh = 1.f;
+            a2 += 1.f;
+          } else if (j < n && !cert) {
+            const float dnew = h_at(ob, e) * iqs;
+            Ln = fmaf(-gh[t], dnew, R[t]) - gl[t] * dnew;
             ff_add_f(ah, al, dnew, nh, nl);
-            // e_{k+1} partial Delta_ij dt_ji: the slice products are exact (8-bit
-            // significands), summed in float-float
-            const float p1 = bf_at(in[u].D[0], e) * dnew;
-            const float p23 = fmaf(bf_at(in[u].D[1], e), dnew, bf_at(in[u].D[2], e) * dnew);
+            // e_{k+1} 2^sig partial Delta_ij 2^sig dt_ji: the slice products are
+            // exact (11-bit significands), summed in float-float
+            const float p1 = h_at(in[u].D[0], e) * dnew;
+            const float p23 = fmaf(h_at(in[u].D[1], e), dnew, h_at(in[u].D[2], e) * dnew);
             float sh, se;
             two_sum(eh, p1, sh, se);
             se += el + p23;
             fast_two_sum(sh, se, eh, el);
             mx = fmaxf(mx, fabsf(dnew));
           }
+          f4set(oh, e, nh);
+          f4set(ol, e, nl);
+          f4set(oL, e, Ln);
         }
-        f4set(oh, e, nh);
-        f4set(ol, e, nl);
-        f4set(oL, e, Ln);
-        ob[e] = bf_bits(dnew);
       }
       const int64_t idx = (int64_t)i * ld + j0;
       if (!cert) {
         st4(Ahn + idx, oh);
         st4(Aln + idx, ol);
         st4(L + idx, oL);
-        *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+        *reinterpret_cast<uint2*>(dtn_out + idx) = ob;
       }
       warp_sum_ff(r2, a2, eh, el);
       if (lane == 0) {
@@ -475,6 +656,9 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     ms->slices = st->slices;
     ms->certify = st->certify;
     ms->cur = st->cur;
+    ms->sig = st->sig;
+    ms->scur = st->sexp[st->cur ^ 1];
+    ms->snew = st->sexp[st->cur];
     for (int s = 0; s < STAGES; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], 1); }
     for (int b = 0; b < NACC; ++b) { mbar_init(&ms->acc_full[b], 1); mbar_init(&ms->acc_empty[b], 1); }
     fence_mbar_init();
@@ -525,7 +709,7 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       mbar_wait(&ms->full[t % STAGES], (t / STAGES) & 1, tflag);
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ----
-    const uint32_t idesc = idesc_bf16_f32(BM, bn);
+    const uint32_t idesc = idesc_f16_f32(BM, bn);
     uint32_t it = 0;
     int lt = 0;   // local tile counter
     bool alive = true;
@@ -558,6 +742,7 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     const int qd = warp & 3;        // TMEM lane quadrant of this warp
     const int half = ew >> 2;       // which 16 of a chunk's 32 columns this warp copies
     const int et = threadIdx.x - 64;
+    const float cs = exp2i(ms->scur), cd = exp2i(ms->sig);
     float mx = 0.f;
     int lt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
@@ -569,8 +754,8 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
       if (et < bn) {
         const int i = n0 + et;
         const bool v = i < p.n;
-        ms->e[et] = v ? p.e_col[i] : 0.f;
-        ms->dprev[et] = v ? p.dprev_col[i] : 0.f;
+        ms->e[et] = v ? (p.e_col[i] * cd) * cs : 0.f;   // e_k 2^sig 2^scur
+        ms->dprev[et] = v ? p.dprev_col[i] * cd : 0.f;
         ms->thh[et] = v ? p.th_hi[i] : 0.f;
         ms->thl[et] = v ? p.th_lo[i] : 0.f;
       }
@@ -616,7 +801,7 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 // the previous sub-chunk (and, for a tile's first sub-chunk, the wait for its
 // accumulator).  A sub-chunk is 16 columns, one per warp.  Each lane keeps its own
 // slots (80 B per column: A_hi, A_lo, L as float4, then dt_{k-1} and the Delta
-// slices as BF16 quadruples), so no barrier guards them.
+// slices as FP16 quadruples), so no barrier guards them.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint8_t* eb_f4(uint8_t* eb, int ew, int u, int f, int lane) {
   return eb + ((ew + u) * 3 + f) * 512 + lane * 16;
@@ -647,7 +832,7 @@ __device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, bo
                                              int sc) {
   const float* Ahc = c1 ? p.A_hi[1] : p.A_hi[0];
   const float* Alc = c1 ? p.A_lo[1] : p.A_lo[0];
-  const __nv_bfloat16* dtp = c1 ? p.dt[0] : p.dt[1];
+  const __half* dtp = c1 ? p.dt[0] : p.dt[1];
   const int j0 = m0 + 4 * lane;
 #pragma unroll
   for (int u = 0; u < 1; ++u) {
@@ -659,7 +844,7 @@ __device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, bo
     cp_async16(eb_f4(eb, ew, u, 2, lane), p.L + idx);
     cp_async8(eb_u2(eb, ew, u, 0, lane), dtp + idx);
     if (cert) continue;
-    const __nv_bfloat16* Drow = p.Dcat + (int64_t)i * p.cat_ld + j0;
+    const __half* Drow = p.Dcat + (int64_t)i * p.cat_ld + j0;
     for (int sl = 0; sl < S; ++sl)
       cp_async8(eb_u2(eb, ew, u, 1 + sl, lane), Drow + (int64_t)sl * p.ld);
   }
@@ -675,9 +860,11 @@ __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc
   const bool cert = ms->certify != 0;     // residual norms only, nothing written
   float* __restrict__ Ahn = c1 ? p.A_hi[0] : p.A_hi[1];
   float* __restrict__ Aln = c1 ? p.A_lo[0] : p.A_lo[1];
-  __nv_bfloat16* __restrict__ dtn_out = c1 ? p.dt[1] : p.dt[0];
+  __half* __restrict__ dtn_out = c1 ? p.dt[1] : p.dt[0];
   float* __restrict__ L = p.L;
-  const float lam = p.lam;
+  // scales as in epilogue_columns
+  const float lam = (p.lam * exp2i(-ms->sig)) * exp2i(-ms->scur);
+  const float qs = exp2i(ms->snew), iqs = exp2i(-ms->snew);
   const int r0 = 4 * lane;
   const int j0 = m0 + r0;
   const float4 thj_h = ld4(p.th_hi + j0);
@@ -703,48 +890,63 @@ __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc
     const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
     const float thh = ms->thh[cl], thl = ms->thl[cl];
     float4 oh, ol, oL;
-    uint32_t ob[4];
     float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
+    uint2 ob;
+    // two rows at a time: their residuals and scaled quotients R / Gap, one packed
+    // FP16 conversion, then the rest of the update with the increments as applied
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int j = j0 + e;
-      const float ah = f4(ah4, e), al = f4(al4, e);
-      float nh = 0.f, nl = 0.f, Ln = 0.f, dnew = 0.f;
-      if (j == i) {
-        nh = 1.f;
-        a2 += 1.f;
-      } else if (j < n) {
-        const float R = f4(L4, e) + lam * (f4(x4, e) - ah * e_i - bf_at(dtp, e) * dp_i);
-        r2 = fmaf(R, R, r2);
-        a2 = fmaf(ah, ah, a2);
-        if (!cert) {
-          float gh, gl;
-          ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
-          // the increment is rounded to BF16 and the remainder keeps R - Gap dnew
-          // exactly, so any reciprocal close to 1/gap serves
-          dnew = bf16_round(R * rcp_approx(gh));
-          Ln = fmaf(-gh, dnew, R) - gl * dnew;
+    for (int hp = 0; hp < 2; ++hp) {
+      float R[2], gh[2], gl[2], q[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int e = 2 * hp + t, j = j0 + e;
+        R[t] = gh[t] = gl[t] = q[t] = 0.f;
+        if (j != i && j < n) {
+          const float ah = f4(ah4, e);
+          R[t] = f4(L4, e) + lam * (f4(x4, e) - ah * e_i - h_at(dtp, e) * dp_i);
+          r2 = fmaf(R[t], R[t], r2);
+          a2 = fmaf(ah, ah, a2);
+          if (!cert) {
+            ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh[t], gl[t]);
+            // the increment is rounded to FP16 and the remainder keeps R - Gap dnew
+            // exactly, so any reciprocal close to 1/gap serves
+            q[t] = R[t] * rcp_approx(gh[t]) * qs;
+          }
+        }
+      }
+      const uint32_t w = f16x2_sat(q[0], q[1]);
+      if (hp == 0) ob.x = w; else ob.y = w;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int e = 2 * hp + t, j = j0 + e;
+        const float ah = f4(ah4, e), al = f4(al4, e);
+        float nh = 0.f, nl = 0.f, Ln = 0.f;
+        if (j == i) {
+          nh = 1.f;
+          a2 += 1.f;
+        } else if (j < n && !cert) {
+          const float dnew = h_at(ob, e) * iqs;
+          Ln = fmaf(-gh[t], dnew, R[t]) - gl[t] * dnew;
           ff_add_f(ah, al, dnew, nh, nl);
-          const float p1 = bf_at(D[0], e) * dnew;
-          const float p23 = fmaf(bf_at(D[1], e), dnew, bf_at(D[2], e) * dnew);
+          const float p1 = h_at(D[0], e) * dnew;
+          const float p23 = fmaf(h_at(D[1], e), dnew, h_at(D[2], e) * dnew);
           float sh, se;
           two_sum(eh, p1, sh, se);
           se += el + p23;
           fast_two_sum(sh, se, eh, el);
           mx = fmaxf(mx, fabsf(dnew));
         }
+        f4set(oh, e, nh);
+        f4set(ol, e, nl);
+        f4set(oL, e, Ln);
       }
-      f4set(oh, e, nh);
-      f4set(ol, e, nl);
-      f4set(oL, e, Ln);
-      ob[e] = bf_bits(dnew);
     }
     const int64_t idx = (int64_t)i * ld + j0;
     if (!cert) {
       st4(Ahn + idx, oh);
       st4(Aln + idx, ol);
       st4(L + idx, oL);
-      *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
+      *reinterpret_cast<uint2*>(dtn_out + idx) = ob;
     }
     warp_sum_ff(r2, a2, eh, el);
     if (lane == 0) {
@@ -800,6 +1002,9 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     ms->slices = st->slices;
     ms->certify = st->certify;
     ms->cur = st->cur;
+    ms->sig = st->sig;
+    ms->scur = st->sexp[st->cur ^ 1];
+    ms->snew = st->sexp[st->cur];
     for (int s = 0; s < MAX_STAGES; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], 1); }
     for (int b = 0; b < NACC; ++b) { mbar_init(&ms->acc_full[b], 1); mbar_init(&ms->acc_empty[b], 2); }
     fence_mbar_init();
@@ -850,7 +1055,7 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       mbar_wait_quiet(&ms->empty[u % nst], (u / nst) & 1, kTailWaitNs);
   } else if (warp == 1 && lane == 0 && rank == 0) {
     // ---- MMA issuer (leader only) ----
-    const uint32_t idesc = idesc_bf16_f32(2 * BM, bn);
+    const uint32_t idesc = idesc_f16_f32(2 * BM, bn);
     uint32_t it = 0;
     int lt = 0;
     bool alive = true;
@@ -890,6 +1095,7 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const bool c1 = (ms->cur != 0);
     const bool cert = ms->certify != 0;
     const int nsub = bn / 16;              // sub-chunks per tile (even: bn is a multiple of 32)
+    const float cs = exp2i(ms->scur), cd = exp2i(ms->sig);
     float mx = 0.f;
     int lt = 0;
     // the first tile's first sub-chunk, while its products run
@@ -909,8 +1115,8 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       if (et < bn) {
         const int i = n0 + et;
         const bool v = i < p.n;
-        ms->e[et] = v ? p.e_col[i] : 0.f;
-        ms->dprev[et] = v ? p.dprev_col[i] : 0.f;
+        ms->e[et] = v ? (p.e_col[i] * cd) * cs : 0.f;   // e_k 2^sig 2^scur
+        ms->dprev[et] = v ? p.dprev_col[i] * cd : 0.f;
         ms->thh[et] = v ? p.th_hi[i] : 0.f;
         ms->thl[et] = v ? p.th_lo[i] : 0.f;
       }
@@ -1080,10 +1286,23 @@ int mixed_tile_n(int n, int nsm) {
   return best;
 }
 
-cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en,
-                              __nv_bfloat16* Dcat, IterState* st, cudaStream_t s) {
+cudaError_t launch_delta_scales(const double* delta, int64_t ld_in, int n, const float* th_hi,
+                                const float* th_lo, double lam, int en, IterState* st,
+                                cudaStream_t s) {
+  (void)lam;   // read from the state
+  k_delta_scales<<<n, 256, 0, s>>>(delta, ld_in, n, th_hi, th_lo, en, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en, int nsl,
+                              __half* Dcat, IterState* st, cudaStream_t s) {
   dim3 grid(ld / 64, (n + 31) / 32), block(32, 8);     // ld is a multiple of 128
-  k_prep_delta<<<grid, block, 0, s>>>(delta, ld_in, n, ld, en, Dcat, st);
+  switch (nsl) {
+    case 1: k_prep_delta<1><<<grid, block, 0, s>>>(delta, ld_in, n, ld, en, Dcat, st); break;
+    case 2: k_prep_delta<2><<<grid, block, 0, s>>>(delta, ld_in, n, ld, en, Dcat, st); break;
+    case 3: k_prep_delta<3><<<grid, block, 0, s>>>(delta, ld_in, n, ld, en, Dcat, st); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -1098,15 +1317,16 @@ cudaError_t launch_theta_ff(int n, const double* th, float* hi, float* lo, cudaS
 }
 
 cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
-                         const float* th_lo, double lam, int n, int ld, int en,
-                         const __nv_bfloat16* Dcat, float* Ahi1, float* Alo1,
-                         __nv_bfloat16* dt0, float* L, double* d, float* part, float* rowpart,
+                         const float* th_lo, double lam, int n, int ld, int en, int nsl,
+                         const __half* Dcat, float* Ahi1, float* Alo1,
+                         __half* dt0, float* L, double* d, float* part, float* rowpart,
                          IterState* st, cudaStream_t s) {
+  if (nsl < 1 || nsl > NSLICE) return cudaErrorInvalidValue;
   const int ntm = (n + IT0 - 1) / IT0, ntn = (n + IT0 - 1) / IT0;
   const float lh = (float)lam;
   const float ll = (float)(lam - (double)lh);
   k_iter0<<<dim3(ntn, ntm), 128, 0, s>>>(delta, ld_in, th_hi, th_lo, lh, ll, n, ld, ntm, en,
-                                         Dcat, Ahi1, Alo1, dt0, L, d, part, rowpart, st);
+                                         nsl, Dcat, Ahi1, Alo1, dt0, L, d, part, rowpart, st);
   return cudaGetLastError();
 }
 

@@ -3,6 +3,7 @@
 
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -53,6 +54,13 @@ struct IterState {
   double lam_k;        // strength the next map application uses (FP64 path)
   int certify;         // mixed single solve: the next product only assesses its iterate
   int certify_on;      // whether such passes may be scheduled (dpt_options::certify)
+  // mixed single solve: Delta and the increments are FP16 tensor-core operands with
+  // power-of-two scales (their range is that of FP16, their scale free)
+  unsigned amax_bits;  // atomicMax scratch: high word of max |Delta_jk| (FP64 bits)
+  unsigned g0max_bits; // atomicMax scratch: max_{j != i} |Delta_ji| / |theta_i - theta_j|
+  int sig;             // the FP16 slices hold Delta * 2^sig
+  int sexp[2];         // increment buffer q holds dt * 2^sexp[q] in FP16
+  double rho_sum;      // sum of the residuals rho_k, k >= 1, the float recursion carried
 };
 
 // State of a dominant-eigenvector solve (single-vector map), device resident.
@@ -153,9 +161,9 @@ struct GemmEpiParams {
   float lam;
   float* A_hi[2];      // float-float iterate, column-major, ping-pong by iteration parity
   float* A_lo[2];
-  __nv_bfloat16* dt[2];   // BF16 increments, column-major (GEMM B operand), ping-pong
+  __half* dt[2];       // FP16 increments (scaled by 2^sexp), column-major (GEMM B operand), ping-pong
   float* L;            // carried remainder, column-major
-  const __nv_bfloat16* Dcat;   // Delta as 3 BF16 slices, row-major, slices side by side
+  const __half* Dcat;  // Delta * 2^sig as up to 3 FP16 slices, row-major, slices side by side
   int64_t cat_ld;      // row pitch of Dcat (3 * ld)
   const float* th_hi;  // theta as float-float
   const float* th_lo;
@@ -173,15 +181,21 @@ cudaError_t launch_gemm_epi_pair(const CUtensorMap& tmA, const CUtensorMap& tmB0
                                  const CUtensorMap& tmB1, const GemmEpiParams& p, int npairs,
                                  cudaStream_t s);
 cudaError_t mixed_set_attributes();   // once per device, before any capture
-cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en,
-                              __nv_bfloat16* Dcat, IterState* st, cudaStream_t s);
+// max |Delta| and max |Delta_ji / (theta_i - theta_j)| (j != i); sets the scales of
+// the FP16 slices and of the first increment (IterState::sig, sexp[0])
+cudaError_t launch_delta_scales(const double* delta, int64_t ld_in, int n, const float* th_hi,
+                                const float* th_lo, double lam, int en, IterState* st,
+                                cudaStream_t s);
+// nsl FP16 slices of Delta * 2^sig (needs launch_delta_scales first)
+cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en, int nsl,
+                              __half* Dcat, IterState* st, cudaStream_t s);
 cudaError_t launch_theta_ff(int n, const double* th, float* hi, float* lo, cudaStream_t s);
 // finite and pairwise distinct theta (status ST_BADINPUT / ST_DEGENERATE), max |theta|
 cudaError_t launch_check_theta(int n, const double* th, IterState* st, cudaStream_t s);
 cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
-                         const float* th_lo, double lam, int n, int ld, int en,
-                         const __nv_bfloat16* Dcat, float* Ahi1, float* Alo1,
-                         __nv_bfloat16* dt0, float* L, double* d, float* part, float* rowpart,
+                         const float* th_lo, double lam, int n, int ld, int en, int nsl,
+                         const __half* Dcat, float* Ahi1, float* Alo1,
+                         __half* dt0, float* L, double* d, float* part, float* rowpart,
                          IterState* st, cudaStream_t s);
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,

@@ -43,7 +43,7 @@ class Info(ctypes.Structure):
                 ("nstar", ctypes.c_int32), ("seconds", ctypes.c_double),
                 ("launches", ctypes.c_int32), ("product_launches", ctypes.c_int32),
                 ("product_ms", ctypes.c_double), ("cta_pair", ctypes.c_int32),
-                ("grouped_form", ctypes.c_int32)]
+                ("grouped_form", ctypes.c_int32), ("fp64_iters", ctypes.c_int32)]
 
     def as_dict(self):
         return {"iters": self.iters, "slice_gemms": self.slice_gemms,
@@ -51,7 +51,7 @@ class Info(ctypes.Structure):
                 "code": self.status, "nstar": self.nstar, "seconds": self.seconds,
                 "launches": self.launches, "product_launches": self.product_launches,
                 "product_ms": self.product_ms, "cta_pair": self.cta_pair,
-                "grouped_form": self.grouped_form}
+                "grouped_form": self.grouped_form, "fp64_iters": self.fp64_iters}
 
 
 class ServerCfg(ctypes.Structure):

@@ -45,12 +45,14 @@ def test_batched_matches_single_solves(dpt):
     probs = inputs.batched_symmetric(count=24, rep=3)
     th, D = _dev(probs, dpt)
     As, Es, infos = dpt.solve_batched(th, D, [p["lam"] for p in probs])
-    # the grouped kernel picks its own tile width per problem, so the order of the
-    # FP32 accumulation differs from the single-problem kernel: agreement is to the
-    # parity bar, not bit for bit
+    # the grouped kernel picks its own tile width per problem and takes BF16 slices
+    # where the single-problem kernel takes FP16 ones, so the rounding differs: the
+    # agreement is to the parity bar, not bit for bit, and the iteration counts of the
+    # mixed recursions (a strongly coupled single solve may add plain FP64 steps)
+    # agree to one step
     for q in (0, 7, 23):
         A1, E1, i1 = dpt.solve_full(th[q], D[q], probs[q]["lam"])
-        assert abs(i1["iters"] - infos[q]["iters"]) <= 1
+        assert abs((i1["iters"] - i1["fp64_iters"]) - infos[q]["iters"]) <= 1
         assert eig_err(to_np(Es[q]), to_np(E1)) <= EIG_RTOL
         assert vec_err(to_np(As[q]), to_np(A1)) <= VEC_TOL
 

@@ -1,0 +1,70 @@
+"""The FP16 operands of the single mixed solve and the FP64 finish of strongly coupled
+solves (through the C ABI).
+
+Delta enters the tensor cores as FP16 slices of Delta 2^sig and each increment as
+FP16 with its own power-of-two scale.  Replacing (Delta, lambda) by
+(2^p Delta, 2^-p lambda) leaves M = diag(theta) + lambda Delta unchanged (Sec. II.B)
+and shifts every scale by an exact power of two, so the solve must return the same
+bits, far outside FP16's own range (|p| up to 60).  A problem whose float recursion
+carried large residuals (the 2 x 2 of Sec. II.E at lambda = 0.3) is finished by the
+plain FP64 map; a weakly coupled one is not."""
+import numpy as np
+import pytest
+
+from gpu_util import EIG_RTOL, VEC_TOL, eig_err, to_np, vec_err
+from paper_2002_12872_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dpt():
+    from paper_2002_12872_gb300 import build, dpt
+    build.build()
+    assert torch.cuda.is_available()
+    return dpt
+
+
+@pytest.mark.parametrize("p", [-60, -20, 24, 60])
+@pytest.mark.parametrize("pair", [True, False])
+def test_power_of_two_rescaling_is_exact(dpt, p, pair):
+    cfg = inputs.full_unsymmetric(n=300)
+    th = torch.tensor(cfg["theta"], device="cuda")
+    D = dpt.colmajor_tensor(cfg["delta"], "cuda")
+    A0, E0, i0 = dpt.solve_full(th, D, cfg["lam"], cta_pair=pair)
+    Ds = dpt.colmajor_tensor(np.ldexp(cfg["delta"], p), "cuda")
+    A1, E1, i1 = dpt.solve_full(th, Ds, np.ldexp(cfg["lam"], -p), cta_pair=pair)
+    assert i0["status"] == "OK" and i1["status"] == "OK"
+    assert i1["iters"] == i0["iters"] and i1["slice_gemms"] == i0["slice_gemms"]
+    assert torch.equal(A0, A1) and torch.equal(E0, E1)
+
+
+def test_weakly_coupled_solve_needs_no_fp64_finish(ora, dpt):
+    cfg = inputs.full_unsymmetric(n=513)
+    th = torch.tensor(cfg["theta"], device="cuda")
+    D = dpt.colmajor_tensor(cfg["delta"], "cuda")
+    A, E, info = dpt.solve_full(th, D, cfg["lam"])
+    assert info["status"] == "OK" and info["fp64_iters"] == 0
+    # two FP16 slices for the first product, one once the increments are small
+    assert info["slice_gemms"] <= 2 * info["iters"]
+    Ao, Eo, io = ora.solve_full(cfg["theta"], cfg["delta"], cfg["lam"], tol=1e-13,
+                                cols=np.array([0, 256, 512]))
+    assert eig_err(to_np(E)[[0, 256, 512]], Eo) <= EIG_RTOL
+    assert vec_err(to_np(A)[:, [0, 256, 512]], Ao) <= VEC_TOL
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_strongly_coupled_solve_is_finished_in_fp64(dpt, host):
+    lam = 0.3
+    th = np.array([0.0, 1.0])
+    D = np.array([[0.0, 1.0], [1.0, 0.0]], order="F")
+    if not host:
+        th, D = torch.tensor(th, device="cuda"), torch.tensor(D, device="cuda")
+    A, E, info = dpt.solve_full(th, D, lam)
+    assert info["status"] == "OK" and info["fp64_iters"] > 0
+    assert info["iters"] > info["fp64_iters"]
+    r = np.sqrt(1 + 4 * lam * lam)
+    E = to_np(E)
+    # the plain FP64 map's bar (its residual at tol 1e-12)
+    assert abs(E[0] - (1 - r) / 2) < 1e-12 and abs(E[1] - (1 + r) / 2) < 1e-12
