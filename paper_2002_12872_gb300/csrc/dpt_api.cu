@@ -372,8 +372,8 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     CK(launch_theta_ff(n, thd, thh, thl, s));
     CK(launch_delta_scales(delta, ldd, n, thh, thl, lambda, o.epstein_nesbet, st, s));
     CK(launch_prep_delta(delta, ldd, n, ld, o.epstein_nesbet, S, Dcat, st, s));
-    CK(launch_iter0(delta, ldd, thh, thl, lambda, n, ld, o.epstein_nesbet, S, Dcat, Ahi[1],
-                    Alo[1], dtb[0], L, d, part, rowpart, st, s));
+    CK(launch_iter0(delta, ldd, thh, thl, lambda, n, ld, o.epstein_nesbet, S, Dcat, dtb[0], L,
+                    d, part, rowpart, st, s));
     CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
 
     const CUtensorMap tA = make_tmap_bf16(Dcat, (uint64_t)3 * ld, n, (uint64_t)3 * ld, 128, true);
@@ -404,7 +404,8 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
       // the outputs are formed inside the chunk in which the iteration stops (the
       // output kernel does nothing while the state is still running)
       const std::function<void()> tail = [&]() {
-        CK(launch_finalize(n, ld, Ahi[0], Alo[0], Ahi[1], Alo[1], Astage, lda_dev, st, 1, s));
+        CK(launch_finalize(n, ld, Ahi[0], Alo[0], Ahi[1], Alo[1], dtb[0], Astage, lda_dev, st, 1,
+                           s));
         if (e_dev)
           CK(cudaMemcpyAsync(E_out, E, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       };

@@ -236,23 +236,25 @@ __global__ void __launch_bounds__(256) k_prep_delta(const double* __restrict__ d
 // Iteration 0 (A_0 = I), computed from the FP64 input in float-float:
 //   R_0 = lambda Delta (off the diagonal), d_0 = diag(Delta),
 //   dt_0 = f16(G o R_0) (stored scaled by 2^sexp[0]), L_1 = R_0 - Gap o dt_0,
-//   A_1 = I + dt_0,
 // plus the column partials of |R_0|^2, |a|^2 = 1, e_1 2^sig = diag(Delta 2^sig dt_0)
 // from the FP16 slices (float-float) and the row partials of sum_k |Delta_jk| for the
-// residual scale.  One block per 128 x 128 tile, 4 warps; each warp walks 32 columns
-// and lane l owns rows 4l..4l+3 (vector loads along the contiguous row index).
+// residual scale.  A_1 = I + dt_0 is not written: the first product and the output
+// kernel form it from dt_0.  One block per 128 x 128 tile, 8 warps; each warp walks
+// 16 columns with the next column's loads in flight, lane l owning rows 4l..4l+3
+// (vector loads along the contiguous row index).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta, int64_t ld_in,
+template <int NSL>
+__global__ void __launch_bounds__(256) k_iter0(const double* __restrict__ delta, int64_t ld_in,
                                                const float* __restrict__ th_hi,
                                                const float* __restrict__ th_lo, float lam_hi,
                                                float lam_lo, int n, int ld, int ntm, int en,
-                                               int nsl, const __half* __restrict__ Dcat,
-                                               float* __restrict__ Ahi1, float* __restrict__ Alo1,
+                                               const __half* __restrict__ Dcat,
                                                __half* __restrict__ dt0,
                                                float* __restrict__ L, double* __restrict__ d,
                                                float* __restrict__ part,
                                                float* __restrict__ rowpart, IterState* st) {
-  __shared__ float rows[4][IT0];
+  constexpr int W = 8, CPW = IT0 / W;   // warps, columns per warp
+  __shared__ float rows[W][IT0];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int n0 = blockIdx.x * IT0, m0 = blockIdx.y * IT0, tm = blockIdx.y;
   const int r0 = 4 * lane, j0 = m0 + r0;
@@ -260,17 +262,38 @@ __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta,
   const float qs = exp2i(st->sexp[0]), iqs = exp2i(-st->sexp[0]);
   const float4 thj_h = *reinterpret_cast<const float4*>(th_hi + j0);
   const float4 thj_l = *reinterpret_cast<const float4*>(th_lo + j0);
+  // 16-byte loads of the four rows where the column start allows them
+  const bool vec = (j0 + 3 < n) && ((((uintptr_t)delta) | ((uintptr_t)ld_in * 8u)) & 15u) == 0;
   float rowabs[4] = {0.f, 0.f, 0.f, 0.f};
   float mx = 0.f;
-  for (int c = 0; c < 32; ++c) {
-    const int i = n0 + 32 * w + c;
-    if (i >= n) break;   // uniform across the warp
-    const float thi_h = th_hi[i], thi_l = th_lo[i];
+  const int cb = n0 + CPW * w, ce = min(n, cb + CPW);
+  double vn[4] = {0.0, 0.0, 0.0, 0.0};
+  uint2 Dn[3] = {make_uint2(0u, 0u), make_uint2(0u, 0u), make_uint2(0u, 0u)};
+  auto fetch = [&](int i) {
+    const double* col = delta + (int64_t)i * ld_in + j0;
+    if (vec) {
+      const double2 x = *reinterpret_cast<const double2*>(col);
+      const double2 y = *reinterpret_cast<const double2*>(col + 2);
+      vn[0] = x.x; vn[1] = x.y; vn[2] = y.x; vn[3] = y.y;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) vn[e] = (j0 + e < n) ? col[e] : 0.0;
+    }
+    // Delta_ij (row i of the slices; columns j < ld are all written)
     const __half* Drow = Dcat + (int64_t)i * cat_ld + j0;
+#pragma unroll
+    for (int sl = 0; sl < NSL; ++sl) Dn[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+  };
+  if (cb < ce) fetch(cb);
+  for (int i = cb; i < ce; ++i) {   // uniform across the warp
+    double v[4];
     uint2 D[3];
 #pragma unroll
-    for (int sl = 0; sl < 3; ++sl)
-      D[sl] = sl < nsl ? *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld) : make_uint2(0u, 0u);
+    for (int e = 0; e < 4; ++e) v[e] = vn[e];
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) D[sl] = Dn[sl];
+    if (i + 1 < ce) fetch(i + 1);
+    const float thi_h = th_hi[i], thi_l = th_lo[i];
     // first pass: R_0 and the scaled quotient of the four rows
     float R0h[4], R0l[4], gh[4], gl[4], q[4];
 #pragma unroll
@@ -278,12 +301,11 @@ __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta,
       const int j = j0 + e;
       R0h[e] = R0l[e] = gh[e] = gl[e] = q[e] = 0.f;
       if (j < n) {
-        const double v = delta[(int64_t)i * ld_in + j];
         float vh, vl;
-        split_double_fast(v, vh, vl);   // |v| < 2^128: checked by the slicing
+        split_double_fast(v[e], vh, vl);   // |v| < 2^128: checked by the slicing
         rowabs[e] += fabsf(vh);
         if (j == i) {
-          d[i] = en ? 0.0 : v;
+          d[i] = en ? 0.0 : v[e];
         } else {
           // R_0 = lambda * Delta_ji as float-float
           float pr, pe;
@@ -291,20 +313,20 @@ __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta,
           pe = fmaf(lam_hi, vl, fmaf(lam_lo, vh, pe));
           fast_two_sum(pr, pe, R0h[e], R0l[e]);
           ff_sub(thi_h, thi_l, f4(thj_h, e), f4(thj_l, e), gh[e], gl[e]);
-          q[e] = R0h[e] * __frcp_rn(gh[e]) * qs;
+          // the remainder below keeps R_0 - Gap dt_0 exactly, so any reciprocal
+          // close to 1/gap serves
+          q[e] = R0h[e] * rcp_approx(gh[e]) * qs;
         }
       }
     }
-    const uint32_t ob01 = f16x2_sat(q[0], q[1]), ob23 = f16x2_sat(q[2], q[3]);
-    const uint2 ob = make_uint2(ob01, ob23);
-    float4 oh, oL;
+    const uint2 ob = make_uint2(f16x2_sat(q[0], q[1]), f16x2_sat(q[2], q[3]));
+    float4 oL;
     float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int j = j0 + e;
-      float nh = 0.f, Ln = 0.f;
+      float Ln = 0.f;
       if (j == i) {
-        nh = 1.f;
         a2 += 1.f;
       } else if (j < n) {
         const float dtn = h_at(ob, e) * iqs;
@@ -313,22 +335,20 @@ __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta,
         two_prod(gh[e], dtn, pp, pq);
         pq = fmaf(gl[e], dtn, pq);
         Ln = (R0h[e] - pp) + (R0l[e] - pq);
-        nh = dtn;
         r2 = fmaf(R0h[e], R0h[e], r2);
         const float p1 = h_at(D[0], e) * dtn;
-        const float p23 = fmaf(h_at(D[1], e), dtn, h_at(D[2], e) * dtn);
+        float p23 = 0.f;
+        if (NSL > 2) p23 = h_at(D[2], e) * dtn;
+        if (NSL > 1) p23 = fmaf(h_at(D[1], e), dtn, p23);
         float sh, se;
         two_sum(eh, p1, sh, se);
         se += el + p23;
         fast_two_sum(sh, se, eh, el);
         mx = fmaxf(mx, fabsf(dtn));
       }
-      f4set(oh, e, nh);
       f4set(oL, e, Ln);
     }
     const int64_t idx = (int64_t)i * ld + j0;
-    st4(Ahi1 + idx, oh);
-    st4(Alo1 + idx, make_float4(0.f, 0.f, 0.f, 0.f));
     st4(L + idx, oL);
     // rows beyond n and the diagonal hold zero increments (q = 0 there)
     *reinterpret_cast<uint2*>(dt0 + idx) = ob;
@@ -344,8 +364,12 @@ __global__ void __launch_bounds__(128) k_iter0(const double* __restrict__ delta,
   for (int e = 0; e < 4; ++e) rows[w][r0 + e] = rowabs[e];
   __syncthreads();
   const int r = threadIdx.x;
-  if (m0 + r < n)
-    rowpart[(int64_t)blockIdx.x * ld + m0 + r] = ((rows[0][r] + rows[1][r]) + rows[2][r]) + rows[3][r];
+  if (r < IT0 && m0 + r < n) {
+    float t = 0.f;
+#pragma unroll
+    for (int q2 = 0; q2 < W; ++q2) t += rows[q2][r];
+    rowpart[(int64_t)blockIdx.x * ld + m0 + r] = t;
+  }
   // the slice count and scale of the first product depend on the size of dt_0
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0 && mx > 0.f) atomicMax(&st->dmax_bits, __float_as_uint(mx));
@@ -512,6 +536,7 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
   // a certifying pass forms only the residual of the current iterate (nothing is
   // written but its norms), see k_ctrl
   const bool cert = ms->certify != 0;
+  const bool a1 = ms->k == 1;             // A_1 = I + dt_0, formed from dt_0
   // explicit selects: indexing the parameter arrays with a runtime value would
   // copy the parameter block to local memory
   const float* __restrict__ Ahc = c1 ? p.A_hi[1] : p.A_hi[0];
@@ -540,10 +565,16 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
       const int i = n0 + cb + u;
       if (i < n) {
         const int64_t idx = (int64_t)i * ld + j0;
-        in[u].ah = ld4(Ahc + idx);
-        in[u].al = cert ? make_float4(0.f, 0.f, 0.f, 0.f) : ld4(Alc + idx);
         in[u].L = ld4(L + idx);
         in[u].dtp = *reinterpret_cast<const uint2*>(dtp + idx);
+        if (a1) {   // off the diagonal A_1 = dt_0 (its diagonal entry is never read)
+          const float isc = exp2i(-ms->scur);
+          in[u].ah = make_float4(h_at(in[u].dtp, 0) * isc, h_at(in[u].dtp, 1) * isc,
+                                 h_at(in[u].dtp, 2) * isc, h_at(in[u].dtp, 3) * isc);
+        } else {
+          in[u].ah = ld4(Ahc + idx);
+        }
+        in[u].al = (cert || a1) ? make_float4(0.f, 0.f, 0.f, 0.f) : ld4(Alc + idx);
         // Delta_ij 2^sig for j = j0..j0+3: row i of the row-major slices.  The
         // diagonal partial uses as many slices as this product: its truncation error
         // then obeys the same bound as the product's (see next_slices_f16)
@@ -827,8 +858,9 @@ __device__ __forceinline__ bool p_epi_bar_and(bool v) {
 
 // Issue the copies of sub-chunk sc (columns 16 sc .. 16 sc + 15) of tile (m0, n0).
 // A certifying pass (cert) needs neither A_lo nor the slices.
-__device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, bool cert, int S,
-                                             uint8_t* eb, int ew, int lane, int m0, int n0,
+// The first product's iterate A_1 = I + dt_0 is not stored (a1): it is formed from dt_0.
+__device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, bool cert, bool a1,
+                                             int S, uint8_t* eb, int ew, int lane, int m0, int n0,
                                              int sc) {
   const float* Ahc = c1 ? p.A_hi[1] : p.A_hi[0];
   const float* Alc = c1 ? p.A_lo[1] : p.A_lo[0];
@@ -839,8 +871,8 @@ __device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, bo
     const int i = n0 + 16 * sc + ew + u;
     if (i >= p.n) continue;
     const int64_t idx = (int64_t)i * p.ld + j0;
-    cp_async16(eb_f4(eb, ew, u, 0, lane), Ahc + idx);
-    if (!cert) cp_async16(eb_f4(eb, ew, u, 1, lane), Alc + idx);
+    if (!a1) cp_async16(eb_f4(eb, ew, u, 0, lane), Ahc + idx);
+    if (!cert && !a1) cp_async16(eb_f4(eb, ew, u, 1, lane), Alc + idx);
     cp_async16(eb_f4(eb, ew, u, 2, lane), p.L + idx);
     cp_async8(eb_u2(eb, ew, u, 0, lane), dtp + idx);
     if (cert) continue;
@@ -852,23 +884,30 @@ __device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, bo
 
 // Update this warp's column of sub-chunk sc from the staged inputs in eb and
 // the accumulator chunk in Xs (which holds columns c0 .. c0 + 31, c0 = 32 (sc / 2)).
+// Launch-constant factors of the staged epilogue (the scales of epilogue_columns),
+// formed once per thread, and the tile's row parameters, loaded once per tile.
+struct EpiConst {
+  float lam;          // lambda 2^-sig 2^-scur
+  float qs, iqs;      // 2^snew, 2^-snew
+  float isc;          // 2^-scur
+};
+
 __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc* ms,
                                             const float* Xs, const uint8_t* eb, int S, int ew,
-                                            int lane, int tm, int m0, int n0, int sc, float& mx) {
+                                            int lane, int tm, int m0, int n0, int sc, float& mx,
+                                            const EpiConst& kc, const float4& thj_h,
+                                            const float4& thj_l) {
   const int n = p.n, ld = p.ld;
   const bool c1 = (ms->cur != 0);
   const bool cert = ms->certify != 0;     // residual norms only, nothing written
+  const bool a1 = ms->k == 1;             // A_1 = I + dt_0, formed from dt_0
   float* __restrict__ Ahn = c1 ? p.A_hi[0] : p.A_hi[1];
   float* __restrict__ Aln = c1 ? p.A_lo[0] : p.A_lo[1];
   __half* __restrict__ dtn_out = c1 ? p.dt[1] : p.dt[0];
   float* __restrict__ L = p.L;
-  // scales as in epilogue_columns
-  const float lam = (p.lam * exp2i(-ms->sig)) * exp2i(-ms->scur);
-  const float qs = exp2i(ms->snew), iqs = exp2i(-ms->snew);
+  const float lam = kc.lam, qs = kc.qs, iqs = kc.iqs;
   const int r0 = 4 * lane;
   const int j0 = m0 + r0;
-  const float4 thj_h = ld4(p.th_hi + j0);
-  const float4 thj_l = ld4(p.th_lo + j0);
   const int c0 = 32 * (sc >> 1);
 #pragma unroll
   for (int u = 0; u < 1; ++u) {
@@ -876,11 +915,15 @@ __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc
     const int i = n0 + cl;
     if (i >= n) continue;   // uniform across the warp
     uint8_t* e8 = const_cast<uint8_t*>(eb);
-    const float4 ah4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 0, lane));
-    const float4 al4 = cert ? make_float4(0.f, 0.f, 0.f, 0.f)
-                            : *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 1, lane));
     const float4 L4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 2, lane));
     const uint2 dtp = *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 0, lane));
+    // off the diagonal A_1 = dt_0 (its diagonal entry is never read)
+    const float isc = kc.isc;
+    const float4 ah4 = a1 ? make_float4(h_at(dtp, 0) * isc, h_at(dtp, 1) * isc,
+                                        h_at(dtp, 2) * isc, h_at(dtp, 3) * isc)
+                          : *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 0, lane));
+    const float4 al4 = (cert || a1) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                    : *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 1, lane));
     const int Se = cert ? 0 : S;
     uint2 D[3];
     D[0] = Se > 0 ? *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 1, lane)) : make_uint2(0u, 0u);
@@ -1094,14 +1137,20 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const uint32_t acc_empty_leader = mapa_shared(&ms->acc_empty[0], 0);
     const bool c1 = (ms->cur != 0);
     const bool cert = ms->certify != 0;
+    const bool a1 = ms->k == 1;            // A_1 = I + dt_0 is formed from dt_0
     const int nsub = bn / 16;              // sub-chunks per tile (even: bn is a multiple of 32)
     const float cs = exp2i(ms->scur), cd = exp2i(ms->sig);
+    EpiConst kc;
+    kc.lam = (p.lam * exp2i(-ms->sig)) * exp2i(-ms->scur);
+    kc.qs = exp2i(ms->snew);
+    kc.iqs = exp2i(-ms->snew);
+    kc.isc = exp2i(-ms->scur);
     float mx = 0.f;
     int lt = 0;
     // the first tile's first sub-chunk, while its products run
     if (pair < ntiles) {
       const int tm = 2 * (pair / ntn) + (int)rank;
-      if (tm < p.ntm) epi_prefetch(p, c1, cert, S, EB, ew, lane, tm * BM, (pair % ntn) * bn, 0);
+      if (tm < p.ntm) epi_prefetch(p, c1, cert, a1, S, EB, ew, lane, tm * BM, (pair % ntn) * bn, 0);
     }
     cp_async_commit();
     for (int t = pair; t < ntiles; t += npairs, ++lt) {
@@ -1111,6 +1160,9 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       const int b = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
       const bool work = tm < p.ntm;        // rows of a pair tile beyond the padded matrix
+      // theta_j of this lane's four rows (padded arrays: rows up to ld exist)
+      const float4 thj_h = work ? ld4(p.th_hi + m0 + 4 * lane) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 thj_l = work ? ld4(p.th_lo + m0 + 4 * lane) : make_float4(0.f, 0.f, 0.f, 0.f);
       p_epi_bar();
       if (et < bn) {
         const int i = n0 + et;
@@ -1147,15 +1199,17 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           // copies of the next sub-chunk: this tile's, or the next tile's first
           uint8_t* nb = EB + ((sc + 1) & 1) * EB_BYTES;
           if (sc + 1 < nsub) {
-            if (work) epi_prefetch(p, c1, cert, S, nb, ew, lane, m0, n0, sc + 1);
+            if (work) epi_prefetch(p, c1, cert, a1, S, nb, ew, lane, m0, n0, sc + 1);
           } else if (t + npairs < ntiles) {
             const int tn2 = 2 * ((t + npairs) / ntn) + (int)rank;
             if (tn2 < p.ntm)
-              epi_prefetch(p, c1, cert, S, nb, ew, lane, tn2 * BM, ((t + npairs) % ntn) * bn, 0);
+              epi_prefetch(p, c1, cert, a1, S, nb, ew, lane, tn2 * BM, ((t + npairs) % ntn) * bn, 0);
           }
           cp_async_commit();
           cp_async_wait<1>();              // this lane's copies of sub-chunk sc have landed
-          if (work) epi_compute(p, ms, Xs, EB + (sc & 1) * EB_BYTES, S, ew, lane, tm, m0, n0, sc, mx);
+          if (work)
+            epi_compute(p, ms, Xs, EB + (sc & 1) * EB_BYTES, S, ew, lane, tm, m0, n0, sc, mx, kc,
+                        thj_h, thj_l);
         }
       }
       if (!all_ok) break;
@@ -1182,6 +1236,7 @@ __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __
                                                   const float* __restrict__ Alo0,
                                                   const float* __restrict__ Ahi1,
                                                   const float* __restrict__ Alo1,
+                                                  const __half* __restrict__ dt0,
                                                   double* __restrict__ Aout, int64_t ld_a,
                                                   const IterState* st, int only_done) {
   const int j = blockIdx.x * 128 + threadIdx.x;
@@ -1191,6 +1246,13 @@ __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __
   const int k = st->k;
   if (k == 0) {
     for (int i = i0; i < i1; ++i) Aout[(int64_t)i * ld_a + j] = (i == j) ? 1.0 : 0.0;
+    return;
+  }
+  if (k == 1) {   // A_1 = I + dt_0 (iteration 0 stores only the increment)
+    const float isc = exp2i(-st->sexp[0]);
+    for (int i = i0; i < i1; ++i)
+      Aout[(int64_t)i * ld_a + j] =
+          (i == j) ? 1.0 : f2d_bits(__half2float(dt0[(int64_t)i * ld + j]) * isc);
     return;
   }
   const float* __restrict__ hi = (st->cur == 0) ? Ahi0 : Ahi1;
@@ -1318,15 +1380,21 @@ cudaError_t launch_theta_ff(int n, const double* th, float* hi, float* lo, cudaS
 
 cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
                          const float* th_lo, double lam, int n, int ld, int en, int nsl,
-                         const __half* Dcat, float* Ahi1, float* Alo1,
-                         __half* dt0, float* L, double* d, float* part, float* rowpart,
-                         IterState* st, cudaStream_t s) {
+                         const __half* Dcat, __half* dt0, float* L, double* d, float* part,
+                         float* rowpart, IterState* st, cudaStream_t s) {
   if (nsl < 1 || nsl > NSLICE) return cudaErrorInvalidValue;
   const int ntm = (n + IT0 - 1) / IT0, ntn = (n + IT0 - 1) / IT0;
   const float lh = (float)lam;
   const float ll = (float)(lam - (double)lh);
-  k_iter0<<<dim3(ntn, ntm), 128, 0, s>>>(delta, ld_in, th_hi, th_lo, lh, ll, n, ld, ntm, en,
-                                         nsl, Dcat, Ahi1, Alo1, dt0, L, d, part, rowpart, st);
+  const dim3 grid(ntn, ntm);
+  switch (nsl) {
+    case 1: k_iter0<1><<<grid, 256, 0, s>>>(delta, ld_in, th_hi, th_lo, lh, ll, n, ld, ntm, en,
+                                            Dcat, dt0, L, d, part, rowpart, st); break;
+    case 2: k_iter0<2><<<grid, 256, 0, s>>>(delta, ld_in, th_hi, th_lo, lh, ll, n, ld, ntm, en,
+                                            Dcat, dt0, L, d, part, rowpart, st); break;
+    default: k_iter0<3><<<grid, 256, 0, s>>>(delta, ld_in, th_hi, th_lo, lh, ll, n, ld, ntm, en,
+                                             Dcat, dt0, L, d, part, rowpart, st); break;
+  }
   return cudaGetLastError();
 }
 
@@ -1416,10 +1484,10 @@ cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
 }
 
 cudaError_t launch_finalize(int n, int ld, const float* Ahi0, const float* Alo0,
-                            const float* Ahi1, const float* Alo1, double* Aout, int64_t ld_a,
-                            const IterState* st, int only_done, cudaStream_t s) {
+                            const float* Ahi1, const float* Alo1, const __half* dt0, double* Aout,
+                            int64_t ld_a, const IterState* st, int only_done, cudaStream_t s) {
   dim3 grid((n + 127) / 128, (n + 31) / 32);   // 128 rows x 32 columns per block
-  k_finalize<<<grid, 128, 0, s>>>(n, ld, Ahi0, Alo0, Ahi1, Alo1, Aout, ld_a, st, only_done);
+  k_finalize<<<grid, 128, 0, s>>>(n, ld, Ahi0, Alo0, Ahi1, Alo1, dt0, Aout, ld_a, st, only_done);
   return cudaGetLastError();
 }
 

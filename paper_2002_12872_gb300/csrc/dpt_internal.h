@@ -194,17 +194,17 @@ cudaError_t launch_theta_ff(int n, const double* th, float* hi, float* lo, cudaS
 cudaError_t launch_check_theta(int n, const double* th, IterState* st, cudaStream_t s);
 cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
                          const float* th_lo, double lam, int n, int ld, int en, int nsl,
-                         const __half* Dcat, float* Ahi1, float* Alo1,
-                         __half* dt0, float* L, double* d, float* part, float* rowpart,
-                         IterState* st, cudaStream_t s);
+                         const __half* Dcat, __half* dt0, float* L, double* d, float* part,
+                         float* rowpart, IterState* st, cudaStream_t s);
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,
                         float* dprev_col, IterState* st, cudaStream_t s);
 cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
                             const CUtensorMap& tmB1, const GemmEpiParams& p, cudaStream_t s);
+// The returned iterate in FP64 (A_1 = I + dt_0 is formed from the first increment dt0).
 cudaError_t launch_finalize(int n, int ld, const float* Ahi0, const float* Alo0,
-                            const float* Ahi1, const float* Alo1, double* Aout, int64_t ld_a,
-                            const IterState* st, int only_done, cudaStream_t s);
+                            const float* Ahi1, const float* Alo1, const __half* dt0, double* Aout,
+                            int64_t ld_a, const IterState* st, int only_done, cudaStream_t s);
 
 // Plain FP64 path (real and complex)
 cudaError_t launch_fp64_init(int n, int ld, int cplx, void* A0, cudaStream_t s);

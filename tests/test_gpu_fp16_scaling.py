@@ -68,3 +68,21 @@ def test_strongly_coupled_solve_is_finished_in_fp64(dpt, host):
     E = to_np(E)
     # the plain FP64 map's bar (its residual at tol 1e-12)
     assert abs(E[0] - (1 - r) / 2) < 1e-12 and abs(E[1] - (1 + r) / 2) < 1e-12
+
+
+@pytest.mark.parametrize("pair", [True, False])
+def test_solve_returning_the_first_iterate(ora, dpt, pair):
+    """Iteration 0 stores only dt_0 (A_1 = I + dt_0 is formed where it is read): at
+    lambda = 1e-7 the first product already certifies A_1, which the output kernel
+    then builds from dt_0."""
+    cfg = inputs.full_unsymmetric(n=300)
+    lam = 1e-7
+    th = torch.tensor(cfg["theta"], device="cuda")
+    D = dpt.colmajor_tensor(cfg["delta"], "cuda")
+    A, E, info = dpt.solve_full(th, D, lam, cta_pair=pair)
+    assert info["status"] == "OK" and info["iters"] == 1, info
+    Ao, Eo, io = ora.solve_full(cfg["theta"], cfg["delta"], lam, tol=1e-13)
+    assert io["status"] == "OK"
+    assert eig_err(to_np(E), Eo) <= EIG_RTOL
+    assert vec_err(to_np(A), Ao) <= VEC_TOL
+    assert np.all(np.diag(to_np(A)) == 1.0)
