@@ -89,9 +89,10 @@ constexpr int P_SMEM_BYTES = P_RING + SMEM_X + 2 * EB_BYTES + 1024 + (int)sizeof
 static_assert(P_SMEM_BYTES <= 232448, "CTA-pair shared memory over the per-block limit");
 
 // ---------------------------------------------------------------------------
-// Scales of the FP16 operands.  One block per column i of Delta (rows j
-// contiguous): the high word of max |Delta_ji| (the FP64 bits without the sign;
-// with its low word filled with ones it bounds max |Delta|) and max_{j != i}
+// Scales of the FP16 operands.  Each block walks columns i of Delta (rows j
+// contiguous; the launch gives one block per column): the high word of max |Delta_ji|
+// (the FP64 bits without the sign; with its low word filled with ones it bounds
+// max |Delta|) and max_{j != i}
 // |Delta_ji| / |theta_i - theta_j| (float-float gaps), both by integer atomicMax.
 // The last block sets sig (max |Delta| 2^sig in [2^14, 2^15)) and the exponent of
 // the first increment: |dt_0| <= |lambda| max |Delta_ji / gap| lands at 2^13.
@@ -101,38 +102,39 @@ __global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__
                                                       const float* __restrict__ th_hi,
                                                       const float* __restrict__ th_lo, int en,
                                                       IterState* st) {
-  const int i = blockIdx.x;
-  const float thh = th_hi[i], thl = th_lo[i];
-  const double* col = delta + (int64_t)i * ld_in;
   unsigned hmax = 0u;
   float gmax = 0.f;
-  // four independent loads in flight per thread (the column streams from HBM)
-  for (int jb = threadIdx.x; jb < n; jb += 1024) {
-    double v[4];
-    float tjh[4], tjl[4];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const float thh = th_hi[i], thl = th_lo[i];
+    const double* col = delta + (int64_t)i * ld_in;
+    // four independent loads in flight per thread (the column streams from HBM)
+    for (int jb = threadIdx.x; jb < n; jb += 1024) {
+      double v[4];
+      float tjh[4], tjl[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = jb + 256 * u;
-      v[u] = j < n ? col[j] : 0.0;
-      tjh[u] = j < n ? th_hi[j] : 0.f;
-      tjl[u] = j < n ? th_lo[j] : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = jb + 256 * u;
-      if (j >= n) break;
-      const unsigned hw = (unsigned)__double2hiint(v[u]) & 0x7FFFFFFFu;
-      if (j == i) {
-        if (!en) hmax = max(hmax, hw);
-        continue;
+      for (int u = 0; u < 4; ++u) {
+        const int j = jb + 256 * u;
+        v[u] = j < n ? col[j] : 0.0;
+        tjh[u] = j < n ? th_hi[j] : 0.f;
+        tjl[u] = j < n ? th_lo[j] : 0.f;
       }
-      hmax = max(hmax, hw);
-      float vh, vl;
-      split_double_fast(v[u], vh, vl);
-      float gh, gl;
-      ff_sub(thh, thl, tjh[u], tjl[u], gh, gl);
-      // a scale bound: an approximate reciprocal serves (NaN never wins fmaxf)
-      gmax = fmaxf(gmax, fabsf(vh) * rcp_approx(fabsf(gh)));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = jb + 256 * u;
+        if (j >= n) break;
+        const unsigned hw = (unsigned)__double2hiint(v[u]) & 0x7FFFFFFFu;
+        if (j == i) {
+          if (!en) hmax = max(hmax, hw);
+          continue;
+        }
+        hmax = max(hmax, hw);
+        float vh, vl;
+        split_double_fast(v[u], vh, vl);
+        float gh, gl;
+        ff_sub(thh, thl, tjh[u], tjl[u], gh, gl);
+        // a scale bound: an approximate reciprocal serves (NaN never wins fmaxf)
+        gmax = fmaxf(gmax, fabsf(vh) * rcp_approx(fabsf(gh)));
+      }
     }
   }
   hmax = __reduce_max_sync(0xffffffffu, hmax);
@@ -892,11 +894,14 @@ struct EpiConst {
   float isc;          // 2^-scur
 };
 
+// Leaves this lane's partial sums of the column (|R|^2, |a|^2, and the diagonal
+// increment as float-float) in part4; the caller reduces two columns at once.
+template <int S>
 __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc* ms,
-                                            const float* Xs, const uint8_t* eb, int S, int ew,
-                                            int lane, int tm, int m0, int n0, int sc, float& mx,
+                                            const float* Xs, const uint8_t* eb, int ew,
+                                            int lane, int m0, int n0, int sc, float& mx,
                                             const EpiConst& kc, const float4& thj_h,
-                                            const float4& thj_l) {
+                                            const float4& thj_l, float (&part4)[4]) {
   const int n = p.n, ld = p.ld;
   const bool c1 = (ms->cur != 0);
   const bool cert = ms->certify != 0;     // residual norms only, nothing written
@@ -924,11 +929,13 @@ __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc
                           : *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 0, lane));
     const float4 al4 = (cert || a1) ? make_float4(0.f, 0.f, 0.f, 0.f)
                                     : *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 1, lane));
-    const int Se = cert ? 0 : S;
-    uint2 D[3];
-    D[0] = Se > 0 ? *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 1, lane)) : make_uint2(0u, 0u);
-    D[1] = Se > 1 ? *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 2, lane)) : make_uint2(0u, 0u);
-    D[2] = Se > 2 ? *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 3, lane)) : make_uint2(0u, 0u);
+    // the slices of Delta_ij this product uses (not loaded by a certifying pass)
+    uint2 D[3] = {make_uint2(0u, 0u), make_uint2(0u, 0u), make_uint2(0u, 0u)};
+    if (!cert) {
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl)
+        D[sl] = *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 1 + sl, lane));
+    }
     const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * BM + r0);
     const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
     const float thh = ms->thh[cl], thl = ms->thl[cl];
@@ -972,7 +979,9 @@ __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc
           Ln = fmaf(-gh[t], dnew, R[t]) - gl[t] * dnew;
           ff_add_f(ah, al, dnew, nh, nl);
           const float p1 = h_at(D[0], e) * dnew;
-          const float p23 = fmaf(h_at(D[1], e), dnew, h_at(D[2], e) * dnew);
+          float p23 = 0.f;
+          if (S > 2) p23 = h_at(D[2], e) * dnew;
+          if (S > 1) p23 = fmaf(h_at(D[1], e), dnew, p23);
           float sh, se;
           two_sum(eh, p1, sh, se);
           se += el + p23;
@@ -991,16 +1000,44 @@ __device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc
       st4(L + idx, oL);
       *reinterpret_cast<uint2*>(dtn_out + idx) = ob;
     }
-    warp_sum_ff(r2, a2, eh, el);
-    if (lane == 0) {
-      p.part[((int64_t)0 * p.ntm + tm) * ld + i] = r2;
-      p.part[((int64_t)1 * p.ntm + tm) * ld + i] = a2;
-      if (!cert) {
-        p.part[((int64_t)2 * p.ntm + tm) * ld + i] = eh;
-        p.part[((int64_t)3 * p.ntm + tm) * ld + i] = el;
-      }
-    }
+    part4[0] = r2; part4[1] = a2; part4[2] = eh; part4[3] = el;
   }
+}
+
+// Warp sums of two columns' lane partials (|R|^2, |a|^2, diagonal increment as
+// float-float) with one transposing exchange: after the first step lanes 0-15 carry
+// column a and lanes 16-31 column b, so the remaining four steps serve both (about
+// half the shuffles and float-float additions of two separate reductions).  On
+// return lane 0 holds the sums of a, lane 16 those of b.
+__device__ __forceinline__ void warp_sum_ff2(float (&a)[4], const float (&b)[4], int lane) {
+  const bool lo = lane < 16;
+  float k[4], o[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    k[q] = lo ? a[q] : b[q];
+    o[q] = __shfl_xor_sync(0xffffffffu, lo ? b[q] : a[q], 16);
+  }
+  k[0] += o[0];
+  k[1] += o[1];
+  {
+    float sh, se;
+    two_sum(k[2], o[2], sh, se);
+    se += k[3] + o[3];
+    fast_two_sum(sh, se, k[2], k[3]);
+  }
+#pragma unroll
+  for (int off = 8; off > 0; off >>= 1) {
+    k[0] += __shfl_xor_sync(0xffffffffu, k[0], off);
+    k[1] += __shfl_xor_sync(0xffffffffu, k[1], off);
+    const float oh = __shfl_xor_sync(0xffffffffu, k[2], off);
+    const float ol = __shfl_xor_sync(0xffffffffu, k[3], off);
+    float sh, se;
+    two_sum(k[2], oh, sh, se);
+    se += k[3] + ol;
+    fast_two_sum(sh, se, k[2], k[3]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) a[q] = k[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -1193,6 +1230,7 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           else mbar_arrive_remote(acc_empty_leader + (uint32_t)b * 8u);
         }
         if (!all_ok) break;
+        float pa[4] = {0.f, 0.f, 0.f, 0.f}, pb[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
           const int sc = c0 / 16 + h;
@@ -1207,9 +1245,35 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           }
           cp_async_commit();
           cp_async_wait<1>();              // this lane's copies of sub-chunk sc have landed
-          if (work)
-            epi_compute(p, ms, Xs, EB + (sc & 1) * EB_BYTES, S, ew, lane, tm, m0, n0, sc, mx, kc,
-                        thj_h, thj_l);
+          if (work) {
+            const uint8_t* eb = EB + (sc & 1) * EB_BYTES;
+            float cur[4] = {0.f, 0.f, 0.f, 0.f};
+            if (S == 1)
+              epi_compute<1>(p, ms, Xs, eb, ew, lane, m0, n0, sc, mx, kc, thj_h, thj_l, cur);
+            else if (S == 2)
+              epi_compute<2>(p, ms, Xs, eb, ew, lane, m0, n0, sc, mx, kc, thj_h, thj_l, cur);
+            else
+              epi_compute<3>(p, ms, Xs, eb, ew, lane, m0, n0, sc, mx, kc, thj_h, thj_l, cur);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {   // registers, no indexing by h
+              if (h == 0) pa[q] = cur[q];
+              else pb[q] = cur[q];
+            }
+          }
+        }
+        if (work) {
+          // this warp's two columns of the chunk, reduced together
+          warp_sum_ff2(pa, pb, lane);
+          const int i = n0 + c0 + 16 * (lane >> 4) + ew;
+          if ((lane & 15) == 0 && i < p.n) {
+            const int64_t ld = p.ld;
+            p.part[((int64_t)0 * p.ntm + tm) * ld + i] = pa[0];
+            p.part[((int64_t)1 * p.ntm + tm) * ld + i] = pa[1];
+            if (!cert) {
+              p.part[((int64_t)2 * p.ntm + tm) * ld + i] = pa[2];
+              p.part[((int64_t)3 * p.ntm + tm) * ld + i] = pa[3];
+            }
+          }
         }
       }
       if (!all_ok) break;
@@ -1352,6 +1416,8 @@ cudaError_t launch_delta_scales(const double* delta, int64_t ld_in, int n, const
                                 const float* th_lo, double lam, int en, IterState* st,
                                 cudaStream_t s) {
   (void)lam;   // read from the state
+  // one block per column (a grid striding over fewer blocks measured slower: 38 us
+  // against 34 us at n = 4096)
   k_delta_scales<<<n, 256, 0, s>>>(delta, ld_in, n, th_hi, th_lo, en, st);
   return cudaGetLastError();
 }
