@@ -417,12 +417,16 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
         CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
       }, sizeof(IterState), /*k_first=*/1, tail, 1);   // the control after iteration 0 set k = 1
     }
-    if (!a_dev)
-      CK(cudaMemcpy2DAsync(A_out, sizeof(double) * ld_a, Astage, sizeof(double) * ld,
-                           sizeof(double) * n, n, cudaMemcpyDeviceToHost, s));
-    if (!e_dev) CK(cudaMemcpyAsync(E_out, E, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(b->host_state, st, sizeof(IterState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    if (!a_dev || !e_dev) {
+      if (!a_dev)
+        CK(cudaMemcpy2DAsync(A_out, sizeof(double) * ld_a, Astage, sizeof(double) * ld,
+                             sizeof(double) * n, n, cudaMemcpyDeviceToHost, s));
+      if (!e_dev) CK(cudaMemcpyAsync(E_out, E, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(b->host_state, st, sizeof(IterState), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    // with device outputs the loop's last read of the state (after the chunk whose
+    // tail formed the outputs) is the final state: no further round trip
     const IterState& fs = *b->host_state;
     ret = from_state(fs.status);
     if (rho_sum) *rho_sum = fs.rho_sum;

@@ -30,6 +30,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "dpt_device.cuh"
 #include "dpt_internal.h"
 
@@ -1474,11 +1476,18 @@ cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
 }
 
 cudaError_t mixed_set_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_epi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       SMEM_BYTES);
+  // once per device (the attribute stays set for the context)
+  static std::atomic<bool> done[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_gemm_epi_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              P_SMEM_BYTES);
+  if (dev >= 0 && dev < 64 && done[dev].load()) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_gemm_epi, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gemm_epi_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           P_SMEM_BYTES);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev].store(true);
+  return e;
 }
 
 // Clusters of two that can be resident at once (0: the pair form cannot run).  The

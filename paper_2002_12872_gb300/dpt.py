@@ -280,6 +280,38 @@ def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
     return res
 
 
+class FullSolve:
+    """dpt_solve_full with its arguments marshalled once, for repeated solves of the
+    same buffers (the library reads theta and Delta and writes A and E in place on
+    every call).  Keyword options are those of solve_full; solve() returns the info
+    dict and raises RuntimeError on a status other than OK unless check=False."""
+
+    def __init__(self, theta, delta, lam, *, A_out=None, E_out=None, stream=None, **opts):
+        cplx = _iscomplex(delta)
+        n = int(theta.shape[0])
+        th_ptr, self._th_keep = _vec_ptr(theta, "float64")
+        d_ptr, ldd, self._d_keep = _colmajor(delta, cplx)
+        self.A = _empty_colmajor(n, delta, cplx) if A_out is None else A_out
+        self.E = _empty_vec(n, delta, cplx) if E_out is None else E_out
+        lda = self.A.stride(1) if _is_torch(self.A) else self.A.strides[1] // self.A.itemsize
+        for k in ("epstein_nesbet", "profile", "certify", "cta_pair"):
+            if opts.get(k) is not None:
+                opts[k] = int(bool(opts[k]))
+        self.opts = options(**opts)
+        self._info = Info()
+        self._fn = lib().dpt_solve_full
+        self._args = (n, C128 if cplx else R64, th_ptr, d_ptr, ldd, float(lam),
+                      ctypes.byref(self.opts), _ptr(self.A), lda, _ptr(self.E),
+                      ctypes.byref(self._info), _stream_of(delta, stream))
+
+    def solve(self, check=True):
+        st = self._fn(*self._args)
+        info = self._info.as_dict()
+        if check and st != OK:
+            raise RuntimeError(f"dpt_solve_full: {status_string(st)}")
+        return info
+
+
 def solve_homotopy(theta, delta, lam, stages, *, prec="mixed", tol=1e-12, max_iter=200,
                    graph_iters=None, max_slices=None, A_out=None, E_out=None, stream=None,
                    check=True):

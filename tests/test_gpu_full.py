@@ -274,3 +274,19 @@ def test_workspace_bytes_matches_pool_growth(dpt, prec):
     ws = dpt.workspace_bytes(n, prec=prec)
     assert ws > 0 and abs(used - ws) <= 8 * 2**20, (used, ws)
     dpt.release_workspace()
+
+
+def test_prepared_solve_matches_solve_full(dpt):
+    """FullSolve (arguments marshalled once) is the same C-ABI call as solve_full: the
+    same bits, call after call, into the caller's buffers."""
+    cfg = inputs.full_unsymmetric(n=300)
+    th, D = _dev(cfg)
+    A0, E0, i0 = dpt.solve_full(th, D, cfg["lam"])
+    A = torch.empty((300, 300), dtype=torch.float64, device="cuda").t()
+    E = torch.empty(300, dtype=torch.float64, device="cuda")
+    fs = dpt.FullSolve(th, D, cfg["lam"], A_out=A, E_out=E, profile=True)
+    for _ in range(2):
+        info = fs.solve()
+        assert info["status"] == "OK" and info["iters"] == i0["iters"]
+        assert info["product_ms"] > 0
+        assert torch.equal(A, A0) and torch.equal(E, E0)
