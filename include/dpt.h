@@ -177,7 +177,9 @@ typedef struct {
                               iters) that finished a strongly coupled solve, whose
                               float recursion could not vouch for the tolerance
                               (2^-23 times the sum of its residuals above
-                              max(tol, 1e-11)); 0 otherwise */
+                              max(tol, 1e-11)); 0 otherwise, and for n > 65535 (the
+                              plain FP64 path's limit), where the mixed result is
+                              returned as it is */
 } dpt_info;
 
 /* Fill *opt with the defaults listed above. */

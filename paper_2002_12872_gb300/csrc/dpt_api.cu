@@ -1491,7 +1491,9 @@ dpt_status mixed_real_finished(int64_t n, std::vector<double> th, const double* 
   double rho_sum = 0.0;
   dpt_status st = solve_full_mixed_real(n, th, theta_dev, delta, delta_dev, ld_delta, lambda, o,
                                         A_out, a_dev, ld_a, E_out, e_dev, &mi, s, &rho_sum);
-  if (st == DPT_OK && rho_sum * 0x1p-23 > std::max(o.tol, 1e-11)) {
+  // the plain FP64 path launches one grid row per column (at most 65535): beyond that
+  // the mixed result is returned as it is
+  if (st == DPT_OK && rho_sum * 0x1p-23 > std::max(o.tol, 1e-11) && n <= 65535) {
     if (th.empty()) {   // device theta, already checked by the mixed solve
       st = host_theta(n, theta_dev, true, th);
       if (st != DPT_OK) return st;
