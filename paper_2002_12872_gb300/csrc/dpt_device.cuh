@@ -146,18 +146,24 @@ __device__ __forceinline__ void slice_tile_32x64(const double* __restrict__ delt
                                                  unsigned* bad, double (*tile)[65]) {
   const int x = threadIdx.x, y = threadIdx.y;
   {
+    // all eight loads are issued before any check (an atomic between them would
+    // keep the next load from starting)
     const int j = by + x;
+    double v[8];
 #pragma unroll
-    for (int r = y; r < 64; r += 8) {
-      const int k = bx + r;
-      double v = 0.0;
-      if (j < n && k < n) {
-        v = delta[(int64_t)k * ld_in + j];
-        if (beyond_float(v)) atomicExch(bad, 1u);   // non-finite, or beyond the float range
-        if (en && j == k) v = 0.0;
-      }
-      tile[x][r] = v;      // tile[j - by][k - bx]
+    for (int m = 0; m < 8; ++m) {
+      const int k = bx + y + 8 * m;
+      v[m] = (j < n && k < n) ? delta[(int64_t)k * ld_in + j] : 0.0;
     }
+    bool badv = false;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = bx + y + 8 * m;
+      badv |= beyond_float(v[m]);   // non-finite, or beyond the float range
+      if (en && j == k) v[m] = 0.0;
+      tile[x][y + 8 * m] = v[m];    // tile[j - by][k - bx]
+    }
+    if (badv) atomicExch(bad, 1u);
   }
   __syncthreads();
   const int k0 = bx + 2 * x;

@@ -91,11 +91,13 @@ constexpr int P_SMEM_BYTES = P_RING + SMEM_X + 2 * EB_BYTES + 1024 + (int)sizeof
 static_assert(P_SMEM_BYTES <= 232448, "CTA-pair shared memory over the per-block limit");
 
 // ---------------------------------------------------------------------------
-// Scales of the FP16 operands.  Each block walks columns i of Delta (rows j
-// contiguous; the launch gives one block per column): the high word of max |Delta_ji|
-// (the FP64 bits without the sign; with its low word filled with ones it bounds
-// max |Delta|) and max_{j != i}
-// |Delta_ji| / |theta_i - theta_j| (float-float gaps), both by integer atomicMax.
+// Scales of the FP16 operands.  One block per column i of Delta (rows j contiguous):
+// the high word of max |Delta_ji| (the FP64 bits without the sign; with its low word
+// filled with ones it bounds max |Delta|) and max_{j != i} |Delta_ji| /
+// |theta_i - theta_j|, both by integer atomicMax.  The ratio only places the first
+// increment's scale, so it is formed cheaply: |Delta_ji| from its high word (20
+// fraction bits) and the gap from the float parts of theta (their low parts where
+// the high parts coincide).
 // The last block sets sig (max |Delta| 2^sig in [2^14, 2^15)) and the exponent of
 // the first increment: |dt_0| <= |lambda| max |Delta_ji / gap| lands at 2^13.
 // ---------------------------------------------------------------------------
@@ -104,39 +106,42 @@ __global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__
                                                       const float* __restrict__ th_hi,
                                                       const float* __restrict__ th_lo, int en,
                                                       IterState* st) {
+  const int i = blockIdx.x;
+  const float thh = th_hi[i], thl = th_lo[i];
+  const double* col = delta + (int64_t)i * ld_in;
   unsigned hmax = 0u;
   float gmax = 0.f;
-  for (int i = blockIdx.x; i < n; i += gridDim.x) {
-    const float thh = th_hi[i], thl = th_lo[i];
-    const double* col = delta + (int64_t)i * ld_in;
-    // four independent loads in flight per thread (the column streams from HBM)
-    for (int jb = threadIdx.x; jb < n; jb += 1024) {
-      double v[4];
-      float tjh[4], tjl[4];
+  // four independent loads in flight per thread (the column streams from HBM)
+  for (int jb = threadIdx.x; jb < n; jb += 1024) {
+    double v[4];
+    float tjh[4], tjl[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = jb + 256 * u;
-        v[u] = j < n ? col[j] : 0.0;
-        tjh[u] = j < n ? th_hi[j] : 0.f;
-        tjl[u] = j < n ? th_lo[j] : 0.f;
-      }
+    for (int u = 0; u < 4; ++u) {
+      const int j = jb + 256 * u;
+      v[u] = j < n ? col[j] : 0.0;
+      tjh[u] = j < n ? th_hi[j] : 0.f;
+      tjl[u] = j < n ? th_lo[j] : 0.f;
+    }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = jb + 256 * u;
-        if (j >= n) break;
-        const unsigned hw = (unsigned)__double2hiint(v[u]) & 0x7FFFFFFFu;
-        if (j == i) {
-          if (!en) hmax = max(hmax, hw);
-          continue;
-        }
-        hmax = max(hmax, hw);
-        float vh, vl;
-        split_double_fast(v[u], vh, vl);
-        float gh, gl;
-        ff_sub(thh, thl, tjh[u], tjl[u], gh, gl);
-        // a scale bound: an approximate reciprocal serves (NaN never wins fmaxf)
-        gmax = fmaxf(gmax, fabsf(vh) * rcp_approx(fabsf(gh)));
+    for (int u = 0; u < 4; ++u) {
+      const int j = jb + 256 * u;
+      if (j >= n) break;
+      const unsigned hw = (unsigned)__double2hiint(v[u]) & 0x7FFFFFFFu;
+      if (j == i) {
+        if (!en) hmax = max(hmax, hw);
+        continue;
       }
+      hmax = max(hmax, hw);
+      // |v| to 20 fraction bits as a float (0 below the float range; inputs beyond
+      // it are rejected by the slicing)
+      const unsigned e = hw >> 20;
+      const float va = (e > 896u && e < 1151u)
+                           ? __uint_as_float(((e - 896u) << 23) | ((hw & 0xFFFFFu) << 3))
+                           : (e >= 1151u ? __int_as_float(0x7f800000) : 0.f);
+      float g = thh - tjh[u];
+      if (g == 0.f) g = thl - tjl[u];
+      // NaN never wins fmaxf
+      gmax = fmaxf(gmax, va * rcp_approx(fabsf(g)));
     }
   }
   hmax = __reduce_max_sync(0xffffffffu, hmax);
@@ -183,18 +188,24 @@ __device__ __forceinline__ void slice16_tile_32x64(const double* __restrict__ de
                                                    unsigned* bad, double (*tile)[65]) {
   const int x = threadIdx.x, y = threadIdx.y;
   {
+    // all eight loads are issued before any check (an atomic between them would
+    // keep the next load from starting)
     const int j = by + x;
+    double v[8];
 #pragma unroll
-    for (int r = y; r < 64; r += 8) {
-      const int k = bx + r;
-      double v = 0.0;
-      if (j < n && k < n) {
-        v = delta[(int64_t)k * ld_in + j];
-        if (beyond_float(v)) atomicExch(bad, 1u);   // non-finite, or beyond the float range
-        if (en && j == k) v = 0.0;
-      }
-      tile[x][r] = v;      // tile[j - by][k - bx]
+    for (int m = 0; m < 8; ++m) {
+      const int k = bx + y + 8 * m;
+      v[m] = (j < n && k < n) ? delta[(int64_t)k * ld_in + j] : 0.0;
     }
+    bool badv = false;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = bx + y + 8 * m;
+      badv |= beyond_float(v[m]);   // non-finite, or beyond the float range
+      if (en && j == k) v[m] = 0.0;
+      tile[x][y + 8 * m] = v[m];    // tile[j - by][k - bx]
+    }
+    if (badv) atomicExch(bad, 1u);
   }
   __syncthreads();
   const int k0 = bx + 2 * x;
