@@ -100,7 +100,12 @@ typedef struct {
   int32_t max_slices;      /* slices of Delta in the mixed path, 1..3 (default 3): that
                               many BF16 slices in grouped and complex solves; a real
                               single solve uses FP16 slices (11 significant bits each),
-                              two for max_slices 2 or 3 and one for 1 */
+                              two for max_slices 2 or 3 and one for 1.  The first
+                              products use all of them, and the slices represent Delta
+                              to about 2^-8 (BF16) or 2^-11 (FP16) relative per slice:
+                              fewer than the default bound the result's accuracy by
+                              that representation (the carried remainder makes up for
+                              the rounding of the increments, not for that of Delta) */
   int32_t profile;         /* nonzero: time every product kernel with CUDA events on
                               the stream it runs on (reported in dpt_info) */
   double slice_tol;        /* mixed path: the first product uses all its slices; a
