@@ -699,9 +699,9 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
     Prof prof;
     prof.on = o.profile != 0;
     prof.launches = 9;
-    CK(cudaMemcpyAsync(b->host_state, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    // run_loop reads k from host_state; DomState and IterState share the layout of k/status
+    // the loop starts at k = 0 (no host read of the state before it); it reads k and
+    // the status back after each chunk (DomState and IterState share the layout of
+    // k/status)
     run_loop(b, reinterpret_cast<IterState*>(st), o.graph_iters, o.max_iter, 2, prof,
              [&](int q) {
                prof.before(q, s);
@@ -709,7 +709,7 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
                                   z64[1], part, st, s));
                prof.after(q, s);
              },
-             sizeof(DomState));
+             sizeof(DomState), /*k_first=*/0);
     CK(launch_dom_out(n, zf[0], zf[1], z64[0], z64[1], ff, zstage, st, s));
     prof.launches += 1;
     if (!z_dev) CK(cudaMemcpyAsync(z_out, zstage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));

@@ -46,34 +46,58 @@ __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, f
 
 // ---------------------------------------------------------------------------
 // Set-up: theta -> float-float, residual scale row sums, CSR validity, argmax.
+// Eight consecutive lanes share a row: they read its indices and values eight
+// apart (a warp's load covers four rows' consecutive entries), sum |v| and reduce
+// with three shuffles; the group's first lane handles theta_m.
 // ---------------------------------------------------------------------------
-__global__ void k_dom_setup(int n, const double* __restrict__ theta,
-                            const int32_t* __restrict__ row_ptr,
-                            const int32_t* __restrict__ col_idx, const float* __restrict__ vals,
-                            float* __restrict__ th_hi, float* __restrict__ th_lo,
-                            DomState* st) {
+constexpr int SETUP_V = 8;
+
+__global__ void __launch_bounds__(256) k_dom_setup(int n, const double* __restrict__ theta,
+                                                   const int32_t* __restrict__ row_ptr,
+                                                   const int32_t* __restrict__ col_idx,
+                                                   const float* __restrict__ vals,
+                                                   float* __restrict__ th_hi,
+                                                   float* __restrict__ th_lo, DomState* st) {
   float rmax = 0.f, amax = 0.f;
   unsigned long long tmax = 0ull;
   bool bad = false;
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
-    const double t = theta[m];
-    if (!finite_bits(t)) bad = true;
-    float h, l;
-    split_double(t, h, l);
-    th_hi[m] = h;
-    th_lo[m] = l;
-    amax = fmaxf(amax, fabsf(h));
-    tmax = max(tmax, ordered_bits(t));
-    const int a = row_ptr[m], b = row_ptr[m + 1];
-    if (b < a) { bad = true; continue; }
+  const int g = threadIdx.x & (SETUP_V - 1);
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;   // a multiple of SETUP_V
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;; base += nthr) {
+    const int64_t m64 = base / SETUP_V;
+    const bool act = m64 < n;
+    if (__all_sync(0xffffffffu, !act)) break;   // the warp leaves together
     float rs = 0.f;
-    for (int q = a; q < b; ++q) {
-      const int c = col_idx[q];
-      const float v = vals[q];
-      if (c < 0 || c >= n || !(fabsf(v) <= 3.4e38f)) bad = true;
-      rs += fabsf(v);
+    if (act) {
+      const int m = (int)m64;
+      const int ra = row_ptr[m], rb = row_ptr[m + 1];
+      if (rb < ra) {
+        bad = true;
+      } else {
+        for (int q = ra + g; q < rb; q += SETUP_V) {
+          const int c = col_idx[q];
+          const float v = vals[q];
+          if (c < 0 || c >= n || !(fabsf(v) <= 3.4e38f)) bad = true;
+          rs += fabsf(v);
+        }
+      }
     }
-    rmax = fmaxf(rmax, rs);
+    // the group's lanes are aligned within the warp: xor 1, 2, 4 stay inside it
+    rs += __shfl_xor_sync(0xffffffffu, rs, 1);
+    rs += __shfl_xor_sync(0xffffffffu, rs, 2);
+    rs += __shfl_xor_sync(0xffffffffu, rs, 4);
+    if (act && g == 0) {
+      const int m = (int)m64;
+      const double t = theta[m];
+      if (!finite_bits(t)) bad = true;
+      float h, l;
+      split_double(t, h, l);
+      th_hi[m] = h;
+      th_lo[m] = l;
+      amax = fmaxf(amax, fabsf(h));
+      tmax = max(tmax, ordered_bits(t));
+      rmax = fmaxf(rmax, rs);
+    }
   }
   if (bad) atomicExch(&st->bad_input, 1u);
   for (int o = 16; o > 0; o >>= 1) {
@@ -449,7 +473,17 @@ cudaError_t launch_dom_check(int n, int64_t nnz, const int32_t* row_ptr, DomStat
 cudaError_t launch_dom_setup(int n, const double* theta, const int32_t* row_ptr,
                              const int32_t* col_idx, const float* vals, float* th_hi,
                              float* th_lo, DomState* st, cudaStream_t s) {
-  k_dom_setup<<<dom_grid(n), 256, 0, s>>>(n, theta, row_ptr, col_idx, vals, th_hi, th_lo, st);
+  // SETUP_V lanes per row, so SETUP_V times the rows' threads
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 132;
+  }
+  const int64_t want = ((int64_t)n * SETUP_V + 255) / 256;
+  const int grid = want < 8 * nsm ? (want > 0 ? (int)want : 1) : 8 * nsm;
+  k_dom_setup<<<grid, 256, 0, s>>>(n, theta, row_ptr, col_idx, vals, th_hi, th_lo, st);
   return launch_dom_select(n, theta, st, s);
 }
 
