@@ -4,8 +4,8 @@ scaling over independent problems).
 Workload: the dense real unsymmetric problem of size n = 4096 (theta sorted
 uniforms with every gap >= 0.5, Delta iid N(0, 1/n), lambda = 0.1), solved from
 A_0 = I to a normalised residual <= 1e-12 (well below the 1e-10 the metric asks
-for) with the mixed-precision path (tcgen05 BF16 products, FP32 accumulation,
-extended-precision state).  One step = one complete solve through the C ABI
+for) with the mixed-precision path (tcgen05 products on FP16 operands with
+power-of-two scales, FP32 accumulation, extended-precision state).  One step = one complete solve through the C ABI
 with the inputs already resident in HBM; L2 is flushed between steps.
 
 The JSON line also carries the plain-FP64 comparator (same problem, same
