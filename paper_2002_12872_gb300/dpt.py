@@ -283,8 +283,10 @@ def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
 class FullSolve:
     """dpt_solve_full with its arguments marshalled once, for repeated solves of the
     same buffers (the library reads theta and Delta and writes A and E in place on
-    every call).  Keyword options are those of solve_full; solve() returns the info
-    dict and raises RuntimeError on a status other than OK unless check=False."""
+    every call).  Keyword options are those of solve_full; the stream is fixed here
+    (`stream`, else the current stream of Delta's device at construction).  solve()
+    returns the info dict and raises RuntimeError on a status other than OK unless
+    check=False."""
 
     def __init__(self, theta, delta, lam, *, A_out=None, E_out=None, stream=None, **opts):
         cplx = _iscomplex(delta)
