@@ -115,8 +115,9 @@ def test_selftest_and_server_arguments_rejected_without_gpu(lib):
 
 def test_workspace_bytes_without_gpu(lib):
     """dpt_workspace_bytes is host arithmetic over the solves' carve layouts: about
-    30 B per element for the mixed real solve (BF16 slices 6, float-float A and its
-    copy 16, BF16 increments 4, remainder 4), 3 n^2 doubles per real component for
+    30 B per element for the mixed real solve (room for three FP16 slices 6,
+    float-float A and its copy 16, FP16 increments 4, remainder 4), 3 n^2 doubles per
+    real component for
     the FP64 map, and -1 outside its domain."""
     from paper_2002_12872_gb300 import dpt
     for n in (256, 4096, 8192):
