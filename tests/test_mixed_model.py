@@ -1,0 +1,193 @@
+"""A NumPy model of the rounding in the mixed full solve (not the oracle, and not the
+CUDA path): the increment recursion of the map of Eq. (dyn) (Sec. II.B) with a carried
+remainder, Delta split into 16-bit slices, the increments rounded to 16 bits, and the
+tensor core's FP32 accumulation truncated every 16 products.  It backs two design
+choices of the mixed path with numbers that can be rerun on a CPU:
+
+* two FP16 slices of Delta 2^sig (22 bits) with FP16 increments under power-of-two
+  scales reach the FP64 fixed point as closely as three BF16 slices (24 bits) with
+  BF16 increments, and need fewer slice-products;
+* a strongly coupled problem (the 2 x 2 of Sec. II.E at lambda = 0.3) carries
+  residuals large enough that the recursion, run in float, lands between 1e-10 and
+  1e-9 from the fixed point depending on the order of its roundings (this model,
+  without fused multiply-adds, gives 3e-9 on E_0), while a weakly coupled one does
+  not: the sum of carried residuals separates the two, which is the test the mixed
+  solve uses to finish strongly coupled problems with plain FP64 steps.
+"""
+import numpy as np
+
+from paper_2002_12872_gb300 import inputs
+
+
+def _bf16(x):
+    x = np.asarray(x, np.float32)
+    b = x.view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _f16(x):
+    return np.float16(np.clip(x, -65504.0, 65504.0)).astype(np.float64)
+
+
+def _trunc32(x):
+    f = x.astype(np.float32)
+    over = np.abs(f.astype(np.float64)) > np.abs(x)
+    f[over] = np.nextafter(f[over], np.float32(0))
+    return f.astype(np.float64)
+
+
+def _fixed_point(theta, D, lam):
+    """The map iterated in FP64 (numpy products) to its fixed point."""
+    n = len(theta)
+    gap = theta[None, :] - theta[:, None]
+    off = ~np.eye(n, dtype=bool)
+    G = np.zeros_like(gap)
+    G[off] = 1.0 / gap[off]
+    A = np.eye(n)
+    for _ in range(200):
+        P = D @ A
+        An = np.eye(n) + lam * G * (P - A * np.diag(P)[None, :])
+        if np.max(np.abs(An - A)) < 1e-16:
+            return An, theta + lam * np.diag(D @ An)
+        A = An
+    return A, theta + lam * np.diag(D @ A)
+
+
+def _product(slices, dtq):
+    """sum_sl slice @ dtq with FP32 accumulation truncated every 16 terms, small
+    slices first (the kernel's order, without its per-tile rotation)."""
+    n = dtq.shape[0]
+    acc = np.zeros((slices[0].shape[0], dtq.shape[1]))
+    for sl in reversed(slices):
+        for g0 in range(0, n, 16):
+            acc = _trunc32(acc + sl[:, g0:g0 + 16] @ dtq[g0:g0 + 16, :])
+    return acc
+
+
+def _model(theta, D, lam, fmt, tol=1e-12):
+    """Returns (A, E, slice-products, sum of rho_k for k >= 1)."""
+    n = len(theta)
+    gap = theta[None, :] - theta[:, None]
+    off = ~np.eye(n, dtype=bool)
+    G = np.zeros_like(gap)
+    G[off] = 1.0 / gap[off]
+    s_scale = np.abs(theta).max() + abs(lam) * np.abs(D).sum(axis=1).max()
+    if fmt == "bf16":
+        hi = D.astype(np.float32).astype(np.float64)
+        s1 = _bf16(hi)
+        s2 = _bf16(hi - s1)
+        s3 = _bf16(hi - s1 - s2 + (D - hi))
+        slices, unsc, bits, S0 = [s1, s2, s3], 1.0, 8, 3
+        rnd = lambda q, s: _bf16(q)
+    else:
+        sig = 14 - int(np.floor(np.log2(np.max(np.abs(D)))))
+        x = D * 2.0 ** sig
+        s1 = _f16(x)
+        s2 = _f16(x - s1)
+        slices, unsc, bits, S0 = [s1, s2], 2.0 ** -sig, 11, 2
+        rnd = lambda q, s: _f16(q * 2.0 ** s) * 2.0 ** -s
+    R = lam * D * off
+    ref = abs(lam) * np.max(np.abs(D * off) * np.abs(G))
+    sexp = 13 - int(np.floor(np.log2(ref)))
+    dt = rnd(G * R, sexp) * off
+    L = R - gap * dt
+    A = np.eye(n) + dt
+    e = np.einsum("ij,ji->i", sum(slices) * unsc, dt)
+    dprev, d = np.diag(D).copy(), np.diag(D) + e
+    d1 = np.max(np.abs(dt))
+    used, rho_sum = 0, 0.0
+    for k in range(1, 40):
+        dm = np.max(np.abs(dt))
+        S = S0
+        while S > 1 and dm <= d1 * 2.0 ** (-bits * (S0 - S + 1)):
+            S -= 1
+        used += S
+        X = _product(slices[:S], dt * 2.0 ** sexp) * unsc * 2.0 ** -sexp
+        Rk = (L + lam * (X - A * e[None, :] - dt * dprev[None, :])) * off
+        rho = np.max(np.sqrt(np.sum(Rk ** 2, axis=0) / np.sum(A ** 2, axis=0))) / s_scale
+        rho_sum += rho
+        if rho <= tol:
+            return A, theta + lam * d, used, rho_sum
+        sexp = 10 - int(np.floor(np.log2(dm)))
+        dtn = rnd(G * Rk, sexp) * off
+        L = Rk - gap * dtn
+        en = np.einsum("ij,ji->i", sum(slices[:S]) * unsc, dtn)
+        A, dprev, d, e, dt = A + dtn, d.copy(), d + en, en, dtn
+    raise AssertionError("model did not converge")
+
+
+def _errs(A, E, Ar, Er):
+    un = lambda X: X / np.linalg.norm(X, axis=0)
+    return (float(np.max(np.linalg.norm(un(A) - un(Ar), axis=0))),
+            float(np.max(np.abs(E - Er) / np.maximum(1.0, np.abs(Er)))))
+
+
+def test_two_fp16_slices_match_three_bf16_slices():
+    cfg = inputs.full_unsymmetric(n=192)
+    th, D, lam = cfg["theta"], np.asarray(cfg["delta"]), cfg["lam"]
+    Ar, Er = _fixed_point(th, D, lam)
+    Ab, Eb, used_b, _ = _model(th, D, lam, "bf16")
+    Af, Ef, used_f, _ = _model(th, D, lam, "fp16")
+    vb, eb = _errs(Ab, Eb, Ar, Er)
+    vf, ef = _errs(Af, Ef, Ar, Er)
+    # both within the parity bar (eigenvalues 1e-10, eigenvectors 1e-9), the FP16
+    # model within a small factor of the BF16 one, with fewer slice-products
+    assert vb <= 1e-9 and vf <= 1e-9 and eb <= 1e-10 and ef <= 1e-10, (vb, vf, eb, ef)
+    assert vf <= 4 * vb + 1e-12
+    assert used_f < used_b
+
+
+def _float_recursion_2x2(lam):
+    """The 2 x 2 of Sec. II.E (theta = (0, 1), Delta = [[0, 1], [1, 0]]) through the
+    recursion with every operation of the epilogue in float32 and FP16 increments
+    under the same power-of-two scales; returns (error of E_0, sum of rho_k).  With
+    this Delta the product Delta dt has no off-diagonal entries (dt has no diagonal),
+    so only the float arithmetic of the update rounds."""
+    f = np.float32
+    th = (0.0, 1.0)
+    em = (1 - np.sqrt(1 + 4 * lam * lam)) / 2
+    lh = f(lam)
+    pairs = ((1, 0), (0, 1))                      # (row j, column i) off the diagonal
+    gap = {(j, i): f(th[i] - th[j]) for (j, i) in pairs}
+    s0 = 13 - int(np.floor(np.log2(abs(lam))))
+    dt, L, Ah = {}, {}, {}
+    for (j, i) in pairs:                         # iteration 0: R_0 = lambda Delta_ji
+        q = f(f(lh / gap[(j, i)]) * f(2.0 ** s0))
+        dt[(j, i)] = f(np.float16(q)) / f(2.0 ** s0)
+        L[(j, i)] = f(lh - f(gap[(j, i)] * dt[(j, i)]))
+        Ah[(j, i)] = dt[(j, i)]
+    e = [float(dt[(1, 0)]), float(dt[(0, 1)])]   # diag(Delta dt_0)
+    dprev, d = [0.0, 0.0], list(e)
+    rho_sum = 0.0
+    for _ in range(60):
+        R = {}
+        for (j, i) in pairs:
+            Y = f(f(-f(Ah[(j, i)] * f(e[i]))) - f(dt[(j, i)] * f(dprev[i])))
+            R[(j, i)] = f(L[(j, i)] + f(lh * Y))
+        rho = max(abs(float(v)) for v in R.values()) / 1.3
+        rho_sum += rho
+        if rho <= 1e-12:
+            break
+        s = 10 - int(np.floor(np.log2(max(abs(float(v)) for v in dt.values()))))
+        dtn = {}
+        for (j, i) in pairs:
+            q = f(f(R[(j, i)] / gap[(j, i)]) * f(2.0 ** s))
+            dtn[(j, i)] = f(np.float16(q)) / f(2.0 ** s)
+            L[(j, i)] = f(R[(j, i)] - f(gap[(j, i)] * dtn[(j, i)]))
+            Ah[(j, i)] = f(Ah[(j, i)] + dtn[(j, i)])
+        en = [float(dtn[(1, 0)]), float(dtn[(0, 1)])]
+        dprev, d, e, dt = list(d), [d[0] + en[0], d[1] + en[1]], en, dtn
+    return abs(th[0] + lam * d[0] - em), rho_sum
+
+
+def test_float_recursion_floor_and_the_strong_coupling_test():
+    err, rho_sum = _float_recursion_2x2(0.3)
+    # the float recursion's floor is far above FP64 rounding for this problem, and
+    # the carried residuals flag it (2^-23 * sum rho above 1e-11)
+    assert err > 1e-12
+    assert rho_sum * 2.0 ** -23 > 1e-11
+    # a weakly coupled problem of the workloads carries small residuals
+    cfg = inputs.full_unsymmetric(n=192)
+    _, _, _, rho_w = _model(cfg["theta"], np.asarray(cfg["delta"]), cfg["lam"], "fp16")
+    assert rho_w * 2.0 ** -23 < 1e-11
