@@ -473,6 +473,12 @@ def bench_batched(dpt, inputs, dev, steps=3, warmup=2):
     D = [dpt.colmajor_tensor(p["delta"], dev) for p in probs]
     lams = [p["lam"] for p in probs]
     batch = dpt.Batch(th, D, lams)          # argument arrays built once, outside the timing
+    # tile shape (grouped product form) chosen by the library's tuner on this group,
+    # outside the timing; the timed solves use it
+    try:
+        form, tune_ms = batch.tune()
+    except RuntimeError as e:               # the default form then
+        form, tune_ms = None, {"error": str(e)}
     for _ in range(warmup):
         batch.solve()
     torch.cuda.synchronize()
@@ -506,6 +512,8 @@ def bench_batched(dpt, inputs, dev, steps=3, warmup=2):
     return {"workload": "20,000 dense symmetric problems, n log-uniform [32, 512], "
                         "lambda U[0.01, 0.1], tol=1e-12",
             "solves_per_s": 20000 * 1e3 / ms, "ms_per_batch": ms,
+            "grouped_form": form,
+            "tuner_product_ms_by_form": {str(f): v for f, v in tune_ms.items()},
             "fp64_comparator": fp64,
             "iters_mean": float(np.mean(its)), "iters_max": int(np.max(its)),
             "product_ms_per_launch": infos[0]["product_ms"] / max(1, infos[0]["product_launches"]),

@@ -238,6 +238,29 @@ DPT_API dpt_status dpt_solve_batched(int64_t count, dpt_dtype dtype, const int64
                                      const int64_t* ld_a, double* const* E_out,
                                      dpt_info* infos, void* stream);
 
+/* Tile-shape autotuner for grouped solves.  Runs the group once with each form of the
+ * grouped product (dpt_options.grouped_form 1: 128-row tiles up to 256 columns wide, the
+ * epilogue reading its inputs from global memory; 2: 128-row tiles up to 128 wide with
+ * the epilogue inputs staged in shared memory; 3: 256-row CTA-pair tiles up to 224 wide),
+ * each with per-launch timing of its product kernels, and returns the form whose product
+ * launches took the least device time in total.  Pass it as opt->grouped_form to later
+ * dpt_solve_batched calls on groups like this one (a problem's result depends on the
+ * form, through the tile boundaries of its accumulation order, within the tolerance).
+ * Arguments as for dpt_solve_batched (opt->grouped_form and opt->profile are set here);
+ * the outputs hold the converged result of the last form tried.
+ *   best_form  out: 1, 2 or 3 (0 when no form converged)
+ *   form_ms    optional out, 3 doubles: each form's summed product time in ms, or -1
+ *              for a form that did not converge or ran as another form (form 3 runs
+ *              as 2 where clusters of two cannot be resident)
+ * Returns DPT_OK when some form converged for every problem, else the last form's
+ * status (DPT_ERR_ARG / DPT_ERR_UNSUPPORTED at once).  Blocks until done. */
+DPT_API dpt_status dpt_tune_batched(int64_t count, dpt_dtype dtype, const int64_t* n,
+                                    const double* const* theta, const double* const* delta,
+                                    const int64_t* ld_delta, const double* lambda,
+                                    const dpt_options* opt, double* const* A_out,
+                                    const int64_t* ld_a, double* const* E_out,
+                                    int32_t* best_form, double* form_ms, void* stream);
+
 /* Device workspace, in bytes, that one dpt_solve_full call of size n takes from the
  * library's pool with the default options and with theta, Delta, A and E in device
  * memory (host buffers add their staging copies: about 8 n^2 bytes each for Delta

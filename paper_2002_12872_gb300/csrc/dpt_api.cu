@@ -1810,6 +1810,41 @@ dpt_status dpt_solve_batched(int64_t count, dpt_dtype dtype, const int64_t* n,
   }
 }
 
+dpt_status dpt_tune_batched(int64_t count, dpt_dtype dtype, const int64_t* n,
+                            const double* const* theta, const double* const* delta,
+                            const int64_t* ld_delta, const double* lambda,
+                            const dpt_options* opt, double* const* A_out, const int64_t* ld_a,
+                            double* const* E_out, int32_t* best_form, double* form_ms,
+                            void* stream) {
+  if (!best_form || count < 1 || count > (1 << 24)) return DPT_ERR_ARG;
+  *best_form = 0;
+  dpt_options o;
+  dpt_options_default(&o);
+  if (opt) o = *opt;
+  o.profile = 1;
+  std::vector<dpt_info> infos((size_t)count);
+  dpt_status last = DPT_ERR_ARG;
+  double best = INFINITY;
+  // each tile shape in turn on the caller's own group: 128 x (<= 256) tiles reading the
+  // epilogue inputs from global memory, 128 x (<= 128) tiles with staged inputs, and
+  // 256 x (<= 224) CTA-pair tiles
+  for (int f = G_PLAIN; f <= G_PAIR; ++f) {
+    o.grouped_form = f;
+    const dpt_status st = dpt_solve_batched(count, dtype, n, theta, delta, ld_delta, lambda, &o,
+                                            A_out, ld_a, E_out, infos.data(), stream);
+    // a form that ran as another one (clusters of two not resident) is not timed as itself
+    const double ms = (st == DPT_OK && infos[0].grouped_form == f) ? infos[0].product_ms : -1.0;
+    if (form_ms) form_ms[f - 1] = ms;
+    if (ms >= 0.0 && ms < best) {
+      best = ms;
+      *best_form = f;
+    }
+    last = st;
+    if (st == DPT_ERR_ARG || st == DPT_ERR_UNSUPPORTED) return st;   // the same for every form
+  }
+  return *best_form ? DPT_OK : last;
+}
+
 void dpt_release_workspace(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   int dev = -1;

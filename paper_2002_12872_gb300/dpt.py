@@ -121,6 +121,9 @@ def lib() -> ctypes.CDLL:
         L.dpt_solve_batched.argtypes = [i64, ctypes.c_int, P, P, P, P, P,
                                         ctypes.POINTER(Options), P, P, P, P, P]
         L.dpt_solve_batched.restype = ctypes.c_int
+        L.dpt_tune_batched.argtypes = [i64, ctypes.c_int, P, P, P, P, P,
+                                       ctypes.POINTER(Options), P, P, P, P, P, P]
+        L.dpt_tune_batched.restype = ctypes.c_int
         L.dpt_server_cfg_default.argtypes = [ctypes.POINTER(ServerCfg)]
         L.dpt_server_cfg_default.restype = None
         L.dpt_server_create.argtypes = [ctypes.POINTER(ServerCfg), ctypes.POINTER(P)]
@@ -400,10 +403,32 @@ class Batch:
         self._lda = (ctypes.c_int64 * count)(*[a.stride(1) for a in A_outs])
         self._e = (P * count)(*[e.data_ptr() for e in E_outs])
         self._dev = thetas[0]
+        self.form = None      # the tile shape tune() chose, used by solve() by default
+
+    def tune(self, *, tol=1e-12, max_iter=200, graph_iters=None, max_slices=None,
+             slice_tol=None, stream=None):
+        """dpt_tune_batched: runs this group with each grouped product form and keeps
+        the one with the least product time for later solve() calls.  Returns
+        (best_form, {form: summed product ms, or -1})."""
+        o = options(tol=tol, max_iter=max_iter, prec="mixed", graph_iters=graph_iters,
+                    max_slices=max_slices, slice_tol=slice_tol)
+        best = ctypes.c_int32(0)
+        ms = (ctypes.c_double * 3)()
+        st = lib().dpt_tune_batched(self.count, C128 if self.cplx else R64, self._n, self._th,
+                                    self._d, self._ldd, self._lam, ctypes.byref(o), self._a,
+                                    self._lda, self._e, ctypes.byref(best), ms,
+                                    _stream_of(self._dev, stream))
+        if st != OK:
+            raise RuntimeError(f"dpt_tune_batched: {status_string(st)}")
+        self.form = int(best.value)
+        return self.form, {f: float(ms[f - 1]) for f in (1, 2, 3)}
 
     def solve(self, *, tol=1e-12, max_iter=200, graph_iters=None, max_slices=None,
               slice_tol=None, profile=False, form=None, stream=None, check=True):
-        """Returns (A_outs, E_outs, infos).  form: the product form (grouped_form)."""
+        """Returns (A_outs, E_outs, infos).  form: the product form (grouped_form);
+        by default the one tune() chose, if it ran."""
+        if form is None:
+            form = self.form
         infos = (Info * self.count)()
         o = options(tol=tol, max_iter=max_iter, prec="mixed", graph_iters=graph_iters,
                     max_slices=max_slices, slice_tol=slice_tol, profile=int(bool(profile)),

@@ -93,6 +93,29 @@ def test_invalid_arguments_rejected_without_gpu(lib):
               ctypes.byref(info), None) == -1
 
 
+def test_tuner_arguments_rejected_without_gpu(lib):
+    """dpt_tune_batched validates like dpt_solve_batched and stops at the first
+    argument error, before any CUDA call."""
+    from paper_2002_12872_gb300 import dpt
+    th, d, A, E = np.zeros(4), np.zeros((4, 4), order="F"), np.zeros((4, 4), order="F"), np.zeros(4)
+    P = ctypes.c_void_p
+    n = (ctypes.c_int64 * 1)(4)
+    ths, ds, As, Es = ((P * 1)(x.ctypes.data) for x in (th, d, A, E))
+    ld = (ctypes.c_int64 * 1)(4)
+    lam = (ctypes.c_double * 1)(0.1)
+    o = dpt.options()
+    best = ctypes.c_int32(7)
+    ms = (ctypes.c_double * 3)(5.0, 5.0, 5.0)
+    tb = lib.dpt_tune_batched
+    assert tb(0, 0, n, ths, ds, ld, lam, ctypes.byref(o), As, ld, Es, ctypes.byref(best), ms,
+              None) == -1
+    assert tb(1, 0, n, ths, ds, ld, lam, ctypes.byref(o), As, ld, Es, None, ms, None) == -1
+    n0 = (ctypes.c_int64 * 1)(0)
+    assert tb(1, 0, n0, ths, ds, ld, lam, ctypes.byref(o), As, ld, Es, ctypes.byref(best), ms,
+              None) == -1
+    assert best.value == 0 and ms[0] == -1.0
+
+
 def test_selftest_and_server_arguments_rejected_without_gpu(lib):
     from paper_2002_12872_gb300 import dpt
     assert lib.dpt_selftest_bounded_wait(0.0, None) == -1

@@ -103,3 +103,33 @@ def test_batched_other_product_forms(ora, dpt, form):
         assert inf["status"] == "OK"
         assert eig_err(to_np(E), Eo) <= EIG_RTOL, (len(Eo), inf)
         assert vec_err(to_np(A), Ao) <= VEC_TOL, (len(Eo), inf)
+
+
+def test_tuner_keeps_the_fastest_tile_shape(ora, dpt):
+    """dpt_tune_batched runs the group with each product form (tile shape), keeps the
+    one with the least product time, and later solves of the group use it: their
+    results equal a direct solve with that form bit for bit and match the oracle."""
+    rng = np.random.Generator(np.random.PCG64(48))
+    sizes = [2, 33, 100, 129, 257, 400]
+    probs = []
+    for n in sizes:
+        th = np.arange(n, dtype=float) + rng.uniform(-0.2, 0.2, n)
+        probs.append({"theta": th, "delta": inputs.symmetric_gaussian(n, 1.0 / n, rng),
+                      "lam": float(rng.uniform(0.01, 0.1))})
+    th, D = _dev(probs, dpt)
+    lams = [p["lam"] for p in probs]
+    batch = dpt.Batch(th, D, lams)
+    best, ms = batch.tune()
+    assert best in (1, 2, 3) and batch.form == best
+    timed = {f: v for f, v in ms.items() if v >= 0}
+    assert best in timed and timed[best] == min(timed.values())
+    As, Es, infos = batch.solve()
+    assert all(i["grouped_form"] == best and i["status"] == "OK" for i in infos)
+    As = [a.clone() for a in As]
+    Es = [e.clone() for e in Es]
+    A2, E2, _ = dpt.solve_batched(th, D, lams, form=best)
+    for q, p in enumerate(probs):
+        assert torch.equal(As[q], A2[q]) and torch.equal(Es[q], E2[q])
+        Ao, Eo, io = ora.solve_full(p["theta"], p["delta"], p["lam"], tol=1e-13)
+        assert eig_err(to_np(Es[q]), Eo) <= EIG_RTOL
+        assert vec_err(to_np(As[q]), Ao) <= VEC_TOL
