@@ -1,10 +1,11 @@
 """The oracle's pins must catch plausible mistakes.  Each mutant below is a copy
 of the oracle's C source with one planted error (a dropped term, a flipped sign,
 a transposed operand, a missing factor), compiled on the CPU into a temporary
-library.  Every mutant must fail at least one of three pins that the real oracle
+library.  Every mutant must fail at least one of the pins that the real oracle
 passes: the exact 2x2 iterates (Sec. II.E), the printed 3x3 polynomials
-(Supplement E), and the trace and right-eigenvector residual of an unsymmetric
-problem (M a = E a, Sec. II.A)."""
+(Supplement E), the trace and right-eigenvector residual of an unsymmetric
+problem (M a = E a, Sec. II.A), and the hand-computed normalised residuals of
+tests/test_oracle_residual.py (full and single-vector forms)."""
 import ctypes
 import os
 import shutil
@@ -28,17 +29,33 @@ MUTANTS = {
         "const T lam_map = ramp_alpha > 0.0 ? lambda * (1.0 - pw) : lambda;\n      pw *= ramp_alpha;",
         "pw *= ramp_alpha;\n      const T lam_map = ramp_alpha > 0.0 ? lambda * (1.0 - pw) : lambda;"),
     "ramp_in_eigenvalue": ("E[c] = theta[i] + lambda * d;", "E[c] = theta[i] + lam_map * d;"),
+    # the normalisation of the residual (the stopping rule and the metric's bar)
+    "residual_without_scale": ("const double v = sqrt(rr) / (s * sqrt(aa));",
+                               "const double v = sqrt(rr) / sqrt(aa);"),
+    "residual_without_norm_a": ("const double v = sqrt(rr) / (s * sqrt(aa));",
+                                "const double v = sqrt(rr) / s;"),
+    "scale_column_sums": ("for (int64_t k = 0; k < n; ++k) row += ABS(delta[j + k * n]);",
+                          "for (int64_t k = 0; k < n; ++k) row += ABS(delta[k + j * n]);"),
+    "scale_without_lambda": ("return tmax + ABS(lambda) * rmax;", "return tmax + rmax;"),
+    "scale_signed_lambda": ("return tmax + ABS(lambda) * rmax;",
+                            "return tmax + creal(lambda) * rmax;"),
+    "scale_signed_theta": ("if (ABS(theta[j]) > tmax) tmax = ABS(theta[j]);",
+                           "if (creal(theta[j]) > tmax) tmax = creal(theta[j]);"),
+    "dominant_scale_without_lambda": ("const double s = tmax + fabs(lambda) * rmax;",
+                                      "const double s = tmax + rmax;", "dpt_oracle.c"),
+    "dominant_residual_without_scale": ("rho = sqrt(rr) / (s * sqrt(zz));",
+                                        "rho = sqrt(rr) / sqrt(zz);", "dpt_oracle.c"),
 }
 
 
-def _build(tmp, name, old, new):
+def _build(tmp, name, old, new, target="dpt_oracle_body.inc"):
     d = os.path.join(tmp, name)
     os.makedirs(d)
     for f in ("dpt_oracle.c", "dpt_oracle_body.inc", "dpt_oracle.h"):
         shutil.copy(os.path.join(ORA, f), d)
-    body = open(os.path.join(d, "dpt_oracle_body.inc")).read()
+    body = open(os.path.join(d, target)).read()
     assert old in body, name
-    open(os.path.join(d, "dpt_oracle_body.inc"), "w").write(body.replace(old, new))
+    open(os.path.join(d, target), "w").write(body.replace(old, new))
     so = os.path.join(d, "lib.so")
     subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", so,
                     os.path.join(d, "dpt_oracle.c"), "-lm"], check=True,
@@ -48,7 +65,44 @@ def _build(tmp, name, old, new):
     lib.ora_step_r.argtypes = [i64, P, P, dbl, P, P, P]
     lib.ora_solve_full_r.argtypes = [i64, P, P, dbl, i64, P, dbl, i64, ctypes.c_int, dbl,
                                      P, P, P, P]
+    lib.ora_residual_r.argtypes = [i64, P, P, dbl, P, P, P]
+    lib.ora_residual_r.restype = dbl
+    lib.ora_solve_dominant_csr.argtypes = [i64, P, P, P, P, i64, dbl, dbl, i64, dbl, P, P,
+                                           P, P]
     return lib
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("residual", ctypes.c_double),
+                ("status", ctypes.c_int64)]
+
+
+def _residual_pins_pass(lib):
+    """The hand-computed residuals of tests/test_oracle_residual.py: the 3 x 3 at
+    A = I (s = 3 + 0.1 * 4.25 from the largest row sum, |theta| and |lambda|) and
+    with a non-unit column, and the single-vector oracle at its start."""
+    p = lambda x: x.ctypes.data_as(ctypes.c_void_p)
+    th = np.ascontiguousarray([0.0, 1.0, -3.0])
+    D = np.asfortranarray([[0.0, 2.0, -1.0], [0.5, 1.0, 0.0], [-4.0, 0.0, 0.25]])
+    s3 = 3.0 + 0.1 * 4.25
+    for A, E, want in (
+            (np.eye(3), [0.0, 0.9, -3.025], [0.1 * np.sqrt(16.25), 0.2, 0.1]),
+            ([[1.0, 0.0, 0.0], [2.0, 1.0, 0.0], [0.0, 0.0, 1.0]], [1.0, 0.9, -3.025],
+             [np.sqrt(1.4**2 + 0.25**2 + 0.4**2) / np.sqrt(5.0), 0.2, 0.1])):
+        A = np.asfortranarray(A, float)
+        E = np.ascontiguousarray(E, float)
+        rho = np.zeros(3)
+        lib.ora_residual_r(3, p(th), p(D), -0.1, p(A), p(E), p(rho))
+        if not np.allclose(rho, np.array(want) / s3, rtol=1e-13, atol=0):
+            return False
+    row_ptr = np.array([0, 2, 4, 6], dtype=np.int32)
+    col_idx = np.array([1, 2, 0, 1, 0, 2], dtype=np.int32)
+    vals = np.array([2.0, -1.0, 0.5, 1.0, -4.0, 0.25], dtype=np.float32)
+    z, Eo, info = np.zeros(3), np.zeros(1), _Info()
+    lib.ora_solve_dominant_csr(3, p(th), p(row_ptr), p(col_idx), p(vals), -1, -0.1, 1e-300, 0,
+                               0.0, None, p(z), p(Eo), ctypes.cast(ctypes.pointer(info),
+                                                                   ctypes.c_void_p))
+    return bool(abs(info.residual - 0.2 / s3) <= 1e-14 * (0.2 / s3))
 
 
 def _solve_ramp(lib, th, D, lam, alpha, max_iter):
@@ -78,6 +132,8 @@ def _step(lib, th, D, lam, A):
 
 
 def _pins_pass(lib):
+    if not _residual_pins_pass(lib):
+        return False
     # 0. the non-autonomous iteration's A_2 in closed form: I + lam (1 - alpha) G o Delta
     #    (zero-diagonal Delta), and E of the iterate read out at the full lambda
     th0 = np.array([0.0, 1.0, 3.0])
@@ -148,6 +204,5 @@ def test_unmutated_copy_passes(tmp_path):
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_mutant_is_caught(tmp_path, name):
-    old, new = MUTANTS[name]
-    lib = _build(str(tmp_path), name, old, new)
+    lib = _build(str(tmp_path), name, *MUTANTS[name])
     assert not _pins_pass(lib), name
