@@ -31,7 +31,9 @@
  *     and nothing is thrown across this boundary.  On an error the outputs are
  *     unspecified, except that *info (when non-NULL) is filled.
  *   - Calls on different streams may run concurrently; each call uses its own
- *     scratch block from the pool.
+ *     scratch block from the pool.  The one exception is
+ *     dpt_solve_dominant_noalloc, whose calls share a single fixed block and must
+ *     not overlap on the GPU.
  */
 #ifndef DPT_H
 #define DPT_H
@@ -76,14 +78,18 @@ typedef enum {
 typedef enum {
   DPT_PREC_FP64 = 0,        /* every product in FP64 on the CUDA cores: the map of
                                Eq. (dyn) applied literally */
-  DPT_PREC_MIXED_BF16 = 1   /* tensor-core products: each iteration multiplies Delta,
+  DPT_PREC_MIXED = 1        /* tensor-core products: each iteration multiplies Delta,
                                split into 16-bit slices, by the 16-bit increment of
                                A, with FP32 accumulation (real single solves: FP16
                                slices and increments with power-of-two scales;
                                complex and grouped solves: BF16); A, the residual
                                and the eigenvalues are carried in extended
                                precision, so the iteration refines to the FP64
-                               fixed point */
+                               fixed point.  There is no TF32 variant: on this GPU
+                               the TF32 tensor rate is half the 16-bit rate and a
+                               TF32 operand takes twice the bytes, while two scaled
+                               FP16 slices already carry 22 significant bits of
+                               Delta (a TF32 value carries 11) */
 } dpt_prec;
 
 typedef struct {
@@ -92,7 +98,7 @@ typedef struct {
                               s = max|theta| + |lambda| max_j sum_k |Delta_jk|.
                               Default 1e-12. */
   int32_t max_iter;        /* maximum map applications (default 200) */
-  int32_t prec;            /* dpt_prec (default DPT_PREC_MIXED_BF16) */
+  int32_t prec;            /* dpt_prec (default DPT_PREC_MIXED) */
   int32_t epstein_nesbet;  /* nonzero: move lambda*diag(Delta) into theta first
                               (the partition of Sec. II.H); same eigenpairs */
   int32_t graph_iters;     /* iterations per captured CUDA graph replay between
@@ -228,7 +234,7 @@ DPT_API dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* thet
  *   A_out[p], E_out[p]   device outputs as for dpt_solve_full (leading dimension ld_a[p])
  *   infos[p]     optional per-problem diagnostics (status of each problem)
  * All pointers must be device pointers (DPT_ERR_UNSUPPORTED otherwise); only
- * opt->prec == DPT_PREC_MIXED_BF16 without the Epstein-Nesbet shift is supported.
+ * opt->prec == DPT_PREC_MIXED without the Epstein-Nesbet shift is supported.
  * Returns DPT_OK when every problem converged, else the first failing problem's
  * status (infos[p] tells which).  Blocks until done. */
 DPT_API dpt_status dpt_solve_batched(int64_t count, dpt_dtype dtype, const int64_t* n,
@@ -238,11 +244,12 @@ DPT_API dpt_status dpt_solve_batched(int64_t count, dpt_dtype dtype, const int64
                                      const int64_t* ld_a, double* const* E_out,
                                      dpt_info* infos, void* stream);
 
-/* Tile-shape autotuner for grouped solves.  Runs the group once with each form of the
+/* Tile-shape autotuner for grouped solves.  Runs the group twice with each form of the
  * grouped product (dpt_options.grouped_form 1: 128-row tiles up to 256 columns wide, the
  * epilogue reading its inputs from global memory; 2: 128-row tiles up to 128 wide with
  * the epilogue inputs staged in shared memory; 3: 256-row CTA-pair tiles up to 224 wide),
- * each with per-launch timing of its product kernels, and returns the form whose product
+ * the first run untimed (it absorbs the form's one-time set-up costs), the second with
+ * per-launch timing of its product kernels, and returns the form whose product
  * launches took the least device time in total.  Pass it as opt->grouped_form to later
  * dpt_solve_batched calls on groups like this one (a problem's result depends on the
  * form, through the tile boundaries of its accumulation order, within the tolerance).
@@ -282,7 +289,7 @@ DPT_API int64_t dpt_workspace_bytes(int64_t n, dpt_dtype dtype, dpt_prec prec);
  *   vals       nnz float (FP32 values; used exactly, promoted to the working precision)
  *   nstar      eigenvector index, or -1 for the first index of max theta
  *   lambda     real perturbation strength
- *   opt        options (prec: DPT_PREC_MIXED_BF16 = float-float working precision
+ *   opt        options (prec: DPT_PREC_MIXED = float-float working precision
  *              on the FP32 pipes, DPT_PREC_FP64 = plain FP64 arithmetic)
  *   z_out      n doubles: the eigenvector with z_out[n*] = 1
  *   E_out      one double: E = theta_{n*} + lambda (Delta z)_{n*}
@@ -350,7 +357,7 @@ DPT_API dpt_status dpt_solve_homotopy(int64_t n, const double* theta, const doub
  *              host or device; a host matrix is first copied to the device
  *   ld_delta   leading dimension, >= n
  *   nstar, lambda, opt, z_out, E_out, info   as for dpt_solve_dominant
- *              (prec DPT_PREC_MIXED_BF16: each FP64 entry is split exactly enough
+ *              (prec DPT_PREC_MIXED: each FP64 entry is split exactly enough
  *              into two floats and the products summed in float-float on the FP32
  *              pipes; DPT_PREC_FP64: plain FP64 arithmetic)
  * A non-finite entry of Delta gives DPT_ERR_ARG (detected during the first pass,
@@ -366,13 +373,13 @@ DPT_API dpt_status dpt_solve_dominant_dense(int64_t n, const double* theta, cons
  * point has no counterpart in the paper; it is a deployment variant of
  * dpt_solve_dominant.)
  *
- * Some callers may not call cudaMalloc at all: code running inside a host callback
- * or while another component is capturing a CUDA graph, processes whose device
- * memory is entirely owned by a framework's caching allocator, and latency-critical
- * loops that must not take the driver's allocation path.  The other entry points
- * take their scratch from a pool that grows with cudaMalloc; this one allocates
- * nothing.  Its scratch is a fixed 6.4 MB block of device memory built into the
- * library, which every GPU that loads the library holds until the process exits.
+ * Some callers may not call cudaMalloc at all: processes whose device memory is
+ * entirely owned by a framework's caching allocator, and latency-critical loops
+ * that must not take the driver's allocation path (cudaMalloc and cudaFree
+ * synchronise the device).  The other entry points take their scratch from a pool
+ * that grows with cudaMalloc; this one allocates nothing.  Its scratch is a fixed
+ * 6.4 MB block of device memory built into the library, which every GPU that
+ * loads the library holds until the process exits.
  *
  *   Limits: n <= 262144 rows (larger problems return DPT_ERR_TOO_LARGE at once);
  *   float-float working precision only (the default of dpt_solve_dominant).
@@ -380,6 +387,8 @@ DPT_API dpt_status dpt_solve_dominant_dense(int64_t n, const double* theta, cons
  *   scratch to stage host buffers through); E_out may be host or device.
  *   Arguments otherwise as for dpt_solve_dominant; tol and max_iter replace the
  *   options struct.
+ *   The call makes blocking CUDA runtime calls (copies and synchronisations on
+ *   `stream`), so it must not be made from a host callback (cudaLaunchHostFunc).
  *   The first call on each device looks up the block's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call before
  *   any stream capture begins.
@@ -406,7 +415,7 @@ DPT_API dpt_status dpt_solve_dominant_noalloc(int64_t n, const double* theta,
  * convergence (each problem is its own fixed-point iteration, Sec. II.B), writing
  * its outputs and freeing its memory for the queue.  A problem's arithmetic does
  * not depend on which other problems share its steps: its results are the same
- * alone and in any mix.  Mixed precision (DPT_PREC_MIXED_BF16) only.
+ * alone and in any mix.  Mixed precision (DPT_PREC_MIXED) only.
  * ------------------------------------------------------------------------ */
 typedef struct dpt_server dpt_server;
 typedef int64_t dpt_req;
@@ -419,7 +428,7 @@ typedef struct {
   int32_t max_queue;      /* queued requests beyond which dpt_submit returns
                              DPT_ERR_BUSY (default 65536) */
   dpt_options opt;        /* tol, max_iter, max_slices, slice_tol for requests that
-                             do not set their own; prec must be MIXED_BF16 and
+                             do not set their own; prec must be DPT_PREC_MIXED and
                              ramp_alpha 0 */
 } dpt_server_cfg;
 

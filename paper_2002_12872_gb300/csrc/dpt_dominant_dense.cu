@@ -12,7 +12,7 @@
 // HBM-bound at 8 bytes and 2 flops per entry.  Its arithmetic avoids the FP64 pipe,
 // which on this GPU is slower than HBM even at one operation per entry: each entry
 // is split into a float pair with integer operations and multiplied with z held as
-// float-float, the row sums kept in float-float (FF = true, DPT_PREC_MIXED_BF16).
+// float-float, the row sums kept in float-float (FF = true, DPT_PREC_MIXED).
 // FF = false is the literal FP64 arithmetic, the comparator.
 //
 // Kernels per iteration:

@@ -1,20 +1,23 @@
 // dpt_solve_dominant_noalloc: the dominant-eigenvector solve of dpt_solve_dominant
 // for callers that cannot allocate device memory.
 //
-// Who needs it: code that runs where cudaMalloc is off limits, for example inside
-// a host callback or a region being captured into a CUDA graph by someone else,
-// a process whose device memory is fully reserved by another allocator (a
-// framework's caching pool), or a real-time loop that must not take the driver's
-// allocation locks.  The regular entry points draw their scratch from a pool that
-// grows with cudaMalloc; this one uses a fixed block of device memory that is part
-// of the library image instead.
+// Who needs it: a process whose device memory is fully reserved by another
+// allocator (a framework's caching pool that owns the GPU's free memory), or a
+// latency-critical loop that must not take the driver's allocation path (whose
+// cudaMalloc / cudaFree calls synchronise the device).  The regular entry points
+// draw their scratch from a pool that grows with cudaMalloc; this one uses a fixed
+// block of device memory that is part of the library image instead.  It still makes
+// ordinary blocking CUDA runtime calls (copies and stream synchronisations on the
+// caller's stream), so it must not be called from a host callback
+// (cudaLaunchHostFunc), where CUDA forbids runtime calls.
 //
 // The scratch block is a file-scope __device__ array of kScratchBytes bytes.  It
 // is created when the library is loaded onto a device and stays resident on every
 // GPU that loads the library until the process exits.  Host code cannot use the
 // array's name as a device address (in host code the symbol is only a host-side
 // stand-in), so the first call on each device looks the address up with
-// cudaGetSymbolAddress, with that device current, and caches it.
+// cudaGetSymbolAddress, with that device current, and caches it; make that first
+// call before any stream capture begins.
 //
 // Every call shares the one block: two calls whose work overlaps on the GPU (on
 // different streams, or from different threads) race on it and give wrong
@@ -172,8 +175,13 @@ extern "C" dpt_status dpt_solve_dominant_noalloc(int64_t n, const double* theta,
   NA_CK(launch_dom_out(ni, z0, z1, nullptr, nullptr, 1, z_out, st, s));
   NA_CK(cudaMemcpyAsync(&h, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
   NA_CK(cudaStreamSynchronize(s));
-  if (on_device(E_out)) NA_CK(cudaMemcpy(E_out, &h.E, sizeof(double), cudaMemcpyHostToDevice));
-  else *E_out = h.E;
+  if (on_device(E_out)) {
+    // ordered on the caller's stream, like every other copy of this call
+    NA_CK(cudaMemcpyAsync(E_out, &h.E, sizeof(double), cudaMemcpyHostToDevice, s));
+    NA_CK(cudaStreamSynchronize(s));
+  } else {
+    *E_out = h.E;
+  }
 #undef NA_CK
   const dpt_status ret = status_of(h.status);
   if (info) {

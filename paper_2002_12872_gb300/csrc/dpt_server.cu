@@ -430,7 +430,7 @@ dpt_status dpt_server_create(const dpt_server_cfg* cfg_in, dpt_server** out) {
   dpt_server_cfg_default(&cfg);
   if (cfg_in) cfg = *cfg_in;
   if (cfg.max_active < 1 || cfg.max_active > 4096 || cfg.max_queue < 0 ||
-      cfg.opt.prec != DPT_PREC_MIXED_BF16 || cfg.opt.epstein_nesbet || !(cfg.opt.tol > 0) ||
+      cfg.opt.prec != DPT_PREC_MIXED || cfg.opt.epstein_nesbet || !(cfg.opt.tol > 0) ||
       cfg.opt.max_iter < 0 || cfg.opt.max_slices < 1 || cfg.opt.max_slices > 3 ||
       cfg.opt.ramp_alpha != 0.0 || cfg.opt.start)
     return DPT_ERR_ARG;
