@@ -166,6 +166,21 @@ typedef struct {
                               pass after all, the same iteration runs again in full.
                               Results and iteration counts are those of 0, which always
                               runs the full map. */
+  double refine_tol;       /* mixed real full solve: accuracy the eigenvectors must keep
+                              against the mixed arithmetic (default 1e-10; <= 0: off).
+                              The tensor-core products round to about 2^-24 of their
+                              largest term and the gaps are float-float, so a column i
+                              with a near-degenerate partner j (a large A_ji over a small
+                              theta_i - theta_j) can land further from the fixed point
+                              than the tolerance suggests.  After the mixed iteration the
+                              solve estimates each column's error as
+                              w_i (2^-22 |lambda| max|Delta| + 2^-46 max|theta|),
+                              w_i = max_{j != i} |A_ji| / |theta_i - theta_j| (first from
+                              a bound that costs nothing, then per column), and finishes
+                              the columns above refine_tol with the plain FP64 map (FP64
+                              gaps and products) on those columns only, until its step is
+                              below refine_tol / 8 (each column is its own map,
+                              Sec. II.B); dpt_info reports them. */
 } dpt_options;
 
 typedef struct {
@@ -190,7 +205,11 @@ typedef struct {
                               (2^-23 times the sum of its residuals above
                               max(tol, 1e-11)); 0 otherwise, and for n > 65535 (the
                               plain FP64 path's limit), where the mixed result is
-                              returned as it is */
+                              returned as it is.  Also counts the FP64 steps that
+                              finished the columns of refined_cols. */
+  int32_t refined_cols;    /* mixed real full solve: columns finished with plain FP64 map
+                              steps because their estimated error exceeded
+                              dpt_options.refine_tol */
 } dpt_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -293,6 +293,118 @@ void layout_full_mixed_real(Carve& c, int n, bool delta_dev, bool a_dev) {
   if (!a_dev) c.take<double>((size_t)ld * n);
 }
 
+// Result of the FP64 finish of at-risk columns (refine_columns).
+struct RefineResult {
+  int cols = 0;        // columns finished in FP64
+  int steps = 0;       // FP64 map steps (summed over the column groups)
+  double rho = 0.0;    // largest normalised residual of a finished column
+  bool ok = true;      // every group's FP64 steps converged
+};
+
+// The mixed solve as it ends would be a strongly coupled one that the plain FP64 map
+// finishes on all columns (mixed_real_finished): then no column is finished here.
+bool strongly_coupled(const IterState& fs, const dpt_options& o, int64_t n) {
+  return fs.rho_sum * 0x1p-23 > std::max(o.tol, 1e-11) && n <= 65535;
+}
+
+// FP64 finish of the columns of a converged mixed solve whose estimated arithmetic
+// error exceeds o.refine_tol (see dpt_refine.cu for the error model).  The estimate of
+// column i is w_i * coef with w_i = max_{j != i} |A_ji| / |theta_i - theta_j| and
+// coef = 2^-22 |lambda| max|Delta| + 2^-46 max|theta|: two FP32 roundings of 2^-24 per
+// product of the increment that carries A_ji, summed over the steps of a contraction
+// (factor 2), and the float-float gap.  A bound of every w_i costs nothing (the sum
+// of the increments' maxima times max 1/|gap|, both tracked by the kernels); only when
+// it exceeds the target is w_i formed per column.  The listed columns (ascending, so
+// that results do not depend on the order the flags were raised in) are taken in
+// groups that fit `region` (the mixed solve's increment buffers, free by now): the
+// plain FP64 map with FP64 gaps and products runs on each group, started from the
+// mixed result, until its step is below refine_tol / 8, and the group's last input
+// iterate and its eigenvalues replace the mixed ones in A (leading dimension lda) and E.
+RefineResult refine_columns(int n, const IterState& fs, const dpt_options& o, double lambda,
+                            const double* thd, const float* thh, const float* thl,
+                            const double* delta, int64_t ldd, int en, double* A, int64_t lda,
+                            double* E, char* region, size_t region_bytes, int* pinned,
+                            cudaStream_t s) {
+  RefineResult r;
+  if (!(o.refine_tol > 0.0) || fs.status != ST_CONVERGED || n < 2) return r;
+  double amax = 0.0;
+  if (fs.amax_bits != 0u) {   // high word of max |Delta| with the low word all ones
+    const uint64_t bits = ((uint64_t)fs.amax_bits << 32) | 0xFFFFFFFFull;
+    std::memcpy(&amax, &bits, sizeof(amax));
+  }
+  float rg = 0.f;
+  std::memcpy(&rg, &fs.rgmax_bits, sizeof(rg));
+  const double coef = 0x1p-22 * std::fabs(lambda) * amax + 0x1p-46 * fs.theta_max;
+  if (coef * (fs.dsum * (double)rg) <= o.refine_tol) return r;   // NaN falls through
+
+  // region: [control | count | column list | E of a group | A of a group x 2 | partials]
+  char* p0 = region;
+  RefineCtl* ctl = reinterpret_cast<RefineCtl*>(p0);
+  int* dcount = reinterpret_cast<int*>(p0 + 64);
+  int* dcols = reinterpret_cast<int*>(p0 + 256);
+  size_t off = 256 + (size_t)round_up((int64_t)n * 4, 256);
+  CK(cudaMemsetAsync(dcount, 0, sizeof(int), s));
+  CK(launch_risk(n, A, lda, thh, thl, coef, o.refine_tol, dcount, dcols, s));
+  CK(cudaMemcpyAsync(pinned, dcount, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int count = pinned[0];
+  if (count <= 0) return r;
+  std::vector<int> cols((size_t)count);
+  CK(cudaMemcpyAsync(cols.data(), dcols, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::sort(cols.begin(), cols.end());
+  CK(cudaMemcpyAsync(dcols, cols.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+  const int nks = refine_k_chunks(n);
+  // per column of a group: its E, two copies of the column, nks partial products
+  const size_t per_col = 8 + (size_t)8 * n * (2 + nks) + 64;
+  const size_t avail = region_bytes > off + 1024 ? region_bytes - off - 1024 : 0;
+  const int gmax = (int)std::min<size_t>((size_t)count, avail / per_col);
+  if (gmax < 1) throw Fail{DPT_ERR_NOMEM};
+  double* Ec = reinterpret_cast<double*>(region + off);
+  off += (size_t)round_up((int64_t)gmax * 8, 256);
+  double* As[2];
+  for (int q = 0; q < 2; ++q) {
+    As[q] = reinterpret_cast<double*>(region + off);
+    off += (size_t)round_up((int64_t)gmax * n * 8, 256);
+  }
+  double* Pp = reinterpret_cast<double*>(region + off);
+  const int max_steps = std::max(1, std::min(o.max_iter, 200));
+  r.cols = count;
+  for (int g0 = 0; g0 < count; g0 += gmax) {
+    const int gc = std::min(gmax, count - g0);
+    const int* gcols = dcols + g0;
+    CK(launch_cols_gather(n, gc, gcols, A, lda, As[0], s));
+    int cur = 0;
+    bool conv = false, finite = true;
+    for (int k = 0; k < max_steps; ++k) {
+      CK(launch_cols_product(n, gc, delta, ldd, As[cur], nks, Pp, s));
+      CK(cudaMemsetAsync(&ctl->step, 0, 2 * sizeof(double), s));
+      CK(launch_cols_epi(n, gc, nks, gcols, thd, delta, ldd, en, lambda, fs.s, Pp, As[cur],
+                         As[cur ^ 1], Ec, ctl, s));
+      double hr[2];
+      CK(cudaMemcpyAsync(pinned, &ctl->step, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::memcpy(hr, pinned, sizeof(hr));
+      ++r.steps;
+      if (!(hr[0] < INFINITY) || !(hr[1] < INFINITY)) { finite = false; break; }
+      if (hr[0] <= o.refine_tol / 8) {   // As[cur] is the finished iterate, Ec its eigenvalues
+        conv = true;
+        r.rho = std::max(r.rho, hr[1]);
+        break;
+      }
+      cur ^= 1;
+    }
+    if (!finite) {   // keep the mixed columns of this group
+      r.ok = false;
+      continue;
+    }
+    if (!conv) r.ok = false;
+    CK(launch_cols_scatter(n, gc, gcols, As[cur], Ec, A, lda, E, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return r;
+}
+
 // rho_sum (optional): the sum of the residuals rho_k (k >= 1) the float recursion
 // carried, whose rounding bounds how far its tracked residual may be from the exact one.
 dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
@@ -417,6 +529,21 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
         CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
       }, sizeof(IterState), /*k_first=*/1, tail, 1);   // the control after iteration 0 set k = 1
     }
+    // columns the mixed arithmetic cannot vouch for are finished in FP64 (the state
+    // read after the last chunk is the final one)
+    RefineResult rr;
+    {
+      const IterState fs0 = *b->host_state;
+      if (!strongly_coupled(fs0, o, n64)) {
+        char* region = reinterpret_cast<char*>(Ahi[0]);
+        const size_t region_bytes = (size_t)((char*)(L + (size_t)ld * n) - region);
+        rr = refine_columns(n, fs0, o, lambda, thd, thh, thl, delta, ldd,
+                            o.epstein_nesbet ? 1 : 0, Astage, lda_dev, E, region, region_bytes,
+                            reinterpret_cast<int*>(b->host_state) + 512, s);
+        if (rr.cols > 0 && e_dev)
+          CK(cudaMemcpyAsync(E_out, E, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      }
+    }
     if (!a_dev || !e_dev) {
       if (!a_dev)
         CK(cudaMemcpy2DAsync(A_out, sizeof(double) * ld_a, Astage, sizeof(double) * ld,
@@ -429,16 +556,19 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     // tail formed the outputs) is the final state: no further round trip
     const IterState& fs = *b->host_state;
     ret = from_state(fs.status);
+    if (ret == DPT_OK && !rr.ok) ret = DPT_ERR_MAXITER;   // an FP64 finish did not settle
     if (rho_sum) *rho_sum = fs.rho_sum;
     if (info) {
-      info->iters = fs.k;
+      info->iters = fs.k + rr.steps;
       info->slice_gemms = fs.slice_gemms;
-      info->residual = fs.rho;
+      info->residual = std::max(fs.rho, rr.rho);
       info->status = ret;
       info->launches = prof.launches;
       info->product_launches = prof.live;
       info->product_ms = prof.ms;
       info->cta_pair = pair ? 1 : 0;
+      info->fp64_iters = rr.steps;
+      info->refined_cols = rr.cols;
     }
     CK(cudaEventRecord(b->ev, s));
     CK(cudaStreamWaitEvent(user, b->ev, 0));
@@ -1561,6 +1691,7 @@ void dpt_options_default(dpt_options* o) {
   o->start = nullptr;
   o->ld_start = 0;
   o->certify = 1;
+  o->refine_tol = 1e-10;
 }
 
 int64_t dpt_workspace_bytes(int64_t n, dpt_dtype dtype, dpt_prec prec) {

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__
   const float thh = th_hi[i], thl = th_lo[i];
   const double* col = delta + (int64_t)i * ld_in;
   unsigned hmax = 0u;
-  float gmax = 0.f;
+  float gmax = 0.f, rgmax = 0.f;   // rgmax: max 1 / |gap| (input of the error bound)
   // four independent loads in flight per thread (the column streams from HBM)
   for (int jb = threadIdx.x; jb < n; jb += 1024) {
     double v[4];
@@ -141,21 +141,25 @@ __global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__
       float g = thh - tjh[u];
       if (g == 0.f) g = thl - tjl[u];
       // NaN never wins fmaxf
-      gmax = fmaxf(gmax, va * rcp_approx(fabsf(g)));
+      const float rg = rcp_approx(fabsf(g));
+      gmax = fmaxf(gmax, va * rg);
+      rgmax = fmaxf(rgmax, rg);
     }
   }
   hmax = __reduce_max_sync(0xffffffffu, hmax);
   unsigned gb = __reduce_max_sync(0xffffffffu, __float_as_uint(gmax));   // gmax >= 0
-  __shared__ unsigned wh[8], wg[8];
+  unsigned rb = __reduce_max_sync(0xffffffffu, __float_as_uint(rgmax));  // rgmax >= 0
+  __shared__ unsigned wh[8], wg[8], wr[8];
   __shared__ bool last;
   const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) { wh[w] = hmax; wg[w] = gb; }
+  if ((threadIdx.x & 31) == 0) { wh[w] = hmax; wg[w] = gb; wr[w] = rb; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned a = 0u, b = 0u;
-    for (int q = 0; q < 8; ++q) { a = max(a, wh[q]); b = max(b, wg[q]); }
+    unsigned a = 0u, b = 0u, r = 0u;
+    for (int q = 0; q < 8; ++q) { a = max(a, wh[q]); b = max(b, wg[q]); r = max(r, wr[q]); }
     atomicMax(&st->amax_bits, a);
     atomicMax(&st->g0max_bits, b);
+    atomicMax(&st->rgmax_bits, r);
     __threadfence();
     last = (atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1);
   }
@@ -480,6 +484,8 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
   vs->rho_bits = 0;
   const float dmax = __uint_as_float(vs->dmax_bits);
   vs->dmax_bits = 0;
+  // every increment of the returned iterate is bounded by one of these maxima
+  vs->dsum = vs->dsum + (double)dmax;
   // the rounding of the float recursion grows with the residuals it carried
   if (!first) vs->rho_sum = vs->rho_sum + rho;
   if (cert) {

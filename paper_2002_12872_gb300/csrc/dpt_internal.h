@@ -61,7 +61,31 @@ struct IterState {
   int sig;             // the FP16 slices hold Delta * 2^sig
   int sexp[2];         // increment buffer q holds dt * 2^sexp[q] in FP16
   double rho_sum;      // sum of the residuals rho_k, k >= 1, the float recursion carried
+  // mixed single solve: inputs of the bound on its arithmetic error (see dpt_refine.cu)
+  unsigned rgmax_bits; // atomicMax scratch: max_{j != i} 1 / |theta_i - theta_j| (float bits)
+  double dsum;         // sum over the updates of max |dt_k|: a bound of max |A_ji - delta_ji|
 };
+
+// Maxima of one FP64 step over the refined columns (dpt_refine.cu).
+struct RefineCtl {
+  unsigned blocks_done;
+  unsigned pad;
+  double step;         // max over the columns of |A' - A| / |A|
+  double rho;          // max over the columns of |M a - E a| / (s |a|) of the step's input
+};
+cudaError_t launch_risk(int n, const double* A, int64_t lda, const float* thh, const float* thl,
+                        double coef, double target, int* count, int* cols, cudaStream_t s);
+cudaError_t launch_cols_gather(int n, int nc, const int* cols, const double* A, int64_t lda,
+                               double* As, cudaStream_t s);
+cudaError_t launch_cols_scatter(int n, int nc, const int* cols, const double* As, const double* Ec,
+                                double* A, int64_t lda, double* E, cudaStream_t s);
+int refine_k_chunks(int n);
+cudaError_t launch_cols_product(int n, int nc, const double* D, int64_t ldd, const double* As,
+                                int nks, double* Pp, cudaStream_t s);
+cudaError_t launch_cols_epi(int n, int nc, int nks, const int* cols, const double* theta,
+                            const double* D, int64_t ldd, int en, double lam, double s_scale,
+                            const double* Pp, const double* Ac, double* An, double* Ec,
+                            RefineCtl* ctl, cudaStream_t s);
 
 // State of a dominant-eigenvector solve (single-vector map), device resident.
 struct DomState {

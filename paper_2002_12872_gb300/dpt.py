@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("profile", ctypes.c_int32), ("slice_tol", ctypes.c_double),
                 ("cta_pair", ctypes.c_int32), ("grouped_form", ctypes.c_int32),
                 ("ramp_alpha", ctypes.c_double), ("start", ctypes.c_void_p),
-                ("ld_start", ctypes.c_int64), ("certify", ctypes.c_int32)]
+                ("ld_start", ctypes.c_int64), ("certify", ctypes.c_int32),
+                ("refine_tol", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -43,7 +44,8 @@ class Info(ctypes.Structure):
                 ("nstar", ctypes.c_int32), ("seconds", ctypes.c_double),
                 ("launches", ctypes.c_int32), ("product_launches", ctypes.c_int32),
                 ("product_ms", ctypes.c_double), ("cta_pair", ctypes.c_int32),
-                ("grouped_form", ctypes.c_int32), ("fp64_iters", ctypes.c_int32)]
+                ("grouped_form", ctypes.c_int32), ("fp64_iters", ctypes.c_int32),
+                ("refined_cols", ctypes.c_int32)]
 
     def as_dict(self):
         return {"iters": self.iters, "slice_gemms": self.slice_gemms,
@@ -51,7 +53,8 @@ class Info(ctypes.Structure):
                 "code": self.status, "nstar": self.nstar, "seconds": self.seconds,
                 "launches": self.launches, "product_launches": self.product_launches,
                 "product_ms": self.product_ms, "cta_pair": self.cta_pair,
-                "grouped_form": self.grouped_form, "fp64_iters": self.fp64_iters}
+                "grouped_form": self.grouped_form, "fp64_iters": self.fp64_iters,
+                "refined_cols": self.refined_cols}
 
 
 class ServerCfg(ctypes.Structure):
@@ -249,7 +252,7 @@ def _iscomplex(x) -> bool:
 def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
                epstein_nesbet=False, graph_iters=None, max_slices=None, slice_tol=None,
                profile=False, cta_pair=None, ramp_alpha=None, start=None, certify=None,
-               A_out=None, E_out=None, stream=None, check=True):
+               refine_tol=None, A_out=None, E_out=None, stream=None, check=True):
     """All eigenpairs of M = diag(theta) + lam * Delta by the DPT map (dpt_solve_full).
 
     Returns (A, E, info): A[:, i] is eigenvector i with A[i, i] = 1 and
@@ -266,7 +269,8 @@ def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
     o = options(tol=tol, max_iter=max_iter, prec=prec, epstein_nesbet=int(bool(epstein_nesbet)),
                 graph_iters=graph_iters, max_slices=max_slices, slice_tol=slice_tol,
                 profile=int(bool(profile)), cta_pair=None if cta_pair is None else int(cta_pair),
-                ramp_alpha=ramp_alpha, certify=None if certify is None else int(bool(certify)))
+                ramp_alpha=ramp_alpha, certify=None if certify is None else int(bool(certify)),
+                refine_tol=refine_tol)
     s_keep = None
     if start is not None:
         s_ptr, s_ld, s_keep = _colmajor(start, cplx)

@@ -28,6 +28,9 @@ sparse perturbations, Sec. II.G-H, are synthetic, so these stand in for them):
                      Hermitian Delta with E|x|^2 = 1/n (real N(0, 1/n) diagonal,
                      off-diagonal real and imaginary parts N(0, 1/(2n))),
                      lam ~ U[0.02, 0.08]
+  near_degenerate    theta_i = base + i with one pair moved to a gap of ratio x its
+                     coupling lambda |Delta|, Delta iid N(0, 1/n), lam 0.1 (the
+                     edge case of the gaps in Eq. (dyn))
   delta_oscillator   the harmonic oscillator with a delta potential (Sec. II.F):
                      theta_n = 2n + 1/2, rank-one Delta from Hermite functions at 0
   served_pool /      the same requests drawn from a pool of distinct Hermitian
@@ -91,6 +94,25 @@ def full_unsymmetric(n: int = 4096, rep: int = 0, lam: float = 0.1) -> dict:
     theta = spaced_uniform(n, 0.5, rng)
     delta = np.asfortranarray(rng.standard_normal((n, n)) / np.sqrt(n))
     return {"n": n, "theta": theta, "delta": delta, "lam": lam, "tol": 1e-12}
+
+
+def near_degenerate(n: int = 260, base: float = 0.0, ratio: float = 10.0, rep: int = 0,
+                    lam: float = 0.1) -> dict:
+    """A near-degenerate, strongly coupled pair in an otherwise regular spectrum (the
+    edge the gaps theta_i - theta_j of Eq. (dyn) put at risk): theta_i = base + i,
+    Delta iid N(0, 1/n) unsymmetric, and level i0 + 1 (i0 = n // 2) moved to
+    theta_i0 + g with g = ratio * lam * max(|Delta_{i0,i0+1}|, |Delta_{i0+1,i0}|), so
+    that the pair's coupling over its gap is 1 / ratio.  The map converges here for
+    ratio >= 5 (at ratio 3 this draw's iteration diverges); base moves the spectrum to
+    large |theta| without changing any gap.  Returns the pair's indices as "pair"."""
+    rng = rng_for(6, rep)
+    theta = base + np.arange(n, dtype=np.float64)
+    delta = np.asfortranarray(rng.standard_normal((n, n)) / np.sqrt(n))
+    i0 = n // 2
+    g = ratio * lam * max(abs(delta[i0, i0 + 1]), abs(delta[i0 + 1, i0]))
+    theta[i0 + 1] = theta[i0] + g
+    return {"n": n, "theta": theta, "delta": delta, "lam": lam, "tol": 1e-15,
+            "pair": (i0, i0 + 1), "gap": g}
 
 
 def full_unsymmetric_device(n: int = 32768, rep: int = 0, lam: float = 0.1, device="cuda"):

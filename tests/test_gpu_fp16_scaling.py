@@ -41,13 +41,21 @@ def test_power_of_two_rescaling_is_exact(dpt, p, pair):
 
 
 def test_weakly_coupled_solve_needs_no_fp64_finish(ora, dpt):
+    """A weakly coupled problem is not finished by the plain FP64 map on all columns;
+    at most a few of its columns, whose estimated error exceeds refine_tol, get FP64
+    steps of their own (none with that finish switched off)."""
     cfg = inputs.full_unsymmetric(n=513)
     th = torch.tensor(cfg["theta"], device="cuda")
     D = dpt.colmajor_tensor(cfg["delta"], "cuda")
+    _, _, off = dpt.solve_full(th, D, cfg["lam"], refine_tol=0.0)
+    assert off["status"] == "OK" and off["fp64_iters"] == 0 and off["refined_cols"] == 0
     A, E, info = dpt.solve_full(th, D, cfg["lam"])
-    assert info["status"] == "OK" and info["fp64_iters"] == 0
+    # the estimate is conservative (two to four times the error measured on
+    # near-degenerate pairs), so a minority of columns gets a few FP64 steps
+    assert info["status"] == "OK" and info["refined_cols"] <= 513 // 8
+    assert info["fp64_iters"] <= 6
     # two FP16 slices for the first product, one once the increments are small
-    assert info["slice_gemms"] <= 2 * info["iters"]
+    assert info["slice_gemms"] <= 2 * (info["iters"] - info["fp64_iters"])
     Ao, Eo, io = ora.solve_full(cfg["theta"], cfg["delta"], cfg["lam"], tol=1e-13,
                                 cols=np.array([0, 256, 512]))
     assert eig_err(to_np(E)[[0, 256, 512]], Eo) <= EIG_RTOL

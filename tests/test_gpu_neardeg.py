@@ -1,0 +1,91 @@
+"""GPU parity at the edge the gaps of Eq. (dyn) put at risk: a near-degenerate,
+strongly coupled pair of levels (the pair's coupling lambda |Delta| is 1/5 .. 1/30 of
+its gap, Sec. II.B: the map divides by theta_i - theta_j), at small and large |theta|.
+
+The mixed path's tensor-core products round to about 2^-24 of their largest term, and
+for such a column the largest term is the partner's (A_ji ~ 0.2), so the tracked
+residual drifts by far more than its tolerance allows once divided by the small gap
+(measured 2e-8 against the 1e-9 bar at ratio 5 before the FP64 finish existed).  The
+solve bounds every column's error and finishes the columns above refine_tol with the
+plain FP64 map on those columns only.  The reference is the oracle iterated to its
+FP64 fixed point (one more map step changes nothing beyond 1e-15): with |theta| ~ 1e4
+the normalised residual of the oracle stalls near 2e-15 (the size of theta's own
+rounding), so its stopping tolerance cannot stand for convergence there."""
+import numpy as np
+import pytest
+
+from gpu_util import EIG_RTOL, VEC_TOL, eig_err, to_np, unit_cols, vec_err
+from paper_2002_12872_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+CASES = [(0.0, 5.0), (0.0, 10.0), (1e4, 5.0), (1e4, 10.0), (1e4, 30.0)]
+
+
+@pytest.fixture(scope="module")
+def dpt():
+    from paper_2002_12872_gb300 import build, dpt
+    build.build()
+    assert torch.cuda.is_available()
+    return dpt
+
+
+@pytest.fixture(scope="module")
+def fixed_points(ora):
+    """The oracle's FP64 fixed point of every case (computed once)."""
+    out = {}
+    for base, ratio in CASES:
+        c = inputs.near_degenerate(base=base, ratio=ratio)
+        A, E, io = ora.solve_full(c["theta"], c["delta"], c["lam"], tol=1e-300, max_iter=150)
+        An, _ = ora.step(c["theta"], c["delta"], c["lam"], A)
+        assert np.abs(An - A).max() <= 1e-15, (base, ratio)   # converged map
+        out[(base, ratio)] = (c, A, E)
+    return out
+
+
+def _run(dpt, c, prec, **kw):
+    th = torch.tensor(c["theta"], device="cuda")
+    D = dpt.colmajor_tensor(c["delta"], "cuda")
+    A, E, info = dpt.solve_full(th, D, c["lam"], prec=prec, tol=c["tol"], max_iter=400, **kw)
+    return to_np(A), to_np(E), info
+
+
+@pytest.mark.parametrize("base,ratio", CASES)
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_near_degenerate_pair(fixed_points, dpt, prec, base, ratio):
+    c, Ao, Eo = fixed_points[(base, ratio)]
+    A, E, info = _run(dpt, c, prec)
+    assert info["status"] == "OK", info
+    assert eig_err(E, Eo) <= EIG_RTOL, (eig_err(E, Eo), info)
+    assert vec_err(A, Ao) <= VEC_TOL, (vec_err(A, Ao), info)
+    i0, i1 = c["pair"]
+    pair_err = np.linalg.norm(unit_cols(A[:, [i0, i1]]) - unit_cols(Ao[:, [i0, i1]]), axis=0)
+    if prec == "mixed":
+        # the pair's columns were finished in FP64: their error is far below the bar
+        assert info["refined_cols"] >= 2 and info["fp64_iters"] > 0, info
+        assert pair_err.max() <= 1e-10, (pair_err, info)
+
+
+def test_finish_off_reports_no_refined_columns(fixed_points, dpt):
+    """refine_tol = 0 switches the FP64 finish off: no column is refined, and the
+    pair's columns then carry the mixed arithmetic's error (reported, not asserted
+    beyond being finite)."""
+    c, Ao, _ = fixed_points[(1e4, 5.0)]
+    A, E, info = _run(dpt, c, "mixed", refine_tol=0.0)
+    assert info["refined_cols"] == 0
+    assert np.all(np.isfinite(A)) and np.all(np.isfinite(E))
+
+
+def test_finish_keeps_the_rescaling_invariance(fixed_points, dpt):
+    """(Delta, lambda) -> (2^p Delta, 2^-p lambda) leaves M unchanged; the error bound
+    and the FP64 finish (exact power-of-two scaling of every FP64 product) keep the
+    result bit for bit."""
+    c, _, _ = fixed_points[(1e4, 10.0)]
+    A1, E1, i1 = _run(dpt, c, "mixed")
+    c2 = dict(c)
+    c2["delta"] = np.asfortranarray(c["delta"] * 2.0**20)
+    c2["lam"] = c["lam"] * 2.0**-20
+    A2, E2, i2 = _run(dpt, c2, "mixed")
+    assert i1["refined_cols"] == i2["refined_cols"] > 0
+    assert np.array_equal(A1, A2) and np.array_equal(E1, E2)
