@@ -209,7 +209,8 @@ typedef struct {
                               finished the columns of refined_cols. */
   int32_t refined_cols;    /* mixed real full solve: columns finished with plain FP64 map
                               steps because their estimated error exceeded
-                              dpt_options.refine_tol */
+                              dpt_options.refine_tol (n when the whole problem was
+                              finished in FP64, see fp64_iters) */
 } dpt_info;
 
 /* Fill *opt with the defaults listed above. */

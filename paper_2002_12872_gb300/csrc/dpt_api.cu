@@ -1651,6 +1651,7 @@ dpt_status mixed_real_finished(int64_t n, std::vector<double> th, const double* 
                          ld_a, E_out, e_dev, &fi, s);
     mi.iters += fi.iters;
     mi.fp64_iters = fi.iters;
+    mi.refined_cols = (int32_t)n;       // every column finished in FP64
     mi.launches += fi.launches;
     mi.product_launches += fi.product_launches;
     mi.product_ms += fi.product_ms;

@@ -913,150 +913,181 @@ struct EpiConst {
   float isc;          // 2^-scur
 };
 
-// Leaves this lane's partial sums of the column (|R|^2, |a|^2, and the diagonal
-// increment as float-float) in part4; the caller reduces two columns at once.
-template <int S>
-__device__ __forceinline__ void epi_compute(const GemmEpiParams& p, GemmSmemMisc* ms,
-                                            const float* Xs, const uint8_t* eb, int ew,
-                                            int lane, int m0, int n0, int sc, float& mx,
-                                            const EpiConst& kc, const float4& thj_h,
-                                            const float4& thj_l, float (&part4)[4]) {
+// One column of a sub-chunk: the update of Eq. (dyn) in increment form for this lane's
+// four rows, from the staged inputs in eb and the accumulator chunk in Xs (columns
+// c0 .. c0 + 31, c0 = 32 (sc / 2)).  Specialised at compile time on
+//   S      the Delta slices this product used (the diagonal partial uses as many),
+//   MODE   0: a full step; 1: the first product, whose iterate A_1 = I + dt_0 is
+//          formed from the increment (its A_lo is zero); 2: a certifying pass, which
+//          forms only the residual norms of its iterate and writes nothing else,
+//   CHECK  the tile holds a diagonal element or rows beyond n (per-element masks).
+// Leaves this lane's partial sums (|R|^2, |a|^2, the diagonal increment) in part3.
+//
+// Arithmetic, per element (j, i), with the scales of EpiConst folded in:
+//   R    = L + lambda (X - A e_i - dt_{k-1} d_{k-1,i})        (the residual of A_k)
+//   gap  = theta_i - theta_j as gs + gl: gs the float difference of the high parts,
+//          gl its exact rounding error plus the difference of the low parts (an
+//          unnormalised float-float pair: the quotient only needs gs + gl to float
+//          accuracy, the remainder takes both parts)
+//   dt_k = f16(R / gap) (packed conversion, scaled), L' = R - gap dt_k (exact feedback)
+//   A'   = A + dt_k as the exact sum (two-sum) with the error added to A_lo (the pair
+//          stays unnormalised: A_hi alone is read by the recursion, A_hi + A_lo only
+//          by the output)
+//   e    = sum_j Delta_ij dt_k,ji over this lane's rows in plain float: the slice
+//          products are exact (11-bit significands) and these increments follow the
+//          first one (summed in float-float by iteration 0), so float sums keep the
+//          eigenvalues far inside their tolerance; tiles are summed in FP64 later.
+template <int S, int MODE, bool CHECK>
+__device__ __forceinline__ void epi_lean(const GemmEpiParams& p, const GemmSmemMisc* ms,
+                                         const float* Xs, const uint8_t* eb, int ew, int lane,
+                                         int m0, int n0, int sc, float& mx, const EpiConst& kc,
+                                         const float4& thj_h, const float4& thj_l,
+                                         float (&part3)[3]) {
+  constexpr bool CERT = MODE == 2, A1 = MODE == 1;
   const int n = p.n, ld = p.ld;
+  const int cl = 16 * sc + ew;
+  const int i = n0 + cl;
+  part3[0] = part3[1] = part3[2] = 0.f;
+  if (i >= n) return;   // uniform across the warp
   const bool c1 = (ms->cur != 0);
-  const bool cert = ms->certify != 0;     // residual norms only, nothing written
-  const bool a1 = ms->k == 1;             // A_1 = I + dt_0, formed from dt_0
   float* __restrict__ Ahn = c1 ? p.A_hi[0] : p.A_hi[1];
   float* __restrict__ Aln = c1 ? p.A_lo[0] : p.A_lo[1];
   __half* __restrict__ dtn_out = c1 ? p.dt[1] : p.dt[0];
-  float* __restrict__ L = p.L;
-  const float lam = kc.lam, qs = kc.qs, iqs = kc.iqs;
   const int r0 = 4 * lane;
   const int j0 = m0 + r0;
   const int c0 = 32 * (sc >> 1);
+  uint8_t* e8 = const_cast<uint8_t*>(eb);
+  const float4 L4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, 0, 2, lane));
+  const uint2 dtp = *reinterpret_cast<const uint2*>(eb_u2(e8, ew, 0, 0, lane));
+  float4 ah4, al4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (A1) {
+    ah4 = make_float4(h_at(dtp, 0) * kc.isc, h_at(dtp, 1) * kc.isc, h_at(dtp, 2) * kc.isc,
+                      h_at(dtp, 3) * kc.isc);
+  } else {
+    ah4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, 0, 0, lane));
+    if (!CERT) al4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, 0, 1, lane));
+  }
+  uint2 D[3] = {make_uint2(0u, 0u), make_uint2(0u, 0u), make_uint2(0u, 0u)};
+  if (!CERT) {
 #pragma unroll
-  for (int u = 0; u < 1; ++u) {
-    const int cl = 16 * sc + ew + u;
-    const int i = n0 + cl;
-    if (i >= n) continue;   // uniform across the warp
-    uint8_t* e8 = const_cast<uint8_t*>(eb);
-    const float4 L4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 2, lane));
-    const uint2 dtp = *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 0, lane));
-    // off the diagonal A_1 = dt_0 (its diagonal entry is never read)
-    const float isc = kc.isc;
-    const float4 ah4 = a1 ? make_float4(h_at(dtp, 0) * isc, h_at(dtp, 1) * isc,
-                                        h_at(dtp, 2) * isc, h_at(dtp, 3) * isc)
-                          : *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 0, lane));
-    const float4 al4 = (cert || a1) ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                    : *reinterpret_cast<const float4*>(eb_f4(e8, ew, u, 1, lane));
-    // the slices of Delta_ij this product uses (not loaded by a certifying pass)
-    uint2 D[3] = {make_uint2(0u, 0u), make_uint2(0u, 0u), make_uint2(0u, 0u)};
-    if (!cert) {
+    for (int sl = 0; sl < S; ++sl) D[sl] = *reinterpret_cast<const uint2*>(eb_u2(e8, ew, 0, 1 + sl, lane));
+  }
+  const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * BM + r0);
+  const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
+  const float thh = ms->thh[cl], thl = ms->thl[cl];
+  const float lam = kc.lam, qs = kc.qs, iqs = kc.iqs;
+  float r2 = 0.f, a2 = 0.f, es = 0.f;
+  float4 oh, ol, oL;
+  uint2 ob;
 #pragma unroll
-      for (int sl = 0; sl < S; ++sl)
-        D[sl] = *reinterpret_cast<const uint2*>(eb_u2(e8, ew, u, 1 + sl, lane));
-    }
-    const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * BM + r0);
-    const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
-    const float thh = ms->thh[cl], thl = ms->thl[cl];
-    float4 oh, ol, oL;
-    float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
-    uint2 ob;
-    // two rows at a time: their residuals and scaled quotients R / Gap, one packed
-    // FP16 conversion, then the rest of the update with the increments as applied
+  for (int hp = 0; hp < 2; ++hp) {
+    float R[2], gs[2], gl[2], q[2];
 #pragma unroll
-    for (int hp = 0; hp < 2; ++hp) {
-      float R[2], gh[2], gl[2], q[2];
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const int e = 2 * hp + t, j = j0 + e;
-        R[t] = gh[t] = gl[t] = q[t] = 0.f;
-        if (j != i && j < n) {
-          const float ah = f4(ah4, e);
-          R[t] = f4(L4, e) + lam * (f4(x4, e) - ah * e_i - h_at(dtp, e) * dp_i);
-          r2 = fmaf(R[t], R[t], r2);
-          a2 = fmaf(ah, ah, a2);
-          if (!cert) {
-            ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh[t], gl[t]);
-            // the increment is rounded to FP16 and the remainder keeps R - Gap dnew
-            // exactly, so any reciprocal close to 1/gap serves
-            q[t] = R[t] * rcp_approx(gh[t]) * qs;
-          }
+    for (int t = 0; t < 2; ++t) {
+      const int e = 2 * hp + t, j = j0 + e;
+      R[t] = gs[t] = gl[t] = q[t] = 0.f;
+      if (!CHECK || (j != i && j < n)) {
+        const float ah = f4(ah4, e);
+        R[t] = f4(L4, e) + lam * (f4(x4, e) - ah * e_i - h_at(dtp, e) * dp_i);
+        r2 = fmaf(R[t], R[t], r2);
+        a2 = fmaf(ah, ah, a2);
+        if (!CERT) {
+          const float bh = f4(thj_h, e);
+          float err;
+          two_sum(thh, -bh, gs[t], err);
+          gl[t] = err + (thl - f4(thj_l, e));
+          // the increment is rounded to FP16 and the remainder keeps R - gap dt exactly,
+          // so any reciprocal close to 1/gap serves
+          q[t] = R[t] * rcp_approx(gs[t] + gl[t]) * qs;
         }
       }
+    }
+    if (!CERT) {
       const uint32_t w = f16x2_sat(q[0], q[1]);
       if (hp == 0) ob.x = w; else ob.y = w;
+    }
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const int e = 2 * hp + t, j = j0 + e;
-        const float ah = f4(ah4, e), al = f4(al4, e);
-        float nh = 0.f, nl = 0.f, Ln = 0.f;
-        if (j == i) {
-          nh = 1.f;
-          a2 += 1.f;
-        } else if (j < n && !cert) {
-          const float dnew = h_at(ob, e) * iqs;
-          Ln = fmaf(-gh[t], dnew, R[t]) - gl[t] * dnew;
-          ff_add_f(ah, al, dnew, nh, nl);
-          const float p1 = h_at(D[0], e) * dnew;
-          float p23 = 0.f;
-          if (S > 2) p23 = h_at(D[2], e) * dnew;
-          if (S > 1) p23 = fmaf(h_at(D[1], e), dnew, p23);
-          float sh, se;
-          two_sum(eh, p1, sh, se);
-          se += el + p23;
-          fast_two_sum(sh, se, eh, el);
-          mx = fmaxf(mx, fabsf(dnew));
-        }
-        f4set(oh, e, nh);
-        f4set(ol, e, nl);
-        f4set(oL, e, Ln);
+    for (int t = 0; t < 2; ++t) {
+      const int e = 2 * hp + t, j = j0 + e;
+      float nh = 0.f, nl = 0.f, Ln = 0.f;
+      if (CHECK && j == i) {
+        nh = 1.f;
+        a2 += 1.f;
+      } else if (!CERT && (!CHECK || j < n)) {
+        const float dnew = h_at(ob, e) * iqs;
+        Ln = fmaf(-gs[t], dnew, R[t]) - gl[t] * dnew;
+        float err;
+        two_sum(f4(ah4, e), dnew, nh, err);
+        nl = f4(al4, e) + err;
+        es = fmaf(h_at(D[0], e), dnew, es);
+        if (S > 1) es = fmaf(h_at(D[1], e), dnew, es);
+        if (S > 2) es = fmaf(h_at(D[2], e), dnew, es);
+        mx = fmaxf(mx, fabsf(dnew));
       }
+      f4set(oh, e, nh);
+      f4set(ol, e, nl);
+      f4set(oL, e, Ln);
     }
-    const int64_t idx = (int64_t)i * ld + j0;
-    if (!cert) {
-      st4(Ahn + idx, oh);
-      st4(Aln + idx, ol);
-      st4(L + idx, oL);
-      *reinterpret_cast<uint2*>(dtn_out + idx) = ob;
-    }
-    part4[0] = r2; part4[1] = a2; part4[2] = eh; part4[3] = el;
   }
+  if (!CERT) {
+    const int64_t idx = (int64_t)i * ld + j0;
+    st4(Ahn + idx, oh);
+    st4(Aln + idx, ol);
+    st4(p.L + idx, oL);
+    *reinterpret_cast<uint2*>(dtn_out + idx) = ob;
+  }
+  part3[0] = r2; part3[1] = a2; part3[2] = es;
 }
 
-// Warp sums of two columns' lane partials (|R|^2, |a|^2, diagonal increment as
-// float-float) with one transposing exchange: after the first step lanes 0-15 carry
-// column a and lanes 16-31 column b, so the remaining four steps serve both (about
-// half the shuffles and float-float additions of two separate reductions).  On
-// return lane 0 holds the sums of a, lane 16 those of b.
-__device__ __forceinline__ void warp_sum_ff2(float (&a)[4], const float (&b)[4], int lane) {
+template <int S, int MODE>
+__device__ __forceinline__ void epi_lean_tile(bool check, const GemmEpiParams& p,
+                                              const GemmSmemMisc* ms, const float* Xs,
+                                              const uint8_t* eb, int ew, int lane, int m0, int n0,
+                                              int sc, float& mx, const EpiConst& kc,
+                                              const float4& thj_h, const float4& thj_l,
+                                              float (&part3)[3]) {
+  if (check) epi_lean<S, MODE, true>(p, ms, Xs, eb, ew, lane, m0, n0, sc, mx, kc, thj_h, thj_l, part3);
+  else epi_lean<S, MODE, false>(p, ms, Xs, eb, ew, lane, m0, n0, sc, mx, kc, thj_h, thj_l, part3);
+}
+
+// Dispatch on the launch's slice count and mode (uniform) and the tile's masks.
+__device__ __forceinline__ void epi_lean_any(int S, int mode, bool check, const GemmEpiParams& p,
+                                             const GemmSmemMisc* ms, const float* Xs,
+                                             const uint8_t* eb, int ew, int lane, int m0, int n0,
+                                             int sc, float& mx, const EpiConst& kc,
+                                             const float4& thj_h, const float4& thj_l,
+                                             float (&part3)[3]) {
+#define DPT_EPI_CASE(SS, MM) \
+  epi_lean_tile<SS, MM>(check, p, ms, Xs, eb, ew, lane, m0, n0, sc, mx, kc, thj_h, thj_l, part3)
+  // the single solve slices Delta into at most two FP16 slices (solve_full_mixed_real)
+  if (mode == 2) {          // certifying passes read no slices
+    DPT_EPI_CASE(1, 2);
+  } else if (mode == 1) {
+    if (S == 1) DPT_EPI_CASE(1, 1);
+    else DPT_EPI_CASE(2, 1);
+  } else {
+    if (S == 1) DPT_EPI_CASE(1, 0);
+    else DPT_EPI_CASE(2, 0);
+  }
+#undef DPT_EPI_CASE
+}
+
+// Warp sums of two columns' lane partials (|R|^2, |a|^2, the diagonal increment) with
+// one transposing exchange: after the first step lanes 0-15 carry column a and lanes
+// 16-31 column b, so the remaining four steps serve both.  On return lane 0 holds the
+// sums of a, lane 16 those of b.
+__device__ __forceinline__ void warp_sum3x2(float (&a)[3], const float (&b)[3], int lane) {
   const bool lo = lane < 16;
-  float k[4], o[4];
+  float k[3];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    k[q] = lo ? a[q] : b[q];
-    o[q] = __shfl_xor_sync(0xffffffffu, lo ? b[q] : a[q], 16);
-  }
-  k[0] += o[0];
-  k[1] += o[1];
-  {
-    float sh, se;
-    two_sum(k[2], o[2], sh, se);
-    se += k[3] + o[3];
-    fast_two_sum(sh, se, k[2], k[3]);
-  }
+  for (int q = 0; q < 3; ++q)
+    k[q] = (lo ? a[q] : b[q]) + __shfl_xor_sync(0xffffffffu, lo ? b[q] : a[q], 16);
 #pragma unroll
-  for (int off = 8; off > 0; off >>= 1) {
-    k[0] += __shfl_xor_sync(0xffffffffu, k[0], off);
-    k[1] += __shfl_xor_sync(0xffffffffu, k[1], off);
-    const float oh = __shfl_xor_sync(0xffffffffu, k[2], off);
-    const float ol = __shfl_xor_sync(0xffffffffu, k[3], off);
-    float sh, se;
-    two_sum(k[2], oh, sh, se);
-    se += k[3] + ol;
-    fast_two_sum(sh, se, k[2], k[3]);
-  }
+  for (int off = 8; off > 0; off >>= 1)
 #pragma unroll
-  for (int q = 0; q < 4; ++q) a[q] = k[q];
+    for (int q = 0; q < 3; ++q) k[q] += __shfl_xor_sync(0xffffffffu, k[q], off);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) a[q] = k[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -1194,6 +1225,7 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const bool c1 = (ms->cur != 0);
     const bool cert = ms->certify != 0;
     const bool a1 = ms->k == 1;            // A_1 = I + dt_0 is formed from dt_0
+    const int mode = cert ? 2 : (a1 ? 1 : 0);
     const int nsub = bn / 16;              // sub-chunks per tile (even: bn is a multiple of 32)
     const float cs = exp2i(ms->scur), cd = exp2i(ms->sig);
     EpiConst kc;
@@ -1216,6 +1248,8 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       const int b = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
       const bool work = tm < p.ntm;        // rows of a pair tile beyond the padded matrix
+      // per-element masks only where the tile holds a diagonal element or rows beyond n
+      const bool check = (m0 + BM > p.n) || (n0 < m0 + BM && m0 < n0 + bn);
       // theta_j of this lane's four rows (padded arrays: rows up to ld exist)
       const float4 thj_h = work ? ld4(p.th_hi + m0 + 4 * lane) : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 thj_l = work ? ld4(p.th_lo + m0 + 4 * lane) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1249,7 +1283,7 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           else mbar_arrive_remote(acc_empty_leader + (uint32_t)b * 8u);
         }
         if (!all_ok) break;
-        float pa[4] = {0.f, 0.f, 0.f, 0.f}, pb[4] = {0.f, 0.f, 0.f, 0.f};
+        float pa[3] = {0.f, 0.f, 0.f}, pb[3] = {0.f, 0.f, 0.f};
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
           const int sc = c0 / 16 + h;
@@ -1266,15 +1300,11 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           cp_async_wait<1>();              // this lane's copies of sub-chunk sc have landed
           if (work) {
             const uint8_t* eb = EB + (sc & 1) * EB_BYTES;
-            float cur[4] = {0.f, 0.f, 0.f, 0.f};
-            if (S == 1)
-              epi_compute<1>(p, ms, Xs, eb, ew, lane, m0, n0, sc, mx, kc, thj_h, thj_l, cur);
-            else if (S == 2)
-              epi_compute<2>(p, ms, Xs, eb, ew, lane, m0, n0, sc, mx, kc, thj_h, thj_l, cur);
-            else
-              epi_compute<3>(p, ms, Xs, eb, ew, lane, m0, n0, sc, mx, kc, thj_h, thj_l, cur);
+            float cur[3];
+            epi_lean_any(S, mode, check, p, ms, Xs, eb, ew, lane, m0, n0, sc, mx, kc, thj_h,
+                         thj_l, cur);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {   // registers, no indexing by h
+            for (int q = 0; q < 3; ++q) {   // registers, no indexing by h
               if (h == 0) pa[q] = cur[q];
               else pb[q] = cur[q];
             }
@@ -1282,15 +1312,16 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         }
         if (work) {
           // this warp's two columns of the chunk, reduced together
-          warp_sum_ff2(pa, pb, lane);
+          warp_sum3x2(pa, pb, lane);
           const int i = n0 + c0 + 16 * (lane >> 4) + ew;
           if ((lane & 15) == 0 && i < p.n) {
             const int64_t ld = p.ld;
             p.part[((int64_t)0 * p.ntm + tm) * ld + i] = pa[0];
             p.part[((int64_t)1 * p.ntm + tm) * ld + i] = pa[1];
             if (!cert) {
+              // the diagonal increment in plain float: its low part is zero
               p.part[((int64_t)2 * p.ntm + tm) * ld + i] = pa[2];
-              p.part[((int64_t)3 * p.ntm + tm) * ld + i] = pa[3];
+              p.part[((int64_t)3 * p.ntm + tm) * ld + i] = 0.f;
             }
           }
         }
