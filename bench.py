@@ -361,6 +361,20 @@ def bench_dominant(dpt, inputs, dev, pk, steps=20, warmup=3, check=True):
                        "achieved": out["mixed"]["achieved_GBs"], "peak": pk["hbm_gbs"],
                        "unit": "GB/s", "frac": out["mixed"]["hbm_frac"],
                        "algorithmic_bytes_per_pass": bytes_iter}
+    # the gather ceiling: the pass's index stream and random 8-byte gathers of the
+    # (L2-resident, 16 MB) float-float iterate without its arithmetic or value loads
+    zprobe = torch.ones((n, 2), dtype=torch.float32, device=dev)
+    gms = dpt.probe_gather(rp, ci, zprobe, reps=20)
+    out["gather_ceiling"] = {
+        "ms_per_pass": gms,
+        "gathers_per_s": nnz / (gms * 1e-3),
+        "spmv_frac_of_ceiling": gms / out["mixed"]["spmv_ms_per_pass"],
+        "probe": "dpt_probe_gather: same grid, row groups, index stream and 8-byte gathers "
+                 f"({nnz / 1e6:.0f} M per pass into a {8 * n / 1e6:.0f} MB vector), no "
+                 "arithmetic, no value loads"}
+    # a solve against its passes: set-up, checks, host reads and the output outside them
+    out["solve_over_passes"] = out["mixed"]["ms_per_solve"] / (
+        (out["mixed"]["iters"] + 1) * out["mixed"]["spmv_ms_per_pass"])
     return out
 
 

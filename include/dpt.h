@@ -523,6 +523,23 @@ DPT_API dpt_status dpt_server_destroy(dpt_server* srv);
  * DPT_ERR_CUDA otherwise.  Blocks until done. */
 DPT_API dpt_status dpt_selftest_bounded_wait(double seconds, void* stream);
 
+/* Gather probe: a calibration of the CSR form's roofline (no counterpart in the
+ * paper).  Each pass of dpt_solve_dominant streams the matrix and gathers one 8-byte
+ * float pair of the iterate per nonzero at a random column; at the problem sizes of
+ * interest the iterate lives in L2 and the gathers, not HBM, set the pace.  This call
+ * runs a kernel with the pass's grid, row groups, index stream and gathers but none
+ * of its arithmetic or value loads, `reps` times after one warm-up run, and returns
+ * the mean device time of one pass (CUDA events on `stream`) in *ms_per_pass: the
+ * fastest a pass with this access pattern can go on this GPU.
+ *   n, row_ptr, col_idx   CSR structure as for dpt_solve_dominant (device pointers;
+ *                         indices are clamped, not validated)
+ *   z                     n interleaved float pairs (device), the gathered vector
+ *   y                     n floats (device), written with the per-row sums
+ * DPT_ERR_UNSUPPORTED for host pointers.  Blocks until done. */
+DPT_API dpt_status dpt_probe_gather(int64_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                    const void* z, float* y, int32_t reps, double* ms_per_pass,
+                                    void* stream);
+
 /* Free the scratch pool of the current device (no solve may be running). */
 DPT_API void dpt_release_workspace(void);
 

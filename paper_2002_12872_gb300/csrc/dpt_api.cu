@@ -277,7 +277,7 @@ struct Timer {
 // Workspace of one mixed real full solve (the carve order of solve_full_mixed_real).
 void layout_full_mixed_real(Carve& c, int n, bool delta_dev, bool a_dev) {
   const int ld = (int)round_up(n, 128);
-  const int ntm = (n + 127) / 128, ntn = (n + 127) / 128;
+  const int ntm = (n + 127) / 128, ntn = (n + kIter0Cols - 1) / kIter0Cols;
   c.take<IterState>(1);
   c.take<double>(ld);                        // theta (shifted)
   c.take<float>(ld); c.take<float>(ld);      // theta hi/lo
@@ -420,7 +420,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
   // FP16 slices of Delta: two (22 significant bits, against 24 for the three BF16
   // slices of the grouped path) unless a single slice is asked for
   const int S = o.max_slices <= 1 ? 1 : 2;
-  const int ntm = (n + 127) / 128, ntn = (n + 127) / 128;
+  const int ntm = (n + 127) / 128, ntn = (n + kIter0Cols - 1) / kIter0Cols;
   auto layout = [&](Carve& c) { layout_full_mixed_real(c, n, delta_dev, a_dev); };
   Block* b = acquire(measure(layout));
   dpt_status ret = DPT_OK;
@@ -808,17 +808,13 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
     static_assert(sizeof(DomState) <= kPinnedBytes, "pinned scratch size");
     *hs = h;
     CK(cudaMemcpyAsync(st, hs, sizeof(DomState), cudaMemcpyHostToDevice, s));
-    // the CSR structure is validated before anything follows it
+    // The row pointer is validated, and malformed or degenerate input ends the solve,
+    // on the device: the set-up's gate sets the status before any kernel follows
+    // row_ptr, every later kernel returns at once, and the first pass validates the
+    // indices and values before it gathers with them.  No host round trip before the
+    // loop.
     CK(launch_dom_check(n, nnz, rpd, st, s));
-    CK(cudaMemcpyAsync(hs, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (hs->bad_input) throw Fail{DPT_ERR_ARG};
-    CK(launch_dom_setup(n, thd, rpd, cid, vad, thh, thl, st, s));
-    CK(cudaMemcpyAsync(hs, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    if (hs->bad_input) throw Fail{DPT_ERR_ARG};
-    if (hs->ties != 1u) throw Fail{DPT_ERR_DEGENERATE};
-    const int nst = hs->nstar;
+    CK(launch_dom_setup(n, thd, thh, thl, st, s));
     if (o.start) {   // z_0 from the caller's start vector (chart z_{n*} = 1)
       const double* v = o.start;
       if (start_host) {
@@ -834,10 +830,21 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
     const int V = avg < 24 ? 4 : (avg < 48 ? 8 : (avg < 96 ? 16 : 32));
     Prof prof;
     prof.on = o.profile != 0;
-    prof.launches = 9;
-    // the loop starts at k = 0 (no host read of the state before it); it reads k and
-    // the status back after each chunk (DomState and IterState share the layout of
-    // k/status)
+    prof.launches = 11;   // check, set-up (5), init, first pass (2), output ...
+    // The first pass (k = 0) is a kernel of its own, enqueued before the loop: it
+    // validates the CSR data before gathering with it and forms the residual scale.
+    cudaEvent_t f0 = nullptr, f1 = nullptr;
+    if (prof.on) {
+      CK(cudaEventCreate(&f0));
+      CK(cudaEventCreate(&f1));
+      CK(cudaEventRecord(f0, s));
+    }
+    CK(launch_dom_iter(n, V, ff, rpd, cid, vad, thh, thl, thd, zf[0], zf[1], z64[0], z64[1], part,
+                       st, s, /*first=*/true));
+    if (prof.on) CK(cudaEventRecord(f1, s));
+    // the loop starts at k = 1 (no host read of the state before it; its kernels return
+    // at once if the first pass ended the solve); it reads k and the status back after
+    // each chunk (DomState and IterState share the layout of k/status)
     run_loop(b, reinterpret_cast<IterState*>(st), o.graph_iters, o.max_iter, 2, prof,
              [&](int q) {
                prof.before(q, s);
@@ -845,7 +852,15 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
                                   z64[1], part, st, s));
                prof.after(q, s);
              },
-             sizeof(DomState), /*k_first=*/0);
+             sizeof(DomState), /*k_first=*/1);
+    prof.live += 1;   // the first pass
+    if (prof.on) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, f0, f1));
+      prof.ms += t;
+      cudaEventDestroy(f0);
+      cudaEventDestroy(f1);
+    }
     CK(launch_dom_out(n, zf[0], zf[1], z64[0], z64[1], ff, zstage, st, s));
     prof.launches += 1;
     if (!z_dev) CK(cudaMemcpyAsync(z_out, zstage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
@@ -862,7 +877,7 @@ dpt_status solve_dominant(int64_t n64, const double* theta, const int32_t* row_p
       info->iters = hs->k;
       info->residual = hs->rho;
       info->status = ret;
-      info->nstar = nst;
+      info->nstar = hs->nstar;
       info->launches = prof.launches;
       info->product_launches = prof.live;
       info->product_ms = prof.ms;
@@ -1998,6 +2013,44 @@ dpt_status dpt_tune_batched(int64_t count, dpt_dtype dtype, const int64_t* n,
     if (st == DPT_ERR_ARG || st == DPT_ERR_UNSUPPORTED) return st;   // the same for every form
   }
   return *best_form ? DPT_OK : last;
+}
+
+dpt_status dpt_probe_gather(int64_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                            const void* z, float* y, int32_t reps, double* ms_per_pass,
+                            void* stream) {
+  if (n < 1 || n >= INT32_MAX || !row_ptr || !col_idx || !z || !y || reps < 1 || !ms_per_pass)
+    return DPT_ERR_ARG;
+  if (!is_device_ptr(row_ptr) || !is_device_ptr(col_idx) || !is_device_ptr(z) ||
+      !is_device_ptr(y))
+    return DPT_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    int32_t nnz = 0;
+    CK(cudaMemcpyAsync(&nnz, row_ptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (nnz < 0) return DPT_ERR_ARG;
+    // the lanes per row the map's pass would use for this mean row length
+    const double avg = (double)nnz / (double)n;
+    const int V = avg < 24 ? 4 : (avg < 48 ? 8 : (avg < 96 ? 16 : 32));
+    const float2* zz = static_cast<const float2*>(z);
+    CK(launch_probe_gather((int)n, V, row_ptr, col_idx, zz, y, s));   // warm-up
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) CK(launch_probe_gather((int)n, V, row_ptr, col_idx, zz, y, s));
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_pass = (double)ms / reps;
+    return DPT_OK;
+  } catch (Fail f) {
+    cudaStreamSynchronize(s);
+    return f.st;
+  }
 }
 
 void dpt_release_workspace(void) {

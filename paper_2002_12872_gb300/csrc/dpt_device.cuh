@@ -588,11 +588,37 @@ __device__ __forceinline__ void warp_sum_ff(float& r2, float& a2, float& eh, flo
 }
 
 // ---------------------------------------------------------------------------
-// Convergence decision shared by the control kernels (run by one thread of the
-// last block).  rho is the normalised max residual of the iterate A_k.
-// Returns true when the iteration continues (k and cur advanced).
+// The state as one register copy.  A control kernel's last block reads the state
+// after every other block's atomics: reading each field through a volatile pointer
+// costs a round trip to L2 per field that a branch depends on, so the deciding
+// thread loads all of it at once (L2 loads, issued together), decides on the copy
+// and writes it back.  No other kernel runs meanwhile, and the grid's other blocks
+// have finished with the state when the last one takes over.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool decide(volatile IterState* vs, double rho) {
+template <class T>
+__device__ __forceinline__ void state_load(const T* st, T& ls) {
+  static_assert(sizeof(T) % 8 == 0, "the state is copied as 8-byte words");
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(st);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(&ls);
+#pragma unroll
+  for (int w = 0; w < (int)(sizeof(T) / 8); ++w) dst[w] = __ldcg(src + w);
+}
+template <class T>
+__device__ __forceinline__ void state_store(T* st, const T& ls) {
+  const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&ls);
+  unsigned long long* dst = reinterpret_cast<unsigned long long*>(st);
+#pragma unroll
+  for (int w = 0; w < (int)(sizeof(T) / 8); ++w) __stcg(dst + w, src[w]);
+}
+
+// ---------------------------------------------------------------------------
+// Convergence decision shared by the control kernels (run by one thread of the
+// last block), on the state or on a register copy of it.  rho is the normalised
+// max residual of the iterate A_k.  Returns true when the iteration continues (k
+// and cur advanced).
+// ---------------------------------------------------------------------------
+template <class SP>
+__device__ __forceinline__ bool decide(SP* vs, double rho) {
   vs->rho = rho;
   if (vs->bad_input) { vs->status = ST_BADINPUT; return false; }
   if (vs->timeout) { vs->status = ST_TIMEOUT; return false; }
@@ -618,7 +644,8 @@ __device__ __forceinline__ bool decide(volatile IterState* vs, double rho) {
 // the statuses of decide() when the iterate fails or passes; otherwise the state is
 // left as it is (k not advanced) so that the same iteration runs again in full.
 // Returns true when the iteration continues.
-__device__ __forceinline__ bool decide_final(volatile IterState* vs, double rho) {
+template <class SP>
+__device__ __forceinline__ bool decide_final(SP* vs, double rho) {
   vs->rho = rho;
   if (vs->bad_input) { vs->status = ST_BADINPUT; return false; }
   if (vs->timeout) { vs->status = ST_TIMEOUT; return false; }
@@ -629,7 +656,8 @@ __device__ __forceinline__ bool decide_final(volatile IterState* vs, double rho)
 
 // The same for a single-vector solve: the next step applies lambda - dlam with
 // dlam = lambda alpha^k (carried in FP64 and as a float pair).
-__device__ __forceinline__ void dom_ramp_advance(volatile DomState* vs) {
+template <class SP>
+__device__ __forceinline__ void dom_ramp_advance(SP* vs) {
   if (!(vs->ramp_alpha > 0.0)) return;
   double pw = vs->ramp_pow * vs->ramp_alpha;
   if (pw < 0x1p-60) pw = 0.0;
@@ -650,7 +678,8 @@ __device__ __forceinline__ void dom_ramp_advance(volatile DomState* vs) {
 // dmax <= 2^-8 dmax1, one once dmax <= 2^-16 dmax1 (or below slice_tol).  The
 // carried remainder makes the fixed point that of the full Delta either way.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int next_slices(volatile IterState* vs, float dmax, bool first) {
+template <class SP>
+__device__ __forceinline__ int next_slices(SP* vs, float dmax, bool first) {
   if (first) vs->dmax1 = dmax;
   const float d1 = vs->dmax1;
   int S = vs->max_slices;
@@ -662,8 +691,8 @@ __device__ __forceinline__ int next_slices(volatile IterState* vs, float dmax, b
 // The same rule for FP16 slices (11 significant bits each, so about 2^(-11 S)
 // relative) of a solve whose first product used nsl of them: S slices once
 // dmax <= 2^(-11 (nsl - S)) dmax1, one below slice_tol.
-__device__ __forceinline__ int next_slices_f16(volatile IterState* vs, float dmax, bool first,
-                                               int nsl) {
+template <class SP>
+__device__ __forceinline__ int next_slices_f16(SP* vs, float dmax, bool first, int nsl) {
   if (first) vs->dmax1 = dmax;
   const float d1 = vs->dmax1;
   if ((double)dmax < vs->slice_tol) return 1;

@@ -45,68 +45,33 @@ __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, f
 }
 
 // ---------------------------------------------------------------------------
-// Set-up: theta -> float-float, residual scale row sums, CSR validity, argmax.
-// Eight consecutive lanes share a row: they read its indices and values eight
-// apart (a warp's load covers four rows' consecutive entries), sum |v| and reduce
-// with three shuffles; the group's first lane handles theta_m.
+// Set-up: theta -> float-float, max |theta| (the residual scale's first term), the
+// largest theta (for n*), finiteness.  The CSR indices and values are validated, and
+// the row sums of |Delta| formed, by the first pass of the map, which reads them
+// anyway (k_dom_iter at k = 0).
 // ---------------------------------------------------------------------------
-constexpr int SETUP_V = 8;
-
 __global__ void __launch_bounds__(256) k_dom_setup(int n, const double* __restrict__ theta,
-                                                   const int32_t* __restrict__ row_ptr,
-                                                   const int32_t* __restrict__ col_idx,
-                                                   const float* __restrict__ vals,
                                                    float* __restrict__ th_hi,
                                                    float* __restrict__ th_lo, DomState* st) {
-  float rmax = 0.f, amax = 0.f;
+  float amax = 0.f;
   unsigned long long tmax = 0ull;
   bool bad = false;
-  const int g = threadIdx.x & (SETUP_V - 1);
-  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;   // a multiple of SETUP_V
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;; base += nthr) {
-    const int64_t m64 = base / SETUP_V;
-    const bool act = m64 < n;
-    if (__all_sync(0xffffffffu, !act)) break;   // the warp leaves together
-    float rs = 0.f;
-    if (act) {
-      const int m = (int)m64;
-      const int ra = row_ptr[m], rb = row_ptr[m + 1];
-      if (rb < ra) {
-        bad = true;
-      } else {
-        for (int q = ra + g; q < rb; q += SETUP_V) {
-          const int c = col_idx[q];
-          const float v = vals[q];
-          if (c < 0 || c >= n || !(fabsf(v) <= 3.4e38f)) bad = true;
-          rs += fabsf(v);
-        }
-      }
-    }
-    // the group's lanes are aligned within the warp: xor 1, 2, 4 stay inside it
-    rs += __shfl_xor_sync(0xffffffffu, rs, 1);
-    rs += __shfl_xor_sync(0xffffffffu, rs, 2);
-    rs += __shfl_xor_sync(0xffffffffu, rs, 4);
-    if (act && g == 0) {
-      const int m = (int)m64;
-      const double t = theta[m];
-      if (!finite_bits(t)) bad = true;
-      float h, l;
-      split_double(t, h, l);
-      th_hi[m] = h;
-      th_lo[m] = l;
-      amax = fmaxf(amax, fabsf(h));
-      tmax = max(tmax, ordered_bits(t));
-      rmax = fmaxf(rmax, rs);
-    }
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+    const double t = theta[m];
+    if (!finite_bits(t)) bad = true;
+    float h, l;
+    split_double(t, h, l);
+    th_hi[m] = h;
+    th_lo[m] = l;
+    amax = fmaxf(amax, fabsf(h));
+    tmax = max(tmax, ordered_bits(t));
   }
   if (bad) atomicExch(&st->bad_input, 1u);
   for (int o = 16; o > 0; o >>= 1) {
-    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
     amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     tmax = max(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
   }
   if ((threadIdx.x & 31) == 0) {
-    atomicMax(&st->row_bits, __float_as_uint(rmax));
     atomicMax(&st->absmax_bits, __float_as_uint(amax));
     atomicMax(&st->theta_bits, tmax);
   }
@@ -133,8 +98,13 @@ __global__ void k_dom_argmax(int n, const double* __restrict__ theta, DomState* 
     if (ordered_bits(theta[m]) == tmax) atomicMin(&st->nstar_min, m);
 }
 
-__global__ void k_dom_pick(DomState* st) {
-  st->nstar = (st->nstar_req >= 0) ? st->nstar_req : st->nstar_min;
+__global__ void k_dom_pick(int n, DomState* st) {
+  int ns = (st->nstar_req >= 0) ? st->nstar_req : st->nstar_min;
+  if (ns < 0 || ns >= n) {   // no index held the largest theta: keep later reads in bounds
+    ns = 0;
+    st->bad_input = 1u;
+  }
+  st->nstar = ns;
 }
 
 // Number of m with theta_m == theta_{n*} (1 unless the map would divide by zero).
@@ -147,21 +117,28 @@ __global__ void k_dom_ties(int n, const double* __restrict__ theta, DomState* st
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->ties, cnt);
 }
 
-// z_0 = e_{n*} and the residual scale s = max|theta| + |lambda| max_m sum_k |Delta_mk|.
+// The checks before the loop, on the device (no host round trip): a malformed row
+// pointer or a non-finite theta ends the solve with ST_BADINPUT, a theta equal to
+// theta_{n*} elsewhere (the map would divide by zero) with ST_DEGENERATE; every later
+// kernel then returns at once, before it follows row_ptr.  One thread, after the
+// set-up, selection and tie count.
+__global__ void k_dom_gate(DomState* st) {
+  if (st->bad_input) st->status = ST_BADINPUT;
+  else if (st->ties != 1u) st->status = ST_DEGENERATE;
+}
+
+// z_0 = e_{n*}.
 __global__ void k_dom_init(int n, float2* __restrict__ z, DomState* st) {
   const int nstar = st->nstar;
   for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x)
     z[m] = make_float2((m == nstar) ? 1.f : 0.f, 0.f);
-  if (blockIdx.x == 0 && threadIdx.x == 0)
-    st->s = (double)__uint_as_float(st->absmax_bits) +
-            fabs(st->lam) * (double)__uint_as_float(st->row_bits);
 }
 
 // ---------------------------------------------------------------------------
 // Pre-pass: y* = (Delta z)_{n*}, one warp.
 // ---------------------------------------------------------------------------
 template <bool FF>
-__global__ void k_dom_ystar(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
+__global__ void k_dom_ystar(int n, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                             const float* __restrict__ vals, const float2* __restrict__ z0,
                             const float2* __restrict__ z1, const double* __restrict__ z64_0,
                             const double* __restrict__ z64_1, DomState* st) {
@@ -169,11 +146,21 @@ __global__ void k_dom_ystar(const int32_t* __restrict__ row_ptr, const int32_t* 
   const int lane = threadIdx.x;
   const int nstar = st->nstar;
   const int a = row_ptr[nstar], b = row_ptr[nstar + 1];
+  // row n*'s indices are checked here: the main pass validates the others before its
+  // first gathers (an index out of range is read as column 0 and ends the solve)
+  auto col = [&](int q) {
+    const int c = col_idx[q];
+    if ((unsigned)c >= (unsigned)n) {
+      atomicExch(&st->bad_input, 1u);
+      return 0;
+    }
+    return c;
+  };
   if (FF) {
     const float2* z = st->cur ? z1 : z0;
     float ah = 0.f, al = 0.f;
     for (int q = a + lane; q < b; q += 32) {
-      const float2 zc = z[col_idx[q]];
+      const float2 zc = z[col(q)];
       ff_fma_acc(vals[q], zc.x, zc.y, ah, al);
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -185,7 +172,7 @@ __global__ void k_dom_ystar(const int32_t* __restrict__ row_ptr, const int32_t* 
   } else {
     const double* z = st->cur ? z64_1 : z64_0;
     double acc = 0.0;
-    for (int q = a + lane; q < b; q += 32) acc = fma((double)vals[q], z[col_idx[q]], acc);
+    for (int q = a + lane; q < b; q += 32) acc = fma((double)vals[q], z[col(q)], acc);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) st->ys64 = acc;
   }
@@ -195,10 +182,81 @@ __global__ void k_dom_ystar(const int32_t* __restrict__ row_ptr, const int32_t* 
 // Main pass: one group of V lanes per row (V = 4, 8, 16 or 32 by mean row
 // length).  Each group sums its row of Delta z, the group leader applies the
 // update and accumulates |R|^2 and |z|^2; per-block partials; the last block
-// reduces them and takes the convergence decision.
+// reduces them and takes the convergence decision.  The first pass (k = 0) also
+// validates every index and value before it gathers with it (a bad one is read as
+// column 0 with value 0 and ends the solve) and forms the row sums of |Delta| for
+// the residual scale s = max|theta| + |lambda| max_m sum_k |Delta_mk|, which its own
+// decision needs.
 // ---------------------------------------------------------------------------
-template <bool FF, int V>
-__global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restrict__ row_ptr,
+// The decision after a pass (one thread of the last block): the fields it reads are
+// loaded together from L2 (one round trip instead of one per field a branch depends
+// on), the eigenvalue and residual of the assessed iterate formed, the residual scale
+// on the first pass, then the statuses of the full-spectrum decision, stored back
+// field by field.  The grid's other blocks are done with the state by now.
+template <bool FF, bool FIRST>
+__device__ __forceinline__ void dom_decide(DomState* st, double theta_star, double R2, double Z2) {
+  const unsigned bad = __ldcg(&st->bad_input);
+  const double lam = __ldcg(&st->lam), tol = __ldcg(&st->tol), best = __ldcg(&st->best);
+  const int grown = __ldcg(&st->grown), k = __ldcg(&st->k), max_iter = __ldcg(&st->max_iter);
+  const double ys = FF ? (double)__ldcg(&st->ys_hi) + (double)__ldcg(&st->ys_lo)
+                       : __ldcg(&st->ys64);
+  double s;
+  if (FIRST) {
+    s = (double)__uint_as_float(__ldcg(&st->absmax_bits)) +
+        fabs(lam) * (double)__uint_as_float(__ldcg(&st->row_bits));
+    st->s = s;
+  } else {
+    s = __ldcg(&st->s);
+  }
+  st->blocks_done = 0;
+  st->E = theta_star + lam * ys;   // eigenvalue of the iterate that was just assessed
+  const double rho = sqrt(R2) / (s * sqrt(Z2));
+  st->rho = rho;
+  if (bad) { st->status = ST_BADINPUT; return; }
+  if (!(rho == rho) || isinf(rho)) { st->status = ST_DIVERGED; return; }
+  if (rho <= tol) { st->status = ST_CONVERGED; return; }
+  if (rho < best) {
+    st->best = rho;
+    st->grown = 0;
+  } else if (rho > 10.0 * best) {
+    if (grown + 1 >= 20) { st->grown = grown + 1; st->status = ST_DIVERGED; return; }
+    st->grown = grown + 1;
+  } else {
+    st->grown = 0;
+  }
+  if (k >= max_iter) { st->status = ST_MAXITER; return; }
+  st->k = k + 1;
+  st->cur = (k + 1) & 1;
+  if (__ldcg(&st->ramp_alpha) > 0.0) dom_ramp_advance(st);
+}
+
+// the next four entries of a lane in the row: index, value; checked on the first pass
+template <bool FIRST>
+__device__ __forceinline__ void dom_fetch4(const int32_t* __restrict__ col_idx,
+                                           const float* __restrict__ vals, int q, int b, int V,
+                                           int n, int (&c)[4], float (&v)[4], bool& bad,
+                                           float& rsum) {
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int qq = q + u * V;
+    const bool ok = qq < b;
+    c[u] = ok ? col_idx[qq] : 0;
+    v[u] = ok ? vals[qq] : 0.f;
+  }
+  if (FIRST) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if ((unsigned)c[u] >= (unsigned)n || !(fabsf(v[u]) <= 3.4e38f)) {
+        bad = true;
+        c[u] = 0;
+        v[u] = 0.f;
+      }
+      rsum += fabsf(v[u]);
+    }
+  }
+}
+template <bool FF, int V, bool FIRST>
+__device__ __forceinline__ void dom_iter_body(int n, const int32_t* __restrict__ row_ptr,
                                                   const int32_t* __restrict__ col_idx,
                                                   const float* __restrict__ vals,
                                                   const float* __restrict__ th_hi,
@@ -209,9 +267,10 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
                                                   double* __restrict__ z64_0,
                                                   double* __restrict__ z64_1,
                                                   double* __restrict__ part, DomState* st) {
-  if (st->status != ST_RUNNING) return;
   const int lane = threadIdx.x & 31;
   const int gl = lane & (V - 1);
+  bool bad = false;        // first pass: an index out of range or a non-finite value
+  float rmax = 0.f;        // first pass: the largest row sum of |Delta| seen
   const int groups_per_block = blockDim.x / V;
   const int g0 = blockIdx.x * groups_per_block + threadIdx.x / V;
   const int gstride = gridDim.x * groups_per_block;
@@ -233,7 +292,7 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
     const int rounds = (n + gstride - 1) / gstride;
     for (int rd = 0; rd < rounds; ++rd) {
       const int m = g0 + rd * gstride;
-      float ah = 0.f, al = 0.f;
+      float ah = 0.f, al = 0.f, rsum = 0.f;
       if (m < n) {
         const int a = row_ptr[m], b = row_ptr[m + 1];
         // Memory-level parallelism: each pass issues the lane's next four index and
@@ -243,13 +302,7 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
           int c[4];
           float v[4];
           float2 zz[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int qq = q + u * V;
-            const bool ok = qq < b;
-            c[u] = ok ? col_idx[qq] : 0;
-            v[u] = ok ? vals[qq] : 0.f;
-          }
+          dom_fetch4<FIRST>(col_idx, vals, q, b, V, n, c, v, bad, rsum);
 #pragma unroll
           for (int u = 0; u < 4; ++u) zz[u] = z[c[u]];
 #pragma unroll
@@ -262,7 +315,9 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
         const float oh = __shfl_xor_sync(0xffffffffu, ah, o);
         const float ol = __shfl_xor_sync(0xffffffffu, al, o);
         ff_add(ah, al, oh, ol, ah, al);
+        if (FIRST) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
       }
+      if (FIRST && gl == 0 && m < n) rmax = fmaxf(rmax, rsum);
       if (gl == 0 && m < n) {
         const float2 zm2 = z[m];
         const float zmh = zm2.x, zml = zm2.y;
@@ -305,6 +360,7 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
     for (int rd = 0; rd < rounds; ++rd) {
       const int m = g0 + rd * gstride;
       double acc = 0.0;
+      float rsum = 0.f;
       if (m < n) {
         const int a = row_ptr[m], b = row_ptr[m + 1];
         int q = a + gl;
@@ -312,13 +368,7 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
           int c[4];
           float v[4];
           double zz[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int qq = q + u * V;
-            const bool ok = qq < b;
-            c[u] = ok ? col_idx[qq] : 0;
-            v[u] = ok ? vals[qq] : 0.f;
-          }
+          dom_fetch4<FIRST>(col_idx, vals, q, b, V, n, c, v, bad, rsum);
 #pragma unroll
           for (int u = 0; u < 4; ++u) zz[u] = z[c[u]];
 #pragma unroll
@@ -327,7 +377,11 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
         }
       }
 #pragma unroll
-      for (int o = V / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      for (int o = V / 2; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (FIRST) rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+      }
+      if (FIRST && gl == 0 && m < n) rmax = fmaxf(rmax, rsum);
       if (gl == 0 && m < n) {
         const double zm = z[m];
         if (m == nstar) {
@@ -345,6 +399,16 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
     }
   }
   if (FF) { r2 = (double)r2f; z2 = (double)z2f; }
+  if (FIRST) {
+    // row sums and validity of the first pass, visible before this block counts in
+    for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    const bool wbad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+      atomicMax(&st->row_bits, __float_as_uint(rmax));
+      if (wbad) atomicExch(&st->bad_input, 1u);
+      __threadfence();
+    }
+  }
   // block reduction, then the last block decides
   for (int o = 16; o > 0; o >>= 1) {
     r2 += __shfl_xor_sync(0xffffffffu, r2, o);
@@ -382,24 +446,27 @@ __global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restri
   if (threadIdx.x != 0) return;
   R2 = 0.0; Z2 = 0.0;
   for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { R2 += sr[0][q]; Z2 += sr[1][q]; }
-  volatile DomState* vs = st;
-  vs->blocks_done = 0;
-  // eigenvalue of the iterate that was just assessed
-  if (FF) vs->E = theta[nstar] + vs->lam * ((double)vs->ys_hi + (double)vs->ys_lo);
-  else vs->E = theta[nstar] + vs->lam * vs->ys64;
-  const double rho = sqrt(R2) / (vs->s * sqrt(Z2));
-  vs->rho = rho;
-  if (vs->bad_input) { vs->status = ST_BADINPUT; return; }
-  if (!(rho == rho) || isinf(rho)) { vs->status = ST_DIVERGED; return; }
-  if (rho <= vs->tol) { vs->status = ST_CONVERGED; return; }
-  if (rho < vs->best) { vs->best = rho; vs->grown = 0; }
-  else if (rho > 10.0 * vs->best) {
-    if (++vs->grown >= 20) { vs->status = ST_DIVERGED; return; }
-  } else vs->grown = 0;
-  if (vs->k >= vs->max_iter) { vs->status = ST_MAXITER; return; }
-  vs->k = vs->k + 1;
-  vs->cur = vs->k & 1;
-  dom_ramp_advance(vs);
+  dom_decide<FF, FIRST>(st, theta[nstar], R2, Z2);
+}
+
+// The pass as a kernel of its own per variant: the first pass (k = 0; it validates
+// the CSR data and forms the row sums) needs more registers than the others, which
+// keep the occupancy of the plain pass.
+template <bool FF, int V, bool FIRST>
+__global__ void __launch_bounds__(256) k_dom_iter(int n, const int32_t* __restrict__ row_ptr,
+                                                  const int32_t* __restrict__ col_idx,
+                                                  const float* __restrict__ vals,
+                                                  const float* __restrict__ th_hi,
+                                                  const float* __restrict__ th_lo,
+                                                  const double* __restrict__ theta,
+                                                  float2* __restrict__ z0,
+                                                  float2* __restrict__ z1,
+                                                  double* __restrict__ z64_0,
+                                                  double* __restrict__ z64_1,
+                                                  double* __restrict__ part, DomState* st) {
+  if (st->status != ST_RUNNING) return;
+  dom_iter_body<FF, V, FIRST>(n, row_ptr, col_idx, vals, th_hi, th_lo, theta, z0, z1, z64_0,
+                              z64_1, part, st);
 }
 
 // Output: z (float-float or FP64) of the assessed iterate -> FP64.
@@ -437,9 +504,6 @@ __global__ void k_dom_start(int n, const double* __restrict__ v, float2* __restr
     if (z64) z64[m] = q;
   }
   if (bad) atomicExch(&st->bad_input, 1u);
-  if (blockIdx.x == 0 && threadIdx.x == 0)
-    st->s = (double)__uint_as_float(st->absmax_bits) +
-            fabs(st->lam) * (double)__uint_as_float(st->row_bits);
 }
 
 __global__ void k_dom_init64(int n, double* z, const DomState* st) {
@@ -470,27 +534,22 @@ cudaError_t launch_dom_check(int n, int64_t nnz, const int32_t* row_ptr, DomStat
   return cudaGetLastError();
 }
 
-cudaError_t launch_dom_setup(int n, const double* theta, const int32_t* row_ptr,
-                             const int32_t* col_idx, const float* vals, float* th_hi,
-                             float* th_lo, DomState* st, cudaStream_t s) {
-  // SETUP_V lanes per row, so SETUP_V times the rows' threads
-  static int nsm = 0;
-  if (nsm == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (nsm <= 0) nsm = 132;
-  }
-  const int64_t want = ((int64_t)n * SETUP_V + 255) / 256;
-  const int grid = want < 8 * nsm ? (want > 0 ? (int)want : 1) : 8 * nsm;
-  k_dom_setup<<<grid, 256, 0, s>>>(n, theta, row_ptr, col_idx, vals, th_hi, th_lo, st);
-  return launch_dom_select(n, theta, st, s);
+// The set-up before the loop: theta split and maxima, n*, the tie count, and the
+// device-side gate that ends malformed or degenerate solves before any kernel follows
+// row_ptr (the row pointer was checked by launch_dom_check just before).
+cudaError_t launch_dom_setup(int n, const double* theta, float* th_hi, float* th_lo, DomState* st,
+                             cudaStream_t s) {
+  k_dom_setup<<<dom_grid(n), 256, 0, s>>>(n, theta, th_hi, th_lo, st);
+  cudaError_t e = launch_dom_select(n, theta, st, s);
+  if (e != cudaSuccess) return e;
+  k_dom_gate<<<1, 1, 0, s>>>(st);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_dom_select(int n, const double* theta, DomState* st, cudaStream_t s) {
   const int g = dom_grid(n);
   k_dom_argmax<<<g, 256, 0, s>>>(n, theta, st);
-  k_dom_pick<<<1, 1, 0, s>>>(st);
+  k_dom_pick<<<1, 1, 0, s>>>(n, st);
   k_dom_ties<<<g, 256, 0, s>>>(n, theta, st);
   return cudaGetLastError();
 }
@@ -513,15 +572,17 @@ cudaError_t launch_dom_iter(int n, int vlanes, int ff, const int32_t* row_ptr,
                             const int32_t* col_idx, const float* vals, const float* th_hi,
                             const float* th_lo, const double* theta, float2* z0, float2* z1,
                             double* z64_0, double* z64_1, double* part, DomState* st,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool first) {
   if (ff)
-    k_dom_ystar<true><<<1, 32, 0, s>>>(row_ptr, col_idx, vals, z0, z1, z64_0, z64_1, st);
+    k_dom_ystar<true><<<1, 32, 0, s>>>(n, row_ptr, col_idx, vals, z0, z1, z64_0, z64_1, st);
   else
-    k_dom_ystar<false><<<1, 32, 0, s>>>(row_ptr, col_idx, vals, z0, z1, z64_0, z64_1, st);
+    k_dom_ystar<false><<<1, 32, 0, s>>>(n, row_ptr, col_idx, vals, z0, z1, z64_0, z64_1, st);
   const int g = dom_grid(n);
-#define DOM_LAUNCH(FFV, VV)                                                                    \
-  k_dom_iter<FFV, VV><<<g, 256, 0, s>>>(n, row_ptr, col_idx, vals, th_hi, th_lo, theta, z0, z1, \
-                                        z64_0, z64_1, part, st)
+#define DOM_LAUNCH1(FFV, VV, FI)                                                                \
+  k_dom_iter<FFV, VV, FI><<<g, 256, 0, s>>>(n, row_ptr, col_idx, vals, th_hi, th_lo, theta, z0, \
+                                            z1, z64_0, z64_1, part, st)
+#define DOM_LAUNCH(FFV, VV) \
+  do { if (first) DOM_LAUNCH1(FFV, VV, true); else DOM_LAUNCH1(FFV, VV, false); } while (0)
   if (ff) {
     switch (vlanes) {
       case 4: DOM_LAUNCH(true, 4); break;
@@ -538,6 +599,7 @@ cudaError_t launch_dom_iter(int n, int vlanes, int ff, const int32_t* row_ptr,
     }
   }
 #undef DOM_LAUNCH
+#undef DOM_LAUNCH1
   return cudaGetLastError();
 }
 
@@ -545,6 +607,65 @@ cudaError_t launch_dom_out(int n, const float2* z0, const float2* z1, const doub
                            const double* z64_1, int ff, double* out, const DomState* st,
                            cudaStream_t s) {
   k_dom_out<<<(n + 255) / 256, 256, 0, s>>>(n, z0, z1, z64_0, z64_1, ff, out, st);
+  return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Gather probe (a calibration of the roofline, not part of the map): the main pass's
+// memory traffic without its arithmetic.  The same grid, the same groups of V lanes
+// per row, the same four index loads in flight per lane and the same 8-byte gathers
+// of an interleaved float pair per nonzero; each row's sum of the gathered high parts
+// is written out so that no load can be dropped.  Reads 4 B of index per nonzero (no
+// values) and writes 4 B per row.
+// ---------------------------------------------------------------------------
+template <int V>
+__global__ void __launch_bounds__(256) k_probe_gather(int n, const int32_t* __restrict__ row_ptr,
+                                                      const int32_t* __restrict__ col_idx,
+                                                      const float2* __restrict__ z,
+                                                      float* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int gl = lane & (V - 1);
+  const int groups_per_block = blockDim.x / V;
+  const int g0 = blockIdx.x * groups_per_block + threadIdx.x / V;
+  const int gstride = gridDim.x * groups_per_block;
+  const int rounds = (n + gstride - 1) / gstride;
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int m = g0 + rd * gstride;
+    float acc = 0.f;
+    if (m < n) {
+      const int a = row_ptr[m], b = row_ptr[m + 1];
+      for (int q = a + gl;; q += 4 * V) {
+        int c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int qq = q + u * V;
+          // the probe does not validate its input: out-of-range indices are clamped
+          c[u] = qq < b ? min(max(col_idx[qq], 0), n - 1) : 0;
+        }
+        float2 zz[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) zz[u] = z[c[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc += zz[u].x;
+        if (q + 4 * V >= b) break;
+      }
+    }
+#pragma unroll
+    for (int o = V / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (gl == 0 && m < n) y[m] = acc;
+  }
+}
+
+cudaError_t launch_probe_gather(int n, int vlanes, const int32_t* row_ptr, const int32_t* col_idx,
+                                const float2* z, float* y, cudaStream_t s) {
+  const int g = dom_grid(n);
+  switch (vlanes) {
+    case 4: k_probe_gather<4><<<g, 256, 0, s>>>(n, row_ptr, col_idx, z, y); break;
+    case 8: k_probe_gather<8><<<g, 256, 0, s>>>(n, row_ptr, col_idx, z, y); break;
+    case 16: k_probe_gather<16><<<g, 256, 0, s>>>(n, row_ptr, col_idx, z, y); break;
+    default: k_probe_gather<32><<<g, 256, 0, s>>>(n, row_ptr, col_idx, z, y); break;
+  }
   return cudaGetLastError();
 }
 

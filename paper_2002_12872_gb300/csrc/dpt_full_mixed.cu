@@ -45,7 +45,7 @@ constexpr int UK = 16;           // K per tcgen05.mma (kind::f16)
 constexpr int STAGES = 4;        // operand ring depth (bytes in flight cover the L2 latency)
 constexpr int MAX_STAGES = 8;    // barrier slots; the CTA-pair kernel fits more, smaller stages
 constexpr int NACC = 2;          // TMEM accumulators (double buffer)
-constexpr int IT0 = 128;         // columns (and rows) per block of iteration 0
+constexpr int IT0 = 128;         // rows per block of iteration 0 (its columns: kIter0Cols)
 constexpr int NSLICE = 3;        // FP16 slices of Delta the layout holds (the solve writes
                                  // max_slices of them, the product uses the first S)
 constexpr int A_TILE = BM * BK * 2;
@@ -272,10 +272,12 @@ __global__ void __launch_bounds__(256) k_iter0(const double* __restrict__ delta,
                                                float* __restrict__ L, double* __restrict__ d,
                                                float* __restrict__ part,
                                                float* __restrict__ rowpart, IterState* st) {
-  constexpr int W = 8, CPW = IT0 / W;   // warps, columns per warp
+  // 128 x 64 tiles: 2048 blocks at n = 4096, 4.5 waves of three resident blocks per SM
+  // (128 x 128 tiles left a last wave a quarter full)
+  constexpr int W = 8, CPW = kIter0Cols / W;   // warps, columns per warp
   __shared__ float rows[W][IT0];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int n0 = blockIdx.x * IT0, m0 = blockIdx.y * IT0, tm = blockIdx.y;
+  const int n0 = blockIdx.x * kIter0Cols, m0 = blockIdx.y * IT0, tm = blockIdx.y;
   const int r0 = 4 * lane, j0 = m0 + r0;
   const int64_t cat_ld = (int64_t)NSLICE * ld;
   const float qs = exp2i(st->sexp[0]), iqs = exp2i(-st->sexp[0]);
@@ -400,6 +402,45 @@ __global__ void __launch_bounds__(256) k_iter0(const double* __restrict__ delta,
 // advance d, and decide: converged / diverged / max_iter / continue (and with
 // how many Delta slices).  The last block to finish takes the decision.
 // ---------------------------------------------------------------------------
+// The decision of k_ctrl on the register copy of the state (see state_load).
+__device__ __forceinline__ void ctrl_decide(IterState& ls, bool first, bool cert) {
+  IterState* vs = &ls;
+  if (first) vs->s = vs->theta_max + fabs(vs->lam) * (double)__uint_as_float(vs->row_bits);
+  const double rho = (double)__uint_as_float(vs->rho_bits) / vs->s;
+  vs->blocks_done = 0;
+  vs->rho_bits = 0;
+  const float dmax = __uint_as_float(vs->dmax_bits);
+  vs->dmax_bits = 0;
+  // every increment of the returned iterate is bounded by one of these maxima
+  vs->dsum = vs->dsum + (double)dmax;
+  // the rounding of the float recursion grows with the residuals it carried
+  if (!first) vs->rho_sum = vs->rho_sum + rho;
+  if (cert) {
+    // the certifying pass assessed A_k: stop if it passed, else run the same
+    // iteration again in full (nothing it depends on was touched)
+    vs->certify = 0;
+    if (decide_final(vs, rho)) vs->slice_gemms = vs->slice_gemms + vs->slices;
+    return;
+  }
+  const double prev = vs->rho_last;
+  vs->rho_last = rho;
+  if (!decide(vs, rho)) return;
+  const int S = next_slices_f16(vs, dmax, first, vs->max_slices);
+  vs->slices = S;
+  vs->slice_gemms = vs->slice_gemms + S;
+  // the next product writes dt_k into buffer cur: scaled so that the largest
+  // increment of the last step, dmax, would land at 2^10 (increments shrink as the
+  // iteration converges; 32-fold growth still fits, more is clamped and the
+  // remainder keeps the rest)
+  vs->sexp[vs->cur] = dt_scale_exp((double)dmax, 10, vs->sig, vs->lam);
+  // When the residual falls geometrically and the next one is predicted below half
+  // the tolerance, the next product only forms the residual of its iterate (no new
+  // iterate, increment or remainder is written): the last product of a converging
+  // solve then costs little more than its matrix product.
+  vs->certify = (vs->certify_on && vs->k >= 3 && prev > 0.0 && rho < prev &&
+                 rho * (rho / prev) <= 0.5 * vs->tol) ? 1 : 0;
+}
+
 __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
                                               const float* __restrict__ part,
                                               const float* __restrict__ rowpart,
@@ -477,42 +518,12 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
   __syncthreads();
   if (!last || threadIdx.x != 0) return;
   __threadfence();
-  volatile IterState* vs = st;
-  if (first) vs->s = vs->theta_max + fabs(vs->lam) * (double)__uint_as_float(vs->row_bits);
-  const double rho = (double)__uint_as_float(vs->rho_bits) / vs->s;
-  vs->blocks_done = 0;
-  vs->rho_bits = 0;
-  const float dmax = __uint_as_float(vs->dmax_bits);
-  vs->dmax_bits = 0;
-  // every increment of the returned iterate is bounded by one of these maxima
-  vs->dsum = vs->dsum + (double)dmax;
-  // the rounding of the float recursion grows with the residuals it carried
-  if (!first) vs->rho_sum = vs->rho_sum + rho;
-  if (cert) {
-    // the certifying pass assessed A_k: stop if it passed, else run the same
-    // iteration again in full (nothing it depends on was touched)
-    vs->certify = 0;
-    if (decide_final(vs, rho)) vs->slice_gemms = vs->slice_gemms + vs->slices;
-    return;
-  }
-  const double prev = vs->rho_last;
-  vs->rho_last = rho;
-  if (!decide(vs, rho)) return;
-  const int S = next_slices_f16(vs, dmax, first, vs->max_slices);
-  vs->slices = S;
-  vs->slice_gemms = vs->slice_gemms + S;
-  // the next product writes dt_k into buffer cur: scaled so that the largest
-  // increment of the last step, dmax, would land at 2^10 (increments shrink as the
-  // iteration converges; 32-fold growth still fits, more is clamped and the
-  // remainder keeps the rest)
-  vs->sexp[vs->cur] = dt_scale_exp((double)dmax, 10, vs->sig, vs->lam);
-  // When the residual falls geometrically and the next one is predicted below half
-  // the tolerance, the next product only forms the residual of its iterate (no new
-  // iterate, increment or remainder is written): the last product of a converging
-  // solve then costs little more than its matrix product.
-  vs->certify = (vs->certify_on && vs->k >= 3 && prev > 0.0 && rho < prev &&
-                 rho * (rho / prev) <= 0.5 * vs->tol) ? 1 : 0;
+  IterState ls;
+  state_load(st, ls);
+  ctrl_decide(ls, first, cert);
+  state_store(st, ls);
 }
+
 
 // ---------------------------------------------------------------------------
 // The tensor-core iteration: X = [D1 D2 D3](:, :S) * dt_{k-1} on tcgen05 with TMA
@@ -1499,7 +1510,7 @@ cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
                          const __half* Dcat, __half* dt0, float* L, double* d, float* part,
                          float* rowpart, IterState* st, cudaStream_t s) {
   if (nsl < 1 || nsl > NSLICE) return cudaErrorInvalidValue;
-  const int ntm = (n + IT0 - 1) / IT0, ntn = (n + IT0 - 1) / IT0;
+  const int ntm = (n + IT0 - 1) / IT0, ntn = (n + kIter0Cols - 1) / kIter0Cols;
   const float lh = (float)lam;
   const float ll = (float)(lam - (double)lh);
   const dim3 grid(ntn, ntm);
@@ -1517,7 +1528,8 @@ cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,
                         float* dprev_col, IterState* st, cudaStream_t s) {
-  const int ntm = (n + BM - 1) / BM, ntn = (n + IT0 - 1) / IT0;   // row partials: 128-wide blocks
+  // row partials: one per block of kIter0Cols columns of iteration 0
+  const int ntm = (n + BM - 1) / BM, ntn = (n + kIter0Cols - 1) / kIter0Cols;
   k_ctrl<<<(n + 31) / 32, 256, 0, s>>>(n, ld, ntm, ntn, part, rowpart, theta, d, E, e_col,
                                        dprev_col, st);
   return cudaGetLastError();

@@ -9,6 +9,10 @@
 
 namespace dpt {
 
+// Columns per block of the mixed solve's iteration 0 (k_iter0); its row sums of |Delta|
+// are left as one partial per such block of columns (rowpart: (n + 63) / 64 rows of ld).
+constexpr int kIter0Cols = 64;
+
 enum : int {
   ST_RUNNING = 0,
   ST_CONVERGED = 1,
@@ -245,16 +249,19 @@ cudaError_t launch_epi_f64(int n, int ld, int cplx, const double* theta, double 
 int dom_blocks(int n);
 cudaError_t launch_dom_check(int n, int64_t nnz, const int32_t* row_ptr, DomState* st,
                              cudaStream_t s);
-cudaError_t launch_dom_setup(int n, const double* theta, const int32_t* row_ptr,
-                             const int32_t* col_idx, const float* vals, float* th_hi,
-                             float* th_lo, DomState* st, cudaStream_t s);
+// theta split and maxima, n*, ties, and the gate (statuses of malformed / degenerate
+// input set on the device); the first pass validates col_idx / vals and forms s
+cudaError_t launch_dom_setup(int n, const double* theta, float* th_hi, float* th_lo, DomState* st,
+                             cudaStream_t s);
+cudaError_t launch_probe_gather(int n, int vlanes, const int32_t* row_ptr, const int32_t* col_idx,
+                                const float2* z, float* y, cudaStream_t s);
 cudaError_t launch_dom_init(int n, float2* z, double* z64, int ff, DomState* st,
                             cudaStream_t s);
 cudaError_t launch_dom_iter(int n, int vlanes, int ff, const int32_t* row_ptr,
                             const int32_t* col_idx, const float* vals, const float* th_hi,
                             const float* th_lo, const double* theta, float2* z0, float2* z1,
                             double* z64_0, double* z64_1, double* part, DomState* st,
-                            cudaStream_t s);
+                            cudaStream_t s, bool first = false);
 cudaError_t launch_dom_select(int n, const double* theta, DomState* st, cudaStream_t s);
 cudaError_t launch_dom_start(int n, const double* v, float2* z, double* z64, DomState* st,
                              cudaStream_t s);

@@ -154,7 +154,7 @@ extern "C" dpt_status dpt_solve_dominant_noalloc(int64_t n, const double* theta,
   NA_CK(cudaMemcpyAsync(&h, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
   NA_CK(cudaStreamSynchronize(s));
   if (h.bad_input) return done(DPT_ERR_ARG);
-  NA_CK(launch_dom_setup(ni, theta, row_ptr, col_idx, vals, thh, thl, st, s));
+  NA_CK(launch_dom_setup(ni, theta, thh, thl, st, s));
   NA_CK(cudaMemcpyAsync(&h, st, sizeof(DomState), cudaMemcpyDeviceToHost, s));
   NA_CK(cudaStreamSynchronize(s));
   if (h.bad_input) return done(DPT_ERR_ARG);
@@ -162,6 +162,9 @@ extern "C" dpt_status dpt_solve_dominant_noalloc(int64_t n, const double* theta,
   NA_CK(launch_dom_init(ni, z0, nullptr, 1, st, s));
   const double avg = (double)nnz32 / (double)n;
   const int V = avg < 24 ? 4 : (avg < 48 ? 8 : (avg < 96 ? 16 : 32));
+  // the first pass (k = 0) validates the CSR data and forms the residual scale
+  NA_CK(launch_dom_iter(ni, V, 1, row_ptr, col_idx, vals, thh, thl, theta, z0, z1, nullptr,
+                        nullptr, part, st, s, /*first=*/true));
   // plain launches (no graph: instantiating one may allocate), host check every 4
   const int per = 4;
   for (int c = 0; c <= max_iter / per + 1; ++c) {

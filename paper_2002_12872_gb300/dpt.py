@@ -121,6 +121,9 @@ def lib() -> ctypes.CDLL:
         L.dpt_solve_dominant_noalloc.argtypes = [i64, P, P, P, P, i64, dbl, dbl,
                                                  ctypes.c_int32, P, P, ctypes.POINTER(Info), P]
         L.dpt_solve_dominant_noalloc.restype = ctypes.c_int
+        L.dpt_probe_gather.argtypes = [i64, P, P, P, P, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_double), P]
+        L.dpt_probe_gather.restype = ctypes.c_int
         L.dpt_solve_batched.argtypes = [i64, ctypes.c_int, P, P, P, P, P,
                                         ctypes.POINTER(Options), P, P, P, P, P]
         L.dpt_solve_batched.restype = ctypes.c_int
@@ -541,6 +544,22 @@ def solve_dominant_noalloc(theta, row_ptr, col_idx, vals, lam, *, nstar=-1, tol=
         err.result = res
         raise err
     return res
+
+
+def probe_gather(row_ptr, col_idx, z, reps=20, stream=None):
+    """dpt_probe_gather: mean device time (ms) of one pass of the CSR form's access
+    pattern without its arithmetic (index stream and 8-byte gathers of z), the
+    ceiling of a pass on this GPU.  row_ptr / col_idx: int32 CUDA tensors; z: n
+    float pairs (an (n, 2) float32 CUDA tensor)."""
+    import torch
+    n = int(row_ptr.shape[0]) - 1
+    y = torch.empty(n, dtype=torch.float32, device=row_ptr.device)
+    ms = ctypes.c_double(0.0)
+    st = lib().dpt_probe_gather(n, _ptr(row_ptr), _ptr(col_idx), _ptr(z), _ptr(y), int(reps),
+                                ctypes.byref(ms), _stream_of(row_ptr, stream))
+    if st != OK:
+        raise RuntimeError(f"dpt_probe_gather: {status_string(st)}")
+    return float(ms.value)
 
 
 def selftest_bounded_wait(seconds=0.5, stream=None):

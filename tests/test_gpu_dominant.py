@@ -99,3 +99,27 @@ def test_dominant_full_size(ora, dpt):
     assert io["status"] == "OK"
     z, E, info = dpt.solve_dominant(*_dev(cfg), cfg["lam"], tol=1e-12)
     _check(z, E, zo, Eo)
+
+
+def test_gather_probe(dpt):
+    """dpt_probe_gather (a calibration of the CSR form's roofline): it gathers exactly
+    what a pass gathers, so its per-row sums of the gathered high parts equal a plain
+    reference, and it reports a positive time per pass."""
+    cfg = inputs.dominant_csr(n=50_000, nnz_per_row=16, rep=2)
+    _, rp, ci, _ = _dev(cfg)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    z = torch.rand((50_000, 2), generator=g, device="cuda", dtype=torch.float32)
+    from paper_2002_12872_gb300 import dpt as d
+    n = 50_000
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    import ctypes
+    ms = ctypes.c_double(0.0)
+    st = d.lib().dpt_probe_gather(n, rp.data_ptr(), ci.data_ptr(), z.data_ptr(), y.data_ptr(), 3,
+                                  ctypes.byref(ms), None)
+    assert st == 0 and ms.value > 0
+    rows = torch.repeat_interleave(torch.arange(n, device="cuda"), rp[1:] - rp[:-1])
+    ref = torch.zeros(n, dtype=torch.float64, device="cuda").index_add_(
+        0, rows, z[ci.long(), 0].double())
+    assert torch.allclose(y.double(), ref, rtol=1e-5, atol=1e-5)
+    assert dpt.probe_gather(rp, ci, z, reps=2) > 0
