@@ -53,7 +53,7 @@ def parse_args():
                     help="skip the dominant (CSR and dense), batched and served workloads")
     ap.add_argument("--only", default="all",
                     choices=["all", "dominant", "dominant_dense", "homotopy", "rs",
-                             "batched", "served", "served_pool"],
+                             "batched", "served", "served_pool", "full_variants"],
                     help="time one secondary workload alone and print its JSON object")
     ap.add_argument("--dense-n", type=int, default=32768,
                     help="dominant_dense: problem size")
@@ -446,6 +446,52 @@ def bench_dominant_dense(dpt, inputs, dev, pk, steps=10, warmup=3, n=32768):
                        "algorithmic_bytes_per_pass": bytes_pass}
     del D, cfg
     torch.cuda.empty_cache()
+    return out
+
+
+def bench_full_variants(dpt, inputs, dev, reps=5, check=True):
+    """The mixed full solve of the headline workload (n = 4096) with the generalised
+    start (the polisher of the closing remark of Sec. II.H: the first increment is the
+    start's offset from I) and with the non-autonomous iteration (ramp alpha = 0.5):
+    time per solve, map applications, FP64 steps, against the solve from I."""
+    import torch
+    cfg = inputs.full_unsymmetric(n=N)
+    th = torch.tensor(cfg["theta"], device=dev)
+    D = dpt.colmajor_tensor(cfg["delta"], dev)
+    Aref, _, _ = dpt.solve_full(th, D, cfg["lam"])
+    g = torch.Generator(device=dev)
+    g.manual_seed(2024)
+    pert = Aref * (1.0 + 1e-6 * torch.randn(Aref.shape, generator=g, device=dev,
+                                            dtype=torch.float64))
+    A = torch.empty((N, N), dtype=torch.float64, device=dev).t()
+    E = torch.empty(N, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": WORKLOAD}
+    rng_c = np.random.Generator(np.random.PCG64(11))
+    ccols = np.unique(np.concatenate([rng_c.choice(N, 16, replace=False),
+                                      tight_columns(cfg["theta"], 8)]))
+    cases = {"from_identity": {}, "start_solution_x_(1+1e-6_N(0,1))": {"start": pert},
+             "start_solution": {"start": Aref}, "ramp_alpha_0.5": {"ramp_alpha": 0.5}}
+    for name, kw in cases.items():
+        dpt.solve_full(th, D, cfg["lam"], A_out=A, E_out=E, **kw)      # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r = 1 if "ramp" in name else reps
+        e0.record(stream)
+        for _ in range(r):
+            _, _, info = dpt.solve_full(th, D, cfg["lam"], A_out=A, E_out=E, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"ms_per_solve": e0.elapsed_time(e1) / r, "iters": info["iters"],
+                     "fp64_iters": info["fp64_iters"], "refined_cols": info["refined_cols"],
+                     "status": info["status"],
+                     "max_abs_diff_to_solution": float((A - Aref).abs().max())}
+        if check:
+            ct = torch.tensor(ccols, device=dev)
+            out[name]["errors_vs_oracle"] = checker_full(
+                cfg["theta"], cfg["delta"], cfg["lam"], A[:, ct].cpu().numpy(),
+                E[ct].cpu().numpy(), ccols, "16 seeded columns and the 8 with the smallest "
+                "gaps; oracle (autonomous map) to tol 1e-13")
     return out
 
 
@@ -978,6 +1024,7 @@ def run_ours(args, world, rank, local):
         f64 = fp64["gemm_fp64_tflops"] if fp64 else None
         extra["dominant_csr"] = bench_dominant(dpt, inputs, dev, pk, check=chk)
         extra["dominant_dense"] = bench_dominant_dense(dpt, inputs, dev, pk)
+        extra["full_variants"] = bench_full_variants(dpt, inputs, dev, check=chk)
         extra["homotopy"] = bench_homotopy(dpt, dev)
         extra["rs_comparator"] = bench_rs_comparator(dpt, inputs, dev)
         extra["batched"] = bench_batched(dpt, inputs, dev, pk, check=chk, fp64_tflops=f64)
@@ -1043,6 +1090,8 @@ def main():
                                        warmup=max(1, min(args.warmup, 3)), n=args.dense_n)
         elif args.only == "homotopy":
             out = bench_homotopy(dpt, dev)
+        elif args.only == "full_variants":
+            out = bench_full_variants(dpt, inputs, dev, check=not args.no_check)
         elif args.only == "rs":
             out = bench_rs_comparator(dpt, inputs, dev)
         elif args.only == "batched":

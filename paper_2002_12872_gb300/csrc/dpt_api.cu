@@ -275,7 +275,8 @@ struct Timer {
 // th: theta checked on the host (host input or Epstein-Nesbet shift); or, when it is
 // empty, theta_dev: the caller's device theta, checked on the device.
 // Workspace of one mixed real full solve (the carve order of solve_full_mixed_real).
-void layout_full_mixed_real(Carve& c, int n, bool delta_dev, bool a_dev) {
+void layout_full_mixed_real(Carve& c, int n, bool delta_dev, bool a_dev, bool start = false,
+                            bool start_dev = true) {
   const int ld = (int)round_up(n, 128);
   const int ntm = (n + 127) / 128, ntn = (n + kIter0Cols - 1) / kIter0Cols;
   c.take<IterState>(1);
@@ -291,6 +292,10 @@ void layout_full_mixed_real(Carve& c, int n, bool delta_dev, bool a_dev) {
   c.take<float>((size_t)ld * n);             // L
   if (!delta_dev) c.take<double>((size_t)ld * n);
   if (!a_dev) c.take<double>((size_t)ld * n);
+  if (start) {
+    c.take<double>(ld);                      // 1 / start_ii
+    if (!start_dev) c.take<double>((size_t)ld * n);   // staged host start
+  }
 }
 
 // Result of the FP64 finish of at-risk columns (refine_columns).
@@ -421,7 +426,10 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
   // slices of the grouped path) unless a single slice is asked for
   const int S = o.max_slices <= 1 ? 1 : 2;
   const int ntm = (n + 127) / 128, ntn = (n + kIter0Cols - 1) / kIter0Cols;
-  auto layout = [&](Carve& c) { layout_full_mixed_real(c, n, delta_dev, a_dev); };
+  const bool start_dev = o.start ? is_device_ptr(o.start) : true;
+  auto layout = [&](Carve& c) {
+    layout_full_mixed_real(c, n, delta_dev, a_dev, o.start != nullptr, start_dev);
+  };
   Block* b = acquire(measure(layout));
   dpt_status ret = DPT_OK;
   try {
@@ -456,6 +464,24 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     }
     double* Astage = a_dev ? A_out : c.take<double>((size_t)ld * n);
     const int64_t lda_dev = a_dev ? ld_a : ld;
+    // the polisher's start (any nonzero multiple of each column will do: divided by its
+    // chart entry on the device)
+    const double* sdev = nullptr;
+    double* sinv = nullptr;
+    int64_t ld_s = 0;
+    if (o.start) {
+      sinv = c.take<double>(ld);
+      if (start_dev) {
+        sdev = o.start;
+        ld_s = o.ld_start;
+      } else {
+        double* t = c.take<double>((size_t)ld * n);
+        CK(cudaMemcpy2DAsync(t, sizeof(double) * ld, o.start, sizeof(double) * o.ld_start,
+                             sizeof(double) * n, n, cudaMemcpyHostToDevice, s));
+        sdev = t;
+        ld_s = ld;
+      }
+    }
 
     IterState h{};
     h.status = ST_RUNNING;
@@ -467,6 +493,13 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     h.slice_tol = o.slice_tol;
     h.best = INFINITY;
     h.certify_on = o.certify ? 1 : 0;
+    // The non-autonomous iteration: the product that forms A_{k+1} applies lambda
+    // (1 - ramp_pow) with ramp_pow advanced by alpha per decision.  Without a start
+    // the ramp's first step (strength 0, the identity) is not run: iteration 0 applies
+    // 1 - alpha; with a start, iteration 0 applies the start and the first product 1 -
+    // alpha.
+    h.ramp_alpha = o.ramp_alpha;
+    h.ramp_pow = o.ramp_alpha > 0.0 ? (o.start ? 1.0 : o.ramp_alpha) : 0.0;
     double tm = 0;
     for (double v : th) tm = std::max(tm, std::fabs(v));
     h.theta_max = tm;                  // 0 for a device theta: set by the check kernel
@@ -482,10 +515,11 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     // every product writes all ld rows of its dt_k before any read, and the operand
     // tensor maps stop at row n (rows beyond read as zero)
     CK(launch_theta_ff(n, thd, thh, thl, s));
-    CK(launch_delta_scales(delta, ldd, n, thh, thl, lambda, o.epstein_nesbet, st, s));
+    CK(launch_delta_scales(delta, ldd, n, thh, thl, lambda, o.epstein_nesbet, sdev, ld_s, sinv,
+                           st, s));
     CK(launch_prep_delta(delta, ldd, n, ld, o.epstein_nesbet, S, Dcat, st, s));
     CK(launch_iter0(delta, ldd, thh, thl, lambda, n, ld, o.epstein_nesbet, S, Dcat, dtb[0], L,
-                    d, part, rowpart, st, s));
+                    d, part, rowpart, sdev, ld_s, sinv, st, s));
     CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
 
     const CUtensorMap tA = make_tmap_bf16(Dcat, (uint64_t)3 * ld, n, (uint64_t)3 * ld, 128, true);
@@ -1661,6 +1695,7 @@ dpt_status mixed_real_finished(int64_t n, std::vector<double> th, const double* 
     po.prec = DPT_PREC_FP64;
     po.start = A_out;
     po.ld_start = ld_a;
+    po.ramp_alpha = 0.0;   // the finish applies the map at lambda itself
     dpt_info fi{};
     st = solve_full_fp64(n, false, th, delta, delta_dev, ld_delta, lambda, po, A_out, a_dev,
                          ld_a, E_out, e_dev, &fi, s);
@@ -1776,14 +1811,13 @@ dpt_status dpt_solve_full(int64_t n, dpt_dtype dtype, const double* theta, const
   if (o.prec == DPT_PREC_MIXED && dtype == DPT_C128 && o.epstein_nesbet)
     return done(DPT_ERR_UNSUPPORTED);
   if (!(o.ramp_alpha >= 0.0 && o.ramp_alpha < 1.0)) return done(DPT_ERR_ARG);
-  // the mixed path carries the residual across steps at one lambda
-  if (o.ramp_alpha > 0.0 && o.prec != DPT_PREC_FP64) return done(DPT_ERR_UNSUPPORTED);
+  // the grouped mixed path (complex solves) carries no ramp or start
+  if ((o.ramp_alpha > 0.0 || o.start) && o.prec == DPT_PREC_MIXED && dtype == DPT_C128)
+    return done(DPT_ERR_UNSUPPORTED);
   if (o.start && o.ld_start < n) return done(DPT_ERR_ARG);
   // the plain FP64 path launches one grid row per column (at most 65535); at that size
   // each of its products would take minutes anyway
   if (o.prec == DPT_PREC_FP64 && n > 65535) return done(DPT_ERR_TOO_LARGE);
-  // the mixed path's first step is exact only from A_0 = I
-  if (o.start && o.prec != DPT_PREC_FP64) return done(DPT_ERR_UNSUPPORTED);
   try {
     cudaStream_t s = (cudaStream_t)stream;
     const bool th_dev = is_device_ptr(theta), d_dev = is_device_ptr(delta),

@@ -69,6 +69,8 @@ struct __align__(16) GemmSmemMisc {
   int sig;            // the slices hold Delta 2^sig
   int scur;           // dt_{k-1} (the B operand) is stored as dt_{k-1} 2^scur
   int snew;           // dt_k is stored as dt_k 2^snew
+  float rpow;         // non-autonomous iteration: this step applies lambda (1 - rpow); 0 off
+  float rq, oq;       // the pair kernel's (1 - rpow) 2^snew and rpow 2^snew (see EpiConst)
   float e[BN];        // e_k 2^sig 2^scur for the tile's columns
   float dprev[BN];    // d_{k-1} 2^sig
   float thh[BN];      // theta_i as float-float
@@ -105,12 +107,34 @@ __global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__
                                                       int64_t ld_in, int n,
                                                       const float* __restrict__ th_hi,
                                                       const float* __restrict__ th_lo, int en,
+                                                      const double* __restrict__ start,
+                                                      int64_t ld_s, double* __restrict__ sinv,
                                                       IterState* st) {
   const int i = blockIdx.x;
   const float thh = th_hi[i], thl = th_lo[i];
   const double* col = delta + (int64_t)i * ld_in;
   unsigned hmax = 0u;
   float gmax = 0.f, rgmax = 0.f;   // rgmax: max 1 / |gap| (input of the error bound)
+  // With a start (the polisher), the first increment is the start's offset from I:
+  // X_0 = v / v_ii off the diagonal (the chart a_i = 1).  Its largest entry places the
+  // first increment's scale instead of the bound |lambda| max |Delta_ji / gap|; a zero
+  // or non-finite chart entry, or a non-finite entry, marks the input bad.
+  float smax = 0.f;
+  bool sbad = false;
+  double inv = 0.0;
+  const double* scol = start ? start + (int64_t)i * ld_s : nullptr;
+  if (start) {
+    const double piv = scol[i];
+    sbad = !(piv != 0.0 && finite_bits(piv));
+    inv = sbad ? 0.0 : 1.0 / piv;
+    if (threadIdx.x == 0) sinv[i] = inv;
+    for (int j = threadIdx.x; j < n; j += 256) {
+      const double x = scol[j];
+      if (!finite_bits(x)) sbad = true;
+      else if (j != i) smax = fmaxf(smax, fabsf((float)(x * inv)));
+    }
+    if (sbad) atomicExch(&st->bad_input, 1u);
+  }
   // four independent loads in flight per thread (the column streams from HBM)
   for (int jb = threadIdx.x; jb < n; jb += 1024) {
     double v[4];
@@ -147,6 +171,7 @@ __global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__
     }
   }
   hmax = __reduce_max_sync(0xffffffffu, hmax);
+  if (start) gmax = smax;   // with a start: the first increment's largest entry
   unsigned gb = __reduce_max_sync(0xffffffffu, __float_as_uint(gmax));   // gmax >= 0
   unsigned rb = __reduce_max_sync(0xffffffffu, __float_as_uint(rgmax));  // rgmax >= 0
   __shared__ unsigned wh[8], wg[8], wr[8];
@@ -172,7 +197,10 @@ __global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__
   if (hm != 0u) sig = 14 - ((int)((hm >> 20) & 0x7FFu) - 1023);   // max |Delta| < 2^(e+1)
   sig = max(-120, min(120, sig));
   const double lam = vs->lam;
-  const double ref = fabs(lam) * (double)__uint_as_float(vs->g0max_bits);
+  // the bound of the first increment: |lambda| max |Delta_ji / gap|, or with a start
+  // the largest entry of its offset from I
+  const double g0 = (double)__uint_as_float(vs->g0max_bits);
+  const double ref = start ? g0 : fabs(lam) * g0;
   const int s0 = dt_scale_exp(ref, 13, sig, lam);
   vs->sig = sig;
   vs->sexp[0] = s0;
@@ -262,7 +290,11 @@ __global__ void __launch_bounds__(256) k_prep_delta(const double* __restrict__ d
 // 16 columns with the next column's loads in flight, lane l owning rows 4l..4l+3
 // (vector loads along the contiguous row index).
 // ---------------------------------------------------------------------------
-template <int NSL>
+// START: the first increment is the start's offset X_0 = v / v_ii from I (the
+// polisher), read from the caller's start matrix with the per-column 1 / v_ii of the
+// scale pass; otherwise dt_0 = f16(r_0 G o R_0) with r_0 = 1 - alpha for the
+// non-autonomous iteration (its first step, the identity, is not run) and 1 without.
+template <int NSL, bool START>
 __global__ void __launch_bounds__(256) k_iter0(const double* __restrict__ delta, int64_t ld_in,
                                                const float* __restrict__ th_hi,
                                                const float* __restrict__ th_lo, float lam_hi,
@@ -271,7 +303,9 @@ __global__ void __launch_bounds__(256) k_iter0(const double* __restrict__ delta,
                                                __half* __restrict__ dt0,
                                                float* __restrict__ L, double* __restrict__ d,
                                                float* __restrict__ part,
-                                               float* __restrict__ rowpart, IterState* st) {
+                                               float* __restrict__ rowpart,
+                                               const double* __restrict__ start, int64_t ld_s,
+                                               const double* __restrict__ sinv, IterState* st) {
   // 128 x 64 tiles: 2048 blocks at n = 4096, 4.5 waves of three resident blocks per SM
   // (128 x 128 tiles left a last wave a quarter full)
   constexpr int W = 8, CPW = kIter0Cols / W;   // warps, columns per warp
@@ -281,6 +315,9 @@ __global__ void __launch_bounds__(256) k_iter0(const double* __restrict__ delta,
   const int r0 = 4 * lane, j0 = m0 + r0;
   const int64_t cat_ld = (int64_t)NSLICE * ld;
   const float qs = exp2i(st->sexp[0]), iqs = exp2i(-st->sexp[0]);
+  // strength factor of this first step (the ramp's 1 - alpha, else 1), folded into the
+  // quotient's scale
+  const float qr = START ? qs : qs * (float)(1.0 - st->ramp_pow);
   const float4 thj_h = *reinterpret_cast<const float4*>(th_hi + j0);
   const float4 thj_l = *reinterpret_cast<const float4*>(th_lo + j0);
   // 16-byte loads of the four rows where the column start allows them
@@ -289,8 +326,14 @@ __global__ void __launch_bounds__(256) k_iter0(const double* __restrict__ delta,
   float mx = 0.f;
   const int cb = n0 + CPW * w, ce = min(n, cb + CPW);
   double vn[4] = {0.0, 0.0, 0.0, 0.0};
+  double sn[4] = {0.0, 0.0, 0.0, 0.0};   // the start's column (START)
   uint2 Dn[3] = {make_uint2(0u, 0u), make_uint2(0u, 0u), make_uint2(0u, 0u)};
   auto fetch = [&](int i) {
+    if (START) {
+      const double* sc = start + (int64_t)i * ld_s + j0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) sn[e] = (j0 + e < n) ? sc[e] : 0.0;
+    }
     const double* col = delta + (int64_t)i * ld_in + j0;
     if (vec) {
       const double2 x = *reinterpret_cast<const double2*>(col);
@@ -307,14 +350,15 @@ __global__ void __launch_bounds__(256) k_iter0(const double* __restrict__ delta,
   };
   if (cb < ce) fetch(cb);
   for (int i = cb; i < ce; ++i) {   // uniform across the warp
-    double v[4];
+    double v[4], sv[4];
     uint2 D[3];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = vn[e];
+    for (int e = 0; e < 4; ++e) { v[e] = vn[e]; sv[e] = sn[e]; }
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) D[sl] = Dn[sl];
     if (i + 1 < ce) fetch(i + 1);
     const float thi_h = th_hi[i], thi_l = th_lo[i];
+    const double inv_i = START ? sinv[i] : 0.0;
     // first pass: R_0 and the scaled quotient of the four rows
     float R0h[4], R0l[4], gh[4], gl[4], q[4];
 #pragma unroll
@@ -335,8 +379,15 @@ __global__ void __launch_bounds__(256) k_iter0(const double* __restrict__ delta,
           fast_two_sum(pr, pe, R0h[e], R0l[e]);
           ff_sub(thi_h, thi_l, f4(thj_h, e), f4(thj_l, e), gh[e], gl[e]);
           // the remainder below keeps R_0 - Gap dt_0 exactly, so any reciprocal
-          // close to 1/gap serves
-          q[e] = R0h[e] * rcp_approx(gh[e]) * qs;
+          // close to 1/gap serves (and any increment at all: with a start it is the
+          // start's offset, rounded to FP16 like every increment)
+          if (START) {
+            float xh, xl;
+            split_double_fast(sv[e] * inv_i, xh, xl);
+            q[e] = xh * qs;
+          } else {
+            q[e] = R0h[e] * rcp_approx(gh[e]) * qr;
+          }
         }
       }
     }
@@ -582,6 +633,8 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
   // scale and the per-column parameters the matching ones (all exact)
   const float lam = (p.lam * exp2i(-ms->sig)) * exp2i(-ms->scur);
   const float qs = exp2i(ms->snew), iqs = exp2i(-ms->snew);
+  // non-autonomous step: dt = r G o R - (1 - r)(A - I), r = 1 - rpow (1 without)
+  const float rq = (1.f - ms->rpow) * qs, oq = ms->rpow * qs;
   const int r0 = 4 * lane;                // rows r0..r0+3 of the tile
   const int j0 = m0 + r0;
   // rows beyond n lie in the padded part of every work array (ld is a multiple of
@@ -645,7 +698,7 @@ __device__ __forceinline__ void epilogue_columns(const GemmEpiParams& p, GemmSme
             a2 = fmaf(ah, ah, a2);
             if (!cert) {
               ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh[t], gl[t]);
-              q[t] = R[t] * __frcp_rn(gh[t]) * qs;
+              q[t] = fmaf(R[t] * __frcp_rn(gh[t]), rq, -ah * oq);
             }
           }
         }
@@ -722,6 +775,7 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
     ms->sig = st->sig;
     ms->scur = st->sexp[st->cur ^ 1];
     ms->snew = st->sexp[st->cur];
+    ms->rpow = (float)st->ramp_pow;
     for (int s = 0; s < STAGES; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], 1); }
     for (int b = 0; b < NACC; ++b) { mbar_init(&ms->acc_full[b], 1); mbar_init(&ms->acc_empty[b], 1); }
     fence_mbar_init();
@@ -923,6 +977,10 @@ struct EpiConst {
   float qs, iqs;      // 2^snew, 2^-snew
   float isc;          // 2^-scur
 };
+// The step's increment is dt = r G o R - (1 - r)(A - I) with r = 1 - rpow: the
+// non-autonomous map at strength lambda r, from the residual at lambda and the identity
+// lambda (P - A diag P) = R + Gap o A; r = 1 without the ramp.  Its scaled factors
+// r 2^snew and (1 - r) 2^snew sit in shared memory (GemmSmemMisc::rq, oq).
 
 // One column of a sub-chunk: the update of Eq. (dyn) in increment form for this lane's
 // four rows, from the staged inputs in eb and the accumulator chunk in Xs (columns
@@ -986,7 +1044,8 @@ __device__ __forceinline__ void epi_lean(const GemmEpiParams& p, const GemmSmemM
   const float4 x4 = *reinterpret_cast<const float4*>(Xs + (cl - c0) * BM + r0);
   const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
   const float thh = ms->thh[cl], thl = ms->thl[cl];
-  const float lam = kc.lam, qs = kc.qs, iqs = kc.iqs;
+  const float lam = kc.lam, iqs = kc.iqs;
+  const float rq = ms->rq, oq = ms->oq;
   float r2 = 0.f, a2 = 0.f, es = 0.f;
   float4 oh, ol, oL;
   uint2 ob;
@@ -1008,8 +1067,9 @@ __device__ __forceinline__ void epi_lean(const GemmEpiParams& p, const GemmSmemM
           two_sum(thh, -bh, gs[t], err);
           gl[t] = err + (thl - f4(thj_l, e));
           // the increment is rounded to FP16 and the remainder keeps R - gap dt exactly,
-          // so any reciprocal close to 1/gap serves
-          q[t] = R[t] * rcp_approx(gs[t] + gl[t]) * qs;
+          // so any reciprocal close to 1/gap serves; with the ramp the increment takes
+          // the share r of the quotient and returns (1 - r) of A - I
+          q[t] = fmaf(R[t] * rcp_approx(gs[t] + gl[t]), rq, -ah * oq);
         }
       }
     }
@@ -1146,6 +1206,9 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     ms->sig = st->sig;
     ms->scur = st->sexp[st->cur ^ 1];
     ms->snew = st->sexp[st->cur];
+    ms->rpow = (float)st->ramp_pow;
+    ms->rq = (1.f - ms->rpow) * exp2i(ms->snew);
+    ms->oq = ms->rpow * exp2i(ms->snew);
     for (int s = 0; s < MAX_STAGES; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], 1); }
     for (int b = 0; b < NACC; ++b) { mbar_init(&ms->acc_full[b], 1); mbar_init(&ms->acc_empty[b], 2); }
     fence_mbar_init();
@@ -1474,12 +1537,12 @@ int mixed_tile_n(int n, int nsm) {
 }
 
 cudaError_t launch_delta_scales(const double* delta, int64_t ld_in, int n, const float* th_hi,
-                                const float* th_lo, double lam, int en, IterState* st,
-                                cudaStream_t s) {
+                                const float* th_lo, double lam, int en, const double* start,
+                                int64_t ld_s, double* sinv, IterState* st, cudaStream_t s) {
   (void)lam;   // read from the state
   // one block per column (a grid striding over fewer blocks measured slower: 38 us
   // against 34 us at n = 4096)
-  k_delta_scales<<<n, 256, 0, s>>>(delta, ld_in, n, th_hi, th_lo, en, st);
+  k_delta_scales<<<n, 256, 0, s>>>(delta, ld_in, n, th_hi, th_lo, en, start, ld_s, sinv, st);
   return cudaGetLastError();
 }
 
@@ -1508,20 +1571,30 @@ cudaError_t launch_theta_ff(int n, const double* th, float* hi, float* lo, cudaS
 cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
                          const float* th_lo, double lam, int n, int ld, int en, int nsl,
                          const __half* Dcat, __half* dt0, float* L, double* d, float* part,
-                         float* rowpart, IterState* st, cudaStream_t s) {
+                         float* rowpart, const double* start, int64_t ld_s, const double* sinv,
+                         IterState* st, cudaStream_t s) {
   if (nsl < 1 || nsl > NSLICE) return cudaErrorInvalidValue;
   const int ntm = (n + IT0 - 1) / IT0, ntn = (n + kIter0Cols - 1) / kIter0Cols;
   const float lh = (float)lam;
   const float ll = (float)(lam - (double)lh);
   const dim3 grid(ntn, ntm);
-  switch (nsl) {
-    case 1: k_iter0<1><<<grid, 256, 0, s>>>(delta, ld_in, th_hi, th_lo, lh, ll, n, ld, ntm, en,
-                                            Dcat, dt0, L, d, part, rowpart, st); break;
-    case 2: k_iter0<2><<<grid, 256, 0, s>>>(delta, ld_in, th_hi, th_lo, lh, ll, n, ld, ntm, en,
-                                            Dcat, dt0, L, d, part, rowpart, st); break;
-    default: k_iter0<3><<<grid, 256, 0, s>>>(delta, ld_in, th_hi, th_lo, lh, ll, n, ld, ntm, en,
-                                             Dcat, dt0, L, d, part, rowpart, st); break;
+#define DPT_IT0(NS, SS)                                                                     \
+  k_iter0<NS, SS><<<grid, 256, 0, s>>>(delta, ld_in, th_hi, th_lo, lh, ll, n, ld, ntm, en, \
+                                       Dcat, dt0, L, d, part, rowpart, start, ld_s, sinv, st)
+  if (start) {
+    switch (nsl) {
+      case 1: DPT_IT0(1, true); break;
+      case 2: DPT_IT0(2, true); break;
+      default: DPT_IT0(3, true); break;
+    }
+  } else {
+    switch (nsl) {
+      case 1: DPT_IT0(1, false); break;
+      case 2: DPT_IT0(2, false); break;
+      default: DPT_IT0(3, false); break;
+    }
   }
+#undef DPT_IT0
   return cudaGetLastError();
 }
 

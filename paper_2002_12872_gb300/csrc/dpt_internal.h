@@ -210,20 +210,25 @@ cudaError_t launch_gemm_epi_pair(const CUtensorMap& tmA, const CUtensorMap& tmB0
                                  cudaStream_t s);
 cudaError_t mixed_set_attributes();   // once per device, before any capture
 // max |Delta| and max |Delta_ji / (theta_i - theta_j)| (j != i); sets the scales of
-// the FP16 slices and of the first increment (IterState::sig, sexp[0])
+// the FP16 slices and of the first increment (IterState::sig, sexp[0]).  With a start
+// (device, leading dimension ld_s) the first increment is its offset from I: its
+// largest entry sets sexp[0], sinv[i] = 1 / start[i, i] (ld doubles) is written, and a
+// zero or non-finite chart entry or value marks the input bad.
 cudaError_t launch_delta_scales(const double* delta, int64_t ld_in, int n, const float* th_hi,
-                                const float* th_lo, double lam, int en, IterState* st,
-                                cudaStream_t s);
+                                const float* th_lo, double lam, int en, const double* start,
+                                int64_t ld_s, double* sinv, IterState* st, cudaStream_t s);
 // nsl FP16 slices of Delta * 2^sig (needs launch_delta_scales first)
 cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld, int en, int nsl,
                               __half* Dcat, IterState* st, cudaStream_t s);
 cudaError_t launch_theta_ff(int n, const double* th, float* hi, float* lo, cudaStream_t s);
 // finite and pairwise distinct theta (status ST_BADINPUT / ST_DEGENERATE), max |theta|
 cudaError_t launch_check_theta(int n, const double* th, IterState* st, cudaStream_t s);
+// iteration 0 from A_0 = I: dt_0 = f16(r_0 G o R_0), or with a start its offset from I
 cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
                          const float* th_lo, double lam, int n, int ld, int en, int nsl,
                          const __half* Dcat, __half* dt0, float* L, double* d, float* part,
-                         float* rowpart, IterState* st, cudaStream_t s);
+                         float* rowpart, const double* start, int64_t ld_s, const double* sinv,
+                         IterState* st, cudaStream_t s);
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,
                         float* dprev_col, IterState* st, cudaStream_t s);

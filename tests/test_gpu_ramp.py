@@ -115,12 +115,44 @@ def test_ramp_full_fp64(ora, dpt):
     assert np.array_equal(to_np(A1), np.eye(cfg["n"]))
 
 
+@pytest.mark.parametrize("which,alpha", [("sym", 0.6), ("unsym", 0.5)])
+def test_ramp_full_mixed(ora, dpt, which, alpha):
+    """The mixed full solve with the non-autonomous iteration: each step's increment
+    is r G o R - (1 - r)(A - I), r = 1 - alpha^(k+1) (the ramp's identity step 0 is not
+    run, so its iterate A_k is the ramped map's A_{k+1}); the carried residual stays
+    the one at lambda, so the limit is the autonomous fixed point, to the bar."""
+    cfg = (inputs.full_symmetric(n=200, lam=0.05) if which == "sym"
+           else inputs.full_unsymmetric(n=300))
+    Ao, Eo, io = ora.solve_full(cfg["theta"], cfg["delta"], cfg["lam"], tol=1e-14,
+                                ramp_alpha=alpha)
+    assert io["status"] == "OK"
+    th = _t(cfg["theta"])
+    from paper_2002_12872_gb300 import dpt as d
+    D = d.colmajor_tensor(cfg["delta"], "cuda")
+    A, E, info = dpt.solve_full(th, D, cfg["lam"], prec="mixed", tol=1e-13, ramp_alpha=alpha)
+    assert info["status"] == "OK", info
+    assert eig_err(to_np(E), Eo) <= EIG_RTOL and vec_err(to_np(A), Ao) <= VEC_TOL, info
+    # the schedule: the mixed A_3 follows the ramped map's A_4 (to the FP16 rounding of
+    # the increments, which the carried remainder corrects in later steps)
+    A3, _, i3 = dpt.solve_full(th, D, cfg["lam"], prec="mixed", max_iter=3, ramp_alpha=alpha,
+                               check=False)
+    assert i3["status"] == "ERR_MAXITER"
+    A4o, _, _ = ora.solve_full(cfg["theta"], cfg["delta"], cfg["lam"], tol=1e-300, max_iter=4,
+                               ramp_alpha=alpha)
+    X = A4o - np.eye(cfg["n"])
+    assert np.abs(to_np(A3) - A4o).max() <= 1e-3 * np.abs(X).max()
+
+
 def test_ramp_refused_where_unsupported(dpt):
+    """The grouped mixed path (complex mixed full solves, batches, the server) runs no
+    ramp; invalid ramp factors are refused everywhere."""
     cfg = inputs.full_symmetric(n=64)
     th = _t(cfg["theta"])
     from paper_2002_12872_gb300 import dpt as d
     D = d.colmajor_tensor(cfg["delta"], "cuda")
-    _, _, info = dpt.solve_full(th, D, cfg["lam"], ramp_alpha=0.5, check=False)
+    rng = np.random.Generator(np.random.PCG64(3))
+    Dc = d.colmajor_tensor(inputs.hermitian_gaussian(64, 1.0 / 64, rng), "cuda")
+    _, _, info = dpt.solve_full(th, Dc, cfg["lam"], ramp_alpha=0.5, check=False)
     assert info["status"] == "ERR_UNSUPPORTED"
     for bad in (-0.5, 1.0):
         _, _, info = dpt.solve_full(th, D, cfg["lam"], prec="fp64", ramp_alpha=bad, check=False)

@@ -9,7 +9,10 @@ against the oracle iterating from the same start, through the C ABI:
   than from e_{n*}, same eigenpair; a host-resident start;
 - the plain-FP64 full solve (real and complex Hermitian) from a perturbed solution,
   invariant under scaling of the start, and its argument errors;
-- the mixed full solve refuses the option."""
+- the mixed real full solve, whose first increment is the start's offset from I:
+  parity from a perturbed solution (device, host and scaled starts), fewer products
+  from the solution itself than from I, a zero chart entry refused; the complex mixed
+  solve refuses the option."""
 import numpy as np
 import pytest
 
@@ -121,7 +124,34 @@ def test_start_full_fp64(ora, dpt, cplx):
     _, _, info = dpt.solve_full(thd, D, lam, prec="fp64", start=np.asfortranarray(bad),
                                 check=False)
     assert info["status"] == "ERR_ARG"
-    if not cplx:
+    if cplx:
         _, _, info = dpt.solve_full(thd, D, lam, start=d.colmajor_tensor(S, "cuda"),
                                     check=False)
         assert info["status"] == "ERR_UNSUPPORTED"
+
+
+def test_start_full_mixed(ora, dpt):
+    from paper_2002_12872_gb300 import dpt as d
+    cfg = inputs.full_unsymmetric(n=300)
+    th, delta, lam = cfg["theta"], cfg["delta"], cfg["lam"]
+    Aref, _, _ = ora.solve_full(th, delta, lam, tol=1e-14)
+    rng = np.random.Generator(np.random.PCG64(14))
+    S = Aref * (1.0 + 1e-3 * rng.standard_normal(Aref.shape))
+    Ao, Eo, io = ora.solve_full(th, delta, lam, tol=1e-14, start=S)
+    assert io["status"] == "OK"
+    D = d.colmajor_tensor(delta, "cuda")
+    thd = _t(th)
+    for start in (d.colmajor_tensor(S, "cuda"), np.asfortranarray(S * 3.0)):
+        A, E, info = dpt.solve_full(thd, D, lam, prec="mixed", tol=1e-13, start=start)
+        assert info["status"] == "OK", info
+        assert eig_err(to_np(E), Eo) <= EIG_RTOL and vec_err(to_np(A), Ao) <= VEC_TOL, info
+    # from the solution itself (its FP16 rounding is all that is left to remove)
+    _, _, i0 = dpt.solve_full(thd, D, lam, prec="mixed", tol=1e-13)
+    _, _, i1 = dpt.solve_full(thd, D, lam, prec="mixed", tol=1e-13,
+                              start=d.colmajor_tensor(Aref, "cuda"))
+    assert i1["status"] == "OK" and i1["iters"] <= i0["iters"], (i0, i1)
+    bad = S.copy()
+    bad[7, 7] = 0.0
+    _, _, info = dpt.solve_full(thd, D, lam, prec="mixed", start=d.colmajor_tensor(bad, "cuda"),
+                                check=False)
+    assert info["status"] == "ERR_ARG"
