@@ -140,7 +140,12 @@ typedef struct {
                               the unperturbed vectors misses near the boundary of its
                               convergence domain; E, the residual and the stopping test
                               always refer to lambda.  Supported by both dominant
-                              forms and by the plain-FP64 full solve; mixed full,
+                              forms and by the real full solve in both precisions: the
+                              mixed one forms each step's increment as
+                              r G o R - (1 - r)(A - I), r = 1 - alpha^k, from the
+                              residual R at lambda it carries (lambda (P - A diag P) =
+                              R + Gap o A), and does not run the ramp's identity step
+                              0 (it reports one map application fewer).  Complex mixed,
                               batched and served solves return DPT_ERR_UNSUPPORTED. */
   const double* start;     /* NULL (default): iterate from the unperturbed vectors
                               (A_0 = I, z_0 = e_{n*}).  Otherwise the starting iterate,
@@ -154,10 +159,12 @@ typedef struct {
                               This is the polisher use of the closing remark of
                               Sec. II.H: approximate eigenvectors from another
                               method, refined by the map's final convergent steps.
-                              Supported by both dominant forms and the plain-FP64
-                              full solve; mixed full, batched and served solves
-                              return DPT_ERR_UNSUPPORTED (their first step is exact
-                              only from A_0 = I). */
+                              Supported by both dominant forms and by the real full
+                              solve in both precisions (the mixed one applies the
+                              start's offset from I as its first increment, rounded
+                              to FP16 like every increment, and counts that as a map
+                              application); complex mixed, batched and served solves
+                              return DPT_ERR_UNSUPPORTED. */
   int64_t ld_start;        /* leading dimension of a full-solve start (>= n) */
   int32_t certify;         /* mixed real full solve: nonzero (default) lets a product whose
                               iterate is predicted to pass the tolerance (the residual
