@@ -119,11 +119,15 @@ typedef struct {
                               2^-11 (FP16) by which its increment's largest entry
                               is below the first increment's, and uses one below
                               slice_tol (default 1e-8) */
-  int32_t cta_pair;        /* real mixed full solve: nonzero (default) runs the product
-                              as CTA pairs (tcgen05 cta_group::2, 256-row tiles split
+  int32_t cta_pair;        /* real mixed full solve: 1 (default) runs the product as
+                              CTA pairs (tcgen05 cta_group::2, 256-row tiles split
                               over two SMs, epilogue inputs staged in the shared memory
-                              this frees) where clusters of two can be resident; 0 one
-                              CTA per 128-row tile */
+                              this frees) where clusters of two can be resident; 2 as
+                              clusters of four (two pairs on 512-row tiles sharing each
+                              increment tile through TMA multicast; pairs where such
+                              clusters cannot be resident; at n = 4096 on GB300 slower
+                              than 1: 254 against 204 us per product); 0 one CTA per
+                              128-row tile */
   int32_t grouped_form;    /* grouped solves, complex single solves and the server:
                               1 (what 0, the default, selects) one CTA per 128-row tile
                               with the epilogue reading global memory; 2 one CTA per
@@ -202,8 +206,8 @@ typedef struct {
   int32_t product_launches;  /* product kernels that did work (one per iteration) */
   double product_ms;       /* with opt->profile: summed device time of those
                               product kernels, else 0 */
-  int32_t cta_pair;        /* mixed path: 1 when the products ran in the CTA-pair
-                              form, else 0 */
+  int32_t cta_pair;        /* mixed path: the product form that ran: 1 CTA pairs, 2
+                              clusters of four, 0 one CTA per tile */
   int32_t grouped_form;    /* grouped solves: the product form that ran (see
                               dpt_options.grouped_form), else 0 */
   int32_t fp64_iters;      /* mixed real full solve: plain FP64 map steps (included in

@@ -528,10 +528,19 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     CK(mixed_set_attributes());
     // CTA-pair form when asked for and clusters of two can be resident
-    int npairs = 0;
-    if (o.cta_pair) npairs = std::min(nsm / 2, mixed_pair_clusters());
+    // (cta_pair 2: clusters of four, two pairs sharing each increment tile, when
+    // such clusters can be resident; pairs otherwise)
+    int npairs = 0, ctas = 2;
+    if (o.cta_pair == 2) {
+      npairs = std::min(nsm / 4, mixed_pair_clusters(4));
+      ctas = 4;
+    }
+    if (o.cta_pair && npairs <= 0) {
+      npairs = std::min(nsm / 2, mixed_pair_clusters(2));
+      ctas = 2;
+    }
     const bool pair = npairs > 0;
-    const int bn = pair ? mixed_pair_tile_n((int)n, npairs) : mixed_tile_n((int)n, nsm);
+    const int bn = pair ? mixed_pair_tile_n((int)n, npairs, ctas) : mixed_tile_n((int)n, nsm);
     const CUtensorMap tB0 = make_tmap_bf16(dtb[0], n, n, ld, pair ? bn / 2 : bn, true);
     const CUtensorMap tB1 = make_tmap_bf16(dtb[1], n, n, ld, pair ? bn / 2 : bn, true);
     GemmEpiParams p{};
@@ -557,7 +566,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
       };
       run_loop(b, st, o.graph_iters, o.max_iter, 2, prof, [&](int q) {
         prof.before(q, s);
-        if (pair) CK(launch_gemm_epi_pair(tA, tB0, tB1, p, npairs, s));
+        if (pair) CK(launch_gemm_epi_pair(tA, tB0, tB1, p, npairs, ctas, s));
         else CK(launch_gemm_epi(tA, tB0, tB1, p, s));
         prof.after(q, s);
         CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
@@ -600,7 +609,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
       info->launches = prof.launches;
       info->product_launches = prof.live;
       info->product_ms = prof.ms;
-      info->cta_pair = pair ? 1 : 0;
+      info->cta_pair = pair ? (ctas == 4 ? 2 : 1) : 0;
       info->fp64_iters = rr.steps;
       info->refined_cols = rr.cols;
     }

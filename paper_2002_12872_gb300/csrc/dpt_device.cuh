@@ -408,6 +408,19 @@ __device__ __forceinline__ void tma_load_2d_pair(void* dst, const void* tmap, ui
       "l"(tmap), "r"(bar_cluster), "r"(x), "r"(y)
       : "memory");
 }
+// cta_group::2 form of the multicast load: `bar_cluster` is the leader's barrier of
+// the issuing CTA's pair; each destination's copy completes on the barrier at that
+// offset in the leader of the destination's own pair
+__device__ __forceinline__ void tma_load_2d_pair_multicast(void* dst, const void* tmap,
+                                                           uint32_t bar_cluster, int32_t x,
+                                                           int32_t y, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      ".multicast::cluster.cta_group::2 [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(bar_cluster), "r"(x), "r"(y), "h"(mask)
+      : "memory");
+}
+
 // D[tmem of both CTAs] (+)= A[smem of both CTAs, M halves] * B[smem of both CTAs, N halves]
 __device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
                                                uint32_t idesc, uint32_t accumulate) {

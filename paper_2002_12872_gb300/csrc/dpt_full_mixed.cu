@@ -1177,10 +1177,19 @@ __device__ __forceinline__ void warp_sum3x2(float (&a)[3], const float (&b)[3], 
 // empty[s] and acc_full[b] of both CTAs (multicast); both epilogues arrive on the
 // leader's acc_empty[b] (count 2).  Every thread of both CTAs reaches the final
 // cluster barrier, also when a bounded wait has given up.
+//
+// QUAD: clusters of four CTAs, two pairs stacked along M (a 512 x bn tile), which
+// share each B half through TMA multicast: cluster ranks 0 and 1 load B halves 0 and
+// 1 into themselves and into ranks 2 and 3, so a stage costs an SM its A tile plus a
+// quarter of B in L2 reads instead of a half.  Each destination's copy completes on
+// full[s] of its own pair's leader, which therefore expects the same bytes as in a
+// lone pair.  Each MMA commit releases the slot in all four CTAs (empty[s] count 2:
+// a slot holds data for both pairs' products).
 // ---------------------------------------------------------------------------
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
-k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
-                const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
+template <bool QUAD>
+__device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const CUtensorMap& tmB0,
+                                                   const CUtensorMap& tmB1,
+                                                   const GemmEpiParams& p) {
   extern __shared__ uint8_t smem_raw[];
   IterState* st = p.st;
   // read before any cluster barrier; nothing changes it during the launch, so both
@@ -1191,12 +1200,15 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   uint8_t* EB = smem + P_RING + SMEM_X;                       // two epilogue input buffers
   GemmSmemMisc* ms = (GemmSmemMisc*)(smem + P_RING + SMEM_X + 2 * EB_BYTES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = cluster_ctarank();
+  constexpr int CR = QUAD ? 4 : 2;       // CTAs per cluster, stacked along M
+  const uint32_t crank = cluster_ctarank();
+  const uint32_t rank = crank & 1u;      // rank within the pair
+  const uint32_t lead = crank & ~1u;     // cluster rank of the pair's leader
   const int bn = p.bn, bh = bn / 2;
   const int ntn = (p.n + bn - 1) / bn;
-  const int ntm2 = (p.n + 2 * BM - 1) / (2 * BM);
-  const int ntiles = ntn * ntm2;
-  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  const int ntmc = (p.n + CR * BM - 1) / (CR * BM);
+  const int ntiles = ntn * ntmc;
+  const int pair = blockIdx.x / CR, npairs = gridDim.x / CR;   // clusters
 
   if (threadIdx.x == 0) {
     ms->k = st->k;
@@ -1209,7 +1221,8 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     ms->rpow = (float)st->ramp_pow;
     ms->rq = (1.f - ms->rpow) * exp2i(ms->snew);
     ms->oq = ms->rpow * exp2i(ms->snew);
-    for (int s = 0; s < MAX_STAGES; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], 1); }
+    const uint32_t nempty = QUAD ? 2u : 1u;
+    for (int s = 0; s < MAX_STAGES; ++s) { mbar_init(&ms->full[s], 1); mbar_init(&ms->empty[s], nempty); }
     for (int b = 0; b < NACC; ++b) { mbar_init(&ms->acc_full[b], 1); mbar_init(&ms->acc_empty[b], 2); }
     fence_mbar_init();
   }
@@ -1218,27 +1231,28 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     tmem_relinquish_pair();
   }
   tc_fence_before();
-  cluster_sync();      // both CTAs' barriers initialised and their TMEM allocated
+  cluster_sync();      // every CTA's barriers initialised and each pair's TMEM allocated
   tc_fence_after();
   const uint32_t tmem = ms->tmem_base;
   const int S = ms->slices;
   const int kb_per_slice = p.ld / BK;
   const int nk = S * kb_per_slice;
-  const uint32_t stage_bytes = (uint32_t)A_TILE + (uint32_t)bh * BK * 2;   // multiple of 1024
+  const uint32_t b_bytes = (uint32_t)bh * BK * 2;
+  const uint32_t stage_bytes = (uint32_t)A_TILE + b_bytes;   // multiple of 1024
   const int nst = min(MAX_STAGES, (int)(P_RING / stage_bytes));
   const CUtensorMap* tmB = (ms->cur == 1) ? &tmB0 : &tmB1;
   unsigned* tflag = &st->timeout;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer (both CTAs): completions go to the leader's full[s] ----
+    // ---- TMA producer (every CTA): A completes on the leader's full[s] ----
     prefetch_tmap(&tmA);
     prefetch_tmap(tmB);
-    const uint32_t full_leader = mapa_shared(&ms->full[0], 0);
+    const uint32_t full_leader = mapa_shared(&ms->full[0], lead);
     uint32_t it = 0;
     bool alive = true;
     for (int t = pair; t < ntiles && alive; t += npairs) {
-      const int tm2 = t / ntn, tn = t % ntn;
-      const int m0 = tm2 * 2 * BM + (int)rank * BM, n0 = tn * bn;
+      const int tmc = t / ntn, tn = t % ntn;
+      const int m0 = tmc * CR * BM + (int)crank * BM, n0 = tn * bn;
       const int kb_last = min(kb_per_slice - 1, (n0 + bn - 1) / BK);
       for (int q = 0; q < nk; ++q, ++it) {
         const int s = it % nst;
@@ -1251,14 +1265,18 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         uint8_t* slot = smem + (size_t)s * stage_bytes;
         const uint32_t fb = full_leader + (uint32_t)s * 8u;
         tma_load_2d_pair(slot, &tmA, fb, sl * p.ld + kb * BK, m0);
-        tma_load_2d_pair(slot + A_TILE, tmB, fb, kb * BK, n0 + (int)rank * bh);
+        if (!QUAD)
+          tma_load_2d_pair(slot + A_TILE, tmB, fb, kb * BK, n0 + (int)rank * bh);
+        else if (crank < 2)
+          tma_load_2d_pair_multicast(slot + A_TILE, tmB, fb, kb * BK, n0 + (int)rank * bh,
+                                     (uint16_t)((1u << crank) | (4u << crank)));
       }
     }
     // the MMA's last commits have arrived on this CTA's empty barriers
     for (uint32_t u = (it > (uint32_t)nst ? it - nst : 0); u < it; ++u)
       mbar_wait_quiet(&ms->empty[u % nst], (u / nst) & 1, kTailWaitNs);
   } else if (warp == 1 && lane == 0 && rank == 0) {
-    // ---- MMA issuer (leader only) ----
+    // ---- MMA issuer (pair leaders only) ----
     const uint32_t idesc = idesc_f16_f32(2 * BM, bn);
     uint32_t it = 0;
     int lt = 0;
@@ -1281,9 +1299,9 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         for (int kk = 0; kk < BK / UK; ++kk)
           umma_bf16_pair(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
                          (q > 0 || kk > 0) ? 1u : 0u);
-        umma_commit_pair(&ms->empty[s], (uint16_t)3);
+        umma_commit_pair(&ms->empty[s], (uint16_t)(QUAD ? 0xF : 0x3));
       }
-      umma_commit_pair(&ms->acc_full[b], (uint16_t)3);
+      umma_commit_pair(&ms->acc_full[b], (uint16_t)(3u << lead));
     }
     // both epilogues have released the last accumulators: their arrivals on this
     // CTA's acc_empty have landed before it can exit
@@ -1295,7 +1313,7 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const int qd = warp & 3;
     const int q4 = ew >> 2;                // which 8 of a chunk's 32 columns this warp stages
     const int et = threadIdx.x - 64;
-    const uint32_t acc_empty_leader = mapa_shared(&ms->acc_empty[0], 0);
+    const uint32_t acc_empty_leader = mapa_shared(&ms->acc_empty[0], lead);
     const bool c1 = (ms->cur != 0);
     const bool cert = ms->certify != 0;
     const bool a1 = ms->k == 1;            // A_1 = I + dt_0 is formed from dt_0
@@ -1311,13 +1329,13 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     int lt = 0;
     // the first tile's first sub-chunk, while its products run
     if (pair < ntiles) {
-      const int tm = 2 * (pair / ntn) + (int)rank;
+      const int tm = CR * (pair / ntn) + (int)crank;
       if (tm < p.ntm) epi_prefetch(p, c1, cert, a1, S, EB, ew, lane, tm * BM, (pair % ntn) * bn, 0);
     }
     cp_async_commit();
     for (int t = pair; t < ntiles; t += npairs, ++lt) {
-      const int tm2 = t / ntn, tn = t % ntn;
-      const int tm = 2 * tm2 + (int)rank;
+      const int tmc = t / ntn, tn = t % ntn;
+      const int tm = CR * tmc + (int)crank;
       const int m0 = tm * BM, n0 = tn * bn;
       const int b = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
@@ -1366,7 +1384,7 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
           if (sc + 1 < nsub) {
             if (work) epi_prefetch(p, c1, cert, a1, S, nb, ew, lane, m0, n0, sc + 1);
           } else if (t + npairs < ntiles) {
-            const int tn2 = 2 * ((t + npairs) / ntn) + (int)rank;
+            const int tn2 = CR * ((t + npairs) / ntn) + (int)crank;
             if (tn2 < p.ntm)
               epi_prefetch(p, c1, cert, a1, S, nb, ew, lane, tn2 * BM, ((t + npairs) % ntn) * bn, 0);
           }
@@ -1408,11 +1426,23 @@ k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   }
   tc_fence_before();
   __syncthreads();
-  cluster_sync();      // no MMA, load or remote arrival of the pair is still in flight
+  cluster_sync();      // no MMA, load or remote arrival of the cluster is still in flight
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc_pair(tmem, NACC * BN);
   }
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
+k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
+                const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
+  gemm_epi_pair_body<false>(tmA, tmB0, tmB1, p);
+}
+
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(P_NTHREADS, 1)
+k_gemm_epi_quad(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
+                const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
+  gemm_epi_pair_body<true>(tmA, tmB0, tmB1, p);
 }
 
 // ---------------------------------------------------------------------------
@@ -1619,46 +1649,53 @@ cudaError_t mixed_set_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_gemm_epi_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            P_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_gemm_epi_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           P_SMEM_BYTES);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev].store(true);
   return e;
 }
 
-// Clusters of two that can be resident at once (0: the pair form cannot run).  The
-// kernel declares its cluster shape at compile time, so the query passes none.
-int mixed_pair_clusters() {
-  static int cached[64];
-  static bool known[64];
+// Clusters of `ctas` (2: one CTA pair; 4: two pairs sharing B) that can be resident
+// at once (0: that form cannot run; call mixed_set_attributes first).  The kernels
+// declare their cluster shape at compile time, so the query passes none.
+int mixed_pair_clusters(int ctas) {
+  static int cached[64][2];
+  static bool known[64][2];
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+  if ((ctas != 2 && ctas != 4) || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
     cudaGetLastError();
     return 0;
   }
-  if (known[dev]) return cached[dev];
+  const int q = ctas == 4;
+  if (known[dev][q]) return cached[dev][q];
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2, 1, 1);
+  cfg.gridDim = dim3(ctas, 1, 1);
   cfg.blockDim = dim3(P_NTHREADS, 1, 1);
   cfg.dynamicSmemBytes = P_SMEM_BYTES;
   cfg.attrs = nullptr;
   cfg.numAttrs = 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k_gemm_epi_pair, &cfg) != cudaSuccess) {
+  const cudaError_t e = q ? cudaOccupancyMaxActiveClusters(&n, k_gemm_epi_quad, &cfg)
+                          : cudaOccupancyMaxActiveClusters(&n, k_gemm_epi_pair, &cfg);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     n = 0;
   }
-  cached[dev] = n;
-  known[dev] = true;
+  cached[dev][q] = n;
+  known[dev][q] = true;
   return n;
 }
 
-// Tile width for the pair form: as mixed_tile_n with 256-row tiles over `npairs`
-// CTA pairs; half of the width (a multiple of 16) goes to each CTA.
-int mixed_pair_tile_n(int n, int npairs) {
-  const int ntm2 = (n + 2 * BM - 1) / (2 * BM);
+// Tile width for the pair forms: as mixed_tile_n with (ctas x 128)-row tiles over
+// `nclusters` clusters; half of the width (a multiple of 16) goes to each CTA of a pair.
+int mixed_pair_tile_n(int n, int nclusters, int ctas) {
+  const int ntmc = (n + ctas * BM - 1) / (ctas * BM);
   int best = BN;
   long long best_cost = -1;
   for (int w = BN; w >= 64; w -= 32) {
-    const long long tiles = (long long)ntm2 * ((n + w - 1) / w);
-    const long long waves = (tiles + npairs - 1) / npairs;
+    const long long tiles = (long long)ntmc * ((n + w - 1) / w);
+    const long long waves = (tiles + nclusters - 1) / nclusters;
     const long long cost = waves * (w + 64);
     if (best_cost < 0 || cost < best_cost) { best_cost = cost; best = w; }
   }
@@ -1666,12 +1703,14 @@ int mixed_pair_tile_n(int n, int npairs) {
 }
 
 cudaError_t launch_gemm_epi_pair(const CUtensorMap& tmA, const CUtensorMap& tmB0,
-                                 const CUtensorMap& tmB1, const GemmEpiParams& p, int npairs,
-                                 cudaStream_t s) {
-  if (p.bn < 64 || p.bn > BN || p.bn % 32 || npairs < 1) return cudaErrorInvalidValue;
-  const int ntiles = ((p.n + p.bn - 1) / p.bn) * ((p.n + 2 * BM - 1) / (2 * BM));
-  const int pairs = ntiles < npairs ? ntiles : npairs;
-  k_gemm_epi_pair<<<2 * pairs, P_NTHREADS, P_SMEM_BYTES, s>>>(tmA, tmB0, tmB1, p);
+                                 const CUtensorMap& tmB1, const GemmEpiParams& p, int nclusters,
+                                 int ctas, cudaStream_t s) {
+  if (p.bn < 64 || p.bn > BN || p.bn % 32 || nclusters < 1 || (ctas != 2 && ctas != 4))
+    return cudaErrorInvalidValue;
+  const int ntiles = ((p.n + p.bn - 1) / p.bn) * ((p.n + ctas * BM - 1) / (ctas * BM));
+  const int ncl = ntiles < nclusters ? ntiles : nclusters;
+  if (ctas == 4) k_gemm_epi_quad<<<4 * ncl, P_NTHREADS, P_SMEM_BYTES, s>>>(tmA, tmB0, tmB1, p);
+  else k_gemm_epi_pair<<<2 * ncl, P_NTHREADS, P_SMEM_BYTES, s>>>(tmA, tmB0, tmB1, p);
   return cudaGetLastError();
 }
 

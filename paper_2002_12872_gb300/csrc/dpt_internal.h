@@ -203,11 +203,12 @@ struct GemmEpiParams {
 
 int mixed_smem_bytes();
 int mixed_tile_n(int n, int nsm);   // columns per output tile of the product kernel
-int mixed_pair_clusters();          // resident clusters of two for the CTA-pair form
-int mixed_pair_tile_n(int n, int npairs);
+// CTA-pair forms: clusters of `ctas` = 2 (one pair) or 4 (two pairs sharing B)
+int mixed_pair_clusters(int ctas);  // resident clusters of that shape (after mixed_set_attributes)
+int mixed_pair_tile_n(int n, int nclusters, int ctas);
 cudaError_t launch_gemm_epi_pair(const CUtensorMap& tmA, const CUtensorMap& tmB0,
-                                 const CUtensorMap& tmB1, const GemmEpiParams& p, int npairs,
-                                 cudaStream_t s);
+                                 const CUtensorMap& tmB1, const GemmEpiParams& p, int nclusters,
+                                 int ctas, cudaStream_t s);
 cudaError_t mixed_set_attributes();   // once per device, before any capture
 // max |Delta| and max |Delta_ji / (theta_i - theta_j)| (j != i); sets the scales of
 // the FP16 slices and of the first increment (IterState::sig, sexp[0]).  With a start

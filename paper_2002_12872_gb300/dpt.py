@@ -306,9 +306,11 @@ class FullSolve:
         self.A = _empty_colmajor(n, delta, cplx) if A_out is None else A_out
         self.E = _empty_vec(n, delta, cplx) if E_out is None else E_out
         lda = self.A.stride(1) if _is_torch(self.A) else self.A.strides[1] // self.A.itemsize
-        for k in ("epstein_nesbet", "profile", "certify", "cta_pair"):
+        for k in ("epstein_nesbet", "profile", "certify"):
             if opts.get(k) is not None:
                 opts[k] = int(bool(opts[k]))
+        if opts.get("cta_pair") is not None:
+            opts["cta_pair"] = int(opts["cta_pair"])
         self.opts = options(**opts)
         self._info = Info()
         self._fn = lib().dpt_solve_full

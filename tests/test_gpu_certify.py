@@ -31,7 +31,7 @@ def _pair(dpt, cfg, **kw):
     return out
 
 
-@pytest.mark.parametrize("cta_pair", [1, 0])
+@pytest.mark.parametrize("cta_pair", [2, 1, 0])
 @pytest.mark.parametrize("case", [("unsym", 4096, 1e-12), ("sym", 256, 1e-12), ("unsym", 513, 1e-13),
                                   ("unsym", 1000, 1e-14), ("sym", 300, 3e-15)])
 def test_certify_matches_plain_iteration(dpt, cta_pair, case):

@@ -1,6 +1,8 @@
-"""The CTA-pair form of the product kernel (tcgen05 cta_group::2: 256-row tiles whose
-operands are split over the two SMs of a cluster) against the oracle and against
-the one-CTA form, through dpt_solve_full with the cta_pair option."""
+"""The CTA-pair forms of the product kernel (tcgen05 cta_group::2: 256-row tiles whose
+operands are split over the two SMs of a pair; cta_pair = 2 stacks two pairs in a
+cluster of four that share each increment tile through TMA multicast) against the
+oracle and against the one-CTA form, through dpt_solve_full with the cta_pair
+option."""
 import numpy as np
 import pytest
 
@@ -22,34 +24,40 @@ def _dev(cfg, dpt):
     return torch.tensor(cfg["theta"], device="cuda"), dpt.colmajor_tensor(cfg["delta"], "cuda")
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("n", [1, 3, 64, 65, 200, 255, 256, 257, 300, 513, 1000])
-def test_pair_parity(ora, dpt, n):
+def test_pair_parity(ora, dpt, n, form):
+    """Ragged sizes: with form 2, n = 300 leaves the fourth CTA of the only row tile
+    beyond the matrix, n = 513 a second row tile with one row, n = 1000 every
+    cluster row tile partly filled."""
     cfg = inputs.full_unsymmetric(n=n, rep=11)
     th, D = _dev(cfg, dpt)
-    A, E, info = dpt.solve_full(th, D, cfg["lam"], cta_pair=1)
+    A, E, info = dpt.solve_full(th, D, cfg["lam"], cta_pair=form)
     Ao, Eo, io = ora.solve_full(cfg["theta"], cfg["delta"], cfg["lam"], tol=1e-13)
     assert info["status"] == "OK" and io["status"] == "OK"
-    assert info["cta_pair"] == 1 or info["iters"] == 0
+    assert info["cta_pair"] == form or info["iters"] == 0
     assert eig_err(to_np(E), Eo) <= EIG_RTOL, (n, info)
     assert vec_err(to_np(A), Ao) <= VEC_TOL, (n, info)
 
 
-def test_pair_matches_single_cta_form(dpt):
+@pytest.mark.parametrize("form", [1, 2])
+def test_pair_matches_single_cta_form(dpt, form):
     cfg = inputs.full_unsymmetric(n=777, rep=12)
     th, D = _dev(cfg, dpt)
     A1, E1, i1 = dpt.solve_full(th, D, cfg["lam"], cta_pair=0)
-    A2, E2, i2 = dpt.solve_full(th, D, cfg["lam"], cta_pair=1)
-    assert i1["cta_pair"] == 0 and i2["cta_pair"] == 1
+    A2, E2, i2 = dpt.solve_full(th, D, cfg["lam"], cta_pair=form)
+    assert i1["cta_pair"] == 0 and i2["cta_pair"] == form
     assert i1["iters"] == i2["iters"]
     assert eig_err(to_np(E2), to_np(E1)) <= EIG_RTOL and vec_err(to_np(A2), to_np(A1)) <= VEC_TOL
 
 
-def test_pair_bench_size_sampled(ora, dpt):
-    """n = 4096 (the bench workload) with the pair form; sampled columns vs the oracle."""
+@pytest.mark.parametrize("form", [1, 2])
+def test_pair_bench_size_sampled(ora, dpt, form):
+    """n = 4096 (the bench workload) with each pair form; sampled columns vs the oracle."""
     cfg = inputs.full_unsymmetric(n=4096)
     th, D = _dev(cfg, dpt)
-    A, E, info = dpt.solve_full(th, D, cfg["lam"], cta_pair=1)
-    assert info["status"] == "OK" and info["cta_pair"] == 1
+    A, E, info = dpt.solve_full(th, D, cfg["lam"], cta_pair=form)
+    assert info["status"] == "OK" and info["cta_pair"] == form
     cols = np.array([0, 1, 1000, 2047, 2048, 4094, 4095])
     Ao, Eo, io = ora.solve_full(cfg["theta"], cfg["delta"], cfg["lam"], tol=1e-13, cols=cols)
     A, E = to_np(A), to_np(E)
