@@ -78,18 +78,24 @@ struct __align__(16) GemmSmemMisc {
 };
 constexpr int SMEM_BYTES = SMEM_TILES + SMEM_X + 1024 + (int)sizeof(GemmSmemMisc);
 
-// CTA-pair layout: a smaller operand ring (a stage holds A and half of B: 30 KB at
-// bn = 224, four stages), the accumulator staging, and two buffers of epilogue
-// inputs filled by per-thread asynchronous copies one sub-chunk (16 columns) ahead.
-// The pair kernel's epilogue has 16 warps (its inputs sit in shared memory, not in
-// registers, so 576 threads fit the register file); each warp updates one column
-// of every 16-column sub-chunk.
-constexpr int P_RING = 4 * (A_TILE + 112 * BK * 2);     // 122880 B
+// CTA-pair layout: an operand ring, the accumulator staging, and buffers of epilogue
+// inputs filled by per-thread asynchronous copies.  The pair kernel's epilogue has 16
+// warps (its inputs sit in shared memory, not in registers, so 576 threads fit the
+// register file); each warp updates one column of every 16-column sub-chunk.
+// With one slice a stage holds A and half of B (30 KB at bn = 224, four stages) and
+// the epilogue double-buffers its inputs, copying one sub-chunk ahead: the second
+// buffer occupies the end of the ring region.  With two slices a stage holds both
+// slices' A tiles and one B half (46 KB at bn = 224, three stages): the increment
+// tile is fetched once for both slices, which cuts the operand bytes an SM receives
+// per flop by a quarter (the products are bound by that inflow, about 42 B per cycle
+// and SM on GB300), and the epilogue, which has time to spare in these launches,
+// works from one buffer.
 constexpr int P_EPI_WARPS = 16;
 constexpr int P_NTHREADS = 64 + 32 * P_EPI_WARPS;       // 576
-constexpr int EB_COL = 80;                              // bytes per lane and column
-constexpr int EB_BYTES = P_EPI_WARPS * 32 * EB_COL;     // one column per warp: 40960 B
-constexpr int P_SMEM_BYTES = P_RING + SMEM_X + 2 * EB_BYTES + 1024 + (int)sizeof(GemmSmemMisc);
+constexpr int EB_COL = 72;                              // bytes per lane and column
+constexpr int EB_BYTES = P_EPI_WARPS * 32 * EB_COL;     // one column per warp: 36864 B
+constexpr int P_RREG = 4 * (A_TILE + 112 * BK * 2) + EB_BYTES;   // 159744 B
+constexpr int P_SMEM_BYTES = P_RREG + EB_BYTES + SMEM_X + 1024 + (int)sizeof(GemmSmemMisc);
 static_assert(P_SMEM_BYTES <= 232448, "CTA-pair shared memory over the per-block limit");
 
 // ---------------------------------------------------------------------------
@@ -920,11 +926,13 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 // slots (80 B per column: A_hi, A_lo, L as float4, then dt_{k-1} and the Delta
 // slices as FP16 quadruples), so no barrier guards them.
 // ---------------------------------------------------------------------------
+// (the pair kernel's products use at most two slices: the increment and two slices
+// fill the three 8-byte slots)
 __device__ __forceinline__ uint8_t* eb_f4(uint8_t* eb, int ew, int u, int f, int lane) {
   return eb + ((ew + u) * 3 + f) * 512 + lane * 16;
 }
 __device__ __forceinline__ uint8_t* eb_u2(uint8_t* eb, int ew, int u, int g, int lane) {
-  return eb + P_EPI_WARPS * 3 * 512 + ((ew + u) * 4 + g) * 256 + lane * 8;
+  return eb + P_EPI_WARPS * 3 * 512 + ((ew + u) * 3 + g) * 256 + lane * 8;
 }
 __device__ __forceinline__ void p_epi_bar() {
   asm volatile("bar.sync 1, %0;" ::"n"(32 * P_EPI_WARPS) : "memory");
@@ -966,6 +974,23 @@ __device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, bo
     for (int sl = 0; sl < S; ++sl)
       cp_async8(eb_u2(eb, ew, u, 1 + sl, lane), Drow + (int64_t)sl * p.ld);
   }
+}
+
+// Copies of sub-chunk u of this tile, or, for u >= nsub, of sub-chunk u - nsub of the
+// CTA's next tile t_next; then one commit group (empty when there is nothing to copy).
+__device__ __forceinline__ void epi_prefetch_at(const GemmEpiParams& p, bool c1, bool cert,
+                                                bool a1, int S, uint8_t* eb, int ew, int lane,
+                                                bool work, int m0, int n0, int u, int nsub,
+                                                int t_next, int ntiles, int ntn, int bn,
+                                                int crank, int cr) {
+  if (u < nsub) {
+    if (work) epi_prefetch(p, c1, cert, a1, S, eb, ew, lane, m0, n0, u);
+  } else if (t_next < ntiles) {
+    const int tm = cr * (t_next / ntn) + crank;
+    if (tm < p.ntm)
+      epi_prefetch(p, c1, cert, a1, S, eb, ew, lane, tm * BM, (t_next % ntn) * bn, u - nsub);
+  }
+  cp_async_commit();
 }
 
 // Update this warp's column of sub-chunk sc from the staged inputs in eb and
@@ -1186,19 +1211,20 @@ __device__ __forceinline__ void warp_sum3x2(float (&a)[3], const float (&b)[3], 
 // lone pair.  Each MMA commit releases the slot in all four CTAs (empty[s] count 2:
 // a slot holds data for both pairs' products).
 // ---------------------------------------------------------------------------
-template <bool QUAD>
+template <bool QUAD, bool MERGED>
 __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const CUtensorMap& tmB0,
                                                    const CUtensorMap& tmB1,
                                                    const GemmEpiParams& p) {
   extern __shared__ uint8_t smem_raw[];
   IterState* st = p.st;
-  // read before any cluster barrier; nothing changes it during the launch, so both
-  // CTAs of a pair take the same branch
+  // read before any cluster barrier; nothing changes it during the launch, so every
+  // CTA of a cluster takes the same branch
   if (*((volatile int*)&st->status) != ST_RUNNING) return;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* Xs = reinterpret_cast<float*>(smem + P_RING);
-  uint8_t* EB = smem + P_RING + SMEM_X;                       // two epilogue input buffers
-  GemmSmemMisc* ms = (GemmSmemMisc*)(smem + P_RING + SMEM_X + 2 * EB_BYTES);
+  // [operand ring | (second epilogue input buffer) | epilogue input buffer at P_RREG |
+  //  accumulator staging | barriers and per-launch constants]
+  float* Xs = reinterpret_cast<float*>(smem + P_RREG + EB_BYTES);
+  GemmSmemMisc* ms = (GemmSmemMisc*)(smem + P_RREG + EB_BYTES + SMEM_X);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   constexpr int CR = QUAD ? 4 : 2;       // CTAs per cluster, stacked along M
   const uint32_t crank = cluster_ctarank();
@@ -1235,11 +1261,20 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
   tc_fence_after();
   const uint32_t tmem = ms->tmem_base;
   const int S = ms->slices;
+  // two slices: a stage holds both slices' A tiles of one K-block and its B half
+  constexpr bool merged = MERGED;
+  const int na = merged ? 2 : 1;
   const int kb_per_slice = p.ld / BK;
-  const int nk = S * kb_per_slice;
+  const int nk = merged ? kb_per_slice : S * kb_per_slice;
   const uint32_t b_bytes = (uint32_t)bh * BK * 2;
-  const uint32_t stage_bytes = (uint32_t)A_TILE + b_bytes;   // multiple of 1024
-  const int nst = min(MAX_STAGES, (int)(P_RING / stage_bytes));
+  const uint32_t stage_bytes = (uint32_t)(na * A_TILE) + b_bytes;   // multiple of 1024
+  // with one buffer of epilogue inputs the ring takes the whole region
+  const uint32_t ring_bytes = (uint32_t)P_RREG - (merged ? 0u : (uint32_t)EB_BYTES);
+  const int nst = min(MAX_STAGES, (int)(ring_bytes / stage_bytes));
+  // the epilogue input buffers: the second for one slice only; with two slices both
+  // names are the one buffer
+  uint8_t* EB = smem + P_RREG;
+  uint8_t* EB2 = merged ? EB : smem + ring_bytes;
   const CUtensorMap* tmB = (ms->cur == 1) ? &tmB0 : &tmB1;
   unsigned* tflag = &st->timeout;
 
@@ -1259,16 +1294,23 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
         const uint32_t ph = (it / nst) & 1;
         if (!mbar_wait(&ms->empty[s], ph ^ 1, tflag)) { alive = false; break; }
         if (rank == 0) mbar_arrive_expect_tx(&ms->full[s], 2 * stage_bytes);
-        // small slices first, the tile's diagonal K-blocks last (see k_gemm_epi)
-        const int sl = S - 1 - q / kb_per_slice;
+        // small slices first, the tile's diagonal K-blocks last (see k_gemm_epi); with
+        // both slices in a stage, slice 1 before slice 0 within each K-block
         const int kb = (kb_last + 1 + q % kb_per_slice) % kb_per_slice;
         uint8_t* slot = smem + (size_t)s * stage_bytes;
         const uint32_t fb = full_leader + (uint32_t)s * 8u;
-        tma_load_2d_pair(slot, &tmA, fb, sl * p.ld + kb * BK, m0);
+        if (merged) {
+          tma_load_2d_pair(slot, &tmA, fb, p.ld + kb * BK, m0);
+          tma_load_2d_pair(slot + A_TILE, &tmA, fb, kb * BK, m0);
+        } else {
+          const int sl = S - 1 - q / kb_per_slice;
+          tma_load_2d_pair(slot, &tmA, fb, sl * p.ld + kb * BK, m0);
+        }
+        uint8_t* bslot = slot + na * A_TILE;
         if (!QUAD)
-          tma_load_2d_pair(slot + A_TILE, tmB, fb, kb * BK, n0 + (int)rank * bh);
+          tma_load_2d_pair(bslot, tmB, fb, kb * BK, n0 + (int)rank * bh);
         else if (crank < 2)
-          tma_load_2d_pair_multicast(slot + A_TILE, tmB, fb, kb * BK, n0 + (int)rank * bh,
+          tma_load_2d_pair_multicast(bslot, tmB, fb, kb * BK, n0 + (int)rank * bh,
                                      (uint16_t)((1u << crank) | (4u << crank)));
       }
     }
@@ -1294,11 +1336,17 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
         tc_fence_after();
         uint8_t* slot = smem + (size_t)s * stage_bytes;
         const uint64_t da = smem_desc_sw128(slot);
-        const uint64_t db = smem_desc_sw128(slot + A_TILE);
+        const uint64_t db = smem_desc_sw128(slot + na * A_TILE);
 #pragma unroll
         for (int kk = 0; kk < BK / UK; ++kk)
           umma_bf16_pair(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
                          (q > 0 || kk > 0) ? 1u : 0u);
+        if (merged) {
+          const uint64_t da0 = smem_desc_sw128(slot + A_TILE);
+#pragma unroll
+          for (int kk = 0; kk < BK / UK; ++kk)
+            umma_bf16_pair(dacc, da0 + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, 1u);
+        }
         umma_commit_pair(&ms->empty[s], (uint16_t)(QUAD ? 0xF : 0x3));
       }
       umma_commit_pair(&ms->acc_full[b], (uint16_t)(3u << lead));
@@ -1327,12 +1375,17 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
     kc.isc = exp2i(-ms->scur);
     float mx = 0.f;
     int lt = 0;
-    // the first tile's first sub-chunk, while its products run
-    if (pair < ntiles) {
-      const int tm = CR * (pair / ntn) + (int)crank;
-      if (tm < p.ntm) epi_prefetch(p, c1, cert, a1, S, EB, ew, lane, tm * BM, (pair % ntn) * bn, 0);
-    }
-    cp_async_commit();
+    // The inputs of sub-chunk sc sit in buffer sc & 1 (one slice) or in the only
+    // buffer (two slices), copied two sub-chunks ahead (one slice: into the buffer just
+    // updated) or one ahead (two slices: after the update, into the same buffer; each
+    // lane copies and reads only its own slots).  The first tile's first sub-chunks,
+    // while its products run:
+    const int ahead = merged ? 1 : 2;
+    for (int u = 0; u < ahead; ++u)
+      epi_prefetch_at(p, c1, cert, a1, S, (u & 1) ? EB2 : EB, ew, lane,
+                      pair < ntiles && CR * (pair / ntn) + (int)crank < p.ntm,
+                      (CR * (pair / ntn) + (int)crank) * BM, (pair % ntn) * bn, u, nsub, pair,
+                      ntiles, ntn, bn, (int)crank, CR);
     for (int t = pair; t < ntiles; t += npairs, ++lt) {
       const int tmc = t / ntn, tn = t % ntn;
       const int tm = CR * tmc + (int)crank;
@@ -1379,19 +1432,14 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
           const int sc = c0 / 16 + h;
-          // copies of the next sub-chunk: this tile's, or the next tile's first
-          uint8_t* nb = EB + ((sc + 1) & 1) * EB_BYTES;
-          if (sc + 1 < nsub) {
-            if (work) epi_prefetch(p, c1, cert, a1, S, nb, ew, lane, m0, n0, sc + 1);
-          } else if (t + npairs < ntiles) {
-            const int tn2 = CR * ((t + npairs) / ntn) + (int)crank;
-            if (tn2 < p.ntm)
-              epi_prefetch(p, c1, cert, a1, S, nb, ew, lane, tn2 * BM, ((t + npairs) % ntn) * bn, 0);
-          }
-          cp_async_commit();
-          cp_async_wait<1>();              // this lane's copies of sub-chunk sc have landed
+          // copies of the next sub-chunk (this tile's, or the next tile's first) into
+          // the other buffer before this one is updated, or, with one buffer, into the
+          // same buffer after it (each lane copies and reads only its own slots)
+          // this lane's copies of sub-chunk sc have landed
+          if (merged) cp_async_wait<0>();
+          else cp_async_wait<1>();
+          uint8_t* eb = (sc & 1) ? EB2 : EB;
           if (work) {
-            const uint8_t* eb = EB + (sc & 1) * EB_BYTES;
             float cur[3];
             epi_lean_any(S, mode, check, p, ms, Xs, eb, ew, lane, m0, n0, sc, mx, kc, thj_h,
                          thj_l, cur);
@@ -1401,6 +1449,8 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
               else pb[q] = cur[q];
             }
           }
+          epi_prefetch_at(p, c1, cert, a1, S, eb, ew, lane, work, m0, n0, sc + ahead, nsub,
+                          t + npairs, ntiles, ntn, bn, (int)crank, CR);
         }
         if (work) {
           // this warp's two columns of the chunk, reduced together
@@ -1433,16 +1483,21 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
   }
 }
 
+// Each slice count runs a body specialised for it (the count is decided on the device
+// by the preceding control kernel and is uniform over the launch): one body with a
+// runtime flag ran the one-slice products 8 % slower.
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
 k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
                 const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
-  gemm_epi_pair_body<false>(tmA, tmB0, tmB1, p);
+  if (*((volatile int*)&p.st->slices) == 2) gemm_epi_pair_body<false, true>(tmA, tmB0, tmB1, p);
+  else gemm_epi_pair_body<false, false>(tmA, tmB0, tmB1, p);
 }
 
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(P_NTHREADS, 1)
 k_gemm_epi_quad(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
                 const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
-  gemm_epi_pair_body<true>(tmA, tmB0, tmB1, p);
+  if (*((volatile int*)&p.st->slices) == 2) gemm_epi_pair_body<true, true>(tmA, tmB0, tmB1, p);
+  else gemm_epi_pair_body<true, false>(tmA, tmB0, tmB1, p);
 }
 
 // ---------------------------------------------------------------------------
