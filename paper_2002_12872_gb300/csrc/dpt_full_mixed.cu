@@ -84,8 +84,9 @@ constexpr int SMEM_BYTES = SMEM_TILES + SMEM_X + 1024 + (int)sizeof(GemmSmemMisc
 // register file); each warp updates one column of every 16-column sub-chunk.
 // With one slice a stage holds A and half of B (30 KB at bn = 224, four stages) and
 // the epilogue double-buffers its inputs, copying one sub-chunk ahead: the second
-// buffer occupies the end of the ring region.  With two slices a stage holds both
-// slices' A tiles and one B half (46 KB at bn = 224, three stages): the increment
+// buffer occupies the end of the ring region.  With two slices (after the first
+// product: see k_gemm_epi_pair) a stage holds both slices' A tiles and one B half
+// (46 KB at bn = 224, three stages): the increment
 // tile is fetched once for both slices, which cuts the operand bytes an SM receives
 // per flop by a quarter (the products are bound by that inflow, about 42 B per cycle
 // and SM on GB300), and the epilogue, which has time to spare in these launches,
@@ -1261,7 +1262,8 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
   tc_fence_after();
   const uint32_t tmem = ms->tmem_base;
   const int S = ms->slices;
-  // two slices: a stage holds both slices' A tiles of one K-block and its B half
+  // two-slice stages (MERGED: two slices, not the first product): a stage holds both
+  // slices' A tiles of one K-block and its B half
   constexpr bool merged = MERGED;
   const int na = merged ? 2 : 1;
   const int kb_per_slice = p.ld / BK;
@@ -1483,20 +1485,33 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
   }
 }
 
-// Each slice count runs a body specialised for it (the count is decided on the device
-// by the preceding control kernel and is uniform over the launch): one body with a
-// runtime flag ran the one-slice products 8 % slower.
+// Which body runs: two-slice stages for a two-slice product after the first.  The
+// tensor core's FP32 accumulation drops the bits below its running sum at every step,
+// so interleaving the small slice with the large one (both slices per K-block) adds
+// that loss at the scale of the full partial sums: about twice the accumulator error
+// of the per-slice order (measured on the GB300 at n = 256 .. 2048, and in a NumPy model
+// of the truncating accumulation).  That error scales with the product's increment,
+// and the first one, dt_0, is the largest by the map's contraction, so the first
+// product keeps the per-slice order (the increment tile loaded once per slice) and
+// the accuracy of the result is that of the per-slice order.  The decision reads
+// fields the preceding control kernel set (uniform over the launch).  Each case runs
+// a body specialised for it: one body with a runtime flag ran the one-slice products
+// 8 % slower.
+__device__ __forceinline__ bool two_slice_stages(const IterState* st) {
+  return *((const volatile int*)&st->slices) == 2 && *((const volatile int*)&st->k) != 1;
+}
+
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
 k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
                 const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
-  if (*((volatile int*)&p.st->slices) == 2) gemm_epi_pair_body<false, true>(tmA, tmB0, tmB1, p);
+  if (two_slice_stages(p.st)) gemm_epi_pair_body<false, true>(tmA, tmB0, tmB1, p);
   else gemm_epi_pair_body<false, false>(tmA, tmB0, tmB1, p);
 }
 
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(P_NTHREADS, 1)
 k_gemm_epi_quad(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
                 const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
-  if (*((volatile int*)&p.st->slices) == 2) gemm_epi_pair_body<true, true>(tmA, tmB0, tmB1, p);
+  if (two_slice_stages(p.st)) gemm_epi_pair_body<true, true>(tmA, tmB0, tmB1, p);
   else gemm_epi_pair_body<true, false>(tmA, tmB0, tmB1, p);
 }
 

@@ -62,3 +62,23 @@ def test_pair_bench_size_sampled(ora, dpt, form):
     Ao, Eo, io = ora.solve_full(cfg["theta"], cfg["delta"], cfg["lam"], tol=1e-13, cols=cols)
     A, E = to_np(A), to_np(E)
     assert eig_err(E[cols], Eo) <= EIG_RTOL and vec_err(A[:, cols], Ao) <= VEC_TOL
+
+
+@pytest.mark.parametrize("n,rep", [(256, 1), (1000, 4)])
+def test_two_slice_stages_keep_the_accuracy(ora, dpt, n, rep):
+    """The pair form loads both slices per K-block after the first product (the
+    increment tile fetched once); the first product, whose increment is the largest,
+    keeps the per-slice accumulation order.  The eigenvector error against the FP64
+    fixed point then stays that of the one-CTA form, which uses the per-slice order
+    throughout (interleaving the slices in the first product too doubled it)."""
+    cfg = inputs.full_unsymmetric(n=n, rep=rep)
+    th, D = _dev(cfg, dpt)
+    Ao, Eo, io = ora.solve_full(cfg["theta"], cfg["delta"], cfg["lam"], tol=1e-14, max_iter=60)
+    assert io["status"] == "OK"
+    errs = []
+    for form in (1, 0):
+        A, E, info = dpt.solve_full(th, D, cfg["lam"], cta_pair=form)
+        assert info["status"] == "OK" and info["cta_pair"] == form
+        errs.append(vec_err(to_np(A), Ao))
+    assert errs[0] <= 1.25 * errs[1] + 1e-12, errs
+    assert errs[0] <= VEC_TOL, errs
