@@ -79,10 +79,9 @@ typedef enum {
   DPT_PREC_FP64 = 0,        /* every product in FP64 on the CUDA cores: the map of
                                Eq. (dyn) applied literally */
   DPT_PREC_MIXED = 1        /* tensor-core products: each iteration multiplies Delta,
-                               split into 16-bit slices, by the 16-bit increment of
-                               A, with FP32 accumulation (real single solves: FP16
-                               slices and increments with power-of-two scales;
-                               complex and grouped solves: BF16); A, the residual
+                               split into FP16 slices, by the FP16 increment of A,
+                               with FP32 accumulation (slices and increments carry
+                               power-of-two scales chosen per problem); A, the residual
                                and the eigenvalues are carried in extended
                                precision, so the iteration refines to the FP64
                                fixed point.  There is no TF32 variant: on this GPU
@@ -103,22 +102,22 @@ typedef struct {
                               (the partition of Sec. II.H); same eigenpairs */
   int32_t graph_iters;     /* iterations per captured CUDA graph replay between
                               host convergence checks (default 4; 0 = no graph) */
-  int32_t max_slices;      /* slices of Delta in the mixed path, 1..3 (default 3): that
-                              many BF16 slices in grouped and complex solves; a real
-                              single solve uses FP16 slices (11 significant bits each),
-                              two for max_slices 2 or 3 and one for 1.  The first
-                              products use all of them, and the slices represent Delta
-                              to about 2^-8 (BF16) or 2^-11 (FP16) relative per slice:
-                              fewer than the default bound the result's accuracy by
+  int32_t max_slices;      /* slices of Delta in the mixed path, 1..3 (default 3): FP16
+                              slices (11 significant bits each); a real single solve
+                              uses two for max_slices 2 or 3 (its FP64 finish covers
+                              the columns two leave uncertain), grouped, served and
+                              complex solves that many.  The first products use all of
+                              them, and the slices represent Delta to about 2^-11
+                              relative per slice: fewer bound the result's accuracy by
                               that representation (the carried remainder makes up for
                               the rounding of the increments, not for that of Delta) */
   int32_t profile;         /* nonzero: time every product kernel with CUDA events on
                               the stream it runs on (reported in dpt_info) */
   double slice_tol;        /* mixed path: the first product uses all its slices; a
-                              later one drops a slice for each factor 2^-8 (BF16) or
-                              2^-11 (FP16) by which its increment's largest entry
-                              is below the first increment's, and uses one below
-                              slice_tol (default 1e-8) */
+                              later one drops a slice for each factor 2^-11 by which
+                              its increment's largest entry is below the first
+                              increment's, and uses one below slice_tol (default
+                              1e-8) */
   int32_t cta_pair;        /* real mixed full solve: 1 (default) runs the product as
                               CTA pairs (tcgen05 cta_group::2, 256-row tiles split
                               over two SMs, epilogue inputs staged in the shared memory

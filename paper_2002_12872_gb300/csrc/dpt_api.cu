@@ -111,10 +111,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D BF16 tensor map: inner extent `inner` (contiguous), outer extent `outer`,
+// 2-D FP16 tensor map: inner extent `inner` (contiguous), outer extent `outer`,
 // row pitch `pitch_elems`, box 64 x box_rows, 128-byte swizzle.
-CUtensorMap make_tmap_bf16(const void* base, uint64_t inner, uint64_t outer,
-                           uint64_t pitch_elems, uint32_t box_rows, bool f16) {
+CUtensorMap make_tmap_f16(const void* base, uint64_t inner, uint64_t outer,
+                          uint64_t pitch_elems, uint32_t box_rows) {
   CUtensorMap m;
   auto fn = encode_fn();
   if (!fn) throw Fail{DPT_ERR_CUDA};
@@ -122,8 +122,7 @@ CUtensorMap make_tmap_bf16(const void* base, uint64_t inner, uint64_t outer,
   cuuint64_t strides[1] = {pitch_elems * 2};
   cuuint32_t box[2] = {64, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(&m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                  2, const_cast<void*>(base), dims,
+  CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims,
                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Fail{DPT_ERR_CUDA};
@@ -522,7 +521,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
                     d, part, rowpart, sdev, ld_s, sinv, st, s));
     CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
 
-    const CUtensorMap tA = make_tmap_bf16(Dcat, (uint64_t)3 * ld, n, (uint64_t)3 * ld, 128, true);
+    const CUtensorMap tA = make_tmap_f16(Dcat, (uint64_t)3 * ld, n, (uint64_t)3 * ld, 128);
     int nsm = 0, dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
@@ -541,8 +540,8 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     }
     const bool pair = npairs > 0;
     const int bn = pair ? mixed_pair_tile_n((int)n, npairs, ctas) : mixed_tile_n((int)n, nsm);
-    const CUtensorMap tB0 = make_tmap_bf16(dtb[0], n, n, ld, pair ? bn / 2 : bn, true);
-    const CUtensorMap tB1 = make_tmap_bf16(dtb[1], n, n, ld, pair ? bn / 2 : bn, true);
+    const CUtensorMap tB0 = make_tmap_f16(dtb[0], n, n, ld, pair ? bn / 2 : bn);
+    const CUtensorMap tB1 = make_tmap_f16(dtb[1], n, n, ld, pair ? bn / 2 : bn);
     GemmEpiParams p{};
     p.n = n; p.ld = ld; p.ntm = ntm; p.bn = bn; p.lam = (float)lambda;
     for (int q = 0; q < 2; ++q) { p.A_hi[q] = Ahi[q]; p.A_lo[q] = Alo[q]; p.dt[q] = dtb[q]; }
@@ -1330,10 +1329,10 @@ static void carve_problem(GProb& P, Carve& c) {
   P.e_col = c.take<float>(w * ld); P.dprev_col = c.take<float>(w * ld);
   P.part = c.take<float>((size_t)(2 + 2 * w) * P.ntm * ld);
   P.rowpart = c.take<float>((size_t)((np + 127) / 128) * ld);
-  P.Dcat = c.take<__nv_bfloat16>((size_t)3 * ld * nr);
+  P.Dcat = c.take<__half>((size_t)3 * ld * nr);
   P.cat_ld = (int64_t)3 * ld;
   for (int q = 0; q < 2; ++q) { P.A_hi[q] = c.take<float>((size_t)ld * np); P.A_lo[q] = c.take<float>((size_t)ld * np); }
-  for (int q = 0; q < 2; ++q) P.dt[q] = c.take<__nv_bfloat16>((size_t)ld * np);
+  for (int q = 0; q < 2; ++q) P.dt[q] = c.take<__half>((size_t)ld * np);
   P.L = c.take<float>((size_t)ld * np);
 }
 
@@ -1508,8 +1507,9 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
       h = IterState{};
       h.status = ST_RUNNING;
       h.max_iter = o.max_iter;
+      // up to three FP16 slices of Delta 2^sig (see dpt_grouped.cu)
       h.max_slices = o.max_slices;
-      h.slices = o.max_slices;
+      h.slices = h.max_slices;
       h.lam = lambda[p];
       h.tol = o.tol;
       h.slice_tol = o.slice_tol;
@@ -1537,6 +1537,8 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
     int max_n = 0;
     for (int p = 0; p < count; ++p) max_n = std::max(max_n, (int)n[p]);
     CK(launch_g_check_theta(probs, count, max_n, flags, s));
+    CK(launch_g_scales(probs, blk, n_blk_r, false, s));
+    CK(launch_g_scales(probs, blk + n_blk_r, n_blk_c, true, s));
     CK(launch_g_prep(probs, prep, n_prep_r, s));
     CK(launch_gc_prep(probs, prep + n_prep_r, n_prep_c, s));
     CK(launch_g_iter0(probs, blk, n_blk_r, s));
@@ -1550,9 +1552,9 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
     std::vector<Maps> maps(count);
     encode_group_maps(g.probs.data(), count, [&](int p) {
       const GProb& P = g.probs[p];
-      maps[p].m[0] = make_tmap_bf16(P.Dcat, (uint64_t)3 * P.ld, P.nr, (uint64_t)3 * P.ld, 128);
+      maps[p].m[0] = make_tmap_f16(P.Dcat, (uint64_t)3 * P.ld, P.nr, (uint64_t)3 * P.ld, 128);
       for (int q = 0; q < 2; ++q)
-        maps[p].m[1 + q] = make_tmap_bf16(P.dt[q], P.nr, P.n, P.ld, gform_box(form, P.bn));
+        maps[p].m[1 + q] = make_tmap_f16(P.dt[q], P.nr, P.n, P.ld, gform_box(form, P.bn));
     });
     static_assert(offsetof(GProb, tmA) == 0 && offsetof(GProb, tmB) == sizeof(CUtensorMap),
                   "descriptors lead the table entry");

@@ -1,9 +1,9 @@
-// Device helpers shared by the libdpt kernels: float-float arithmetic, BF16
-// rounding, bounded mbarrier waits, TMA loads and tcgen05 (TMEM / UMMA) wrappers
+// Device helpers shared by the libdpt kernels: float-float arithmetic, scaled FP16
+// operands, bounded mbarrier waits, TMA loads and tcgen05 (TMEM / UMMA) wrappers
 // written as inline PTX for sm_103a.
 #pragma once
 
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -128,69 +128,6 @@ __device__ __forceinline__ double f2d_bits(float f) {
   }
   const unsigned long long de = (e == 0xFFu) ? 0x7FFull : (unsigned long long)(e - 127 + 1023);
   return __longlong_as_double((long long)(sign | (de << 52) | m));
-}
-
-// One 32-row x 64-column tile of the Delta -> BF16-slice conversion, block (32, 8).
-// Reads Delta (FP64, column-major, rows j contiguous) at rows [by, by+32) and
-// columns [bx, bx+64) into shared memory, then writes row j of each of the three
-// slices (row-major, pitch ld inside a row of cat_ld = 3 ld elements) as BF16
-// pairs: with v = hi + lo (split_double_fast), D1 = bf16(hi), D2 = bf16(hi - D1),
-// D3 = bf16(hi - D1 - D2 + lo); the first two remainders are exact in float (hi has
-// 24 significant bits), so D1 + D2 + D3 = v to 2^-24 relative.  Columns
-// in [n, ld) are written as zeros; en != 0 zeroes the diagonal.  A non-finite
-// entry, or one of magnitude 2^128 or more (beyond the float range of the slices),
-// sets *bad.
-__device__ __forceinline__ void slice_tile_32x64(const double* __restrict__ delta, int64_t ld_in,
-                                                 int n, int ld, int en, int bx, int by,
-                                                 __nv_bfloat16* __restrict__ Dcat, int64_t cat_ld,
-                                                 unsigned* bad, double (*tile)[65]) {
-  const int x = threadIdx.x, y = threadIdx.y;
-  {
-    // all eight loads are issued before any check (an atomic between them would
-    // keep the next load from starting)
-    const int j = by + x;
-    double v[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int k = bx + y + 8 * m;
-      v[m] = (j < n && k < n) ? delta[(int64_t)k * ld_in + j] : 0.0;
-    }
-    bool badv = false;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int k = bx + y + 8 * m;
-      badv |= beyond_float(v[m]);   // non-finite, or beyond the float range
-      if (en && j == k) v[m] = 0.0;
-      tile[x][y + 8 * m] = v[m];    // tile[j - by][k - bx]
-    }
-    if (badv) atomicExch(bad, 1u);
-  }
-  __syncthreads();
-  const int k0 = bx + 2 * x;
-  if (k0 >= ld) return;
-#pragma unroll
-  for (int r = y; r < 32; r += 8) {
-    const int j = by + r;
-    if (j >= n) break;
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-    if (k0 < n) split_double_fast(tile[r][2 * x], h0, l0);
-    if (k0 + 1 < n) split_double_fast(tile[r][2 * x + 1], h1, l1);
-    __nv_bfloat16* row = Dcat + (int64_t)j * cat_ld + k0;
-    // hi has 24 significant bits: D1 and D2 take 8 each with exact remainders, and
-    // the third slice rounds what is left together with lo
-    const __nv_bfloat16 a0 = __float2bfloat16_rn(h0), a1 = __float2bfloat16_rn(h1);
-    const float r0 = h0 - __bfloat162float(a0), r1 = h1 - __bfloat162float(a1);
-    const __nv_bfloat16 b0 = __float2bfloat16_rn(r0), b1 = __float2bfloat16_rn(r1);
-    const __nv_bfloat16 c0 = __float2bfloat16_rn((r0 - __bfloat162float(b0)) + l0);
-    const __nv_bfloat16 c1 = __float2bfloat16_rn((r1 - __bfloat162float(b1)) + l1);
-    *reinterpret_cast<__nv_bfloat162*>(row) = __halves2bfloat162(a0, a1);
-    *reinterpret_cast<__nv_bfloat162*>(row + ld) = __halves2bfloat162(b0, b1);
-    *reinterpret_cast<__nv_bfloat162*>(row + 2 * (int64_t)ld) = __halves2bfloat162(c0, c1);
-  }
-}
-
-__device__ __forceinline__ float bf16_round(float x) {
-  return __bfloat162float(__float2bfloat16_rn(x));
 }
 
 // ---------------------------------------------------------------------------
@@ -322,8 +259,9 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// D[tmem] (+)= A[smem] * B[smem], kind::f16 (BF16 inputs, FP32 accumulator)
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+// D[tmem] (+)= A[smem] * B[smem], kind::f16 (16-bit inputs of the type idesc names,
+// FP32 accumulator)
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
                                           uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -422,7 +360,7 @@ __device__ __forceinline__ void tma_load_2d_pair_multicast(void* dst, const void
 }
 
 // D[tmem of both CTAs] (+)= A[smem of both CTAs, M halves] * B[smem of both CTAs, N halves]
-__device__ __forceinline__ void umma_bf16_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+__device__ __forceinline__ void umma_f16_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
                                                uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -463,7 +401,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile stored with the
-// 128-byte swizzle (rows of 64 BF16 = 128 B; 8-row groups 1024 B apart).
+// 128-byte swizzle (rows of 64 16-bit elements = 128 B; 8-row groups 1024 B apart).
 //   bits  0-13  start address >> 4
 //   bits 16-29  leading-dimension byte offset >> 4 (unused for this layout: 1)
 //   bits 32-45  stride-dimension byte offset >> 4 (1024 B between 8-row groups)
@@ -480,14 +418,10 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(const void* tile) {
   return d;
 }
 
-// Instruction descriptor, kind::f16: BF16 A and B, FP32 D, both K-major.
-//   bits 4-5 D format (1 = F32), 7-9 A format (1 = BF16), 10-12 B format (1 = BF16),
+// Instruction descriptor, kind::f16: FP16 A and B (type fields 0; both operands of one
+// MMA have the same type), FP32 D, both K-major.
+//   bits 4-5 D format (1 = F32), 7-9 A format, 10-12 B format (0 = F16),
 //   15/16 A/B major (0 = K), 17-22 N >> 3, 24-28 M >> 4
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-// The same with FP16 A and B (type fields 0): both operands of one MMA are FP16.
 __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
@@ -546,8 +480,8 @@ __device__ __forceinline__ int transpose_sum16_col(int lane) {
 // ---------------------------------------------------------------------------
 struct Col4 {
   float4 ah, al, L;
-  uint2 dtp;      // four BF16
-  uint2 D[3];     // Delta_ij as three BF16 slices, four rows each
+  uint2 dtp;      // four FP16 (the stored, scaled previous increment)
+  uint2 D[3];     // Delta_ij 2^sig as FP16 slices, four rows each
 };
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -557,14 +491,6 @@ __device__ __forceinline__ float f4(const float4& v, int e) {
 }
 __device__ __forceinline__ void f4set(float4& v, int e, float x) {
   if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
-}
-__device__ __forceinline__ float bf_at(uint2 u, int e) {
-  const uint32_t w = (e < 2) ? u.x : u.y;
-  const uint32_t h = (e & 1) ? (w >> 16) : (w & 0xFFFFu);
-  return __uint_as_float(h << 16);
-}
-__device__ __forceinline__ uint32_t bf_bits(float x) {
-  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x));
 }
 // Element e (0..3) of four FP16 values packed in a uint2, as a float (exact).
 __device__ __forceinline__ float h_at(uint2 u, int e) {
@@ -584,6 +510,75 @@ __device__ __forceinline__ float exp2i(int e) { return __uint_as_float((unsigned
 __device__ __forceinline__ int ilog2_bits(double x) {
   return (int)(((unsigned)__double2hiint(x) >> 20) & 0x7FFu) - 1023;
 }
+
+// x qs rounded to FP16 (nearest even, +-65504 beyond the range): the FP16 bits in
+// `bits` and the rounded value times iqs (exact for power-of-two qs, iqs = 1 / qs)
+__device__ __forceinline__ float f16_scaled(float x, float qs, float iqs, uint32_t& bits) {
+  const uint32_t w = f16x2_sat(x * qs, 0.f);
+  bits = w & 0xFFFFu;
+  return __half2float(__ushort_as_half((unsigned short)bits)) * iqs;
+}
+
+// One 32-row x 64-column tile of the Delta -> FP16-slice conversion, block (32, 8).
+// Reads Delta (FP64, column-major, rows j contiguous) at rows [by, by+32) and columns
+// [bx, bx+64) into shared memory, then writes row j of NSL slices (row-major, pitch ld
+// inside a row of cat_ld elements) as FP16 pairs of Delta 2^sig (sc = 2^sig): with
+// v = hi + lo (split_double_fast), D1 = f16(hi sc), each further slice the FP16
+// rounding of what is left (the remainders are exact in float), the last one taking
+// lo sc as well.  Columns in [n, ld) are written as zeros; en != 0 zeroes the
+// diagonal.  A non-finite entry, or one of magnitude 2^128 or more (beyond the float
+// range), sets *bad.
+template <int NSL>
+__device__ __forceinline__ void slice16_tile_32x64(const double* __restrict__ delta, int64_t ld_in,
+                                                   int n, int ld, int en, float sc, int bx,
+                                                   int by, __half* __restrict__ Dcat, int64_t cat_ld,
+                                                   unsigned* bad, double (*tile)[65]) {
+  const int x = threadIdx.x, y = threadIdx.y;
+  {
+    // all eight loads are issued before any check (an atomic between them would
+    // keep the next load from starting)
+    const int j = by + x;
+    double v[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = bx + y + 8 * m;
+      v[m] = (j < n && k < n) ? delta[(int64_t)k * ld_in + j] : 0.0;
+    }
+    bool badv = false;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = bx + y + 8 * m;
+      badv |= beyond_float(v[m]);   // non-finite, or beyond the float range
+      if (en && j == k) v[m] = 0.0;
+      tile[x][y + 8 * m] = v[m];    // tile[j - by][k - bx]
+    }
+    if (badv) atomicExch(bad, 1u);
+  }
+  __syncthreads();
+  const int k0 = bx + 2 * x;
+  if (k0 >= ld) return;
+#pragma unroll
+  for (int r = y; r < 32; r += 8) {
+    const int j = by + r;
+    if (j >= n) break;
+    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+    if (k0 < n) split_double_fast(tile[r][2 * x], h0, l0);
+    if (k0 + 1 < n) split_double_fast(tile[r][2 * x + 1], h1, l1);
+    __half* row = Dcat + (int64_t)j * cat_ld + k0;
+    float r0 = h0 * sc, r1 = h1 * sc;
+#pragma unroll
+    for (int sl = 0; sl < NSL; ++sl) {
+      const bool lastsl = (sl == NSL - 1);
+      const float t0 = lastsl ? r0 + l0 * sc : r0;
+      const float t1 = lastsl ? r1 + l1 * sc : r1;
+      const __half q0 = __float2half_rn(t0), q1 = __float2half_rn(t1);
+      r0 = t0 - __half2float(q0);
+      r1 = t1 - __half2float(q1);
+      *reinterpret_cast<__half2*>(row + (int64_t)sl * ld) = __halves2half2(q0, q1);
+    }
+  }
+}
+
 // Warp reduction of the column sums: |R|^2 and |a|^2 in float, the diagonal
 // increment (eh, el) in float-float.
 __device__ __forceinline__ void warp_sum_ff(float& r2, float& a2, float& eh, float& el) {
@@ -684,23 +679,12 @@ __device__ __forceinline__ void dom_ramp_advance(SP* vs) {
 
 // ---------------------------------------------------------------------------
 // Slices of Delta for the next product, from the largest increment dmax it will
-// multiply.  With S BF16 slices the truncation of Delta is about 2^(-8S) relative,
-// so a product's truncation error is about 2^(-8S) |Delta| dmax.  The first product
-// (three slices on the increment dt_0 of size dmax1) sets the error the solve
-// accepts; later products take the fewest slices that stay below it: two once
-// dmax <= 2^-8 dmax1, one once dmax <= 2^-16 dmax1 (or below slice_tol).  The
-// carried remainder makes the fixed point that of the full Delta either way.
+// multiply.  With S FP16 slices the truncation of Delta is about 2^(-11 S) relative,
+// so a product's truncation error is about 2^(-11 S) |Delta| dmax.  The first product
+// (nsl slices on the increment dt_0 of size dmax1) sets the error the solve accepts;
+// later products take the fewest slices that stay below it.  The carried remainder
+// makes the fixed point that of the full Delta either way.
 // ---------------------------------------------------------------------------
-template <class SP>
-__device__ __forceinline__ int next_slices(SP* vs, float dmax, bool first) {
-  if (first) vs->dmax1 = dmax;
-  const float d1 = vs->dmax1;
-  int S = vs->max_slices;
-  if ((double)dmax < vs->slice_tol || dmax <= d1 * 0x1p-16f) S = 1;
-  else if (dmax <= d1 * 0x1p-8f) S = 2;
-  return S < vs->max_slices ? S : vs->max_slices;
-}
-
 // The same rule for FP16 slices (11 significant bits each, so about 2^(-11 S)
 // relative) of a solve whose first product used nsl of them: S slices once
 // dmax <= 2^(-11 (nsl - S)) dmax1, one below slice_tol.

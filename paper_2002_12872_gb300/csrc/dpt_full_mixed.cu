@@ -27,7 +27,6 @@
 // convergence test without a second product.
 
 #include <cuda.h>
-#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -213,62 +212,6 @@ __global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__
   vs->sexp[0] = s0;
   vs->sexp[1] = s0;
   vs->blocks_done = 0;
-}
-
-// One 32-row x 64-column tile of the Delta -> FP16-slice conversion, block (32, 8):
-// as slice_tile_32x64 (shared-memory transpose, row-major slices of pitch cat_ld),
-// with NSL FP16 slices of Delta 2^sig: D1 = f16(hi 2^sig), each further slice the
-// FP16 rounding of what is left (the remainders are exact in float), the last one
-// taking lo as well.
-template <int NSL>
-__device__ __forceinline__ void slice16_tile_32x64(const double* __restrict__ delta, int64_t ld_in,
-                                                   int n, int ld, int en, float sc, int bx,
-                                                   int by, __half* __restrict__ Dcat, int64_t cat_ld,
-                                                   unsigned* bad, double (*tile)[65]) {
-  const int x = threadIdx.x, y = threadIdx.y;
-  {
-    // all eight loads are issued before any check (an atomic between them would
-    // keep the next load from starting)
-    const int j = by + x;
-    double v[8];
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int k = bx + y + 8 * m;
-      v[m] = (j < n && k < n) ? delta[(int64_t)k * ld_in + j] : 0.0;
-    }
-    bool badv = false;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int k = bx + y + 8 * m;
-      badv |= beyond_float(v[m]);   // non-finite, or beyond the float range
-      if (en && j == k) v[m] = 0.0;
-      tile[x][y + 8 * m] = v[m];    // tile[j - by][k - bx]
-    }
-    if (badv) atomicExch(bad, 1u);
-  }
-  __syncthreads();
-  const int k0 = bx + 2 * x;
-  if (k0 >= ld) return;
-#pragma unroll
-  for (int r = y; r < 32; r += 8) {
-    const int j = by + r;
-    if (j >= n) break;
-    float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
-    if (k0 < n) split_double_fast(tile[r][2 * x], h0, l0);
-    if (k0 + 1 < n) split_double_fast(tile[r][2 * x + 1], h1, l1);
-    __half* row = Dcat + (int64_t)j * cat_ld + k0;
-    float r0 = h0 * sc, r1 = h1 * sc;
-#pragma unroll
-    for (int sl = 0; sl < NSL; ++sl) {
-      const bool lastsl = (sl == NSL - 1);
-      const float t0 = lastsl ? r0 + l0 * sc : r0;
-      const float t1 = lastsl ? r1 + l1 * sc : r1;
-      const __half q0 = __float2half_rn(t0), q1 = __float2half_rn(t1);
-      r0 = t0 - __half2float(q0);
-      r1 = t1 - __half2float(q1);
-      *reinterpret_cast<__half2*>(row + (int64_t)sl * ld) = __halves2half2(q0, q1);
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -853,7 +796,7 @@ k_gemm_epi(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUte
 #pragma unroll
         for (int kk = 0; kk < BK / UK; ++kk) {
           // advance the start address by kk * 32 bytes inside the swizzle atom
-          umma_bf16(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+          umma_f16(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
                     (q > 0 || kk > 0) ? 1u : 0u);
         }
         umma_commit(&ms->empty[s]);
@@ -1341,13 +1284,13 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
         const uint64_t db = smem_desc_sw128(slot + na * A_TILE);
 #pragma unroll
         for (int kk = 0; kk < BK / UK; ++kk)
-          umma_bf16_pair(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+          umma_f16_pair(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
                          (q > 0 || kk > 0) ? 1u : 0u);
         if (merged) {
           const uint64_t da0 = smem_desc_sw128(slot + A_TILE);
 #pragma unroll
           for (int kk = 0; kk < BK / UK; ++kk)
-            umma_bf16_pair(dacc, da0 + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, 1u);
+            umma_f16_pair(dacc, da0 + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, 1u);
         }
         umma_commit_pair(&ms->empty[s], (uint16_t)(QUAD ? 0xF : 0x3));
       }

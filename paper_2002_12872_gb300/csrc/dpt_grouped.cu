@@ -10,13 +10,22 @@
 // Sec. II.B; the arithmetic per problem is that of the single-problem mixed path,
 // see dpt_full_mixed.cu).
 //
+// Operands: as in the single solve, Delta 2^sig as FP16 slices and each increment as
+// FP16 scaled by a power of two chosen from the size of the previous one
+// (IterState::sig, sexp[2]); the scales are exact, so every product and partial is
+// unscaled by a power of two (see dpt_full_mixed.cu).  Up to three slices (33
+// significant bits of Delta): the grouped solves have no FP64 finish of the columns
+// two slices leave uncertain (measured: a strongly coupled complex n = 3 problem
+// missed the 1e-10 eigenvalue bar with two), and the slice rule drops to two and one
+// as the increments shrink by 2^-11 and 2^-22.
+//
 // Tile shape per problem (chosen on the host from n): M = 128 rows, N = the
 // smallest multiple of 32 that covers n in ceil(n / 256) column tiles, so small
 // problems do not pay for 256-wide tiles.  The host orders the tile list by cost
 // (K extent x width, largest first) so that the round-robin assignment to the
 // persistent CTAs stays balanced across problems of very different size.
 #include <cuda.h>
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "dpt_device.cuh"
@@ -92,7 +101,76 @@ __global__ void __launch_bounds__(128) k_g_check_theta(const GProb* __restrict__
 }
 
 // ---------------------------------------------------------------------------
-// Delta -> three BF16 slices (row-major) and theta -> float-float.
+// The FP16 scales of each problem, from its Delta and theta (before the slicing):
+// sig places max |Delta| 2^sig in [2^14, 2^15) (entries of the largest slice keep 11
+// bits; the second slice takes what the first drops), and the first increment's scale
+// sexp[0] places its bound |lambda| max |Delta_ji| / |theta_i - theta_j| at 2^13 (as
+// the single solve's k_delta_scales).  Work item: a 128 x 128 tile of iteration 0
+// (for a complex problem 128 columns by 64 complex rows); thread r owns a row.  The
+// maxima reach the state by atomicMax on non-negative float / double-high-word bits;
+// the problem's last item sets the scales.
+// ---------------------------------------------------------------------------
+template <bool CPLX>
+__global__ void __launch_bounds__(128) k_g_scales(const GProb* __restrict__ probs,
+                                                  const int4* __restrict__ items) {
+  const int4 it = items[blockIdx.x];
+  const GProb* P = probs + it.x;
+  if ((P->cplx != 0) != CPLX || !g_running(P)) return;
+  IterState* st = P->st;
+  const int n = P->n;
+  const int i0 = it.y * 128, i1 = min(n, i0 + 128);
+  const int j = (CPLX ? it.z * 64 : it.z * 128) + (int)threadIdx.x;
+  unsigned hmax = 0u;
+  float gmax = 0.f;
+  if (j < n && (!CPLX || threadIdx.x < 64)) {
+    const double tj = P->theta[j];
+    for (int i = i0; i < i1; ++i) {
+      double vmax;
+      if (CPLX) {
+        const double2 v = reinterpret_cast<const double2*>(P->delta_in)[(int64_t)i * P->ld_in + j];
+        vmax = fmax(fabs(v.x), fabs(v.y));
+      } else {
+        vmax = fabs(P->delta_in[(int64_t)i * P->ld_in + j]);
+      }
+      hmax = max(hmax, (unsigned)__double2hiint(vmax) & 0x7FFFFFFFu);
+      if (i != j) {
+        // NaN never wins fmaxf (the slicing rejects non-finite entries)
+        const float g = fabsf((float)(P->theta[i] - tj));
+        gmax = fmaxf(gmax, (float)vmax / g);
+      }
+    }
+  }
+  hmax = __reduce_max_sync(0xffffffffu, hmax);
+  const unsigned gb = __reduce_max_sync(0xffffffffu, __float_as_uint(gmax));
+  __shared__ unsigned wh[4], wg[4];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { wh[w] = hmax; wg[w] = gb; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const unsigned a = max(max(wh[0], wh[1]), max(wh[2], wh[3]));
+  const unsigned b = max(max(wg[0], wg[1]), max(wg[2], wg[3]));
+  atomicMax(&st->amax_bits, a);
+  atomicMax(&st->g0max_bits, b);
+  __threadfence();
+  const unsigned nitems = (unsigned)(P->ntm * ((n + 127) / 128));
+  if (atomicAdd(&st->blocks_done, 1u) != nitems - 1u) return;
+  __threadfence();
+  volatile IterState* vs = st;
+  const unsigned hm = vs->amax_bits;
+  int sig = 0;
+  if (hm != 0u) sig = 14 - ((int)((hm >> 20) & 0x7FFu) - 1023);   // max |Delta| < 2^(e+1)
+  sig = max(-120, min(120, sig));
+  const double lam = vs->lam;
+  const double g0 = (double)__uint_as_float(vs->g0max_bits);
+  const int s0 = dt_scale_exp(fabs(lam) * g0, 13, sig, lam);
+  vs->sig = sig;
+  vs->sexp[0] = s0;
+  vs->sexp[1] = s0;
+  vs->blocks_done = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Delta -> three FP16 slices of Delta 2^sig (row-major) and theta -> float-float.
 // Work item: (problem, 64-column block, 32-row block); block 32 x 8.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_g_prep(const GProb* __restrict__ probs,
@@ -112,8 +190,8 @@ __global__ void __launch_bounds__(256) k_g_prep(const GProb* __restrict__ probs,
       P->th_lo[j] = l;
     }
   }
-  slice_tile_32x64(P->delta_in, P->ld_in, n, ld, 0, it.y * 64, by, P->Dcat, P->cat_ld,
-                   &P->st->bad_input, tile);
+  slice16_tile_32x64<3>(P->delta_in, P->ld_in, n, ld, 0, exp2i(P->st->sig), it.y * 64, by,
+                        P->Dcat, P->cat_ld, &P->st->bad_input, tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -131,6 +209,9 @@ __global__ void __launch_bounds__(128) k_g_iter0(const GProb* __restrict__ probs
   const int r0 = 4 * lane, j0 = m0 + r0;
   const int64_t cat_ld = P->cat_ld;
   const float lam_hi = P->lam, lam_lo = P->lam_lo;
+  // dt_0 stored as dt_0 2^sexp[0]; the slices hold Delta 2^sig
+  const float qs = exp2i(P->st->sexp[0]), iqs = exp2i(-P->st->sexp[0]);
+  const float isig = exp2i(-P->st->sig);
   const float4 thj_h = *reinterpret_cast<const float4*>(P->th_hi + j0);
   const float4 thj_l = *reinterpret_cast<const float4*>(P->th_lo + j0);
   const double* delta = P->delta_in;
@@ -141,12 +222,12 @@ __global__ void __launch_bounds__(128) k_g_iter0(const GProb* __restrict__ probs
     const int i = n0 + 32 * w + c;
     if (i >= n) break;
     const float thi_h = P->th_hi[i], thi_l = P->th_lo[i];
-    const __nv_bfloat16* Drow = P->Dcat + (int64_t)i * cat_ld + j0;
+    const __half* Drow = P->Dcat + (int64_t)i * cat_ld + j0;
     uint2 D[3];
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
     float4 oh, oL;
-    uint32_t ob[4];
+    uint32_t ob[4] = {0u, 0u, 0u, 0u};
     float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -169,15 +250,18 @@ __global__ void __launch_bounds__(128) k_g_iter0(const GProb* __restrict__ probs
           fast_two_sum(pr, pe, R0h, R0l);
           float gh, gl;
           ff_sub(thi_h, thi_l, f4(thj_h, e), f4(thj_l, e), gh, gl);
-          dtn = bf16_round(R0h * __frcp_rn(gh));
+          // the remainder below keeps R_0 - Gap dt_0 exactly, so any reciprocal
+          // close to 1/gap serves
+          dtn = f16_scaled(R0h * rcp_approx(gh), qs, iqs, ob[e]);
           float q, qe;
           two_prod(gh, dtn, q, qe);
           qe = fmaf(gl, dtn, qe);
           Ln = (R0h - q) + (R0l - qe);
           nh = dtn;
           r2 = fmaf(R0h, R0h, r2);
-          const float p1 = bf_at(D[0], e) * dtn;
-          const float p23 = fmaf(bf_at(D[1], e), dtn, bf_at(D[2], e) * dtn);
+          // e_1 2^sig from the slices (exact products)
+          const float p1 = h_at(D[0], e) * dtn;
+          const float p23 = fmaf(h_at(D[1], e), dtn, h_at(D[2], e) * dtn);
           float sh, se;
           two_sum(eh, p1, sh, se);
           se += el + p23;
@@ -187,7 +271,6 @@ __global__ void __launch_bounds__(128) k_g_iter0(const GProb* __restrict__ probs
       }
       f4set(oh, e, nh);
       f4set(oL, e, Ln);
-      ob[e] = bf_bits(dtn);
     }
     const int64_t idx = (int64_t)i * ld + j0;
     st4(P->A_hi[1] + idx, oh);
@@ -196,6 +279,8 @@ __global__ void __launch_bounds__(128) k_g_iter0(const GProb* __restrict__ probs
     *reinterpret_cast<uint2*>(P->dt[0] + idx) =
         make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
     warp_sum_ff(r2, a2, eh, el);
+    eh *= isig;
+    el *= isig;
     if (lane == 0) {
       P->part[((int64_t)0 * ntm + tm) * ld + i] = r2;
       P->part[((int64_t)1 * ntm + tm) * ld + i] = a2;
@@ -222,10 +307,10 @@ __global__ void __launch_bounds__(128) k_g_iter0(const GProb* __restrict__ probs
 // lambda are real.
 // ===========================================================================
 
-// Delta (complex, column-major, interleaved doubles) -> three BF16 slices of the
-// embedding; theta -> float-float.  Work item: (problem, 32 complex columns, 32
-// complex rows); block 32 x 8.  Each embedded row pair (2j, 2j+1) gets the two
-// BF16 pairs (Re, -Im) and (Im, Re) of element (j, k) at columns (2k, 2k+1), one
+// Delta (complex, column-major, interleaved doubles) -> three FP16 slices of the
+// embedding of Delta 2^sig; theta -> float-float.  Work item: (problem, 32 complex
+// columns, 32 complex rows); block 32 x 8.  Each embedded row pair (2j, 2j+1) gets the
+// two FP16 pairs (Re, -Im) and (Im, Re) of element (j, k) at columns (2k, 2k+1), one
 // 4-byte store per row and slice, so a warp writes 128 contiguous bytes.
 __global__ void __launch_bounds__(256) k_gc_prep(const GProb* __restrict__ probs,
                                                  const int4* __restrict__ items) {
@@ -259,23 +344,29 @@ __global__ void __launch_bounds__(256) k_gc_prep(const GProb* __restrict__ probs
   const int64_t cat_ld = P->cat_ld;
   const int k = bx + threadIdx.x;                 // complex column written by this thread
   if (2 * k >= ld) return;
+  const double sc = (double)exp2i(P->st->sig);
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int j = by + r;
     if (j >= n) break;
     const double2 v = (k < n) ? tile[threadIdx.x][r] : make_double2(0.0, 0.0);
-    float rh[2], rl[2], ih[2], il[2];
-    split_double(v.x, rh[0], rl[0]);
-    split_double(v.y, ih[0], il[0]);
-    __nv_bfloat16* row0 = P->Dcat + (int64_t)(2 * j) * cat_ld + 2 * k;
-    __nv_bfloat16* row1 = row0 + cat_ld;
-    for (int sl = 0; sl < G_NSLICE; ++sl) {
-      const __nv_bfloat16 br = __float2bfloat16_rn(rh[0]);
-      const __nv_bfloat16 bi = __float2bfloat16_rn(ih[0]);
-      // -Im rounds to -bf16(Im): the slices of -Im are the negated slices of Im
-      *reinterpret_cast<__nv_bfloat162*>(row0 + (int64_t)sl * ld) = __halves2bfloat162(br, __hneg(bi));
-      *reinterpret_cast<__nv_bfloat162*>(row1 + (int64_t)sl * ld) = __halves2bfloat162(bi, br);
-      two_sum(rh[0] - __bfloat162float(br), rl[0], rh[0], rl[0]);
-      two_sum(ih[0] - __bfloat162float(bi), il[0], ih[0], il[0]);
+    // entries beyond the float range after scaling: rejected (sig keeps the
+    // largest below 2^15, so this is a non-finite or overflowing input)
+    if (beyond_float(v.x * sc) || beyond_float(v.y * sc)) atomicExch(&P->st->bad_input, 1u);
+    float rh, rl, ih, il;
+    split_double(v.x * sc, rh, rl);
+    split_double(v.y * sc, ih, il);
+    __half* row0 = P->Dcat + (int64_t)(2 * j) * cat_ld + 2 * k;
+    __half* row1 = row0 + cat_ld;
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+      // the last slice takes the low parts as well; the remainders are exact in float
+      const float tr = sl == 2 ? rh + rl : rh, ti = sl == 2 ? ih + il : ih;
+      const __half br = __float2half_rn(tr), bi = __float2half_rn(ti);
+      // -Im rounds to -f16(Im): the slices of -Im are the negated slices of Im
+      *reinterpret_cast<__half2*>(row0 + (int64_t)sl * ld) = __halves2half2(br, __hneg(bi));
+      *reinterpret_cast<__half2*>(row1 + (int64_t)sl * ld) = __halves2half2(bi, br);
+      rh = tr - __half2float(br);
+      ih = ti - __half2float(bi);
     }
   }
 }
@@ -300,6 +391,9 @@ __global__ void __launch_bounds__(128) k_gc_iter0(const GProb* __restrict__ prob
   const int r0 = 4 * lane, jc0 = (m0 + r0) / 2;   // embedded rows m0+r0.., complex rows jc0, jc0+1
   const int64_t cat_ld = P->cat_ld;
   const float lam_hi = P->lam, lam_lo = P->lam_lo;
+  // dt_0 stored as dt_0 2^sexp[0]; the slices hold Delta 2^sig
+  const float qs = exp2i(P->st->sexp[0]), iqs = exp2i(-P->st->sexp[0]);
+  const float isig = exp2i(-P->st->sig);
   const double2* delta = reinterpret_cast<const double2*>(P->delta_in);
   const int64_t ld_in = P->ld_in;
   float thj_h[2], thj_l[2];
@@ -315,12 +409,12 @@ __global__ void __launch_bounds__(128) k_gc_iter0(const GProb* __restrict__ prob
     if (i >= n) break;
     const float thi_h = P->th_hi[i], thi_l = P->th_lo[i];
     // Delta(i, jc0..jc0+1) from embedded row 2i: (Re, -Im) pairs
-    const __nv_bfloat16* Drow = P->Dcat + (int64_t)(2 * i) * cat_ld + 2 * jc0;
+    const __half* Drow = P->Dcat + (int64_t)(2 * i) * cat_ld + 2 * jc0;
     uint2 D[3];
 #pragma unroll
     for (int sl = 0; sl < 3; ++sl) D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
     float oh[4], oL[4];
-    uint32_t ob[4];
+    uint32_t ob[4] = {0u, 0u, 0u, 0u};
     float r2 = 0.f, a2 = 0.f, erh = 0.f, erl = 0.f, eih = 0.f, eil = 0.f;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -340,7 +434,7 @@ __global__ void __launch_bounds__(128) k_gc_iter0(const GProb* __restrict__ prob
         } else {
           float gh, gl;
           ff_sub(thi_h, thi_l, thj_h[e], thj_l[e], gh, gl);
-          const float g = __frcp_rn(gh);
+          const float g = rcp_approx(gh);
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             float pr, pe;
@@ -348,7 +442,7 @@ __global__ void __launch_bounds__(128) k_gc_iter0(const GProb* __restrict__ prob
             pe = fmaf(lam_hi, vl[q], fmaf(lam_lo, vh[q], pe));
             float R0h, R0l;
             fast_two_sum(pr, pe, R0h, R0l);
-            dn[q] = bf16_round(R0h * g);
+            dn[q] = f16_scaled(R0h * g, qs, iqs, ob[2 * e + q]);
             float qq, qe;
             two_prod(gh, dn[q], qq, qe);
             qe = fmaf(gl, dn[q], qe);
@@ -356,13 +450,13 @@ __global__ void __launch_bounds__(128) k_gc_iter0(const GProb* __restrict__ prob
             A2[q] = dn[q];
             r2 = fmaf(R0h, R0h, r2);
           }
-          // e_1 partial: Delta(i, j) dt(j, i), slices exact
+          // e_1 2^sig partial: Delta(i, j) 2^sig dt(j, i), slices exact
           float pr1, pi1, pr2, pi2;
-          const float a1 = bf_at(D[0], 2 * e), b1 = bf_at(D[0], 2 * e + 1);
+          const float a1 = h_at(D[0], 2 * e), b1 = h_at(D[0], 2 * e + 1);
           pr1 = fmaf(a1, dn[0], b1 * dn[1]);          // a x + b' y   (b' = -Im)
           pi1 = fmaf(a1, dn[1], -b1 * dn[0]);         // a y - b' x
-          const float a2s = bf_at(D[1], 2 * e) + bf_at(D[2], 2 * e);
-          const float b2s = bf_at(D[1], 2 * e + 1) + bf_at(D[2], 2 * e + 1);
+          const float a2s = h_at(D[1], 2 * e) + h_at(D[2], 2 * e);
+          const float b2s = h_at(D[1], 2 * e + 1) + h_at(D[2], 2 * e + 1);
           pr2 = fmaf(a2s, dn[0], b2s * dn[1]);
           pi2 = fmaf(a2s, dn[1], -b2s * dn[0]);
           float sh, se;
@@ -373,7 +467,6 @@ __global__ void __launch_bounds__(128) k_gc_iter0(const GProb* __restrict__ prob
       }
       oh[2 * e] = A2[0]; oh[2 * e + 1] = A2[1];
       oL[2 * e] = L2[0]; oL[2 * e + 1] = L2[1];
-      ob[2 * e] = bf_bits(dn[0]); ob[2 * e + 1] = bf_bits(dn[1]);
     }
     const int64_t idx = (int64_t)i * ld + m0 + r0;
     st4(P->A_hi[1] + idx, make_float4(oh[0], oh[1], oh[2], oh[3]));
@@ -383,6 +476,7 @@ __global__ void __launch_bounds__(128) k_gc_iter0(const GProb* __restrict__ prob
     warp_sum_ff(r2, a2, erh, erl);
     float z0 = 0.f, z1 = 0.f;
     warp_sum_ff(z0, z1, eih, eil);
+    erh *= isig; erl *= isig; eih *= isig; eil *= isig;
     if (lane == 0) {
       P->part[((int64_t)0 * ntm + tm) * ld + i] = r2;
       P->part[((int64_t)1 * ntm + tm) * ld + i] = a2;
@@ -509,9 +603,12 @@ __global__ void __launch_bounds__(256) k_g_ctrl(const GProb* __restrict__ probs,
     atomicSub(running, 1);
     return;
   }
-  const int S = next_slices(vs, dmax, first);
+  const int S = next_slices_f16(vs, dmax, first, vs->max_slices);
   vs->slices = S;
   vs->slice_gemms = vs->slice_gemms + S;
+  // the next product writes dt_k into buffer cur, scaled so that the largest increment
+  // of the last step would land at 2^10 (as the single solve's control)
+  vs->sexp[vs->cur] = dt_scale_exp((double)dmax, 10, vs->sig, vs->lam);
 }
 
 // Output of complex problems (interleaved FP64): thread r owns embedded row r of
@@ -557,10 +654,34 @@ __global__ void __launch_bounds__(128) k_gc_finalize(const GProb* __restrict__ p
 // The grouped product kernel (persistent, warp-specialised; one CTA per SM).
 // Same structure and arithmetic as k_gemm_epi, with per-tile problem data.
 // ---------------------------------------------------------------------------
+// Scale factors of a tile's problem for the current product (see dpt_full_mixed.cu's
+// EpiConst): the epilogue works on X = (Delta 2^sig)(dt_{k-1} 2^scur) and the stored
+// previous increment as they are, with e and d_{k-1} staged as e 2^sig 2^scur and
+// d_{k-1} 2^sig and lambda as lambda 2^-sig 2^-scur; the new increment is stored as
+// dt_k 2^snew and the diagonal partials (from the slices) are scaled back by 2^-sig.
+struct GScale {
+  float lams;          // lambda 2^-sig 2^-scur
+  float fsig, fcur;    // 2^sig, 2^scur
+  float qs, iqs;       // 2^snew, 2^-snew
+  float isig;          // 2^-sig
+};
+__device__ __forceinline__ GScale g_scale(const GProb* P, const IterState* st, int cur) {
+  GScale g;
+  const int sig = st->sig, scur = st->sexp[cur ^ 1], snew = st->sexp[cur];
+  g.lams = (P->lam * exp2i(-sig)) * exp2i(-scur);
+  g.fsig = exp2i(sig);
+  g.fcur = exp2i(scur);
+  g.qs = exp2i(snew);
+  g.iqs = exp2i(-snew);
+  g.isig = exp2i(-sig);
+  return g;
+}
+
 struct GTileInfo {
   const GProb* P;
   int tm, tn, m0, n0, bn, S, cur, kbs;
   bool live;
+  GScale sc;
 };
 
 __device__ __forceinline__ GTileInfo g_tile(const GProb* probs, const int2* tiles, int t) {
@@ -577,6 +698,7 @@ __device__ __forceinline__ GTileInfo g_tile(const GProb* probs, const int2* tile
   ti.S = st->slices;
   ti.cur = st->cur;
   ti.kbs = ti.P->ld / G_BK;
+  ti.sc = g_scale(ti.P, st, ti.cur);
   return ti;
 }
 
@@ -590,10 +712,10 @@ __device__ __forceinline__ void g_epilogue_columns(const GTileInfo& ti, GSmem* m
   const float* __restrict__ Alc = c1 ? P->A_lo[1] : P->A_lo[0];
   float* __restrict__ Ahn = c1 ? P->A_hi[0] : P->A_hi[1];
   float* __restrict__ Aln = c1 ? P->A_lo[0] : P->A_lo[1];
-  const __nv_bfloat16* __restrict__ dtp = c1 ? P->dt[0] : P->dt[1];
-  __nv_bfloat16* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
+  const __half* __restrict__ dtp = c1 ? P->dt[0] : P->dt[1];
+  __half* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
   float* __restrict__ L = P->L;
-  const float lam = P->lam;
+  const float lam = ti.sc.lams;     // lambda 2^-sig 2^-scur (see GScale)
   const int r0 = 4 * lane;
   const int j0 = ti.m0 + r0;
   const float4 thj_h = ld4(P->th_hi + j0);
@@ -611,7 +733,7 @@ __device__ __forceinline__ void g_epilogue_columns(const GTileInfo& ti, GSmem* m
       in[u].L = ld4(L + idx);
       in[u].dtp = *reinterpret_cast<const uint2*>(dtp + idx);
       // as many slices as this product (the bound of next_slices)
-      const __nv_bfloat16* Drow = P->Dcat + (int64_t)i * P->cat_ld + j0;
+      const __half* Drow = P->Dcat + (int64_t)i * P->cat_ld + j0;
       in[u].D[0] = *reinterpret_cast<const uint2*>(Drow);
       in[u].D[1] = ti.S > 1 ? *reinterpret_cast<const uint2*>(Drow + ld) : make_uint2(0u, 0u);
       in[u].D[2] = ti.S > 2 ? *reinterpret_cast<const uint2*>(Drow + 2 * (int64_t)ld) : make_uint2(0u, 0u);
@@ -626,7 +748,7 @@ __device__ __forceinline__ void g_epilogue_columns(const GTileInfo& ti, GSmem* m
     const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
     const float thh = ms->thh[cl], thl = ms->thl[cl];
     float4 oh, ol, oL;
-    uint32_t ob[4];
+    uint32_t ob[4] = {0u, 0u, 0u, 0u};
     float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -638,16 +760,17 @@ __device__ __forceinline__ void g_epilogue_columns(const GTileInfo& ti, GSmem* m
         a2 += 1.f;
       } else if (j < n) {
         const float R = f4(in[u].L, e) +
-                        lam * (f4(x4, e) - ah * e_i - bf_at(in[u].dtp, e) * dp_i);
+                        lam * (f4(x4, e) - ah * e_i - h_at(in[u].dtp, e) * dp_i);
         float gh, gl;
         ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
-        dnew = bf16_round(R * __frcp_rn(gh));
+        // the remainder keeps R - Gap dt exactly: any reciprocal close to 1/gap serves
+        dnew = f16_scaled(R * rcp_approx(gh), ti.sc.qs, ti.sc.iqs, ob[e]);
         Ln = fmaf(-gh, dnew, R) - gl * dnew;
         ff_add_f(ah, al, dnew, nh, nl);
         r2 = fmaf(R, R, r2);
         a2 = fmaf(ah, ah, a2);
-        const float p1 = bf_at(in[u].D[0], e) * dnew;
-        const float p23 = fmaf(bf_at(in[u].D[1], e), dnew, bf_at(in[u].D[2], e) * dnew);
+        const float p1 = h_at(in[u].D[0], e) * dnew;
+        const float p23 = fmaf(h_at(in[u].D[1], e), dnew, h_at(in[u].D[2], e) * dnew);
         float sh, se;
         two_sum(eh, p1, sh, se);
         se += el + p23;
@@ -657,7 +780,6 @@ __device__ __forceinline__ void g_epilogue_columns(const GTileInfo& ti, GSmem* m
       f4set(oh, e, nh);
       f4set(ol, e, nl);
       f4set(oL, e, Ln);
-      ob[e] = bf_bits(dnew);
     }
     const int64_t idx = (int64_t)i * ld + j0;
     st4(Ahn + idx, oh);
@@ -665,6 +787,8 @@ __device__ __forceinline__ void g_epilogue_columns(const GTileInfo& ti, GSmem* m
     st4(L + idx, oL);
     *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
     warp_sum_ff(r2, a2, eh, el);
+    eh *= ti.sc.isig;
+    el *= ti.sc.isig;
     if (lane == 0) {
       const int ntm = P->ntm;
       P->part[((int64_t)0 * ntm + ti.tm) * ld + i] = r2;
@@ -686,10 +810,10 @@ __device__ __forceinline__ void gc_epilogue_columns(const GTileInfo& ti, GSmem* 
   const float* __restrict__ Alc = c1 ? P->A_lo[1] : P->A_lo[0];
   float* __restrict__ Ahn = c1 ? P->A_hi[0] : P->A_hi[1];
   float* __restrict__ Aln = c1 ? P->A_lo[0] : P->A_lo[1];
-  const __nv_bfloat16* __restrict__ dtp = c1 ? P->dt[0] : P->dt[1];
-  __nv_bfloat16* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
+  const __half* __restrict__ dtp = c1 ? P->dt[0] : P->dt[1];
+  __half* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
   float* __restrict__ L = P->L;
-  const float lam = P->lam;
+  const float lam = ti.sc.lams;     // lambda 2^-sig 2^-scur (see GScale)
   const int r0 = 4 * lane;
   const int jc0 = (ti.m0 + r0) / 2;
   float thj_h[2], thj_l[2];
@@ -711,7 +835,7 @@ __device__ __forceinline__ void gc_epilogue_columns(const GTileInfo& ti, GSmem* 
       in[u].al = ld4(Alc + idx);
       in[u].L = ld4(L + idx);
       in[u].dtp = *reinterpret_cast<const uint2*>(dtp + idx);
-      const __nv_bfloat16* Drow = P->Dcat + (int64_t)(2 * i) * P->cat_ld + 2 * jc0;
+      const __half* Drow = P->Dcat + (int64_t)(2 * i) * P->cat_ld + 2 * jc0;
       in[u].D[0] = *reinterpret_cast<const uint2*>(Drow);
       in[u].D[1] = ti.S > 1 ? *reinterpret_cast<const uint2*>(Drow + ld) : make_uint2(0u, 0u);
       in[u].D[2] = ti.S > 2 ? *reinterpret_cast<const uint2*>(Drow + 2 * (int64_t)ld) : make_uint2(0u, 0u);
@@ -728,7 +852,7 @@ __device__ __forceinline__ void gc_epilogue_columns(const GTileInfo& ti, GSmem* 
     const float dr = ms->dprev[2 * cl], di = ms->dprev[2 * cl + 1];
     const float thh = ms->thh[cl], thl = ms->thl[cl];
     float oh[4], ol[4], oL[4];
-    uint32_t ob[4];
+    uint32_t ob[4] = {0u, 0u, 0u, 0u};
     float r2 = 0.f, a2 = 0.f, erh = 0.f, erl = 0.f, eih = 0.f, eil = 0.f;
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -742,26 +866,26 @@ __device__ __forceinline__ void gc_epilogue_columns(const GTileInfo& ti, GSmem* 
       } else if (j < n) {
         float aer, aei, pdr, pdi;
         cmulf(ar, ai, er, ei, aer, aei);
-        cmulf(bf_at(in[u].dtp, 2 * e), bf_at(in[u].dtp, 2 * e + 1), dr, di, pdr, pdi);
+        cmulf(h_at(in[u].dtp, 2 * e), h_at(in[u].dtp, 2 * e + 1), dr, di, pdr, pdi);
         float R[2];
         R[0] = f4(in[u].L, 2 * e) + lam * (f4(x4, 2 * e) - aer - pdr);
         R[1] = f4(in[u].L, 2 * e + 1) + lam * (f4(x4, 2 * e + 1) - aei - pdi);
         float gh, gl;
         ff_sub(thh, thl, thj_h[e], thj_l[e], gh, gl);
-        const float g = __frcp_rn(gh);
+        const float g = rcp_approx(gh);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          dn[q] = bf16_round(R[q] * g);
+          dn[q] = f16_scaled(R[q] * g, ti.sc.qs, ti.sc.iqs, ob[2 * e + q]);
           Ln[q] = fmaf(-gh, dn[q], R[q]) - gl * dn[q];
           r2 = fmaf(R[q], R[q], r2);
         }
         ff_add_f(ar, alr, dn[0], nh[0], nl[0]);
         ff_add_f(ai, ali, dn[1], nh[1], nl[1]);
         a2 = fmaf(ar, ar, fmaf(ai, ai, a2));
-        const float a1 = bf_at(in[u].D[0], 2 * e), b1 = bf_at(in[u].D[0], 2 * e + 1);
+        const float a1 = h_at(in[u].D[0], 2 * e), b1 = h_at(in[u].D[0], 2 * e + 1);
         const float pr1 = fmaf(a1, dn[0], b1 * dn[1]), pi1 = fmaf(a1, dn[1], -b1 * dn[0]);
-        const float a2s = bf_at(in[u].D[1], 2 * e) + bf_at(in[u].D[2], 2 * e);
-        const float b2s = bf_at(in[u].D[1], 2 * e + 1) + bf_at(in[u].D[2], 2 * e + 1);
+        const float a2s = h_at(in[u].D[1], 2 * e) + h_at(in[u].D[2], 2 * e);
+        const float b2s = h_at(in[u].D[1], 2 * e + 1) + h_at(in[u].D[2], 2 * e + 1);
         const float pr2 = fmaf(a2s, dn[0], b2s * dn[1]), pi2 = fmaf(a2s, dn[1], -b2s * dn[0]);
         float sh, se;
         two_sum(erh, pr1, sh, se); se += erl + pr2; fast_two_sum(sh, se, erh, erl);
@@ -771,7 +895,6 @@ __device__ __forceinline__ void gc_epilogue_columns(const GTileInfo& ti, GSmem* 
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         oh[2 * e + q] = nh[q]; ol[2 * e + q] = nl[q]; oL[2 * e + q] = Ln[q];
-        ob[2 * e + q] = bf_bits(dn[q]);
       }
     }
     const int64_t idx = (int64_t)i * ld + ti.m0 + r0;
@@ -782,6 +905,7 @@ __device__ __forceinline__ void gc_epilogue_columns(const GTileInfo& ti, GSmem* 
     warp_sum_ff(r2, a2, erh, erl);
     float z0 = 0.f, z1 = 0.f;
     warp_sum_ff(z0, z1, eih, eil);
+    erh *= ti.sc.isig; erl *= ti.sc.isig; eih *= ti.sc.isig; eil *= ti.sc.isig;
     if (lane == 0) {
       const int ntm = P->ntm;
       P->part[((int64_t)0 * ntm + ti.tm) * ld + i] = r2;
@@ -876,7 +1000,7 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
       if (!mbar_wait(&ms->acc_empty[b], (use & 1) ^ 1, timeout)) break;
       tc_fence_after();
       const uint32_t dacc = tmem + (uint32_t)(b * G_BNMAX);
-      const uint32_t idesc = idesc_bf16_f32(G_BM, ti.bn);
+      const uint32_t idesc = idesc_f16_f32(G_BM, ti.bn);
       const int nk = ti.S * ti.kbs;
       for (int q = 0; q < nk; ++q, ++it) {
         const int s = it % G_STAGES;
@@ -887,7 +1011,7 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
         const uint64_t db = smem_desc_sw128(sB + s * G_B_TILE);
 #pragma unroll
         for (int kk = 0; kk < G_BK / G_UK; ++kk)
-          umma_bf16(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+          umma_f16(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
                     (q > 0 || kk > 0) ? 1u : 0u);
         umma_commit(&ms->empty[s]);
       }
@@ -926,8 +1050,8 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
           const int q = et + 256 * h;
           const int i = ti.n0 + (q >> 1);
           const bool v = (q < 2 * ti.bn) && (i < ti.P->n);
-          ms->e[q] = v ? ti.P->e_col[2 * ti.n0 + q] : 0.f;
-          ms->dprev[q] = v ? ti.P->dprev_col[2 * ti.n0 + q] : 0.f;
+          ms->e[q] = v ? (ti.P->e_col[2 * ti.n0 + q] * ti.sc.fsig) * ti.sc.fcur : 0.f;
+          ms->dprev[q] = v ? ti.P->dprev_col[2 * ti.n0 + q] * ti.sc.fsig : 0.f;
         }
         const int ic = ti.n0 + et;
         const bool vc = (et < ti.bn) && (ic < ti.P->n);
@@ -936,8 +1060,8 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
       } else {
         const int i = ti.n0 + et;
         const bool v = (et < ti.bn) && (i < ti.P->n);
-        ms->e[et] = v ? ti.P->e_col[i] : 0.f;
-        ms->dprev[et] = v ? ti.P->dprev_col[i] : 0.f;
+        ms->e[et] = v ? (ti.P->e_col[i] * ti.sc.fsig) * ti.sc.fcur : 0.f;
+        ms->dprev[et] = v ? ti.P->dprev_col[i] * ti.sc.fsig : 0.f;
         ms->thh[et] = v ? ti.P->th_hi[i] : 0.f;
         ms->thl[et] = v ? ti.P->th_lo[i] : 0.f;
       }
@@ -983,7 +1107,7 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
 // leader issues the MMA, and each CTA runs a 16-warp epilogue on its own rows with
 // the inputs staged in shared memory by per-lane cp.async one 16-column sub-chunk
 // ahead.  The arithmetic per element is that of g_/gc_epilogue_columns, with the
-// approximate reciprocal (the increment is rounded to BF16 and the remainder keeps
+// approximate reciprocal (the increment is rounded to FP16 and the remainder keeps
 // R - Gap dt exactly, so any reciprocal close to 1/gap serves).
 // ===========================================================================
 constexpr int GP_EPI_WARPS = 16;
@@ -1000,6 +1124,7 @@ struct GPairTile {
   const GProb* P;
   int tm2, tn, bn, n0, S, cur, kbs;
   bool live;
+  GScale sc;
 };
 
 __device__ __forceinline__ GPairTile gp_tile(const GProb* probs, const int2* tiles, int t) {
@@ -1015,6 +1140,7 @@ __device__ __forceinline__ GPairTile gp_tile(const GProb* probs, const int2* til
   ti.S = st->slices;
   ti.cur = st->cur;
   ti.kbs = ti.P->ld / G_BK;
+  ti.sc = g_scale(ti.P, st, ti.cur);
   return ti;
 }
 
@@ -1054,7 +1180,7 @@ __device__ __forceinline__ void gp_prefetch(const GPairTile& ti, uint8_t* eb, in
   cp_async16(gp_f4(eb, ew, 2, lane), P->L + idx);
   cp_async8(gp_u2(eb, ew, 0, lane), (c1 ? P->dt[0] : P->dt[1]) + idx);
   // Delta_ij, j = the lane's rows: row i of the slices (row 2i of the embedding)
-  const __nv_bfloat16* Drow = P->Dcat + (int64_t)(CPLX ? 2 * i : i) * P->cat_ld + m0 + 4 * lane;
+  const __half* Drow = P->Dcat + (int64_t)(CPLX ? 2 * i : i) * P->cat_ld + m0 + 4 * lane;
   for (int sl = 0; sl < ti.S; ++sl) cp_async8(gp_u2(eb, ew, 1 + sl, lane), Drow + (int64_t)sl * P->ld);
 }
 
@@ -1070,8 +1196,8 @@ __device__ __forceinline__ void gp_compute_real(const GPairTile& ti, GSmem* ms, 
   const bool c1 = (ti.cur != 0);
   float* __restrict__ Ahn = c1 ? P->A_hi[0] : P->A_hi[1];
   float* __restrict__ Aln = c1 ? P->A_lo[0] : P->A_lo[1];
-  __nv_bfloat16* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
-  const float lam = P->lam;
+  __half* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
+  const float lam = ti.sc.lams;     // lambda 2^-sig 2^-scur (see GScale)
   const int r0 = 4 * lane, j0 = m0 + r0;
   const float4 thj_h = ld4(P->th_hi + j0);
   const float4 thj_l = ld4(P->th_lo + j0);
@@ -1088,7 +1214,7 @@ __device__ __forceinline__ void gp_compute_real(const GPairTile& ti, GSmem* ms, 
   const float e_i = ms->e[cl], dp_i = ms->dprev[cl];
   const float thh = ms->thh[cl], thl = ms->thl[cl];
   float4 oh, ol, oL;
-  uint32_t ob[4];
+  uint32_t ob[4] = {0u, 0u, 0u, 0u};
   float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
@@ -1099,16 +1225,16 @@ __device__ __forceinline__ void gp_compute_real(const GPairTile& ti, GSmem* ms, 
       nh = 1.f;
       a2 += 1.f;
     } else if (j < n) {
-      const float R = f4(L4, e) + lam * (f4(x4, e) - ah * e_i - bf_at(dtp, e) * dp_i);
+      const float R = f4(L4, e) + lam * (f4(x4, e) - ah * e_i - h_at(dtp, e) * dp_i);
       float gh, gl;
       ff_sub(thh, thl, f4(thj_h, e), f4(thj_l, e), gh, gl);
-      dnew = bf16_round(R * rcp_approx(gh));
+      dnew = f16_scaled(R * rcp_approx(gh), ti.sc.qs, ti.sc.iqs, ob[e]);
       Ln = fmaf(-gh, dnew, R) - gl * dnew;
       ff_add_f(ah, al, dnew, nh, nl);
       r2 = fmaf(R, R, r2);
       a2 = fmaf(ah, ah, a2);
-      const float p1 = bf_at(D[0], e) * dnew;
-      const float p23 = fmaf(bf_at(D[1], e), dnew, bf_at(D[2], e) * dnew);
+      const float p1 = h_at(D[0], e) * dnew;
+      const float p23 = fmaf(h_at(D[1], e), dnew, h_at(D[2], e) * dnew);
       float sh, se;
       two_sum(eh, p1, sh, se);
       se += el + p23;
@@ -1118,7 +1244,6 @@ __device__ __forceinline__ void gp_compute_real(const GPairTile& ti, GSmem* ms, 
     f4set(oh, e, nh);
     f4set(ol, e, nl);
     f4set(oL, e, Ln);
-    ob[e] = bf_bits(dnew);
   }
   const int64_t idx = (int64_t)i * ld + j0;
   st4(Ahn + idx, oh);
@@ -1126,6 +1251,8 @@ __device__ __forceinline__ void gp_compute_real(const GPairTile& ti, GSmem* ms, 
   st4(P->L + idx, oL);
   *reinterpret_cast<uint2*>(dtn_out + idx) = make_uint2(ob[0] | (ob[1] << 16), ob[2] | (ob[3] << 16));
   warp_sum_ff(r2, a2, eh, el);
+  eh *= ti.sc.isig;
+  el *= ti.sc.isig;
   if (lane == 0) {
     const int ntm = P->ntm;
     P->part[((int64_t)0 * ntm + tm) * ld + i] = r2;
@@ -1147,8 +1274,8 @@ __device__ __forceinline__ void gp_compute_cplx(const GPairTile& ti, GSmem* ms, 
   const bool c1 = (ti.cur != 0);
   float* __restrict__ Ahn = c1 ? P->A_hi[0] : P->A_hi[1];
   float* __restrict__ Aln = c1 ? P->A_lo[0] : P->A_lo[1];
-  __nv_bfloat16* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
-  const float lam = P->lam;
+  __half* __restrict__ dtn_out = c1 ? P->dt[1] : P->dt[0];
+  const float lam = ti.sc.lams;     // lambda 2^-sig 2^-scur (see GScale)
   const int r0 = 4 * lane;
   const int jc0 = (m0 + r0) / 2;
   float thj_h[2], thj_l[2];
@@ -1172,7 +1299,7 @@ __device__ __forceinline__ void gp_compute_cplx(const GPairTile& ti, GSmem* ms, 
   const float dr = ms->dprev[2 * cl], di = ms->dprev[2 * cl + 1];
   const float thh = ms->thh[cl], thl = ms->thl[cl];
   float oh[4], ol[4], oL[4];
-  uint32_t ob[4];
+  uint32_t ob[4] = {0u, 0u, 0u, 0u};
   float r2 = 0.f, a2 = 0.f, erh = 0.f, erl = 0.f, eih = 0.f, eil = 0.f;
 #pragma unroll
   for (int e = 0; e < 2; ++e) {
@@ -1186,7 +1313,7 @@ __device__ __forceinline__ void gp_compute_cplx(const GPairTile& ti, GSmem* ms, 
     } else if (j < n) {
       float aer, aei, pdr, pdi;
       cmulf(ar, ai, er, ei, aer, aei);
-      cmulf(bf_at(dtp, 2 * e), bf_at(dtp, 2 * e + 1), dr, di, pdr, pdi);
+      cmulf(h_at(dtp, 2 * e), h_at(dtp, 2 * e + 1), dr, di, pdr, pdi);
       float R[2];
       R[0] = f4(L4, 2 * e) + lam * (f4(x4, 2 * e) - aer - pdr);
       R[1] = f4(L4, 2 * e + 1) + lam * (f4(x4, 2 * e + 1) - aei - pdi);
@@ -1195,17 +1322,17 @@ __device__ __forceinline__ void gp_compute_cplx(const GPairTile& ti, GSmem* ms, 
       const float g = rcp_approx(gh);
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
-        dn[q] = bf16_round(R[q] * g);
+        dn[q] = f16_scaled(R[q] * g, ti.sc.qs, ti.sc.iqs, ob[2 * e + q]);
         Ln[q] = fmaf(-gh, dn[q], R[q]) - gl * dn[q];
         r2 = fmaf(R[q], R[q], r2);
       }
       ff_add_f(ar, alr, dn[0], nh[0], nl[0]);
       ff_add_f(ai, ali, dn[1], nh[1], nl[1]);
       a2 = fmaf(ar, ar, fmaf(ai, ai, a2));
-      const float a1 = bf_at(D[0], 2 * e), b1 = bf_at(D[0], 2 * e + 1);
+      const float a1 = h_at(D[0], 2 * e), b1 = h_at(D[0], 2 * e + 1);
       const float pr1 = fmaf(a1, dn[0], b1 * dn[1]), pi1 = fmaf(a1, dn[1], -b1 * dn[0]);
-      const float a2s = bf_at(D[1], 2 * e) + bf_at(D[2], 2 * e);
-      const float b2s = bf_at(D[1], 2 * e + 1) + bf_at(D[2], 2 * e + 1);
+      const float a2s = h_at(D[1], 2 * e) + h_at(D[2], 2 * e);
+      const float b2s = h_at(D[1], 2 * e + 1) + h_at(D[2], 2 * e + 1);
       const float pr2 = fmaf(a2s, dn[0], b2s * dn[1]), pi2 = fmaf(a2s, dn[1], -b2s * dn[0]);
       float sh, se;
       two_sum(erh, pr1, sh, se); se += erl + pr2; fast_two_sum(sh, se, erh, erl);
@@ -1215,7 +1342,6 @@ __device__ __forceinline__ void gp_compute_cplx(const GPairTile& ti, GSmem* ms, 
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       oh[2 * e + q] = nh[q]; ol[2 * e + q] = nl[q]; oL[2 * e + q] = Ln[q];
-      ob[2 * e + q] = bf_bits(dn[q]);
     }
   }
   const int64_t idx = (int64_t)i * ld + m0 + r0;
@@ -1226,6 +1352,7 @@ __device__ __forceinline__ void gp_compute_cplx(const GPairTile& ti, GSmem* ms, 
   warp_sum_ff(r2, a2, erh, erl);
   float z0 = 0.f, z1 = 0.f;
   warp_sum_ff(z0, z1, eih, eil);
+  erh *= ti.sc.isig; erl *= ti.sc.isig; eih *= ti.sc.isig; eil *= ti.sc.isig;
   if (lane == 0) {
     const int ntm = P->ntm;
     P->part[((int64_t)0 * ntm + tm) * ld + i] = r2;
@@ -1339,7 +1466,7 @@ k_g_gemm_epi_x(const GProb* __restrict__ probs, const int2* __restrict__ tiles, 
       if (!mbar_wait(&ms->acc_empty[b], (use & 1) ^ 1, timeout)) break;
       tc_fence_after();
       const uint32_t dacc = tmem + (uint32_t)(b * G_BNMAX);
-      const uint32_t idesc = idesc_bf16_f32(Sh::rows, ti.bn);
+      const uint32_t idesc = idesc_f16_f32(Sh::rows, ti.bn);
       const int nk = ti.S * ti.kbs;
       for (int q = 0; q < nk; ++q, ++it) {
         const int s = it % Sh::stages;
@@ -1352,10 +1479,10 @@ k_g_gemm_epi_x(const GProb* __restrict__ probs, const int2* __restrict__ tiles, 
 #pragma unroll
         for (int kk = 0; kk < G_BK / G_UK; ++kk) {
           if constexpr (PAIR)
-            umma_bf16_pair(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+            umma_f16_pair(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
                            (q > 0 || kk > 0) ? 1u : 0u);
           else
-            umma_bf16(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
+            umma_f16(dacc, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc,
                       (q > 0 || kk > 0) ? 1u : 0u);
         }
         if constexpr (PAIR) umma_commit_pair(&ms->empty[s], (uint16_t)3);
@@ -1406,8 +1533,8 @@ k_g_gemm_epi_x(const GProb* __restrict__ probs, const int2* __restrict__ tiles, 
       if constexpr (CPLX) {
         const int i = ti.n0 + (et >> 1);
         const bool v = (et < 2 * ti.bn) && (i < ti.P->n);
-        ms->e[et] = v ? ti.P->e_col[2 * ti.n0 + et] : 0.f;
-        ms->dprev[et] = v ? ti.P->dprev_col[2 * ti.n0 + et] : 0.f;
+        ms->e[et] = v ? (ti.P->e_col[2 * ti.n0 + et] * ti.sc.fsig) * ti.sc.fcur : 0.f;
+        ms->dprev[et] = v ? ti.P->dprev_col[2 * ti.n0 + et] * ti.sc.fsig : 0.f;
         if (et < G_BNMAX) {
           const int ic = ti.n0 + et;
           const bool vc = (et < ti.bn) && (ic < ti.P->n);
@@ -1418,8 +1545,8 @@ k_g_gemm_epi_x(const GProb* __restrict__ probs, const int2* __restrict__ tiles, 
         if (et < G_BNMAX) {
           const int i = ti.n0 + et;
           const bool v = (et < ti.bn) && (i < ti.P->n);
-          ms->e[et] = v ? ti.P->e_col[i] : 0.f;
-          ms->dprev[et] = v ? ti.P->dprev_col[i] : 0.f;
+          ms->e[et] = v ? (ti.P->e_col[i] * ti.sc.fsig) * ti.sc.fcur : 0.f;
+          ms->dprev[et] = v ? ti.P->dprev_col[i] * ti.sc.fsig : 0.f;
           ms->thh[et] = v ? ti.P->th_hi[i] : 0.f;
           ms->thl[et] = v ? ti.P->th_lo[i] : 0.f;
         }
@@ -1633,6 +1760,14 @@ cudaError_t launch_g_check_theta(const GProb* probs, int count, int max_n, int* 
     k_g_check_theta<<<dim3(count, (max_n + 127) / 128), 128, 0, s>>>(probs, count, running);
   return cudaGetLastError();
 }
+cudaError_t launch_g_scales(const GProb* probs, const int4* items, int nitems, bool cplx,
+                            cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  if (cplx) k_g_scales<true><<<nitems, 128, 0, s>>>(probs, items);
+  else k_g_scales<false><<<nitems, 128, 0, s>>>(probs, items);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_g_prep(const GProb* probs, const int4* items, int nitems, cudaStream_t s) {
   if (nitems) k_g_prep<<<nitems, dim3(32, 8), 0, s>>>(probs, items);
   return cudaGetLastError();

@@ -59,11 +59,10 @@ size_t measure(F&& f) {
   return (size_t)round_up((int64_t)c.off, 256) + 256;
 }
 
-// 2-D tensor map of 16-bit elements (BF16, or FP16 when f16): inner extent `inner`
-// (contiguous), outer extent `outer`, row pitch `pitch_elems`, box 64 x box_rows,
-// 128-byte swizzle.  Throws Fail.
-CUtensorMap make_tmap_bf16(const void* base, uint64_t inner, uint64_t outer,
-                           uint64_t pitch_elems, uint32_t box_rows, bool f16 = false);
+// 2-D tensor map of FP16 elements: inner extent `inner` (contiguous), outer extent
+// `outer`, row pitch `pitch_elems`, box 64 x box_rows, 128-byte swizzle.  Throws Fail.
+CUtensorMap make_tmap_f16(const void* base, uint64_t inner, uint64_t outer,
+                          uint64_t pitch_elems, uint32_t box_rows);
 
 // dpt_status of a device-side ST_* code.
 dpt_status from_state(int s);

@@ -2,7 +2,6 @@
 #pragma once
 
 #include <cuda.h>
-#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -32,7 +31,7 @@ enum : int {
 struct IterState {
   int k;               // index of the current iterate A_k
   int status;          // ST_*
-  int slices;          // BF16 slices of Delta used by the next product
+  int slices;          // FP16 slices of Delta used by the next product
   int cur;             // ping-pong index of the buffers holding A_k
   int grown;           // consecutive iterations with residual > 10 x best
   int max_iter;
@@ -126,7 +125,7 @@ struct DomState {
 // One problem of a grouped (batched / served) solve: a device-resident table entry
 // with the problem's size, tile shape, work arrays, state and TMA descriptors.
 struct alignas(128) GProb {
-  CUtensorMap tmA;          // Delta slices (row-major BF16, 3 slices side by side)
+  CUtensorMap tmA;          // Delta slices (row-major scaled FP16, 3 slice places side by side)
   CUtensorMap tmB[2];       // increment buffers dt[0], dt[1]
   // n: problem size; nr: rows of the real product (n, or 2n for a complex problem,
   // whose rows and K index interleave real and imaginary parts); ld: row pitch of
@@ -136,9 +135,9 @@ struct alignas(128) GProb {
   double lam64;
   float* A_hi[2];
   float* A_lo[2];
-  __nv_bfloat16* dt[2];
+  __half* dt[2];            // increments, FP16 scaled by 2^sexp[buffer] of the state
   float* L;
-  __nv_bfloat16* Dcat;
+  __half* Dcat;             // FP16 slices of Delta 2^sig (the state's sig)
   int64_t cat_ld;
   float* th_hi;
   float* th_lo;
@@ -161,6 +160,9 @@ cudaError_t g_set_attributes();
 // max_n: the largest problem size among the first `count` table entries
 cudaError_t launch_g_check_theta(const GProb* probs, int count, int max_n, int* running,
                                  cudaStream_t s);
+// the FP16 scales of every problem (items: the iteration-0 tiles of one kind)
+cudaError_t launch_g_scales(const GProb* probs, const int4* items, int nitems, bool cplx,
+                            cudaStream_t s);
 cudaError_t launch_g_prep(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
 cudaError_t launch_g_iter0(const GProb* probs, const int4* items, int nitems, cudaStream_t s);
 cudaError_t launch_g_ctrl(const GProb* probs, int count, int max_n, bool cplx, int* running,

@@ -182,9 +182,9 @@ void admit(dpt_server* S, Request* r) {
   plan_group(g, 1, r->cplx, &n, &th, &dl, &ldd, &lam, &A, &lda, &E, plan_base,
              S->states_dev + r->slot, S->form);
   GProb& P = g.probs[0];
-  P.tmA = make_tmap_bf16(P.Dcat, (uint64_t)3 * P.ld, P.nr, (uint64_t)3 * P.ld, 128);
+  P.tmA = make_tmap_f16(P.Dcat, (uint64_t)3 * P.ld, P.nr, (uint64_t)3 * P.ld, 128);
   for (int q = 0; q < 2; ++q)
-    P.tmB[q] = make_tmap_bf16(P.dt[q], P.nr, P.n, P.ld, gform_box(S->form, P.bn));
+    P.tmB[q] = make_tmap_f16(P.dt[q], P.nr, P.n, P.ld, gform_box(S->form, P.bn));
   r->P = P;
   r->tiles = (int)g.tiles.size();
   const std::vector<int4>& prep = r->cplx ? g.prep_c : g.prep_r;
@@ -200,8 +200,9 @@ void admit(dpt_server* S, Request* r) {
   h = IterState{};
   h.status = ST_RUNNING;
   h.max_iter = r->p.max_iter > 0 ? r->p.max_iter : o.max_iter;
+  // up to three FP16 slices of Delta 2^sig (see dpt_grouped.cu)
   h.max_slices = o.max_slices;
-  h.slices = o.max_slices;
+  h.slices = h.max_slices;
   h.lam = lam;
   h.tol = r->p.tol > 0 ? r->p.tol : o.tol;
   h.slice_tol = o.slice_tol;
@@ -216,6 +217,7 @@ void admit(dpt_server* S, Request* r) {
   if (r->nblk) CK(cudaMemcpyAsync(r->blk, r->items_h.data() + nprep, sizeof(int4) * r->nblk,
                                   cudaMemcpyHostToDevice, S->s));
   CK(launch_g_check_theta(Pd, 1, (int)n, S->flags_dev, S->s));
+  CK(launch_g_scales(Pd, r->blk, r->nblk, r->cplx != 0, S->s));
   if (r->cplx) {
     CK(launch_gc_prep(Pd, prep_dev, nprep, S->s));
     CK(launch_gc_iter0(Pd, r->blk, r->nblk, S->s));

@@ -45,11 +45,11 @@ def test_batched_matches_single_solves(dpt):
     probs = inputs.batched_symmetric(count=24, rep=3)
     th, D = _dev(probs, dpt)
     As, Es, infos = dpt.solve_batched(th, D, [p["lam"] for p in probs])
-    # the grouped kernel picks its own tile width per problem and takes BF16 slices
-    # where the single-problem kernel takes FP16 ones, so the rounding differs: the
-    # agreement is to the parity bar, not bit for bit, and the iteration counts of the
-    # mixed recursions (a strongly coupled single solve may add plain FP64 steps)
-    # agree to one step
+    # the grouped kernel picks its own tile width per problem (and with it the order of
+    # its FP32 accumulation) and its own reciprocals, so the rounding differs from the
+    # single-problem kernel's: the agreement is to the parity bar, not bit for bit, and
+    # the iteration counts of the mixed recursions (a strongly coupled single solve may
+    # add plain FP64 steps) agree to one step
     for q in (0, 7, 23):
         A1, E1, i1 = dpt.solve_full(th[q], D[q], probs[q]["lam"])
         assert abs((i1["iters"] - i1["fp64_iters"]) - infos[q]["iters"]) <= 1

@@ -1,5 +1,5 @@
-"""The FP16 operands of the single mixed solve and the FP64 finish of strongly coupled
-solves (through the C ABI).
+"""The FP16 operands of the mixed solves (single and grouped) and the FP64 finish of
+strongly coupled single solves (through the C ABI).
 
 Delta enters the tensor cores as FP16 slices of Delta 2^sig and each increment as
 FP16 with its own power-of-two scale.  Replacing (Delta, lambda) by
@@ -38,6 +38,38 @@ def test_power_of_two_rescaling_is_exact(dpt, p, pair):
     assert i0["status"] == "OK" and i1["status"] == "OK"
     assert i1["iters"] == i0["iters"] and i1["slice_gemms"] == i0["slice_gemms"]
     assert torch.equal(A0, A1) and torch.equal(E0, E1)
+
+
+@pytest.mark.parametrize("p", [-40, 30])
+@pytest.mark.parametrize("form", [1, 2, 3])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_grouped_power_of_two_rescaling_is_exact(dpt, p, form, cplx):
+    """The grouped solves (batched, served, complex) carry each problem's own FP16
+    scales (sig from its Delta, the increments' from its iteration): rescaling one
+    problem of a group leaves its result, and every other problem's, bit for bit."""
+    rng = np.random.Generator(np.random.PCG64(77 + form))
+    sizes = [40, 130, 257]
+    ths, Ds, Dss, lams = [], [], [], []
+    for q, n in enumerate(sizes):
+        th = np.arange(n, dtype=np.float64) + rng.uniform(-0.2, 0.2, n)
+        D = rng.standard_normal((n, n)) / np.sqrt(n)
+        if cplx:
+            D = (D + 1j * rng.standard_normal((n, n)) / np.sqrt(n)) / np.sqrt(2)
+            D = (D + D.conj().T) / 2
+        else:
+            D = (D + D.T) / 2
+        ths.append(torch.tensor(th, device="cuda"))
+        Ds.append(dpt.colmajor_tensor(D, "cuda"))
+        Dss.append(dpt.colmajor_tensor(D * 2.0 ** p if q == 1 else D, "cuda"))
+        lams.append(0.05)
+    lams_s = [lams[0], np.ldexp(lams[1], -p), lams[2]]
+    A0, E0, i0 = dpt.solve_batched(ths, Ds, lams, form=form)
+    A1, E1, i1 = dpt.solve_batched(ths, Dss, lams_s, form=form)
+    for q in range(len(sizes)):
+        assert i0[q]["status"] == "OK" and i1[q]["status"] == "OK", (q, i0[q], i1[q])
+        assert i1[q]["iters"] == i0[q]["iters"]
+        assert i1[q]["slice_gemms"] == i0[q]["slice_gemms"]
+        assert torch.equal(A0[q], A1[q]) and torch.equal(E0[q], E1[q]), q
 
 
 def test_weakly_coupled_solve_needs_no_fp64_finish(ora, dpt):

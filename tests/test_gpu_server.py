@@ -101,8 +101,8 @@ def test_host_buffers(ora, dpt):
 def test_admission_against_a_small_budget(dpt):
     probs = [_problem(600, 8300 + q, 1, 0.05) for q in range(6)]
     # one complex n = 600 problem holds about 28 MB on the device (float-float A
-    # and its ping-pong, the remainder, two BF16 increments, three BF16 slices of
-    # the 1200 x 1200 real embedding), so 70 MB admits two at a time
+    # and its ping-pong, the remainder, two FP16 increments, three FP16 slice places
+    # of the 1200 x 1200 real embedding), so 70 MB admits two at a time
     budget = 70 << 20
     with dpt.Server(hbm_budget=budget, max_active=8) as srv:
         ids = [srv.submit(*_dev(p, dpt), p[2]) for p in probs]
