@@ -685,16 +685,22 @@ __device__ __forceinline__ void dom_ramp_advance(SP* vs) {
 // later products take the fewest slices that stay below it.  The carried remainder
 // makes the fixed point that of the full Delta either way.
 // ---------------------------------------------------------------------------
-// The same rule for FP16 slices (11 significant bits each, so about 2^(-11 S)
-// relative) of a solve whose first product used nsl of them: S slices once
-// dmax <= 2^(-11 (nsl - S)) dmax1, one below slice_tol.
+// The rule for FP16 slices (11 significant bits each, so about 2^(-11 S) relative) of
+// a solve whose first product used nsl of them: the accepted truncation is that of the
+// first product, 2^(-11 nsl) dmax1, but no finer than the FP32 accumulation's own
+// 2^-24 dmax1 (three slices would otherwise keep 33 bits long after the accumulator
+// has stopped resolving them); a later product takes the fewest slices S with
+// 2^(-11 S) dmax within it, and one below slice_tol.  With nsl = 2 this drops to one
+// slice once dmax <= 2^-11 dmax1; with nsl = 3 to two once dmax <= dmax1 / 4 and to
+// one once dmax <= 2^-13 dmax1.
 template <class SP>
 __device__ __forceinline__ int next_slices_f16(SP* vs, float dmax, bool first, int nsl) {
   if (first) vs->dmax1 = dmax;
   const float d1 = vs->dmax1;
   if ((double)dmax < vs->slice_tol) return 1;
+  const int b = min(11 * nsl, 24);
   int S = nsl;
-  while (S > 1 && dmax <= d1 * exp2i(-11 * (nsl - S + 1))) --S;
+  while (S > 1 && dmax <= d1 * exp2i(11 * (S - 1) - b)) --S;
   return S;
 }
 
