@@ -106,10 +106,21 @@ __global__ void __launch_bounds__(128) k_g_check_theta(const GProb* __restrict__
 // bits; the second slice takes what the first drops), and the first increment's scale
 // sexp[0] places its bound |lambda| max |Delta_ji| / |theta_i - theta_j| at 2^13 (as
 // the single solve's k_delta_scales).  Work item: a 128 x 128 tile of iteration 0
-// (for a complex problem 128 columns by 64 complex rows); thread r owns a row.  The
-// maxima reach the state by atomicMax on non-negative float / double-high-word bits;
-// the problem's last item sets the scales.
+// (for a complex problem 128 columns by 64 complex rows); a thread owns a row (a
+// complex row: two threads, half of the columns each).  Only integer and float
+// operations per entry: magnitudes from the doubles' high words, gaps from theta in
+// float-float.  The maxima reach the state by atomicMax on non-negative float /
+// double-high-word bits; the problem's last item sets the scales.
 // ---------------------------------------------------------------------------
+// |v| from the high word of a double (sign cleared): exact to 20 fraction bits as a
+// float, 0 below the float range, +inf above it (the slicing rejects those inputs).
+// Integer operations only: the FP64 pipe is the GB300's slowest.
+__device__ __forceinline__ float abs_hi_float(unsigned hw) {
+  const unsigned e = hw >> 20;
+  return (e > 896u && e < 1151u) ? __uint_as_float(((e - 896u) << 23) | ((hw & 0xFFFFFu) << 3))
+                                 : (e >= 1151u ? __int_as_float(0x7f800000) : 0.f);
+}
+
 template <bool CPLX>
 __global__ void __launch_bounds__(128) k_g_scales(const GProb* __restrict__ probs,
                                                   const int4* __restrict__ items) {
@@ -119,24 +130,57 @@ __global__ void __launch_bounds__(128) k_g_scales(const GProb* __restrict__ prob
   IterState* st = P->st;
   const int n = P->n;
   const int i0 = it.y * 128, i1 = min(n, i0 + 128);
-  const int j = (CPLX ? it.z * 64 : it.z * 128) + (int)threadIdx.x;
+  // theta of the tile's columns as float-float (the gaps of near-degenerate levels
+  // survive in the low part)
+  __shared__ float thh[128], thl[128];
+  {
+    const int i = i0 + (int)threadIdx.x;
+    float h = 0.f, l = 0.f;
+    if (i < n) split_double(P->theta[i], h, l);
+    thh[threadIdx.x] = h;
+    thl[threadIdx.x] = l;
+  }
+  __syncthreads();
+  // a real tile's 128 rows: one per thread; a complex tile's 64 complex rows: two
+  // threads per row, each taking half of the columns
+  const int r = CPLX ? (int)(threadIdx.x & 63) : (int)threadIdx.x;
+  const int j = (CPLX ? it.z * 64 : it.z * 128) + r;
+  const int ia = CPLX ? i0 + 64 * (int)(threadIdx.x >> 6) : i0;
+  const int ib_end = CPLX ? min(i1, ia + 64) : i1;
   unsigned hmax = 0u;
   float gmax = 0.f;
-  if (j < n && (!CPLX || threadIdx.x < 64)) {
-    const double tj = P->theta[j];
-    for (int i = i0; i < i1; ++i) {
-      double vmax;
-      if (CPLX) {
-        const double2 v = reinterpret_cast<const double2*>(P->delta_in)[(int64_t)i * P->ld_in + j];
-        vmax = fmax(fabs(v.x), fabs(v.y));
-      } else {
-        vmax = fabs(P->delta_in[(int64_t)i * P->ld_in + j]);
+  if (j < n) {
+    float tjh, tjl;
+    split_double(P->theta[j], tjh, tjl);
+    // eight columns' loads in flight per thread (a small problem's pass is one block
+    // whose time is its load latencies)
+    for (int ib = ia; ib < ib_end; ib += 8) {
+      unsigned hw[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = ib + u;
+        hw[u] = 0u;
+        if (i < ib_end) {
+          if (CPLX) {
+            const double2 v =
+                reinterpret_cast<const double2*>(P->delta_in)[(int64_t)i * P->ld_in + j];
+            hw[u] = max((unsigned)__double2hiint(v.x) & 0x7FFFFFFFu,
+                        (unsigned)__double2hiint(v.y) & 0x7FFFFFFFu);
+          } else {
+            hw[u] = (unsigned)__double2hiint(P->delta_in[(int64_t)i * P->ld_in + j]) & 0x7FFFFFFFu;
+          }
+        }
       }
-      hmax = max(hmax, (unsigned)__double2hiint(vmax) & 0x7FFFFFFFu);
-      if (i != j) {
-        // NaN never wins fmaxf (the slicing rejects non-finite entries)
-        const float g = fabsf((float)(P->theta[i] - tj));
-        gmax = fmaxf(gmax, (float)vmax / g);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = ib + u;
+        hmax = max(hmax, hw[u]);
+        if (i < ib_end && i != j) {
+          float g = thh[i - i0] - tjh;
+          if (g == 0.f) g = thl[i - i0] - tjl;
+          // NaN never wins fmaxf
+          gmax = fmaxf(gmax, abs_hi_float(hw[u]) * rcp_approx(fabsf(g)));
+        }
       }
     }
   }
@@ -684,7 +728,10 @@ struct GTileInfo {
   GScale sc;
 };
 
-__device__ __forceinline__ GTileInfo g_tile(const GProb* probs, const int2* tiles, int t) {
+// with_scale: the epilogue's copy, which needs the problem's scales (the producer and
+// the MMA issuer skip their loads)
+__device__ __forceinline__ GTileInfo g_tile(const GProb* probs, const int2* tiles, int t,
+                                            bool with_scale = false) {
   GTileInfo ti;
   const int2 e = tiles[t];
   ti.P = probs + e.x;
@@ -698,7 +745,7 @@ __device__ __forceinline__ GTileInfo g_tile(const GProb* probs, const int2* tile
   ti.S = st->slices;
   ti.cur = st->cur;
   ti.kbs = ti.P->ld / G_BK;
-  ti.sc = g_scale(ti.P, st, ti.cur);
+  if (with_scale) ti.sc = g_scale(ti.P, st, ti.cur);
   return ti;
 }
 
@@ -1027,7 +1074,7 @@ k_g_gemm_epi(const GProb* __restrict__ probs, const int2* __restrict__ tiles, in
     const GProb* mxP = nullptr;
     int lt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const GTileInfo ti = g_tile(probs, tiles, t);
+      const GTileInfo ti = g_tile(probs, tiles, t, true);
       if (!ti.live) continue;
       const int b = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
@@ -1127,7 +1174,8 @@ struct GPairTile {
   GScale sc;
 };
 
-__device__ __forceinline__ GPairTile gp_tile(const GProb* probs, const int2* tiles, int t) {
+__device__ __forceinline__ GPairTile gp_tile(const GProb* probs, const int2* tiles, int t,
+                                             bool with_scale = false) {
   GPairTile ti;
   const int2 e = tiles[t];
   ti.P = probs + e.x;
@@ -1140,7 +1188,7 @@ __device__ __forceinline__ GPairTile gp_tile(const GProb* probs, const int2* til
   ti.S = st->slices;
   ti.cur = st->cur;
   ti.kbs = ti.P->ld / G_BK;
-  ti.sc = g_scale(ti.P, st, ti.cur);
+  if (with_scale) ti.sc = g_scale(ti.P, st, ti.cur);
   return ti;
 }
 
@@ -1506,7 +1554,7 @@ k_g_gemm_epi_x(const GProb* __restrict__ probs, const int2* __restrict__ tiles, 
     int lt = 0;
     int pref_t = -1;      // tile whose first sub-chunk is in flight
     for (int t = pair; t < ntiles; t += npairs) {
-      const GPairTile ti = gp_tile(probs, tiles, t);
+      const GPairTile ti = gp_tile(probs, tiles, t, true);
       if (!ti.live) continue;
       const int b = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
