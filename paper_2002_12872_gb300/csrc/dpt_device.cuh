@@ -98,6 +98,13 @@ __device__ __forceinline__ void split_double_fast(double v, float& hi, float& lo
   lo = (e >= 920u) ? l : 0.f;
 }
 
+// Finite doubles are equal exactly when their bit patterns are, once -0 is read as +0:
+// the comparisons run as 64-bit integer compares (the FP64 pipe of GB300 is slow).
+__device__ __forceinline__ unsigned long long eq_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return b == 0x8000000000000000ull ? 0ull : b;
+}
+
 // True for values split_double_fast cannot represent: |v| >= 2^128, inf and NaN.
 __device__ __forceinline__ bool beyond_float(double v) {
   return (((unsigned)__double2hiint(v) >> 20) & 0x7FFu) >= 1151u;

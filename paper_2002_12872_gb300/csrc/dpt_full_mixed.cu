@@ -1508,12 +1508,7 @@ __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __
 // atomicMax on the bits of a non-negative double.  Grid (256-blocks of i, 256-blocks
 // of j), upper triangle only: each block stages its 256 theta_j in shared memory and
 // thread i compares theta_i with those j > i.
-// Finite doubles are equal exactly when their bit patterns are, once -0 is read as +0:
-// the comparisons run as 64-bit integer compares (the FP64 pipe of GB300 is slow).
-__device__ __forceinline__ unsigned long long eq_key(double v) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-  return b == 0x8000000000000000ull ? 0ull : b;
-}
+// (eq_key: 64-bit integer equality keys of finite doubles, dpt_device.cuh)
 
 __global__ void __launch_bounds__(256) k_check_theta(int n, const double* __restrict__ th,
                                                      IterState* st) {

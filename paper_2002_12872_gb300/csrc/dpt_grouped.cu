@@ -74,26 +74,43 @@ __device__ __forceinline__ void g_fail(const GProb* P, int code, int* running) {
 }
 
 // Grid (problems, chunks of 128 indices i); thread i compares theta_i with every
-// theta_j, j > i, and the chunk's max |theta| goes to the state by atomicMax on
-// the bits of a non-negative double (which order like the values).
+// theta_j, j > i, chunk by chunk: the block stages each chunk of 128 equality keys of
+// theta_j in shared memory, so the comparisons are 64-bit integer compares against
+// broadcast reads (the FP64 pipe of GB300 is slow; equal finite doubles have equal
+// keys, eq_key).  The chunk's max |theta| goes to the state by atomicMax on the bits of
+// a non-negative double (which order like the values).
 __global__ void __launch_bounds__(128) k_g_check_theta(const GProb* __restrict__ probs,
                                                        int count, int* running) {
   const int p = blockIdx.x;
   if (p >= count) return;
   const GProb* P = probs + p;
   const int n = P->n;
-  const int i = blockIdx.y * 128 + threadIdx.x;
-  if (blockIdx.y * 128 >= n) return;
+  const int c0 = blockIdx.y * 128;
+  if (c0 >= n) return;
+  const int i = c0 + threadIdx.x;
   const double* __restrict__ th = P->theta;
+  __shared__ unsigned long long tk[128];
   double amax = 0.0;
+  bool fin = false;
+  unsigned long long ki = 0ull;
   if (i < n) {
     const double ti = th[i];
-    if (!finite_bits(ti)) g_fail(P, ST_BADINPUT, running);
-    else amax = fabs(ti);
-    bool dup = false;
-    for (int j = i + 1; j < n; ++j) dup |= (th[j] == ti);
-    if (dup) g_fail(P, ST_DEGENERATE, running);
+    fin = finite_bits(ti);
+    if (!fin) g_fail(P, ST_BADINPUT, running);
+    else { amax = fabs(ti); ki = eq_key(ti); }
   }
+  bool dup = false;
+  for (int j0 = c0; j0 < n; j0 += 128) {
+    __syncthreads();
+    // entries past n hold a pattern no finite value has
+    tk[threadIdx.x] = (j0 + (int)threadIdx.x < n) ? eq_key(th[j0 + threadIdx.x]) : ~0ull;
+    __syncthreads();
+    // the diagonal chunk: only j > i; later chunks: all 128
+    const int q0 = (j0 == c0) ? (int)threadIdx.x + 1 : 0;
+#pragma unroll 8
+    for (int q = 0; q < 128; ++q) dup |= (q >= q0) & (tk[q] == ki);
+  }
+  if (fin && dup) g_fail(P, ST_DEGENERATE, running);
   for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   if ((threadIdx.x & 31) == 0 && amax > 0.0)
     atomicMax(reinterpret_cast<unsigned long long*>(&P->st->theta_max),
