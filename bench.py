@@ -232,7 +232,7 @@ def run_reference(args, world, rank):
             "ms_per_step": 1e3 * wall / args.steps,
             "ms_per_solve_equivalent": 1e3 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": N},
+            "config": {"workload": WORKLOAD, "n": N, "lambda": cfg["lam"], "tol": 1e-12},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores,
                              "kind": "oracle",
                              "sample": f"{ncols} of {N} columns per step, scaled by n/{ncols}"},
