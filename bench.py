@@ -972,8 +972,11 @@ def run_ours(args, world, rank, local):
     outs = [(A, E)] + [(torch.empty((N, N), dtype=torch.float64, device=dev).t(),
                         torch.empty((N,), dtype=torch.float64, device=dev))
                        for _ in range(STREAMS - 1)]
-    solvers = [prepared] + [dpt.FullSolve(th, D, cfg["lam"], prec="mixed", tol=1e-12,
-                                          A_out=outs[k][0], E_out=outs[k][1],
+    # each stream its own copy of the inputs (no stream reads lines another just loaded)
+    ins = [(th, D)] + [(th.clone(), dpt.colmajor_tensor(cfg["delta"], dev))
+                       for _ in range(STREAMS - 1)]
+    solvers = [prepared] + [dpt.FullSolve(ins[k][0], ins[k][1], cfg["lam"], prec="mixed",
+                                          tol=1e-12, A_out=outs[k][0], E_out=outs[k][1],
                                           stream=sts[k].cuda_stream)
                             for k in range(1, STREAMS)]
     for f in solvers[1:]:
