@@ -40,6 +40,9 @@ PROFILE = os.path.join(ROOT, "profiles", "k_gemm_epi_pair_n4096.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2002_12872_gb300", "csrc", "dpt_full_mixed.cu")
 
 
+STREAMS = 2   # default: independent solve streams per GPU in the timed throughput region
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -58,6 +61,9 @@ def parse_args():
                     help="time one secondary workload alone and print its JSON object")
     ap.add_argument("--dense-n", type=int, default=32768,
                     help="dominant_dense: problem size")
+    ap.add_argument("--streams", type=int, default=STREAMS,
+                    help="independent solve streams (one host thread each) in the timed "
+                         "throughput region of the headline solve")
     ap.add_argument("--pool-max-n", type=int, default=None,
                     help="served_pool: keep pool entries with n up to this size")
     return ap.parse_args()
@@ -881,7 +887,6 @@ def bench_served(dpt, inputs, dev, rates=(250, 500, 1000, 2000), window_s=1.0, p
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-STREAMS = 2   # independent solve streams per GPU in the timed throughput region
 
 
 def run_streams(calls, streams, nsolves):
@@ -907,11 +912,14 @@ def run_streams(calls, streams, nsolves):
     t0.record(streams[0])
     for st in streams[1:]:
         st.wait_event(t0)
-    threads = [threading.Thread(target=worker, args=(k,)) for k in range(ns)]
-    for t in threads:
-        t.start()
-    for t in threads:
-        t.join()
+    if ns == 1:
+        worker(0)   # one stream: on this thread
+    else:
+        threads = [threading.Thread(target=worker, args=(k,)) for k in range(ns)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
     if errors:
         raise errors[0]
     for st in streams[1:]:
@@ -965,20 +973,23 @@ def run_ours(args, world, rank, local):
                   "unit": "solves/s", "solves": nlat,
                   "l2": "flushed before each solve (256 MB write, untimed)"}
 
-    # throughput, the timed region: K solves over STREAMS independent solve streams;
+    # throughput, the timed region: K solves over the independent solve streams (--streams);
     # a solve's working set (Delta 134 MB, about 0.5 GB of iterate state) exceeds L2,
     # so nothing is flushed between solves
-    sts = [stream] + [torch.cuda.Stream(dev) for _ in range(STREAMS - 1)]
+    nstr = args.streams
+    if nstr < 1:
+        raise ValueError("--streams must be at least 1")
+    sts = [stream] + [torch.cuda.Stream(dev) for _ in range(nstr - 1)]
     outs = [(A, E)] + [(torch.empty((N, N), dtype=torch.float64, device=dev).t(),
                         torch.empty((N,), dtype=torch.float64, device=dev))
-                       for _ in range(STREAMS - 1)]
+                       for _ in range(nstr - 1)]
     # each stream its own copy of the inputs (no stream reads lines another just loaded)
     ins = [(th, D)] + [(th.clone(), dpt.colmajor_tensor(cfg["delta"], dev))
-                       for _ in range(STREAMS - 1)]
+                       for _ in range(nstr - 1)]
     solvers = [prepared] + [dpt.FullSolve(ins[k][0], ins[k][1], cfg["lam"], prec="mixed",
                                           tol=1e-12, A_out=outs[k][0], E_out=outs[k][1],
                                           stream=sts[k].cuda_stream)
-                            for k in range(1, STREAMS)]
+                            for k in range(1, nstr)]
     for f in solvers[1:]:
         for _ in range(max(3, args.warmup)):
             f.solve()
@@ -1057,10 +1068,10 @@ def run_ours(args, world, rank, local):
     e2e_steps = max(4, min(args.steps, 20))
     outs_h = [(A_h, E_h)] + [(torch.empty((N, N), dtype=torch.float64).pin_memory().t(),
                               torch.empty((N,), dtype=torch.float64).pin_memory())
-                             for _ in range(STREAMS - 1)]
+                             for _ in range(nstr - 1)]
     e2e_calls = [lambda k=k: dpt.solve_full(th_h, D_h, cfg["lam"], A_out=outs_h[k][0],
                                             E_out=outs_h[k][1], stream=sts[k].cuda_stream)
-                 for k in range(STREAMS)]
+                 for k in range(nstr)]
     for c in e2e_calls:
         c()
     barrier(world)
@@ -1070,7 +1081,7 @@ def run_ours(args, world, rank, local):
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e = {"value": job_throughput(e2e_steps, world, e2e_s), "unit": "solves/s",
            "h2d_bytes_per_step": 8 * N + 8 * N * N, "d2h_bytes_per_step": 8 * N * N + 8 * N,
-           "streams": STREAMS}
+           "streams": nstr}
 
     # plain FP64 comparator (same problem, same tolerance)
     fp64 = None
@@ -1117,7 +1128,7 @@ def run_ours(args, world, rank, local):
                            "scales, FP32 accumulate, float-float state)",
                    "l2": "inputs larger than L2: a solve's working set (Delta 134 MB, about "
                          "0.5 GB of iterate state) exceeds the 129 MB L2; no flush",
-                   "parallelism": f"{STREAMS} independent solve streams per GPU (one host "
+                   "parallelism": f"{nstr} independent solve stream(s) per GPU (one host "
                                   f"thread each), {world} GPU(s)"},
         "one_stream": one_stream,
         "streams_results_equal": bool(same),

@@ -129,6 +129,25 @@ CUtensorMap make_tmap_f16(const void* base, uint64_t inner, uint64_t outer,
   return m;
 }
 
+// 2-D FP64 tensor map of a column-major matrix: `inner` rows (contiguous), `outer`
+// columns, column pitch `pitch_elems` (even: a multiple of 16 bytes), 16 x 16 boxes,
+// 128-byte swizzle (one box line = 16 doubles), zero fill beyond the extents.
+CUtensorMap make_tmap_f64(const void* base, uint64_t inner, uint64_t outer,
+                          uint64_t pitch_elems) {
+  CUtensorMap m;
+  auto fn = encode_fn();
+  if (!fn) throw Fail{DPT_ERR_CUDA};
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {pitch_elems * 8};
+  cuuint32_t box[2] = {16, 16};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Fail{DPT_ERR_CUDA};
+  return m;
+}
+
 dpt_status from_state(int s) {
   switch (s) {
     case ST_CONVERGED: return DPT_OK;
@@ -277,13 +296,13 @@ struct Timer {
 void layout_full_mixed_real(Carve& c, int n, bool delta_dev, bool a_dev, bool start = false,
                             bool start_dev = true) {
   const int ld = (int)round_up(n, 128);
-  const int ntm = (n + 127) / 128, ntn = (n + kIter0Cols - 1) / kIter0Cols;
+  const int ntn = (n + kIter0Cols - 1) / kIter0Cols;
   c.take<IterState>(1);
   c.take<double>(ld);                        // theta (shifted)
   c.take<float>(ld); c.take<float>(ld);      // theta hi/lo
   c.take<double>(ld); c.take<double>(ld);    // d, E
   c.take<float>(ld); c.take<float>(ld);      // e_col, dprev_col
-  c.take<float>((size_t)4 * ntm * ld);       // column partials
+  c.take<float>((size_t)4 * (ld / 64) * ld); // column partials (64-row slots at most)
   c.take<float>((size_t)ntn * ld);           // row partials
   c.take<__half>((size_t)3 * ld * n);        // Dcat (room for three FP16 slices)
   for (int q = 0; q < 2; ++q) { c.take<float>((size_t)ld * n); c.take<float>((size_t)ld * n); }
@@ -441,7 +460,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     double* E = c.take<double>(ld);
     float* e_col = c.take<float>(ld);
     float* dprev = c.take<float>(ld);
-    float* part = c.take<float>((size_t)4 * ntm * ld);
+    float* part = c.take<float>((size_t)4 * (ld / 64) * ld);
     float* rowpart = c.take<float>((size_t)ntn * ld);
     __half* Dcat = c.take<__half>((size_t)3 * ld * n);
     float *Ahi[2], *Alo[2];
@@ -516,10 +535,21 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     CK(launch_theta_ff(n, thd, thh, thl, s));
     CK(launch_delta_scales(delta, ldd, n, thh, thl, lambda, o.epstein_nesbet, sdev, ld_s, sinv,
                            st, s));
-    CK(launch_prep_delta(delta, ldd, n, ld, o.epstein_nesbet, S, Dcat, st, s));
-    CK(launch_iter0(delta, ldd, thh, thl, lambda, n, ld, o.epstein_nesbet, S, Dcat, dtb[0], L,
-                    d, part, rowpart, sdev, ld_s, sinv, st, s));
-    CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
+    // Iteration 0 and the slicing in one pass over pairs of mirrored tiles (Delta read
+    // by TMA: a 16-byte aligned base and an even column pitch); from a start, or for
+    // other layouts, the slicing pass and then iteration 0
+    const bool fused0 = !sdev && ((uintptr_t)delta & 15u) == 0 && (ldd & 1) == 0;
+    if (fused0) {
+      const CUtensorMap tD = make_tmap_f64(delta, n, n, ldd);
+      CK(launch_iter0_pairs(tD, thh, thl, lambda, n, ld, o.epstein_nesbet, S, Dcat, dtb[0], L,
+                            d, part, rowpart, st, s));
+      CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s, ld / 64));
+    } else {
+      CK(launch_prep_delta(delta, ldd, n, ld, o.epstein_nesbet, S, Dcat, st, s));
+      CK(launch_iter0(delta, ldd, thh, thl, lambda, n, ld, o.epstein_nesbet, S, Dcat, dtb[0],
+                      L, d, part, rowpart, sdev, ld_s, sinv, st, s));
+      CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
+    }
 
     const CUtensorMap tA = make_tmap_f16(Dcat, (uint64_t)3 * ld, n, (uint64_t)3 * ld, 128);
     int nsm = 0, dev = 0;
@@ -552,8 +582,8 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     // state buffer may still be the source of the pending upload above: not touched)
     Prof prof;
     prof.on = o.profile != 0;
-    prof.launches = th.empty() ? 6 : 5;   // (theta check,) theta split, scales, slicing,
-                                          // iteration 0, control
+    // (theta check,) theta split, scales, (slicing,) iteration 0, control
+    prof.launches = (th.empty() ? 6 : 5) - (fused0 ? 1 : 0);
     {
       // the outputs are formed inside the chunk in which the iteration stops (the
       // output kernel does nothing while the state is still running)

@@ -29,7 +29,10 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
+#include <climits>
+#include <type_traits>
 
 #include "dpt_device.cuh"
 #include "dpt_internal.h"
@@ -99,15 +102,140 @@ constexpr int P_SMEM_BYTES = P_RREG + EB_BYTES + SMEM_X + 1024 + (int)sizeof(Gem
 static_assert(P_SMEM_BYTES <= 232448, "CTA-pair shared memory over the per-block limit");
 
 // ---------------------------------------------------------------------------
-// Scales of the FP16 operands.  One block per column i of Delta (rows j contiguous):
+// Scales of the FP16 operands: the block maxima of the scale pass (256 threads) reach
+// the state by integer atomicMax; the grid's last block sets sig (max |Delta| 2^sig in
+// [2^14, 2^15)) and the exponent of the first increment (its bound lands at 2^13).
+// hmax: high word of max |Delta| (sign cleared); gmax: the first increment's bound
+// before the factor |lambda| (with a start: its largest entry); rgmax: max 1 / |gap|.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void scales_finish(unsigned hmax, float gmax, float rgmax,
+                                              bool start, IterState* st) {
+  hmax = __reduce_max_sync(0xffffffffu, hmax);
+  unsigned gb = __reduce_max_sync(0xffffffffu, __float_as_uint(gmax));   // gmax >= 0
+  unsigned rb = __reduce_max_sync(0xffffffffu, __float_as_uint(rgmax));  // rgmax >= 0
+  __shared__ unsigned wh[8], wg[8], wr[8];
+  __shared__ bool last;
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { wh[w] = hmax; wg[w] = gb; wr[w] = rb; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned a = 0u, b = 0u, r = 0u;
+    for (int q = 0; q < 8; ++q) { a = max(a, wh[q]); b = max(b, wg[q]); r = max(r, wr[q]); }
+    atomicMax(&st->amax_bits, a);
+    atomicMax(&st->g0max_bits, b);
+    atomicMax(&st->rgmax_bits, r);
+    __threadfence();
+    last = (atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  __threadfence();
+  volatile IterState* vs = st;
+  const unsigned hm = vs->amax_bits;
+  int sig = 0;
+  if (hm != 0u) sig = 14 - ((int)((hm >> 20) & 0x7FFu) - 1023);   // max |Delta| < 2^(e+1)
+  sig = max(-120, min(120, sig));
+  const double lam = vs->lam;
+  // the bound of the first increment: |lambda| max |Delta_ji / gap|, or with a start
+  // the largest entry of its offset from I
+  const double g0 = (double)__uint_as_float(vs->g0max_bits);
+  const double ref = start ? g0 : fabs(lam) * g0;
+  const int s0 = dt_scale_exp(ref, 13, sig, lam);
+  vs->sig = sig;
+  vs->sexp[0] = s0;
+  vs->sexp[1] = s0;
+  vs->blocks_done = 0;
+}
+
+// |v| to 20 fraction bits as a float from the high word of a double (sign cleared):
+// 0 below the float range, +inf beyond it (inputs beyond it are rejected by the
+// slicing)
+__device__ __forceinline__ float abs_from_hiword(unsigned hw) {
+  const unsigned e = hw >> 20;
+  return (e > 896u && e < 1151u) ? __uint_as_float(((e - 896u) << 23) | ((hw & 0xFFFFFu) << 3))
+                                 : (e >= 1151u ? __int_as_float(0x7f800000) : 0.f);
+}
+
+// The scale pass without a start.  Thread per row j (theta_j in registers); a work
+// item is 256 rows x 8 columns, eight loads in flight per thread (a warp reads 256
+// contiguous bytes of each column), and the items are strided over a grid of a few
+// blocks per SM, so that the block's reduction (scales_finish) runs once per block.
+// Column i's theta is a block-uniform 16-byte load.  The quantities are those of
+// k_delta_scales below: the high word of max |Delta_ji| (the diagonal only without
+// Epstein-Nesbet), and over j != i the ratio |Delta_ji| / |theta_i - theta_j|
+// (|Delta_ji| from its high word, the gap from the float parts of theta, their low
+// parts where the high parts coincide) and 1 / |gap|.
+constexpr int kScaleCols = 8;   // a multiple of 4 (16-byte theta loads)
+__device__ __forceinline__ void scale_entry(unsigned hw, float tih, float til, float tjh,
+                                            float tjl, unsigned& hmax, float& gmax,
+                                            float& rgmax) {
+  hmax = max(hmax, hw);
+  float g = tih - tjh;
+  if (g == 0.f) g = til - tjl;
+  // NaN never wins fmaxf
+  const float rg = rcp_approx(fabsf(g));
+  gmax = fmaxf(gmax, abs_from_hiword(hw) * rg);
+  rgmax = fmaxf(rgmax, rg);
+}
+__global__ void __launch_bounds__(256) k_delta_scales_rows(const double* __restrict__ delta,
+                                                           int64_t ld_in, int n, int nrb,
+                                                           int nitems,
+                                                           const float* __restrict__ th_hi,
+                                                           const float* __restrict__ th_lo,
+                                                           int en, IterState* st) {
+  unsigned hmax = 0u;
+  float gmax = 0.f, rgmax = 0.f;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int rb = it % nrb, cb = it / nrb;
+    const int j = rb * 256 + threadIdx.x, i0 = cb * kScaleCols;
+    if (j >= n) continue;
+    const float tjh = th_hi[j], tjl = th_lo[j];
+    const double* p = delta + (int64_t)i0 * ld_in + j;
+    const int nc = min(kScaleCols, n - i0);
+    if (nc == kScaleCols && (unsigned)(j - i0) >= (unsigned)kScaleCols) {
+      // a full item away from the diagonal
+      double v[kScaleCols];
+#pragma unroll
+      for (int u = 0; u < kScaleCols; ++u) {
+        v[u] = *p;
+        p += ld_in;
+      }
+      float tih[kScaleCols], til[kScaleCols];
+#pragma unroll
+      for (int u = 0; u < kScaleCols; u += 4) {
+        const float4 a = *reinterpret_cast<const float4*>(th_hi + i0 + u);
+        const float4 b = *reinterpret_cast<const float4*>(th_lo + i0 + u);
+        tih[u] = a.x; tih[u + 1] = a.y; tih[u + 2] = a.z; tih[u + 3] = a.w;
+        til[u] = b.x; til[u + 1] = b.y; til[u + 2] = b.z; til[u + 3] = b.w;
+      }
+#pragma unroll
+      for (int u = 0; u < kScaleCols; ++u)
+        scale_entry((unsigned)__double2hiint(v[u]) & 0x7FFFFFFFu, tih[u], til[u], tjh, tjl,
+                    hmax, gmax, rgmax);
+    } else {
+      // the ragged last item, or the one holding the diagonal entry of row j
+      for (int u = 0; u < nc; ++u) {
+        const int i = i0 + u;
+        const unsigned hw = (unsigned)__double2hiint(delta[(int64_t)i * ld_in + j]) & 0x7FFFFFFFu;
+        if (i == j) {
+          if (!en) hmax = max(hmax, hw);
+          continue;
+        }
+        scale_entry(hw, th_hi[i], th_lo[i], tjh, tjl, hmax, gmax, rgmax);
+      }
+    }
+  }
+  scales_finish(hmax, gmax, rgmax, false, st);
+}
+
+// ---------------------------------------------------------------------------
+// The scale pass from a start.  One block per column i of Delta (rows j contiguous):
 // the high word of max |Delta_ji| (the FP64 bits without the sign; with its low word
 // filled with ones it bounds max |Delta|) and max_{j != i} |Delta_ji| /
 // |theta_i - theta_j|, both by integer atomicMax.  The ratio only places the first
 // increment's scale, so it is formed cheaply: |Delta_ji| from its high word (20
 // fraction bits) and the gap from the float parts of theta (their low parts where
 // the high parts coincide).
-// The last block sets sig (max |Delta| 2^sig in [2^14, 2^15)) and the exponent of
-// the first increment: |dt_0| <= |lambda| max |Delta_ji / gap| lands at 2^13.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__ delta,
                                                       int64_t ld_in, int n,
@@ -162,12 +290,7 @@ __global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__
         continue;
       }
       hmax = max(hmax, hw);
-      // |v| to 20 fraction bits as a float (0 below the float range; inputs beyond
-      // it are rejected by the slicing)
-      const unsigned e = hw >> 20;
-      const float va = (e > 896u && e < 1151u)
-                           ? __uint_as_float(((e - 896u) << 23) | ((hw & 0xFFFFFu) << 3))
-                           : (e >= 1151u ? __int_as_float(0x7f800000) : 0.f);
+      const float va = abs_from_hiword(hw);
       float g = thh - tjh[u];
       if (g == 0.f) g = thl - tjl[u];
       // NaN never wins fmaxf
@@ -176,42 +299,8 @@ __global__ void __launch_bounds__(256) k_delta_scales(const double* __restrict__
       rgmax = fmaxf(rgmax, rg);
     }
   }
-  hmax = __reduce_max_sync(0xffffffffu, hmax);
   if (start) gmax = smax;   // with a start: the first increment's largest entry
-  unsigned gb = __reduce_max_sync(0xffffffffu, __float_as_uint(gmax));   // gmax >= 0
-  unsigned rb = __reduce_max_sync(0xffffffffu, __float_as_uint(rgmax));  // rgmax >= 0
-  __shared__ unsigned wh[8], wg[8], wr[8];
-  __shared__ bool last;
-  const int w = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) { wh[w] = hmax; wg[w] = gb; wr[w] = rb; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned a = 0u, b = 0u, r = 0u;
-    for (int q = 0; q < 8; ++q) { a = max(a, wh[q]); b = max(b, wg[q]); r = max(r, wr[q]); }
-    atomicMax(&st->amax_bits, a);
-    atomicMax(&st->g0max_bits, b);
-    atomicMax(&st->rgmax_bits, r);
-    __threadfence();
-    last = (atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!last || threadIdx.x != 0) return;
-  __threadfence();
-  volatile IterState* vs = st;
-  const unsigned hm = vs->amax_bits;
-  int sig = 0;
-  if (hm != 0u) sig = 14 - ((int)((hm >> 20) & 0x7FFu) - 1023);   // max |Delta| < 2^(e+1)
-  sig = max(-120, min(120, sig));
-  const double lam = vs->lam;
-  // the bound of the first increment: |lambda| max |Delta_ji / gap|, or with a start
-  // the largest entry of its offset from I
-  const double g0 = (double)__uint_as_float(vs->g0max_bits);
-  const double ref = start ? g0 : fabs(lam) * g0;
-  const int s0 = dt_scale_exp(ref, 13, sig, lam);
-  vs->sig = sig;
-  vs->sexp[0] = s0;
-  vs->sexp[1] = s0;
-  vs->blocks_done = 0;
+  scales_finish(hmax, gmax, rgmax, start != nullptr, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -393,6 +482,325 @@ __global__ void __launch_bounds__(256) k_iter0(const double* __restrict__ delta,
     rowpart[(int64_t)blockIdx.x * ld + m0 + r] = t;
   }
   // the slice count and scale of the first product depend on the size of dt_0
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0 && mx > 0.f) atomicMax(&st->dmax_bits, __float_as_uint(mx));
+}
+
+// ---------------------------------------------------------------------------
+// Iteration 0 fused with the slicing of Delta, over pairs of mirrored 64 x 64 tiles.
+// Iteration 0 needs, for each entry (j, i), both Delta_ji (its increment, remainder
+// and |R_0|^2) and the transposed entry Delta_ij (the diagonal term
+// e_i 2^sig = sum_j Delta_ij 2^sig dt0_ji, from the FP16 slices), and the slicing
+// writes Delta_ij into row i of the row-major slices.  A block that holds tile
+// (M, C) and its mirror (C, M) therefore does both kernels' work while reading each
+// entry of Delta from HBM once (the separate slicing pass and the transposed re-read
+// of the slices are gone).
+//
+// Roles (128 threads): threads 0-63 own the columns f of tile C (entries (l, f),
+// l in M); threads 64-127 own the columns f of tile M (entries (l, f), l in C) in
+// 16-column slabs, 16 threads per column, each over 16 of the 64 rows.  A thread
+// that owns entry (l, f) also takes the transposed entry (f, l): its slices go to row
+// f of Dcat, its magnitude to the row sum of row f, and its product with the
+// increment of (l, f) to e_f.  Every column's sums are then thread-local (no warp
+// reductions), and every output a thread writes is a run along its own column (dt0,
+// L) or row (Dcat).  The diagonal tiles (M = C) use the first role only.
+//
+// Data: slabs of 16 rows of M, staged by TMA (FP64, 16 x 16 boxes, 128-byte swizzle,
+// zero fill beyond n) in a two-stage ring: the main slab (rows of the slab x the 64
+// columns of C) and the mirror slab (the 64 rows of C x the slab's columns).  With the
+// swizzle every shared-memory access pattern below is free of bank conflicts.
+// Column partials go to 64-row slots (part, nslot = ld / 64 slots per quantity), row
+// partials to rowpart (one per 64 columns, as the unfused kernel).
+// ---------------------------------------------------------------------------
+constexpr int F0T = 64;                        // tile edge
+constexpr int F0_BOX = 16 * 128;               // one 16 x 16 FP64 box (16 lines of 128 B)
+constexpr int F0_HALF = (F0T / 16) * F0_BOX;   // main or mirror slab: 8 KB
+constexpr int F0_STAGE = 2 * F0_HALF;          // 16 KB per ring stage
+constexpr int F0_NST = 2;                      // ring stages
+constexpr int F0_SMEM = F0_NST * F0_STAGE + 1024;   // the ring + 1024-byte alignment slack
+
+__device__ __forceinline__ void lds_f64x2(const unsigned char* p, double& a, double& b) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ double lds_f64(const unsigned char* p) {
+  return *reinterpret_cast<const double*>(p);
+}
+__device__ __forceinline__ void bar_sync_mirror() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+template <int NSL>
+__global__ void __launch_bounds__(128) k_iter0_pairs(const __grid_constant__ CUtensorMap tmD,
+                                                     const float* __restrict__ th_hi,
+                                                     const float* __restrict__ th_lo,
+                                                     float lam_hi, float lam_lo, int n, int ld,
+                                                     int nt, int en, __half* __restrict__ Dcat,
+                                                     __half* __restrict__ dt0,
+                                                     float* __restrict__ L, double* __restrict__ d,
+                                                     float* __restrict__ part,
+                                                     float* __restrict__ rowpart, IterState* st) {
+  extern __shared__ unsigned char f0_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)f0_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full[F0_NST];
+  __shared__ __align__(16) float thA_h[F0T], thA_l[F0T], thB_h[F0T], thB_l[F0T];   // theta of M, C
+  __shared__ float red[4][16];   // second mirror warp's column sums, handed to the first
+
+  // unit -> tile pair (tm <= tc): the off-diagonal pairs first, the diagonal tiles last
+  const int u = blockIdx.x;
+  const int noff = nt * (nt - 1) / 2;
+  int tm, tc;
+  if (u < noff) {
+    int b = (int)((1.f + sqrtf(1.f + 8.f * (float)u)) * 0.5f);
+    while (b * (b - 1) / 2 > u) --b;
+    while ((b + 1) * b / 2 <= u) ++b;
+    tc = b;
+    tm = u - b * (b - 1) / 2;
+  } else {
+    tm = tc = u - noff;
+  }
+  const int M0 = tm * F0T, C0 = tc * F0T;
+  if (M0 >= n) return;   // both tiles beyond n (M0 <= C0): nothing to write
+  const bool diag = (tm == tc);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned* tflag = &st->timeout;
+
+  if (tid == 0) {
+    for (int q = 0; q < F0_NST; ++q) mbar_init(&full[q], 1);
+    fence_mbar_init();
+  }
+  if (tid < F0T) {
+    const int r = M0 + tid, c = C0 + tid;
+    thA_h[tid] = r < n ? th_hi[r] : 0.f;
+    thA_l[tid] = r < n ? th_lo[r] : 0.f;
+    thB_h[tid] = c < n ? th_hi[c] : 0.f;
+    thB_l[tid] = c < n ? th_lo[c] : 0.f;
+  }
+  __syncthreads();
+  // slab s: main = rows [M0 + 16 s, +16) x columns C, mirror = rows C x those columns
+  auto issue = [&](int s) {
+    uint64_t* bar = &full[s % F0_NST];
+    unsigned char* base = sm + (s % F0_NST) * F0_STAGE;
+    mbar_arrive_expect_tx(bar, F0_STAGE);
+#pragma unroll
+    for (int b = 0; b < F0T / 16; ++b) {
+      tma_load_2d(base + b * F0_BOX, &tmD, bar, M0 + 16 * s, C0 + 16 * b);
+      tma_load_2d(base + F0_HALF + b * F0_BOX, &tmD, bar, C0 + 16 * b, M0 + 16 * s);
+    }
+  };
+  constexpr int NSLAB = F0T / 16;
+  if (tid == 0)
+    for (int q = 0; q < F0_NST && q < NSLAB; ++q) issue(q);
+
+  const float sc = exp2i(st->sig);
+  const int se0 = st->sexp[0];
+  const float iqs = exp2i(-se0);
+  // strength factor of this first step (the ramp's 1 - alpha, else 1), folded into the
+  // quotient's scale
+  const float qr = exp2i(se0) * (float)(1.0 - st->ramp_pow);
+  const int64_t cat_ld = (int64_t)NSLICE * ld;
+  const bool mainr = tid < F0T;
+  const int t = mainr ? tid : tid - F0T;
+  const int ml = t & 15, g = t >> 4;   // mirror role: column in the slab, group of 16 rows
+  float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f, rows = 0.f, mx = 0.f;
+  bool badv = false;
+  bool ok = true;
+  int s = 0;
+  for (; s < NSLAB; ++s) {
+    const bool got = mbar_wait(&full[s % F0_NST], (s / F0_NST) & 1, tflag);
+    if (!__syncthreads_and(got)) {
+      ok = false;
+      break;
+    }
+    const unsigned char* mb = sm + (s % F0_NST) * F0_STAGE;   // main slab
+    const unsigned char* rb = mb + F0_HALF;              // mirror slab
+    if (mainr || !diag) {
+      // the fixed index f (owned column, row of the transposed entries) and the
+      // first loop index of this slab
+      const int f = mainr ? C0 + t : M0 + 16 * s + ml;
+      const float tfh = mainr ? thB_h[t] : thA_h[16 * s + ml];
+      const float tfl = mainr ? thB_l[t] : thA_l[16 * s + ml];
+      if (!mainr) { r2 = 0.f; eh = 0.f; el = 0.f; rows = 0.f; }
+      // Eight loop indices l = lb .. lb + 7 of this thread: the owned entries (l, f) and
+      // the transposed ones (f, l).  PLAIN: no diagonal entry and every l < n (all
+      // but the diagonal tiles and the ragged last tile), so no per-entry tests.
+      auto eight = [&](int h, auto plain_tag) {
+        constexpr bool PLAIN = decltype(plain_tag)::value;
+        const int lb = mainr ? M0 + 16 * s + 8 * h : C0 + 16 * g + 8 * h;
+        const int tl0 = mainr ? 16 * s + 8 * h : 16 * g + 8 * h;   // theta of l, in shared
+        const float* tlh = mainr ? thA_h + tl0 : thB_h + tl0;
+        const float* tll = mainr ? thA_l + tl0 : thB_l + tl0;
+        double vo[8], vr[8];   // owned (l, f), transposed (f, l)
+        if (mainr) {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            lds_f64x2(mb + t * 128 + (((4 * h + kk) ^ (t & 7)) << 4), vo[2 * kk], vo[2 * kk + 1]);
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            vr[k] = lds_f64(rb + (t >> 4) * F0_BOX + (8 * h + k) * 128 +
+                            ((((t & 15) >> 1) ^ k) << 4) + ((t & 1) << 3));
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            lds_f64x2(rb + g * F0_BOX + ml * 128 + (((4 * h + kk) ^ (ml & 7)) << 4), vo[2 * kk],
+                      vo[2 * kk + 1]);
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            vr[k] = lds_f64(mb + (16 * g + 8 * h + k) * 128 + (((ml >> 1) ^ k) << 4) +
+                            ((ml & 1) << 3));
+        }
+        float tlv_h[8], tlv_l[8];
+#pragma unroll
+        for (int k = 0; k < 8; k += 4) {
+          const float4 a = *reinterpret_cast<const float4*>(tlh + k);
+          const float4 b = *reinterpret_cast<const float4*>(tll + k);
+          tlv_h[k] = a.x; tlv_h[k + 1] = a.y; tlv_h[k + 2] = a.z; tlv_h[k + 3] = a.w;
+          tlv_l[k] = b.x; tlv_l[k + 1] = b.y; tlv_l[k + 2] = b.z; tlv_l[k + 3] = b.w;
+        }
+        uint32_t qw[4];
+        float Lo[8];
+        uint32_t Dw[NSL][4];
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+          float R0h[2], R0l[2], gh[2], gl[2], q[2], Ds[NSL][2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int l = lb + k + e;
+            const bool on = !PLAIN && (l == f);
+            // transposed entry (f, l): FP16 slices of Delta_fl 2^sig, as the slicing
+            // kernel forms them (hi 2^sig, then the rounding remainders; the last slice
+            // takes lo 2^sig as well); zero on the diagonal with Epstein-Nesbet
+            float rh, rl;
+            split_double_fast(vr[k + e], rh, rl);
+            badv |= beyond_float(vr[k + e]);
+            rows += fabsf(rh);
+            if (!PLAIN && en && on) rh = rl = 0.f;
+            float r = rh * sc;
+#pragma unroll
+            for (int sl = 0; sl < NSL; ++sl) {
+              const float tt = (sl == NSL - 1) ? r + rl * sc : r;
+              const float qh = __half2float(__float2half_rn(tt));
+              r = tt - qh;
+              Ds[sl][e] = qh;
+            }
+            // owned entry (l, f): R_0 = lambda Delta_lf (float-float), the gap
+            // theta_f - theta_l, the scaled quotient
+            R0h[e] = R0l[e] = gh[e] = gl[e] = q[e] = 0.f;
+            if (on) {
+              d[f] = en ? 0.0 : vo[k + e];
+              a2 += 1.f;
+            } else if (PLAIN || l < n) {
+              float vh, vl;
+              split_double_fast(vo[k + e], vh, vl);
+              float pr, pe;
+              two_prod(lam_hi, vh, pr, pe);
+              pe = fmaf(lam_hi, vl, fmaf(lam_lo, vh, pe));
+              fast_two_sum(pr, pe, R0h[e], R0l[e]);
+              ff_sub(tfh, tfl, tlv_h[k + e], tlv_l[k + e], gh[e], gl[e]);
+              q[e] = R0h[e] * rcp_approx(gh[e]) * qr;
+            }
+          }
+          const uint32_t w = f16x2_sat(q[0], q[1]);
+          qw[k >> 1] = w;
+          const float2 dq = __half22float2(*reinterpret_cast<const __half2*>(&w));
+          const float dtn[2] = {dq.x * iqs, dq.y * iqs};
+#pragma unroll
+          for (int sl = 0; sl < NSL; ++sl) {
+            const __half2 hp = __floats2half2_rn(Ds[sl][0], Ds[sl][1]);   // exact
+            Dw[sl][k >> 1] = *reinterpret_cast<const uint32_t*>(&hp);
+          }
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            // L_1 = R_0 - Gap dt_0 (R0h - p exact: p is R0h to FP16 accuracy)
+            float pp, pq;
+            two_prod(gh[e], dtn[e], pp, pq);
+            pq = fmaf(gl[e], dtn[e], pq);
+            Lo[k + e] = (R0h[e] - pp) + (R0l[e] - pq);
+            r2 = fmaf(R0h[e], R0h[e], r2);
+            const float p1 = Ds[0][e] * dtn[e];
+            float p23 = 0.f;
+            if (NSL > 2) p23 = Ds[2][e] * dtn[e];
+            if (NSL > 1) p23 = fmaf(Ds[1][e], dtn[e], p23);
+            float sh, se;
+            two_sum(eh, p1, sh, se);
+            se += el + p23;
+            fast_two_sum(sh, se, eh, el);
+            mx = fmaxf(mx, fabsf(dtn[e]));
+          }
+        }
+        const int64_t oc = (int64_t)f * ld + lb;   // column f, rows lb.. (dt0, L)
+        *reinterpret_cast<uint4*>(dt0 + oc) = make_uint4(qw[0], qw[1], qw[2], qw[3]);
+        st4(L + oc, make_float4(Lo[0], Lo[1], Lo[2], Lo[3]));
+        st4(L + oc + 4, make_float4(Lo[4], Lo[5], Lo[6], Lo[7]));
+        const int64_t orow = (int64_t)f * cat_ld + lb;   // row f of the slices
+#pragma unroll
+        for (int sl = 0; sl < NSL; ++sl)
+          *reinterpret_cast<uint4*>(Dcat + orow + (int64_t)sl * ld) =
+              make_uint4(Dw[sl][0], Dw[sl][1], Dw[sl][2], Dw[sl][3]);
+      };
+      if (f < n) {
+        const int lend = mainr ? M0 + 16 * s + 16 : C0 + 16 * g + 16;
+        if (!diag && lend <= n) {
+          eight(0, std::true_type{});
+          eight(1, std::true_type{});
+        } else {
+          eight(0, std::false_type{});
+          eight(1, std::false_type{});
+        }
+      }
+      if (!mainr) {
+        // column f over the 64 rows of C: the four groups of 16 rows (lanes l and
+        // l + 16 of each mirror warp, then the two warps)
+        float o2 = __shfl_xor_sync(0xffffffffu, r2, 16);
+        float ohh = __shfl_xor_sync(0xffffffffu, eh, 16);
+        float oll = __shfl_xor_sync(0xffffffffu, el, 16);
+        float orw = __shfl_xor_sync(0xffffffffu, rows, 16);
+        {
+          float sh, se;
+          two_sum(eh, ohh, sh, se);
+          se += el + oll;
+          fast_two_sum(sh, se, eh, el);
+          r2 += o2;
+          rows += orw;
+        }
+        if (warp == 3 && lane < 16) {
+          red[0][lane] = r2; red[1][lane] = eh; red[2][lane] = el; red[3][lane] = rows;
+        }
+        bar_sync_mirror();
+        if (warp == 2 && lane < 16 && f < n) {
+          float sh, se;
+          two_sum(eh, red[1][lane], sh, se);
+          se += el + red[2][lane];
+          fast_two_sum(sh, se, eh, el);
+          r2 += red[0][lane];
+          rows += red[3][lane];
+          const int nslot = nt;
+          part[((int64_t)0 * nslot + tc) * ld + f] = r2;
+          part[((int64_t)1 * nslot + tc) * ld + f] = 0.f;
+          part[((int64_t)2 * nslot + tc) * ld + f] = eh;
+          part[((int64_t)3 * nslot + tc) * ld + f] = el;
+          if (C0 < n) rowpart[(int64_t)tc * ld + f] = rows;
+        }
+      }
+    }
+    __syncthreads();   // the slab's stage is free again
+    if (tid == 0 && s + F0_NST < NSLAB) issue(s + F0_NST);
+  }
+  if (!ok) {
+    // let the copies in flight land before the block exits
+    if (tid == 0)
+      for (int x = s; x < NSLAB && x < s + F0_NST; ++x)
+        mbar_wait_quiet(&full[x % F0_NST], (x / F0_NST) & 1, kTailWaitNs);
+    return;
+  }
+  if (mainr && C0 + t < n) {
+    const int f = C0 + t, nslot = nt;
+    part[((int64_t)0 * nslot + tm) * ld + f] = r2;
+    part[((int64_t)1 * nslot + tm) * ld + f] = a2;
+    part[((int64_t)2 * nslot + tm) * ld + f] = eh;
+    part[((int64_t)3 * nslot + tm) * ld + f] = el;
+    rowpart[(int64_t)tm * ld + f] = rows;
+  }
+  if (badv) atomicExch(&st->bad_input, 1u);
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0 && mx > 0.f) atomicMax(&st->dmax_bits, __float_as_uint(mx));
 }
@@ -1578,8 +1986,23 @@ cudaError_t launch_delta_scales(const double* delta, int64_t ld_in, int n, const
                                 const float* th_lo, double lam, int en, const double* start,
                                 int64_t ld_s, double* sinv, IterState* st, cudaStream_t s) {
   (void)lam;   // read from the state
-  // one block per column (a grid striding over fewer blocks measured slower: 38 us
-  // against 34 us at n = 4096)
+  if (!start) {
+    static int nsm = 0;
+    if (nsm == 0) {
+      int dev = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+    }
+    const int nrb = (n + 255) / 256, ncb = (n + kScaleCols - 1) / kScaleCols;
+    const long long items = (long long)nrb * ncb;
+    if (items > INT_MAX) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<long long>(items, 6LL * nsm);
+    k_delta_scales_rows<<<grid, 256, 0, s>>>(delta, ld_in, n, nrb, (int)items, th_hi, th_lo, en,
+                                             st);
+    return cudaGetLastError();
+  }
+  // from a start: one block per column
   k_delta_scales<<<n, 256, 0, s>>>(delta, ld_in, n, th_hi, th_lo, en, start, ld_s, sinv, st);
   return cudaGetLastError();
 }
@@ -1636,11 +2059,37 @@ cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
   return cudaGetLastError();
 }
 
+cudaError_t launch_iter0_pairs(const CUtensorMap& tmD, const float* th_hi, const float* th_lo,
+                               double lam, int n, int ld, int en, int nsl, __half* Dcat,
+                               __half* dt0, float* L, double* d, float* part, float* rowpart,
+                               IterState* st, cudaStream_t s) {
+  if (nsl < 1 || nsl > NSLICE || ld % F0T) return cudaErrorInvalidValue;
+  const cudaError_t ea = mixed_set_attributes();
+  if (ea != cudaSuccess) return ea;
+  const int nt = ld / F0T;
+  const long long units = (long long)nt * (nt + 1) / 2;
+  const float lh = (float)lam;
+  const float ll = (float)(lam - (double)lh);
+#define DPT_IT0P(NS)                                                                         \
+  k_iter0_pairs<NS><<<(unsigned)units, 128, F0_SMEM, s>>>(tmD, th_hi, th_lo, lh, ll, n, ld, nt, \
+                                                          en, Dcat, dt0, L, d, part, rowpart, st)
+  switch (nsl) {
+    case 1: DPT_IT0P(1); break;
+    case 2: DPT_IT0P(2); break;
+    default: DPT_IT0P(3); break;
+  }
+#undef DPT_IT0P
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,
-                        float* dprev_col, IterState* st, cudaStream_t s) {
-  // row partials: one per block of kIter0Cols columns of iteration 0
-  const int ntm = (n + BM - 1) / BM, ntn = (n + kIter0Cols - 1) / kIter0Cols;
+                        float* dprev_col, IterState* st, cudaStream_t s, int nslot) {
+  // column partials: one per 128-row tile of the product, or nslot of them (the fused
+  // iteration 0's 64-row slots); row partials: one per block of kIter0Cols columns of
+  // iteration 0
+  const int ntm = nslot > 0 ? nslot : (n + BM - 1) / BM;
+  const int ntn = (n + kIter0Cols - 1) / kIter0Cols;
   k_ctrl<<<(n + 31) / 32, 256, 0, s>>>(n, ld, ntm, ntn, part, rowpart, theta, d, E, e_col,
                                        dprev_col, st);
   return cudaGetLastError();
@@ -1660,6 +2109,12 @@ cudaError_t mixed_set_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_gemm_epi_quad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            P_SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_iter0_pairs<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, F0_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_iter0_pairs<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, F0_SMEM);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_iter0_pairs<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, F0_SMEM);
   if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev].store(true);
   return e;
 }

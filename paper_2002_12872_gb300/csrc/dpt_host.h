@@ -63,6 +63,9 @@ size_t measure(F&& f) {
 // `outer`, row pitch `pitch_elems`, box 64 x box_rows, 128-byte swizzle.  Throws Fail.
 CUtensorMap make_tmap_f16(const void* base, uint64_t inner, uint64_t outer,
                           uint64_t pitch_elems, uint32_t box_rows);
+// 2-D FP64 tensor map (column-major, even pitch), 16 x 16 boxes, 128-byte swizzle.
+CUtensorMap make_tmap_f64(const void* base, uint64_t inner, uint64_t outer,
+                          uint64_t pitch_elems);
 
 // dpt_status of a device-side ST_* code.
 dpt_status from_state(int s);

@@ -232,9 +232,17 @@ cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
                          const __half* Dcat, __half* dt0, float* L, double* d, float* part,
                          float* rowpart, const double* start, int64_t ld_s, const double* sinv,
                          IterState* st, cudaStream_t s);
+// iteration 0 fused with the slicing (no start; Delta as an FP64 tensor map with
+// 16 x 16 boxes, make_tmap_f64): writes Dcat, dt0, L, d and the column partials in
+// ld / 64 slots of 64 rows (pass that count to the first launch_ctrl)
+cudaError_t launch_iter0_pairs(const CUtensorMap& tmD, const float* th_hi, const float* th_lo,
+                               double lam, int n, int ld, int en, int nsl, __half* Dcat,
+                               __half* dt0, float* L, double* d, float* part, float* rowpart,
+                               IterState* st, cudaStream_t s);
+// nslot > 0: the column partials are in nslot row slots (else one per 128-row tile)
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,
-                        float* dprev_col, IterState* st, cudaStream_t s);
+                        float* dprev_col, IterState* st, cudaStream_t s, int nslot = 0);
 cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
                             const CUtensorMap& tmB1, const GemmEpiParams& p, cudaStream_t s);
 // The returned iterate in FP64 (A_1 = I + dt_0 is formed from the first increment dt0).
