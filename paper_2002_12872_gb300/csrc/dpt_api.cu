@@ -501,10 +501,30 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
       }
     }
 
+    int nsm = 0, dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CK(mixed_set_attributes());
+    // CTA-pair form when asked for and clusters of two can be resident
+    // (cta_pair 2: clusters of four, two pairs sharing each increment tile, when
+    // such clusters can be resident; pairs otherwise)
+    int npairs = 0, ctas = 2;
+    if (o.cta_pair == 2) {
+      npairs = std::min(nsm / 4, mixed_pair_clusters(4));
+      ctas = 4;
+    }
+    if (o.cta_pair && npairs <= 0) {
+      npairs = std::min(nsm / 2, mixed_pair_clusters(2));
+      ctas = 2;
+    }
+    const bool pair = npairs > 0;
     IterState h{};
     h.status = ST_RUNNING;
     h.max_iter = o.max_iter;
     h.max_slices = S;
+    // the pair kernel's certifying pass also writes the FP64 output (so the output
+    // kernel has nothing left to do when that pass certifies the iterate)
+    h.cert_out = pair ? 1 : 0;
     h.slices = S;
     h.lam = lambda;
     h.tol = o.tol;
@@ -552,23 +572,6 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     }
 
     const CUtensorMap tA = make_tmap_f16(Dcat, (uint64_t)3 * ld, n, (uint64_t)3 * ld, 128);
-    int nsm = 0, dev = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    CK(mixed_set_attributes());
-    // CTA-pair form when asked for and clusters of two can be resident
-    // (cta_pair 2: clusters of four, two pairs sharing each increment tile, when
-    // such clusters can be resident; pairs otherwise)
-    int npairs = 0, ctas = 2;
-    if (o.cta_pair == 2) {
-      npairs = std::min(nsm / 4, mixed_pair_clusters(4));
-      ctas = 4;
-    }
-    if (o.cta_pair && npairs <= 0) {
-      npairs = std::min(nsm / 2, mixed_pair_clusters(2));
-      ctas = 2;
-    }
-    const bool pair = npairs > 0;
     const int bn = pair ? mixed_pair_tile_n((int)n, npairs, ctas) : mixed_tile_n((int)n, nsm);
     const CUtensorMap tB0 = make_tmap_f16(dtb[0], n, n, ld, pair ? bn / 2 : bn);
     const CUtensorMap tB1 = make_tmap_f16(dtb[1], n, n, ld, pair ? bn / 2 : bn);
@@ -577,6 +580,8 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     for (int q = 0; q < 2; ++q) { p.A_hi[q] = Ahi[q]; p.A_lo[q] = Alo[q]; p.dt[q] = dtb[q]; }
     p.L = L; p.Dcat = Dcat; p.cat_ld = (int64_t)3 * ld; p.th_hi = thh; p.th_lo = thl; p.e_col = e_col; p.dprev_col = dprev;
     p.part = part; p.st = st;
+    p.Aout = Astage; p.ld_a = lda_dev;
+    p.aout_v8 = (((uintptr_t)Astage & 31u) == 0 && (lda_dev & 3) == 0) ? 1 : 0;
     // no host round trip here: the loop's kernels return at once if the iteration
     // stopped at iteration 0, and the loop reads the state after each chunk (the pinned
     // state buffer may still be the source of the pending upload above: not touched)

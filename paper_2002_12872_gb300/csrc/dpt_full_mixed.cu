@@ -164,7 +164,8 @@ __device__ __forceinline__ float abs_from_hiword(unsigned hw) {
 // k_delta_scales below: the high word of max |Delta_ji| (the diagonal only without
 // Epstein-Nesbet), and over j != i the ratio |Delta_ji| / |theta_i - theta_j|
 // (|Delta_ji| from its high word, the gap from the float parts of theta, their low
-// parts where the high parts coincide) and 1 / |gap|.
+// parts where the high parts coincide) and 1 / |gap|.  (Two rows per thread with
+// 16-byte loads measured no faster: about 4.5 TB/s of reads either way.)
 constexpr int kScaleCols = 8;   // a multiple of 4 (16-byte theta loads)
 __device__ __forceinline__ void scale_entry(unsigned hw, float tih, float til, float tjh,
                                             float tjl, unsigned& hmax, float& gmax,
@@ -503,7 +504,8 @@ __global__ void __launch_bounds__(256) k_iter0(const double* __restrict__ delta,
 // f of Dcat, its magnitude to the row sum of row f, and its product with the
 // increment of (l, f) to e_f.  Every column's sums are then thread-local (no warp
 // reductions), and every output a thread writes is a run along its own column (dt0,
-// L) or row (Dcat).  The diagonal tiles (M = C) use the first role only.
+// L) or row (Dcat): per slab, 32-byte stores (one sector each; 16-byte stores of half
+// slabs measured 14 % slower).  The diagonal tiles (M = C) use the first role only.
 //
 // Data: slabs of 16 rows of M, staged by TMA (FP64, 16 x 16 boxes, 128-byte swizzle,
 // zero fill beyond n) in a two-stage ring: the main slab (rows of the slab x the 64
@@ -623,7 +625,8 @@ __global__ void __launch_bounds__(128) k_iter0_pairs(const __grid_constant__ CUt
       // Eight loop indices l = lb .. lb + 7 of this thread: the owned entries (l, f) and
       // the transposed ones (f, l).  PLAIN: no diagonal entry and every l < n (all
       // but the diagonal tiles and the ragged last tile), so no per-entry tests.
-      auto eight = [&](int h, auto plain_tag) {
+      auto eight = [&](int h, auto plain_tag, uint32_t(&qw)[4], float(&Lo)[8],
+                       uint32_t(&Dw)[NSL][4]) {
         constexpr bool PLAIN = decltype(plain_tag)::value;
         const int lb = mainr ? M0 + 16 * s + 8 * h : C0 + 16 * g + 8 * h;
         const int tl0 = mainr ? 16 * s + 8 * h : 16 * g + 8 * h;   // theta of l, in shared
@@ -656,9 +659,6 @@ __global__ void __launch_bounds__(128) k_iter0_pairs(const __grid_constant__ CUt
           tlv_h[k] = a.x; tlv_h[k + 1] = a.y; tlv_h[k + 2] = a.z; tlv_h[k + 3] = a.w;
           tlv_l[k] = b.x; tlv_l[k + 1] = b.y; tlv_l[k + 2] = b.z; tlv_l[k + 3] = b.w;
         }
-        uint32_t qw[4];
-        float Lo[8];
-        uint32_t Dw[NSL][4];
 #pragma unroll
         for (int k = 0; k < 8; k += 2) {
           float R0h[2], R0l[2], gh[2], gl[2], q[2], Ds[NSL][2];
@@ -727,25 +727,35 @@ __global__ void __launch_bounds__(128) k_iter0_pairs(const __grid_constant__ CUt
             mx = fmaxf(mx, fabsf(dtn[e]));
           }
         }
+      };
+      if (f < n) {
+        // the sixteen loop indices of the slab, then 32-byte stores (one FP16 sector of
+        // dt_0 and of each slice, two of L_1) along column f and row f
+        uint32_t qw[2][4], Dw[2][NSL][4];
+        float Lo[2][8];
+        const int lend = mainr ? M0 + 16 * s + 16 : C0 + 16 * g + 16;
+        if (!diag && lend <= n) {
+          eight(0, std::true_type{}, qw[0], Lo[0], Dw[0]);
+          eight(1, std::true_type{}, qw[1], Lo[1], Dw[1]);
+        } else {
+          eight(0, std::false_type{}, qw[0], Lo[0], Dw[0]);
+          eight(1, std::false_type{}, qw[1], Lo[1], Dw[1]);
+        }
+        const int lb = mainr ? M0 + 16 * s : C0 + 16 * g;
         const int64_t oc = (int64_t)f * ld + lb;   // column f, rows lb.. (dt0, L)
-        *reinterpret_cast<uint4*>(dt0 + oc) = make_uint4(qw[0], qw[1], qw[2], qw[3]);
-        st4(L + oc, make_float4(Lo[0], Lo[1], Lo[2], Lo[3]));
-        st4(L + oc + 4, make_float4(Lo[4], Lo[5], Lo[6], Lo[7]));
+        st_global_v8(dt0 + oc, qw[0][0], qw[0][1], qw[0][2], qw[0][3], qw[1][0], qw[1][1],
+                     qw[1][2], qw[1][3]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          st_global_v8(L + oc + 8 * h, __float_as_uint(Lo[h][0]), __float_as_uint(Lo[h][1]),
+                       __float_as_uint(Lo[h][2]), __float_as_uint(Lo[h][3]),
+                       __float_as_uint(Lo[h][4]), __float_as_uint(Lo[h][5]),
+                       __float_as_uint(Lo[h][6]), __float_as_uint(Lo[h][7]));
         const int64_t orow = (int64_t)f * cat_ld + lb;   // row f of the slices
 #pragma unroll
         for (int sl = 0; sl < NSL; ++sl)
-          *reinterpret_cast<uint4*>(Dcat + orow + (int64_t)sl * ld) =
-              make_uint4(Dw[sl][0], Dw[sl][1], Dw[sl][2], Dw[sl][3]);
-      };
-      if (f < n) {
-        const int lend = mainr ? M0 + 16 * s + 16 : C0 + 16 * g + 16;
-        if (!diag && lend <= n) {
-          eight(0, std::true_type{});
-          eight(1, std::true_type{});
-        } else {
-          eight(0, std::false_type{});
-          eight(1, std::false_type{});
-        }
+          st_global_v8(Dcat + orow + (int64_t)sl * ld, Dw[0][sl][0], Dw[0][sl][1], Dw[0][sl][2],
+                       Dw[0][sl][3], Dw[1][sl][0], Dw[1][sl][1], Dw[1][sl][2], Dw[1][sl][3]);
       }
       if (!mainr) {
         // column f over the 64 rows of C: the four groups of 16 rows (lanes l and
@@ -829,6 +839,9 @@ __device__ __forceinline__ void ctrl_decide(IterState& ls, bool first, bool cert
     // iteration again in full (nothing it depends on was touched)
     vs->certify = 0;
     if (decide_final(vs, rho)) vs->slice_gemms = vs->slice_gemms + vs->slices;
+    // a pass that certified A_k and wrote it as the FP64 output leaves the output
+    // kernel nothing to do
+    else if (vs->status == ST_CONVERGED && vs->cert_out) vs->out_done = 1;
     return;
   }
   const double prev = vs->rho_last;
@@ -1303,7 +1316,7 @@ __device__ __forceinline__ bool p_epi_bar_and(bool v) {
 }
 
 // Issue the copies of sub-chunk sc (columns 16 sc .. 16 sc + 15) of tile (m0, n0).
-// A certifying pass (cert) needs neither A_lo nor the slices.
+// A certifying pass (cert) needs no slices, and A_lo only to write the FP64 output.
 // The first product's iterate A_1 = I + dt_0 is not stored (a1): it is formed from dt_0.
 __device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, bool cert, bool a1,
                                              int S, uint8_t* eb, int ew, int lane, int m0, int n0,
@@ -1318,7 +1331,7 @@ __device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, bo
     if (i >= p.n) continue;
     const int64_t idx = (int64_t)i * p.ld + j0;
     if (!a1) cp_async16(eb_f4(eb, ew, u, 0, lane), Ahc + idx);
-    if (!cert && !a1) cp_async16(eb_f4(eb, ew, u, 1, lane), Alc + idx);
+    if ((!cert || p.Aout) && !a1) cp_async16(eb_f4(eb, ew, u, 1, lane), Alc + idx);
     cp_async16(eb_f4(eb, ew, u, 2, lane), p.L + idx);
     cp_async8(eb_u2(eb, ew, u, 0, lane), dtp + idx);
     if (cert) continue;
@@ -1365,7 +1378,8 @@ struct EpiConst {
 //   S      the Delta slices this product used (the diagonal partial uses as many),
 //   MODE   0: a full step; 1: the first product, whose iterate A_1 = I + dt_0 is
 //          formed from the increment (its A_lo is zero); 2: a certifying pass, which
-//          forms only the residual norms of its iterate and writes nothing else,
+//          forms only the residual norms of its iterate and, given p.Aout, writes the
+//          iterate as the FP64 output A_hi + A_lo (used when the pass certifies it),
 //   CHECK  the tile holds a diagonal element or rows beyond n (per-element masks).
 // Leaves this lane's partial sums (|R|^2, |a|^2, the diagonal increment) in part3.
 //
@@ -1411,7 +1425,7 @@ __device__ __forceinline__ void epi_lean(const GemmEpiParams& p, const GemmSmemM
                       h_at(dtp, 3) * kc.isc);
   } else {
     ah4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, 0, 0, lane));
-    if (!CERT) al4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, 0, 1, lane));
+    if (!CERT || p.Aout) al4 = *reinterpret_cast<const float4*>(eb_f4(e8, ew, 0, 1, lane));
   }
   uint2 D[3] = {make_uint2(0u, 0u), make_uint2(0u, 0u), make_uint2(0u, 0u)};
   if (!CERT) {
@@ -1483,6 +1497,22 @@ __device__ __forceinline__ void epi_lean(const GemmEpiParams& p, const GemmSmemM
     st4(Aln + idx, ol);
     st4(p.L + idx, oL);
     *reinterpret_cast<uint2*>(dtn_out + idx) = ob;
+  } else if (p.Aout) {
+    // the iterate as the FP64 output (as the output kernel forms it: hi + lo); rows
+    // beyond n are not the caller's
+    double v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = f2d_bits(f4(ah4, e)) + f2d_bits(f4(al4, e));
+    double* o = p.Aout + (int64_t)i * p.ld_a + j0;
+    if (!CHECK && p.aout_v8) {
+      st_global_v8(o, __double2loint(v[0]), __double2hiint(v[0]), __double2loint(v[1]),
+                   __double2hiint(v[1]), __double2loint(v[2]), __double2hiint(v[2]),
+                   __double2loint(v[3]), __double2hiint(v[3]));
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (j0 + e < n) o[e] = v[e];
+    }
   }
   part3[0] = r2; part3[1] = a2; part3[2] = es;
 }
@@ -1881,6 +1911,7 @@ __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __
   const int j = blockIdx.x * 128 + threadIdx.x;
   if (j >= n) return;
   if (only_done && st->status == ST_RUNNING) return;   // not the final iterate yet
+  if (only_done && st->out_done) return;   // written by the certifying pass
   const int i0 = blockIdx.y * 32, i1 = min(n, i0 + 32);
   const int k = st->k;
   if (k == 0) {

@@ -63,6 +63,8 @@ struct IterState {
   unsigned g0max_bits; // atomicMax scratch: max_{j != i} |Delta_ji| / |theta_i - theta_j|
   int sig;             // the FP16 slices hold Delta * 2^sig
   int sexp[2];         // increment buffer q holds dt * 2^sexp[q] in FP16
+  int cert_out;        // mixed single solve: a certifying pass also writes the FP64 output
+  int out_done;        // ... and the pass that certified the returned iterate wrote it
   double rho_sum;      // sum of the residuals rho_k, k >= 1, the float recursion carried
   // mixed single solve: inputs of the bound on its arithmetic error (see dpt_refine.cu)
   unsigned rgmax_bits; // atomicMax scratch: max_{j != i} 1 / |theta_i - theta_j| (float bits)
@@ -201,6 +203,9 @@ struct GemmEpiParams {
   const float* dprev_col;  // d_{k-1}
   float* part;         // column partials [4][ntm][ld]: |R|^2, |a|^2, diag hi, diag lo
   IterState* st;
+  double* Aout;        // FP64 output (column-major, ld_a), written by certifying passes
+  int64_t ld_a;        // of the pair kernel (IterState::cert_out)
+  int aout_v8;         // Aout 32-byte aligned and ld_a a multiple of 4 (32-byte stores)
 };
 
 int mixed_smem_bytes();
