@@ -1388,6 +1388,20 @@ void plan_group(GroupPlan& g, int count, int cplx, const int64_t* n, const doubl
   Carve c{base};
   g.probs.assign(count, GProb{});
   g.tiles.clear(); g.prep_r.clear(); g.prep_c.clear(); g.blk_r.clear(); g.blk_c.clear();
+  {
+    // the lists' sizes first (a 20,000-problem batch has about 10^6 work items)
+    size_t nt = 0, npr = 0, nbl = 0;
+    for (int p = 0; p < count; ++p) {
+      const int np = (int)n[p], nr = cplx ? 2 * np : np, ld = (int)round_up(nr, 128);
+      const int bn = group_tile_n(np, gform_wmax(form));
+      nt += (size_t)((nr + gform_rows(form) - 1) / gform_rows(form)) * ((np + bn - 1) / bn);
+      npr += (size_t)((np + 31) / 32) * (ld / 64);
+      nbl += (size_t)((nr + 127) / 128) * ((np + 127) / 128);
+    }
+    g.tiles.reserve(nt);
+    (cplx ? g.prep_c : g.prep_r).reserve(npr);
+    (cplx ? g.blk_c : g.blk_r).reserve(nbl);
+  }
   for (int p = 0; p < count; ++p) {
     GProb& P = g.probs[p];
     const int np = (int)n[p];
@@ -1489,11 +1503,14 @@ cudaError_t launch_gform(int form, const GProb* probs, const int2* tiles, int nt
 // Largest tiles first (cost ~ K extent x tile width), problems kept contiguous
 // among equal costs.
 void sort_tiles(std::vector<int2>& tiles, const GProb* probs) {
-  std::stable_sort(tiles.begin(), tiles.end(), [probs](int2 a, int2 b) {
-    const GProb& A = probs[a.x];
-    const GProb& B = probs[b.x];
-    return (int64_t)A.ld * A.bn > (int64_t)B.ld * B.bn;
-  });
+  // the cost key per problem in one compact array (the comparator would otherwise
+  // read two table entries of several hundred bytes per comparison)
+  int max_p = -1;
+  for (const int2& t : tiles) max_p = std::max(max_p, t.x);
+  std::vector<int64_t> key((size_t)max_p + 1);
+  for (int p = 0; p <= max_p; ++p) key[p] = (int64_t)probs[p].ld * probs[p].bn;
+  std::stable_sort(tiles.begin(), tiles.end(),
+                   [&key](int2 a, int2 b) { return key[a.x] > key[b.x]; });
 }
 
 }  // namespace dpt
@@ -1551,9 +1568,9 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
       h.best = INFINITY;
       h.theta_max = 0.0;   // set by the theta check on the device
     }
-    std::vector<int4> preps(g.prep_r), blks(g.blk_r);
-    preps.insert(preps.end(), g.prep_c.begin(), g.prep_c.end());
-    blks.insert(blks.end(), g.blk_c.begin(), g.blk_c.end());
+    // a group is all real or all complex: one of each pair of lists is empty
+    const std::vector<int4>& preps = g.prep_c.empty() ? g.prep_r : g.prep_c;
+    const std::vector<int4>& blks = g.blk_c.empty() ? g.blk_r : g.blk_c;
     const int n_prep_r = (int)g.prep_r.size(), n_prep_c = (int)g.prep_c.size();
     const int n_blk_r = (int)g.blk_r.size(), n_blk_c = (int)g.blk_c.size();
     cudaStream_t s = b->stream;

@@ -12,6 +12,7 @@ calls raise.
 from __future__ import annotations
 
 import ctypes
+from collections.abc import Sequence
 import os
 
 import numpy as np
@@ -55,6 +56,23 @@ class Info(ctypes.Structure):
                 "product_ms": self.product_ms, "cta_pair": self.cta_pair,
                 "grouped_form": self.grouped_form, "fp64_iters": self.fp64_iters,
                 "refined_cols": self.refined_cols}
+
+
+class InfoList(Sequence):
+    """The per-problem dpt_info of a grouped solve as a read-only sequence of dicts,
+    converted on access (building 20,000 dicts on every call would cost the host more
+    than some solves take on the device)."""
+
+    def __init__(self, arr):
+        self._arr = arr
+
+    def __len__(self):
+        return len(self._arr)
+
+    def __getitem__(self, k):
+        if isinstance(k, slice):
+            return [self._arr[q].as_dict() for q in range(*k.indices(len(self._arr)))]
+        return self._arr[k].as_dict()
 
 
 class ServerCfg(ctypes.Structure):
@@ -445,7 +463,7 @@ class Batch:
         st = lib().dpt_solve_batched(self.count, C128 if self.cplx else R64, self._n, self._th,
                                      self._d, self._ldd, self._lam, ctypes.byref(o), self._a,
                                      self._lda, self._e, infos, _stream_of(self._dev, stream))
-        res = (self.A_outs, self.E_outs, [i.as_dict() for i in infos])
+        res = (self.A_outs, self.E_outs, InfoList(infos))
         if check and st != OK:
             err = RuntimeError(f"dpt_solve_batched: {status_string(st)}")
             err.result = res
