@@ -13,6 +13,7 @@
 #include <cstring>
 #include <functional>
 #include <mutex>
+#include <memory>
 #include <thread>
 #include <type_traits>
 #include <vector>
@@ -1528,6 +1529,34 @@ void layout_batched(Carve& c, int count, const GroupPlan& g) {
   c.take<char>(g.bytes);
 }
 
+// The last planned group (before placement in a workspace), reused when a call names
+// the same problems, pointers and form again (a Batch object's repeated solves): the
+// planning pass over a 20,000-problem group takes several milliseconds while the device
+// idles.  A call takes the plan out of the cache for its duration, so concurrent calls
+// never share one; the key is compared byte for byte.
+struct PlanCache {
+  std::mutex mu;
+  std::vector<uint8_t> key;
+  std::unique_ptr<GroupPlan> plan;
+};
+PlanCache g_plan_cache;
+
+std::vector<uint8_t> plan_key(int count, int cplx, int form, const int64_t* n,
+                              const double* const* theta, const double* const* delta,
+                              const int64_t* ld_delta, const double* lambda,
+                              double* const* A_out, const int64_t* ld_a,
+                              double* const* E_out) {
+  const int head[3] = {count, cplx, form};
+  const size_t per = (size_t)count * 8;
+  std::vector<uint8_t> k(sizeof(head) + 9 * per);
+  uint8_t* q = k.data();
+  std::memcpy(q, head, sizeof(head));
+  q += sizeof(head);
+  const void* arrays[9] = {n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, nullptr};
+  for (int a = 0; a < 8; ++a, q += per) std::memcpy(q, arrays[a], per);
+  return k;
+}
+
 dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* const* theta,
                          const double* const* delta, const int64_t* ld_delta,
                          const double* lambda, const dpt_options& o, double* const* A_out,
@@ -1536,9 +1565,30 @@ dpt_status solve_batched(int count, int cplx, const int64_t* n, const double* co
   int npairs = 0;
   const int form = choose_gform(o.grouped_form, count, n, &npairs);
   const bool pair = form == G_PAIR;
-  GroupPlan g;
-  plan_group(g, count, cplx, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, nullptr, nullptr,
-             form);
+  std::vector<uint8_t> key =
+      plan_key(count, cplx, form, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out);
+  std::unique_ptr<GroupPlan> gp;
+  {
+    std::lock_guard<std::mutex> lk(g_plan_cache.mu);
+    if (g_plan_cache.plan && g_plan_cache.key == key) gp = std::move(g_plan_cache.plan);
+  }
+  if (!gp) {
+    gp = std::make_unique<GroupPlan>();
+    plan_group(*gp, count, cplx, n, theta, delta, ld_delta, lambda, A_out, ld_a, E_out, nullptr,
+               nullptr, form);
+  }
+  // back into the cache when the call ends, however it ends (place_group below
+  // rewrites every placement-dependent field on the next use)
+  struct PutBack {
+    std::vector<uint8_t>& key;
+    std::unique_ptr<GroupPlan>& gp;
+    ~PutBack() {
+      std::lock_guard<std::mutex> lk(g_plan_cache.mu);
+      g_plan_cache.key = std::move(key);
+      g_plan_cache.plan = std::move(gp);
+    }
+  } put_back{key, gp};
+  GroupPlan& g = *gp;
   const size_t arena = g.bytes;
   auto layout = [&](Carve& c) { layout_batched(c, count, g); };
   Block* b = acquire(measure(layout));
@@ -2151,6 +2201,12 @@ dpt_status dpt_probe_gather(int64_t n, const int32_t* row_ptr, const int32_t* co
 }
 
 void dpt_release_workspace(void) {
+  {
+    std::lock_guard<std::mutex> lk(g_plan_cache.mu);
+    g_plan_cache.key.clear();
+    g_plan_cache.key.shrink_to_fit();
+    g_plan_cache.plan.reset();
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   int dev = -1;
   cudaGetDevice(&dev);

@@ -133,3 +133,38 @@ def test_tuner_keeps_the_fastest_tile_shape(ora, dpt):
         Ao, Eo, io = ora.solve_full(p["theta"], p["delta"], p["lam"], tol=1e-13)
         assert eig_err(to_np(Es[q]), Eo) <= EIG_RTOL
         assert vec_err(to_np(As[q]), Ao) <= VEC_TOL
+
+
+def test_repeated_batch_reuses_its_plan(dpt):
+    """A Batch solved again reuses the library's cached plan of the group (same problems,
+    pointers and form); another group in between replaces the cache, and inputs changed
+    in place are read afresh.  Every result equals a fresh call's bit for bit."""
+
+    def group(sizes, seed):
+        r = np.random.Generator(np.random.PCG64(seed))
+        return [{"theta": np.arange(n, dtype=float) + r.uniform(-0.2, 0.2, n),
+                 "delta": inputs.symmetric_gaussian(n, 1.0 / n, r),
+                 "lam": float(r.uniform(0.01, 0.1))} for n in sizes]
+
+    pa = group([5, 40, 130, 257], 1)
+    pb = group([7, 64, 200], 2)
+    tha, Da = _dev(pa, dpt)
+    thb, Db = _dev(pb, dpt)
+    ba = dpt.Batch(tha, Da, [p["lam"] for p in pa])
+    bb = dpt.Batch(thb, Db, [p["lam"] for p in pb])
+    A1 = [a.clone() for a in ba.solve()[0]]
+    A2 = [a.clone() for a in ba.solve()[0]]            # the cached plan
+    Bb = [a.clone() for a in bb.solve()[0]]            # another group replaces it
+    A3 = [a.clone() for a in ba.solve()[0]]            # planned again
+    for x, y, z in zip(A1, A2, A3):
+        assert torch.equal(x, y) and torch.equal(x, z)
+    fresh = dpt.solve_batched(thb, Db, [p["lam"] for p in pb])[0]
+    for x, y in zip(Bb, fresh):
+        assert torch.equal(x, y)
+    # new values in the same buffers: the cached plan reads them afresh
+    Da[1].mul_(0.5)
+    A4 = ba.solve()[0]
+    ref = dpt.solve_batched(tha, Da, [p["lam"] for p in pa])[0]
+    assert not torch.equal(A4[1], A1[1])
+    for x, y in zip(A4, ref):
+        assert torch.equal(x, y)
