@@ -46,6 +46,11 @@ struct Block {
   IterState* host_state = nullptr;   // pinned
   cudaStream_t stream = nullptr;     // internal non-blocking stream
   cudaEvent_t ev = nullptr;
+  // the instantiated iteration graph of the last mixed full solve that used this block,
+  // with the bytes of every argument its launches were captured with (the same solve
+  // on the same buffers replays it without capturing and instantiating it again)
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<uint8_t> gkey;
 };
 
 std::mutex g_mu;
@@ -239,15 +244,22 @@ struct Prof {
 // kernel that acts only once the state has left ST_RUNNING), so that the chunk in
 // which the iteration stops also produces the outputs without another host round
 // trip; tail_launches counts its kernels.
+// key: when given (and nothing is profiled), the graph is kept in the block with these
+// bytes and replayed by a later call whose key is the same; key must hold every
+// argument the captured launches read on the host.
 template <class F>
 void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kernels_per_iter,
               Prof& prof, F&& iter, size_t state_bytes = sizeof(IterState), int k_first = -1,
-              const std::function<void()>& tail = nullptr, int tail_launches = 0) {
+              const std::function<void()>& tail = nullptr, int tail_launches = 0,
+              const std::vector<uint8_t>* key = nullptr) {
   cudaStream_t s = b->stream;
   const int per = graph_iters > 0 ? graph_iters : 4;
   prof.make(per);
   cudaGraphExec_t exec = nullptr;
-  if (graph_iters > 0) {
+  const bool cache = key && graph_iters > 0 && !prof.on;
+  if (cache && b->gexec && b->gkey == *key) {
+    exec = b->gexec;
+  } else if (graph_iters > 0) {
     cudaGraph_t g;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int q = 0; q < per; ++q) iter(q);
@@ -256,7 +268,13 @@ void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kerne
     cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) throw Fail{DPT_ERR_CUDA};
+    if (cache) {
+      if (b->gexec) cudaGraphExecDestroy(b->gexec);
+      b->gexec = exec;
+      b->gkey = *key;
+    }
   }
+  const bool owned = exec && !(cache && exec == b->gexec);
   const int max_chunks = max_iter / per + 2;
   try {
     for (int c = 0; c < max_chunks; ++c) {
@@ -275,10 +293,10 @@ void run_loop(Block* b, IterState* dst, int graph_iters, int max_iter, int kerne
       if (!running) break;
     }
   } catch (...) {
-    if (exec) cudaGraphExecDestroy(exec);
+    if (owned) cudaGraphExecDestroy(exec);
     throw;
   }
-  if (exec) cudaGraphExecDestroy(exec);
+  if (owned) cudaGraphExecDestroy(exec);
 }
 
 struct Timer {
@@ -576,7 +594,8 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     const int bn = pair ? mixed_pair_tile_n((int)n, npairs, ctas) : mixed_tile_n((int)n, nsm);
     const CUtensorMap tB0 = make_tmap_f16(dtb[0], n, n, ld, pair ? bn / 2 : bn);
     const CUtensorMap tB1 = make_tmap_f16(dtb[1], n, n, ld, pair ? bn / 2 : bn);
-    GemmEpiParams p{};
+    GemmEpiParams p;
+    std::memset(&p, 0, sizeof(p));   // padding too: the bytes are part of the graph key
     p.n = n; p.ld = ld; p.ntm = ntm; p.bn = bn; p.lam = (float)lambda;
     for (int q = 0; q < 2; ++q) { p.A_hi[q] = Ahi[q]; p.A_lo[q] = Alo[q]; p.dt[q] = dtb[q]; }
     p.L = L; p.Dcat = Dcat; p.cat_ld = (int64_t)3 * ld; p.th_hi = thh; p.th_lo = thl; p.e_col = e_col; p.dprev_col = dprev;
@@ -599,13 +618,27 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
         if (e_dev)
           CK(cudaMemcpyAsync(E_out, E, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
       };
+      // every host value the captured launches read (the parameter block, the tensor
+      // maps, the form, the control and output kernels' arguments)
+      std::vector<uint8_t> key;
+      auto put = [&key](const void* v, size_t nb) {
+        const uint8_t* c = static_cast<const uint8_t*>(v);
+        key.insert(key.end(), c, c + nb);
+      };
+      put(&p, sizeof(p));
+      put(&tA, sizeof(tA)); put(&tB0, sizeof(tB0)); put(&tB1, sizeof(tB1));
+      const int64_t scal[7] = {n, ld, npairs, ctas, pair ? 1 : 0, e_dev ? 1 : 0, o.graph_iters};
+      put(scal, sizeof(scal));
+      const void* ptrs[12] = {part, rowpart, thd, d, E, e_col, dprev, st, Astage, E_out,
+                              dtb[0], reinterpret_cast<const void*>(lda_dev)};
+      put(ptrs, sizeof(ptrs));
       run_loop(b, st, o.graph_iters, o.max_iter, 2, prof, [&](int q) {
         prof.before(q, s);
         if (pair) CK(launch_gemm_epi_pair(tA, tB0, tB1, p, npairs, ctas, s));
         else CK(launch_gemm_epi(tA, tB0, tB1, p, s));
         prof.after(q, s);
         CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
-      }, sizeof(IterState), /*k_first=*/1, tail, 1);   // the control after iteration 0 set k = 1
+      }, sizeof(IterState), /*k_first=*/1, tail, 1, &key);   // the control after iteration 0 set k = 1
     }
     // columns the mixed arithmetic cannot vouch for are finished in FP64 (the state
     // read after the last chunk is the final one)
@@ -2213,6 +2246,7 @@ void dpt_release_workspace(void) {
   std::vector<Block*> keep;
   for (Block* b : g_pool) {
     if (b->dev == dev && !b->busy) {
+      if (b->gexec) cudaGraphExecDestroy(b->gexec);
       if (b->ptr) cudaFree(b->ptr);
       if (b->host_state) cudaFreeHost(b->host_state);
       if (b->stream) cudaStreamDestroy(b->stream);

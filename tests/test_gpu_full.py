@@ -252,6 +252,43 @@ def test_repeated_solves_identical(dpt):
     assert torch.equal(A1, A2) and torch.equal(E1, E2)
 
 
+def test_prepared_solve_replays_its_graph(dpt):
+    """A prepared solve called again replays the iteration graph kept with its workspace
+    (same buffers, form and parameters); another problem, another lambda or another
+    chunk size in between capture a new one, and inputs changed in place are read
+    afresh.  Each result equals that of a fresh call (new output buffers, so a new
+    graph) bit for bit."""
+    cfg = inputs.full_unsymmetric(n=300)
+    th, D = _dev(cfg)
+    fs = dpt.FullSolve(th, D, cfg["lam"], prec="mixed", tol=1e-12)
+
+    def fresh(lam=cfg["lam"], **kw):
+        return dpt.solve_full(th, D, lam, prec="mixed", tol=1e-12, **kw)
+
+    fs.solve()
+    A1 = fs.A.clone()
+    fs.solve()                                        # replayed
+    assert torch.equal(fs.A, A1)
+    other = inputs.full_symmetric(n=333)
+    dpt.solve_full(*_dev(other), other["lam"])        # another problem, same pool
+    fs.solve()
+    assert torch.equal(fs.A, A1)
+    assert torch.equal(fresh()[0], A1)
+    fs2 = dpt.FullSolve(th, D, 0.5 * cfg["lam"], prec="mixed", tol=1e-12, A_out=fs.A,
+                        E_out=fs.E)                   # another lambda, same outputs
+    fs2.solve()
+    assert torch.equal(fs.A, fresh(0.5 * cfg["lam"])[0])
+    fs3 = dpt.FullSolve(th, D, cfg["lam"], prec="mixed", tol=1e-12, graph_iters=2,
+                        A_out=fs.A, E_out=fs.E)       # another chunk size
+    fs3.solve()
+    assert torch.equal(fs.A, A1)
+    D.mul_(0.5)                                       # new values in the same buffer
+    fs.solve()
+    ref = fresh()[0]
+    assert not torch.equal(ref, A1)
+    assert torch.equal(fs.A, ref)
+
+
 @pytest.mark.parametrize("graph_iters", [0, 1, 2, 3, 4, 5, 7])
 def test_profiled_solves_any_chunk_size(dpt, graph_iters):
     """Per-launch profiling with every chunk size, including chunks that end exactly at
