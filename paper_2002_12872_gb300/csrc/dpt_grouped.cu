@@ -279,14 +279,31 @@ __global__ void __launch_bounds__(128) k_g_iter0(const GProb* __restrict__ probs
   const int64_t ld_in = P->ld_in;
   float rowabs[4] = {0.f, 0.f, 0.f, 0.f};
   float mx = 0.f;
-  for (int c = 0; c < 32; ++c) {
-    const int i = n0 + 32 * w + c;
-    if (i >= n) break;
-    const float thi_h = P->th_hi[i], thi_l = P->th_lo[i];
+  // the warp's columns, each one's loads issued while the one before is computed
+  const int cend = min(32, n - (n0 + 32 * w));
+  float nth_h = 0.f, nth_l = 0.f;
+  uint2 nD[3];
+  double nv[4];
+  auto fetch = [&](int i) {
+    nth_h = P->th_hi[i];
+    nth_l = P->th_lo[i];
     const __half* Drow = P->Dcat + (int64_t)i * cat_ld + j0;
-    uint2 D[3];
 #pragma unroll
-    for (int sl = 0; sl < 3; ++sl) D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+    for (int sl = 0; sl < 3; ++sl) nD[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) nv[e] = (j0 + e < n) ? delta[(int64_t)i * ld_in + j0 + e] : 0.0;
+  };
+  if (cend > 0) fetch(n0 + 32 * w);
+  for (int c = 0; c < cend; ++c) {
+    const int i = n0 + 32 * w + c;
+    const float thi_h = nth_h, thi_l = nth_l;
+    uint2 D[3];
+    double vv[4];
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) D[sl] = nD[sl];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) vv[e] = nv[e];
+    if (c + 1 < cend) fetch(i + 1);
     float4 oh, oL;
     uint32_t ob[4] = {0u, 0u, 0u, 0u};
     float r2 = 0.f, a2 = 0.f, eh = 0.f, el = 0.f;
@@ -295,9 +312,9 @@ __global__ void __launch_bounds__(128) k_g_iter0(const GProb* __restrict__ probs
       const int j = j0 + e;
       float nh = 0.f, Ln = 0.f, dtn = 0.f;
       if (j < n) {
-        const double v = delta[(int64_t)i * ld_in + j];
+        const double v = vv[e];
         float vh, vl;
-        split_double(v, vh, vl);
+        split_double_fast(v, vh, vl);   // |v| < 2^128: checked by the slicing
         rowabs[e] += fabsf(vh);
         if (j == i) {
           nh = 1.f;
@@ -465,15 +482,33 @@ __global__ void __launch_bounds__(128) k_gc_iter0(const GProb* __restrict__ prob
   }
   float rowabs[2] = {0.f, 0.f};
   float mx = 0.f;
-  for (int c = 0; c < 32; ++c) {
-    const int i = n0 + 32 * w + c;
-    if (i >= n) break;
-    const float thi_h = P->th_hi[i], thi_l = P->th_lo[i];
+  // the warp's columns, each one's loads issued while the one before is computed
+  const int cend = min(32, n - (n0 + 32 * w));
+  float nth_h = 0.f, nth_l = 0.f;
+  uint2 nD[3];
+  double2 nv[2];
+  auto fetch = [&](int i) {
+    nth_h = P->th_hi[i];
+    nth_l = P->th_lo[i];
     // Delta(i, jc0..jc0+1) from embedded row 2i: (Re, -Im) pairs
     const __half* Drow = P->Dcat + (int64_t)(2 * i) * cat_ld + 2 * jc0;
-    uint2 D[3];
 #pragma unroll
-    for (int sl = 0; sl < 3; ++sl) D[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+    for (int sl = 0; sl < 3; ++sl) nD[sl] = *reinterpret_cast<const uint2*>(Drow + (int64_t)sl * ld);
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+      nv[e] = (jc0 + e < n) ? delta[(int64_t)i * ld_in + jc0 + e] : make_double2(0.0, 0.0);
+  };
+  if (cend > 0) fetch(n0 + 32 * w);
+  for (int c = 0; c < cend; ++c) {
+    const int i = n0 + 32 * w + c;
+    const float thi_h = nth_h, thi_l = nth_l;
+    uint2 D[3];
+    double2 vv[2];
+#pragma unroll
+    for (int sl = 0; sl < 3; ++sl) D[sl] = nD[sl];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) vv[e] = nv[e];
+    if (c + 1 < cend) fetch(i + 1);
     float oh[4], oL[4];
     uint32_t ob[4] = {0u, 0u, 0u, 0u};
     float r2 = 0.f, a2 = 0.f, erh = 0.f, erl = 0.f, eih = 0.f, eil = 0.f;
@@ -482,10 +517,10 @@ __global__ void __launch_bounds__(128) k_gc_iter0(const GProb* __restrict__ prob
       const int j = jc0 + e;
       float dn[2] = {0.f, 0.f}, L2[2] = {0.f, 0.f}, A2[2] = {0.f, 0.f};
       if (j < n) {
-        const double2 v = delta[(int64_t)i * ld_in + j];
+        const double2 v = vv[e];
         float vh[2], vl[2];
-        split_double(v.x, vh[0], vl[0]);
-        split_double(v.y, vh[1], vl[1]);
+        split_double_fast(v.x, vh[0], vl[0]);   // |v| < 2^128: checked by the slicing
+        split_double_fast(v.y, vh[1], vl[1]);
         rowabs[e] += sqrtf(vh[0] * vh[0] + vh[1] * vh[1]);
         if (j == i) {
           A2[0] = 1.f;
