@@ -45,7 +45,6 @@ constexpr int G_NTHREADS = 64 + 32 * G_EPI_WARPS;
 constexpr int G_XCH = 32;
 constexpr int G_SMEM_TILES = G_STAGES * (G_A_TILE + G_B_TILE);
 constexpr int G_SMEM_X = G_BM * G_XCH * 4;
-constexpr int G_NSLICE = 3;
 
 struct __align__(16) GSmem {
   uint64_t full[G_STAGES];
