@@ -40,7 +40,7 @@ PROFILE = os.path.join(ROOT, "profiles", "k_gemm_epi_pair_n4096.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2002_12872_gb300", "csrc", "dpt_full_mixed.cu")
 
 
-STREAMS = 2   # default: independent solve streams per GPU in the timed throughput region
+STREAMS = 3   # default: independent solve streams per GPU in the timed throughput regions
 
 
 def parse_args():
