@@ -564,14 +564,14 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     CK(cudaMemcpyAsync(st, b->host_state, sizeof(IterState), cudaMemcpyHostToDevice, s));
     if (th.empty()) {
       thd = const_cast<double*>(theta_dev);   // read in place, never written
-      CK(launch_check_theta(n, thd, st, s));
+      CK(launch_check_theta(n, thd, st, s, thh, thl));   // also the float-float split
     } else {
       CK(cudaMemcpyAsync(thd, th.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      CK(launch_theta_ff(n, thd, thh, thl, s));
     }
     // no clearing of the increment buffers: iteration 0 writes all ld rows of dt_0,
     // every product writes all ld rows of its dt_k before any read, and the operand
     // tensor maps stop at row n (rows beyond read as zero)
-    CK(launch_theta_ff(n, thd, thh, thl, s));
     CK(launch_delta_scales(delta, ldd, n, thh, thl, lambda, o.epstein_nesbet, sdev, ld_s, sinv,
                            st, s));
     // Iteration 0 and the slicing in one pass over pairs of mirrored tiles (Delta read
@@ -607,8 +607,9 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     // state buffer may still be the source of the pending upload above: not touched)
     Prof prof;
     prof.on = o.profile != 0;
-    // (theta check,) theta split, scales, (slicing,) iteration 0, control
-    prof.launches = (th.empty() ? 6 : 5) - (fused0 ? 1 : 0);
+    // theta check with the split (or the split alone), scales, (slicing,) iteration 0,
+    // control
+    prof.launches = fused0 ? 4 : 5;
     {
       // the outputs are formed inside the chunk in which the iteration stops (the
       // output kernel does nothing while the state is still running)
@@ -637,7 +638,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
         if (pair) CK(launch_gemm_epi_pair(tA, tB0, tB1, p, npairs, ctas, s));
         else CK(launch_gemm_epi(tA, tB0, tB1, p, s));
         prof.after(q, s);
-        CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
+        CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s, 0, pair ? 0 : 1));
       }, sizeof(IterState), /*k_first=*/1, tail, 1, &key);   // the control after iteration 0 set k = 1
     }
     // columns the mixed arithmetic cannot vouch for are finished in FP64 (the state

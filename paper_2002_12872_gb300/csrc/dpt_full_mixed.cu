@@ -869,7 +869,8 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
                                               const double* __restrict__ theta,
                                               double* __restrict__ d, double* __restrict__ E,
                                               float* __restrict__ e_col,
-                                              float* __restrict__ dprev_col, IterState* st) {
+                                              float* __restrict__ dprev_col, IterState* st,
+                                              int hilo) {
   if (st->status != ST_RUNNING) return;
   // 32 columns per block, 8 threads per column each summing every 8th tile partial
   // (short chains of independent loads: the partials were just written, in L2)
@@ -887,15 +888,26 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
     float r2 = 0.f, a2 = 0.f, rs = 0.f;
     double ep = 0.0;
     if (i < n) {
+      if (first || hilo) {
 #pragma unroll 4
-      for (int t = g; t < ntm; t += 8) {
-        r2 += part[((int64_t)0 * ntm + t) * ld + i];
-        a2 += part[((int64_t)1 * ntm + t) * ld + i];
-        ep += (double)part[((int64_t)2 * ntm + t) * ld + i] +
-              (double)part[((int64_t)3 * ntm + t) * ld + i];
+        for (int t = g; t < ntm; t += 8) {
+          r2 += part[((int64_t)0 * ntm + t) * ld + i];
+          a2 += part[((int64_t)1 * ntm + t) * ld + i];
+          ep += (double)part[((int64_t)2 * ntm + t) * ld + i] +
+                (double)part[((int64_t)3 * ntm + t) * ld + i];
+        }
+        if (first)
+          for (int t = g; t < ntn; t += 8) rs += rowpart[(int64_t)t * ld + i];
+      } else {
+        // the pair kernel's diagonal partials are plain floats (their low parts are
+        // zero, and x + 0 = x): one conversion and one FP64 add per partial
+#pragma unroll 4
+        for (int t = g; t < ntm; t += 8) {
+          r2 += part[((int64_t)0 * ntm + t) * ld + i];
+          a2 += part[((int64_t)1 * ntm + t) * ld + i];
+          ep += (double)part[((int64_t)2 * ntm + t) * ld + i];
+        }
       }
-      if (first)
-        for (int t = g; t < ntn; t += 8) rs += rowpart[(int64_t)t * ld + i];
     }
     sh[0][g][c] = r2; sh[1][g][c] = a2; sh[2][g][c] = rs; she[g][c] = ep;
   }
@@ -1949,8 +1961,11 @@ __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __
 // thread i compares theta_i with those j > i.
 // (eq_key: 64-bit integer equality keys of finite doubles, dpt_device.cuh)
 
+// The diagonal blocks also split theta into float-float (hi, lo), as k_theta_ff does, when
+// hi is given (one launch less for a device theta).
 __global__ void __launch_bounds__(256) k_check_theta(int n, const double* __restrict__ th,
-                                                     IterState* st) {
+                                                     IterState* st, float* __restrict__ hi,
+                                                     float* __restrict__ lo) {
   if (blockIdx.y < blockIdx.x) return;
   __shared__ unsigned long long tj[256];
   const int i = blockIdx.x * 256 + threadIdx.x;
@@ -1961,6 +1976,11 @@ __global__ void __launch_bounds__(256) k_check_theta(int n, const double* __rest
   double amax = 0.0;
   if (i < n) {
     const double ti = th[i];
+    if (hi && blockIdx.y == blockIdx.x) {
+      const float h = (float)ti;
+      hi[i] = h;
+      lo[i] = (float)(ti - (double)h);
+    }
     if (!finite_bits(ti)) {
       if (blockIdx.y == blockIdx.x) atomicCAS(&st->status, ST_RUNNING, ST_BADINPUT);
     } else {
@@ -2050,8 +2070,9 @@ cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld,
   return cudaGetLastError();
 }
 
-cudaError_t launch_check_theta(int n, const double* th, IterState* st, cudaStream_t s) {
-  k_check_theta<<<dim3((n + 255) / 256, (n + 255) / 256), 256, 0, s>>>(n, th, st);
+cudaError_t launch_check_theta(int n, const double* th, IterState* st, cudaStream_t s, float* hi,
+                               float* lo) {
+  k_check_theta<<<dim3((n + 255) / 256, (n + 255) / 256), 256, 0, s>>>(n, th, st, hi, lo);
   return cudaGetLastError();
 }
 
@@ -2115,14 +2136,14 @@ cudaError_t launch_iter0_pairs(const CUtensorMap& tmD, const float* th_hi, const
 
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,
-                        float* dprev_col, IterState* st, cudaStream_t s, int nslot) {
+                        float* dprev_col, IterState* st, cudaStream_t s, int nslot, int hilo) {
   // column partials: one per 128-row tile of the product, or nslot of them (the fused
   // iteration 0's 64-row slots); row partials: one per block of kIter0Cols columns of
   // iteration 0
   const int ntm = nslot > 0 ? nslot : (n + BM - 1) / BM;
   const int ntn = (n + kIter0Cols - 1) / kIter0Cols;
   k_ctrl<<<(n + 31) / 32, 256, 0, s>>>(n, ld, ntm, ntn, part, rowpart, theta, d, E, e_col,
-                                       dprev_col, st);
+                                       dprev_col, st, hilo);
   return cudaGetLastError();
 }
 

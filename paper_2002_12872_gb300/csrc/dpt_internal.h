@@ -230,7 +230,9 @@ cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld,
                               __half* Dcat, IterState* st, cudaStream_t s);
 cudaError_t launch_theta_ff(int n, const double* th, float* hi, float* lo, cudaStream_t s);
 // finite and pairwise distinct theta (status ST_BADINPUT / ST_DEGENERATE), max |theta|
-cudaError_t launch_check_theta(int n, const double* th, IterState* st, cudaStream_t s);
+// (hi, lo given: theta split into float-float as launch_theta_ff does, in the same launch)
+cudaError_t launch_check_theta(int n, const double* th, IterState* st, cudaStream_t s,
+                               float* hi = nullptr, float* lo = nullptr);
 // iteration 0 from A_0 = I: dt_0 = f16(r_0 G o R_0), or with a start its offset from I
 cudaError_t launch_iter0(const double* delta, int64_t ld_in, const float* th_hi,
                          const float* th_lo, double lam, int n, int ld, int en, int nsl,
@@ -244,10 +246,12 @@ cudaError_t launch_iter0_pairs(const CUtensorMap& tmD, const float* th_hi, const
                                double lam, int n, int ld, int en, int nsl, __half* Dcat,
                                __half* dt0, float* L, double* d, float* part, float* rowpart,
                                IterState* st, cudaStream_t s);
-// nslot > 0: the column partials are in nslot row slots (else one per 128-row tile)
+// nslot > 0: the column partials are in nslot row slots (else one per 128-row tile);
+// hilo = 0: the products' diagonal partials have zero low parts (the pair kernel's)
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,
-                        float* dprev_col, IterState* st, cudaStream_t s, int nslot = 0);
+                        float* dprev_col, IterState* st, cudaStream_t s, int nslot = 0,
+                        int hilo = 1);
 cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
                             const CUtensorMap& tmB1, const GemmEpiParams& p, cudaStream_t s);
 // The returned iterate in FP64 (A_1 = I + dt_0 is formed from the first increment dt0).
