@@ -155,6 +155,14 @@ __device__ __forceinline__ float abs_from_hiword(unsigned hw) {
   return (e > 896u && e < 1151u) ? __uint_as_float(((e - 896u) << 23) | ((hw & 0xFFFFFu) << 3))
                                  : (e >= 1151u ? __int_as_float(0x7f800000) : 0.f);
 }
+// The same in two integer operations: the high word clamped to [2^-127, 2^128] (the
+// clamp drops the fraction at the top, giving +inf) and rebiased from 1023 to 127 in
+// the wrapping 32-bit product (896 = 512 + 384; 384 << 23 = 0xC0000000).  It differs
+// from abs_from_hiword only in [2^-127, 2^-126), which it keeps as subnormals.
+__device__ __forceinline__ float abs_from_hiword_clamped(unsigned hw) {
+  const unsigned c = min(max(hw, 896u << 20), 1151u << 20);
+  return __uint_as_float(c * 8u + 0x40000000u);
+}
 
 // The scale pass without a start.  Thread per row j (theta_j in registers); a work
 // item is 256 rows x 8 columns, eight loads in flight per thread (a warp reads 256
@@ -175,7 +183,7 @@ __device__ __forceinline__ void scale_entry(unsigned hw, float tih, float til, f
   if (g == 0.f) g = til - tjl;
   // NaN never wins fmaxf
   const float rg = rcp_approx(fabsf(g));
-  gmax = fmaxf(gmax, abs_from_hiword(hw) * rg);
+  gmax = fmaxf(gmax, abs_from_hiword_clamped(hw) * rg);
   rgmax = fmaxf(rgmax, rg);
 }
 __global__ void __launch_bounds__(256) k_delta_scales_rows(const double* __restrict__ delta,
@@ -186,21 +194,36 @@ __global__ void __launch_bounds__(256) k_delta_scales_rows(const double* __restr
                                                            int en, IterState* st) {
   unsigned hmax = 0u;
   float gmax = 0.f, rgmax = 0.f;
+  // a full item away from the diagonal takes the fast path; its loads are issued one
+  // item ahead, so that they are in flight while the previous item is processed
+  auto full_item = [&](int it) {
+    const int j = (it % nrb) * 256 + threadIdx.x, i0 = (it / nrb) * kScaleCols;
+    return j < n && i0 + kScaleCols <= n && (unsigned)(j - i0) >= (unsigned)kScaleCols;
+  };
+  double v[kScaleCols];
+  auto fetch = [&](int it) {
+    if (it < nitems && full_item(it)) {
+      const int j = (it % nrb) * 256 + threadIdx.x, i0 = (it / nrb) * kScaleCols;
+      const double* p = delta + (int64_t)i0 * ld_in + j;
+#pragma unroll
+      for (int u = 0; u < kScaleCols; ++u) v[u] = p[(int64_t)u * ld_in];
+    }
+  };
+  fetch(blockIdx.x);
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int rb = it % nrb, cb = it / nrb;
     const int j = rb * 256 + threadIdx.x, i0 = cb * kScaleCols;
-    if (j >= n) continue;
+    if (j >= n) {   // a ragged row block (a later item may hold rows of this thread)
+      fetch(it + gridDim.x);
+      continue;
+    }
     const float tjh = th_hi[j], tjl = th_lo[j];
-    const double* p = delta + (int64_t)i0 * ld_in + j;
-    const int nc = min(kScaleCols, n - i0);
-    if (nc == kScaleCols && (unsigned)(j - i0) >= (unsigned)kScaleCols) {
-      // a full item away from the diagonal
-      double v[kScaleCols];
+    if (full_item(it)) {
+      unsigned hw[kScaleCols];
 #pragma unroll
-      for (int u = 0; u < kScaleCols; ++u) {
-        v[u] = *p;
-        p += ld_in;
-      }
+      for (int u = 0; u < kScaleCols; ++u)
+        hw[u] = (unsigned)__double2hiint(v[u]) & 0x7FFFFFFFu;
+      fetch(it + gridDim.x);
       float tih[kScaleCols], til[kScaleCols];
 #pragma unroll
       for (int u = 0; u < kScaleCols; u += 4) {
@@ -211,10 +234,11 @@ __global__ void __launch_bounds__(256) k_delta_scales_rows(const double* __restr
       }
 #pragma unroll
       for (int u = 0; u < kScaleCols; ++u)
-        scale_entry((unsigned)__double2hiint(v[u]) & 0x7FFFFFFFu, tih[u], til[u], tjh, tjl,
-                    hmax, gmax, rgmax);
+        scale_entry(hw[u], tih[u], til[u], tjh, tjl, hmax, gmax, rgmax);
     } else {
+      fetch(it + gridDim.x);
       // the ragged last item, or the one holding the diagonal entry of row j
+      const int nc = min(kScaleCols, n - i0);
       for (int u = 0; u < nc; ++u) {
         const int i = i0 + u;
         const unsigned hw = (unsigned)__double2hiint(delta[(int64_t)i * ld_in + j]) & 0x7FFFFFFFu;
@@ -2038,17 +2062,22 @@ cudaError_t launch_delta_scales(const double* delta, int64_t ld_in, int n, const
                                 int64_t ld_s, double* sinv, IterState* st, cudaStream_t s) {
   (void)lam;   // read from the state
   if (!start) {
-    static int nsm = 0;
+    // one wave of resident blocks (the items are strided over it)
+    static int nsm = 0, per_sm = 0;
     if (nsm == 0) {
-      int dev = 0;
+      int dev = 0, ns = 0, occ = 0;
       cudaError_t e = cudaGetDevice(&dev);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_delta_scales_rows, 256, 0);
       if (e != cudaSuccess) return e;
+      per_sm = std::max(1, std::min(occ, 6));
+      nsm = ns;
     }
     const int nrb = (n + 255) / 256, ncb = (n + kScaleCols - 1) / kScaleCols;
     const long long items = (long long)nrb * ncb;
     if (items > INT_MAX) return cudaErrorInvalidValue;
-    const int grid = (int)std::min<long long>(items, 6LL * nsm);
+    const int grid = (int)std::min<long long>(items, (long long)per_sm * nsm);
     k_delta_scales_rows<<<grid, 256, 0, s>>>(delta, ld_in, n, nrb, (int)items, th_hi, th_lo, en,
                                              st);
     return cudaGetLastError();
