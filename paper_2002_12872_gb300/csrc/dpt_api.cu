@@ -582,12 +582,12 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
       const CUtensorMap tD = make_tmap_f64(delta, n, n, ldd);
       CK(launch_iter0_pairs(tD, thh, thl, lambda, n, ld, o.epstein_nesbet, S, Dcat, dtb[0], L,
                             d, part, rowpart, st, s));
-      CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s, ld / 64));
+      CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s, ld / 64, 1, 1));
     } else {
       CK(launch_prep_delta(delta, ldd, n, ld, o.epstein_nesbet, S, Dcat, st, s));
       CK(launch_iter0(delta, ldd, thh, thl, lambda, n, ld, o.epstein_nesbet, S, Dcat, dtb[0],
                       L, d, part, rowpart, sdev, ld_s, sinv, st, s));
-      CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s));
+      CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s, 0, 1, 1));
     }
 
     const CUtensorMap tA = make_tmap_f16(Dcat, (uint64_t)3 * ld, n, (uint64_t)3 * ld, 128);
@@ -638,7 +638,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
         if (pair) CK(launch_gemm_epi_pair(tA, tB0, tB1, p, npairs, ctas, s));
         else CK(launch_gemm_epi(tA, tB0, tB1, p, s));
         prof.after(q, s);
-        CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s, 0, pair ? 0 : 1));
+        CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s, 0, pair ? 0 : 1, 0));
       }, sizeof(IterState), /*k_first=*/1, tail, 1, &key);   // the control after iteration 0 set k = 1
     }
     // columns the mixed arithmetic cannot vouch for are finished in FP64 (the state

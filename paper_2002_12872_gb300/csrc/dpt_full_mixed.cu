@@ -894,20 +894,16 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
                                               double* __restrict__ d, double* __restrict__ E,
                                               float* __restrict__ e_col,
                                               float* __restrict__ dprev_col, IterState* st,
-                                              int hilo) {
-  if (st->status != ST_RUNNING) return;
+                                              int hilo, int first_step) {
   // 32 columns per block, 8 threads per column each summing every 8th tile partial
-  // (short chains of independent loads: the partials were just written, in L2)
+  // (short chains of independent loads: the partials were just written, in L2).  The
+  // loads depend on nothing in the state (first_step: this control follows iteration
+  // 0), so they are issued before the state is read; the status test follows them.
   __shared__ float sh[3][8][32];
   __shared__ double she[8][32];
   const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
   const int i = blockIdx.x * 32 + c;
-  const bool first = (st->k == 0);
-  // after a certifying product only its residual norms are valid: the iterate, d and
-  // the column parameters of the next product stay as they are
-  const bool cert = st->certify != 0;
-  // the diagonal partials are of Delta 2^sig dt (FP16 slices): exact rescaling
-  const double isg = (double)exp2i(-st->sig);
+  const bool first = first_step != 0;
   {
     float r2 = 0.f, a2 = 0.f, rs = 0.f;
     double ep = 0.0;
@@ -935,6 +931,12 @@ __global__ void __launch_bounds__(256) k_ctrl(int n, int ld, int ntm, int ntn,
     }
     sh[0][g][c] = r2; sh[1][g][c] = a2; sh[2][g][c] = rs; she[g][c] = ep;
   }
+  if (st->status != ST_RUNNING) return;   // the same for every thread of the launch
+  // after a certifying product only its residual norms are valid: the iterate, d and
+  // the column parameters of the next product stay as they are
+  const bool cert = st->certify != 0;
+  // the diagonal partials are of Delta 2^sig dt (FP16 slices): exact rescaling
+  const double isg = (double)exp2i(-st->sig);
   __syncthreads();
   float rho_raw = 0.f;
   if (g == 0 && i < n) {
@@ -1935,8 +1937,8 @@ k_gemm_epi_quad(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 // ---------------------------------------------------------------------------
 // Output: A (float-float -> FP64) and E of the returned iterate.
 // ---------------------------------------------------------------------------
-// Output: grid (128-row tiles, 32-column tiles); thread j owns row j of the tile
-// and issues the loads of eight columns before their stores.
+// Output: tiles of 128 rows x 32 columns, strided over a grid of one wave; thread j
+// owns row j of the tile and issues the loads of eight columns before their stores.
 __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __restrict__ Ahi0,
                                                   const float* __restrict__ Alo0,
                                                   const float* __restrict__ Ahi1,
@@ -1944,80 +1946,92 @@ __global__ void __launch_bounds__(128) k_finalize(int n, int ld, const float* __
                                                   const __half* __restrict__ dt0,
                                                   double* __restrict__ Aout, int64_t ld_a,
                                                   const IterState* st, int only_done) {
-  const int j = blockIdx.x * 128 + threadIdx.x;
-  if (j >= n) return;
   if (only_done && st->status == ST_RUNNING) return;   // not the final iterate yet
   if (only_done && st->out_done) return;   // written by the certifying pass
-  const int i0 = blockIdx.y * 32, i1 = min(n, i0 + 32);
   const int k = st->k;
-  if (k == 0) {
-    for (int i = i0; i < i1; ++i) Aout[(int64_t)i * ld_a + j] = (i == j) ? 1.0 : 0.0;
-    return;
-  }
-  if (k == 1) {   // A_1 = I + dt_0 (iteration 0 stores only the increment)
-    const float isc = exp2i(-st->sexp[0]);
-    for (int i = i0; i < i1; ++i)
-      Aout[(int64_t)i * ld_a + j] =
-          (i == j) ? 1.0 : f2d_bits(__half2float(dt0[(int64_t)i * ld + j]) * isc);
-    return;
-  }
+  const float isc = exp2i(-st->sexp[0]);
   const float* __restrict__ hi = (st->cur == 0) ? Ahi0 : Ahi1;
   const float* __restrict__ lo = (st->cur == 0) ? Alo0 : Alo1;
-  int i = i0;
-  for (; i + 8 <= i1; i += 8) {
-    float h[8], l[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      h[u] = hi[(int64_t)(i + u) * ld + j];
-      l[u] = lo[(int64_t)(i + u) * ld + j];
+  // tiles of 128 rows x 32 columns, strided over one wave of blocks (the launch
+  // that finds nothing to do then ends at once)
+  const int nrt = (n + 127) / 128, ntiles = nrt * ((n + 31) / 32);
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int j = (t % nrt) * 128 + threadIdx.x;
+    if (j >= n) continue;
+    const int i0 = (t / nrt) * 32, i1 = min(n, i0 + 32);
+    if (k == 0) {
+      for (int i = i0; i < i1; ++i) Aout[(int64_t)i * ld_a + j] = (i == j) ? 1.0 : 0.0;
+      continue;
     }
+    if (k == 1) {   // A_1 = I + dt_0 (iteration 0 stores only the increment)
+      for (int i = i0; i < i1; ++i)
+        Aout[(int64_t)i * ld_a + j] =
+            (i == j) ? 1.0 : f2d_bits(__half2float(dt0[(int64_t)i * ld + j]) * isc);
+      continue;
+    }
+    int i = i0;
+    for (; i + 8 <= i1; i += 8) {
+      float h[8], l[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) Aout[(int64_t)(i + u) * ld_a + j] = f2d_bits(h[u]) + f2d_bits(l[u]);
+      for (int u = 0; u < 8; ++u) {
+        h[u] = hi[(int64_t)(i + u) * ld + j];
+        l[u] = lo[(int64_t)(i + u) * ld + j];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        Aout[(int64_t)(i + u) * ld_a + j] = f2d_bits(h[u]) + f2d_bits(l[u]);
+    }
+    for (; i < i1; ++i)
+      Aout[(int64_t)i * ld_a + j] =
+          f2d_bits(hi[(int64_t)i * ld + j]) + f2d_bits(lo[(int64_t)i * ld + j]);
   }
-  for (; i < i1; ++i)
-    Aout[(int64_t)i * ld_a + j] = f2d_bits(hi[(int64_t)i * ld + j]) + f2d_bits(lo[(int64_t)i * ld + j]);
 }
 
 // Checks of a device-resident theta: finite, pairwise distinct (Sec. II.B: simple
 // unperturbed levels), and max |theta| into the state (the residual scale), by
-// atomicMax on the bits of a non-negative double.  Grid (256-blocks of i, 256-blocks
-// of j), upper triangle only: each block stages its 256 theta_j in shared memory and
-// thread i compares theta_i with those j > i.
+// atomicMax on the bits of a non-negative double.  Grid (256-blocks of i, 32-chunks of
+// j), upper triangle only: each block stages its 32 keys of theta_j in shared memory
+// and thread i compares theta_i with those j > i (many short blocks: the comparisons
+// spread over every SM).  The block whose chunk starts at the i-block's first index
+// also tests theta_i for finiteness, takes max |theta_i| and, when hi is given, splits
+// theta into float-float (hi, lo) as k_theta_ff does (one launch less for a device
+// theta).
 // (eq_key: 64-bit integer equality keys of finite doubles, dpt_device.cuh)
-
-// The diagonal blocks also split theta into float-float (hi, lo), as k_theta_ff does, when
-// hi is given (one launch less for a device theta).
+constexpr int kThetaChunk = 32;
 __global__ void __launch_bounds__(256) k_check_theta(int n, const double* __restrict__ th,
                                                      IterState* st, float* __restrict__ hi,
                                                      float* __restrict__ lo) {
-  if (blockIdx.y < blockIdx.x) return;
-  __shared__ unsigned long long tj[256];
-  const int i = blockIdx.x * 256 + threadIdx.x;
-  const int j0 = blockIdx.y * 256;
+  const int ib = blockIdx.x * 256, j0 = blockIdx.y * kThetaChunk;
+  if (j0 + kThetaChunk <= ib) return;   // every j of the chunk is below every i
+  __shared__ unsigned long long tj[kThetaChunk];
+  const int i = ib + threadIdx.x;
   // entries past n hold a pattern no finite value has
-  tj[threadIdx.x] = (j0 + (int)threadIdx.x < n) ? eq_key(th[j0 + threadIdx.x]) : ~0ull;
+  if (threadIdx.x < kThetaChunk)
+    tj[threadIdx.x] = (j0 + (int)threadIdx.x < n) ? eq_key(th[j0 + threadIdx.x]) : ~0ull;
   __syncthreads();
+  const bool lead = (j0 == ib);
   double amax = 0.0;
   if (i < n) {
     const double ti = th[i];
-    if (hi && blockIdx.y == blockIdx.x) {
+    if (hi && lead) {
       const float h = (float)ti;
       hi[i] = h;
       lo[i] = (float)(ti - (double)h);
     }
     if (!finite_bits(ti)) {
-      if (blockIdx.y == blockIdx.x) atomicCAS(&st->status, ST_RUNNING, ST_BADINPUT);
+      if (lead) atomicCAS(&st->status, ST_RUNNING, ST_BADINPUT);
     } else {
-      if (blockIdx.y == blockIdx.x) amax = fabs(ti);
+      if (lead) amax = fabs(ti);
       const unsigned long long ki = eq_key(ti);
-      // diagonal block: only j > i; blocks to the right: all 256
-      const int q0 = (blockIdx.y == blockIdx.x) ? (int)threadIdx.x + 1 : 0;
+      // only the j > i of the chunk
+      const int q0 = max(0, i + 1 - j0);
       bool dup = false;
 #pragma unroll 8
-      for (int q = 0; q < 256; ++q) dup |= (q >= q0) & (tj[q] == ki);
+      for (int q = 0; q < kThetaChunk; ++q) dup |= (q >= q0) & (tj[q] == ki);
       if (dup) atomicCAS(&st->status, ST_RUNNING, ST_DEGENERATE);
     }
   }
+  if (!lead) return;
   for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
   if ((threadIdx.x & 31) == 0 && amax > 0.0)
     atomicMax(reinterpret_cast<unsigned long long*>(&st->theta_max),
@@ -2057,23 +2071,34 @@ int mixed_tile_n(int n, int nsm) {
   return best;
 }
 
+// SM count of the current device, queried once (a thread-safe static initialisation:
+// several host threads launch solves); 0 if the query failed
+static int device_sms() {
+  static const int v = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 0;
+    return n;
+  }();
+  return v;
+}
+
 cudaError_t launch_delta_scales(const double* delta, int64_t ld_in, int n, const float* th_hi,
                                 const float* th_lo, double lam, int en, const double* start,
                                 int64_t ld_s, double* sinv, IterState* st, cudaStream_t s) {
   (void)lam;   // read from the state
   if (!start) {
     // one wave of resident blocks (the items are strided over it)
-    static int nsm = 0, per_sm = 0;
-    if (nsm == 0) {
-      int dev = 0, ns = 0, occ = 0;
-      cudaError_t e = cudaGetDevice(&dev);
-      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_delta_scales_rows, 256, 0);
-      if (e != cudaSuccess) return e;
-      per_sm = std::max(1, std::min(occ, 6));
-      nsm = ns;
-    }
+    static const int per_sm = [] {
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_delta_scales_rows, 256, 0) !=
+          cudaSuccess)
+        occ = 1;
+      return std::max(1, std::min(occ, 6));
+    }();
+    const int nsm = device_sms();
+    if (nsm <= 0) return cudaErrorInvalidDevice;
     const int nrb = (n + 255) / 256, ncb = (n + kScaleCols - 1) / kScaleCols;
     const long long items = (long long)nrb * ncb;
     if (items > INT_MAX) return cudaErrorInvalidValue;
@@ -2101,7 +2126,8 @@ cudaError_t launch_prep_delta(const double* delta, int64_t ld_in, int n, int ld,
 
 cudaError_t launch_check_theta(int n, const double* th, IterState* st, cudaStream_t s, float* hi,
                                float* lo) {
-  k_check_theta<<<dim3((n + 255) / 256, (n + 255) / 256), 256, 0, s>>>(n, th, st, hi, lo);
+  k_check_theta<<<dim3((n + 255) / 256, (n + kThetaChunk - 1) / kThetaChunk), 256, 0, s>>>(
+      n, th, st, hi, lo);
   return cudaGetLastError();
 }
 
@@ -2165,14 +2191,15 @@ cudaError_t launch_iter0_pairs(const CUtensorMap& tmD, const float* th_hi, const
 
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,
-                        float* dprev_col, IterState* st, cudaStream_t s, int nslot, int hilo) {
+                        float* dprev_col, IterState* st, cudaStream_t s, int nslot, int hilo,
+                        int first_step) {
   // column partials: one per 128-row tile of the product, or nslot of them (the fused
   // iteration 0's 64-row slots); row partials: one per block of kIter0Cols columns of
   // iteration 0
   const int ntm = nslot > 0 ? nslot : (n + BM - 1) / BM;
   const int ntn = (n + kIter0Cols - 1) / kIter0Cols;
   k_ctrl<<<(n + 31) / 32, 256, 0, s>>>(n, ld, ntm, ntn, part, rowpart, theta, d, E, e_col,
-                                       dprev_col, st, hilo);
+                                       dprev_col, st, hilo, first_step);
   return cudaGetLastError();
 }
 
@@ -2277,7 +2304,10 @@ cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
 cudaError_t launch_finalize(int n, int ld, const float* Ahi0, const float* Alo0,
                             const float* Ahi1, const float* Alo1, const __half* dt0, double* Aout,
                             int64_t ld_a, const IterState* st, int only_done, cudaStream_t s) {
-  dim3 grid((n + 127) / 128, (n + 31) / 32);   // 128 rows x 32 columns per block
+  const int nsm = device_sms();
+  if (nsm <= 0) return cudaErrorInvalidDevice;
+  const long long tiles = (long long)((n + 127) / 128) * ((n + 31) / 32);
+  const int grid = (int)std::min<long long>(tiles, 16LL * nsm);   // 16 blocks of 128 per SM
   k_finalize<<<grid, 128, 0, s>>>(n, ld, Ahi0, Alo0, Ahi1, Alo1, dt0, Aout, ld_a, st, only_done);
   return cudaGetLastError();
 }

@@ -247,11 +247,12 @@ cudaError_t launch_iter0_pairs(const CUtensorMap& tmD, const float* th_hi, const
                                __half* dt0, float* L, double* d, float* part, float* rowpart,
                                IterState* st, cudaStream_t s);
 // nslot > 0: the column partials are in nslot row slots (else one per 128-row tile);
-// hilo = 0: the products' diagonal partials have zero low parts (the pair kernel's)
+// hilo = 0: the products' diagonal partials have zero low parts (the pair kernel's);
+// first_step: the partials are iteration 0's (else a product's)
 cudaError_t launch_ctrl(int n, int ld, const float* part, const float* rowpart,
                         const double* theta, double* d, double* E, float* e_col,
-                        float* dprev_col, IterState* st, cudaStream_t s, int nslot = 0,
-                        int hilo = 1);
+                        float* dprev_col, IterState* st, cudaStream_t s, int nslot, int hilo,
+                        int first_step);
 cudaError_t launch_gemm_epi(const CUtensorMap& tmA, const CUtensorMap& tmB0,
                             const CUtensorMap& tmB1, const GemmEpiParams& p, cudaStream_t s);
 // The returned iterate in FP64 (A_1 = I + dt_0 is formed from the first increment dt0).

@@ -91,6 +91,51 @@ def test_degenerate_theta(dpt, prec):
     assert info["status"] == "ERR_DEGENERATE"
 
 
+# a device theta is checked on the device over 256-index blocks of i and 32-index chunks
+# of j: pairs within a chunk, across chunk and block boundaries, and in the ragged end
+@pytest.mark.parametrize("pair", [(5, 6), (40, 300), (255, 256), (31, 32), (600, 699),
+                                  (0, 699), (287, 288)])
+def test_device_theta_duplicates_found_anywhere(dpt, pair):
+    n = 700
+    cfg = inputs.full_unsymmetric(n=n)
+    th, D = _dev(cfg)
+    a, b = pair
+    th[b] = th[a]
+    _, _, info = dpt.solve_full(th, D, cfg["lam"], prec="mixed", check=False)
+    assert info["status"] == "ERR_DEGENERATE", (pair, info)
+
+
+@pytest.mark.parametrize("where,value", [(0, float("nan")), (257, float("inf")),
+                                         (699, float("-inf")), (32, float("nan"))])
+def test_device_theta_nonfinite_rejected(dpt, where, value):
+    n = 700
+    cfg = inputs.full_unsymmetric(n=n)
+    th, D = _dev(cfg)
+    th[where] = value
+    _, _, info = dpt.solve_full(th, D, cfg["lam"], prec="mixed", check=False)
+    assert info["status"] == "ERR_ARG", (where, info)
+
+
+def test_device_theta_signed_zeros_are_equal(dpt):
+    n = 300
+    cfg = inputs.full_unsymmetric(n=n)
+    th, D = _dev(cfg)
+    th[10], th[270] = 0.0, -0.0
+    _, _, info = dpt.solve_full(th, D, cfg["lam"], prec="mixed", check=False)
+    assert info["status"] == "ERR_DEGENERATE"
+
+
+def test_device_theta_adjacent_doubles_are_distinct(dpt):
+    """theta_j one ulp above theta_i is a distinct level: the check must not flag it
+    (the solve itself may then fail to converge, with the gap at rounding level)."""
+    n = 300
+    cfg = inputs.full_unsymmetric(n=n)
+    th, D = _dev(cfg)
+    th[200] = float(np.nextafter(float(th[40]), np.inf))
+    _, _, info = dpt.solve_full(th, D, cfg["lam"], prec="mixed", check=False, max_iter=3)
+    assert info["status"] not in ("ERR_DEGENERATE", "ERR_ARG"), info
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_nonfinite_delta_rejected(dpt, prec):
     cfg = inputs.full_unsymmetric(n=40)
