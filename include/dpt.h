@@ -191,6 +191,12 @@ typedef struct {
                               gaps and products) on those columns only, until its step is
                               below refine_tol / 8 (each column is its own map,
                               Sec. II.B); dpt_info reports them. */
+  int32_t pair_clusters;   /* mixed real full solve in the CTA-pair form: 0 (default)
+                              runs as many clusters as can be resident; k > 0 at most k
+                              (the tile schedule of a large problem on a small one:
+                              several tiles per cluster and, where they cut the padding,
+                              column tiles of two widths).  Results agree with the
+                              default to rounding (the tiles' K orders differ). */
 } dpt_options;
 
 typedef struct {

@@ -536,6 +536,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
       npairs = std::min(nsm / 2, mixed_pair_clusters(2));
       ctas = 2;
     }
+    if (npairs > 0 && o.pair_clusters > 0) npairs = std::min(npairs, (int)o.pair_clusters);
     const bool pair = npairs > 0;
     IterState h{};
     h.status = ST_RUNNING;
@@ -597,6 +598,11 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
     GemmEpiParams p;
     std::memset(&p, 0, sizeof(p));   // padding too: the bytes are part of the graph key
     p.n = n; p.ld = ld; p.ntm = ntm; p.bn = bn; p.lam = (float)lambda;
+    p.nw = (n + bn - 1) / bn;
+    if (pair) mixed_pair_split((int)n, bn, npairs, ctas, &p.nw, &p.nnar);
+    // the narrow tiles' increment maps (the wide ones stand in when there are none)
+    const CUtensorMap tB0n = p.nnar > 0 ? make_tmap_f16(dtb[0], n, n, ld, bn / 2 - 16) : tB0;
+    const CUtensorMap tB1n = p.nnar > 0 ? make_tmap_f16(dtb[1], n, n, ld, bn / 2 - 16) : tB1;
     for (int q = 0; q < 2; ++q) { p.A_hi[q] = Ahi[q]; p.A_lo[q] = Alo[q]; p.dt[q] = dtb[q]; }
     p.L = L; p.Dcat = Dcat; p.cat_ld = (int64_t)3 * ld; p.th_hi = thh; p.th_lo = thl; p.e_col = e_col; p.dprev_col = dprev;
     p.part = part; p.st = st;
@@ -628,6 +634,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
       };
       put(&p, sizeof(p));
       put(&tA, sizeof(tA)); put(&tB0, sizeof(tB0)); put(&tB1, sizeof(tB1));
+      put(&tB0n, sizeof(tB0n)); put(&tB1n, sizeof(tB1n));
       const int64_t scal[7] = {n, ld, npairs, ctas, pair ? 1 : 0, e_dev ? 1 : 0, o.graph_iters};
       put(scal, sizeof(scal));
       const void* ptrs[12] = {part, rowpart, thd, d, E, e_col, dprev, st, Astage, E_out,
@@ -635,7 +642,7 @@ dpt_status solve_full_mixed_real(int64_t n64, const std::vector<double>& th,
       put(ptrs, sizeof(ptrs));
       run_loop(b, st, o.graph_iters, o.max_iter, 2, prof, [&](int q) {
         prof.before(q, s);
-        if (pair) CK(launch_gemm_epi_pair(tA, tB0, tB1, p, npairs, ctas, s));
+        if (pair) CK(launch_gemm_epi_pair(tA, tB0, tB1, tB0n, tB1n, p, npairs, ctas, s));
         else CK(launch_gemm_epi(tA, tB0, tB1, p, s));
         prof.after(q, s);
         CK(launch_ctrl(n, ld, part, rowpart, thd, d, E, e_col, dprev, st, s, 0, pair ? 0 : 1, 0));
@@ -1890,6 +1897,7 @@ void dpt_options_default(dpt_options* o) {
   o->ld_start = 0;
   o->certify = 1;
   o->refine_tol = 1e-10;
+  o->pair_clusters = 0;
 }
 
 int64_t dpt_workspace_bytes(int64_t n, dpt_dtype dtype, dpt_prec prec) {

@@ -1379,19 +1379,37 @@ __device__ __forceinline__ void epi_prefetch(const GemmEpiParams& p, bool c1, bo
   }
 }
 
+// Tile t of the CTA-pair kernel's order.  The column tiles are p.nw wide ones (p.bn
+// columns) and then p.nnar narrow ones (p.bn - 32 columns, from column p.nw p.bn on),
+// which together cover n with less padding than one width alone; the order takes
+// every row block's wide tiles first, so that the round-robin over the clusters gives
+// no cluster more than one wide tile above another and leaves the narrow tiles, with
+// their shorter epilogues, for the last round.
+struct PairTile {
+  int tmc;   // row block (of CR x 128 rows)
+  int n0;    // first column
+  int w;     // width
+};
+__device__ __forceinline__ PairTile pair_tile(const GemmEpiParams& p, int t, int ntmc) {
+  const int tw = ntmc * p.nw;
+  if (t < tw) return {t / p.nw, (t % p.nw) * p.bn, p.bn};
+  const int u = t - tw;
+  return {u / p.nnar, p.nw * p.bn + (u % p.nnar) * (p.bn - 32), p.bn - 32};
+}
+
 // Copies of sub-chunk u of this tile, or, for u >= nsub, of sub-chunk u - nsub of the
 // CTA's next tile t_next; then one commit group (empty when there is nothing to copy).
 __device__ __forceinline__ void epi_prefetch_at(const GemmEpiParams& p, bool c1, bool cert,
                                                 bool a1, int S, uint8_t* eb, int ew, int lane,
                                                 bool work, int m0, int n0, int u, int nsub,
-                                                int t_next, int ntiles, int ntn, int bn,
-                                                int crank, int cr) {
+                                                int t_next, int ntiles, int ntmc, int crank,
+                                                int cr) {
   if (u < nsub) {
     if (work) epi_prefetch(p, c1, cert, a1, S, eb, ew, lane, m0, n0, u);
   } else if (t_next < ntiles) {
-    const int tm = cr * (t_next / ntn) + crank;
-    if (tm < p.ntm)
-      epi_prefetch(p, c1, cert, a1, S, eb, ew, lane, tm * BM, (t_next % ntn) * bn, u - nsub);
+    const PairTile nt = pair_tile(p, t_next, ntmc);
+    const int tm = cr * nt.tmc + crank;
+    if (tm < p.ntm) epi_prefetch(p, c1, cert, a1, S, eb, ew, lane, tm * BM, nt.n0, u - nsub);
   }
   cp_async_commit();
 }
@@ -1634,6 +1652,8 @@ __device__ __forceinline__ void warp_sum3x2(float (&a)[3], const float (&b)[3], 
 template <bool QUAD, bool MERGED>
 __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const CUtensorMap& tmB0,
                                                    const CUtensorMap& tmB1,
+                                                   const CUtensorMap& tmB0n,
+                                                   const CUtensorMap& tmB1n,
                                                    const GemmEpiParams& p) {
   extern __shared__ uint8_t smem_raw[];
   IterState* st = p.st;
@@ -1650,10 +1670,9 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
   const uint32_t crank = cluster_ctarank();
   const uint32_t rank = crank & 1u;      // rank within the pair
   const uint32_t lead = crank & ~1u;     // cluster rank of the pair's leader
-  const int bn = p.bn, bh = bn / 2;
-  const int ntn = (p.n + bn - 1) / bn;
+  const int bn = p.bn, bh = bn / 2;   // the wide tiles (the ring's stage size)
   const int ntmc = (p.n + CR * BM - 1) / (CR * BM);
-  const int ntiles = ntn * ntmc;
+  const int ntiles = (p.nw + p.nnar) * ntmc;
   const int pair = blockIdx.x / CR, npairs = gridDim.x / CR;   // clusters
 
   if (threadIdx.x == 0) {
@@ -1697,24 +1716,31 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
   uint8_t* EB = smem + P_RREG;
   uint8_t* EB2 = merged ? EB : smem + ring_bytes;
   const CUtensorMap* tmB = (ms->cur == 1) ? &tmB0 : &tmB1;
+  const CUtensorMap* tmBn = (ms->cur == 1) ? &tmB0n : &tmB1n;   // boxes of bn/2 - 16 rows
   unsigned* tflag = &st->timeout;
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer (every CTA): A completes on the leader's full[s] ----
     prefetch_tmap(&tmA);
     prefetch_tmap(tmB);
+    if (p.nnar > 0) prefetch_tmap(tmBn);
     const uint32_t full_leader = mapa_shared(&ms->full[0], lead);
     uint32_t it = 0;
     bool alive = true;
     for (int t = pair; t < ntiles && alive; t += npairs) {
-      const int tmc = t / ntn, tn = t % ntn;
-      const int m0 = tmc * CR * BM + (int)crank * BM, n0 = tn * bn;
-      const int kb_last = min(kb_per_slice - 1, (n0 + bn - 1) / BK);
+      const PairTile pt = pair_tile(p, t, ntmc);
+      const int m0 = pt.tmc * CR * BM + (int)crank * BM, n0 = pt.n0;
+      // a narrow tile loads B halves of its own width (a smaller stage)
+      const bool wide = pt.w == bn;
+      const int bh_t = pt.w / 2;
+      const CUtensorMap* tb = wide ? tmB : tmBn;
+      const uint32_t tx = 2u * ((uint32_t)(na * A_TILE) + (uint32_t)bh_t * BK * 2);
+      const int kb_last = min(kb_per_slice - 1, (n0 + pt.w - 1) / BK);
       for (int q = 0; q < nk; ++q, ++it) {
         const int s = it % nst;
         const uint32_t ph = (it / nst) & 1;
         if (!mbar_wait(&ms->empty[s], ph ^ 1, tflag)) { alive = false; break; }
-        if (rank == 0) mbar_arrive_expect_tx(&ms->full[s], 2 * stage_bytes);
+        if (rank == 0) mbar_arrive_expect_tx(&ms->full[s], tx);
         // small slices first, the tile's diagonal K-blocks last (see k_gemm_epi); with
         // both slices in a stage, slice 1 before slice 0 within each K-block
         const int kb = (kb_last + 1 + q % kb_per_slice) % kb_per_slice;
@@ -1729,9 +1755,9 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
         }
         uint8_t* bslot = slot + na * A_TILE;
         if (!QUAD)
-          tma_load_2d_pair(bslot, tmB, fb, kb * BK, n0 + (int)rank * bh);
+          tma_load_2d_pair(bslot, tb, fb, kb * BK, n0 + (int)rank * bh_t);
         else if (crank < 2)
-          tma_load_2d_pair_multicast(bslot, tmB, fb, kb * BK, n0 + (int)rank * bh,
+          tma_load_2d_pair_multicast(bslot, tb, fb, kb * BK, n0 + (int)rank * bh_t,
                                      (uint16_t)((1u << crank) | (4u << crank)));
       }
     }
@@ -1740,11 +1766,13 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
       mbar_wait_quiet(&ms->empty[u % nst], (u / nst) & 1, kTailWaitNs);
   } else if (warp == 1 && lane == 0 && rank == 0) {
     // ---- MMA issuer (pair leaders only) ----
-    const uint32_t idesc = idesc_f16_f32(2 * BM, bn);
+    const uint32_t idesc_w = idesc_f16_f32(2 * BM, bn);
+    const uint32_t idesc_n = idesc_f16_f32(2 * BM, bn - 32);
     uint32_t it = 0;
     int lt = 0;
     bool alive = true;
     for (int t = pair; t < ntiles && alive; t += npairs, ++lt) {
+      const uint32_t idesc = (t < ntmc * p.nw) ? idesc_w : idesc_n;   // see pair_tile
       const int b = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
       if (!mbar_wait(&ms->acc_empty[b], (use & 1) ^ 1, tflag)) break;
@@ -1787,7 +1815,6 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
     const bool cert = ms->certify != 0;
     const bool a1 = ms->k == 1;            // A_1 = I + dt_0 is formed from dt_0
     const int mode = cert ? 2 : (a1 ? 1 : 0);
-    const int nsub = bn / 16;              // sub-chunks per tile (even: bn is a multiple of 32)
     const float cs = exp2i(ms->scur), cd = exp2i(ms->sig);
     EpiConst kc;
     kc.lam = (p.lam * exp2i(-ms->sig)) * exp2i(-ms->scur);
@@ -1802,25 +1829,26 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
     // lane copies and reads only its own slots).  The first tile's first sub-chunks,
     // while its products run:
     const int ahead = merged ? 1 : 2;
-    for (int u = 0; u < ahead; ++u)
-      epi_prefetch_at(p, c1, cert, a1, S, (u & 1) ? EB2 : EB, ew, lane,
-                      pair < ntiles && CR * (pair / ntn) + (int)crank < p.ntm,
-                      (CR * (pair / ntn) + (int)crank) * BM, (pair % ntn) * bn, u, nsub, pair,
-                      ntiles, ntn, bn, (int)crank, CR);
+    for (int u = 0; u < ahead; ++u)   // the first tile's (as the "next" of none)
+      epi_prefetch_at(p, c1, cert, a1, S, (u & 1) ? EB2 : EB, ew, lane, false, 0, 0, u, 0,
+                      pair, ntiles, ntmc, (int)crank, CR);
     for (int t = pair; t < ntiles; t += npairs, ++lt) {
-      const int tmc = t / ntn, tn = t % ntn;
-      const int tm = CR * tmc + (int)crank;
-      const int m0 = tm * BM, n0 = tn * bn;
+      const PairTile pt = pair_tile(p, t, ntmc);
+      const int tm = CR * pt.tmc + (int)crank;
+      const int m0 = tm * BM, n0 = pt.n0;
+      const bool work = tm < p.ntm;        // rows of a pair tile beyond the padded matrix
+      // the tile's width (see pair_tile), a multiple of 32
+      const int w = bn - ((t >= ntmc * p.nw) ? 32 : 0);
+      const int nsub = w / 16;             // sub-chunks of the tile
       const int b = lt & 1;
       const uint32_t use = (uint32_t)(lt >> 1);
-      const bool work = tm < p.ntm;        // rows of a pair tile beyond the padded matrix
       // per-element masks only where the tile holds a diagonal element or rows beyond n
-      const bool check = (m0 + BM > p.n) || (n0 < m0 + BM && m0 < n0 + bn);
+      const bool check = (m0 + BM > p.n) || (n0 < m0 + BM && m0 < n0 + w);
       // theta_j of this lane's four rows (padded arrays: rows up to ld exist)
       const float4 thj_h = work ? ld4(p.th_hi + m0 + 4 * lane) : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 thj_l = work ? ld4(p.th_lo + m0 + 4 * lane) : make_float4(0.f, 0.f, 0.f, 0.f);
       p_epi_bar();
-      if (et < bn) {
+      if (et < w) {
         const int i = n0 + et;
         const bool v = i < p.n;
         ms->e[et] = v ? (p.e_col[i] * cd) * cs : 0.f;   // e_k 2^sig 2^scur
@@ -1833,7 +1861,7 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
       const uint32_t src = tmem + (uint32_t)(b * BN) + ((uint32_t)(qd * 32) << 16);
       bool all_ok = true;
 #pragma unroll 1
-      for (int c0 = 0; c0 < bn; c0 += XCH) {
+      for (int c0 = 0; c0 < w; c0 += XCH) {
         if (c0 > 0) p_epi_bar();
         if (ok) {
           float x[8];
@@ -1842,9 +1870,9 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
 #pragma unroll
           for (int c = 0; c < 8; ++c) Xs[(cc + c) * BM + qd * 32 + lane] = x[c];
         }
-        if (c0 + XCH == bn) tc_fence_before();
+        if (c0 + XCH == w) tc_fence_before();
         all_ok = p_epi_bar_and(ok);
-        if (c0 + XCH == bn && et == 0) {
+        if (c0 + XCH == w && et == 0) {
           if (rank == 0) mbar_arrive(&ms->acc_empty[b]);
           else mbar_arrive_remote(acc_empty_leader + (uint32_t)b * 8u);
         }
@@ -1871,7 +1899,7 @@ __device__ __forceinline__ void gemm_epi_pair_body(const CUtensorMap& tmA, const
             }
           }
           epi_prefetch_at(p, c1, cert, a1, S, eb, ew, lane, work, m0, n0, sc + ahead, nsub,
-                          t + npairs, ntiles, ntn, bn, (int)crank, CR);
+                          t + npairs, ntiles, ntmc, (int)crank, CR);
         }
         if (work) {
           // this warp's two columns of the chunk, reduced together
@@ -1922,16 +1950,20 @@ __device__ __forceinline__ bool two_slice_stages(const IterState* st) {
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(P_NTHREADS, 1)
 k_gemm_epi_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
-                const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
-  if (two_slice_stages(p.st)) gemm_epi_pair_body<false, true>(tmA, tmB0, tmB1, p);
-  else gemm_epi_pair_body<false, false>(tmA, tmB0, tmB1, p);
+                const __grid_constant__ CUtensorMap tmB1,
+                const __grid_constant__ CUtensorMap tmB0n,
+                const __grid_constant__ CUtensorMap tmB1n, const GemmEpiParams p) {
+  if (two_slice_stages(p.st)) gemm_epi_pair_body<false, true>(tmA, tmB0, tmB1, tmB0n, tmB1n, p);
+  else gemm_epi_pair_body<false, false>(tmA, tmB0, tmB1, tmB0n, tmB1n, p);
 }
 
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(P_NTHREADS, 1)
 k_gemm_epi_quad(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB0,
-                const __grid_constant__ CUtensorMap tmB1, const GemmEpiParams p) {
-  if (two_slice_stages(p.st)) gemm_epi_pair_body<true, true>(tmA, tmB0, tmB1, p);
-  else gemm_epi_pair_body<true, false>(tmA, tmB0, tmB1, p);
+                const __grid_constant__ CUtensorMap tmB1,
+                const __grid_constant__ CUtensorMap tmB0n,
+                const __grid_constant__ CUtensorMap tmB1n, const GemmEpiParams p) {
+  if (two_slice_stages(p.st)) gemm_epi_pair_body<true, true>(tmA, tmB0, tmB1, tmB0n, tmB1n, p);
+  else gemm_epi_pair_body<true, false>(tmA, tmB0, tmB1, tmB0n, tmB1n, p);
 }
 
 // ---------------------------------------------------------------------------
@@ -2273,15 +2305,47 @@ int mixed_pair_tile_n(int n, int nclusters, int ctas) {
   return best;
 }
 
+// The split of the columns into p.nw tiles of bn and nnar tiles of bn - 32 (see
+// pair_tile): as many narrow tiles as the padding of ceil(n / bn) wide ones leaves
+// room for, where the round-robin over the clusters then ends sooner (the same cost
+// model as mixed_pair_tile_n: a tile costs its width plus 64).
+void mixed_pair_split(int n, int bn, int nclusters, int ctas, int* nw, int* nnar) {
+  const int ntn = (n + bn - 1) / bn;
+  const int ntmc = (n + ctas * BM - 1) / (ctas * BM);
+  *nw = ntn;
+  *nnar = 0;
+  if (bn - 32 < 64 || nclusters < 1) return;
+  const int bmax = std::min(ntn - 1, (ntn * bn - n) / 32);
+  long long best = -1;
+  for (int b = 0; b <= bmax; ++b) {
+    const int a = ntn - b;
+    const long long wide = (long long)ntmc * a, all = (long long)ntmc * ntn;
+    // the busiest cluster: the first (all % nclusters) clusters take one tile more;
+    // wide tiles come first in the order
+    long long worst = 0;
+    for (int c = 0; c < nclusters && c < all; ++c) {
+      const long long cnt = (all - c + nclusters - 1) / nclusters;   // tiles c, c + ncl, ..
+      const long long nwide = wide > c ? std::min(cnt, (wide - c + nclusters - 1) / nclusters) : 0;
+      worst = std::max(worst, nwide * (bn + 64) + (cnt - nwide) * (bn - 32 + 64));
+    }
+    if (best < 0 || worst < best) { best = worst; *nw = a; *nnar = b; }
+  }
+}
+
 cudaError_t launch_gemm_epi_pair(const CUtensorMap& tmA, const CUtensorMap& tmB0,
-                                 const CUtensorMap& tmB1, const GemmEpiParams& p, int nclusters,
+                                 const CUtensorMap& tmB1, const CUtensorMap& tmB0n,
+                                 const CUtensorMap& tmB1n, const GemmEpiParams& p, int nclusters,
                                  int ctas, cudaStream_t s) {
-  if (p.bn < 64 || p.bn > BN || p.bn % 32 || nclusters < 1 || (ctas != 2 && ctas != 4))
+  if (p.bn < 64 || p.bn > BN || p.bn % 32 || nclusters < 1 || (ctas != 2 && ctas != 4) ||
+      p.nw < 1 || p.nnar < 0 || (p.nnar > 0 && p.bn - 32 < 64) ||
+      (long long)p.nw * p.bn + (long long)p.nnar * (p.bn - 32) < p.n)
     return cudaErrorInvalidValue;
-  const int ntiles = ((p.n + p.bn - 1) / p.bn) * ((p.n + ctas * BM - 1) / (ctas * BM));
+  const int ntiles = (p.nw + p.nnar) * ((p.n + ctas * BM - 1) / (ctas * BM));
   const int ncl = ntiles < nclusters ? ntiles : nclusters;
-  if (ctas == 4) k_gemm_epi_quad<<<4 * ncl, P_NTHREADS, P_SMEM_BYTES, s>>>(tmA, tmB0, tmB1, p);
-  else k_gemm_epi_pair<<<2 * ncl, P_NTHREADS, P_SMEM_BYTES, s>>>(tmA, tmB0, tmB1, p);
+  if (ctas == 4)
+    k_gemm_epi_quad<<<4 * ncl, P_NTHREADS, P_SMEM_BYTES, s>>>(tmA, tmB0, tmB1, tmB0n, tmB1n, p);
+  else
+    k_gemm_epi_pair<<<2 * ncl, P_NTHREADS, P_SMEM_BYTES, s>>>(tmA, tmB0, tmB1, tmB0n, tmB1n, p);
   return cudaGetLastError();
 }
 

@@ -206,6 +206,8 @@ struct GemmEpiParams {
   double* Aout;        // FP64 output (column-major, ld_a), written by certifying passes
   int64_t ld_a;        // of the pair kernel (IterState::cert_out)
   int aout_v8;         // Aout 32-byte aligned and ld_a a multiple of 4 (32-byte stores)
+  int nw;              // pair kernel: column tiles of width bn, then
+  int nnar;            //   nnar of width bn - 32 (mixed_pair_split)
 };
 
 int mixed_smem_bytes();
@@ -213,8 +215,11 @@ int mixed_tile_n(int n, int nsm);   // columns per output tile of the product ke
 // CTA-pair forms: clusters of `ctas` = 2 (one pair) or 4 (two pairs sharing B)
 int mixed_pair_clusters(int ctas);  // resident clusters of that shape (after mixed_set_attributes)
 int mixed_pair_tile_n(int n, int nclusters, int ctas);
+void mixed_pair_split(int n, int bn, int nclusters, int ctas, int* nw, int* nnar);
+// tmB0n / tmB1n: the increment maps with boxes of bn / 2 - 16 rows (the narrow tiles)
 cudaError_t launch_gemm_epi_pair(const CUtensorMap& tmA, const CUtensorMap& tmB0,
-                                 const CUtensorMap& tmB1, const GemmEpiParams& p, int nclusters,
+                                 const CUtensorMap& tmB1, const CUtensorMap& tmB0n,
+                                 const CUtensorMap& tmB1n, const GemmEpiParams& p, int nclusters,
                                  int ctas, cudaStream_t s);
 cudaError_t mixed_set_attributes();   // once per device, before any capture
 // max |Delta| and max |Delta_ji / (theta_i - theta_j)| (j != i); sets the scales of

@@ -36,7 +36,7 @@ class Options(ctypes.Structure):
                 ("cta_pair", ctypes.c_int32), ("grouped_form", ctypes.c_int32),
                 ("ramp_alpha", ctypes.c_double), ("start", ctypes.c_void_p),
                 ("ld_start", ctypes.c_int64), ("certify", ctypes.c_int32),
-                ("refine_tol", ctypes.c_double)]
+                ("refine_tol", ctypes.c_double), ("pair_clusters", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -273,7 +273,8 @@ def _iscomplex(x) -> bool:
 def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
                epstein_nesbet=False, graph_iters=None, max_slices=None, slice_tol=None,
                profile=False, cta_pair=None, ramp_alpha=None, start=None, certify=None,
-               refine_tol=None, A_out=None, E_out=None, stream=None, check=True):
+               refine_tol=None, pair_clusters=None, A_out=None, E_out=None, stream=None,
+               check=True):
     """All eigenpairs of M = diag(theta) + lam * Delta by the DPT map (dpt_solve_full).
 
     Returns (A, E, info): A[:, i] is eigenvector i with A[i, i] = 1 and
@@ -291,7 +292,8 @@ def solve_full(theta, delta, lam, *, prec="mixed", tol=1e-12, max_iter=200,
                 graph_iters=graph_iters, max_slices=max_slices, slice_tol=slice_tol,
                 profile=int(bool(profile)), cta_pair=None if cta_pair is None else int(cta_pair),
                 ramp_alpha=ramp_alpha, certify=None if certify is None else int(bool(certify)),
-                refine_tol=refine_tol)
+                refine_tol=refine_tol,
+                pair_clusters=None if pair_clusters is None else int(pair_clusters))
     s_keep = None
     if start is not None:
         s_ptr, s_ld, s_keep = _colmajor(start, cplx)

@@ -156,3 +156,41 @@ def test_workspace_bytes_without_gpu(lib):
     assert lib.dpt_workspace_bytes((1 << 20) + 1, 0, 1) == -1
     assert lib.dpt_workspace_bytes(16, 7, 1) == -1
     assert lib.dpt_workspace_bytes(16, 0, 9) == -1
+
+
+# ctypes mirrors of the header's structs (field names as in C but for `lambda`, a
+# Python keyword)
+_STRUCTS = [("Options", "dpt_options"), ("Info", "dpt_info"), ("ServerCfg", "dpt_server_cfg"),
+            ("Problem", "dpt_problem"), ("ServerStats", "dpt_server_stats")]
+_RENAME = {("Problem", "lam"): "lambda"}
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every field of the binding's ctypes structs sits at the offset a C compiler
+    gives it from include/dpt.h, and the sizes agree (a mismatch would make the
+    library write past the binding's buffers)."""
+    import shutil
+    import subprocess
+    from paper_2002_12872_gb300 import dpt
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dpt.h"', 'int main(void) {']
+    for py, c in _STRUCTS:
+        lines.append(f'  printf("{py} . %zu\\n", sizeof({c}));')
+        for f, _ in getattr(dpt, py)._fields_:
+            cf = _RENAME.get((py, f), f)
+            lines.append(f'  printf("{py} {f} %zu\\n", offsetof({c}, {cf}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(v) for a, b, v in (ln.split() for ln in out if ln.strip())}
+    for py, _ in _STRUCTS:
+        cls = getattr(dpt, py)
+        assert got[(py, ".")] == ctypes.sizeof(cls), py
+        for f, _ in cls._fields_:
+            assert got[(py, f)] == getattr(cls, f).offset, (py, f)

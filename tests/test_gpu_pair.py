@@ -82,3 +82,30 @@ def test_two_slice_stages_keep_the_accuracy(ora, dpt, n, rep):
         errs.append(vec_err(to_np(A), Ao))
     assert errs[0] <= 1.25 * errs[1] + 1e-12, errs
     assert errs[0] <= VEC_TOL, errs
+
+
+# Few clusters (pair_clusters): several tiles per cluster and, where they cut the
+# padding, column tiles of two widths (bn, then bn - 32; the narrow ones load
+# increment boxes of their own height).  In each case here the schedule has narrow
+# tiles (14 wide and 5 narrow ones per row block at the bench's n = 4096); the last
+# case of each form keeps one width.
+@pytest.mark.parametrize("form,n,clusters", [(1, 390, 3), (1, 520, 2), (1, 1000, 5),
+                                             (1, 1200, 3), (1, 777, 2), (2, 390, 1),
+                                             (2, 700, 2), (2, 1000, 5), (2, 1500, 3),
+                                             (2, 1000, 2)])
+def test_few_clusters_two_tile_widths(ora, dpt, form, n, clusters):
+    cfg = inputs.full_unsymmetric(n=n, rep=13)
+    th, D = _dev(cfg, dpt)
+    A, E, info = dpt.solve_full(th, D, cfg["lam"], cta_pair=form, pair_clusters=clusters)
+    Ao, Eo, io = ora.solve_full(cfg["theta"], cfg["delta"], cfg["lam"], tol=1e-13)
+    assert info["status"] == "OK" and io["status"] == "OK" and info["cta_pair"] == form
+    assert eig_err(to_np(E), Eo) <= EIG_RTOL, (n, clusters, info)
+    assert vec_err(to_np(A), Ao) <= VEC_TOL, (n, clusters, info)
+    # against the schedule over every resident cluster: the tile widths differ, and
+    # with them the K order of every accumulation (each tile takes its diagonal
+    # K-blocks last), so the two differ by the rounding of two orders: at most twice
+    # the accumulation error each keeps against the fixed point (VEC_TOL / 2 here)
+    A2, E2, i2 = dpt.solve_full(th, D, cfg["lam"], cta_pair=form)
+    E, E2 = to_np(E), to_np(E2)
+    assert np.max(np.abs(E - E2) / np.maximum(1.0, np.abs(E2))) <= 1e-11
+    assert vec_err(to_np(A), to_np(A2)) <= VEC_TOL / 2
