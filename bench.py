@@ -1065,7 +1065,9 @@ def run_ours(args, world, rank, local):
     D_h = dpt.colmajor_tensor(cfg["delta"], pin=True)   # column-major pinned buffer
     A_h = torch.empty((N, N), dtype=torch.float64).pin_memory().t()
     E_h = torch.empty((N,), dtype=torch.float64).pin_memory()
-    e2e_steps = max(4, min(args.steps, 20))
+    # enough solves that the first input copy and the last output copy (about 1.3 ms,
+    # which no other solve overlaps) are a small part of the timed region
+    e2e_steps = max(4, min(args.steps, 60))
     outs_h = [(A_h, E_h)] + [(torch.empty((N, N), dtype=torch.float64).pin_memory().t(),
                               torch.empty((N,), dtype=torch.float64).pin_memory())
                              for _ in range(nstr - 1)]
